@@ -1,0 +1,309 @@
+"""Benchmark: G + grad G path-steps/s of the two-step MC-AAD algorithm on GB300.
+
+One step = one mc_value_and_grad call (forward sweep, E y / lambda / G,
+reverse sweep with recompute, grad G) over the Heston workload: 2^20 paths x
+512 steps (Delta = 1/256, 2y), 64 calls, FP32 paths, FP64 sums.  The metric is
+path-steps per second, P * S / (time per step).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs under torchrun: rank r evaluates its own independent path range
+[r P, (r+1) P) (weak scaling, no collective inside the timed region).
+--impl reference times the FP64 CPU oracle on a bounded sample instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "G+grad G path-steps/s (Heston FT, 2^20 paths x 512 steps, m=64, M=5)"
+UNIT = "path-steps/s"
+
+# Algorithmic ALU operations per path-step, counted from the formulas with
+# ideal fusion (one FMA per a*b+c, one wide multiply for both halves of a
+# 32x32 product, one three-input logic op, one MUFU per log2/sqrt/rsqrt/sin/cos):
+#   Philox-4x32-10: 10 rounds x (2 wide multiplies + 2 xor3) per block of 4
+#     normals -> 20 INT per Heston step (2 normals);
+#   uniforms: 2 x (bit op + or) INT, 2 FADD;
+#   Box-Muller pair: FP32 7 (scale of log, clamp, shift, 2 angle scalings,
+#     2 products), MUFU 4 (lg2, sqrt, sin, cos);
+#   Heston full-truncation step: FP32 13, MUFU 1 (rsqrt);
+#   => F = 22 FP32 + 5 MUFU + 24 INT = 51 ops;
+#   Heston adjoint step R: 17 FP32.
+# Forward kernel runs F; reverse kernel runs F (recompute) + R.
+OPS = {"forward_sweep": {"fp32": 22, "mufu": 5, "int": 24},
+       "reverse_sweep": {"fp32": 39, "mufu": 5, "int": 24}}
+
+
+def _ops(kernel):
+    return sum(OPS[kernel].values())
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if not self.proc:
+            return out
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return out
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "", 1).isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "", 1).isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        loaded = [s for s in sm if mx and s > 0.5 * max(mx)] or sm
+        out.update(sm_mhz=statistics.median(loaded) if loaded else None,
+                   sm_max_mhz=max(mx) if mx else None, reasons=reasons, samples=len(rows))
+        return out
+
+
+def cpu_baseline(workload, n_paths, threads=None):
+    """The FP64 oracle's value_and_grad on a bounded sample of the same workload."""
+    import oracle
+    oracle.build()
+    threads = threads or os.cpu_count() or 1
+    pb = workload.problem
+    t0 = time.perf_counter()
+    oracle.value_and_grad(pb, workload.theta, workload.C, n_paths, n_threads=threads)
+    dt = time.perf_counter() - t0
+    steps = pb.last_step
+    return {"value": n_paths * steps / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": "%d of the workload's paths x %d steps, FP64, value+grad, %.1f s wall" % (n_paths, steps, dt)}
+
+
+def dist_setup(n_gpus):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(0)
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def run_reference(args):
+    """The oracle timed on the host cores, as the reference arm."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_1901_04200_gb300 import inputs
+    w = inputs.heston_config()
+    n = args.ref_paths
+    for _ in range(args.warmup):
+        cpu_baseline(w, max(n // 8, 256))
+    vals = [cpu_baseline(w, n) for _ in range(args.steps)]
+    v = statistics.median(x["value"] for x in vals)
+    ms = w.problem.last_step * w.n_paths / v * 1e3
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": w.name, "paths": w.n_paths, "steps": w.problem.last_step,
+                       "sample_paths_per_step": n},
+            "cpu_baseline": dict(vals[0], value=v),
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--paths", type=int, default=1 << 20)
+    ap.add_argument("--cpu-paths", type=int, default=1 << 16)
+    ap.add_argument("--ref-paths", type=int, default=1 << 15)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+
+    from paper_1901_04200_gb300 import _lib, inputs
+    from paper_1901_04200_gb300 import build as _build
+
+    rank, world, local = dist_setup(args.gpus)
+    if rank == 0:
+        _build.build()
+    barrier(world)
+    w = inputs.heston_config(n_paths=args.paths)
+    pb, P, S = w.problem, w.n_paths, w.problem.last_step
+    path0 = rank * P
+    dev = torch.device("cuda", torch.cuda.current_device())
+    ctx = _lib.Context(pb, max_paths=P, device=dev)
+    theta = torch.tensor(w.theta, dtype=torch.float64, device=dev)
+    C = torch.tensor(w.C, dtype=torch.float64, device=dev)
+    out = (torch.empty(1, dtype=torch.float64, device=dev), torch.empty(ctx.M, dtype=torch.float64, device=dev),
+           torch.empty(ctx.m, dtype=torch.float64, device=dev))
+    seed = pb.seed
+    stream = torch.cuda.current_stream()
+
+    def step():
+        ctx.value_and_grad(theta, C, seed, P, path0=path0, out=out)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+
+    # ---------------- device-timed region (inputs resident in HBM)
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    barrier(world)
+    torch.cuda.synchronize()
+    ctx.profile_begin(8 * args.steps)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    prof = ctx.profile_end()
+    ms_total = e0.elapsed_time(e1)
+    # ---------------- end to end: host buffers in, host results out, every step
+    th_h = torch.tensor(w.theta, dtype=torch.float64).pin_memory()
+    C_h = torch.tensor(w.C, dtype=torch.float64).pin_memory()
+    res_h = torch.empty(1 + ctx.M + ctx.m, dtype=torch.float64).pin_memory()
+    th_d = torch.empty_like(theta)
+    C_d = torch.empty_like(C)
+    res_d = torch.empty(1 + ctx.M + ctx.m, dtype=torch.float64, device=dev)
+    outs = (res_d[0:1], res_d[1:1 + ctx.M], res_d[1 + ctx.M:])
+
+    def e2e_step():
+        th_d.copy_(th_h, non_blocking=True)
+        C_d.copy_(C_h, non_blocking=True)
+        ctx.value_and_grad(th_d, C_d, seed, P, path0=path0, out=outs)
+        res_h.copy_(res_d, non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_step()
+        torch.cuda.current_stream().synchronize()
+    e2e_s = time.perf_counter() - t0
+    clk = clocks.stop()
+
+    ms_step = max_over_ranks(ms_total / args.steps, world)
+    e2e_ms = max_over_ranks(e2e_s * 1e3 / args.steps, world)
+    value = world * P * S / (ms_step * 1e-3)
+    peaks, peak_src = load_peaks()
+    sm_mhz_peak = float(peaks.get("sm_max_mhz", 2070.0))
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    issue_peak = 128 * n_sm * sm_mhz_peak * 1e6  # thread-ops/s: 4 warp instructions per SM per clock
+    rev_ms, rev_n = prof["reverse_sweep"]
+    fwd_ms, fwd_n = prof["forward_sweep"]
+    rev_avg = rev_ms / max(rev_n, 1)
+    achieved = P * S * _ops("reverse_sweep") / (rev_avg * 1e-3)
+    launches = sum(n for _, n in prof.values())
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": ms_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": w.name, "paths_per_gpu": P, "steps": S, "instruments": pb.m, "params": 5,
+                       "ckpt_every": pb.ckpt_every, "precision": "fp32 paths, fp64 sums",
+                       "l2": "inputs larger than L2: checkpoints %.0f MB per step" %
+                             (P * (S // pb.ckpt_every) * 2 * 4 / 1e6)},
+            "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": issue_peak / 1e12,
+                         "unit": "Tops/s", "frac": achieved / issue_peak, "traffic": None,
+                         "kernel": "path_reverse_kernel<Heston,f32,8>",
+                         "ops_per_path_step": _ops("reverse_sweep"),
+                         "peak_basis": "SM issue rate 128 thread-ops/clk x %d SMs x %.0f MHz (%s max clock)"
+                                       % (n_sm, sm_mhz_peak, peak_src),
+                         "fp32_frac": P * S * OPS["reverse_sweep"]["fp32"] / (rev_avg * 1e-3) / issue_peak},
+            "kernels_ms_per_step": {k: v[0] / max(v[1], 1) for k, v in prof.items() if v[1]},
+            "gpu_launches": launches,
+            "e2e": {"value": world * P * S / (e2e_ms * 1e-3), "unit": UNIT,
+                    "h2d_bytes_per_step": 8 * (ctx.M + ctx.m), "d2h_bytes_per_step": 8 * (1 + ctx.M + ctx.m)},
+            "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"]},
+        }
+        if not args.no_cpu_baseline and world == 1:
+            line["cpu_baseline"] = cpu_baseline(w, args.cpu_paths)
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,191 @@
+/*
+ * mcaad.h -- C ABI of libmcaad.so: the Monte Carlo value and adjoint gradient
+ * of the calibration objective
+ *
+ *     G(theta) = 1/2 sum_{i=1..m} (E y_i(theta) - C_i)^2            (eq. 241118A)
+ *
+ * of Goloubentsev & Lakshtanov, "Remarks on Automatic Adjoint Differentiation
+ * for gradient descent and models calibration" (arXiv 1901.04200), computed
+ * with the paper's two-step algorithm: step 1, E y_i by a forward sweep over
+ * paths (eq. 1211A); step 2, per path, the reverse algorithm R seeded with
+ * lambda_i = E y_i - C_i (eq. 0711A), re-running F from checkpoints because the
+ * forward results are not all stored; step 3, the sum over paths.  Total cost
+ * (2 K_F + K_R)/c * paths * Cost(F) (eq. 0711C).
+ *
+ * Conventions for every entry point:
+ *  - All pointers are DEVICE pointers unless the name ends in `_host`.
+ *    The caller owns every buffer it passes; the library never frees them.
+ *  - Work is enqueued on the caller's `stream` (a cudaStream_t passed as
+ *    void*; NULL = legacy default stream) and is asynchronous: outputs are
+ *    valid once the stream reaches that point.
+ *  - Every call returns an mc_status.  Argument errors are detected on the
+ *    host before any work is enqueued (MC_ERR_INVALID_ARG, nothing written).
+ *    A launch error returns MC_ERR_CUDA.  Errors from earlier asynchronous
+ *    work surface in a later call or in mc_sync.  mc_last_error() gives a
+ *    message owned by the context (valid until the next call on it).
+ *  - A context is used from one host thread at a time; calls enqueued on
+ *    different streams that share a context race on its workspace.
+ *  - Floating-point inputs and outputs at the boundary are FP64.  Path
+ *    arithmetic runs in the model's precision (MC_FP32 or MC_FP64); sums over
+ *    paths, E y, lambda, G and grad G are FP64.
+ *
+ * Random numbers: normal j of global path p is Box-Muller on the
+ * Philox-4x32-10 block (Salmon et al., SC'11) with counter
+ * (j>>2 as 64-bit in words 0-1, p as 64-bit in words 2-3) and key
+ * (seed & 0xffffffff, seed >> 32); u(w) = ((w >> 9) + 0.5) * 2^-23;
+ * block words (o0,o1) give normals 0,1 and (o2,o3) give 2,3 with
+ * rad = sqrt(-2 ln u(o_2q)), z_2q = rad cos(2 pi u(o_2q+1)),
+ * z_2q+1 = rad sin(2 pi u(o_2q+1)).  Global path indices make results
+ * independent of how a path range is split across calls or devices.
+ */
+#ifndef MCAAD_H
+#define MCAAD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MC_OK = 0,
+    MC_ERR_INVALID_ARG = 1,
+    MC_ERR_CUDA = 2,
+    MC_ERR_OOM = 3,
+    MC_ERR_UNSUPPORTED = 4,
+    MC_ERR_STATE = 5
+} mc_status;
+
+typedef enum {
+    MC_MODEL_GBM_PWC = 0,     /* GBM, piecewise-constant vol, log-Euler       */
+    MC_MODEL_HESTON_FT = 1,   /* Heston, full-truncation Euler                */
+    MC_MODEL_LV_BILINEAR = 2  /* local vol, bilinear node surface, log-Euler  */
+} mc_model_kind;
+
+typedef enum { MC_FP64 = 0, MC_FP32 = 1 } mc_precision;
+
+/*
+ * The stochastic model F (paper: F maps M parameters and N random numbers to
+ * the m payoffs of one path; Heston SLV test paragraph: Euler discretisation).
+ * State x = ln(S/S0) starts at 0.  Step n (time n*dt) of each model:
+ *   GBM_PWC:     theta[b] = vol of bucket b; step n is in the first bucket b
+ *                with n < bucket_end_host[b];
+ *                x += (r - theta_b^2/2) dt + theta_b sqrt(dt) z_n.       M = n_buckets
+ *   HESTON_FT:   theta = (kappa, theta_h, xi, rho, v0); v+ = max(v,0);
+ *                x += (r - v+/2) dt + sqrt(v+ dt) z1;
+ *                v += kappa (theta_h - v+) dt + xi sqrt(v+ dt) (rho z1 + sqrt(1-rho^2) z2),
+ *                z1, z2 = normals 2n, 2n+1; v starts at v0.             M = 5
+ *   LV_BILINEAR: theta[j*nx + c] = sigma at t_j = j t_max/(nt-1),
+ *                x_c = x_lo + c (x_hi-x_lo)/(nx-1); sigma(t_n, x_n) bilinear
+ *                with flat extrapolation;
+ *                x += (r - sigma^2/2) dt + sigma sqrt(dt) z_n.           M = nt*nx
+ * ckpt_every: checkpoint interval k of the reverse sweep (0 = library
+ * default); it must divide every maturity step.
+ * normals: optional device FP64 table [rows][n_steps * normals_per_step]
+ * (row = global path - normals_path0) used instead of Philox; GBM only.
+ */
+typedef struct {
+    int32_t kind;        /* mc_model_kind */
+    int32_t precision;   /* mc_precision  */
+    double S0, r, dt;
+    int32_t n_steps;
+    int32_t ckpt_every;
+    int32_t n_buckets;
+    const int32_t *bucket_end_host;
+    int32_t nt, nx;
+    double t_max, x_lo, x_hi;
+    const double *normals;
+    uint64_t normals_path0;
+    uint64_t normals_rows;
+} mc_model;
+
+/* European calls y_i = exp(-r T_i) max(S0 e^{x_{n_i}} - K_i, 0), T_i = n_i dt
+ * (Heston SLV test paragraph: European options as the y_i).  Host arrays,
+ * copied at context creation; 1 <= mat_step_host[i] <= n_steps. */
+typedef struct {
+    int32_t m;
+    const double *K_host;
+    const int32_t *mat_step_host;
+} mc_instruments;
+
+typedef struct mc_ctx mc_ctx;
+
+/* Bytes of device workspace a context needs for up to max_paths paths per
+ * call (checkpoints, per-block partial sums, seeds, model tables).
+ * Errors: MC_ERR_INVALID_ARG for an invalid model/instruments (same checks
+ * as mc_context_create). */
+mc_status mc_workspace_size(const mc_model *model, const mc_instruments *inst,
+                            uint64_t max_paths, int device, size_t *bytes_out);
+
+/* Create a context on `device` for one model and instrument set (a plan:
+ * tables and launch shapes are fixed here, nothing is allocated per call).
+ * workspace: caller-owned device buffer of >= mc_workspace_size bytes,
+ * 256-byte aligned; NULL makes the context cudaMalloc (and later free) its own.
+ * The model's `normals` table pointer, if any, must stay valid for the
+ * context's life.  Synchronous.  Errors: MC_ERR_INVALID_ARG (bad model,
+ * maturities not multiples of ckpt_every, workspace too small or misaligned),
+ * MC_ERR_OOM, MC_ERR_CUDA. */
+mc_status mc_context_create(int device, const mc_model *model, const mc_instruments *inst,
+                            uint64_t max_paths, void *workspace, size_t workspace_bytes,
+                            mc_ctx **out);
+void mc_context_destroy(mc_ctx *ctx);
+const char *mc_last_error(const mc_ctx *ctx);
+/* Parameter count M and instrument count m of a context. */
+int32_t mc_n_params(const mc_ctx *ctx);
+int32_t mc_n_instruments(const mc_ctx *ctx);
+/* Synchronise `stream` and report any asynchronous CUDA error. */
+mc_status mc_sync(mc_ctx *ctx, void *stream);
+
+/* Step 1 of the two-step algorithm (eq. 1211A): Ey_out[i] = mean over global
+ * paths [path0, path0+n_paths) of y_i.  theta: FP64 [M]; Ey_out: FP64 [m].
+ * keep_checkpoints != 0 stores the state every ckpt_every steps so that a
+ * following mc_vjp can run the reverse sweep; theta must then stay unchanged
+ * until that mc_vjp.  1 <= n_paths <= max_paths.  For a GBM normals table,
+ * the paths must lie inside its rows. */
+mc_status mc_forward(mc_ctx *ctx, const double *theta, uint64_t seed, uint64_t path0,
+                     uint64_t n_paths, double *Ey_out, int keep_checkpoints, void *stream);
+
+/* Steps 2-3 after mc_forward(keep_checkpoints=1): theta_bar_out[j] =
+ * sum_i ybar[i] d(E y_i)/d theta_j for the last forward's paths and theta
+ * (eq. 0711A per path, re-running F between checkpoints, then the mean over
+ * paths).  ybar: FP64 [m]; theta_bar_out: FP64 [M].  MC_ERR_STATE if no
+ * forward kept checkpoints. */
+mc_status mc_vjp(mc_ctx *ctx, const double *ybar, double *theta_bar_out, void *stream);
+
+/* The whole two-step algorithm: E y, lambda = E y - C, G = 1/2 |lambda|^2
+ * (eq. 241118A) and grad G = E(sum_i lambda_i dy_i/dtheta) (gradient
+ * identity), with no host round trip.  theta, grad_out: FP64 [M]; C: FP64 [m];
+ * G_out: FP64 [1]; Ey_out: FP64 [m] or NULL.  Leaves checkpoints for mc_vjp. */
+mc_status mc_value_and_grad(mc_ctx *ctx, const double *theta, const double *C, uint64_t seed,
+                            uint64_t path0, uint64_t n_paths, double *G_out, double *grad_out,
+                            double *Ey_out, void *stream);
+
+/* Test hooks for the generator.  mc_philox_fill: out uint32
+ * [n_paths][n_calls][4], block (call c, path path0+i).  mc_normals_fill:
+ * out [n_paths][n_per_path] of normals 0.. of each path, FP64 when
+ * precision == MC_FP64 (double*), else FP32 (float*), computed exactly as the
+ * path kernels compute them. */
+mc_status mc_philox_fill(uint64_t seed, uint64_t path0, uint32_t n_paths, uint32_t n_calls,
+                         uint32_t *out, void *stream);
+mc_status mc_normals_fill(uint64_t seed, uint64_t path0, uint32_t n_paths, uint32_t n_per_path,
+                          int32_t precision, void *out, void *stream);
+
+/* Per-kernel timing with CUDA events recorded on the launching stream around
+ * every kernel the context launches (no counterpart in the paper; it measures
+ * the terms of eq. 0711C).  Kernel ids: MC_K_FORWARD (forward sweep),
+ * MC_K_FINALIZE_Y (E y / lambda / G), MC_K_SEED (mc_vjp seeds),
+ * MC_K_REVERSE (reverse sweep), MC_K_FINALIZE_G (grad G).
+ * mc_profile_begin creates events for up to max_launches launches (host
+ * call).  mc_profile_end waits for the recorded events, writes the summed
+ * milliseconds and launch counts per kernel id into ms_out[MC_N_KERNELS] and
+ * launches_out[MC_N_KERNELS] (either may be NULL), and stops recording. */
+enum { MC_K_FORWARD = 0, MC_K_FINALIZE_Y = 1, MC_K_SEED = 2, MC_K_REVERSE = 3, MC_K_FINALIZE_G = 4,
+       MC_N_KERNELS = 5 };
+mc_status mc_profile_begin(mc_ctx *ctx, int32_t max_launches);
+mc_status mc_profile_end(mc_ctx *ctx, double *ms_out, int32_t *launches_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MCAAD_H */

@@ -1,0 +1,642 @@
+// mc_api.cu -- host side of the C ABI declared in include/mcaad.h: argument
+// checks, the context (a plan holding the model tables, launch shapes and
+// workspace), and the stream-ordered launch sequences of the two-step
+// algorithm (arXiv 1901.04200): forward sweep -> finalize (E y, lambda, G)
+// -> reverse sweep -> finalize (grad G).
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "mcaad.h"
+#include "mc_internal.h"
+#include "mc_paths.cuh"
+
+using namespace mcaad;
+
+struct mc_ctx {
+    int device = 0;
+    int kind = 0, precision = 0, K = 1;
+    int m = 0, M = 0, n_groups = 0, n_seg = 0, state_dim = 1;
+    uint64_t max_paths = 0, ckpt_stride = 0;
+    int n_sm = 1;
+    int grid_fwd = 1, grid_rev = 1, grid_max = 1;
+    size_t smem_fwd = 0, smem_rev = 0;
+    KernelPair kern;
+    DevProblem pb{};
+    // workspace
+    bool owns_ws = false;
+    unsigned char *ws = nullptr;
+    size_t ws_bytes = 0;
+    void *ckpt = nullptr;
+    double *part_y = nullptr, *part_g = nullptr, *seed_w = nullptr;
+    // state for mc_vjp
+    bool have_ckpt = false;
+    DevCall last{};
+    std::string err;
+    // per-kernel event timing
+    bool prof_on = false;
+    int prof_max = 0, prof_n = 0;
+    std::vector<cudaEvent_t> prof_ev;
+    std::vector<int> prof_id;
+};
+
+namespace {
+
+mc_status fail(mc_ctx *ctx, mc_status st, const char *fmt, ...) __attribute__((format(printf, 3, 4)));
+mc_status fail(mc_ctx *ctx, mc_status st, const char *fmt, ...) {
+    if (ctx) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        ctx->err = buf;
+    }
+    return st;
+}
+
+mc_status cuda_fail(mc_ctx *ctx, cudaError_t e, const char *what) {
+    return fail(ctx, e == cudaErrorMemoryAllocation ? MC_ERR_OOM : MC_ERR_CUDA, "%s: %s", what,
+                cudaGetErrorString(e));
+}
+
+const int kGbmK[] = {16, 8, 4, 2, 1};
+const int kHestonK[] = {8, 4, 2, 1};
+const int kLvK[] = {25, 5, 1};
+
+int model_params(const mc_model *md) {
+    switch (md->kind) {
+    case MC_MODEL_GBM_PWC: return md->n_buckets;
+    case MC_MODEL_HESTON_FT: return 5;
+    case MC_MODEL_LV_BILINEAR: return md->nt * md->nx;
+    }
+    return -1;
+}
+
+// Everything a context derives from (model, instruments), computed on the host.
+struct Plan {
+    int kind, precision, K, n_last, n_seg, m, M, n_groups, state_dim;
+    std::vector<int> order;  // sorted position -> caller index
+    std::vector<double> strike, disc;
+    std::vector<int> perm, grp_seg, grp_begin, bucket, lv_jt;
+    std::vector<double> lv_a;
+    double hx = 1.0;
+};
+
+mc_status make_plan(const mc_model *md, const mc_instruments *in, Plan &p, std::string &why) {
+    char buf[256];
+    auto bad = [&](const char *msg) {
+        why = msg;
+        return MC_ERR_INVALID_ARG;
+    };
+    if (!md || !in) return bad("null model or instruments");
+    if (md->kind < 0 || md->kind > 2) return bad("unknown model kind");
+    if (md->precision != MC_FP32 && md->precision != MC_FP64) return bad("unknown precision");
+    if (!(md->S0 > 0.0) || !(md->dt > 0.0) || !std::isfinite(md->r)) return bad("need S0 > 0, dt > 0, finite r");
+    if (md->n_steps < 1) return bad("n_steps must be >= 1");
+    if (in->m < 1 || in->m > kMaxInstruments) return bad("instrument count out of range [1, 1024]");
+    if (!in->K_host || !in->mat_step_host) return bad("null instrument arrays");
+    p.kind = md->kind;
+    p.precision = md->precision;
+    p.m = in->m;
+    p.M = model_params(md);
+    if (p.M < 1 || p.M > kMaxParams) return bad("parameter count out of range [1, 256]");
+    p.state_dim = md->kind == MC_MODEL_HESTON_FT ? 2 : 1;
+    int n_last = 0, g = 0;
+    for (int i = 0; i < in->m; ++i) {
+        const int s = in->mat_step_host[i];
+        if (s < 1 || s > md->n_steps) return bad("maturity step outside [1, n_steps]");
+        if (!std::isfinite(in->K_host[i])) return bad("non-finite strike");
+        n_last = s > n_last ? s : n_last;
+        g = std::gcd(g, s);
+    }
+    p.n_last = n_last;
+    if (md->kind == MC_MODEL_GBM_PWC) {
+        if (md->n_buckets < 1 || !md->bucket_end_host) return bad("GBM needs bucket ends");
+        for (int b = 0; b < md->n_buckets; ++b) {
+            const int prev = b ? md->bucket_end_host[b - 1] : 0;
+            if (md->bucket_end_host[b] <= prev) return bad("bucket ends must increase");
+        }
+        if (md->bucket_end_host[md->n_buckets - 1] < n_last) return bad("buckets end before the last maturity");
+    } else if (md->normals) {
+        return bad("a normals table is supported for GBM only");
+    }
+    if (md->kind == MC_MODEL_LV_BILINEAR) {
+        if (md->nt < 2 || md->nx < 2 || !(md->t_max > 0.0) || !(md->x_hi > md->x_lo))
+            return bad("LV needs nt, nx >= 2, t_max > 0, x_hi > x_lo");
+    }
+    // segment length: must divide every maturity step
+    const int *ks = md->kind == MC_MODEL_GBM_PWC ? kGbmK : md->kind == MC_MODEL_HESTON_FT ? kHestonK : kLvK;
+    const int nk = md->kind == MC_MODEL_GBM_PWC ? 5 : md->kind == MC_MODEL_HESTON_FT ? 4 : 3;
+    p.K = 0;
+    if (md->ckpt_every > 0) {
+        if (g % md->ckpt_every != 0) {
+            snprintf(buf, sizeof buf, "ckpt_every=%d does not divide every maturity step (gcd %d)",
+                     md->ckpt_every, g);
+            why = buf;
+            return MC_ERR_INVALID_ARG;
+        }
+        for (int q = 0; q < nk; ++q)
+            if (ks[q] == md->ckpt_every) p.K = ks[q];
+        if (!p.K) {
+            snprintf(buf, sizeof buf, "ckpt_every=%d is not an instantiated segment length", md->ckpt_every);
+            why = buf;
+            return MC_ERR_UNSUPPORTED;
+        }
+    } else {
+        for (int q = 0; q < nk && !p.K; ++q)
+            if (g % ks[q] == 0) p.K = ks[q];
+    }
+    p.n_seg = n_last / p.K;
+    // instruments sorted by maturity (stable), grouped per maturity step
+    p.order.resize(p.m);
+    std::iota(p.order.begin(), p.order.end(), 0);
+    std::stable_sort(p.order.begin(), p.order.end(),
+                     [&](int a, int b) { return in->mat_step_host[a] < in->mat_step_host[b]; });
+    p.strike.resize(p.m);
+    p.disc.resize(p.m);
+    p.perm.resize(p.m);
+    p.grp_begin.clear();
+    p.grp_seg.clear();
+    int prev = -1;
+    for (int q = 0; q < p.m; ++q) {
+        const int i = p.order[q];
+        const int s = in->mat_step_host[i];
+        p.strike[q] = in->K_host[i];
+        p.disc[q] = std::exp(-md->r * (double)s * md->dt);
+        p.perm[q] = i;
+        if (s != prev) {
+            p.grp_begin.push_back(q);
+            p.grp_seg.push_back(s / p.K - 1);
+            prev = s;
+        }
+    }
+    p.n_groups = (int)p.grp_seg.size();
+    p.grp_begin.push_back(p.m);
+    if (md->kind == MC_MODEL_GBM_PWC) {
+        p.bucket.resize(n_last);
+        int b = 0;
+        for (int n = 0; n < n_last; ++n) {
+            while (n >= md->bucket_end_host[b]) ++b;
+            p.bucket[n] = b;
+        }
+    }
+    if (md->kind == MC_MODEL_LV_BILINEAR) {
+        // time cell and weight of step n, in FP64 as u_t = (n dt) / (t_max / (nt - 1))
+        const double ht = md->t_max / (double)(md->nt - 1);
+        p.lv_jt.resize(n_last);
+        p.lv_a.resize(n_last);
+        for (int n = 0; n < n_last; ++n) {
+            const double ut = ((double)n * md->dt) / ht;
+            int jt = (int)std::floor(ut);
+            jt = jt < 0 ? 0 : (jt > md->nt - 2 ? md->nt - 2 : jt);
+            double a = ut - (double)jt;
+            a = a < 0.0 ? 0.0 : (a > 1.0 ? 1.0 : a);
+            p.lv_jt[n] = jt;
+            p.lv_a[n] = a;
+        }
+        p.hx = (md->x_hi - md->x_lo) / (double)(md->nx - 1);
+    }
+    return MC_OK;
+}
+
+// Workspace carve-out (256-byte aligned pieces).
+struct WsLayout {
+    size_t strike, disc, perm, grp_seg, grp_begin, bucket, lv_jt, lv_a, seed_w, part_y, part_g, ckpt, total;
+    WsLayout(const Plan &p, int grid_max, uint64_t ckpt_stride) {
+        size_t o = 0;
+        auto take = [&](size_t bytes) {
+            size_t at = o;
+            o = align_up(o + bytes, 256);
+            return at;
+        };
+        strike = take(p.m * 8);
+        disc = take(p.m * 8);
+        perm = take(p.m * 4);
+        grp_seg = take(p.n_groups * 4);
+        grp_begin = take((p.n_groups + 1) * 4);
+        bucket = take(p.bucket.size() * 4);
+        lv_jt = take(p.lv_jt.size() * 4);
+        lv_a = take(p.lv_a.size() * 8);
+        seed_w = take(p.m * 8);
+        part_y = take((size_t)grid_max * p.m * 8);
+        part_g = take((size_t)grid_max * p.M * 8);
+        const size_t real = p.precision == MC_FP64 ? 8 : 4;
+        ckpt = take((size_t)p.n_seg * p.state_dim * ckpt_stride * real);
+        total = o;
+    }
+};
+
+bool kernels_for(const Plan &p, KernelPair *kp) {
+    switch (p.kind) {
+    case kGbm: return gbm_kernels(p.precision, p.K, kp);
+    case kHeston: return heston_kernels(p.precision, p.K, kp);
+    case kLv: return lv_kernels(p.precision, p.K, kp);
+    }
+    return false;
+}
+
+// Launch shape: blocks of kBlock threads, at most (resident blocks per SM) x
+// (SMs) of them; each warp loops over 32-path chunks.
+mc_status launch_shape(const Plan &p, int device, const KernelPair &kp, int nx, int *n_sm,
+                       int *grid_fwd, int *grid_rev, size_t *smem_fwd, size_t *smem_rev,
+                       std::string &why) {
+    cudaError_t e = cudaDeviceGetAttribute(n_sm, cudaDevAttrMultiProcessorCount, device);
+    if (e != cudaSuccess) {
+        why = cudaGetErrorString(e);
+        return MC_ERR_CUDA;
+    }
+    const int real = p.precision == MC_FP64 ? 8 : 4;
+    const int n_steps = p.n_seg * p.K;
+    *smem_fwd = SmemPlan(p.kind, real, p.m, p.n_groups, p.M, n_steps, nx, false).total;
+    *smem_rev = SmemPlan(p.kind, real, p.m, p.n_groups, p.M, n_steps, nx, true).total;
+    int optin = 0;
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+    if (*smem_fwd > (size_t)optin || *smem_rev > (size_t)optin) {
+        why = "problem tables exceed shared memory";
+        return MC_ERR_UNSUPPORTED;
+    }
+    const void *fns[2] = {kp.fwd, kp.rev};
+    size_t sm[2] = {*smem_fwd, *smem_rev};
+    int *grids[2] = {grid_fwd, grid_rev};
+    for (int q = 0; q < 2; ++q) {
+        e = cudaFuncSetAttribute(fns[q], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm[q]);
+        if (e != cudaSuccess) {
+            why = cudaGetErrorString(e);
+            return MC_ERR_CUDA;
+        }
+        int occ = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fns[q], kBlock, sm[q]);
+        if (e != cudaSuccess || occ < 1) {
+            why = e != cudaSuccess ? cudaGetErrorString(e) : "path kernel does not fit on an SM";
+            return e != cudaSuccess ? MC_ERR_CUDA : MC_ERR_UNSUPPORTED;
+        }
+        *grids[q] = occ * *n_sm;
+    }
+    return MC_OK;
+}
+
+int grid_for_paths(int grid_max, uint64_t n_paths) {
+    const uint64_t chunks = (n_paths + kWarp - 1) / kWarp;
+    const uint64_t want = (chunks + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    return (int)(want < (uint64_t)grid_max ? want : (uint64_t)grid_max);
+}
+
+cudaError_t launch(const void *fn, int grid, size_t smem, const DevProblem &pb, const DevCall &cl,
+                   cudaStream_t st) {
+    void *args[2] = {(void *)&pb, (void *)&cl};
+    return cudaLaunchKernel(fn, dim3(grid), dim3(kBlock), args, smem, st);
+}
+
+// Launch f() on st; when profiling, bracket it with events tagged `id`.
+template <class F>
+cudaError_t timed(mc_ctx *ctx, int id, cudaStream_t st, F &&f) {
+    const bool rec = ctx->prof_on && ctx->prof_n < ctx->prof_max;
+    if (rec) cudaEventRecord(ctx->prof_ev[2 * ctx->prof_n], st);
+    cudaError_t e = f();
+    if (rec) {
+        cudaEventRecord(ctx->prof_ev[2 * ctx->prof_n + 1], st);
+        ctx->prof_id[ctx->prof_n++] = id;
+    }
+    return e;
+}
+
+void prof_free(mc_ctx *ctx) {
+    for (cudaEvent_t ev : ctx->prof_ev) cudaEventDestroy(ev);
+    ctx->prof_ev.clear();
+    ctx->prof_id.clear();
+    ctx->prof_on = false;
+    ctx->prof_max = ctx->prof_n = 0;
+}
+
+template <typename T>
+bool aligned8(const T *p) {
+    return ((uintptr_t)p & 7u) == 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+mc_status mc_workspace_size(const mc_model *model, const mc_instruments *inst, uint64_t max_paths,
+                            int device, size_t *bytes_out) {
+    if (!bytes_out || max_paths == 0) return MC_ERR_INVALID_ARG;
+    Plan p;
+    std::string why;
+    mc_status st = make_plan(model, inst, p, why);
+    if (st != MC_OK) return st;
+    KernelPair kp;
+    if (!kernels_for(p, &kp)) return MC_ERR_UNSUPPORTED;
+    int n_sm, gf, gr;
+    size_t sf, sr;
+    st = launch_shape(p, device, kp, model->nx, &n_sm, &gf, &gr, &sf, &sr, why);
+    if (st != MC_OK) return st;
+    const uint64_t stride = (max_paths + kWarp - 1) / kWarp * kWarp;
+    *bytes_out = WsLayout(p, gf > gr ? gf : gr, stride).total;
+    return MC_OK;
+}
+
+mc_status mc_context_create(int device, const mc_model *model, const mc_instruments *inst,
+                            uint64_t max_paths, void *workspace, size_t workspace_bytes,
+                            mc_ctx **out) {
+    if (!out) return MC_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (max_paths == 0) return MC_ERR_INVALID_ARG;
+    Plan p;
+    std::string why;
+    mc_status st = make_plan(model, inst, p, why);
+    if (st != MC_OK) {
+        fprintf(stderr, "mc_context_create: %s\n", why.c_str());
+        return st;
+    }
+    KernelPair kp;
+    if (!kernels_for(p, &kp)) return MC_ERR_UNSUPPORTED;
+    cudaError_t e = cudaSetDevice(device);
+    if (e != cudaSuccess) {
+        fprintf(stderr, "mc_context_create: cudaSetDevice: %s\n", cudaGetErrorString(e));
+        return MC_ERR_CUDA;
+    }
+    mc_ctx *ctx = new (std::nothrow) mc_ctx();
+    if (!ctx) return MC_ERR_OOM;
+    ctx->device = device;
+    ctx->kind = p.kind;
+    ctx->precision = p.precision;
+    ctx->K = p.K;
+    ctx->m = p.m;
+    ctx->M = p.M;
+    ctx->n_groups = p.n_groups;
+    ctx->n_seg = p.n_seg;
+    ctx->state_dim = p.state_dim;
+    ctx->kern = kp;
+    st = launch_shape(p, device, kp, model->nx, &ctx->n_sm, &ctx->grid_fwd, &ctx->grid_rev,
+                      &ctx->smem_fwd, &ctx->smem_rev, why);
+    if (st != MC_OK) {
+        fprintf(stderr, "mc_context_create: %s\n", why.c_str());
+        delete ctx;
+        return st;
+    }
+    ctx->grid_max = ctx->grid_fwd > ctx->grid_rev ? ctx->grid_fwd : ctx->grid_rev;
+    ctx->max_paths = max_paths;
+    ctx->ckpt_stride = (max_paths + kWarp - 1) / kWarp * kWarp;
+    WsLayout L(p, ctx->grid_max, ctx->ckpt_stride);
+    if (workspace) {
+        if (workspace_bytes < L.total || ((uintptr_t)workspace & 255u)) {
+            fprintf(stderr, "mc_context_create: workspace needs %zu bytes, 256-byte aligned\n", L.total);
+            delete ctx;
+            return MC_ERR_INVALID_ARG;
+        }
+        ctx->ws = (unsigned char *)workspace;
+        ctx->owns_ws = false;
+    } else {
+        e = cudaMalloc((void **)&ctx->ws, L.total);
+        if (e != cudaSuccess) {
+            fprintf(stderr, "mc_context_create: cudaMalloc(%zu): %s\n", L.total, cudaGetErrorString(e));
+            delete ctx;
+            return e == cudaErrorMemoryAllocation ? MC_ERR_OOM : MC_ERR_CUDA;
+        }
+        ctx->owns_ws = true;
+    }
+    ctx->ws_bytes = L.total;
+    unsigned char *w = ctx->ws;
+    auto up = [&](size_t off, const void *src, size_t bytes) {
+        return bytes ? cudaMemcpy(w + off, src, bytes, cudaMemcpyHostToDevice) : cudaSuccess;
+    };
+    e = up(L.strike, p.strike.data(), p.m * 8);
+    if (e == cudaSuccess) e = up(L.disc, p.disc.data(), p.m * 8);
+    if (e == cudaSuccess) e = up(L.perm, p.perm.data(), p.m * 4);
+    if (e == cudaSuccess) e = up(L.grp_seg, p.grp_seg.data(), p.n_groups * 4);
+    if (e == cudaSuccess) e = up(L.grp_begin, p.grp_begin.data(), (p.n_groups + 1) * 4);
+    if (e == cudaSuccess) e = up(L.bucket, p.bucket.data(), p.bucket.size() * 4);
+    if (e == cudaSuccess) e = up(L.lv_jt, p.lv_jt.data(), p.lv_jt.size() * 4);
+    if (e == cudaSuccess) e = up(L.lv_a, p.lv_a.data(), p.lv_a.size() * 8);
+    if (e != cudaSuccess) {
+        fprintf(stderr, "mc_context_create: table upload: %s\n", cudaGetErrorString(e));
+        mc_context_destroy(ctx);
+        return MC_ERR_CUDA;
+    }
+    ctx->ckpt = w + L.ckpt;
+    ctx->part_y = (double *)(w + L.part_y);
+    ctx->part_g = (double *)(w + L.part_g);
+    ctx->seed_w = (double *)(w + L.seed_w);
+    DevProblem &pb = ctx->pb;
+    pb.kind = p.kind;
+    pb.K = p.K;
+    pb.n_seg = p.n_seg;
+    pb.m = p.m;
+    pb.M = p.M;
+    pb.n_groups = p.n_groups;
+    pb.S0 = model->S0;
+    pb.r = model->r;
+    pb.dt = model->dt;
+    pb.strike = (const double *)(w + L.strike);
+    pb.disc = (const double *)(w + L.disc);
+    pb.perm = (const int *)(w + L.perm);
+    pb.grp_seg = (const int *)(w + L.grp_seg);
+    pb.grp_begin = (const int *)(w + L.grp_begin);
+    pb.bucket_of_step = (const int *)(w + L.bucket);
+    pb.lv_jt = (const int *)(w + L.lv_jt);
+    pb.lv_a = (const double *)(w + L.lv_a);
+    pb.nt = model->nt;
+    pb.nx = model->nx;
+    pb.x_lo = model->x_lo;
+    pb.hx = p.hx;
+    pb.normals = model->normals;
+    pb.normals_path0 = model->normals_path0;
+    pb.normals_rows = model->normals_rows;
+    pb.normals_stride = model->n_steps * (p.kind == kHeston ? 2 : 1);
+    *out = ctx;
+    return MC_OK;
+}
+
+void mc_context_destroy(mc_ctx *ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    prof_free(ctx);
+    if (ctx->owns_ws && ctx->ws) cudaFree(ctx->ws);
+    delete ctx;
+}
+
+const char *mc_last_error(const mc_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+int32_t mc_n_params(const mc_ctx *ctx) { return ctx ? ctx->M : -1; }
+int32_t mc_n_instruments(const mc_ctx *ctx) { return ctx ? ctx->m : -1; }
+
+mc_status mc_sync(mc_ctx *ctx, void *stream) {
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "stream synchronize");
+    return MC_OK;
+}
+
+static mc_status check_call(mc_ctx *ctx, const double *theta, uint64_t path0, uint64_t n_paths) {
+    if (!theta || !aligned8(theta)) return fail(ctx, MC_ERR_INVALID_ARG, "theta must be a non-null FP64 device pointer");
+    if (n_paths == 0 || n_paths > ctx->max_paths)
+        return fail(ctx, MC_ERR_INVALID_ARG, "n_paths=%llu outside [1, max_paths=%llu]",
+                    (unsigned long long)n_paths, (unsigned long long)ctx->max_paths);
+    if (path0 + n_paths < path0) return fail(ctx, MC_ERR_INVALID_ARG, "path range overflows");
+    if (ctx->pb.normals) {
+        if (path0 < ctx->pb.normals_path0 || path0 + n_paths > ctx->pb.normals_path0 + ctx->pb.normals_rows)
+            return fail(ctx, MC_ERR_INVALID_ARG, "paths outside the normals table");
+    }
+    return MC_OK;
+}
+
+static mc_status do_forward(mc_ctx *ctx, const double *theta, uint64_t seed, uint64_t path0,
+                            uint64_t n_paths, int keep, cudaStream_t st, DevCall &cl, int &grid) {
+    cl = DevCall{};
+    cl.theta = theta;
+    cl.seed = seed;
+    cl.path0 = path0;
+    cl.n_paths = n_paths;
+    cl.ckpt = ctx->ckpt;
+    cl.ckpt_stride = ctx->ckpt_stride;
+    cl.keep_ckpt = keep;
+    cl.part_y = ctx->part_y;
+    cl.part_g = ctx->part_g;
+    cl.seed_w = ctx->seed_w;
+    grid = grid_for_paths(ctx->grid_fwd, n_paths);
+    cudaError_t e = timed(ctx, MC_K_FORWARD, st, [&] { return launch(ctx->kern.fwd, grid, ctx->smem_fwd, ctx->pb, cl, st); });
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "forward sweep launch");
+    return MC_OK;
+}
+
+static mc_status do_reverse(mc_ctx *ctx, cudaStream_t st, double *grad_out) {
+    const int grid = grid_for_paths(ctx->grid_rev, ctx->last.n_paths);
+    cudaError_t e = timed(ctx, MC_K_REVERSE, st, [&] { return launch(ctx->kern.rev, grid, ctx->smem_rev, ctx->pb, ctx->last, st); });
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "reverse sweep launch");
+    e = timed(ctx, MC_K_FINALIZE_G, st, [&] {
+        return launch_finalize_grad(ctx->part_g, grid, ctx->M, 1.0 / (double)ctx->last.n_paths, grad_out, st);
+    });
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "gradient finalize launch");
+    return MC_OK;
+}
+
+mc_status mc_forward(mc_ctx *ctx, const double *theta, uint64_t seed, uint64_t path0,
+                     uint64_t n_paths, double *Ey_out, int keep_checkpoints, void *stream) {
+    if (!ctx) return MC_ERR_INVALID_ARG;
+    mc_status s = check_call(ctx, theta, path0, n_paths);
+    if (s != MC_OK) return s;
+    if (!Ey_out || !aligned8(Ey_out)) return fail(ctx, MC_ERR_INVALID_ARG, "Ey_out must be a non-null FP64 device pointer");
+    cudaStream_t st = (cudaStream_t)stream;
+    DevCall cl;
+    int grid;
+    ctx->have_ckpt = false;
+    s = do_forward(ctx, theta, seed, path0, n_paths, keep_checkpoints ? 1 : 0, st, cl, grid);
+    if (s != MC_OK) return s;
+    cudaError_t e = timed(ctx, MC_K_FINALIZE_Y, st, [&] {
+        return launch_finalize_forward(ctx->part_y, grid, ctx->m, 1.0 / (double)n_paths, ctx->pb.disc,
+                                       ctx->pb.perm, nullptr, Ey_out, nullptr, nullptr, st);
+    });
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "forward finalize launch");
+    if (keep_checkpoints) {
+        ctx->last = cl;
+        ctx->have_ckpt = true;
+    }
+    return MC_OK;
+}
+
+mc_status mc_vjp(mc_ctx *ctx, const double *ybar, double *theta_bar_out, void *stream) {
+    if (!ctx) return MC_ERR_INVALID_ARG;
+    if (!ctx->have_ckpt) return fail(ctx, MC_ERR_STATE, "mc_vjp needs a preceding mc_forward with keep_checkpoints");
+    if (!ybar || !theta_bar_out || !aligned8(ybar) || !aligned8(theta_bar_out))
+        return fail(ctx, MC_ERR_INVALID_ARG, "ybar and theta_bar_out must be non-null FP64 device pointers");
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = timed(ctx, MC_K_SEED, st, [&] {
+        return launch_seed_from_ybar(ybar, ctx->pb.perm, ctx->pb.disc, ctx->m, ctx->seed_w, st);
+    });
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "seed launch");
+    return do_reverse(ctx, st, theta_bar_out);
+}
+
+mc_status mc_value_and_grad(mc_ctx *ctx, const double *theta, const double *C, uint64_t seed,
+                            uint64_t path0, uint64_t n_paths, double *G_out, double *grad_out,
+                            double *Ey_out, void *stream) {
+    if (!ctx) return MC_ERR_INVALID_ARG;
+    mc_status s = check_call(ctx, theta, path0, n_paths);
+    if (s != MC_OK) return s;
+    if (!C || !G_out || !grad_out || !aligned8(C) || !aligned8(G_out) || !aligned8(grad_out) ||
+        (Ey_out && !aligned8(Ey_out)))
+        return fail(ctx, MC_ERR_INVALID_ARG, "C, G_out, grad_out must be non-null FP64 device pointers");
+    cudaStream_t st = (cudaStream_t)stream;
+    DevCall cl;
+    int grid;
+    ctx->have_ckpt = false;
+    s = do_forward(ctx, theta, seed, path0, n_paths, 1, st, cl, grid);
+    if (s != MC_OK) return s;
+    cudaError_t e = timed(ctx, MC_K_FINALIZE_Y, st, [&] {
+        return launch_finalize_forward(ctx->part_y, grid, ctx->m, 1.0 / (double)n_paths, ctx->pb.disc,
+                                       ctx->pb.perm, C, Ey_out, ctx->seed_w, G_out, st);
+    });
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "forward finalize launch");
+    ctx->last = cl;
+    ctx->have_ckpt = true;
+    return do_reverse(ctx, st, grad_out);
+}
+
+mc_status mc_profile_begin(mc_ctx *ctx, int32_t max_launches) {
+    if (!ctx || max_launches < 1) return MC_ERR_INVALID_ARG;
+    cudaSetDevice(ctx->device);
+    prof_free(ctx);
+    ctx->prof_ev.resize(2 * (size_t)max_launches, nullptr);
+    ctx->prof_id.resize(max_launches, -1);
+    for (auto &ev : ctx->prof_ev) {
+        cudaError_t e = cudaEventCreate(&ev);
+        if (e != cudaSuccess) {
+            prof_free(ctx);
+            return cuda_fail(ctx, e, "profile event create");
+        }
+    }
+    ctx->prof_max = max_launches;
+    ctx->prof_n = 0;
+    ctx->prof_on = true;
+    return MC_OK;
+}
+
+mc_status mc_profile_end(mc_ctx *ctx, double *ms_out, int32_t *launches_out) {
+    if (!ctx || !ctx->prof_on) return ctx ? fail(ctx, MC_ERR_STATE, "profiling was not started") : MC_ERR_INVALID_ARG;
+    double ms[MC_N_KERNELS] = {0};
+    int32_t cnt[MC_N_KERNELS] = {0};
+    mc_status st = MC_OK;
+    for (int q = 0; q < ctx->prof_n; ++q) {
+        cudaError_t e = cudaEventSynchronize(ctx->prof_ev[2 * q + 1]);
+        float t = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, ctx->prof_ev[2 * q], ctx->prof_ev[2 * q + 1]);
+        if (e != cudaSuccess) {
+            st = cuda_fail(ctx, e, "profile event read");
+            break;
+        }
+        ms[ctx->prof_id[q]] += t;
+        cnt[ctx->prof_id[q]] += 1;
+    }
+    prof_free(ctx);
+    for (int k = 0; k < MC_N_KERNELS; ++k) {
+        if (ms_out) ms_out[k] = ms[k];
+        if (launches_out) launches_out[k] = cnt[k];
+    }
+    return st;
+}
+
+mc_status mc_philox_fill(uint64_t seed, uint64_t path0, uint32_t n_paths, uint32_t n_calls,
+                         uint32_t *out, void *stream) {
+    if (!out || n_paths == 0 || n_calls == 0 || ((uintptr_t)out & 15u)) return MC_ERR_INVALID_ARG;
+    return launch_philox_fill(seed, path0, n_paths, n_calls, out, (cudaStream_t)stream) == cudaSuccess
+               ? MC_OK
+               : MC_ERR_CUDA;
+}
+
+mc_status mc_normals_fill(uint64_t seed, uint64_t path0, uint32_t n_paths, uint32_t n_per_path,
+                          int32_t precision, void *out, void *stream) {
+    if (!out || n_paths == 0 || n_per_path == 0) return MC_ERR_INVALID_ARG;
+    if (precision != MC_FP32 && precision != MC_FP64) return MC_ERR_INVALID_ARG;
+    if (((uintptr_t)out & (precision == MC_FP64 ? 7u : 3u))) return MC_ERR_INVALID_ARG;
+    return launch_normals_fill(seed, path0, n_paths, n_per_path, precision, out,
+                               (cudaStream_t)stream) == cudaSuccess
+               ? MC_OK
+               : MC_ERR_CUDA;
+}
+
+}  // extern "C"

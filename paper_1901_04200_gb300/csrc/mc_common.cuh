@@ -1,0 +1,152 @@
+// mc_common.cuh -- device building blocks shared by the path kernels:
+// Philox-4x32-10 (Salmon et al., SC'11), the uniform map, Box-Muller, warp
+// sums, and the parameter blocks handed to every kernel by value.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mcaad {
+
+constexpr int kWarp = 32;
+constexpr int kBlock = 128;             // threads per path-kernel block
+constexpr int kWarpsPerBlock = kBlock / kWarp;
+constexpr int kMaxInstruments = 1024;   // m limit (shared-memory tables)
+constexpr int kMaxParams = 256;         // M limit
+
+// ------------------------------------------------------------------ RNG ----
+
+// Ten rounds of the Philox 4x32 bijection: each round multiplies words 0 and
+// 2 by the two Philox constants, keeps the low halves as the new words 1 and
+// 3, and xors the high halves with the other two words and the round key;
+// the key advances by the Weyl increments between rounds.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const uint32_t lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    }
+    return c;
+}
+
+// u(w) = ((w >> 9) + 0.5) * 2^-23.  In FP32: the float 1 + (w>>9)*2^-23 built
+// from its bit pattern, minus (1 - 2^-24); the difference is representable,
+// so the single rounded subtraction is exact.
+__device__ __forceinline__ float uniform_f32(uint32_t w) {
+    return __fsub_rn(__uint_as_float(0x3f800000u | (w >> 9)), 0.99999994f);
+}
+__device__ __forceinline__ double uniform_f64(uint32_t w) {
+    return ((double)(w >> 9) + 0.5) * (1.0 / 8388608.0);
+}
+
+__device__ __forceinline__ float sqrt_approx(float x) {
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// Box-Muller on one pair of uniforms: rad = sqrt(-2 ln u_a),
+// (za, zb) = rad (cos 2 pi u_b, sin 2 pi u_b).  The FP32 version evaluates the
+// angle as 2 pi (u_b - 1/2) + pi, i.e. negates cos and sin of an argument in
+// (-pi, pi), where the fast hardware sine/cosine are accurate; u_b - 1/2 is
+// exact.  -2 ln u_a is clamped at 0 against the approximate log near u = 1.
+__device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, float &za, float &zb) {
+    const float ua = uniform_f32(a);
+    const float ub = uniform_f32(b);
+    const float rad = sqrt_approx(fmaxf(-2.0f * __logf(ua), 0.0f));
+    float s, c;
+    __sincosf(6.28318530717958648f * (ub - 0.5f), &s, &c);
+    za = -rad * c;
+    zb = -rad * s;
+}
+__device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, double &za, double &zb) {
+    const double ua = uniform_f64(a);
+    const double ub = uniform_f64(b);
+    const double rad = sqrt(-2.0 * log(ua));
+    double s, c;
+    sincospi(2.0 * ub, &s, &c);
+    za = rad * c;
+    zb = rad * s;
+}
+
+// Normals of one path, one Philox block (4 normals) at a time.
+template <typename Real>
+struct PathNormals {
+    uint32_t k0, k1, p_lo, p_hi;
+    Real z0, z1, z2, z3;
+    __device__ __forceinline__ void init(uint64_t seed, uint64_t path) {
+        k0 = (uint32_t)seed;
+        k1 = (uint32_t)(seed >> 32);
+        p_lo = (uint32_t)path;
+        p_hi = (uint32_t)(path >> 32);
+    }
+    __device__ __forceinline__ void fill(uint32_t call) {
+        const uint4 o = philox4x32_10(make_uint4(call, 0u, p_lo, p_hi), k0, k1);
+        box_muller(o.x, o.y, z0, z1);
+        box_muller(o.z, o.w, z2, z3);
+    }
+    __device__ __forceinline__ Real pick(uint32_t q) const {
+        return q == 0 ? z0 : (q == 1 ? z1 : (q == 2 ? z2 : z3));
+    }
+};
+
+// ------------------------------------------------------------ reductions ----
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// ----------------------------------------------------------- parameters ----
+
+enum ModelKind { kGbm = 0, kHeston = 1, kLv = 2 };
+
+// Problem tables fixed at context creation (device pointers into the
+// context's workspace).  Instruments are kept sorted by maturity; maturity
+// group g covers sorted instruments [grp_begin[g], grp_begin[g+1]) and pays at
+// step (grp_seg[g] + 1) * K, the end of segment grp_seg[g].
+struct DevProblem {
+    int kind;
+    int K;            // checkpoint interval = segment length
+    int n_seg;        // segments up to the last maturity
+    int m, M;
+    int n_groups;
+    double S0, r, dt;
+    const double *strike;       // [m] sorted
+    const double *disc;         // [m] sorted, exp(-r T_i)
+    const int *perm;            // [m] sorted index -> caller index
+    const int *grp_seg;         // [n_groups]
+    const int *grp_begin;       // [n_groups + 1]
+    const int *bucket_of_step;  // GBM [n_seg * K]
+    const int *lv_jt;           // LV   [n_seg * K] time cell of step n
+    const double *lv_a;         // LV   [n_seg * K] time weight of step n
+    int nt, nx;
+    double x_lo, hx;
+    const double *normals;      // optional GBM table
+    uint64_t normals_path0, normals_rows;
+    int normals_stride;
+};
+
+// One evaluation.
+struct DevCall {
+    const double *theta;  // [M]
+    uint64_t seed;
+    uint64_t path0;       // first global path
+    uint64_t n_paths;
+    void *ckpt;           // [n_seg][state_dim][ckpt_stride] of Real
+    uint64_t ckpt_stride; // paths padded to a multiple of 32
+    int keep_ckpt;
+    double *part_y;       // [gridDim.x][m] per-block payoff sums (sorted order)
+    double *part_g;       // [gridDim.x][M] per-block gradient sums
+    const double *seed_w; // [m] sorted: lambda_i * disc_i (reverse sweep seeds)
+};
+
+}  // namespace mcaad

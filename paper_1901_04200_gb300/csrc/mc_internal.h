@@ -1,0 +1,35 @@
+// mc_internal.h -- declarations shared by the host API and the kernel
+// translation units of libmcaad (not part of the public ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "mc_common.cuh"
+
+namespace mcaad {
+
+struct KernelPair {
+    const void *fwd = nullptr;
+    const void *rev = nullptr;
+};
+
+// Path kernels of (kind, precision, K); false if that K is not instantiated.
+bool gbm_kernels(int precision, int K, KernelPair *out);
+bool heston_kernels(int precision, int K, KernelPair *out);
+bool lv_kernels(int precision, int K, KernelPair *out);
+
+// Small kernels (mc_aux.cu).
+cudaError_t launch_finalize_forward(const double *part_y, int nb, int m, double inv_n,
+                                    const double *disc, const int *perm, const double *C,
+                                    double *Ey_out, double *seed_w, double *G_out,
+                                    cudaStream_t st);
+cudaError_t launch_seed_from_ybar(const double *ybar, const int *perm, const double *disc, int m,
+                                  double *seed_w, cudaStream_t st);
+cudaError_t launch_finalize_grad(const double *part_g, int nb, int M, double inv_n, double *grad,
+                                 cudaStream_t st);
+cudaError_t launch_philox_fill(uint64_t seed, uint64_t path0, uint32_t n_paths, uint32_t n_calls,
+                               uint32_t *out, cudaStream_t st);
+cudaError_t launch_normals_fill(uint64_t seed, uint64_t path0, uint32_t n_paths,
+                                uint32_t n_per_path, int precision, void *out, cudaStream_t st);
+
+}  // namespace mcaad

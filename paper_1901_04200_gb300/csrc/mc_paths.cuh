@@ -1,0 +1,543 @@
+// mc_paths.cuh -- the forward sweep F_v and the reverse sweep R_v of the
+// two-step algorithm (arXiv 1901.04200), one thread per Monte Carlo path.
+//
+// Paths are processed in warps of 32 consecutive global paths; a block of
+// kBlock threads walks its warps over path chunks chunk = blockIdx*W + warp,
+// + gridDim*W, ...  The time axis is cut into segments of K steps (K a
+// template constant, so a segment's steps are unrolled and the reverse
+// sweep's tape lives in registers).  Every maturity lies on a segment end.
+//
+// Forward kernel (step 1, eq. 1211A): per segment, optionally store the state
+// (checkpoint, SoA [seg][state][path], coalesced), run K Euler steps with
+// Philox normals, and at a maturity sum the undiscounted call payoffs of the
+// warp's 32 paths (FP32 warp sum) into per-warp FP64 accumulators.  Block
+// end: the warps' sums in warp order -> part_y[block][i].
+//
+// Reverse kernel (step 2, eq. 0711A): per path, segments from last to first:
+// reload the checkpoint, re-run the segment's K steps (regenerating the
+// normals) while recording what the adjoint needs, add the payoff seeds
+// lambda_i e^{-rT_i} 1{S>K_i} S of a maturity at the segment end to x-bar,
+// then run the adjoint of the K steps backwards.  Parameter adjoints are
+// summed per path in the path precision, then warp-summed and added in FP64
+// to per-warp accumulators; block end -> part_g[block][j].  No atomics: the
+// result is deterministic for a given launch shape.
+#pragma once
+#include "mc_common.cuh"
+
+namespace mcaad {
+
+template <typename T>
+__device__ __forceinline__ T rsqrt_r(T x);
+template <>
+__device__ __forceinline__ float rsqrt_r<float>(float x) { return rsqrtf(x); }
+template <>
+__device__ __forceinline__ double rsqrt_r<double>(double x) { return rsqrt(x); }
+
+template <typename T>
+__device__ __forceinline__ T exp_r(T x);
+template <>
+__device__ __forceinline__ float exp_r<float>(float x) { return expf(x); }
+template <>
+__device__ __forceinline__ double exp_r<double>(double x) { return exp(x); }
+
+template <typename T>
+__device__ __forceinline__ T tiny_r();
+template <>
+__device__ __forceinline__ float tiny_r<float>() { return 1e-30f; }
+template <>
+__device__ __forceinline__ double tiny_r<double>() { return 1e-300; }
+
+// ------------------------------------------------------- shared layout ----
+
+__host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Dynamic shared memory of a path kernel, identical on host and device.
+struct SmemPlan {
+    size_t strike, grp_seg, grp_begin, seed_w, wacc_y, wacc_g, model, total;
+    __host__ __device__ SmemPlan(int kind, int real_bytes, int m, int n_groups, int M, int n_steps,
+                                 int nx, bool reverse) {
+        size_t o = 0;
+        strike = o;    o = align_up(o + (size_t)m * real_bytes, 16);
+        grp_seg = o;   o = align_up(o + (size_t)n_groups * 4, 16);
+        grp_begin = o; o = align_up(o + (size_t)(n_groups + 1) * 4, 16);
+        seed_w = o;    o = align_up(o + (reverse ? (size_t)m * real_bytes : 0), 16);
+        wacc_y = o;    o = align_up(o + (reverse ? 0 : (size_t)kWarpsPerBlock * m * 8), 16);
+        wacc_g = o;    o = align_up(o + (reverse ? (size_t)kWarpsPerBlock * M * 8 : 0), 16);
+        model = o;
+        if (kind == kGbm) {
+            o += (size_t)M * real_bytes;
+            o = align_up(o, 16);
+            o += (size_t)n_steps * 4;
+        } else if (kind == kLv) {
+            o += (size_t)n_steps * nx * real_bytes;  // time-interpolated node rows
+            o = align_up(o, 16);
+            o += (size_t)n_steps * real_bytes;       // time weight a_n
+            o = align_up(o, 16);
+            o += (size_t)n_steps * 4;                // time cell jt_n
+            o = align_up(o, 16);
+            if (reverse) o += (size_t)nx * 2 * real_bytes * kBlock;  // per-thread row adjoints
+        }
+        total = align_up(o, 16);
+    }
+};
+
+// Per-warp FP64 accumulation of a warp-summed value (lane 0 writes).
+template <typename Real>
+__device__ __forceinline__ void warp_flush(double *wacc_row, int idx, Real v, int lane) {
+    const Real s = warp_sum(v);
+    if (lane == 0) wacc_row[idx] += (double)s;
+}
+
+// ================================================================ models ====
+
+// GBM, piecewise-constant volatility theta_b over buckets of steps, log-Euler:
+// x += (r - theta_b^2/2) dt + theta_b sqrt(dt) z_n.
+template <typename Real_>
+struct GbmModel {
+    using Real = Real_;
+    static constexpr int kind = kGbm;
+    static constexpr int DZ = 1, SD = 1;
+    struct State { Real x; };
+    struct Tape { Real z; };
+    struct Shared {
+        const Real *vol;
+        const int *bucket;
+    };
+    struct Par { Real rdt, dt, sdt; };
+    struct Acc { Real g; int b; };
+
+    __device__ static void setup(unsigned char *base, const SmemPlan &sp, const DevProblem &pb,
+                                 const double *theta, int n_steps, Shared &sh, Par &par) {
+        Real *vol = (Real *)(base + sp.model);
+        int *bucket = (int *)(base + align_up(sp.model + (size_t)pb.M * sizeof(Real), 16));
+        for (int j = threadIdx.x; j < pb.M; j += blockDim.x) vol[j] = (Real)theta[j];
+        for (int n = threadIdx.x; n < n_steps; n += blockDim.x) bucket[n] = pb.bucket_of_step[n];
+        sh.vol = vol;
+        sh.bucket = bucket;
+        par.dt = (Real)pb.dt;
+        par.rdt = (Real)(pb.r * pb.dt);
+        par.sdt = (Real)sqrt(pb.dt);
+    }
+    __device__ static State init(const Par &) { return State{Real(0)}; }
+    __device__ __forceinline__ static void step(State &s, const Real *z, int n, const Par &p,
+                                                const Shared &sh, Tape *t) {
+        const Real vol = sh.vol[sh.bucket[n]];
+        s.x = s.x + ((p.rdt - Real(0.5) * vol * vol * p.dt) + vol * p.sdt * z[0]);
+        if (t) t->z = z[0];
+    }
+    __device__ static void acc_begin(Acc &a, int n_last, const Shared &sh) {
+        a.g = Real(0);
+        a.b = sh.bucket[n_last - 1];
+    }
+    // x_{n+1} = x_n + ... : x-bar passes through; theta_b-bar += xb (-vol dt + sqrt(dt) z).
+    __device__ __forceinline__ static void adjoint(const Tape &t, int n, Real &xb, Real &, Acc &a,
+                                                   const Par &p, const Shared &sh, double *wacc,
+                                                   int lane) {
+        const int b = sh.bucket[n];
+        if (b != a.b) {  // uniform across the warp: all lanes are at step n
+            warp_flush(wacc, a.b, a.g, lane);
+            a.g = Real(0);
+            a.b = b;
+        }
+        const Real vol = sh.vol[b];
+        a.g += xb * (p.sdt * t.z - vol * p.dt);
+    }
+    __device__ static void acc_end(Acc &a, Real, const Par &, double *wacc, int lane) {
+        warp_flush(wacc, a.b, a.g, lane);
+    }
+};
+
+// Heston with full-truncation Euler, theta = (kappa, theta_h, xi, rho, v0):
+// vdt = max(v,0) dt, sq = sqrt(vdt) (as vdt * rsqrt(max(vdt, tiny)), which is
+// exactly 0 at vdt = 0), w = rho z1 + sqrt(1-rho^2) z2,
+// x += (r dt - vdt/2) + sq z1,  v += (kappa theta_h dt - kappa vdt) + xi sq w.
+template <typename Real_>
+struct HestonModel {
+    using Real = Real_;
+    static constexpr int kind = kHeston;
+    static constexpr int DZ = 2, SD = 2;
+    struct State { Real x, v; };
+    struct Tape { Real vdt, rs, z1, w; };
+    struct Shared {};
+    struct Par { Real kappa, thh, xi, rho, rhob, v0, dt, rdt, kthdt; };
+    // per-path adjoint sums: kappa-bar, sum vb, sum vb sq z1, sum vb sq w
+    struct Acc { Real kb, cs, a, b; };
+
+    __device__ static void setup(unsigned char *, const SmemPlan &, const DevProblem &pb,
+                                 const double *theta, int, Shared &, Par &par) {
+        const double kappa = theta[0], thh = theta[1], xi = theta[2], rho = theta[3];
+        par.kappa = (Real)kappa;
+        par.thh = (Real)thh;
+        par.xi = (Real)xi;
+        par.rho = (Real)rho;
+        par.rhob = (Real)sqrt(1.0 - rho * rho);
+        par.v0 = (Real)theta[4];
+        par.dt = (Real)pb.dt;
+        par.rdt = (Real)(pb.r * pb.dt);
+        par.kthdt = (Real)(kappa * thh * pb.dt);
+    }
+    __device__ static State init(const Par &p) { return State{Real(0), p.v0}; }
+    __device__ __forceinline__ static void step(State &s, const Real *z, int, const Par &p,
+                                                const Shared &, Tape *t) {
+        const Real vdt = fmax(s.v, Real(0)) * p.dt;
+        const Real rs = rsqrt_r<Real>(fmax(vdt, tiny_r<Real>()));
+        const Real sq = vdt * rs;
+        const Real z1 = z[0];
+        const Real w = fma(p.rho, z1, p.rhob * z[1]);
+        s.x = s.x + fma(sq, z1, fma(Real(-0.5), vdt, p.rdt));
+        s.v = s.v + fma(p.xi * sq, w, fma(-p.kappa, vdt, p.kthdt));
+        if (t) {
+            t->vdt = vdt;
+            t->rs = rs;
+            t->z1 = z1;
+            t->w = w;
+        }
+    }
+    __device__ static void acc_begin(Acc &a, int, const Shared &) {
+        a.kb = a.cs = a.a = a.b = Real(0);
+    }
+    // Adjoint of one step given xb, vb of the state after it:
+    //   kappa-bar += vb (theta_h dt - vdt), theta_h-bar += vb kappa dt,
+    //   xi-bar += vb sq w, rho-bar += vb xi sq dw/drho,
+    //   vdt-bar = -xb/2 - kappa vb + (xb z1 + xi vb w) / (2 sq),
+    //   vb_prev = vb + 1{v > 0} dt vdt-bar,  xb_prev = xb.
+    __device__ __forceinline__ static void adjoint(const Tape &t, int, Real &xb, Real &vb, Acc &a,
+                                                   const Par &p, const Shared &, double *, int) {
+        const Real sq = t.vdt * t.rs;
+        const Real vsq = vb * sq;
+        a.a = fma(vsq, t.z1, a.a);
+        a.b = fma(vsq, t.w, a.b);
+        a.cs += vb;
+        a.kb = fma(vb, p.thh * p.dt - t.vdt, a.kb);
+        const Real sqb = fma(xb, t.z1, p.xi * vb * t.w);
+        const Real vdtb = fma(Real(0.5) * t.rs, sqb, fma(Real(-0.5), xb, -p.kappa * vb));
+        vb = (t.vdt > Real(0)) ? fma(vdtb, p.dt, vb) : vb;
+    }
+    // theta-bar = (kb, kappa dt cs, b, xi (a - rho b) / (1 - rho^2), vb at step 0);
+    // d w / d rho = z1 - rho z2 / rhob = (z1 - rho w) / rhob^2.
+    __device__ static void acc_end(Acc &a, Real vb, const Par &p, double *wacc, int lane) {
+        warp_flush(wacc, 0, a.kb, lane);
+        warp_flush(wacc, 1, p.kappa * p.dt * a.cs, lane);
+        warp_flush(wacc, 2, a.b, lane);
+        warp_flush(wacc, 3, p.xi * (a.a - p.rho * a.b) / (p.rhob * p.rhob), lane);
+        warp_flush(wacc, 4, vb, lane);
+    }
+};
+
+// Local volatility on a bilinear node surface theta[j*nx + c] over
+// (t_j, x_c), flat extrapolation; log-Euler with sigma at (t_n, x_n):
+// x += (r - sigma^2/2) dt + sigma sqrt(dt) z_n.  The time interpolation is the
+// same for every path at step n, so each block first forms the rows
+// row_n[c] = (1 - a_n) theta[jt_n][c] + a_n theta[jt_n + 1][c].
+template <typename Real_>
+struct LvModel {
+    using Real = Real_;
+    static constexpr int kind = kLv;
+    static constexpr int DZ = 1, SD = 1;
+    struct State { Real x; };
+    struct Tape { Real u, z; };  // u = (x - x_lo)/hx, z
+    struct Shared {
+        const Real *row;  // [n_steps][nx]
+        const Real *a;    // [n_steps]
+        const int *jt;    // [n_steps]
+        Real *racc;       // [nx][2][kBlock] per-thread row adjoints (reverse)
+        int nx;
+    };
+    struct Par { Real rdt, dt, sdt, x_lo, inv_hx; int nxm2; };
+    struct Acc { int jt; };
+
+    __device__ static void setup(unsigned char *base, const SmemPlan &sp, const DevProblem &pb,
+                                 const double *theta, int n_steps, Shared &sh, Par &par) {
+        const int nx = pb.nx;
+        Real *row = (Real *)(base + sp.model);
+        size_t o = align_up(sp.model + (size_t)n_steps * nx * sizeof(Real), 16);
+        Real *a = (Real *)(base + o);
+        o = align_up(o + (size_t)n_steps * sizeof(Real), 16);
+        int *jt = (int *)(base + o);
+        o = align_up(o + (size_t)n_steps * 4, 16);
+        sh.racc = (Real *)(base + o);
+        for (int n = threadIdx.x; n < n_steps; n += blockDim.x) {
+            a[n] = (Real)pb.lv_a[n];
+            jt[n] = pb.lv_jt[n];
+        }
+        for (int q = threadIdx.x; q < n_steps * nx; q += blockDim.x) {
+            const int n = q / nx, c = q - n * nx;
+            const int j = pb.lv_jt[n];
+            const double w = pb.lv_a[n];
+            row[q] = (Real)((1.0 - w) * theta[j * nx + c] + w * theta[(j + 1) * nx + c]);
+        }
+        sh.row = row;
+        sh.a = a;
+        sh.jt = jt;
+        sh.nx = nx;
+        par.dt = (Real)pb.dt;
+        par.rdt = (Real)(pb.r * pb.dt);
+        par.sdt = (Real)sqrt(pb.dt);
+        par.x_lo = (Real)pb.x_lo;
+        par.inv_hx = (Real)(1.0 / pb.hx);
+        par.nxm2 = nx - 2;
+    }
+    __device__ static State init(const Par &) { return State{Real(0)}; }
+
+    // Cell c = clamp(floor(u), 0, nx-2) and weight b = clamp(u - c, 0, 1).
+    __device__ __forceinline__ static void cell(Real u, const Par &p, int &c, Real &b, bool &inside) {
+        const Real f = floor(u);
+        c = (int)fmin(fmax(f, Real(0)), (Real)p.nxm2);
+        const Real bb = u - (Real)c;
+        inside = (bb >= Real(0)) && (bb <= Real(1));
+        b = fmin(fmax(bb, Real(0)), Real(1));
+    }
+    __device__ __forceinline__ static void step(State &s, const Real *z, int n, const Par &p,
+                                                const Shared &sh, Tape *t) {
+        const Real u = (s.x - p.x_lo) * p.inv_hx;
+        int c;
+        Real b;
+        bool inside;
+        cell(u, p, c, b, inside);
+        const Real *rw = sh.row + n * sh.nx;
+        const Real s0 = rw[c], s1 = rw[c + 1];
+        const Real sig = fma(b, s1 - s0, s0);
+        s.x = s.x + fma(sig, fma(p.sdt, z[0], Real(-0.5) * sig * p.dt), p.rdt);
+        if (t) {
+            t->u = u;
+            t->z = z[0];
+        }
+    }
+    __device__ static void acc_begin(Acc &a, int n_last, const Shared &sh) {
+        a.jt = sh.jt[n_last - 1];
+        Real *r = sh.racc;
+        for (int q = 0; q < 2 * sh.nx; ++q) r[q * kBlock + threadIdx.x] = Real(0);
+    }
+    __device__ static void flush_rows(Acc &a, const Shared &sh, double *wacc, int lane) {
+        Real *r = sh.racc;
+        for (int c = 0; c < sh.nx; ++c) {
+            Real *q0 = r + (2 * c) * kBlock + threadIdx.x;
+            Real *q1 = r + (2 * c + 1) * kBlock + threadIdx.x;
+            warp_flush(wacc, a.jt * sh.nx + c, *q0, lane);
+            warp_flush(wacc, (a.jt + 1) * sh.nx + c, *q1, lane);
+            *q0 = Real(0);
+            *q1 = Real(0);
+        }
+    }
+    // sigma-bar = xb (sqrt(dt) z - sigma dt); node adjoints sigma-bar times the
+    // bilinear weights; xb += sigma-bar d sigma/dx (0 where x is clamped).
+    __device__ __forceinline__ static void adjoint(const Tape &t, int n, Real &xb, Real &, Acc &a,
+                                                   const Par &p, const Shared &sh, double *wacc,
+                                                   int lane) {
+        const int jt = sh.jt[n];
+        if (jt != a.jt) {  // uniform across the warp
+            flush_rows(a, sh, wacc, lane);
+            a.jt = jt;
+        }
+        int c;
+        Real b;
+        bool inside;
+        cell(t.u, p, c, b, inside);
+        const Real *rw = sh.row + n * sh.nx;
+        const Real s0 = rw[c], s1 = rw[c + 1];
+        const Real ds = s1 - s0;
+        const Real sig = fma(b, ds, s0);
+        const Real sb = xb * fma(p.sdt, t.z, -sig * p.dt);
+        const Real at = sh.a[n];
+        const Real g1 = sb * b, g0 = sb - g1;
+        Real *r = sh.racc + threadIdx.x;
+        r[(2 * c) * kBlock] = fma(Real(1) - at, g0, r[(2 * c) * kBlock]);
+        r[(2 * c + 1) * kBlock] = fma(at, g0, r[(2 * c + 1) * kBlock]);
+        r[(2 * c + 2) * kBlock] = fma(Real(1) - at, g1, r[(2 * c + 2) * kBlock]);
+        r[(2 * c + 3) * kBlock] = fma(at, g1, r[(2 * c + 3) * kBlock]);
+        if (inside) xb = fma(sb * p.inv_hx, ds, xb);
+    }
+    __device__ static void acc_end(Acc &a, Real, const Par &, double *wacc, int lane,
+                                   const Shared &sh) {
+        flush_rows(a, sh, wacc, lane);
+    }
+};
+
+// ============================================================== kernels ====
+
+template <class Md>
+struct NormalSource {
+    using Real = typename Md::Real;
+    PathNormals<Real> gen;
+    const double *table;
+    __device__ __forceinline__ void init(const DevProblem &pb, const DevCall &cl, uint64_t p) {
+        gen.init(cl.seed, p);
+        table = pb.normals ? pb.normals + (size_t)(p - pb.normals_path0) * pb.normals_stride
+                           : nullptr;
+    }
+    // Normals of step n, first == true at a segment's first step.
+    __device__ __forceinline__ void get(int n, bool first, Real *z) {
+#pragma unroll
+        for (int c = 0; c < Md::DZ; ++c) {
+            const uint32_t j = (uint32_t)(n * Md::DZ + c);
+            if (table) {
+                z[c] = (Real)table[j];
+            } else {
+                if ((first && c == 0) || (j & 3u) == 0u) gen.fill(j >> 2);
+                z[c] = gen.pick(j & 3u);
+            }
+        }
+    }
+};
+
+template <class Md>
+__device__ __forceinline__ void load_tables(unsigned char *base, const SmemPlan &sp,
+                                            const DevProblem &pb, bool reverse, const DevCall &cl) {
+    using Real = typename Md::Real;
+    Real *strike = (Real *)(base + sp.strike);
+    int *gseg = (int *)(base + sp.grp_seg);
+    int *gbeg = (int *)(base + sp.grp_begin);
+    for (int i = threadIdx.x; i < pb.m; i += blockDim.x) strike[i] = (Real)pb.strike[i];
+    for (int g = threadIdx.x; g < pb.n_groups; g += blockDim.x) gseg[g] = pb.grp_seg[g];
+    for (int g = threadIdx.x; g <= pb.n_groups; g += blockDim.x) gbeg[g] = pb.grp_begin[g];
+    if (reverse) {
+        Real *sw = (Real *)(base + sp.seed_w);
+        for (int i = threadIdx.x; i < pb.m; i += blockDim.x) sw[i] = (Real)cl.seed_w[i];
+        double *wg = (double *)(base + sp.wacc_g);
+        for (int q = threadIdx.x; q < kWarpsPerBlock * pb.M; q += blockDim.x) wg[q] = 0.0;
+    } else {
+        double *wy = (double *)(base + sp.wacc_y);
+        for (int q = threadIdx.x; q < kWarpsPerBlock * pb.m; q += blockDim.x) wy[q] = 0.0;
+    }
+}
+
+template <class Md, int K>
+__global__ void __launch_bounds__(kBlock) path_forward_kernel(const DevProblem pb, const DevCall cl) {
+    using Real = typename Md::Real;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int n_steps = pb.n_seg * K;
+    const SmemPlan sp(Md::kind, sizeof(Real), pb.m, pb.n_groups, pb.M, n_steps, pb.nx, false);
+    load_tables<Md>(smem, sp, pb, false, cl);
+    typename Md::Shared sh;
+    typename Md::Par par;
+    Md::setup(smem, sp, pb, cl.theta, n_steps, sh, par);
+    __syncthreads();
+
+    const Real *strike = (const Real *)(smem + sp.strike);
+    const int *gseg = (const int *)(smem + sp.grp_seg);
+    const int *gbeg = (const int *)(smem + sp.grp_begin);
+    const int warp = threadIdx.x / kWarp, lane = threadIdx.x % kWarp;
+    double *wy = (double *)(smem + sp.wacc_y) + warp * pb.m;
+    const Real S0 = (Real)pb.S0;
+    Real *ck = (Real *)cl.ckpt;
+
+    const uint64_t n_chunks = (cl.n_paths + kWarp - 1) / kWarp;
+    for (uint64_t ch = (uint64_t)blockIdx.x * kWarpsPerBlock + warp; ch < n_chunks;
+         ch += (uint64_t)gridDim.x * kWarpsPerBlock) {
+        const uint64_t local = ch * kWarp + lane;
+        const bool active = local < cl.n_paths;
+        NormalSource<Md> rng;
+        rng.init(pb, cl, cl.path0 + (active ? local : 0));
+        typename Md::State st = Md::init(par);
+        int g = 0;
+        for (int s = 0; s < pb.n_seg; ++s) {
+            if (cl.keep_ckpt) {
+                Real *c0 = ck + ((size_t)s * Md::SD) * cl.ckpt_stride + local;
+                c0[0] = st.x;
+                if constexpr (Md::SD == 2) c0[cl.ckpt_stride] = st.v;
+            }
+#pragma unroll
+            for (int i = 0; i < K; ++i) {
+                const int n = s * K + i;
+                Real z[Md::DZ];
+                rng.get(n, i == 0, z);
+                Md::step(st, z, n, par, sh, nullptr);
+            }
+            if (g < pb.n_groups && gseg[g] == s) {
+                const Real S = S0 * exp_r<Real>(st.x);
+                for (int i = gbeg[g]; i < gbeg[g + 1]; ++i) {
+                    const Real pay = active ? fmax(S - strike[i], Real(0)) : Real(0);
+                    warp_flush(wy, i, pay, lane);
+                }
+                ++g;
+            }
+        }
+    }
+    __syncthreads();
+    const double *wall = (const double *)(smem + sp.wacc_y);
+    for (int i = threadIdx.x; i < pb.m; i += blockDim.x) {
+        double s = 0.0;
+        for (int w = 0; w < kWarpsPerBlock; ++w) s += wall[w * pb.m + i];
+        cl.part_y[(size_t)blockIdx.x * pb.m + i] = s;
+    }
+}
+
+template <class Md>
+__device__ __forceinline__ void acc_end_dispatch(typename Md::Acc &a, typename Md::Real vb,
+                                                 const typename Md::Par &p, double *wacc, int lane,
+                                                 const typename Md::Shared &sh) {
+    if constexpr (Md::kind == kLv) {
+        Md::acc_end(a, vb, p, wacc, lane, sh);
+    } else {
+        Md::acc_end(a, vb, p, wacc, lane);
+    }
+}
+
+template <class Md, int K>
+__global__ void __launch_bounds__(kBlock) path_reverse_kernel(const DevProblem pb, const DevCall cl) {
+    using Real = typename Md::Real;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int n_steps = pb.n_seg * K;
+    const SmemPlan sp(Md::kind, sizeof(Real), pb.m, pb.n_groups, pb.M, n_steps, pb.nx, true);
+    load_tables<Md>(smem, sp, pb, true, cl);
+    typename Md::Shared sh;
+    typename Md::Par par;
+    Md::setup(smem, sp, pb, cl.theta, n_steps, sh, par);
+    __syncthreads();
+
+    const Real *strike = (const Real *)(smem + sp.strike);
+    const Real *sw = (const Real *)(smem + sp.seed_w);
+    const int *gseg = (const int *)(smem + sp.grp_seg);
+    const int *gbeg = (const int *)(smem + sp.grp_begin);
+    const int warp = threadIdx.x / kWarp, lane = threadIdx.x % kWarp;
+    double *wg = (double *)(smem + sp.wacc_g) + warp * pb.M;
+    const Real S0 = (Real)pb.S0;
+    const Real *ck = (const Real *)cl.ckpt;
+
+    const uint64_t n_chunks = (cl.n_paths + kWarp - 1) / kWarp;
+    for (uint64_t ch = (uint64_t)blockIdx.x * kWarpsPerBlock + warp; ch < n_chunks;
+         ch += (uint64_t)gridDim.x * kWarpsPerBlock) {
+        const uint64_t local = ch * kWarp + lane;
+        const bool active = local < cl.n_paths;
+        NormalSource<Md> rng;
+        rng.init(pb, cl, cl.path0 + (active ? local : 0));
+        typename Md::Acc acc;
+        Md::acc_begin(acc, n_steps, sh);
+        Real xb = Real(0), vb = Real(0);
+        int g = pb.n_groups - 1;
+        for (int s = pb.n_seg - 1; s >= 0; --s) {
+            typename Md::State st;
+            const Real *c0 = ck + ((size_t)s * Md::SD) * cl.ckpt_stride + local;
+            st.x = c0[0];
+            if constexpr (Md::SD == 2) st.v = c0[cl.ckpt_stride];
+            typename Md::Tape tape[K];
+#pragma unroll
+            for (int i = 0; i < K; ++i) {
+                const int n = s * K + i;
+                Real z[Md::DZ];
+                rng.get(n, i == 0, z);
+                Md::step(st, z, n, par, sh, &tape[i]);
+            }
+            if (g >= 0 && gseg[g] == s) {
+                const Real S = S0 * exp_r<Real>(st.x);
+                Real seed = Real(0);
+                for (int i = gbeg[g]; i < gbeg[g + 1]; ++i)
+                    if (S > strike[i]) seed = fma(sw[i], S, seed);
+                if (active) xb += seed;
+                --g;
+            }
+#pragma unroll
+            for (int i = K - 1; i >= 0; --i) Md::adjoint(tape[i], s * K + i, xb, vb, acc, par, sh, wg, lane);
+        }
+        acc_end_dispatch<Md>(acc, vb, par, wg, lane, sh);
+    }
+    __syncthreads();
+    const double *wall = (const double *)(smem + sp.wacc_g);
+    for (int j = threadIdx.x; j < pb.M; j += blockDim.x) {
+        double s = 0.0;
+        for (int w = 0; w < kWarpsPerBlock; ++w) s += wall[w * pb.M + j];
+        cl.part_g[(size_t)blockIdx.x * pb.M + j] = s;
+    }
+}
+
+}  // namespace mcaad

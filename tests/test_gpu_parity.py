@@ -1,0 +1,242 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances: Philox blocks bit-exact; FP64 paths: E y, G and grad G within
+1e-10 relative (normwise for vectors); FP32 paths: grad G within 1e-4
+normwise, E y within 2e-6 of max |E y|, G within 1e-4 relative.
+"""
+from dataclasses import replace
+
+import numpy as np
+import pytest
+
+from paper_1901_04200_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def rel(a, b):
+    a, b = np.asarray(a, dtype=np.float64), np.asarray(b, dtype=np.float64)
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+@pytest.fixture(scope="module")
+def L():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1901_04200_gb300 import build as b
+    b.build()
+    from paper_1901_04200_gb300 import _lib
+    _lib.load()
+    return _lib
+
+
+def gpu_vg(L, w, n_paths=None, path0=0, seed=None):
+    n = n_paths or w.n_paths
+    ctx = L.Context(w.problem, max_paths=n)
+    G, g, Ey = ctx.value_and_grad(w.theta, w.C, w.problem.seed if seed is None else seed, n, path0=path0)
+    torch.cuda.synchronize()
+    return Ey.cpu().numpy(), G.item(), g.cpu().numpy()
+
+
+def check(L, orc, w, tol_g, tol_ey, n_paths=None, path0=0):
+    n = n_paths or w.n_paths
+    Ey, G, g = gpu_vg(L, w, n, path0)
+    Eo, Go, go = orc.value_and_grad(w.problem, w.theta, w.C, n, path0=path0)
+    assert rel(Ey, Eo) <= tol_ey, ("Ey", rel(Ey, Eo))
+    assert abs(G - Go) <= tol_g * abs(Go), ("G", G, Go)
+    assert rel(g, go) <= tol_g, ("grad", rel(g, go), g, go)
+    return Ey, G, g
+
+
+# ------------------------------------------------------------- generator
+
+@pytest.mark.parametrize("seed,path0", [(0x190104200, 0), (0, (1 << 32) - 7), (0xFFFFFFFFFFFFFFFF, 12345)])
+def test_philox_bit_exact(L, orc, seed, path0):
+    n_paths, n_calls = 37, 9
+    got = L.philox_fill(seed, path0, n_paths, n_calls).cpu().numpy().view(np.uint32)
+    ref = orc.philox_fill(seed, path0, n_paths, n_calls)
+    assert np.array_equal(got, ref)
+
+
+def test_normals_match_oracle(L, orc):
+    seed, path0, n_paths, n = 0x190104200, 1000, 257, 61
+    ref = orc.normals_fill(seed, path0, n_paths, n)
+    z64 = L.normals_fill(seed, path0, n_paths, n, "fp64").cpu().numpy()
+    assert np.max(np.abs(z64 - ref)) <= 1e-13
+    z32 = L.normals_fill(seed, path0, n_paths, n, "fp32").cpu().numpy().astype(np.float64)
+    err = np.abs(z32 - ref)
+    assert np.max(err) <= 5e-5 and np.mean(err) <= 2e-6, (np.max(err), np.mean(err))
+
+
+def test_philox_against_curand_device_api(L, tmp_path):
+    """Counter layout = cuRAND device API philox4_32_10 with subsequence = path, offset = 4 * call."""
+    import os
+    import subprocess
+    src = os.path.join(os.path.dirname(__file__), "cuda", "curand_philox_dump.cu")
+    exe = str(tmp_path / "curand_dump")
+    subprocess.run(["nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-O2", src, "-o", exe], check=True)
+    for seed, path0 in [(0x190104200, 0), (7, (1 << 32) - 3), (0xDEADBEEFCAFEF00D, (5 << 32) + 11)]:
+        out = subprocess.run([exe, str(seed), str(path0), "40", "6"], check=True, capture_output=True).stdout
+        ref = np.frombuffer(out, dtype=np.uint32).reshape(40, 6, 4)
+        got = L.philox_fill(seed, path0, 40, 6).cpu().numpy().view(np.uint32)
+        assert np.array_equal(got, ref), (seed, path0)
+
+
+# ----------------------------------------------------------- FP64 exact
+
+def test_gbm_fp64_config(L, orc):
+    """The GBM workload (normals table input, FP64 path) within 1e-10."""
+    w = inputs.gbm_config()
+    check(L, orc, w, 1e-10, 1e-12)
+
+
+def test_gbm_fp64_philox_ragged(L, orc):
+    w = inputs.gbm_config(n_paths=16)
+    w = replace(w, problem=replace(w.problem, normals=None))
+    check(L, orc, w, 1e-10, 1e-12, n_paths=1001, path0=(1 << 32) - 500)
+
+
+@pytest.mark.parametrize("K", [1, 2, 4, 8])
+def test_heston_fp64_all_segment_lengths(L, orc, K):
+    w = inputs.heston_config(n_paths=3000, steps_per_year=32, T=1.0, n_mat=4, n_strike=5)
+    w = replace(w, problem=replace(w.problem, precision="fp64", ckpt_every=K))
+    check(L, orc, w, 1e-10, 1e-12, n_paths=3000, path0=77)
+
+
+def test_heston_fp64_no_feller(L, orc):
+    """Exact arithmetic agrees even where v often truncates (FP64 on both sides)."""
+    w = inputs.heston_config(n_paths=2048, steps_per_year=32, T=1.0, n_mat=4, n_strike=5, feller=False)
+    w = replace(w, problem=replace(w.problem, precision="fp64"))
+    check(L, orc, w, 1e-9, 1e-12)
+
+
+@pytest.mark.parametrize("K", [1, 5, 25])
+def test_lv_fp64(L, orc, K):
+    w = inputs.lv_config(n_paths=1500, n_steps=100, T=2.0, nt=5, nx=6, n_mat=4, n_strike=5)
+    w = replace(w, problem=replace(w.problem, precision="fp64", ckpt_every=K))
+    check(L, orc, w, 1e-10, 1e-12)
+
+
+def test_lv_fp64_clamped_surface(L, orc):
+    w = inputs.lv_config(n_paths=999, n_steps=100, T=2.0, nt=5, nx=6, n_mat=4, n_strike=5)
+    w = replace(w, problem=replace(w.problem, precision="fp64", x_lo=-0.1, x_hi=0.15))
+    check(L, orc, w, 1e-10, 1e-12)
+
+
+# ------------------------------------------------------------ FP32 paths
+
+def test_heston_fp32_small(L, orc):
+    w = inputs.heston_config(n_paths=1 << 14, steps_per_year=64, T=2.0)
+    check(L, orc, w, 1e-4, 2e-6)
+
+
+def test_lv_fp32_small(L, orc):
+    w = inputs.lv_config(n_paths=1 << 13)
+    check(L, orc, w, 1e-4, 2e-6)
+
+
+def test_gbm_fp32(L, orc):
+    w = inputs.gbm_config()
+    w = replace(w, problem=replace(w.problem, precision="fp32"))
+    check(L, orc, w, 1e-4, 2e-6)
+
+
+# -------------------------------------------------------------- edge cases
+
+@pytest.mark.parametrize("n", [1, 31, 33, 4097])
+def test_ragged_path_counts(L, orc, n):
+    w = inputs.heston_config(n_paths=n, steps_per_year=16, T=1.0, n_mat=2, n_strike=3)
+    w = replace(w, problem=replace(w.problem, precision="fp64"))
+    check(L, orc, w, 1e-10, 1e-12)
+
+
+def test_unsorted_instruments_and_single_segment(L, orc):
+    w = inputs.heston_config(n_paths=700, steps_per_year=16, T=1.0, n_mat=4, n_strike=3)
+    pb = w.problem
+    rng = np.random.default_rng(5)
+    order = rng.permutation(pb.m)
+    pb = replace(pb, K=pb.K[order], mat_step=pb.mat_step[order], precision="fp64", ckpt_every=4)
+    w = replace(w, problem=pb, C=w.C[order])
+    check(L, orc, w, 1e-10, 1e-12)
+    # a single maturity at the first segment end
+    pb1 = replace(pb, K=np.array([95.0, 100.0, 105.0]), mat_step=np.array([4, 4, 4], dtype=np.int32))
+    w1 = replace(w, problem=pb1, C=np.array([5.0, 2.0, 1.0]))
+    check(L, orc, w1, 1e-10, 1e-12)
+
+
+def test_vjp_and_forward_match_oracle(L, orc):
+    w = inputs.lv_config(n_paths=2000, n_steps=100, T=2.0, nt=5, nx=6, n_mat=4, n_strike=5)
+    w = replace(w, problem=replace(w.problem, precision="fp64"))
+    ctx = L.Context(w.problem, max_paths=2000)
+    ybar = np.random.default_rng(3).standard_normal(w.problem.m)
+    Ey = ctx.forward(w.theta, w.problem.seed, 2000, path0=5, keep=True)
+    tb = ctx.vjp(ybar)
+    torch.cuda.synchronize()
+    assert rel(Ey.cpu().numpy(), orc.forward(w.problem, w.theta, 2000, path0=5)) <= 1e-12
+    assert rel(tb.cpu().numpy(), orc.vjp(w.problem, w.theta, ybar, 2000, path0=5)) <= 1e-10
+
+
+def test_vjp_requires_kept_checkpoints(L):
+    w = inputs.heston_config(n_paths=64, steps_per_year=16, T=1.0, n_mat=2, n_strike=2)
+    ctx = L.Context(w.problem, max_paths=64)
+    ctx.forward(w.theta, 1, 64, keep=False)
+    with pytest.raises(L.McError) as e:
+        ctx.vjp(np.ones(w.problem.m))
+    assert e.value.status == L.MC_ERR_STATE
+
+
+def test_call_argument_errors(L):
+    w = inputs.heston_config(n_paths=64, steps_per_year=16, T=1.0, n_mat=2, n_strike=2)
+    ctx = L.Context(w.problem, max_paths=64)
+    with pytest.raises(L.McError) as e:
+        ctx.forward(w.theta, 1, 65)
+    assert e.value.status == L.MC_ERR_INVALID_ARG
+
+
+def test_partition_invariance(L):
+    """Global path indices: two half ranges combine to the full range."""
+    w = inputs.heston_config(n_paths=1 << 14, steps_per_year=64, T=1.0, n_mat=4, n_strike=4)
+    ctx = L.Context(w.problem, max_paths=1 << 14)
+    full = ctx.forward(w.theta, 9, 1 << 14).cpu().numpy()
+    a = ctx.forward(w.theta, 9, 6000).cpu().numpy()
+    b = ctx.forward(w.theta, 9, (1 << 14) - 6000, path0=6000).cpu().numpy()
+    comb = (6000 * a + ((1 << 14) - 6000) * b) / (1 << 14)
+    assert rel(comb, full) <= 1e-13
+
+
+def test_deterministic_repeat(L):
+    w = inputs.heston_config(n_paths=1 << 15, steps_per_year=64, T=1.0, n_mat=4, n_strike=4)
+    a = gpu_vg(L, w)
+    b = gpu_vg(L, w)
+    assert np.array_equal(a[0], b[0]) and a[1] == b[1] and np.array_equal(a[2], b[2])
+
+
+# ------------------------------------------------------------ full sizes
+
+@pytest.mark.slow
+def test_heston_full_size(L, orc):
+    """The benchmark workload (2^20 paths x 512 steps, launch shape of the bench) vs the oracle."""
+    w = inputs.heston_config()
+    check(L, orc, w, 1e-4, 2e-6)
+
+
+@pytest.mark.slow
+def test_lv_full_size_sampled(L, orc):
+    """2^22 x 500 local vol: a 2^13-path slice at the top of the range vs the oracle, and the
+    full run equals the size-weighted combination of its two halves."""
+    w = inputs.lv_config()
+    n = w.n_paths
+    ctx = L.Context(w.problem, max_paths=n)
+    p0 = n - (1 << 13)
+    Ey_s = ctx.forward(w.theta, w.problem.seed, 1 << 13, path0=p0).cpu().numpy()
+    Eo = orc.forward(w.problem, w.theta, 1 << 13, path0=p0)
+    assert rel(Ey_s, Eo) <= 2e-6
+    G, g, Ey = ctx.value_and_grad(w.theta, w.C, w.problem.seed, n)
+    Ey = Ey.cpu().numpy()
+    h = n // 2
+    a = ctx.forward(w.theta, w.problem.seed, h).cpu().numpy()
+    b = ctx.forward(w.theta, w.problem.seed, n - h, path0=h).cpu().numpy()
+    assert rel((a + b) / 2, Ey) <= 1e-12
+    assert np.all(np.isfinite(g.cpu().numpy()))
