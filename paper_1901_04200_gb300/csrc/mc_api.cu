@@ -34,7 +34,8 @@ struct mc_ctx {
     unsigned char *ws = nullptr;
     size_t ws_bytes = 0;
     void *ckpt = nullptr;
-    double *part_y = nullptr, *part_g = nullptr, *seed_w = nullptr;
+    double *part_y = nullptr, *part_g = nullptr, *seed_w = nullptr, *lam2 = nullptr;
+    unsigned int *ticket = nullptr;
     // state for mc_vjp
     bool have_ckpt = false;
     DevCall last{};
@@ -208,7 +209,8 @@ mc_status make_plan(const mc_model *md, const mc_instruments *in, Plan &p, std::
 
 // Workspace carve-out (256-byte aligned pieces).
 struct WsLayout {
-    size_t strike, disc, perm, grp_seg, grp_begin, bucket, lv_jt, lv_a, seed_w, part_y, part_g, ckpt, total;
+    size_t strike, disc, perm, grp_seg, grp_begin, bucket, lv_jt, lv_a, seed_w, lam2, ticket, part_y, part_g,
+        ckpt, total;
     WsLayout(const Plan &p, int grid_max, uint64_t ckpt_stride) {
         size_t o = 0;
         auto take = [&](size_t bytes) {
@@ -225,6 +227,8 @@ struct WsLayout {
         lv_jt = take(p.lv_jt.size() * 4);
         lv_a = take(p.lv_a.size() * 8);
         seed_w = take(p.m * 8);
+        lam2 = take(p.m * 8);
+        ticket = take(4);
         part_y = take((size_t)grid_max * p.m * 8);
         part_g = take((size_t)grid_max * p.M * 8);
         const size_t real = p.precision == MC_FP64 ? 8 : 4;
@@ -415,6 +419,7 @@ mc_status mc_context_create(int device, const mc_model *model, const mc_instrume
     if (e == cudaSuccess) e = up(L.bucket, p.bucket.data(), p.bucket.size() * 4);
     if (e == cudaSuccess) e = up(L.lv_jt, p.lv_jt.data(), p.lv_jt.size() * 4);
     if (e == cudaSuccess) e = up(L.lv_a, p.lv_a.data(), p.lv_a.size() * 8);
+    if (e == cudaSuccess) e = cudaMemset(w + L.ticket, 0, 4);
     if (e != cudaSuccess) {
         fprintf(stderr, "mc_context_create: table upload: %s\n", cudaGetErrorString(e));
         mc_context_destroy(ctx);
@@ -424,6 +429,8 @@ mc_status mc_context_create(int device, const mc_model *model, const mc_instrume
     ctx->part_y = (double *)(w + L.part_y);
     ctx->part_g = (double *)(w + L.part_g);
     ctx->seed_w = (double *)(w + L.seed_w);
+    ctx->lam2 = (double *)(w + L.lam2);
+    ctx->ticket = (unsigned int *)(w + L.ticket);
     DevProblem &pb = ctx->pb;
     pb.kind = p.kind;
     pb.K = p.K;
@@ -529,7 +536,7 @@ mc_status mc_forward(mc_ctx *ctx, const double *theta, uint64_t seed, uint64_t p
     if (s != MC_OK) return s;
     cudaError_t e = timed(ctx, MC_K_FINALIZE_Y, st, [&] {
         return launch_finalize_forward(ctx->part_y, grid, ctx->m, 1.0 / (double)n_paths, ctx->pb.disc,
-                                       ctx->pb.perm, nullptr, Ey_out, nullptr, nullptr, st);
+                                       ctx->pb.perm, nullptr, Ey_out, nullptr, nullptr, nullptr, nullptr, st);
     });
     if (e != cudaSuccess) return cuda_fail(ctx, e, "forward finalize launch");
     if (keep_checkpoints) {
@@ -569,7 +576,7 @@ mc_status mc_value_and_grad(mc_ctx *ctx, const double *theta, const double *C, u
     if (s != MC_OK) return s;
     cudaError_t e = timed(ctx, MC_K_FINALIZE_Y, st, [&] {
         return launch_finalize_forward(ctx->part_y, grid, ctx->m, 1.0 / (double)n_paths, ctx->pb.disc,
-                                       ctx->pb.perm, C, Ey_out, ctx->seed_w, G_out, st);
+                                       ctx->pb.perm, C, Ey_out, ctx->seed_w, ctx->lam2, ctx->ticket, G_out, st);
     });
     if (e != cudaSuccess) return cuda_fail(ctx, e, "forward finalize launch");
     ctx->last = cl;

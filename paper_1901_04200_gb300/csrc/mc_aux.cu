@@ -8,32 +8,55 @@ namespace mcaad {
 
 constexpr int kFinBlock = 256;
 
-// E y_i = disc_i * (sum over blocks, in block order) / P  (caller order via
-// perm); with targets C: lambda_i = E y_i - C_i, seed_i = lambda_i disc_i and
-// G = 1/2 sum_i lambda_i^2 summed in sorted-instrument order by one thread.
+// Fixed-order sum of v[0], v[stride], ... v[(n-1)*stride] by one block: each
+// thread adds its strided subsequence in order, then a fixed tree over the
+// threads.  Deterministic for a given n.
+__device__ double block_ordered_sum(const double *__restrict__ v, int n, size_t stride, double *red) {
+    double s = 0.0;
+    for (int b = threadIdx.x; b < n; b += blockDim.x) s += v[(size_t)b * stride];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    return red[0];
+}
+
+// One block per instrument i (sorted order): E y_i = disc_i * (sum over the
+// forward sweep's blocks) / P, written in caller order via perm.  With
+// targets C: lambda_i = E y_i - C_i, seed_i = lambda_i disc_i, and the last
+// block to finish (atomic ticket, no waiting) forms G = 1/2 sum_i lambda_i^2 in
+// instrument order and resets the ticket.
 __global__ void __launch_bounds__(kFinBlock)
 finalize_forward_kernel(const double *__restrict__ part_y, int nb, int m, double inv_n,
                         const double *__restrict__ disc, const int *__restrict__ perm,
                         const double *__restrict__ C, double *Ey_out, double *seed_w,
-                        double *G_out) {
-    extern __shared__ double lam2[];
-    for (int i = threadIdx.x; i < m; i += blockDim.x) {
-        double s = 0.0;
-        for (int b = 0; b < nb; ++b) s += part_y[(size_t)b * m + i];
+                        double *lam2, unsigned int *ticket, double *G_out) {
+    __shared__ double red[kFinBlock];
+    __shared__ bool last;
+    const int i = blockIdx.x;
+    const double s = block_ordered_sum(part_y + i, nb, (size_t)m, red);
+    if (threadIdx.x == 0) {
         const double ey = disc[i] * (s * inv_n);
         const int ci = perm[i];
         if (Ey_out) Ey_out[ci] = ey;
+        last = false;
         if (C) {
             const double lam = ey - C[ci];
             seed_w[i] = lam * disc[i];
             lam2[i] = lam * lam;
+            __threadfence();
+            last = atomicAdd(ticket, 1u) == (unsigned)(m - 1);
         }
     }
     __syncthreads();
-    if (C && threadIdx.x == 0) {
+    if (last && threadIdx.x == 0) {
+        __threadfence();
         double g = 0.0;
-        for (int i = 0; i < m; ++i) g += lam2[i];
+        for (int q = 0; q < m; ++q) g += ((volatile double *)lam2)[q];
         *G_out = 0.5 * g;
+        *ticket = 0u;
     }
 }
 
@@ -43,13 +66,13 @@ __global__ void seed_from_ybar_kernel(const double *__restrict__ ybar, const int
         seed_w[i] = ybar[perm[i]] * disc[i];
 }
 
+// One block per parameter j: grad_j = (sum over the reverse sweep's blocks) / P.
 __global__ void __launch_bounds__(kFinBlock)
 finalize_grad_kernel(const double *__restrict__ part_g, int nb, int M, double inv_n, double *grad) {
-    for (int j = threadIdx.x; j < M; j += blockDim.x) {
-        double s = 0.0;
-        for (int b = 0; b < nb; ++b) s += part_g[(size_t)b * M + j];
-        grad[j] = s * inv_n;
-    }
+    __shared__ double red[kFinBlock];
+    const int j = blockIdx.x;
+    const double s = block_ordered_sum(part_g + j, nb, (size_t)M, red);
+    if (threadIdx.x == 0) grad[j] = s * inv_n;
 }
 
 __global__ void philox_fill_kernel(uint64_t seed, uint64_t path0, uint32_t n_paths, uint32_t n_calls,
@@ -93,10 +116,10 @@ static int grid_for(uint64_t work, int block) {
 
 cudaError_t launch_finalize_forward(const double *part_y, int nb, int m, double inv_n,
                                     const double *disc, const int *perm, const double *C,
-                                    double *Ey_out, double *seed_w, double *G_out,
-                                    cudaStream_t st) {
-    finalize_forward_kernel<<<1, kFinBlock, (size_t)m * sizeof(double), st>>>(
-        part_y, nb, m, inv_n, disc, perm, C, Ey_out, seed_w, G_out);
+                                    double *Ey_out, double *seed_w, double *lam2,
+                                    unsigned int *ticket, double *G_out, cudaStream_t st) {
+    finalize_forward_kernel<<<m, kFinBlock, 0, st>>>(part_y, nb, m, inv_n, disc, perm, C, Ey_out,
+                                                      seed_w, lam2, ticket, G_out);
     return cudaGetLastError();
 }
 
@@ -108,7 +131,7 @@ cudaError_t launch_seed_from_ybar(const double *ybar, const int *perm, const dou
 
 cudaError_t launch_finalize_grad(const double *part_g, int nb, int M, double inv_n, double *grad,
                                  cudaStream_t st) {
-    finalize_grad_kernel<<<1, kFinBlock, 0, st>>>(part_g, nb, M, inv_n, grad);
+    finalize_grad_kernel<<<M, kFinBlock, 0, st>>>(part_g, nb, M, inv_n, grad);
     return cudaGetLastError();
 }
 

@@ -21,8 +21,8 @@ bool lv_kernels(int precision, int K, KernelPair *out);
 // Small kernels (mc_aux.cu).
 cudaError_t launch_finalize_forward(const double *part_y, int nb, int m, double inv_n,
                                     const double *disc, const int *perm, const double *C,
-                                    double *Ey_out, double *seed_w, double *G_out,
-                                    cudaStream_t st);
+                                    double *Ey_out, double *seed_w, double *lam2,
+                                    unsigned int *ticket, double *G_out, cudaStream_t st);
 cudaError_t launch_seed_from_ybar(const double *ybar, const int *perm, const double *disc, int m,
                                   double *seed_w, cudaStream_t st);
 cudaError_t launch_finalize_grad(const double *part_g, int nb, int M, double inv_n, double *grad,

@@ -362,15 +362,17 @@ struct NormalSource {
     const double *table;
     __device__ __forceinline__ void init(const DevProblem &pb, const DevCall &cl, uint64_t p) {
         gen.init(cl.seed, p);
-        table = pb.normals ? pb.normals + (size_t)(p - pb.normals_path0) * pb.normals_stride
-                           : nullptr;
+        table = nullptr;
+        if constexpr (Md::kind == kGbm) {  // a normals table is accepted for GBM only
+            if (pb.normals) table = pb.normals + (size_t)(p - pb.normals_path0) * pb.normals_stride;
+        }
     }
     // Normals of step n, first == true at a segment's first step.
     __device__ __forceinline__ void get(int n, bool first, Real *z) {
 #pragma unroll
         for (int c = 0; c < Md::DZ; ++c) {
             const uint32_t j = (uint32_t)(n * Md::DZ + c);
-            if (table) {
+            if (Md::kind == kGbm && table) {
                 z[c] = (Real)table[j];
             } else {
                 if ((first && c == 0) || (j & 3u) == 0u) gen.fill(j >> 2);
