@@ -185,6 +185,28 @@ enum { MC_K_FORWARD = 0, MC_K_FINALIZE_Y = 1, MC_K_SEED = 2, MC_K_REVERSE = 3, M
 mc_status mc_profile_begin(mc_ctx *ctx, int32_t max_launches);
 mc_status mc_profile_end(mc_ctx *ctx, double *ms_out, int32_t *launches_out);
 
+/* E y with no device allocation at all: the same forward sweep and E y
+ * finalize as mc_forward, for callers that cannot call cudaMalloc -- for
+ * example code running in a process whose device memory is owned by another
+ * allocator's pool, or a latency-critical loop that must not pay
+ * cudaMalloc's implicit device synchronisation.  The paper has no
+ * counterpart; it is a deployment convenience.
+ * The caller passes the model, instruments (as for mc_context_create), theta
+ * (FP64 [M], device) and Ey_out (FP64 [m], device); no context is needed.
+ * Scratch (model tables and per-block partial sums) lives in one fixed
+ * device array of MC_STATIC_SCRATCH_BYTES that every GPU loading the library
+ * holds until the process exits.  The first call on a device looks up that
+ * array's device address, so make the first call on each device before any
+ * stream capture.  A problem whose tables and one row of partial sums do not
+ * fit returns MC_ERR_INVALID_ARG with a message on stderr.  Every call
+ * shares the array and leaves the last call's contents in it (nothing is read
+ * before this call writes it); calls that overlap on the GPU, on any stream,
+ * race on it.  No checkpoints are kept (use a context for mc_vjp). */
+#define MC_STATIC_SCRATCH_BYTES ((size_t)4 << 20)
+mc_status mc_forward_static(const mc_model *model, const mc_instruments *inst, const double *theta,
+                            uint64_t seed, uint64_t path0, uint64_t n_paths, double *Ey_out,
+                            void *stream);
+
 #ifdef __cplusplus
 }
 #endif

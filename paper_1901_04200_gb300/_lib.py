@@ -71,6 +71,7 @@ SIGNATURES = [
     ("mc_normals_fill", ctypes.c_int, [_U64, _U64, _U32, _U32, _I32, _V, _V]),
     ("mc_profile_begin", ctypes.c_int, [_V, _I32]),
     ("mc_profile_end", ctypes.c_int, [_V, _P(ctypes.c_double), _P(_I32)]),
+    ("mc_forward_static", ctypes.c_int, [_P(mc_model), _P(mc_instruments), _V, _U64, _U64, _U64, _V, _V]),
 ]
 KERNEL_NAMES = ["forward_sweep", "finalize_y", "seed", "reverse_sweep", "finalize_grad"]
 

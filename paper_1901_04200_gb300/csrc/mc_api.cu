@@ -647,3 +647,145 @@ mc_status mc_normals_fill(uint64_t seed, uint64_t path0, uint32_t n_paths, uint3
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// mc_forward_static: E y with no device allocation by anyone.  Its scratch
+// (model tables and per-block partial sums) lives in one file-scope device
+// array that every GPU loading this library holds until the process exits.
+// Host code may not use the array's name as an address; the device address
+// is looked up once per device with cudaGetSymbolAddress.
+// ---------------------------------------------------------------------------
+
+#include <mutex>
+
+namespace {
+
+constexpr size_t kStaticScratchBytes = (size_t)4 << 20;  // MC_STATIC_SCRATCH_BYTES
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+unsigned char *g_static_ptr[kMaxDevices] = {nullptr};
+
+}  // namespace
+
+extern "C" mc_status mc_forward_static(const mc_model *model, const mc_instruments *inst,
+                                       const double *theta, uint64_t seed, uint64_t path0,
+                                       uint64_t n_paths, double *Ey_out, void *stream) {
+    if (!theta || !Ey_out || ((uintptr_t)theta & 7u) || ((uintptr_t)Ey_out & 7u) || n_paths == 0) {
+        fprintf(stderr, "mc_forward_static: theta and Ey_out must be FP64 device pointers, n_paths >= 1\n");
+        return MC_ERR_INVALID_ARG;
+    }
+    Plan p;
+    std::string why;
+    mc_status st = make_plan(model, inst, p, why);
+    if (st != MC_OK) {
+        fprintf(stderr, "mc_forward_static: %s\n", why.c_str());
+        return st;
+    }
+    if (model->normals) {
+        if (path0 < model->normals_path0 || path0 + n_paths > model->normals_path0 + model->normals_rows) {
+            fprintf(stderr, "mc_forward_static: paths outside the normals table\n");
+            return MC_ERR_INVALID_ARG;
+        }
+    }
+    KernelPair kp;
+    if (!kernels_for(p, &kp)) return MC_ERR_UNSUPPORTED;
+    int device = 0;
+    cudaError_t e = cudaGetDevice(&device);
+    if (e != cudaSuccess || device < 0 || device >= kMaxDevices) {
+        fprintf(stderr, "mc_forward_static: no usable current device\n");
+        return MC_ERR_CUDA;
+    }
+    unsigned char *scratch = nullptr;
+    {
+        // set-up, once per device, with that device current
+        std::lock_guard<std::mutex> lk(g_static_mu);
+        if (!g_static_ptr[device]) {
+            void *ptr = nullptr;
+            e = cudaGetSymbolAddress(&ptr, g_static_scratch);
+            if (e != cudaSuccess || !ptr) {
+                fprintf(stderr, "mc_forward_static: cudaGetSymbolAddress: %s\n", cudaGetErrorString(e));
+                return MC_ERR_CUDA;
+            }
+            g_static_ptr[device] = (unsigned char *)ptr;
+        }
+        scratch = g_static_ptr[device];
+    }
+    int n_sm = 1, grid_fwd = 1, grid_rev = 1;
+    size_t smem_fwd = 0, smem_rev = 0;
+    st = launch_shape(p, device, kp, model->nx, &n_sm, &grid_fwd, &grid_rev, &smem_fwd, &smem_rev, why);
+    if (st != MC_OK) {
+        fprintf(stderr, "mc_forward_static: %s\n", why.c_str());
+        return st;
+    }
+    // scratch layout: the context's table layout with no checkpoints, then as
+    // many per-block partial rows as fit
+    WsLayout L(p, 0, 0);
+    const size_t part_bytes = (size_t)p.m * 8;
+    if (L.total + part_bytes > kStaticScratchBytes) {
+        fprintf(stderr, "mc_forward_static: problem needs %zu bytes of scratch, limit %zu\n",
+                L.total + part_bytes, kStaticScratchBytes);
+        return MC_ERR_INVALID_ARG;
+    }
+    const int fit = (int)((kStaticScratchBytes - L.total) / part_bytes);
+    int grid = grid_for_paths(grid_fwd < fit ? grid_fwd : fit, n_paths);
+    cudaStream_t s = (cudaStream_t)stream;
+    auto up = [&](size_t off, const void *src, size_t bytes) {
+        return bytes ? cudaMemcpyAsync(scratch + off, src, bytes, cudaMemcpyHostToDevice, s) : cudaSuccess;
+    };
+    e = up(L.strike, p.strike.data(), p.m * 8);
+    if (e == cudaSuccess) e = up(L.disc, p.disc.data(), p.m * 8);
+    if (e == cudaSuccess) e = up(L.perm, p.perm.data(), p.m * 4);
+    if (e == cudaSuccess) e = up(L.grp_seg, p.grp_seg.data(), p.n_groups * 4);
+    if (e == cudaSuccess) e = up(L.grp_begin, p.grp_begin.data(), (p.n_groups + 1) * 4);
+    if (e == cudaSuccess) e = up(L.bucket, p.bucket.data(), p.bucket.size() * 4);
+    if (e == cudaSuccess) e = up(L.lv_jt, p.lv_jt.data(), p.lv_jt.size() * 4);
+    if (e == cudaSuccess) e = up(L.lv_a, p.lv_a.data(), p.lv_a.size() * 8);
+    if (e != cudaSuccess) {
+        fprintf(stderr, "mc_forward_static: table upload: %s\n", cudaGetErrorString(e));
+        return MC_ERR_CUDA;
+    }
+    DevProblem pb{};
+    pb.kind = p.kind;
+    pb.K = p.K;
+    pb.n_seg = p.n_seg;
+    pb.m = p.m;
+    pb.M = p.M;
+    pb.n_groups = p.n_groups;
+    pb.S0 = model->S0;
+    pb.r = model->r;
+    pb.dt = model->dt;
+    pb.strike = (const double *)(scratch + L.strike);
+    pb.disc = (const double *)(scratch + L.disc);
+    pb.perm = (const int *)(scratch + L.perm);
+    pb.grp_seg = (const int *)(scratch + L.grp_seg);
+    pb.grp_begin = (const int *)(scratch + L.grp_begin);
+    pb.bucket_of_step = (const int *)(scratch + L.bucket);
+    pb.lv_jt = (const int *)(scratch + L.lv_jt);
+    pb.lv_a = (const double *)(scratch + L.lv_a);
+    pb.nt = model->nt;
+    pb.nx = model->nx;
+    pb.x_lo = model->x_lo;
+    pb.hx = p.hx;
+    pb.normals = model->normals;
+    pb.normals_path0 = model->normals_path0;
+    pb.normals_rows = model->normals_rows;
+    pb.normals_stride = model->n_steps * (p.kind == kHeston ? 2 : 1);
+    DevCall cl{};
+    cl.theta = theta;
+    cl.seed = seed;
+    cl.path0 = path0;
+    cl.n_paths = n_paths;
+    cl.keep_ckpt = 0;
+    cl.part_y = (double *)(scratch + L.total);
+    e = launch(kp.fwd, grid, smem_fwd, pb, cl, s);
+    if (e == cudaSuccess)
+        e = launch_finalize_forward(cl.part_y, grid, p.m, 1.0 / (double)n_paths, pb.disc, pb.perm, nullptr,
+                                    Ey_out, nullptr, nullptr, nullptr, nullptr, s);
+    if (e != cudaSuccess) {
+        fprintf(stderr, "mc_forward_static: launch: %s\n", cudaGetErrorString(e));
+        return MC_ERR_CUDA;
+    }
+    return MC_OK;
+}
