@@ -30,8 +30,9 @@ def test_backward_equals_value_and_grad(L):
     G = calibration_objective(mc, th, C, 11, 1 << 14)
     G.backward()
     G2, g2, _ = mc.value_and_grad(w.theta, w.C, 11, 1 << 14)
-    assert G.item() == G2.item()
-    assert torch.equal(th.grad, g2)
+    # torch sums lambda^2 in its own order: G agrees to rounding; the seeds are identical
+    assert abs(G.item() - G2.item()) <= 1e-14 * abs(G2.item())
+    assert torch.allclose(th.grad, g2, rtol=1e-14, atol=0)
 
 
 def test_backward_after_another_forward(L):
