@@ -188,6 +188,8 @@ def main():
     ap.add_argument("--cpu-paths", type=int, default=1 << 16)
     ap.add_argument("--ref-paths", type=int, default=1 << 15)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ppt", type=int, default=0, help="paths per GPU thread (0 = library default)")
+    ap.add_argument("--ckpt", type=int, default=0, help="checkpoint interval (0 = workload default)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -203,6 +205,9 @@ def main():
         _build.build()
     barrier(world)
     w = inputs.heston_config(n_paths=args.paths)
+    if args.ppt or args.ckpt:
+        w.problem.paths_per_thread = args.ppt
+        w.problem.ckpt_every = args.ckpt or w.problem.ckpt_every
     pb, P, S = w.problem, w.n_paths, w.problem.last_step
     path0 = rank * P
     dev = torch.device("cuda", torch.cuda.current_device())
@@ -281,12 +286,13 @@ def main():
             "warmup": max(args.warmup, 3), "ms_per_step": ms_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": w.name, "paths_per_gpu": P, "steps": S, "instruments": pb.m, "params": 5,
-                       "ckpt_every": pb.ckpt_every, "precision": "fp32 paths, fp64 sums",
+                       "ckpt_every": pb.ckpt_every, "paths_per_thread": pb.paths_per_thread or "default",
+                       "precision": "fp32 paths, fp64 sums",
                        "l2": "inputs larger than L2: checkpoints %.0f MB per step" %
                              (P * (S // pb.ckpt_every) * 2 * 4 / 1e6)},
             "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": issue_peak / 1e12,
                          "unit": "Tops/s", "frac": achieved / issue_peak, "traffic": None,
-                         "kernel": "path_reverse_kernel<Heston,f32,8>",
+                         "kernel": "path_reverse_kernel<Heston,f32,K=%d>" % pb.ckpt_every,
                          "ops_per_path_step": _ops("reverse_sweep"),
                          "peak_basis": "SM issue rate 128 thread-ops/clk x %d SMs x %.0f MHz (%s max clock)"
                                        % (n_sm, sm_mhz_peak, peak_src),

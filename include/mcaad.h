@@ -82,6 +82,8 @@ typedef enum { MC_FP64 = 0, MC_FP32 = 1 } mc_precision;
  *                x += (r - sigma^2/2) dt + sigma sqrt(dt) z_n.           M = nt*nx
  * ckpt_every: checkpoint interval k of the reverse sweep (0 = library
  * default); it must divide every maturity step.
+ * paths_per_thread: 1 or 2 independent paths per GPU thread (0 = library
+ * default); results agree to rounding of the FP32 warp sums.
  * normals: optional device FP64 table [rows][n_steps * normals_per_step]
  * (row = global path - normals_path0) used instead of Philox; GBM only.
  */
@@ -98,6 +100,7 @@ typedef struct {
     const double *normals;
     uint64_t normals_path0;
     uint64_t normals_rows;
+    int32_t paths_per_thread;
 } mc_model;
 
 /* European calls y_i = exp(-r T_i) max(S0 e^{x_{n_i}} - K_i, 0), T_i = n_i dt
@@ -160,6 +163,22 @@ mc_status mc_vjp(mc_ctx *ctx, const double *ybar, double *theta_bar_out, void *s
 mc_status mc_value_and_grad(mc_ctx *ctx, const double *theta, const double *C, uint64_t seed,
                             uint64_t path0, uint64_t n_paths, double *G_out, double *grad_out,
                             double *Ey_out, void *stream);
+
+/* Forward-mode Jacobian for many Heston parameter vectors (the gradient
+ * identity's pathwise derivatives dy_i/dtheta_j, carried forward as five
+ * tangents per path instead of one reverse sweep per instrument; the labels
+ * of the pricing surrogate).  For t < n_theta: Ey_out[t][i] = mean of y_i and
+ * J_out[t][i][j] = mean of dy_i/dtheta_j over global paths
+ * [t n_paths, (t+1) n_paths) of `seed`, at thetas[t][0..5) (Heston contexts
+ * only; MC_ERR_UNSUPPORTED otherwise).  strikes: optional FP64 [n_theta][m]
+ * replacing the context's strikes per t (maturities stay the context's).
+ * Ey_out (nullable) FP64 [n_theta][m]; J_out FP64 [n_theta][m][5]; scratch:
+ * device buffer of mc_price_jacobian_scratch_size bytes.  Kink conventions
+ * as the reverse sweep.  1 <= n_theta <= 65535. */
+mc_status mc_price_jacobian_scratch_size(mc_ctx *ctx, int32_t n_theta, uint64_t n_paths, size_t *bytes_out);
+mc_status mc_price_jacobian(mc_ctx *ctx, const double *thetas, const double *strikes, int32_t n_theta,
+                            uint64_t seed, uint64_t n_paths, double *Ey_out, double *J_out, void *scratch,
+                            size_t scratch_bytes, void *stream);
 
 /* Test hooks for the generator.  mc_philox_fill: out uint32
  * [n_paths][n_calls][4], block (call c, path path0+i).  mc_normals_fill:

@@ -40,7 +40,7 @@ class mc_model(ctypes.Structure):
         ("nt", ctypes.c_int32), ("nx", ctypes.c_int32),
         ("t_max", ctypes.c_double), ("x_lo", ctypes.c_double), ("x_hi", ctypes.c_double),
         ("normals", ctypes.c_void_p), ("normals_path0", ctypes.c_uint64),
-        ("normals_rows", ctypes.c_uint64),
+        ("normals_rows", ctypes.c_uint64), ("paths_per_thread", ctypes.c_int32),
     ]
 
 
@@ -72,6 +72,8 @@ SIGNATURES = [
     ("mc_profile_begin", ctypes.c_int, [_V, _I32]),
     ("mc_profile_end", ctypes.c_int, [_V, _P(ctypes.c_double), _P(_I32)]),
     ("mc_forward_static", ctypes.c_int, [_P(mc_model), _P(mc_instruments), _V, _U64, _U64, _U64, _V, _V]),
+    ("mc_price_jacobian_scratch_size", ctypes.c_int, [_V, _I32, _U64, _P(_SZ)]),
+    ("mc_price_jacobian", ctypes.c_int, [_V, _V, _V, _I32, _U64, _U64, _V, _V, _V, _SZ, _V]),
 ]
 KERNEL_NAMES = ["forward_sweep", "finalize_y", "seed", "reverse_sweep", "finalize_grad"]
 
@@ -119,6 +121,7 @@ class _ProblemC:
         md.S0, md.r, md.dt = float(pb.S0), float(pb.r), float(pb.dt)
         md.n_steps = int(pb.n_steps)
         md.ckpt_every = int(pb.ckpt_every or 0)
+        md.paths_per_thread = int(getattr(pb, "paths_per_thread", 0) or 0)
         if pb.kind == "gbm":
             be = np.ascontiguousarray(pb.bucket_end, dtype=np.int32)
             self.keep.append(be)
@@ -215,6 +218,25 @@ class Context:
                                         _stream(stream)), self.handle)
         self._theta_keep = th
         return G, grad, Ey
+
+    def price_jacobian(self, thetas, seed: int, n_paths: int, strikes=None, stream=None):
+        """(E y [n_theta, m], J [n_theta, m, 5]) by forward-mode tangents (mc_price_jacobian)."""
+        th = torch.as_tensor(thetas, dtype=torch.float64, device=self.device).reshape(-1, self.M).contiguous()
+        nt = th.shape[0]
+        kt = None
+        if strikes is not None:
+            kt = torch.as_tensor(strikes, dtype=torch.float64, device=self.device).reshape(nt, self.m).contiguous()
+        nbytes = ctypes.c_size_t(0)
+        _check(load().mc_price_jacobian_scratch_size(self.handle, nt, int(n_paths), ctypes.byref(nbytes)),
+               self.handle)
+        scratch = torch.empty(max(int(nbytes.value), 8) // 8 + 1, dtype=torch.float64, device=self.device)
+        Ey = torch.empty((nt, self.m), dtype=torch.float64, device=self.device)
+        J = torch.empty((nt, self.m, self.M), dtype=torch.float64, device=self.device)
+        _check(load().mc_price_jacobian(self.handle, _ptr(th), _ptr(kt) if kt is not None else None, nt, int(seed),
+                                        int(n_paths), _ptr(Ey), _ptr(J), _ptr(scratch), scratch.numel() * 8,
+                                        _stream(stream)), self.handle)
+        self._jac_keep = (th, kt, scratch)
+        return Ey, J
 
     def profile_begin(self, max_launches: int):
         _check(load().mc_profile_begin(self.handle, int(max_launches)), self.handle)

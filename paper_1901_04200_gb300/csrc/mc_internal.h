@@ -13,10 +13,11 @@ struct KernelPair {
     const void *rev = nullptr;
 };
 
-// Path kernels of (kind, precision, K); false if that K is not instantiated.
-bool gbm_kernels(int precision, int K, KernelPair *out);
-bool heston_kernels(int precision, int K, KernelPair *out);
-bool lv_kernels(int precision, int K, KernelPair *out);
+// Path kernels of (kind, precision, segment length K, paths per thread);
+// false if that combination is not instantiated.
+bool gbm_kernels(int precision, int K, int ppt, KernelPair *out);
+bool heston_kernels(int precision, int K, int ppt, KernelPair *out);
+bool lv_kernels(int precision, int K, int ppt, KernelPair *out);
 
 // Small kernels (mc_aux.cu).
 cudaError_t launch_finalize_forward(const double *part_y, int nb, int m, double inv_n,
@@ -31,5 +32,13 @@ cudaError_t launch_philox_fill(uint64_t seed, uint64_t path0, uint32_t n_paths, 
                                uint32_t *out, cudaStream_t st);
 cudaError_t launch_normals_fill(uint64_t seed, uint64_t path0, uint32_t n_paths,
                                 uint32_t n_per_path, int precision, void *out, cudaStream_t st);
+
+// Forward-mode Jacobian (mc_jacobian.cu).
+size_t jacobian_smem_bytes(int m, int n_groups, int precision);
+const void *jacobian_kernel(int precision);
+cudaError_t launch_jacobian(const DevProblem &pb, int precision, const double *thetas, const double *strikes_t,
+                            int n_theta, uint64_t seed, uint64_t n_paths, int bpt, size_t smem,
+                            double *part, const double *disc, const int *perm, double *Ey_out,
+                            double *J_out, cudaStream_t st);
 
 }  // namespace mcaad

@@ -1,8 +1,10 @@
 // mc_paths.cuh -- the forward sweep F_v and the reverse sweep R_v of the
 // two-step algorithm (arXiv 1901.04200), one thread per Monte Carlo path.
 //
-// Paths are processed in warps of 32 consecutive global paths; a block of
-// kBlock threads walks its warps over path chunks chunk = blockIdx*W + warp,
+// Paths are processed in chunks of 32*PPT consecutive global paths per warp:
+// lane l carries paths chunk*32*PPT + q*32 + l for q < PPT (PPT independent
+// recursions per thread give the scheduler instruction-level parallelism);
+// a block of kBlock threads walks its warps over chunks blockIdx*W + warp,
 // + gridDim*W, ...  The time axis is cut into segments of K steps (K a
 // template constant, so a segment's steps are unrolled and the reverse
 // sweep's tape lives in registers).  Every maturity lies on a segment end.
@@ -18,9 +20,10 @@
 // normals) while recording what the adjoint needs, add the payoff seeds
 // lambda_i e^{-rT_i} 1{S>K_i} S of a maturity at the segment end to x-bar,
 // then run the adjoint of the K steps backwards.  Parameter adjoints are
-// summed per path in the path precision, then warp-summed and added in FP64
-// to per-warp accumulators; block end -> part_g[block][j].  No atomics: the
-// result is deterministic for a given launch shape.
+// summed per thread over its paths in the path precision, then warp-summed
+// and added in FP64 to per-warp accumulators (one lane per value); block end
+// -> part_g[block][j].  No atomics: the result is deterministic for a given
+// launch shape.
 #pragma once
 #include "mc_common.cuh"
 
@@ -81,14 +84,33 @@ struct SmemPlan {
     }
 };
 
-// Per-warp FP64 accumulation of a warp-summed value (lane 0 writes).
-template <typename Real>
-__device__ __forceinline__ void warp_flush(double *wacc_row, int idx, Real v, int lane) {
-    const Real s = warp_sum(v);
-    if (lane == 0) wacc_row[idx] += (double)s;
+// Warp-sum n values v[0..n) and add sum j, in FP64, to wacc_row[idx0 + j];
+// lane j performs the add for value j (one FP64 instruction per 32 values).
+template <typename Real, int N>
+__device__ __forceinline__ void warp_flush_n(double *wacc_row, int idx0, const Real (&v)[N], int lane) {
+    Real mine = Real(0);
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+        const Real s = warp_sum(v[j]);
+        mine = (lane == (j & 31)) ? s : mine;
+        if ((j & 31) == 31 || j == N - 1) {
+            if (lane <= (j & 31)) wacc_row[idx0 + (j & ~31) + lane] += (double)mine;
+            mine = Real(0);
+        }
+    }
 }
 
 // ================================================================ models ====
+//
+// Model interface used by the kernels:
+//   State / Tape        per path; Tape is what the adjoint of one step needs
+//   Acc                 per thread: linear sums over the thread's paths of a chunk
+//   setup(...)          block-level preparation (shared tables, parameters)
+//   step(st, z, n, ...) one Euler step; records the tape when given one
+//   boundary(acc, n, ...)  before the adjoints of step n (warp-uniform): flush
+//                       accumulators whose parameter slot changes
+//   adjoint(tape, n, xb, vb, acc, ...)  adjoint of step n for one path
+//   acc_end(acc, vb_sum, ...)  flush at the end of a chunk
 
 // GBM, piecewise-constant volatility theta_b over buckets of steps, log-Euler:
 // x += (r - theta_b^2/2) dt + theta_b sqrt(dt) z_n.
@@ -129,21 +151,24 @@ struct GbmModel {
         a.g = Real(0);
         a.b = sh.bucket[n_last - 1];
     }
-    // x_{n+1} = x_n + ... : x-bar passes through; theta_b-bar += xb (-vol dt + sqrt(dt) z).
-    __device__ __forceinline__ static void adjoint(const Tape &t, int n, Real &xb, Real &, Acc &a,
-                                                   const Par &p, const Shared &sh, double *wacc,
-                                                   int lane) {
+    __device__ __forceinline__ static void boundary(Acc &a, int n, const Shared &sh, double *wacc, int lane) {
         const int b = sh.bucket[n];
         if (b != a.b) {  // uniform across the warp: all lanes are at step n
-            warp_flush(wacc, a.b, a.g, lane);
+            const Real v[1] = {a.g};
+            warp_flush_n(wacc, a.b, v, lane);
             a.g = Real(0);
             a.b = b;
         }
-        const Real vol = sh.vol[b];
+    }
+    // x_{n+1} = x_n + ... : x-bar passes through; theta_b-bar += xb (-vol dt + sqrt(dt) z).
+    __device__ __forceinline__ static void adjoint(const Tape &t, int, Real &xb, Real &, Acc &a,
+                                                   const Par &p, const Shared &sh) {
+        const Real vol = sh.vol[a.b];
         a.g += xb * (p.sdt * t.z - vol * p.dt);
     }
-    __device__ static void acc_end(Acc &a, Real, const Par &, double *wacc, int lane) {
-        warp_flush(wacc, a.b, a.g, lane);
+    __device__ static void acc_end(Acc &a, Real, const Par &, const Shared &, double *wacc, int lane) {
+        const Real v[1] = {a.g};
+        warp_flush_n(wacc, a.b, v, lane);
     }
 };
 
@@ -160,7 +185,7 @@ struct HestonModel {
     struct Tape { Real vdt, rs, z1, w; };
     struct Shared {};
     struct Par { Real kappa, thh, xi, rho, rhob, v0, dt, rdt, kthdt; };
-    // per-path adjoint sums: kappa-bar, sum vb, sum vb sq z1, sum vb sq w
+    // sums over paths: kappa-bar, vb, vb sq z1, vb sq w
     struct Acc { Real kb, cs, a, b; };
 
     __device__ static void setup(unsigned char *, const SmemPlan &, const DevProblem &pb,
@@ -193,16 +218,15 @@ struct HestonModel {
             t->w = w;
         }
     }
-    __device__ static void acc_begin(Acc &a, int, const Shared &) {
-        a.kb = a.cs = a.a = a.b = Real(0);
-    }
+    __device__ static void acc_begin(Acc &a, int, const Shared &) { a.kb = a.cs = a.a = a.b = Real(0); }
+    __device__ __forceinline__ static void boundary(Acc &, int, const Shared &, double *, int) {}
     // Adjoint of one step given xb, vb of the state after it:
     //   kappa-bar += vb (theta_h dt - vdt), theta_h-bar += vb kappa dt,
     //   xi-bar += vb sq w, rho-bar += vb xi sq dw/drho,
     //   vdt-bar = -xb/2 - kappa vb + (xb z1 + xi vb w) / (2 sq),
     //   vb_prev = vb + 1{v > 0} dt vdt-bar,  xb_prev = xb.
     __device__ __forceinline__ static void adjoint(const Tape &t, int, Real &xb, Real &vb, Acc &a,
-                                                   const Par &p, const Shared &, double *, int) {
+                                                   const Par &p, const Shared &) {
         const Real sq = t.vdt * t.rs;
         const Real vsq = vb * sq;
         a.a = fma(vsq, t.z1, a.a);
@@ -213,14 +237,12 @@ struct HestonModel {
         const Real vdtb = fma(Real(0.5) * t.rs, sqb, fma(Real(-0.5), xb, -p.kappa * vb));
         vb = (t.vdt > Real(0)) ? fma(vdtb, p.dt, vb) : vb;
     }
-    // theta-bar = (kb, kappa dt cs, b, xi (a - rho b) / (1 - rho^2), vb at step 0);
+    // theta-bar = (kb, kappa dt cs, b, xi (a - rho b) / (1 - rho^2), sum of vb at step 0);
     // d w / d rho = z1 - rho z2 / rhob = (z1 - rho w) / rhob^2.
-    __device__ static void acc_end(Acc &a, Real vb, const Par &p, double *wacc, int lane) {
-        warp_flush(wacc, 0, a.kb, lane);
-        warp_flush(wacc, 1, p.kappa * p.dt * a.cs, lane);
-        warp_flush(wacc, 2, a.b, lane);
-        warp_flush(wacc, 3, p.xi * (a.a - p.rho * a.b) / (p.rhob * p.rhob), lane);
-        warp_flush(wacc, 4, vb, lane);
+    __device__ static void acc_end(Acc &a, Real vb_sum, const Par &p, const Shared &, double *wacc, int lane) {
+        const Real v[5] = {a.kb, p.kappa * p.dt * a.cs, a.b, p.xi * (a.a - p.rho * a.b) / (p.rhob * p.rhob),
+                           vb_sum};
+        warp_flush_n(wacc, 0, v, lane);
     }
 };
 
@@ -234,6 +256,7 @@ struct LvModel {
     using Real = Real_;
     static constexpr int kind = kLv;
     static constexpr int DZ = 1, SD = 1;
+    static constexpr int kMaxNx = 32;
     struct State { Real x; };
     struct Tape { Real u, z; };  // u = (x - x_lo)/hx, z
     struct Shared {
@@ -308,27 +331,32 @@ struct LvModel {
         Real *r = sh.racc;
         for (int q = 0; q < 2 * sh.nx; ++q) r[q * kBlock + threadIdx.x] = Real(0);
     }
-    __device__ static void flush_rows(Acc &a, const Shared &sh, double *wacc, int lane) {
-        Real *r = sh.racc;
-        for (int c = 0; c < sh.nx; ++c) {
-            Real *q0 = r + (2 * c) * kBlock + threadIdx.x;
-            Real *q1 = r + (2 * c + 1) * kBlock + threadIdx.x;
-            warp_flush(wacc, a.jt * sh.nx + c, *q0, lane);
-            warp_flush(wacc, (a.jt + 1) * sh.nx + c, *q1, lane);
-            *q0 = Real(0);
-            *q1 = Real(0);
+    // Rows jt and jt+1 are the contiguous node range [jt*nx, (jt+2)*nx).
+    __device__ __noinline__ static void flush_rows(Acc &a, const Shared &sh, double *wacc, int lane) {
+        Real *r = sh.racc + threadIdx.x;
+        const int nx = sh.nx;
+        for (int row = 0; row < 2; ++row) {
+            Real mine = Real(0);
+            for (int c = 0; c < nx; ++c) {
+                Real *q = r + (2 * c + row) * kBlock;
+                const Real s = warp_sum(*q);
+                *q = Real(0);
+                mine = (lane == c) ? s : mine;
+            }
+            if (lane < nx) wacc[(a.jt + row) * nx + lane] += (double)mine;
         }
     }
-    // sigma-bar = xb (sqrt(dt) z - sigma dt); node adjoints sigma-bar times the
-    // bilinear weights; xb += sigma-bar d sigma/dx (0 where x is clamped).
-    __device__ __forceinline__ static void adjoint(const Tape &t, int n, Real &xb, Real &, Acc &a,
-                                                   const Par &p, const Shared &sh, double *wacc,
-                                                   int lane) {
+    __device__ __forceinline__ static void boundary(Acc &a, int n, const Shared &sh, double *wacc, int lane) {
         const int jt = sh.jt[n];
         if (jt != a.jt) {  // uniform across the warp
             flush_rows(a, sh, wacc, lane);
             a.jt = jt;
         }
+    }
+    // sigma-bar = xb (sqrt(dt) z - sigma dt); node adjoints sigma-bar times the
+    // bilinear weights; xb += sigma-bar d sigma/dx (0 where x is clamped).
+    __device__ __forceinline__ static void adjoint(const Tape &t, int n, Real &xb, Real &, Acc &,
+                                                   const Par &p, const Shared &sh) {
         int c;
         Real b;
         bool inside;
@@ -347,8 +375,7 @@ struct LvModel {
         r[(2 * c + 3) * kBlock] = fma(at, g1, r[(2 * c + 3) * kBlock]);
         if (inside) xb = fma(sb * p.inv_hx, ds, xb);
     }
-    __device__ static void acc_end(Acc &a, Real, const Par &, double *wacc, int lane,
-                                   const Shared &sh) {
+    __device__ static void acc_end(Acc &a, Real, const Par &, const Shared &sh, double *wacc, int lane) {
         flush_rows(a, sh, wacc, lane);
     }
 };
@@ -403,7 +430,7 @@ __device__ __forceinline__ void load_tables(unsigned char *base, const SmemPlan 
     }
 }
 
-template <class Md, int K>
+template <class Md, int K, int PPT>
 __global__ void __launch_bounds__(kBlock) path_forward_kernel(const DevProblem pb, const DevCall cl) {
     using Real = typename Md::Real;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -423,33 +450,57 @@ __global__ void __launch_bounds__(kBlock) path_forward_kernel(const DevProblem p
     const Real S0 = (Real)pb.S0;
     Real *ck = (Real *)cl.ckpt;
 
-    const uint64_t n_chunks = (cl.n_paths + kWarp - 1) / kWarp;
+    constexpr uint64_t kChunk = (uint64_t)kWarp * PPT;
+    const uint64_t n_chunks = (cl.n_paths + kChunk - 1) / kChunk;
     for (uint64_t ch = (uint64_t)blockIdx.x * kWarpsPerBlock + warp; ch < n_chunks;
          ch += (uint64_t)gridDim.x * kWarpsPerBlock) {
-        const uint64_t local = ch * kWarp + lane;
-        const bool active = local < cl.n_paths;
-        NormalSource<Md> rng;
-        rng.init(pb, cl, cl.path0 + (active ? local : 0));
-        typename Md::State st = Md::init(par);
+        uint64_t local[PPT];
+        bool active[PPT];
+        NormalSource<Md> rng[PPT];
+        typename Md::State st[PPT];
+#pragma unroll
+        for (int q = 0; q < PPT; ++q) {
+            local[q] = ch * kChunk + q * kWarp + lane;
+            active[q] = local[q] < cl.n_paths;
+            rng[q].init(pb, cl, cl.path0 + (active[q] ? local[q] : 0));
+            st[q] = Md::init(par);
+        }
         int g = 0;
         for (int s = 0; s < pb.n_seg; ++s) {
             if (cl.keep_ckpt) {
-                Real *c0 = ck + ((size_t)s * Md::SD) * cl.ckpt_stride + local;
-                c0[0] = st.x;
-                if constexpr (Md::SD == 2) c0[cl.ckpt_stride] = st.v;
+#pragma unroll
+                for (int q = 0; q < PPT; ++q) {
+                    Real *c0 = ck + ((size_t)s * Md::SD) * cl.ckpt_stride + local[q];
+                    c0[0] = st[q].x;
+                    if constexpr (Md::SD == 2) c0[cl.ckpt_stride] = st[q].v;
+                }
             }
 #pragma unroll
             for (int i = 0; i < K; ++i) {
                 const int n = s * K + i;
-                Real z[Md::DZ];
-                rng.get(n, i == 0, z);
-                Md::step(st, z, n, par, sh, nullptr);
+#pragma unroll
+                for (int q = 0; q < PPT; ++q) {
+                    Real z[Md::DZ];
+                    rng[q].get(n, i == 0, z);
+                    Md::step(st[q], z, n, par, sh, nullptr);
+                }
             }
             if (g < pb.n_groups && gseg[g] == s) {
-                const Real S = S0 * exp_r<Real>(st.x);
-                for (int i = gbeg[g]; i < gbeg[g + 1]; ++i) {
-                    const Real pay = active ? fmax(S - strike[i], Real(0)) : Real(0);
-                    warp_flush(wy, i, pay, lane);
+                Real S[PPT];
+#pragma unroll
+                for (int q = 0; q < PPT; ++q) S[q] = S0 * exp_r<Real>(st[q].x);
+                for (int i0 = gbeg[g]; i0 < gbeg[g + 1]; i0 += kWarp) {
+                    const int cnt = min(kWarp, gbeg[g + 1] - i0);
+                    Real mine = Real(0);
+                    for (int j = 0; j < cnt; ++j) {
+                        Real pay = Real(0);
+#pragma unroll
+                        for (int q = 0; q < PPT; ++q)
+                            pay += active[q] ? fmax(S[q] - strike[i0 + j], Real(0)) : Real(0);
+                        const Real sum = warp_sum(pay);
+                        mine = (lane == j) ? sum : mine;
+                    }
+                    if (lane < cnt) wy[i0 + lane] += (double)mine;
                 }
                 ++g;
             }
@@ -464,18 +515,7 @@ __global__ void __launch_bounds__(kBlock) path_forward_kernel(const DevProblem p
     }
 }
 
-template <class Md>
-__device__ __forceinline__ void acc_end_dispatch(typename Md::Acc &a, typename Md::Real vb,
-                                                 const typename Md::Par &p, double *wacc, int lane,
-                                                 const typename Md::Shared &sh) {
-    if constexpr (Md::kind == kLv) {
-        Md::acc_end(a, vb, p, wacc, lane, sh);
-    } else {
-        Md::acc_end(a, vb, p, wacc, lane);
-    }
-}
-
-template <class Md, int K>
+template <class Md, int K, int PPT>
 __global__ void __launch_bounds__(kBlock) path_reverse_kernel(const DevProblem pb, const DevCall cl) {
     using Real = typename Md::Real;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -496,42 +536,67 @@ __global__ void __launch_bounds__(kBlock) path_reverse_kernel(const DevProblem p
     const Real S0 = (Real)pb.S0;
     const Real *ck = (const Real *)cl.ckpt;
 
-    const uint64_t n_chunks = (cl.n_paths + kWarp - 1) / kWarp;
+    constexpr uint64_t kChunk = (uint64_t)kWarp * PPT;
+    const uint64_t n_chunks = (cl.n_paths + kChunk - 1) / kChunk;
     for (uint64_t ch = (uint64_t)blockIdx.x * kWarpsPerBlock + warp; ch < n_chunks;
          ch += (uint64_t)gridDim.x * kWarpsPerBlock) {
-        const uint64_t local = ch * kWarp + lane;
-        const bool active = local < cl.n_paths;
-        NormalSource<Md> rng;
-        rng.init(pb, cl, cl.path0 + (active ? local : 0));
+        uint64_t local[PPT];
+        bool active[PPT];
+        NormalSource<Md> rng[PPT];
+        Real xb[PPT], vb[PPT];
+#pragma unroll
+        for (int q = 0; q < PPT; ++q) {
+            local[q] = ch * kChunk + q * kWarp + lane;
+            active[q] = local[q] < cl.n_paths;
+            rng[q].init(pb, cl, cl.path0 + (active[q] ? local[q] : 0));
+            xb[q] = Real(0);
+            vb[q] = Real(0);
+        }
         typename Md::Acc acc;
         Md::acc_begin(acc, n_steps, sh);
-        Real xb = Real(0), vb = Real(0);
         int g = pb.n_groups - 1;
         for (int s = pb.n_seg - 1; s >= 0; --s) {
-            typename Md::State st;
-            const Real *c0 = ck + ((size_t)s * Md::SD) * cl.ckpt_stride + local;
-            st.x = c0[0];
-            if constexpr (Md::SD == 2) st.v = c0[cl.ckpt_stride];
-            typename Md::Tape tape[K];
+            typename Md::State st[PPT];
+            typename Md::Tape tape[PPT][K];
+#pragma unroll
+            for (int q = 0; q < PPT; ++q) {
+                const Real *c0 = ck + ((size_t)s * Md::SD) * cl.ckpt_stride + local[q];
+                st[q].x = c0[0];
+                if constexpr (Md::SD == 2) st[q].v = c0[cl.ckpt_stride];
+            }
 #pragma unroll
             for (int i = 0; i < K; ++i) {
                 const int n = s * K + i;
-                Real z[Md::DZ];
-                rng.get(n, i == 0, z);
-                Md::step(st, z, n, par, sh, &tape[i]);
+#pragma unroll
+                for (int q = 0; q < PPT; ++q) {
+                    Real z[Md::DZ];
+                    rng[q].get(n, i == 0, z);
+                    Md::step(st[q], z, n, par, sh, &tape[q][i]);
+                }
             }
             if (g >= 0 && gseg[g] == s) {
-                const Real S = S0 * exp_r<Real>(st.x);
-                Real seed = Real(0);
-                for (int i = gbeg[g]; i < gbeg[g + 1]; ++i)
-                    if (S > strike[i]) seed = fma(sw[i], S, seed);
-                if (active) xb += seed;
+#pragma unroll
+                for (int q = 0; q < PPT; ++q) {
+                    const Real S = S0 * exp_r<Real>(st[q].x);
+                    Real seed = Real(0);
+                    for (int i = gbeg[g]; i < gbeg[g + 1]; ++i)
+                        if (S > strike[i]) seed = fma(sw[i], S, seed);
+                    if (active[q]) xb[q] += seed;
+                }
                 --g;
             }
 #pragma unroll
-            for (int i = K - 1; i >= 0; --i) Md::adjoint(tape[i], s * K + i, xb, vb, acc, par, sh, wg, lane);
+            for (int i = K - 1; i >= 0; --i) {
+                const int n = s * K + i;
+                Md::boundary(acc, n, sh, wg, lane);
+#pragma unroll
+                for (int q = 0; q < PPT; ++q) Md::adjoint(tape[q][i], n, xb[q], vb[q], acc, par, sh);
+            }
         }
-        acc_end_dispatch<Md>(acc, vb, par, wg, lane, sh);
+        Real vb_sum = Real(0);
+#pragma unroll
+        for (int q = 0; q < PPT; ++q) vb_sum += vb[q];
+        Md::acc_end(acc, vb_sum, par, sh, wg, lane);
     }
     __syncthreads();
     const double *wall = (const double *)(smem + sp.wacc_g);

@@ -1,36 +1,52 @@
 // mc_paths_heston.cu -- instantiations of the forward and reverse path kernels
-// for the HestonModel model, one per (precision, segment length K).
+// for the HestonModel model, one per (precision, segment length K, paths per thread).
 #include "mc_internal.h"
 #include "mc_paths.cuh"
 
 namespace mcaad {
 
 template <typename Real>
-static bool pick(int K, KernelPair *out) {
-    switch (K) {
-    case 8:
-        out->fwd = (const void *)path_forward_kernel<HestonModel<Real>, 8>;
-        out->rev = (const void *)path_reverse_kernel<HestonModel<Real>, 8>;
+static bool pick(int K, int ppt, KernelPair *out) {
+    if (K == 8 && ppt == 1) {
+        out->fwd = (const void *)path_forward_kernel<HestonModel<Real>, 8, 1>;
+        out->rev = (const void *)path_reverse_kernel<HestonModel<Real>, 8, 1>;
         return true;
-    case 4:
-        out->fwd = (const void *)path_forward_kernel<HestonModel<Real>, 4>;
-        out->rev = (const void *)path_reverse_kernel<HestonModel<Real>, 4>;
-        return true;
-    case 2:
-        out->fwd = (const void *)path_forward_kernel<HestonModel<Real>, 2>;
-        out->rev = (const void *)path_reverse_kernel<HestonModel<Real>, 2>;
-        return true;
-    case 1:
-        out->fwd = (const void *)path_forward_kernel<HestonModel<Real>, 1>;
-        out->rev = (const void *)path_reverse_kernel<HestonModel<Real>, 1>;
-        return true;
-    default:
-        return false;
     }
+    if (K == 4 && ppt == 1) {
+        out->fwd = (const void *)path_forward_kernel<HestonModel<Real>, 4, 1>;
+        out->rev = (const void *)path_reverse_kernel<HestonModel<Real>, 4, 1>;
+        return true;
+    }
+    if (K == 2 && ppt == 1) {
+        out->fwd = (const void *)path_forward_kernel<HestonModel<Real>, 2, 1>;
+        out->rev = (const void *)path_reverse_kernel<HestonModel<Real>, 2, 1>;
+        return true;
+    }
+    if (K == 1 && ppt == 1) {
+        out->fwd = (const void *)path_forward_kernel<HestonModel<Real>, 1, 1>;
+        out->rev = (const void *)path_reverse_kernel<HestonModel<Real>, 1, 1>;
+        return true;
+    }
+    if (K == 8 && ppt == 2) {
+        out->fwd = (const void *)path_forward_kernel<HestonModel<Real>, 8, 2>;
+        out->rev = (const void *)path_reverse_kernel<HestonModel<Real>, 8, 2>;
+        return true;
+    }
+    if (K == 4 && ppt == 2) {
+        out->fwd = (const void *)path_forward_kernel<HestonModel<Real>, 4, 2>;
+        out->rev = (const void *)path_reverse_kernel<HestonModel<Real>, 4, 2>;
+        return true;
+    }
+    if (K == 2 && ppt == 2) {
+        out->fwd = (const void *)path_forward_kernel<HestonModel<Real>, 2, 2>;
+        out->rev = (const void *)path_reverse_kernel<HestonModel<Real>, 2, 2>;
+        return true;
+    }
+    return false;
 }
 
-bool heston_kernels(int precision, int K, KernelPair *out) {
-    return precision == 0 ? pick<double>(K, out) : pick<float>(K, out);
+bool heston_kernels(int precision, int K, int ppt, KernelPair *out) {
+    return precision == 0 ? pick<double>(K, ppt, out) : pick<float>(K, ppt, out);
 }
 
 }  // namespace mcaad

@@ -46,7 +46,7 @@ class Problem:
     Instrument i: call with strike K[i] paying at step mat_step[i].
     normals: optional FP64 table [P, n_steps * normals_per_step] for global
     paths normals_path0.. (GBM workload); otherwise Philox with key ``seed``.
-    precision / ckpt_every are knobs of the CUDA path ("fp64" | "fp32").
+    precision / ckpt_every / paths_per_thread are knobs of the CUDA path.
     """
     kind: str
     S0: float
@@ -66,6 +66,7 @@ class Problem:
     normals_path0: int = 0
     precision: str = "fp32"
     ckpt_every: int = 0
+    paths_per_thread: int = 0
 
     @property
     def m(self) -> int:

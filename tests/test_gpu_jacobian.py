@@ -1,0 +1,79 @@
+"""Forward-mode Jacobian (surrogate labels) against the oracle.
+
+Row i of d E y/d theta is the oracle's vector-Jacobian product with the unit
+seed e_i; J^T lambda must equal grad G of the two-step algorithm on the same
+paths (the gradient identity)."""
+from dataclasses import replace
+
+import numpy as np
+import pytest
+
+from paper_1901_04200_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def L():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1901_04200_gb300 import build as b
+    b.build()
+    from paper_1901_04200_gb300 import _lib
+    return _lib
+
+
+def rel(a, b):
+    return float(np.max(np.abs(np.asarray(a) - np.asarray(b))) / max(np.max(np.abs(b)), 1e-300))
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("fp32", 1e-4)])
+def test_jacobian_matches_oracle(L, orc, precision, tol):
+    w = inputs.heston_config(n_paths=1500, steps_per_year=32, T=1.0, n_mat=4, n_strike=4)
+    pb = replace(w.problem, precision=precision)
+    n, seed = 1500, 5
+    rng = np.random.default_rng(7)
+    thetas = np.stack([w.theta] + [inputs.draw_heston_theta(rng) for _ in range(2)])
+    strikes = rng.uniform(70.0, 130.0, (3, pb.m))
+    ctx = L.Context(pb, max_paths=n)
+    Ey, J = ctx.price_jacobian(thetas, seed, n, strikes=strikes)
+    Ey, J = Ey.cpu().numpy(), J.cpu().numpy()
+    for t in range(3):
+        pbt = replace(pb, K=strikes[t], seed=seed)
+        Eo = orc.forward(pbt, thetas[t], n, path0=t * n)
+        Jo = np.stack([orc.vjp(pbt, thetas[t], np.eye(pb.m)[i], n, path0=t * n) for i in range(pb.m)])
+        assert rel(Ey[t], Eo) <= (1e-12 if precision == "fp64" else 2e-6)
+        assert rel(J[t], Jo) <= tol, (t, rel(J[t], Jo))
+
+
+def test_jacobian_transpose_lambda_is_grad_G(L):
+    w = inputs.heston_config(n_paths=1 << 14, steps_per_year=64, T=1.0, n_mat=4, n_strike=4)
+    pb = replace(w.problem, precision="fp64")
+    n, seed = 1 << 14, 21
+    ctx = L.Context(pb, max_paths=n)
+    G, g, Ey = ctx.value_and_grad(w.theta, w.C, seed, n)
+    Ey2, J = ctx.price_jacobian(w.theta[None, :], seed, n)
+    lam = Ey2[0] - torch.tensor(w.C, dtype=torch.float64, device="cuda")
+    g2 = J[0].T @ lam
+    assert rel(Ey2[0].cpu().numpy(), Ey.cpu().numpy()) <= 1e-12
+    assert rel(g2.cpu().numpy(), g.cpu().numpy()) <= 1e-10
+
+
+def test_jacobian_many_thetas_fp32(L, orc):
+    """The label-generation shape: many parameter vectors, one block each."""
+    w = inputs.heston_config(n_paths=1024, steps_per_year=64, T=2.0)
+    pb = w.problem
+    rng = np.random.default_rng(11)
+    nt, n = 2048, 1024
+    thetas = np.stack([inputs.draw_heston_theta(rng) for _ in range(nt)])
+    ctx = L.Context(pb, max_paths=n)
+    Ey, J = ctx.price_jacobian(thetas, 3, n)
+    Ey, J = Ey.cpu().numpy(), J.cpu().numpy()
+    assert np.all(np.isfinite(Ey)) and np.all(np.isfinite(J))
+    for t in [0, 777, nt - 1]:
+        pbt = replace(pb, seed=3)
+        Eo = orc.forward(pbt, thetas[t], n, path0=t * n)
+        assert rel(Ey[t], Eo) <= 2e-6
+        gi = orc.vjp(pbt, thetas[t], np.eye(pb.m)[10], n, path0=t * n)
+        assert rel(J[t, 10], gi) <= 1e-4

@@ -98,10 +98,10 @@ def test_gbm_fp64_philox_ragged(L, orc):
     check(L, orc, w, 1e-10, 1e-12, n_paths=1001, path0=(1 << 32) - 500)
 
 
-@pytest.mark.parametrize("K", [1, 2, 4, 8])
-def test_heston_fp64_all_segment_lengths(L, orc, K):
+@pytest.mark.parametrize("K,ppt", [(1, 1), (2, 1), (4, 1), (8, 1), (2, 2), (4, 2), (8, 2)])
+def test_heston_fp64_all_segment_lengths(L, orc, K, ppt):
     w = inputs.heston_config(n_paths=3000, steps_per_year=32, T=1.0, n_mat=4, n_strike=5)
-    w = replace(w, problem=replace(w.problem, precision="fp64", ckpt_every=K))
+    w = replace(w, problem=replace(w.problem, precision="fp64", ckpt_every=K, paths_per_thread=ppt))
     check(L, orc, w, 1e-10, 1e-12, n_paths=3000, path0=77)
 
 
@@ -112,10 +112,10 @@ def test_heston_fp64_no_feller(L, orc):
     check(L, orc, w, 1e-9, 1e-12)
 
 
-@pytest.mark.parametrize("K", [1, 5, 25])
-def test_lv_fp64(L, orc, K):
+@pytest.mark.parametrize("K,ppt", [(1, 1), (5, 1), (25, 1), (5, 2)])
+def test_lv_fp64(L, orc, K, ppt):
     w = inputs.lv_config(n_paths=1500, n_steps=100, T=2.0, nt=5, nx=6, n_mat=4, n_strike=5)
-    w = replace(w, problem=replace(w.problem, precision="fp64", ckpt_every=K))
+    w = replace(w, problem=replace(w.problem, precision="fp64", ckpt_every=K, paths_per_thread=ppt))
     check(L, orc, w, 1e-10, 1e-12)
 
 
@@ -127,8 +127,10 @@ def test_lv_fp64_clamped_surface(L, orc):
 
 # ------------------------------------------------------------ FP32 paths
 
-def test_heston_fp32_small(L, orc):
+@pytest.mark.parametrize("K,ppt", [(8, 1), (4, 2), (2, 2)])
+def test_heston_fp32_small(L, orc, K, ppt):
     w = inputs.heston_config(n_paths=1 << 14, steps_per_year=64, T=2.0)
+    w = replace(w, problem=replace(w.problem, ckpt_every=K, paths_per_thread=ppt))
     check(L, orc, w, 1e-4, 2e-6)
 
 
