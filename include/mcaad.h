@@ -180,6 +180,16 @@ mc_status mc_price_jacobian(mc_ctx *ctx, const double *thetas, const double *str
                             uint64_t seed, uint64_t n_paths, double *Ey_out, double *J_out, void *scratch,
                             size_t scratch_bytes, void *stream);
 
+/* The tensor-core GEMM used by the pricing surrogate, as a plain operation:
+ * D[s][M][N] (row stride ldd, slice stride M*ldd) = A[:, s*k_slice .. +k_slice)
+ * B[:, same]^T for s < K / k_slice, with A [M][lda] and B [N][ldb] BF16 (K
+ * contiguous), FP32 accumulation on tcgen05 tensor cores.  M % 128 == 0,
+ * N % 16 == 0 and N <= 256, K and k_slice multiples of 64, lda/ldb multiples
+ * of 8, A and B 16-byte aligned.  err: optional device int set to 1 if a
+ * wait on the tensor cores exceeded its limit (the result is then invalid). */
+mc_status mc_tc_gemm_bf16(const void *A, int64_t lda, const void *B, int64_t ldb, int32_t M, int32_t N, int32_t K,
+                          int32_t k_slice, float *D, int64_t ldd, int32_t *err, void *stream);
+
 /* Test hooks for the generator.  mc_philox_fill: out uint32
  * [n_paths][n_calls][4], block (call c, path path0+i).  mc_normals_fill:
  * out [n_paths][n_per_path] of normals 0.. of each path, FP64 when

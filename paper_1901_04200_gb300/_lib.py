@@ -74,6 +74,8 @@ SIGNATURES = [
     ("mc_forward_static", ctypes.c_int, [_P(mc_model), _P(mc_instruments), _V, _U64, _U64, _U64, _V, _V]),
     ("mc_price_jacobian_scratch_size", ctypes.c_int, [_V, _I32, _U64, _P(_SZ)]),
     ("mc_price_jacobian", ctypes.c_int, [_V, _V, _V, _I32, _U64, _U64, _V, _V, _V, _SZ, _V]),
+    ("mc_tc_gemm_bf16", ctypes.c_int, [_V, ctypes.c_int64, _V, ctypes.c_int64, _I32, _I32, _I32, _I32, _V,
+                                       ctypes.c_int64, _V, _V]),
 ]
 KERNEL_NAMES = ["forward_sweep", "finalize_y", "seed", "reverse_sweep", "finalize_grad"]
 
@@ -250,6 +252,17 @@ class Context:
 
     def sync(self, stream=None):
         _check(load().mc_sync(self.handle, _stream(stream)), self.handle)
+
+
+def tc_gemm_bf16(A: torch.Tensor, B: torch.Tensor, k_slice: int = 0, err: torch.Tensor = None):
+    """FP32 [K/k_slice, M, N] = A [M,K] @ B [N,K]^T per K slice on the tensor cores (mc_tc_gemm_bf16)."""
+    M, K = A.shape
+    N = B.shape[0]
+    ks = k_slice or K
+    D = torch.empty((K // ks, M, N), dtype=torch.float32, device=A.device)
+    _check(load().mc_tc_gemm_bf16(_ptr(A), A.stride(0), _ptr(B), B.stride(0), M, N, K, ks, _ptr(D), N,
+                                  _ptr(err) if err is not None else None, _stream()), what="mc_tc_gemm_bf16")
+    return D
 
 
 def philox_fill(seed: int, path0: int, n_paths: int, n_calls: int, device="cuda"):

@@ -1,0 +1,46 @@
+// tc_gemm_test.cu -- the plain tensor-core GEMM (FP32 result stored
+// row-major, one slice per K split) behind the mc_tc_gemm_bf16 entry point.
+#include "mcaad.h"
+#include "tc_gemm.cuh"
+
+namespace mcaad {
+namespace tc {
+
+struct StoreEpi {
+    float *D;
+    long long ldd;
+    long long slice_stride;  // elements between K-slice outputs
+    __device__ __forceinline__ void apply(long long row, int c0, const float (&v)[32], int n, int ks) const {
+        float *o = D + ks * slice_stride + row * ldd + c0;
+#pragma unroll
+        for (int i = 0; i < 32; ++i)
+            if (i < n) o[i] = v[i];
+    }
+};
+
+__global__ void __launch_bounds__(kThreads) gemm_store_kernel(const GemmShape g, const StoreEpi e) {
+    gemm_body(g, e);
+}
+
+}  // namespace tc
+}  // namespace mcaad
+
+using namespace mcaad;
+
+extern "C" mc_status mc_tc_gemm_bf16(const void *A, int64_t lda, const void *B, int64_t ldb, int32_t M, int32_t N,
+                                     int32_t K, int32_t k_slice, float *D, int64_t ldd, int32_t *err,
+                                     void *stream) {
+    if (!A || !B || !D || M <= 0 || N <= 0 || K <= 0) return MC_ERR_INVALID_ARG;
+    if (M % tc::kBM || N % 16 || N > 256 || K % tc::kBK || k_slice <= 0 || k_slice % tc::kBK || K % k_slice)
+        return MC_ERR_INVALID_ARG;
+    if (lda < K || ldb < K || lda % 8 || ldb % 8 || ldd < N) return MC_ERR_INVALID_ARG;
+    if (((uintptr_t)A & 15u) || ((uintptr_t)B & 15u)) return MC_ERR_INVALID_ARG;
+    tc::GemmShape g{(const __nv_bfloat16 *)A, lda, (const __nv_bfloat16 *)B, ldb, M, N, K, k_slice, err};
+    tc::StoreEpi e{D, ldd, (long long)M * ldd};
+    const int kb = (k_slice / tc::kBK) < tc::kMaxKB ? (k_slice / tc::kBK) : tc::kMaxKB;
+    const size_t smem = tc::smem_bytes(N, kb);
+    cudaError_t st = cudaFuncSetAttribute(tc::gemm_store_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (st != cudaSuccess) return MC_ERR_CUDA;
+    tc::gemm_store_kernel<<<dim3(M / tc::kBM, K / k_slice), tc::kThreads, smem, (cudaStream_t)stream>>>(g, e);
+    return cudaGetLastError() == cudaSuccess ? MC_OK : MC_ERR_CUDA;
+}
