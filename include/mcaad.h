@@ -190,6 +190,41 @@ mc_status mc_price_jacobian(mc_ctx *ctx, const double *thetas, const double *str
 mc_status mc_tc_gemm_bf16(const void *A, int64_t lda, const void *B, int64_t ldb, int32_t M, int32_t N, int32_t K,
                           int32_t k_slice, float *D, int64_t ldd, int32_t *err, void *stream);
 
+/* ---- Pricing surrogate (learned part; no counterpart in the paper, which
+ * prices every calibration step by Monte Carlo).  MLP 7 -> 256 -> 256 -> 256
+ * -> 256 -> 1, SiLU, input (Heston theta[5], K, T) normalised by the caller,
+ * BF16 operands and FP32 accumulation on tcgen05 tensor cores, FP32 master
+ * parameters in a flat caller-owned buffer of mlp_n_params() floats laid out
+ * W1 [256][7], b1, W2 [256][256], b2, W3, b3, W4, b4, w5 [256], b5.
+ * A context owns the activation workspace for `batch` rows (a multiple of 128)
+ * and the BF16 copies of the weights; mlp_set_weights (or mlp_adam_step)
+ * refreshes those copies from the FP32 parameters.  Stream-ordered; the
+ * status conventions are those of the mc_ entry points. */
+typedef struct mlp_ctx mlp_ctx;
+int64_t mlp_n_params(void);
+mc_status mlp_workspace_size(int32_t batch, size_t *bytes_out);
+/* workspace: caller-owned device buffer (256-byte aligned, >= mlp_workspace_size)
+ * or NULL to let the context allocate its own.  Synchronous (zeroes it). */
+mc_status mlp_create(int device, int32_t batch, void *workspace, size_t workspace_bytes, mlp_ctx **out);
+void mlp_destroy(mlp_ctx *ctx);
+mc_status mlp_set_weights(mlp_ctx *ctx, const float *params, void *stream);
+/* out[r] = net(X[r]) for r < n_rows <= batch; X FP32 [n_rows][7]; dout_dx
+ * (nullable) FP32 [n_rows][7] = d net/d x (the input gradient). */
+mc_status mlp_forward(mlp_ctx *ctx, const float *params, const float *X, int32_t n_rows, float *out,
+                      float *dout_dx, void *stream);
+/* Differential loss over one full batch, L = mean (net - y)^2 + alpha mean
+ * sum_{j<5} (d net/d x_j - dy_j)^2, and its gradient with respect to every
+ * parameter (double backward through the input gradient).  X [batch][7],
+ * y [batch], dy [batch][5]; loss_out (nullable) FP32 [1]; grads FP32 [n_params]. */
+mc_status mlp_loss_grad(mlp_ctx *ctx, const float *params, const float *X, const float *y, const float *dy,
+                        float alpha, float *loss_out, float *grads, void *stream);
+/* Adam (Kingma & Ba) step t >= 1 on the FP32 parameters and moments, then the
+ * BF16 weight copies are refreshed. */
+mc_status mlp_adam_step(mlp_ctx *ctx, float *params, const float *grads, float *m, float *v, int32_t t, float lr,
+                        float beta1, float beta2, float eps, void *stream);
+/* Host copy of the tensor-core wait-expiry flag (0 = every wait completed). Synchronous. */
+mc_status mlp_error_flag(mlp_ctx *ctx, int32_t *flag_host);
+
 /* Test hooks for the generator.  mc_philox_fill: out uint32
  * [n_paths][n_calls][4], block (call c, path path0+i).  mc_normals_fill:
  * out [n_paths][n_per_path] of normals 0.. of each path, FP64 when

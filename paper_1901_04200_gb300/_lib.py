@@ -76,6 +76,16 @@ SIGNATURES = [
     ("mc_price_jacobian", ctypes.c_int, [_V, _V, _V, _I32, _U64, _U64, _V, _V, _V, _SZ, _V]),
     ("mc_tc_gemm_bf16", ctypes.c_int, [_V, ctypes.c_int64, _V, ctypes.c_int64, _I32, _I32, _I32, _I32, _V,
                                        ctypes.c_int64, _V, _V]),
+    ("mlp_n_params", ctypes.c_int64, []),
+    ("mlp_workspace_size", ctypes.c_int, [_I32, _P(_SZ)]),
+    ("mlp_create", ctypes.c_int, [ctypes.c_int, _I32, _V, _SZ, _P(_V)]),
+    ("mlp_destroy", None, [_V]),
+    ("mlp_set_weights", ctypes.c_int, [_V, _V, _V]),
+    ("mlp_forward", ctypes.c_int, [_V, _V, _V, _I32, _V, _V, _V]),
+    ("mlp_loss_grad", ctypes.c_int, [_V, _V, _V, _V, _V, ctypes.c_float, _V, _V, _V]),
+    ("mlp_adam_step", ctypes.c_int, [_V, _V, _V, _V, _V, _I32, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                     ctypes.c_float, _V]),
+    ("mlp_error_flag", ctypes.c_int, [_V, _P(_I32)]),
 ]
 KERNEL_NAMES = ["forward_sweep", "finalize_y", "seed", "reverse_sweep", "finalize_grad"]
 
@@ -280,3 +290,54 @@ def normals_fill(seed: int, path0: int, n_paths: int, n_per_path: int, precision
                                   MC_FP64 if precision == "fp64" else MC_FP32, _ptr(out), _stream()),
            what="mc_normals_fill")
     return out
+
+
+class Mlp:
+    """An mlp_ctx: the surrogate's activation workspace for `batch` rows (torch-allocated)."""
+
+    def __init__(self, batch: int, device=None):
+        lib = load()
+        self.device = torch.device(device if device is not None else "cuda")
+        if self.device.index is None:
+            self.device = torch.device("cuda", torch.cuda.current_device())
+        nbytes = ctypes.c_size_t(0)
+        _check(lib.mlp_workspace_size(int(batch), ctypes.byref(nbytes)), what="mlp_workspace_size")
+        self.workspace = torch.empty(int(nbytes.value) + 256, dtype=torch.uint8, device=self.device)
+        aligned = (self.workspace.data_ptr() + 255) // 256 * 256
+        h = ctypes.c_void_p()
+        _check(lib.mlp_create(self.device.index, int(batch), ctypes.c_void_p(aligned), int(nbytes.value),
+                              ctypes.byref(h)), what="mlp_create")
+        self.handle = h
+        self.batch = int(batch)
+        self.n_params = int(lib.mlp_n_params())
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h and _lib is not None:
+            _lib.mlp_destroy(h)
+            self.handle = None
+
+    def set_weights(self, params, stream=None):
+        _check(load().mlp_set_weights(self.handle, _ptr(params), _stream(stream)), what="mlp_set_weights")
+
+    def forward(self, params, X, with_grad=False, stream=None):
+        n = X.shape[0]
+        out = torch.empty(n, dtype=torch.float32, device=self.device)
+        dx = torch.empty((n, 7), dtype=torch.float32, device=self.device) if with_grad else None
+        _check(load().mlp_forward(self.handle, _ptr(params), _ptr(X), n, _ptr(out), _ptr(dx) if dx is not None else None,
+                                  _stream(stream)), what="mlp_forward")
+        return (out, dx) if with_grad else out
+
+    def loss_grad(self, params, X, y, dy, alpha, grads, loss=None, stream=None):
+        _check(load().mlp_loss_grad(self.handle, _ptr(params), _ptr(X), _ptr(y), _ptr(dy), float(alpha),
+                                    _ptr(loss) if loss is not None else None, _ptr(grads), _stream(stream)),
+               what="mlp_loss_grad")
+
+    def adam_step(self, params, grads, m, v, t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+        _check(load().mlp_adam_step(self.handle, _ptr(params), _ptr(grads), _ptr(m), _ptr(v), int(t), float(lr),
+                                    float(beta1), float(beta2), float(eps), _stream(stream)), what="mlp_adam_step")
+
+    def error_flag(self):
+        f = ctypes.c_int32(0)
+        _check(load().mlp_error_flag(self.handle, ctypes.byref(f)), what="mlp_error_flag")
+        return f.value

@@ -1,0 +1,621 @@
+// mlp.cu -- the pricing surrogate on the tensor cores: MLP 7 -> 256 x 4 -> 1
+// with SiLU, BF16 operands, FP32 accumulation (tcgen05 GEMM of tc_gemm.cuh),
+// trained with the differential loss
+//     L = mean (out - y)^2 + alpha * mean sum_{j<5} (d out/d x_j - dy_j)^2
+// whose labels come from the Monte Carlo method (E y and its pathwise
+// Jacobian).  Every matrix product is one tensor-core GEMM whose epilogue
+// applies the elementwise work of that stage (bias, SiLU and its first and
+// second derivatives, the products of the double-backward chain) and stores
+// the operands of the following products, row-major and transposed:
+//
+//   F1..F4   z_l = h_{l-1} W_l^T + b_l, h_l = silu(z_l); F4 also forms
+//            out = h_4 . w5 + b5, out_bar = 2 (out - y)/B and p_4 = w5 silu'(z_4)
+//   T4..T1   g_{l-1} = p_l W_l, p_{l-1} = g_{l-1} silu'(z_{l-1}); T1 forms
+//            g0_bar = 2 alpha (g_0 - dy)/B on the theta columns
+//   R1..R4   p_bar_l = g_bar_{l-1} W_l^T, g_bar_l = p_bar_l silu'(z_l),
+//            z_bar_l(tangent) = p_bar_l g_l silu''(z_l); R4 also forms
+//            z_bar_4 = out_bar w5 silu'(z_4) + z_bar_4(tangent)
+//   D4..D2   h_bar_{l-1} = z_bar_l W_l, z_bar_{l-1} = h_bar_{l-1} silu'(z_{l-1}) + tangent part
+//   G1..G4   dW_l = [p_l ; z_bar_l]^T [g_bar_{l-1} ; h_{l-1}]  (K = 2B, split over CTAs)
+//
+// then fixed-order reductions (split-K slices, bias and w5 column sums, the
+// loss) and Adam on FP32 master parameters, which also refreshes the BF16
+// weight copies (W_l and W_l^T) the GEMMs read.
+#include <cuda_bf16.h>
+
+#include <cstdio>
+#include <new>
+
+#include "mcaad.h"
+#include "tc_gemm.cuh"
+
+namespace mcaad {
+namespace mlp {
+
+using bf16 = __nv_bfloat16;
+constexpr int H = 256, DIN = 7, NTH = 5, KX = 64, NX = 16;
+constexpr int kSplit = 16;  // K slices of the weight-gradient GEMMs
+
+// flat FP32 parameter layout
+constexpr long long oW1 = 0, ob1 = oW1 + H * DIN, oW2 = ob1 + H, ob2 = oW2 + H * H, oW3 = ob2 + H,
+                    ob3 = oW3 + H * H, oW4 = ob3 + H, ob4 = oW4 + H * H, ow5 = ob4 + H, ob5 = ow5 + H,
+                    kParams = ob5 + 1;
+__host__ __device__ constexpr long long oW(int l) { return l == 1 ? oW1 : (l == 2 ? oW2 : (l == 3 ? oW3 : oW4)); }
+__host__ __device__ constexpr long long ob(int l) { return l == 1 ? ob1 : (l == 2 ? ob2 : (l == 3 ? ob3 : ob4)); }
+
+__device__ __forceinline__ float sigm(float z) { return 1.0f / (1.0f + __expf(-z)); }
+__device__ __forceinline__ float silu(float z) { return z * sigm(z); }
+__device__ __forceinline__ float dsilu(float z) {
+    const float s = sigm(z);
+    return s * (1.0f + z * (1.0f - s));
+}
+__device__ __forceinline__ float d2silu(float z) {
+    const float s = sigm(z);
+    return s * (1.0f - s) * (2.0f + z * (1.0f - 2.0f * s));
+}
+
+struct Bufs {
+    int B;
+    bf16 *x0;            // [B][KX]
+    float *z[5];         // [B][H], l = 1..4
+    bf16 *h[5];          // [B][H], l = 1..4
+    float *out, *obar, *loss_rows;  // [B]
+    bf16 *p[5];          // [B][H], l = 1..4
+    float *g[5];         // [B][H], l = 1..3 ; g[0]: [B][NX]
+    bf16 *gb0;           // [B][KX]
+    bf16 *gb[5];         // [B][H], l = 1..3
+    float *gb4f;         // [B][H]
+    float *zbt[5];       // [B][H]
+    float *zb[5];        // [B][H]
+    bf16 *zbb[5];        // [B][H], l = 2..4
+    bf16 *Aop[5];        // [H][2B]
+    bf16 *Bop[5];        // l = 1: [NX][2B], else [H][2B]
+    float *part;         // [kSplit][H][H]
+    bf16 *Wb[5], *Wt[5];  // W1b [H][KX], W1t [NX][H], Wlb/Wlt [H][H]
+    float *lsum;         // [1] loss scratch
+    int *err;            // [1] tensor-core wait expiry flag
+};
+
+// ------------------------------------------------------------ epilogues ----
+
+// transposed BF16 store: T[col][off + row] for the 32 (or n) columns of this row
+__device__ __forceinline__ void store_t(bf16 *T, long long ldt, long long off, long long row, int c0, const float *v,
+                                        int n) {
+    for (int i = 0; i < n; ++i) T[(long long)(c0 + i) * ldt + off + row] = __float2bfloat16_rn(v[i]);
+}
+__device__ __forceinline__ void store_row_bf16(bf16 *D, long long ld, long long row, int c0, const float *v, int n) {
+    for (int i = 0; i < n; i += 2) {
+        __nv_bfloat162 t;
+        t.x = __float2bfloat16_rn(v[i]);
+        t.y = __float2bfloat16_rn(v[i + 1]);
+        *(__nv_bfloat162 *)(D + row * ld + c0 + i) = t;
+    }
+}
+__device__ __forceinline__ void store_row_f32(float *D, long long ld, long long row, int c0, const float *v, int n) {
+    for (int i = 0; i < n; i += 4) *(float4 *)(D + row * ld + c0 + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+}
+
+// F1..F3: z = acc + b; h = silu(z)
+struct EpiFwd {
+    const float *bias;
+    float *z;
+    bf16 *h;
+    bf16 *hT;  // Bop_{l+1}: [H][2B], column B + row
+    long long B2, Boff;
+    __device__ void apply(long long row, int c0, const float (&acc)[32], int n, int, float &) const {
+        float zz[32], hh[32];
+        for (int i = 0; i < 32; ++i) {
+            zz[i] = acc[i] + bias[c0 + i];
+            hh[i] = silu(zz[i]);
+        }
+        store_row_f32(z, H, row, c0, zz, n);
+        store_row_bf16(h, H, row, c0, hh, n);
+        store_t(hT, B2, Boff, row, c0, hh, n);
+    }
+};
+
+// F4: as F1..F3, plus out = h . w5 + b5 (accumulated over the column pieces of
+// this thread's row), out_bar, the value loss and p_4 = w5 silu'(z_4).
+struct EpiFwdLast {
+    const float *bias, *w5, *b5, *y;
+    float *z, *out, *obar, *loss_rows;
+    bf16 *h, *p4, *p4T;  // p4T = Aop_4, column row
+    long long B2;
+    float inv_b;
+    __device__ void apply(long long row, int c0, const float (&acc)[32], int n, int, float &acc_out) const {
+        float zz[32], hh[32], pp[32];
+        for (int i = 0; i < 32; ++i) {
+            zz[i] = acc[i] + bias[c0 + i];
+            hh[i] = silu(zz[i]);
+            pp[i] = w5[c0 + i] * dsilu(zz[i]);
+            acc_out = fmaf(hh[i], w5[c0 + i], acc_out);
+        }
+        store_row_f32(z, H, row, c0, zz, n);
+        store_row_bf16(h, H, row, c0, hh, n);
+        store_row_bf16(p4, H, row, c0, pp, n);
+        store_t(p4T, B2, 0, row, c0, pp, n);
+        if (c0 + n >= H) {
+            const float o = acc_out + b5[0];
+            out[row] = o;
+            if (y) {
+                const float d = o - y[row];
+                obar[row] = 2.0f * d * inv_b;
+                loss_rows[row] = d * d * inv_b;
+            }
+        }
+    }
+};
+
+// T4..T2: g = acc; p = g silu'(z_{l-1})
+struct EpiTan {
+    const float *zprev;
+    float *g;
+    bf16 *p, *pT;  // pT = Aop_{l-1}, column row
+    long long B2;
+    __device__ void apply(long long row, int c0, const float (&acc)[32], int n, int, float &) const {
+        float pp[32];
+        for (int i = 0; i < 32; ++i) pp[i] = acc[i] * dsilu(zprev[row * H + c0 + i]);
+        store_row_f32(g, H, row, c0, acc, n);
+        store_row_bf16(p, H, row, c0, pp, n);
+        store_t(pT, B2, 0, row, c0, pp, n);
+    }
+};
+
+// T1: g_0 = acc (16 columns, 7 valid); g0_bar on the theta columns; derivative loss
+struct EpiTanIn {
+    float *g0;
+    const float *dy;  // [B][NTH] or null (inference)
+    bf16 *gb0, *gb0T;  // gb0 [B][KX]; gb0T = Bop_1 [NX][2B], column row
+    float *loss_rows;
+    long long B2;
+    float two_alpha_inv_b, alpha_inv_b;
+    __device__ void apply(long long row, int c0, const float (&acc)[32], int n, int, float &) const {
+        float gbar[32];
+        float l = 0.0f;
+        for (int i = 0; i < 32; ++i) gbar[i] = 0.0f;
+        for (int i = 0; i < NX; ++i) g0[row * NX + i] = acc[i];
+        if (dy) {
+            for (int j = 0; j < NTH; ++j) {
+                const float d = acc[j] - dy[row * NTH + j];
+                gbar[j] = two_alpha_inv_b * d;
+                l = fmaf(d * d, alpha_inv_b, l);
+            }
+            loss_rows[row] += l;
+            store_row_bf16(gb0, KX, row, 0, gbar, NX);
+            store_t(gb0T, B2, 0, row, 0, gbar, NX);
+        }
+        (void)c0;
+        (void)n;
+    }
+};
+
+// R1..R3: g_bar = acc silu'(z_l); z_bar(tangent) = acc g_l silu''(z_l)
+struct EpiTbar {
+    const float *zl, *gl;
+    bf16 *gb, *gbT;  // gbT = Bop_{l+1}, column row
+    float *zbt;
+    long long B2;
+    __device__ void apply(long long row, int c0, const float (&acc)[32], int n, int, float &) const {
+        float a[32], t[32];
+        for (int i = 0; i < 32; ++i) {
+            const float zz = zl[row * H + c0 + i];
+            a[i] = acc[i] * dsilu(zz);
+            t[i] = acc[i] * gl[row * H + c0 + i] * d2silu(zz);
+        }
+        store_row_bf16(gb, H, row, c0, a, n);
+        store_t(gbT, B2, 0, row, c0, a, n);
+        store_row_f32(zbt, H, row, c0, t, n);
+    }
+};
+
+// R4: g_bar_4 (FP32, for dw5), and the full z_bar_4 = out_bar w5 silu'(z_4) + tangent part
+struct EpiTbarLast {
+    const float *z4, *w5, *obar;
+    float *gb4f, *zb4;
+    bf16 *zbb4, *zb4T;  // zb4T = Aop_4, column B + row
+    long long B2, Boff;
+    __device__ void apply(long long row, int c0, const float (&acc)[32], int n, int, float &) const {
+        float a[32], zb[32];
+        const float ob = obar[row];
+        for (int i = 0; i < 32; ++i) {
+            const float zz = z4[row * H + c0 + i];
+            const float ds = dsilu(zz);
+            a[i] = acc[i] * ds;
+            const float t = acc[i] * w5[c0 + i] * d2silu(zz);
+            zb[i] = fmaf(ob * w5[c0 + i], ds, t);
+        }
+        store_row_f32(gb4f, H, row, c0, a, n);
+        store_row_f32(zb4, H, row, c0, zb, n);
+        store_row_bf16(zbb4, H, row, c0, zb, n);
+        store_t(zb4T, B2, Boff, row, c0, zb, n);
+    }
+};
+
+// D4..D2: z_bar_{l-1} = acc silu'(z_{l-1}) + z_bar_{l-1}(tangent)
+struct EpiDbar {
+    const float *zprev, *zbt;
+    float *zb;
+    bf16 *zbb, *zbT;  // zbb may be null (layer 1); zbT = Aop_{l-1}, column B + row
+    long long B2, Boff;
+    __device__ void apply(long long row, int c0, const float (&acc)[32], int n, int, float &) const {
+        float v[32];
+        for (int i = 0; i < 32; ++i) v[i] = fmaf(acc[i], dsilu(zprev[row * H + c0 + i]), zbt[row * H + c0 + i]);
+        store_row_f32(zb, H, row, c0, v, n);
+        if (zbb) store_row_bf16(zbb, H, row, c0, v, n);
+        store_t(zbT, B2, Boff, row, c0, v, n);
+    }
+};
+
+// G1..G4: FP32 partial of K slice s
+struct EpiPartial {
+    float *part;
+    int N;
+    long long M;
+    __device__ void apply(long long row, int c0, const float (&acc)[32], int n, int ks, float &) const {
+        float *o = part + (long long)ks * M * N + row * N + c0;
+        for (int i = 0; i < 32; ++i)
+            if (i < n) o[i] = acc[i];
+    }
+};
+
+template <class Epi>
+__global__ void __launch_bounds__(tc::kThreads) gemm_kernel(const tc::GemmShape g, const Epi e) {
+    tc::gemm_body(g, e);
+}
+
+template <class Epi>
+cudaError_t gemm(const bf16 *A, long long lda, const bf16 *Bm, long long ldb, int M, int N, int K, int k_slice,
+                 const Epi &e, int *err, cudaStream_t st) {
+    tc::GemmShape g{A, lda, Bm, ldb, M, N, K, k_slice, err};
+    const int kb = (k_slice / tc::kBK) < tc::kMaxKB ? (k_slice / tc::kBK) : tc::kMaxKB;
+    const size_t smem = tc::smem_bytes(N, kb);
+    static bool attr_set = false;  // the largest tile any call uses: N = 256, four k-blocks
+    if (!attr_set) {
+        cudaError_t r = cudaFuncSetAttribute(gemm_kernel<Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)tc::smem_bytes(256, tc::kMaxKB));
+        if (r != cudaSuccess) return r;
+        attr_set = true;
+    }
+    gemm_kernel<Epi><<<dim3(M / tc::kBM, K / k_slice), tc::kThreads, smem, st>>>(g, e);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ small kernels --
+
+// X [n_rows][7] FP32 -> x0 [B][KX] BF16 (zero padding) and X^T into Bop_1 columns B + row.
+__global__ void prep_input_kernel(const float *__restrict__ X, int n_rows, int B, bf16 *x0, bf16 *xT, long long B2) {
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < B * DIN; q += gridDim.x * blockDim.x) {
+        const int r = q / DIN, j = q - r * DIN;
+        const float v = r < n_rows ? X[(long long)r * DIN + j] : 0.0f;
+        const bf16 b = __float2bfloat16_rn(v);
+        x0[(long long)r * KX + j] = b;
+        if (xT) xT[(long long)j * B2 + B + r] = b;
+    }
+}
+
+// FP32 parameters -> BF16 W_l (row-major, layer 1 padded to KX columns) and W_l^T.
+__global__ void weights_to_bf16_kernel(const float *__restrict__ prm, bf16 *W1b, bf16 *W1t, bf16 *W2b, bf16 *W2t,
+                                       bf16 *W3b, bf16 *W3t, bf16 *W4b, bf16 *W4t) {
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < 3 * H * H + H * DIN; q += gridDim.x * blockDim.x) {
+        if (q < H * DIN) {
+            const int n = q / DIN, k = q - n * DIN;
+            const bf16 b = __float2bfloat16_rn(prm[oW1 + q]);
+            W1b[n * KX + k] = b;
+            W1t[k * H + n] = b;
+        } else {
+            const int r = q - H * DIN;
+            const int l = 2 + r / (H * H);
+            const int e = r % (H * H), n = e / H, k = e - n * H;
+            const bf16 b = __float2bfloat16_rn(prm[oW(l) + e]);
+            bf16 *Wb = l == 2 ? W2b : (l == 3 ? W3b : W4b);
+            bf16 *Wt = l == 2 ? W2t : (l == 3 ? W3t : W4t);
+            Wb[n * H + k] = b;
+            Wt[k * H + n] = b;
+        }
+    }
+}
+
+// dW_l[i][k] = sum over K slices in order (layer 1: k < 7 of the 16 computed columns).
+__global__ void reduce_split_kernel(const float *__restrict__ part, int N, int ncopy, float *dW) {
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < H * ncopy; q += gridDim.x * blockDim.x) {
+        const int i = q / ncopy, k = q - i * ncopy;
+        float s = 0.0f;
+        for (int sl = 0; sl < kSplit; ++sl) s += part[((long long)sl * H + i) * N + k];
+        dW[q] = s;
+    }
+}
+
+// Column sums in a fixed order: db_l = sum_rows z_bar_l, dw5 = sum_rows (g_bar_4 + h_4 out_bar),
+// db5 = sum out_bar, loss = sum loss_rows.  One block per output.
+__global__ void __launch_bounds__(256) colsum_kernel(const Bufs b, float *grads, float *loss_out) {
+    __shared__ float red[256];
+    const int col = blockIdx.x;  // 0..4H-1: biases; 4H..5H-1: w5; 5H: b5; 5H+1: loss
+    const int B = b.B;
+    float s = 0.0f;
+    if (col < 4 * H) {
+        const int l = 1 + col / H, c = col % H;
+        for (int r = threadIdx.x; r < B; r += blockDim.x) s += b.zb[l][(long long)r * H + c];
+    } else if (col < 5 * H) {
+        const int c = col - 4 * H;
+        for (int r = threadIdx.x; r < B; r += blockDim.x)
+            s += b.gb4f[(long long)r * H + c] + __bfloat162float(b.h[4][(long long)r * H + c]) * b.obar[r];
+    } else if (col == 5 * H) {
+        for (int r = threadIdx.x; r < B; r += blockDim.x) s += b.obar[r];
+    } else {
+        for (int r = threadIdx.x; r < B; r += blockDim.x) s += b.loss_rows[r];
+    }
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        if (col < 4 * H) grads[ob(1 + col / H) + col % H] = red[0];
+        else if (col < 5 * H) grads[ow5 + col - 4 * H] = red[0];
+        else if (col == 5 * H) grads[ob5] = red[0];
+        else if (loss_out) loss_out[0] = red[0];
+    }
+}
+
+// Adam (Kingma & Ba) on the FP32 master parameters; t counts from 1.
+__global__ void adam_kernel(float *prm, const float *__restrict__ g, float *m, float *v, long long n, float lr,
+                            float b1, float b2, float eps, float c1, float c2) {
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
+        const float gg = g[q];
+        const float mm = fmaf(b1, m[q], (1.0f - b1) * gg);
+        const float vv = fmaf(b2, v[q], (1.0f - b2) * gg * gg);
+        m[q] = mm;
+        v[q] = vv;
+        prm[q] -= lr * (mm * c1) / (sqrtf(vv * c2) + eps);
+    }
+}
+
+int grid_for(long long work) {
+    long long g = (work + 255) / 256;
+    return (int)(g < 1 ? 1 : (g > 4096 ? 4096 : g));
+}
+
+}  // namespace mlp
+}  // namespace mcaad
+
+using namespace mcaad;
+using namespace mcaad::mlp;
+
+struct mlp_ctx {
+    int device = 0;
+    int B = 0;
+    Bufs b{};
+    unsigned char *ws = nullptr;
+    bool owns = false;
+};
+
+namespace {
+
+struct Carve {
+    unsigned char *base;
+    size_t off = 0;
+    template <typename T>
+    T *take(size_t n) {
+        T *p = base ? (T *)(base + off) : nullptr;
+        off = (off + n * sizeof(T) + 255) / 256 * 256;
+        return p;
+    }
+};
+
+size_t layout(unsigned char *base, int B, Bufs *out) {
+    Carve c{base};
+    Bufs b{};
+    b.B = B;
+    const size_t BH = (size_t)B * H, B2 = 2 * (size_t)B;
+    b.x0 = c.take<bf16>((size_t)B * KX);
+    for (int l = 1; l <= 4; ++l) b.z[l] = c.take<float>(BH);
+    for (int l = 1; l <= 4; ++l) b.h[l] = c.take<bf16>(BH);
+    b.out = c.take<float>(B);
+    b.obar = c.take<float>(B);
+    b.loss_rows = c.take<float>(B);
+    for (int l = 1; l <= 4; ++l) b.p[l] = c.take<bf16>(BH);
+    b.g[0] = c.take<float>((size_t)B * NX);
+    for (int l = 1; l <= 3; ++l) b.g[l] = c.take<float>(BH);
+    b.gb0 = c.take<bf16>((size_t)B * KX);
+    for (int l = 1; l <= 3; ++l) b.gb[l] = c.take<bf16>(BH);
+    b.gb4f = c.take<float>(BH);
+    for (int l = 1; l <= 4; ++l) b.zbt[l] = c.take<float>(BH);
+    for (int l = 1; l <= 4; ++l) b.zb[l] = c.take<float>(BH);
+    for (int l = 2; l <= 4; ++l) b.zbb[l] = c.take<bf16>(BH);
+    for (int l = 1; l <= 4; ++l) b.Aop[l] = c.take<bf16>(H * B2);
+    b.Bop[1] = c.take<bf16>(NX * B2);
+    for (int l = 2; l <= 4; ++l) b.Bop[l] = c.take<bf16>(H * B2);
+    b.part = c.take<float>((size_t)kSplit * H * H);
+    b.Wb[1] = c.take<bf16>((size_t)H * KX);
+    b.Wt[1] = c.take<bf16>((size_t)NX * H);
+    for (int l = 2; l <= 4; ++l) {
+        b.Wb[l] = c.take<bf16>((size_t)H * H);
+        b.Wt[l] = c.take<bf16>((size_t)H * H);
+    }
+    b.lsum = c.take<float>(1);
+    b.err = c.take<int>(1);
+    if (out) *out = b;
+    return c.off;
+}
+
+mc_status cuda_st(cudaError_t e, const char *what) {
+    if (e == cudaSuccess) return MC_OK;
+    fprintf(stderr, "mlp: %s: %s\n", what, cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? MC_ERR_OOM : MC_ERR_CUDA;
+}
+
+// F1..F4 (+ T4..T1 when grad) for the batch already staged in x0.
+cudaError_t run_forward(mlp_ctx *c, const float *prm, const float *y, const float *dy, float alpha, bool tangent,
+                        cudaStream_t st) {
+    Bufs &b = c->b;
+    const int B = b.B;
+    const long long B2 = 2LL * B;
+    const float inv_b = 1.0f / (float)B;
+    cudaError_t e;
+    for (int l = 1; l <= 3; ++l) {
+        EpiFwd ep{prm + ob(l), b.z[l], b.h[l], b.Bop[l + 1], B2, B};
+        const bf16 *A = l == 1 ? b.x0 : b.h[l - 1];
+        const int K = l == 1 ? KX : H;
+        e = gemm(A, K, b.Wb[l], K, B, H, K, K, ep, b.err, st);
+        if (e != cudaSuccess) return e;
+    }
+    {
+        EpiFwdLast ep{prm + ob4, prm + ow5, prm + ob5, y, b.z[4], b.out, b.obar, b.loss_rows, b.h[4], b.p[4],
+                      b.Aop[4], B2, inv_b};
+        e = gemm(b.h[3], H, b.Wb[4], H, B, H, H, H, ep, b.err, st);
+        if (e != cudaSuccess) return e;
+    }
+    if (!tangent) return cudaSuccess;
+    for (int l = 4; l >= 2; --l) {
+        EpiTan ep{b.z[l - 1], b.g[l - 1], b.p[l - 1], b.Aop[l - 1], B2};
+        e = gemm(b.p[l], H, b.Wt[l], H, B, H, H, H, ep, b.err, st);
+        if (e != cudaSuccess) return e;
+    }
+    EpiTanIn ep{b.g[0], dy, b.gb0, b.Bop[1], b.loss_rows, B2, 2.0f * alpha * inv_b, alpha * inv_b};
+    return gemm(b.p[1], H, b.Wt[1], H, B, NX, H, H, ep, b.err, st);
+}
+
+}  // namespace
+
+extern "C" {
+
+int64_t mlp_n_params(void) { return kParams; }
+
+mc_status mlp_workspace_size(int32_t batch, size_t *bytes_out) {
+    if (!bytes_out || batch < 128 || batch % 128) return MC_ERR_INVALID_ARG;
+    *bytes_out = layout(nullptr, batch, nullptr);
+    return MC_OK;
+}
+
+mc_status mlp_create(int device, int32_t batch, void *workspace, size_t workspace_bytes, mlp_ctx **out) {
+    if (!out || batch < 128 || batch % 128) return MC_ERR_INVALID_ARG;
+    *out = nullptr;
+    const size_t need = layout(nullptr, batch, nullptr);
+    mc_status s = cuda_st(cudaSetDevice(device), "cudaSetDevice");
+    if (s != MC_OK) return s;
+    mlp_ctx *c = new (std::nothrow) mlp_ctx();
+    if (!c) return MC_ERR_OOM;
+    c->device = device;
+    c->B = batch;
+    if (workspace) {
+        if (workspace_bytes < need || ((uintptr_t)workspace & 255u)) {
+            delete c;
+            return MC_ERR_INVALID_ARG;
+        }
+        c->ws = (unsigned char *)workspace;
+    } else {
+        s = cuda_st(cudaMalloc((void **)&c->ws, need), "cudaMalloc");
+        if (s != MC_OK) {
+            delete c;
+            return s;
+        }
+        c->owns = true;
+    }
+    layout(c->ws, batch, &c->b);
+    // padding columns and rows that no kernel writes must read as zero
+    s = cuda_st(cudaMemset(c->ws, 0, need), "cudaMemset");
+    if (s != MC_OK) {
+        if (c->owns) cudaFree(c->ws);
+        delete c;
+        return s;
+    }
+    *out = c;
+    return MC_OK;
+}
+
+void mlp_destroy(mlp_ctx *c) {
+    if (!c) return;
+    if (c->owns && c->ws) {
+        cudaSetDevice(c->device);
+        cudaFree(c->ws);
+    }
+    delete c;
+}
+
+mc_status mlp_set_weights(mlp_ctx *c, const float *params, void *stream) {
+    if (!c || !params) return MC_ERR_INVALID_ARG;
+    Bufs &b = c->b;
+    weights_to_bf16_kernel<<<grid_for(3LL * H * H + H * DIN), 256, 0, (cudaStream_t)stream>>>(
+        params, b.Wb[1], b.Wt[1], b.Wb[2], b.Wt[2], b.Wb[3], b.Wt[3], b.Wb[4], b.Wt[4]);
+    return cuda_st(cudaGetLastError(), "weights_to_bf16");
+}
+
+mc_status mlp_forward(mlp_ctx *c, const float *params, const float *X, int32_t n_rows, float *out, float *dout_dx,
+                      void *stream) {
+    if (!c || !params || !X || !out || n_rows < 1 || n_rows > c->B) return MC_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    Bufs &b = c->b;
+    prep_input_kernel<<<grid_for((long long)c->B * DIN), 256, 0, st>>>(X, n_rows, c->B, b.x0, nullptr, 0);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = run_forward(c, params, nullptr, nullptr, 0.0f, dout_dx != nullptr, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, b.out, sizeof(float) * n_rows, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess && dout_dx)
+        e = cudaMemcpy2DAsync(dout_dx, sizeof(float) * DIN, b.g[0], sizeof(float) * NX, sizeof(float) * DIN, n_rows,
+                              cudaMemcpyDeviceToDevice, st);
+    return cuda_st(e, "mlp_forward");
+}
+
+mc_status mlp_loss_grad(mlp_ctx *c, const float *params, const float *X, const float *y, const float *dy, float alpha,
+                        float *loss_out, float *grads, void *stream) {
+    if (!c || !params || !X || !y || !dy || !grads) return MC_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    Bufs &b = c->b;
+    const int B = b.B;
+    const long long B2 = 2LL * B;
+    prep_input_kernel<<<grid_for((long long)B * DIN), 256, 0, st>>>(X, B, B, b.x0, b.Bop[1], B2);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = run_forward(c, params, y, dy, alpha, true, st);
+    // R1..R4: up the tangent chain
+    for (int l = 1; l <= 4 && e == cudaSuccess; ++l) {
+        const bf16 *A = l == 1 ? b.gb0 : b.gb[l - 1];
+        const int K = l == 1 ? KX : H;
+        if (l < 4) {
+            EpiTbar ep{b.z[l], b.g[l], b.gb[l], b.Bop[l + 1], b.zbt[l], B2};
+            e = gemm(A, K, b.Wb[l], K, B, H, K, K, ep, b.err, st);
+        } else {
+            EpiTbarLast ep{b.z[4], params + ow5, b.obar, b.gb4f, b.zb[4], b.zbb[4], b.Aop[4], B2, B};
+            e = gemm(A, K, b.Wb[4], K, B, H, K, K, ep, b.err, st);
+        }
+    }
+    // D4..D2: down the forward chain
+    for (int l = 4; l >= 2 && e == cudaSuccess; --l) {
+        EpiDbar ep{b.z[l - 1], b.zbt[l - 1], b.zb[l - 1], l - 1 >= 2 ? b.zbb[l - 1] : nullptr, b.Aop[l - 1], B2, B};
+        e = gemm(b.zbb[l], H, b.Wt[l], H, B, H, H, H, ep, b.err, st);
+    }
+    // G1..G4: weight gradients over the concatenated 2B rows, split along K
+    for (int l = 1; l <= 4 && e == cudaSuccess; ++l) {
+        const int N = l == 1 ? NX : H;
+        EpiPartial ep{b.part, N, H};
+        e = gemm(b.Aop[l], B2, b.Bop[l], B2, H, N, (int)B2, (int)(B2 / kSplit), ep, b.err, st);
+        if (e == cudaSuccess) {
+            const int ncopy = l == 1 ? DIN : H;
+            reduce_split_kernel<<<grid_for((long long)H * ncopy), 256, 0, st>>>(b.part, N, ncopy, grads + oW(l));
+            e = cudaGetLastError();
+        }
+    }
+    if (e == cudaSuccess) {
+        colsum_kernel<<<5 * H + 2, 256, 0, st>>>(b, grads, loss_out);
+        e = cudaGetLastError();
+    }
+    return cuda_st(e, "mlp_loss_grad");
+}
+
+mc_status mlp_adam_step(mlp_ctx *c, float *params, const float *grads, float *m, float *v, int32_t t, float lr,
+                        float beta1, float beta2, float eps, void *stream) {
+    if (!c || !params || !grads || !m || !v || t < 1) return MC_ERR_INVALID_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const float c1 = 1.0f / (1.0f - powf(beta1, (float)t));
+    const float c2 = 1.0f / (1.0f - powf(beta2, (float)t));
+    adam_kernel<<<grid_for(kParams), 256, 0, st>>>(params, grads, m, v, kParams, lr, beta1, beta2, eps, c1, c2);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_st(e, "adam");
+    return mlp_set_weights(c, params, stream);
+}
+
+mc_status mlp_error_flag(mlp_ctx *c, int32_t *flag_host) {
+    if (!c || !flag_host) return MC_ERR_INVALID_ARG;
+    return cuda_st(cudaMemcpy(flag_host, c->b.err, sizeof(int), cudaMemcpyDeviceToHost), "error flag");
+}
+
+}  // extern "C"

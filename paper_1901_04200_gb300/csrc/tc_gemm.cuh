@@ -135,8 +135,10 @@ struct GemmShape {
     int *err;       // set to 1 if an mbarrier wait expired
 };
 
-// The GEMM body; Epi::apply(row, col0, v[32], ncols, kslice) consumes the
-// accumulator columns col0..col0+ncols-1 of global row `row`.
+// The GEMM body; Epi::apply(row, col0, v[32], ncols, kslice, state) consumes
+// the accumulator columns col0..col0+ncols-1 of global row `row`, in
+// increasing col0; `state` is a per-thread float the epilogue may carry from
+// one piece of its row to the next (it starts at 0).
 template <class Epi>
 __device__ __forceinline__ void gemm_body(const GemmShape &g, const Epi &epi) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -210,11 +212,12 @@ __device__ __forceinline__ void gemm_body(const GemmShape &g, const Epi &epi) {
     } else {
         const long long row = row0 + warp * 32 + lane;
         const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+        float state = 0.0f;
         for (int c0 = 0; c0 < N; c0 += 32) {
             float v[32];
             if (N - c0 >= 32) tmem_ld32(trow + (uint32_t)c0, v);
             else tmem_ld16(trow + (uint32_t)c0, v);
-            epi.apply(row, c0, v, (N - c0) < 32 ? (N - c0) : 32, blockIdx.y);
+            epi.apply(row, c0, v, (N - c0) < 32 ? (N - c0) : 32, blockIdx.y, state);
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");

@@ -10,7 +10,7 @@ struct StoreEpi {
     float *D;
     long long ldd;
     long long slice_stride;  // elements between K-slice outputs
-    __device__ __forceinline__ void apply(long long row, int c0, const float (&v)[32], int n, int ks) const {
+    __device__ __forceinline__ void apply(long long row, int c0, const float (&v)[32], int n, int ks, float &) const {
         float *o = D + ks * slice_stride + row * ldd + c0;
 #pragma unroll
         for (int i = 0; i < 32; ++i)

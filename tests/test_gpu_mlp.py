@@ -1,0 +1,94 @@
+"""The tensor-core surrogate kernels against the FP64 oracle run with the same
+bfloat16 rounding of every matrix-product operand."""
+import numpy as np
+import pytest
+
+from oracle import mlp as omlp
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def L():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1901_04200_gb300 import build as b
+    b.build()
+    from paper_1901_04200_gb300 import _lib
+    return _lib
+
+
+def setup(B, seed=3):
+    rng = np.random.default_rng(seed)
+    p = omlp.init_params(seed)
+    for k in p:
+        if k.startswith("b"):
+            p[k] = rng.normal(scale=0.05, size=p[k].shape)
+    X = rng.uniform(-1, 1, (B, 7)).astype(np.float32).astype(np.float64)
+    y = rng.normal(size=B).astype(np.float32).astype(np.float64)
+    dy = rng.normal(size=(B, 5)).astype(np.float32).astype(np.float64)
+    return p, X, y, dy
+
+
+def cuda32(a):
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float32, device="cuda")
+
+
+def rel(a, b):
+    return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+
+
+@pytest.mark.parametrize("B,n", [(128, 128), (256, 200), (4096, 4096)])
+def test_forward_and_input_grad(L, B, n):
+    p, X, _, _ = setup(n)
+    net = L.Mlp(B)
+    prm = cuda32(omlp.flatten(p))
+    net.set_weights(prm)
+    out, dx = net.forward(prm, cuda32(X), with_grad=True)
+    torch.cuda.synchronize()
+    assert net.error_flag() == 0
+    o_ref, cache = omlp.forward(p, X, bf16=True)
+    g_ref, _ = omlp.input_grad(p, cache, bf16=True)
+    assert rel(out.cpu().numpy(), o_ref) <= 2e-3
+    assert rel(dx.cpu().numpy(), g_ref) <= 5e-3
+
+
+@pytest.mark.parametrize("alpha", [0.0, 0.5])
+def test_loss_grad_matches_oracle(L, alpha):
+    B = 512
+    p, X, y, dy = setup(B, seed=11)
+    net = L.Mlp(B)
+    prm = cuda32(omlp.flatten(p))
+    net.set_weights(prm)
+    grads = torch.zeros(net.n_params, dtype=torch.float32, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    net.loss_grad(prm, cuda32(X), cuda32(y), cuda32(dy), alpha, grads, loss)
+    torch.cuda.synchronize()
+    assert net.error_flag() == 0
+    L_ref, g_ref, _, _ = omlp.loss_grad(p, X, y, dy, alpha, bf16=True)
+    assert abs(loss.item() - L_ref) <= 2e-3 * abs(L_ref)
+    gv = grads.cpu().numpy().astype(np.float64)
+    gr = omlp.flatten(g_ref)
+    for name, s in omlp.SHAPES:
+        a = omlp.unflatten(gv)[name]
+        b = omlp.unflatten(gr)[name]
+        assert np.max(np.abs(a - b)) <= 2e-2 * np.max(np.abs(gr)), (name, np.max(np.abs(a - b)), np.max(np.abs(b)))
+    assert rel(gv, gr) <= 1e-2
+
+
+def test_adam_step_matches_oracle(L):
+    B = 128
+    p, X, y, dy = setup(B, seed=2)
+    net = L.Mlp(B)
+    vec = omlp.flatten(p)
+    prm = cuda32(vec)
+    g = np.random.default_rng(0).normal(size=vec.size)
+    m = torch.zeros_like(prm)
+    v = torch.zeros_like(prm)
+    pv, mv, vv = vec.copy(), np.zeros_like(vec), np.zeros_like(vec)
+    for t in range(1, 4):
+        net.adam_step(prm, cuda32(g * t), m, v, t, lr=1e-3)
+        pv, mv, vv = omlp.adam(pv, g * t, mv, vv, t, lr=1e-3)
+    torch.cuda.synchronize()
+    assert np.max(np.abs(prm.cpu().numpy() - pv)) <= 1e-6
