@@ -60,6 +60,7 @@ struct Bufs {
     float *z[5];         // [B][H], l = 1..4
     bf16 *h[5];          // [B][H], l = 1..4
     float *out, *obar, *loss_rows;  // [B]
+    float *outp;         // [H / kBN][B] partial dot products of F4
     bf16 *p[5];          // [B][H], l = 1..4
     float *g[5];         // [B][H], l = 1..3 ; g[0]: [B][NX]
     bf16 *gb0;           // [B][KX]
@@ -114,14 +115,14 @@ struct EpiFwd {
     }
 };
 
-// F4: as F1..F3, plus out = h . w5 + b5 (accumulated over the column pieces of
-// this thread's row), out_bar, the value loss and p_4 = w5 silu'(z_4).
+// F4: as F1..F3, plus the partial dot product h . w5 of this CTA's columns
+// (outp[tile][row], summed by finish_out_kernel) and p_4 = w5 silu'(z_4).
 struct EpiFwdLast {
-    const float *bias, *w5, *b5, *y;
-    float *z, *out, *obar, *loss_rows;
+    const float *bias, *w5;
+    float *z, *outp;
     bf16 *h, *p4, *p4T;  // p4T = Aop_4, column row
-    long long B2;
-    float inv_b;
+    long long B2, B;
+    int BN;
     __device__ void apply(long long row, int c0, const float (&acc)[32], int n, int, float &acc_out) const {
         float zz[32], hh[32], pp[32];
         for (int i = 0; i < 32; ++i) {
@@ -134,15 +135,7 @@ struct EpiFwdLast {
         store_row_bf16(h, H, row, c0, hh, n);
         store_row_bf16(p4, H, row, c0, pp, n);
         store_t(p4T, B2, 0, row, c0, pp, n);
-        if (c0 + n >= H) {
-            const float o = acc_out + b5[0];
-            out[row] = o;
-            if (y) {
-                const float d = o - y[row];
-                obar[row] = 2.0f * d * inv_b;
-                loss_rows[row] = d * d * inv_b;
-            }
-        }
+        if ((c0 + n) % BN == 0) outp[(long long)(c0 / BN) * B + row] = acc_out;
     }
 };
 
@@ -263,20 +256,24 @@ __global__ void __launch_bounds__(tc::kThreads) gemm_kernel(const tc::GemmShape 
     tc::gemm_body(g, e);
 }
 
+constexpr int kBN = 64;  // columns per CTA for N >= 64
+__host__ __device__ constexpr int tile_n(int N) { return N >= kBN ? kBN : N; }
+
 template <class Epi>
 cudaError_t gemm(const bf16 *A, long long lda, const bf16 *Bm, long long ldb, int M, int N, int K, int k_slice,
                  const Epi &e, int *err, cudaStream_t st) {
-    tc::GemmShape g{A, lda, Bm, ldb, M, N, K, k_slice, err};
+    const int BN = tile_n(N);
+    tc::GemmShape g{A, lda, Bm, ldb, M, N, K, BN, k_slice, err};
     const int kb = (k_slice / tc::kBK) < tc::kMaxKB ? (k_slice / tc::kBK) : tc::kMaxKB;
-    const size_t smem = tc::smem_bytes(N, kb);
-    static bool attr_set = false;  // the largest tile any call uses: N = 256, four k-blocks
+    const size_t smem = tc::smem_bytes(BN, kb);
+    static bool attr_set = false;  // the largest tile any call uses: BN = 64, four k-blocks
     if (!attr_set) {
         cudaError_t r = cudaFuncSetAttribute(gemm_kernel<Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)tc::smem_bytes(256, tc::kMaxKB));
+                                             (int)tc::smem_bytes(kBN, tc::kMaxKB));
         if (r != cudaSuccess) return r;
         attr_set = true;
     }
-    gemm_kernel<Epi><<<dim3(M / tc::kBM, K / k_slice), tc::kThreads, smem, st>>>(g, e);
+    gemm_kernel<Epi><<<dim3(M / tc::kBM, N / BN, K / k_slice), tc::kThreads, smem, st>>>(g, e);
     return cudaGetLastError();
 }
 
@@ -315,6 +312,23 @@ __global__ void weights_to_bf16_kernel(const float *__restrict__ prm, bf16 *W1b,
     }
 }
 
+// out = sum of the F4 partial dot products (tile order) + b5; with labels,
+// out_bar = 2 (out - y)/B and the value part of the loss.
+__global__ void finish_out_kernel(const float *__restrict__ outp, int ntile, int B, const float *__restrict__ b5,
+                                  const float *__restrict__ y, float inv_b, float *out, float *obar,
+                                  float *loss_rows) {
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < B; r += gridDim.x * blockDim.x) {
+        float o = b5[0];
+        for (int t = 0; t < ntile; ++t) o += outp[(long long)t * B + r];
+        out[r] = o;
+        if (y) {
+            const float d = o - y[r];
+            obar[r] = 2.0f * d * inv_b;
+            loss_rows[r] = d * d * inv_b;
+        }
+    }
+}
+
 // dW_l[i][k] = sum over K slices in order (layer 1: k < 7 of the 16 computed columns).
 __global__ void reduce_split_kernel(const float *__restrict__ part, int N, int ncopy, float *dW) {
     for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < H * ncopy; q += gridDim.x * blockDim.x) {
@@ -325,36 +339,35 @@ __global__ void reduce_split_kernel(const float *__restrict__ part, int N, int n
     }
 }
 
-// Column sums in a fixed order: db_l = sum_rows z_bar_l, dw5 = sum_rows (g_bar_4 + h_4 out_bar),
-// db5 = sum out_bar, loss = sum loss_rows.  One block per output.
+// Column sums in a fixed order, coalesced: block q covers 32 consecutive
+// columns of one source; lane = column, the 8 warps take rows w, w+8, ... and
+// the warps' sums are added in warp order.  Sources: q < 32: db_l = sum_rows
+// z_bar_l (l = 1 + q/8); q < 40: dw5 = sum_rows (g_bar_4 + h_4 out_bar);
+// q == 40: db5 = sum out_bar (column 0) and the loss (column 1).
 __global__ void __launch_bounds__(256) colsum_kernel(const Bufs b, float *grads, float *loss_out) {
-    __shared__ float red[256];
-    const int col = blockIdx.x;  // 0..4H-1: biases; 4H..5H-1: w5; 5H: b5; 5H+1: loss
+    __shared__ float red[8][33];
+    const int q = blockIdx.x, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int B = b.B;
     float s = 0.0f;
-    if (col < 4 * H) {
-        const int l = 1 + col / H, c = col % H;
-        for (int r = threadIdx.x; r < B; r += blockDim.x) s += b.zb[l][(long long)r * H + c];
-    } else if (col < 5 * H) {
-        const int c = col - 4 * H;
-        for (int r = threadIdx.x; r < B; r += blockDim.x)
+    if (q < 32) {
+        const int l = 1 + q / 8, c = (q % 8) * 32 + lane;
+        for (int r = w; r < B; r += 8) s += b.zb[l][(long long)r * H + c];
+    } else if (q < 40) {
+        const int c = (q - 32) * 32 + lane;
+        for (int r = w; r < B; r += 8)
             s += b.gb4f[(long long)r * H + c] + __bfloat162float(b.h[4][(long long)r * H + c]) * b.obar[r];
-    } else if (col == 5 * H) {
-        for (int r = threadIdx.x; r < B; r += blockDim.x) s += b.obar[r];
-    } else {
-        for (int r = threadIdx.x; r < B; r += blockDim.x) s += b.loss_rows[r];
+    } else if (lane < 2) {
+        for (int r = w; r < B; r += 8) s += lane == 0 ? b.obar[r] : b.loss_rows[r];
     }
-    red[threadIdx.x] = s;
+    red[w][lane] = s;
     __syncthreads();
-    for (int w = 128; w > 0; w >>= 1) {
-        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        if (col < 4 * H) grads[ob(1 + col / H) + col % H] = red[0];
-        else if (col < 5 * H) grads[ow5 + col - 4 * H] = red[0];
-        else if (col == 5 * H) grads[ob5] = red[0];
-        else if (loss_out) loss_out[0] = red[0];
+    if (w == 0) {
+        float t = 0.0f;
+        for (int k = 0; k < 8; ++k) t += red[k][lane];
+        if (q < 32) grads[ob(1 + q / 8) + (q % 8) * 32 + lane] = t;
+        else if (q < 40) grads[ow5 + (q - 32) * 32 + lane] = t;
+        else if (lane == 0) grads[ob5] = t;
+        else if (lane == 1 && loss_out) loss_out[0] = t;
     }
 }
 
@@ -414,6 +427,7 @@ size_t layout(unsigned char *base, int B, Bufs *out) {
     b.out = c.take<float>(B);
     b.obar = c.take<float>(B);
     b.loss_rows = c.take<float>(B);
+    b.outp = c.take<float>((size_t)(H / 64) * B);
     for (int l = 1; l <= 4; ++l) b.p[l] = c.take<bf16>(BH);
     b.g[0] = c.take<float>((size_t)B * NX);
     for (int l = 1; l <= 3; ++l) b.g[l] = c.take<float>(BH);
@@ -461,9 +475,12 @@ cudaError_t run_forward(mlp_ctx *c, const float *prm, const float *y, const floa
         if (e != cudaSuccess) return e;
     }
     {
-        EpiFwdLast ep{prm + ob4, prm + ow5, prm + ob5, y, b.z[4], b.out, b.obar, b.loss_rows, b.h[4], b.p[4],
-                      b.Aop[4], B2, inv_b};
+        EpiFwdLast ep{prm + ob4, prm + ow5, b.z[4], b.outp, b.h[4], b.p[4], b.Aop[4], B2, B, kBN};
         e = gemm(b.h[3], H, b.Wb[4], H, B, H, H, H, ep, b.err, st);
+        if (e != cudaSuccess) return e;
+        finish_out_kernel<<<grid_for(B), 256, 0, st>>>(b.outp, H / kBN, B, prm + ob5, y, inv_b, b.out, b.obar,
+                                                      b.loss_rows);
+        e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
     if (!tangent) return cudaSuccess;
@@ -595,7 +612,7 @@ mc_status mlp_loss_grad(mlp_ctx *c, const float *params, const float *X, const f
         }
     }
     if (e == cudaSuccess) {
-        colsum_kernel<<<5 * H + 2, 256, 0, st>>>(b, grads, loss_out);
+        colsum_kernel<<<41, 256, 0, st>>>(b, grads, loss_out);
         e = cudaGetLastError();
     }
     return cuda_st(e, "mlp_loss_grad");

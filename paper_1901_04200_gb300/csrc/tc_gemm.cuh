@@ -2,8 +2,9 @@
 // (tcgen05.mma, accumulator in tensor memory), D[M x N] = A[M x K] B[N x K]^T,
 // with both operands K-major ("row-major, K contiguous") in global memory.
 //
-// One CTA of 128 threads computes a 128 x N tile (N <= 256, a multiple of 16)
-// over its K slice (blockIdx.y picks the slice when K is split).  Operand
+// One CTA of 128 threads computes a 128 x BN tile (BN <= 256, a multiple of
+// 16) of D: blockIdx.x picks the 128 rows, blockIdx.y the BN columns and
+// blockIdx.z the K slice when K is split.  Operand
 // k-blocks of 64 elements (128 bytes per row) are copied to shared memory with
 // 16-byte cp.async in the 128-byte-swizzle K-major layout (row r at r*128 B,
 // 16-byte chunk c stored at chunk c ^ (r & 7), tiles 1024-byte aligned), up to
@@ -130,20 +131,22 @@ struct GemmShape {
     long long lda;  // elements between rows of A (>= K, multiple of 8)
     const __nv_bfloat16 *B;
     long long ldb;
-    int M, N, K;    // M % 128 == 0, N % 16 == 0 and 16 <= N <= 256, K % 64 == 0
-    int k_slice;    // K per CTA (a multiple of 64); gridDim.y = K / k_slice
+    int M, N, K;    // M % 128 == 0, N % BN == 0, K % 64 == 0
+    int BN;         // columns per CTA: a multiple of 16, at most 256; gridDim.y = N / BN
+    int k_slice;    // K per CTA (a multiple of 64); gridDim.z = K / k_slice
     int *err;       // set to 1 if an mbarrier wait expired
 };
 
 // The GEMM body; Epi::apply(row, col0, v[32], ncols, kslice, state) consumes
-// the accumulator columns col0..col0+ncols-1 of global row `row`, in
-// increasing col0; `state` is a per-thread float the epilogue may carry from
-// one piece of its row to the next (it starts at 0).
+// the accumulator columns col0..col0+ncols-1 (global column indices) of
+// global row `row`, in increasing col0 within this CTA's BN columns; `state`
+// is a per-thread float the epilogue may carry from one piece of its row to
+// the next (it starts at 0).
 template <class Epi>
 __device__ __forceinline__ void gemm_body(const GemmShape &g, const Epi &epi) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *base = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    const int N = g.N;
+    const int N = g.BN;
     const int kb_total = g.k_slice / kBK;
     const int kb_round = kb_total < kMaxKB ? kb_total : kMaxKB;
     unsigned char *tA = base;
@@ -169,7 +172,8 @@ __device__ __forceinline__ void gemm_body(const GemmShape &g, const Epi &epi) {
     const uint32_t bar_s = smem_u32(bar);
     const uint32_t idesc = idesc_bf16(kBM, N);
     const long long row0 = (long long)blockIdx.x * kBM;
-    const long long kbase = (long long)blockIdx.y * g.k_slice;
+    const long long col_base = (long long)blockIdx.y * g.BN;
+    const long long kbase = (long long)blockIdx.z * g.k_slice;
     uint32_t phase = 0;
     bool ok = true;
 
@@ -183,7 +187,7 @@ __device__ __forceinline__ void gemm_body(const GemmShape &g, const Epi &epi) {
         }
         for (int q = tid; q < nkb * N * 8; q += kThreads) {
             const int kb = q / (N * 8), rem = q - kb * (N * 8), r = rem >> 3, c = rem & 7;
-            const __nv_bfloat16 *src = g.B + (long long)r * g.ldb + kbase + (long long)(kb0 + kb) * kBK + c * 8;
+            const __nv_bfloat16 *src = g.B + (col_base + r) * g.ldb + kbase + (long long)(kb0 + kb) * kBK + c * 8;
             cp_async16(smem_u32(tB + kb * tile_b_bytes(N) + r * 128 + ((c ^ (r & 7)) << 4)), src);
         }
         asm volatile("cp.async.wait_all;" ::: "memory");
@@ -217,7 +221,7 @@ __device__ __forceinline__ void gemm_body(const GemmShape &g, const Epi &epi) {
             float v[32];
             if (N - c0 >= 32) tmem_ld32(trow + (uint32_t)c0, v);
             else tmem_ld16(trow + (uint32_t)c0, v);
-            epi.apply(row, c0, v, (N - c0) < 32 ? (N - c0) : 32, blockIdx.y, state);
+            epi.apply(row, (int)col_base + c0, v, (N - c0) < 32 ? (N - c0) : 32, blockIdx.z, state);
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");

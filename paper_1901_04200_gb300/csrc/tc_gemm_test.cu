@@ -35,12 +35,13 @@ extern "C" mc_status mc_tc_gemm_bf16(const void *A, int64_t lda, const void *B, 
         return MC_ERR_INVALID_ARG;
     if (lda < K || ldb < K || lda % 8 || ldb % 8 || ldd < N) return MC_ERR_INVALID_ARG;
     if (((uintptr_t)A & 15u) || ((uintptr_t)B & 15u)) return MC_ERR_INVALID_ARG;
-    tc::GemmShape g{(const __nv_bfloat16 *)A, lda, (const __nv_bfloat16 *)B, ldb, M, N, K, k_slice, err};
+    const int BN = N >= 64 && N % 64 == 0 ? 64 : N;
+    tc::GemmShape g{(const __nv_bfloat16 *)A, lda, (const __nv_bfloat16 *)B, ldb, M, N, K, BN, k_slice, err};
     tc::StoreEpi e{D, ldd, (long long)M * ldd};
     const int kb = (k_slice / tc::kBK) < tc::kMaxKB ? (k_slice / tc::kBK) : tc::kMaxKB;
-    const size_t smem = tc::smem_bytes(N, kb);
+    const size_t smem = tc::smem_bytes(BN, kb);
     cudaError_t st = cudaFuncSetAttribute(tc::gemm_store_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (st != cudaSuccess) return MC_ERR_CUDA;
-    tc::gemm_store_kernel<<<dim3(M / tc::kBM, K / k_slice), tc::kThreads, smem, (cudaStream_t)stream>>>(g, e);
+    tc::gemm_store_kernel<<<dim3(M / tc::kBM, N / BN, K / k_slice), tc::kThreads, smem, (cudaStream_t)stream>>>(g, e);
     return cudaGetLastError() == cudaSuccess ? MC_OK : MC_ERR_CUDA;
 }
