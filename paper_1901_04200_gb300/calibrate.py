@@ -64,8 +64,10 @@ class _Converged(Exception):
     pass
 
 
-def descend_lbfgs(value_and_grad, theta0, lo, hi, tol, max_evals=500, gtol=1e-12):
-    """L-BFGS-B on u = (theta - lo)/(hi - lo) in [0, 1]^5; stops when G < tol."""
+def descend_lbfgs(value_and_grad, theta0, lo, hi, tol, max_evals=500, gtol=1e-12, restarts=20):
+    """L-BFGS-B on u = (theta - lo)/(hi - lo) in [0, 1]^5; stops when G < tol.
+    When the line search gives up before that, it restarts from the best point
+    (fresh curvature memory) while evaluations remain."""
     from scipy.optimize import minimize
     lo = np.asarray(lo, dtype=np.float64)
     width = np.asarray(hi, dtype=np.float64) - lo
@@ -84,16 +86,76 @@ def descend_lbfgs(value_and_grad, theta0, lo, hi, tol, max_evals=500, gtol=1e-12
         return G, g * width
 
     t0 = time.perf_counter()
-    u0 = np.clip((np.asarray(theta0, dtype=np.float64) - lo) / width, 0.0, 1.0)
     iters = 0
+    messages = []
     try:
-        res = minimize(f, u0, jac=True, method="L-BFGS-B", bounds=[(0.0, 1.0)] * len(u0),
-                       options={"maxfun": max_evals, "maxiter": max_evals, "ftol": 0.0, "gtol": gtol})
-        iters = int(res.nit)
+        for _ in range(restarts + 1):
+            left = max_evals - best["evals"]
+            if left <= 0:
+                break
+            u0 = np.clip((best["theta"] - lo) / width, 0.0, 1.0)
+            g_before = best["G"]
+            res = minimize(f, u0, jac=True, method="L-BFGS-B", bounds=[(0.0, 1.0)] * len(u0),
+                           options={"maxfun": left, "maxiter": left, "ftol": 0.0, "gtol": gtol})
+            iters += int(res.nit)
+            messages.append(str(res.message))
+            if not best["G"] < g_before and res.nit == 0:
+                break
     except _Converged:
-        iters = -1
-    return DescentResult(best["theta"], best["G"], iters, best["evals"], time.perf_counter() - t0,
-                         best["G"] < tol, trace)
+        pass
+    out = DescentResult(best["theta"], best["G"], iters, best["evals"], time.perf_counter() - t0,
+                        best["G"] < tol, trace)
+    out.messages = messages
+    return out
+
+
+def descend_metric(value_and_grad, metric, theta0, lo, hi, tol, max_evals=100, damping=1e-6, max_halvings=12):
+    """Descent on G with the gradient from value_and_grad (the MC-AAD two-step
+    algorithm) and a metric from metric(theta) -> J [m, 5]: the step solves
+    (J^T J + damping tr/5 I) d = -grad in box-scaled coordinates, halved until
+    G decreases, projected onto the box.  With J the surrogate's pathwise-trained
+    Jacobian this is a Gauss-Newton step whose curvature costs no Monte Carlo."""
+    lo = np.asarray(lo, dtype=np.float64)
+    width = np.asarray(hi, dtype=np.float64) - lo
+    t0 = time.perf_counter()
+    u = np.clip((np.asarray(theta0, dtype=np.float64) - lo) / width, 0.0, 1.0)
+    G, g = value_and_grad(lo + u * width)
+    evals, iters = 1, 0
+    trace = [(1, G)]
+    while G >= tol and evals < max_evals:
+        J = metric(lo + u * width) * width[None, :]
+        Hm = J.T @ J
+        Hm = Hm + damping * max(np.trace(Hm) / len(u), 1e-300) * np.eye(len(u))
+        d = -np.linalg.solve(Hm, g * width)
+        t = 1.0
+        accepted = False
+        for _ in range(max_halvings):
+            cand = np.clip(u + t * d, 0.0, 1.0)
+            Gc, gc = value_and_grad(lo + cand * width)
+            evals += 1
+            trace.append((evals, Gc))
+            if np.isfinite(Gc) and Gc < G:
+                u, G, g = cand, Gc, gc
+                accepted = True
+                break
+            t *= 0.5
+            if evals >= max_evals:
+                break
+        iters += 1
+        if not accepted:
+            break
+    return DescentResult(lo + u * width, G, iters, evals, time.perf_counter() - t0, G < tol, trace)
+
+
+def surrogate_jacobian(sur, K, T):
+    Kt = torch.as_tensor(K, dtype=torch.float64, device=sur.device)
+    Tt = torch.as_tensor(T, dtype=torch.float64, device=sur.device)
+
+    def f(theta):
+        _, dp = sur.prices(torch.as_tensor(theta, dtype=torch.float64), Kt, Tt, with_grad=True)
+        return dp.cpu().numpy()
+
+    return f
 
 
 def mc_objective(ctx, C, seed, n_paths):
@@ -135,6 +197,6 @@ def run_experiment(ctx, sur, theta0, C, seed, n_paths, tol=1e-8, max_evals=500, 
     sf = surrogate_objective(sur, pb.K, T, C)
     sf(np.asarray(theta0))
     s1 = descend_lbfgs(sf, theta0, lo, hi, 0.0, max_evals=sur_evals)
-    s2 = descend_lbfgs(mc, s1.theta, lo, hi, tol, max_evals=max_evals)
+    s2 = descend_metric(mc, surrogate_jacobian(sur, pb.K, T), s1.theta, lo, hi, tol, max_evals=max_evals)
     return {"plain": plain, "surrogate_phase": s1, "mc_phase": s2,
             "surrogate_total_seconds": s1.seconds + s2.seconds}
