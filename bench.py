@@ -42,12 +42,18 @@ UNIT = "path-steps/s"
 #   => F = 22 FP32 + 5 MUFU + 24 INT = 51 ops;
 #   Heston adjoint step R: 17 FP32.
 # Forward kernel runs F; reverse kernel runs F (recompute) + R.
-OPS = {"forward_sweep": {"fp32": 22, "mufu": 5, "int": 24},
-       "reverse_sweep": {"fp32": 39, "mufu": 5, "int": 24}}
+OPS = {"heston": {"forward_sweep": {"fp32": 22, "mufu": 5, "int": 24},
+                  "reverse_sweep": {"fp32": 39, "mufu": 5, "int": 24}},
+       # local vol, per path-step (one normal): Philox 10 INT + uniform 2 INT, Box-Muller half a
+       # pair (3.5 FP32 + 2 MUFU, 1 FADD), bilinear step 16 FP32 (cell, clamp, lerp, Euler);
+       # adjoint: cell and lerp again 12 FP32, sigma-bar and weights 6, four row-adjoint FMAs 4,
+       # d sigma/dx term 2 (shared-memory loads and stores not counted)
+       "lv": {"forward_sweep": {"fp32": 21, "mufu": 2, "int": 12},
+              "reverse_sweep": {"fp32": 45, "mufu": 2, "int": 12}}}
 
 
-def _ops(kernel):
-    return sum(OPS[kernel].values())
+def _ops(model, kernel):
+    return sum(OPS[model][kernel].values())
 
 
 def load_peaks():
@@ -125,6 +131,46 @@ def cpu_baseline(workload, n_paths, threads=None):
             "sample": "%d of the workload's paths x %d steps, FP64, value+grad, %.1f s wall" % (n_paths, steps, dt)}
 
 
+def calibration_experiment(cases):
+    """Surrogate labels and training (the learned part), then Heston calibration to
+    G < 1e-8 at 2^22 paths: surrogate-assisted vs plain MC-AAD descent from the same starts."""
+    import numpy as np
+    import torch
+
+    from paper_1901_04200_gb300 import _lib, calibrate, inputs, surrogate
+    pb = inputs.heston_config().problem
+    n_theta, n_paths = 16384, 1 << 16
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    X, y, dy = surrogate.make_dataset(pb, n_theta, n_paths)
+    torch.cuda.synchronize()
+    t_data = time.perf_counter() - t0
+    sur = surrogate.Surrogate(batch=4096)
+    epochs = 40
+    t_train = sur.train(X, y, dy, epochs=epochs, lr=2e-3)
+    P, seed = 1 << 22, 777
+    ctx = _lib.Context(pb, max_paths=P)
+    rows = []
+    for sd in range(cases):
+        rng = np.random.default_rng(1000 + sd)
+        theta_star, theta0 = inputs.draw_heston_theta(rng), inputs.draw_heston_theta(rng)
+        C = ctx.forward(theta_star, seed, P).cpu().numpy()
+        r = calibrate.run_experiment(ctx, sur, theta0, C, seed, P, tol=1e-8, max_evals=300)
+        rows.append((r["plain"].converged, r["plain"].evals, r["plain"].seconds, r["mc_phase"].converged,
+                     r["mc_phase"].evals, r["surrogate_phase"].seconds + r["mc_phase"].seconds))
+    a = np.array(rows, dtype=float)
+    n_samples = n_theta * pb.m
+    return {"tol": 1e-8, "paths": P, "cases": cases, "start": "theta*, theta0 drawn in the Heston box (Feller)",
+            "labels": {"samples": n_samples, "paths_per_sample": n_paths, "seconds": t_data},
+            "training": {"epochs": epochs, "batch": 4096, "seconds": t_train,
+                         "samples_per_s": epochs * (n_samples // 4096) * 4096 / t_train},
+            "plain": {"converged": float(a[:, 0].mean()), "median_mc_evals": float(np.median(a[:, 1])),
+                      "median_seconds": float(np.median(a[:, 2]))},
+            "surrogate": {"converged": float(a[:, 3].mean()), "median_mc_evals": float(np.median(a[:, 4])),
+                          "median_seconds_excl_training": float(np.median(a[:, 5])),
+                          "one_off_seconds": t_data + t_train}}
+
+
 def dist_setup(n_gpus):
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -189,6 +235,10 @@ def main():
     ap.add_argument("--ref-paths", type=int, default=1 << 15)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ppt", type=int, default=0, help="paths per GPU thread (0 = library default)")
+    ap.add_argument("--workload", default="heston", choices=["heston", "lv"],
+                    help="heston (the metric's workload) or lv (2^22 x 500 local vol, for measurement)")
+    ap.add_argument("--no-calibration", action="store_true", help="skip the surrogate vs plain calibration")
+    ap.add_argument("--calib-cases", type=int, default=4)
     ap.add_argument("--ckpt", type=int, default=0, help="checkpoint interval (0 = workload default)")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -204,7 +254,10 @@ def main():
     if rank == 0:
         _build.build()
     barrier(world)
-    w = inputs.heston_config(n_paths=args.paths)
+    if args.workload == "lv":
+        w = inputs.lv_config(n_paths=args.paths if args.paths != (1 << 20) else (1 << 22))
+    else:
+        w = inputs.heston_config(n_paths=args.paths)
     if args.ppt or args.ckpt:
         w.problem.paths_per_thread = args.ppt
         w.problem.ckpt_every = args.ckpt or w.problem.ckpt_every
@@ -275,28 +328,30 @@ def main():
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     issue_peak = 128 * n_sm * sm_mhz_peak * 1e6  # thread-ops/s: 4 warp instructions per SM per clock
     rev_ms, rev_n = prof["reverse_sweep"]
-    fwd_ms, fwd_n = prof["forward_sweep"]
     rev_avg = rev_ms / max(rev_n, 1)
-    achieved = P * S * _ops("reverse_sweep") / (rev_avg * 1e-3)
+    model = args.workload
+    achieved = P * S * _ops(model, "reverse_sweep") / (rev_avg * 1e-3)
     launches = sum(n for _, n in prof.values())
 
     if rank == 0:
         line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "metric": METRIC if model == "heston" else METRIC.replace("Heston FT, 2^20 paths x 512 steps, m=64, M=5",
+                                                                      "local vol, 2^22 paths x 500 steps, m=200, M=200"),
+            "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": ms_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": w.name, "paths_per_gpu": P, "steps": S, "instruments": pb.m, "params": 5,
+            "config": {"workload": w.name, "paths_per_gpu": P, "steps": S, "instruments": pb.m, "params": pb.n_params,
                        "ckpt_every": pb.ckpt_every, "paths_per_thread": pb.paths_per_thread or "default",
                        "precision": "fp32 paths, fp64 sums",
                        "l2": "inputs larger than L2: checkpoints %.0f MB per step" %
-                             (P * (S // pb.ckpt_every) * 2 * 4 / 1e6)},
+                             (P * (S // pb.ckpt_every) * (2 if model == "heston" else 1) * 4 / 1e6)},
             "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": issue_peak / 1e12,
                          "unit": "Tops/s", "frac": achieved / issue_peak, "traffic": None,
-                         "kernel": "path_reverse_kernel<Heston,f32,K=%d>" % pb.ckpt_every,
-                         "ops_per_path_step": _ops("reverse_sweep"),
+                         "kernel": "path_reverse_kernel<%s,f32,K=%d>" % (model, pb.ckpt_every),
+                         "ops_per_path_step": _ops(model, "reverse_sweep"),
                          "peak_basis": "SM issue rate 128 thread-ops/clk x %d SMs x %.0f MHz (%s max clock)"
                                        % (n_sm, sm_mhz_peak, peak_src),
-                         "fp32_frac": P * S * OPS["reverse_sweep"]["fp32"] / (rev_avg * 1e-3) / issue_peak},
+                         "fp32_frac": P * S * OPS[model]["reverse_sweep"]["fp32"] / (rev_avg * 1e-3) / issue_peak},
             "kernels_ms_per_step": {k: v[0] / max(v[1], 1) for k, v in prof.items() if v[1]},
             "gpu_launches": launches,
             "e2e": {"value": world * P * S / (e2e_ms * 1e-3), "unit": UNIT,
@@ -304,7 +359,9 @@ def main():
             "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"]},
         }
         if not args.no_cpu_baseline and world == 1:
-            line["cpu_baseline"] = cpu_baseline(w, args.cpu_paths)
+            line["cpu_baseline"] = cpu_baseline(w, args.cpu_paths if model == "heston" else args.cpu_paths // 4)
+        if not args.no_calibration and world == 1 and model == "heston":
+            line["calibration"] = calibration_experiment(args.calib_cases)
         print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist

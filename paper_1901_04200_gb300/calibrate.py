@@ -109,41 +109,37 @@ def descend_lbfgs(value_and_grad, theta0, lo, hi, tol, max_evals=500, gtol=1e-12
     return out
 
 
-def descend_metric(value_and_grad, metric, theta0, lo, hi, tol, max_evals=100, damping=1e-6, max_halvings=12):
+def descend_metric(value_and_grad, metric, theta0, lo, hi, tol, max_evals=100, mu0=1e-6, mu_max=1e8):
     """Descent on G with the gradient from value_and_grad (the MC-AAD two-step
-    algorithm) and a metric from metric(theta) -> J [m, 5]: the step solves
-    (J^T J + damping tr/5 I) d = -grad in box-scaled coordinates, halved until
-    G decreases, projected onto the box.  With J the surrogate's pathwise-trained
-    Jacobian this is a Gauss-Newton step whose curvature costs no Monte Carlo."""
+    algorithm) and the metric from metric(theta) -> J [m, 5]: in box-scaled
+    coordinates the step solves (J^T J + mu diag(J^T J)) d = -grad, projected
+    onto the box (Levenberg-Marquardt damping: mu grows tenfold after a step
+    that does not lower G, shrinks threefold after one that does).  With J the
+    surrogate's Jacobian this is a Gauss-Newton step whose curvature costs no
+    Monte Carlo; with a poor J it falls back towards scaled gradient steps."""
     lo = np.asarray(lo, dtype=np.float64)
     width = np.asarray(hi, dtype=np.float64) - lo
     t0 = time.perf_counter()
     u = np.clip((np.asarray(theta0, dtype=np.float64) - lo) / width, 0.0, 1.0)
     G, g = value_and_grad(lo + u * width)
-    evals, iters = 1, 0
+    evals, iters, mu = 1, 0, mu0
     trace = [(1, G)]
-    while G >= tol and evals < max_evals:
-        J = metric(lo + u * width) * width[None, :]
+    J = metric(lo + u * width) * width[None, :]
+    while G >= tol and evals < max_evals and mu <= mu_max:
         Hm = J.T @ J
-        Hm = Hm + damping * max(np.trace(Hm) / len(u), 1e-300) * np.eye(len(u))
-        d = -np.linalg.solve(Hm, g * width)
-        t = 1.0
-        accepted = False
-        for _ in range(max_halvings):
-            cand = np.clip(u + t * d, 0.0, 1.0)
-            Gc, gc = value_and_grad(lo + cand * width)
-            evals += 1
-            trace.append((evals, Gc))
-            if np.isfinite(Gc) and Gc < G:
-                u, G, g = cand, Gc, gc
-                accepted = True
-                break
-            t *= 0.5
-            if evals >= max_evals:
-                break
-        iters += 1
-        if not accepted:
-            break
+        dg = np.maximum(np.diag(Hm), 1e-12 * max(np.trace(Hm), 1e-300))
+        d = -np.linalg.solve(Hm + mu * np.diag(dg), g * width)
+        cand = np.clip(u + d, 0.0, 1.0)
+        Gc, gc = value_and_grad(lo + cand * width)
+        evals += 1
+        trace.append((evals, Gc))
+        if np.isfinite(Gc) and Gc < G:
+            u, G, g = cand, Gc, gc
+            mu = max(mu / 3.0, 1e-12)
+            iters += 1
+            J = metric(lo + u * width) * width[None, :]
+        else:
+            mu *= 10.0
     return DescentResult(lo + u * width, G, iters, evals, time.perf_counter() - t0, G < tol, trace)
 
 
