@@ -7,8 +7,10 @@ path-steps per second, P * S / (time per step).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-N > 1 runs under torchrun: rank r evaluates its own independent path range
-[r P, (r+1) P) (weak scaling, no collective inside the timed region).
+N > 1 runs under torchrun: rank r evaluates global paths [r P, (r+1) P) of
+one estimator over N P paths (weak scaling); the two exchange steps of the
+algorithm (E y partials before lambda, gradient partials after the reverse
+sweep) are NCCL all-gathers of m + 1 and M + 1 numbers.
 --impl reference times the FP64 CPU oracle on a bounded sample instead.
 """
 from __future__ import annotations
@@ -54,6 +56,29 @@ OPS = {"heston": {"forward_sweep": {"fp32": 22, "mufu": 5, "int": 24},
 
 def _ops(model, kernel):
     return sum(OPS[model][kernel].values())
+
+
+# DRAM bytes (read + write) per launch of the dominant kernel, from one ncu
+# capture of the bench command (profiles/heston_fp32_p2e20_s512_value_and_grad.md);
+# reported only while the kernel sources hash to the profiled version.
+MEASURED_TRAFFIC = {("heston", 8, 2): {"bytes": 536916992 + 3986944, "sources": "cce0c5dafaa043b5"}}
+KERNEL_SOURCES = ["mc_common.cuh", "mc_paths.cuh", "mc_paths_heston.cu"]
+
+
+def kernel_sources_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1901_04200_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(model, k, ppt):
+    rec = MEASURED_TRAFFIC.get((model, k, ppt))
+    if rec and rec["sources"] == kernel_sources_hash():
+        return rec["bytes"]
+    return None
 
 
 def load_peaks():
@@ -129,6 +154,69 @@ def cpu_baseline(workload, n_paths, threads=None):
     steps = pb.last_step
     return {"value": n_paths * steps / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": "%d of the workload's paths x %d steps, FP64, value+grad, %.1f s wall" % (n_paths, steps, dt)}
+
+
+def surrogate_flops_per_step(B=4096):
+    """Dense FLOPs of the tensor-core GEMMs of one training step (2 M N K each,
+    padded shapes as launched)."""
+    H, KX, NX = 256, 64, 16
+    f = 0
+    f += 2 * B * H * KX + 3 * 2 * B * H * H          # F1..F4
+    f += 3 * 2 * B * H * H + 2 * B * NX * H          # T4..T1
+    f += 2 * B * H * KX + 3 * 2 * B * H * H          # R1..R4
+    f += 3 * 2 * B * H * H                           # D4..D2
+    f += 3 * 2 * H * H * (2 * B) + 2 * H * NX * (2 * B)  # G1..G4
+    return f
+
+
+def surrogate_step_bench(args, rank, world):
+    """Training-step throughput of the pricing surrogate (differential loss + Adam), batch 4096."""
+    import torch
+
+    from paper_1901_04200_gb300 import surrogate
+    B = 4096
+    dev = torch.device("cuda", torch.cuda.current_device())
+    g = torch.Generator(device=dev).manual_seed(rank)
+    X = torch.rand((B, 7), device=dev, generator=g) * 2 - 1
+    y = torch.rand(B, device=dev, generator=g) * 0.3
+    dy = torch.randn((B, 5), device=dev, generator=g) * 0.05
+    sur = surrogate.Surrogate(batch=B, device=dev)
+
+    def step(t):
+        sur.train_net.loss_grad(sur.params, X, y, dy, 1.0, sur.grads, sur.loss)
+        sur.train_net.adam_step(sur.params, sur.grads, sur.m, sur.v, t, lr=1e-4)
+
+    for t in range(1, max(args.warmup, 3) + 1):
+        step(t)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks.start()
+    time.sleep(0.3)
+    barrier(world)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for t in range(args.steps):
+        step(100 + t)
+    e1.record()
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world)
+    peaks, src = load_peaks()
+    flops = surrogate_flops_per_step(B)
+    if rank == 0:
+        print(json.dumps({
+            "metric": "surrogate training samples/s (MLP 7->256x4->1, differential loss, batch 4096)",
+            "value": world * B / (ms * 1e-3), "unit": "samples/s", "n_gpus": world, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": "surrogate_mlp_train_step", "batch": B, "params": sur.params.numel()},
+            "roofline": {"bound": "tensor", "achieved": flops / (ms * 1e-3) / 1e12,
+                         "peak": float(peaks.get("bf16_tflops", 1900.0)), "unit": "TFLOP/s",
+                         "frac": flops / (ms * 1e-3) / 1e12 / float(peaks.get("bf16_tflops", 1900.0)),
+                         "traffic": None, "kernel": "all tcgen05 GEMMs of the step (whole-step time)",
+                         "flops_per_step": flops, "peak_basis": "%s bf16 dense burst" % src},
+            "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"]}}))
 
 
 def calibration_experiment(cases):
@@ -235,8 +323,9 @@ def main():
     ap.add_argument("--ref-paths", type=int, default=1 << 15)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ppt", type=int, default=0, help="paths per GPU thread (0 = library default)")
-    ap.add_argument("--workload", default="heston", choices=["heston", "lv"],
-                    help="heston (the metric's workload) or lv (2^22 x 500 local vol, for measurement)")
+    ap.add_argument("--workload", default="heston", choices=["heston", "lv", "surrogate"],
+                    help="heston (the metric's workload), lv (2^22 x 500 local vol) or surrogate "
+                         "(one differential-loss training step of the pricing network), for measurement")
     ap.add_argument("--no-calibration", action="store_true", help="skip the surrogate vs plain calibration")
     ap.add_argument("--calib-cases", type=int, default=4)
     ap.add_argument("--ckpt", type=int, default=0, help="checkpoint interval (0 = workload default)")
@@ -254,6 +343,8 @@ def main():
     if rank == 0:
         _build.build()
     barrier(world)
+    if args.workload == "surrogate":
+        return surrogate_step_bench(args, rank, world)
     if args.workload == "lv":
         w = inputs.lv_config(n_paths=args.paths if args.paths != (1 << 20) else (1 << 22))
     else:
@@ -272,8 +363,14 @@ def main():
     seed = pb.seed
     stream = torch.cuda.current_stream()
 
-    def step():
-        ctx.value_and_grad(theta, C, seed, P, path0=path0, out=out)
+    if world > 1:
+        from paper_1901_04200_gb300.sharding import sharded_value_and_grad
+
+        def step():
+            sharded_value_and_grad(lambda: ctx.forward(theta, seed, P, path0=path0, keep=True), ctx.vjp, C, P)
+    else:
+        def step():
+            ctx.value_and_grad(theta, C, seed, P, path0=path0, out=out)
 
     for _ in range(max(args.warmup, 3)):
         step()
@@ -307,7 +404,14 @@ def main():
     def e2e_step():
         th_d.copy_(th_h, non_blocking=True)
         C_d.copy_(C_h, non_blocking=True)
-        ctx.value_and_grad(th_d, C_d, seed, P, path0=path0, out=outs)
+        if world > 1:
+            Ey_g, G_g, g_g = sharded_value_and_grad(lambda: ctx.forward(th_d, seed, P, path0=path0, keep=True),
+                                                    ctx.vjp, C_d, P)
+            res_d[0:1].copy_(G_g.reshape(1))
+            res_d[1:1 + ctx.M].copy_(g_g)
+            res_d[1 + ctx.M:].copy_(Ey_g)
+        else:
+            ctx.value_and_grad(th_d, C_d, seed, P, path0=path0, out=outs)
         res_h.copy_(res_d, non_blocking=True)
 
     e2e_step()
@@ -346,7 +450,10 @@ def main():
                        "l2": "inputs larger than L2: checkpoints %.0f MB per step" %
                              (P * (S // pb.ckpt_every) * (2 if model == "heston" else 1) * 4 / 1e6)},
             "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": issue_peak / 1e12,
-                         "unit": "Tops/s", "frac": achieved / issue_peak, "traffic": None,
+                         "unit": "Tops/s", "frac": achieved / issue_peak,
+                         "traffic": measured_traffic(model, pb.ckpt_every, pb.paths_per_thread or
+                                                     (2 if model == "heston" else 1)),
+                         "algorithmic_bytes": P * (S // pb.ckpt_every) * (2 if model == "heston" else 1) * 4,
                          "kernel": "path_reverse_kernel<%s,f32,K=%d>" % (model, pb.ckpt_every),
                          "ops_per_path_step": _ops(model, "reverse_sweep"),
                          "peak_basis": "SM issue rate 128 thread-ops/clk x %d SMs x %.0f MHz (%s max clock)"

@@ -72,6 +72,7 @@ struct Bufs {
     bf16 *Aop[5];        // [H][2B]
     bf16 *Bop[5];        // l = 1: [NX][2B], else [H][2B]
     float *part;         // [kSplit][H][H]
+    float *colpart;      // [B / 128][41 * 32] column-sum chunks
     bf16 *Wb[5], *Wt[5];  // W1b [H][KX], W1t [NX][H], Wlb/Wlt [H][H]
     float *lsum;         // [1] loss scratch
     int *err;            // [1] tensor-core wait expiry flag
@@ -339,31 +340,45 @@ __global__ void reduce_split_kernel(const float *__restrict__ part, int N, int n
     }
 }
 
-// Column sums in a fixed order, coalesced: block q covers 32 consecutive
-// columns of one source; lane = column, the 8 warps take rows w, w+8, ... and
-// the warps' sums are added in warp order.  Sources: q < 32: db_l = sum_rows
-// z_bar_l (l = 1 + q/8); q < 40: dw5 = sum_rows (g_bar_4 + h_4 out_bar);
-// q == 40: db5 = sum out_bar (column 0) and the loss (column 1).
-__global__ void __launch_bounds__(256) colsum_kernel(const Bufs b, float *grads, float *loss_out) {
+// Column sums in a fixed order, coalesced, in two passes.  Pass 1: block
+// (q, c) covers 32 consecutive columns of one source over row chunk c of
+// kColChunk rows; lane = column, the 8 warps take rows r0 + w, r0 + w + 8, ...
+// and their sums are added in warp order into colpart[c][...].  Sources:
+// q < 32: db_l = sum_rows z_bar_l (l = 1 + q/8); q < 40: dw5 = sum_rows
+// (g_bar_4 + h_4 out_bar); q == 40: db5 = sum out_bar (column 0) and the loss
+// (column 1).  Pass 2 adds the chunks in chunk order.
+constexpr int kColChunk = 128;
+constexpr int kColOut = 41 * 32;
+
+__global__ void __launch_bounds__(256) colsum_kernel(const Bufs b, float *colpart) {
     __shared__ float red[8][33];
-    const int q = blockIdx.x, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int B = b.B;
+    const int q = blockIdx.x, chunk = blockIdx.y, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int r0 = chunk * kColChunk, r1 = min(b.B, r0 + kColChunk);
     float s = 0.0f;
     if (q < 32) {
         const int l = 1 + q / 8, c = (q % 8) * 32 + lane;
-        for (int r = w; r < B; r += 8) s += b.zb[l][(long long)r * H + c];
+        for (int r = r0 + w; r < r1; r += 8) s += b.zb[l][(long long)r * H + c];
     } else if (q < 40) {
         const int c = (q - 32) * 32 + lane;
-        for (int r = w; r < B; r += 8)
+        for (int r = r0 + w; r < r1; r += 8)
             s += b.gb4f[(long long)r * H + c] + __bfloat162float(b.h[4][(long long)r * H + c]) * b.obar[r];
     } else if (lane < 2) {
-        for (int r = w; r < B; r += 8) s += lane == 0 ? b.obar[r] : b.loss_rows[r];
+        for (int r = r0 + w; r < r1; r += 8) s += lane == 0 ? b.obar[r] : b.loss_rows[r];
     }
     red[w][lane] = s;
     __syncthreads();
     if (w == 0) {
         float t = 0.0f;
         for (int k = 0; k < 8; ++k) t += red[k][lane];
+        colpart[(long long)chunk * kColOut + q * 32 + lane] = t;
+    }
+}
+
+__global__ void colsum_finish_kernel(const float *__restrict__ colpart, int n_chunks, float *grads, float *loss_out) {
+    for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < kColOut; o += gridDim.x * blockDim.x) {
+        float t = 0.0f;
+        for (int c = 0; c < n_chunks; ++c) t += colpart[(long long)c * kColOut + o];
+        const int q = o / 32, lane = o % 32;
         if (q < 32) grads[ob(1 + q / 8) + (q % 8) * 32 + lane] = t;
         else if (q < 40) grads[ow5 + (q - 32) * 32 + lane] = t;
         else if (lane == 0) grads[ob5] = t;
@@ -441,6 +456,7 @@ size_t layout(unsigned char *base, int B, Bufs *out) {
     b.Bop[1] = c.take<bf16>(NX * B2);
     for (int l = 2; l <= 4; ++l) b.Bop[l] = c.take<bf16>(H * B2);
     b.part = c.take<float>((size_t)kSplit * H * H);
+    b.colpart = c.take<float>((size_t)(B / 128) * 41 * 32);
     b.Wb[1] = c.take<bf16>((size_t)H * KX);
     b.Wt[1] = c.take<bf16>((size_t)NX * H);
     for (int l = 2; l <= 4; ++l) {
@@ -612,7 +628,9 @@ mc_status mlp_loss_grad(mlp_ctx *c, const float *params, const float *X, const f
         }
     }
     if (e == cudaSuccess) {
-        colsum_kernel<<<41, 256, 0, st>>>(b, grads, loss_out);
+        const int n_chunks = B / kColChunk;
+        colsum_kernel<<<dim3(41, n_chunks), 256, 0, st>>>(b, b.colpart);
+        colsum_finish_kernel<<<grid_for(kColOut), 256, 0, st>>>(b.colpart, n_chunks, grads, loss_out);
         e = cudaGetLastError();
     }
     return cuda_st(e, "mlp_loss_grad");
