@@ -49,3 +49,36 @@ def test_surrogate_assisted_calibration_beats_plain(trained):
             assert r["mc_phase"].G < 1e-8
     assert sum(sur_conv) >= 3
     assert np.median(sur_evals) < np.median(plain_evals)
+
+
+def test_gpu_calibration_matches_oracle_calibration(orc):
+    """Gauss-Newton-metric descent on the FP64 CUDA path (Jacobian from the
+    forward-mode kernel) and on the oracle (Jacobian from unit-seed vjps) both
+    recover theta* under common random numbers."""
+    from dataclasses import replace
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1901_04200_gb300 import _lib, calibrate
+    from paper_1901_04200_gb300 import build as b
+    b.build()
+    w = inputs.heston_config(n_paths=2048, steps_per_year=32, T=1.0, n_mat=4, n_strike=4)
+    n, seed = 2048, 99
+    pb = replace(w.problem, precision="fp64", seed=seed)
+    rng = np.random.default_rng(5)
+    theta_star, theta0 = inputs.draw_heston_theta(rng), inputs.draw_heston_theta(rng)
+    C = orc.forward(pb, theta_star, n, n_threads=4)
+    lo, hi = inputs.HESTON_RANGES["lo"], inputs.HESTON_RANGES["hi"]
+    ctx = _lib.Context(pb, max_paths=n)
+    jac_gpu = lambda th: ctx.price_jacobian(np.asarray(th)[None, :], seed, n)[1][0].cpu().numpy()
+    r_gpu = calibrate.descend_metric(calibrate.mc_objective(ctx, C, seed, n), jac_gpu, theta0, lo, hi, 1e-12,
+                                     max_evals=80)
+    eye = np.eye(pb.m)
+
+    def of(th):
+        _, G, g = orc.value_and_grad(pb, th, C, n, n_threads=4)
+        return G, g
+    jac_cpu = lambda th: np.stack([orc.vjp(pb, th, eye[i], n, n_threads=4) for i in range(pb.m)])
+    r_cpu = calibrate.descend_metric(of, jac_cpu, theta0, lo, hi, 1e-12, max_evals=80)
+    assert r_gpu.converged and r_cpu.converged
+    assert np.max(np.abs(r_gpu.theta - theta_star) / (hi - lo)) < 1e-4
+    assert np.max(np.abs(r_cpu.theta - theta_star) / (hi - lo)) < 1e-4
