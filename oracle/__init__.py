@@ -30,7 +30,7 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-KIND = {"gbm": 0, "heston": 1, "lv": 2}
+KIND = {"gbm": 0, "heston": 1, "lv": 2, "slv": 3}
 
 
 def build(force: bool = False) -> str:
@@ -117,7 +117,7 @@ class _Bound:
             be = arr(pb.bucket_end, np.int32)
             s.n_buckets = len(be)
             s.bucket_end = _iptr(be)
-        if pb.kind == "lv":
+        if pb.kind in ("lv", "slv"):
             s.nt, s.nx = int(pb.nt), int(pb.nx)
             s.t_max, s.x_lo, s.x_hi = float(pb.t_max), float(pb.x_lo), float(pb.x_hi)
         K = arr(pb.K, np.float64)

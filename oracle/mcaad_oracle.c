@@ -13,7 +13,10 @@
  *     (paper, Heston SLV model paragraph: "standard Euler discretization"):
  *       GBM with piecewise-constant volatility (log-Euler),
  *       Heston with full-truncation Euler,
- *       local volatility on a bilinear node surface (log-Euler);
+ *       local volatility on a bilinear node surface (log-Euler),
+ *       Heston stochastic local volatility (the paper's test model: the
+ *       Heston variance process times a leverage surface L(t, S) on fixed
+ *       nodes, interpolated bilinearly; full-truncation Euler);
  *     every state of a path is stored (no checkpointing);
  *   Monte Carlo mean E y_i = (1/P) sum_p y_i(omega_p) (paper, "Some remarks
  *     on the Monte-Carlo simulations");
@@ -118,8 +121,12 @@ void orc_normals_fill(uint64_t seed, uint64_t path0, uint32_t n_paths, uint32_t 
 
 /* ------------------------------------------------------- problem helpers */
 
-int orc_state_dim(const orc_problem *pb) { return pb->kind == ORC_HESTON_FT ? 2 : 1; }
-int orc_normals_per_step(const orc_problem *pb) { return pb->kind == ORC_HESTON_FT ? 2 : 1; }
+static int has_variance(const orc_problem *pb)
+{
+    return pb->kind == ORC_HESTON_FT || pb->kind == ORC_HESTON_SLV;
+}
+int orc_state_dim(const orc_problem *pb) { return has_variance(pb) ? 2 : 1; }
+int orc_normals_per_step(const orc_problem *pb) { return has_variance(pb) ? 2 : 1; }
 
 int orc_n_params(const orc_problem *pb)
 {
@@ -127,6 +134,7 @@ int orc_n_params(const orc_problem *pb)
     case ORC_GBM_PWC: return pb->n_buckets;
     case ORC_HESTON_FT: return 5;
     case ORC_LV_BILINEAR: return pb->nt * pb->nx;
+    case ORC_HESTON_SLV: return 5 + pb->nt * pb->nx;
     }
     return -1;
 }
@@ -142,7 +150,7 @@ int orc_last_step(const orc_problem *pb)
 
 int orc_check(const orc_problem *pb, const double *theta)
 {
-    if (pb->kind < 0 || pb->kind > 2) return ORC_ERR;
+    if (pb->kind < 0 || pb->kind > 3) return ORC_ERR;
     if (pb->m < 1 || pb->n_steps < 1 || !(pb->dt > 0.0)) return ORC_ERR;
     for (int i = 0; i < pb->m; ++i)
         if (pb->mat_step[i] < 1 || pb->mat_step[i] > pb->n_steps) return ORC_ERR;
@@ -154,10 +162,10 @@ int orc_check(const orc_problem *pb, const double *theta)
         }
         if (pb->bucket_end[pb->n_buckets - 1] < orc_last_step(pb)) return ORC_ERR;
     }
-    if (pb->kind == ORC_HESTON_FT && theta) {
+    if (has_variance(pb) && theta) {
         if (!(fabs(theta[3]) < 1.0)) return ORC_ERR;
     }
-    if (pb->kind == ORC_LV_BILINEAR) {
+    if (pb->kind == ORC_LV_BILINEAR || pb->kind == ORC_HESTON_SLV) {
         if (pb->nt < 2 || pb->nx < 2 || !(pb->t_max > 0.0) || !(pb->x_hi > pb->x_lo)) return ORC_ERR;
     }
     return ORC_OK;
@@ -236,7 +244,7 @@ int orc_path_forward(const orc_problem *pb, const double *theta, uint64_t p,
     int sd = orc_state_dim(pb), dz = orc_normals_per_step(pb);
     double dt = pb->dt, sdt = sqrt(pb->dt), r = pb->r;
     states[0] = 0.0;
-    if (pb->kind == ORC_HESTON_FT) states[1] = theta[4];
+    if (has_variance(pb)) states[1] = theta[4];
     for (int n = 0; n < nl; ++n) {
         for (int c = 0; c < dz; ++c) z[n * dz + c] = path_normal(pb, p, (uint64_t)n * dz + c);
         const double *s = states + (size_t)n * sd;
@@ -252,6 +260,16 @@ int orc_path_forward(const orc_problem *pb, const double *theta, uint64_t p,
             double z1 = z[2 * n], z2 = z[2 * n + 1];
             double w = rho * z1 + sqrt(1.0 - rho * rho) * z2;
             s1[0] = x + (r - 0.5 * vp) * dt + sq * z1;
+            s1[1] = v + kappa * (th - vp) * dt + xi * sq * w;
+        } else if (pb->kind == ORC_HESTON_SLV) {
+            double kappa = theta[0], th = theta[1], xi = theta[2], rho = theta[3];
+            double x = s[0], v = s[1];
+            double vp = v > 0.0 ? v : 0.0;
+            double sq = sqrt(vp * dt);
+            double lev = lv_sigma(pb, theta + 5, n, x).sigma;
+            double z1 = z[2 * n], z2 = z[2 * n + 1];
+            double w = rho * z1 + sqrt(1.0 - rho * rho) * z2;
+            s1[0] = x + (r - 0.5 * lev * lev * vp) * dt + lev * sq * z1;
             s1[1] = v + kappa * (th - vp) * dt + xi * sq * w;
         } else {
             lv_eval e = lv_sigma(pb, theta, n, s[0]);
@@ -315,6 +333,27 @@ int orc_path_adjoint(const orc_problem *pb, const double *theta, const double *s
             double vb_new = vb + (v > 0.0 ? vpb : 0.0);
             vb = vb_new;
             /* xb unchanged: x_k enters x_n with coefficient 1 */
+        } else if (pb->kind == ORC_HESTON_SLV) {
+            double kappa = theta[0], th = theta[1], xi = theta[2], rho = theta[3];
+            double v = s[1];
+            double vp = v > 0.0 ? v : 0.0;
+            double sq = sqrt(vp * dt);
+            lv_eval e = lv_sigma(pb, theta + 5, k, s[0]);
+            double lev = e.sigma;
+            double z1 = z[2 * k], z2 = z[2 * k + 1];
+            double rhob = sqrt(1.0 - rho * rho);
+            double w = rho * z1 + rhob * z2;
+            /* leverage: x_n depends on lev through -lev^2 vp dt / 2 + lev sq z1 */
+            double levb = xb * (-lev * vp * dt + sq * z1);
+            for (int q = 0; q < 4; ++q) g[5 + e.node[q]] += levb * e.wgt[q];
+            g[0] += vb * (th - vp) * dt;
+            g[1] += vb * kappa * dt;
+            g[2] += vb * sq * w;
+            g[3] += vb * xi * sq * (z1 - rho / rhob * z2);
+            double vpb = xb * (-0.5 * lev * lev * dt) + vb * (-kappa * dt);
+            if (vp > 0.0) vpb += (xb * lev * z1 + vb * xi * w) * dt / (2.0 * sq);
+            vb = vb + (v > 0.0 ? vpb : 0.0);
+            xb = xb + levb * e.dsdx;
         } else {
             lv_eval e = lv_sigma(pb, theta, k, s[0]);
             double sb = xb * (-e.sigma * dt + sdt * z[k]);
@@ -322,7 +361,7 @@ int orc_path_adjoint(const orc_problem *pb, const double *theta, const double *s
             xb = xb + sb * e.dsdx;
         }
     }
-    if (pb->kind == ORC_HESTON_FT) g[4] += vb;
+    if (has_variance(pb)) g[4] += vb;
     return ORC_OK;
 }
 

@@ -13,7 +13,7 @@ extern "C" {
 #endif
 
 enum { ORC_OK = 0, ORC_ERR = 1 };
-enum { ORC_GBM_PWC = 0, ORC_HESTON_FT = 1, ORC_LV_BILINEAR = 2 };
+enum { ORC_GBM_PWC = 0, ORC_HESTON_FT = 1, ORC_LV_BILINEAR = 2, ORC_HESTON_SLV = 3 };
 
 /* One calibration problem.  All arrays are host memory owned by the caller.
  * State x = ln(S/S0) starts at 0; Heston's v starts at theta[4].
@@ -22,6 +22,8 @@ enum { ORC_GBM_PWC = 0, ORC_HESTON_FT = 1, ORC_LV_BILINEAR = 2 };
  *   HESTON_FT:    theta = (kappa, theta_h, xi, rho, v0).
  *   LV_BILINEAR:  theta[j*nx + c] = sigma at time t_j = j*t_max/(nt-1) and
  *                 log-moneyness x_c = x_lo + c*(x_hi-x_lo)/(nx-1).
+ *   HESTON_SLV:   theta = (kappa, theta_h, xi, rho, v0, L[0..nt*nx)) with the
+ *                 leverage L on the same node grid as LV_BILINEAR.
  * Instrument i is a call with strike K[i] paying at step mat_step[i]
  * (time mat_step[i]*dt), discounted at rate r.
  * normals: optional [P][n_steps*normals_per_step] table for global paths

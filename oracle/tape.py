@@ -135,10 +135,27 @@ def full_tape_value_and_grad(pb, theta, C, normals):
     last = int(np.max(pb.mat_step))
     x = T.const(0.0)
     states = [x]
-    if pb.kind == "heston":
-        kappa, thh, xi, rho, v0 = th
+    if pb.kind in ("heston", "slv"):
+        kappa, thh, xi, rho, v0 = th[:5]
         v = v0 * 1.0
         rhob = sqrt(1.0 - rho * rho)
+
+    def surface(nodes, xv, n):
+        """Bilinear node surface at (t_n, x) as a sum of tensor-product hat functions."""
+        nt, nx = int(pb.nt), int(pb.nx)
+        ht = pb.t_max / (nt - 1)
+        hx = (pb.x_hi - pb.x_lo) / (nx - 1)
+        ut = min(max(n * dt / ht, 0.0), nt - 1.0)
+        ux = clamp((xv - pb.x_lo) * (1.0 / hx), 0.0, nx - 1.0)
+        acc = None
+        for j in range(nt):
+            wt = max(0.0, 1.0 - abs(ut - j))
+            if wt == 0.0:
+                continue
+            for c in range(nx):
+                term = nodes[j * nx + c] * relu(1.0 - absv(ux - float(c))) * wt
+                acc = term if acc is None else acc + term
+        return acc
     for n in range(last):
         if pb.kind == "gbm":
             b = int(np.searchsorted(np.asarray(pb.bucket_end), n, side="right"))
@@ -154,21 +171,18 @@ def full_tape_value_and_grad(pb, theta, C, normals):
             x_new = x + (r - 0.5 * vp) * dt + sq * z1
             v = v + kappa * (thh - vp) * dt + xi * sq * w
             x = x_new
+        elif pb.kind == "slv":
+            z1 = T.const(normals[:, 2 * n])
+            z2 = T.const(normals[:, 2 * n + 1])
+            lev = surface(th[5:], x, n)
+            vp = relu(v)
+            sq = sqrt(vp * dt)
+            w = rho * z1 + rhob * z2
+            x_new = x + (r - 0.5 * lev * lev * vp) * dt + lev * sq * z1
+            v = v + kappa * (thh - vp) * dt + xi * sq * w
+            x = x_new
         else:
-            nt, nx = int(pb.nt), int(pb.nx)
-            ht = pb.t_max / (nt - 1)
-            hx = (pb.x_hi - pb.x_lo) / (nx - 1)
-            ut = min(max(n * dt / ht, 0.0), nt - 1.0)
-            ux = clamp((x - pb.x_lo) * (1.0 / hx), 0.0, nx - 1.0)
-            sigma = None
-            for j in range(nt):
-                wt = max(0.0, 1.0 - abs(ut - j))
-                if wt == 0.0:
-                    continue
-                for c in range(nx):
-                    hat = relu(1.0 - absv(ux - float(c)))
-                    term = th[j * nx + c] * hat * wt
-                    sigma = term if sigma is None else sigma + term
+            sigma = surface(th, x, n)
             z = T.const(normals[:, n])
             x = x + (r - 0.5 * sigma * sigma) * dt + sigma * sdt * z
         states.append(x)

@@ -78,11 +78,13 @@ class Problem:
             return len(self.bucket_end)
         if self.kind == "heston":
             return 5
+        if self.kind == "slv":
+            return 5 + self.nt * self.nx
         return self.nt * self.nx
 
     @property
     def normals_per_step(self) -> int:
-        return 2 if self.kind == "heston" else 1
+        return 2 if self.kind in ("heston", "slv") else 1
 
     @property
     def last_step(self) -> int:
@@ -194,6 +196,20 @@ def lv_config(n_paths: int = 1 << 22, n_steps: int = 500, T: float = 5.0, nt: in
                  seed=seed, nt=nt, nx=nx, t_max=T, x_lo=-1.0, x_hi=1.0,
                  precision="fp32", ckpt_every=ckpt_every)
     return Workload("lv_bilinear_m200_s500_fp32", pb, theta, C, n_paths, {"hidden_vol": hidden})
+
+
+def slv_config(n_paths: int = 1 << 20, steps_per_year: int = 256, T: float = 2.0, n_mat: int = 8,
+               n_strike: int = 8, nt: int = 9, nx: int = 10, seed: int = PHILOX_SEED,
+               ckpt_every: int = 8) -> Workload:
+    """Heston stochastic local volatility (the paper's test model): Heston parameters drawn as in
+    heston_config and a leverage surface L(t, x) on nt x nx nodes (t_j = j T/(nt-1), x in [-1, 1]),
+    values U(0.8, 1.2); parameters (kappa, theta_h, xi, rho, v0, L...)."""
+    w = heston_config(n_paths=n_paths, steps_per_year=steps_per_year, T=T, n_mat=n_mat, n_strike=n_strike,
+                      seed=seed, ckpt_every=ckpt_every)
+    lev = np.random.default_rng(SEED_PARAMS + 1).uniform(0.8, 1.2, nt * nx)
+    pb = replace(w.problem, kind="slv", nt=nt, nx=nx, t_max=T, x_lo=-1.0, x_hi=1.0)
+    theta = np.concatenate([w.theta, lev])
+    return Workload("heston_slv_m%d_s%d_fp32" % (pb.m, pb.n_steps), pb, theta, w.C, n_paths, w.extra)
 
 
 def with_paths(w: Workload, n_paths: int) -> Workload:

@@ -298,3 +298,65 @@ def test_paper_cost_table_satisfies_eq_0711C():
     for row in tab["rows"]:
         total = 2 * row["KF_over_c"] + row["KR_over_c"]
         assert abs(total - row["cost_G_over_paths_costF"]) <= 0.005 + 1e-12, row
+
+
+# ------------------------------------------------------- Heston SLV (paper's model)
+
+def slv_small(P=16, nt=3, nx=4):
+    return inputs.slv_config(n_paths=P, steps_per_year=4, T=1.0, n_mat=2, n_strike=3, nt=nt, nx=nx)
+
+
+def test_slv_two_step_equals_full_tape(orc):
+    from oracle import tape
+    w = slv_small()
+    pb, P = w.problem, 16
+    Z = orc.normals_fill(pb.seed, 0, P, pb.n_steps * 2)
+    _, G, g = orc.value_and_grad(pb, w.theta, w.C, P)
+    Gt, gt = tape.full_tape_value_and_grad(pb, w.theta, w.C, Z)
+    assert math.isclose(G, Gt, rel_tol=1e-13)
+    assert np.max(np.abs(g - gt)) <= 1e-13 * np.max(np.abs(gt))
+
+
+def test_slv_with_unit_leverage_is_heston(orc):
+    """L = 1 everywhere gives exactly the Heston prices and Heston-parameter gradient."""
+    w = inputs.slv_config(n_paths=512, steps_per_year=32, T=1.0, n_mat=4, n_strike=4)
+    pb = w.problem
+    th = w.theta.copy()
+    th[5:] = 1.0
+    wh = inputs.heston_config(n_paths=512, steps_per_year=32, T=1.0, n_mat=4, n_strike=4)
+    Ey_s, G_s, g_s = orc.value_and_grad(pb, th, w.C, 512)
+    Ey_h, G_h, g_h = orc.value_and_grad(wh.problem, th[:5], w.C, 512)
+    assert np.array_equal(Ey_s, Ey_h) and G_s == G_h
+    assert np.allclose(g_s[:5], g_h, rtol=1e-12, atol=1e-12 * np.max(np.abs(g_h)))
+
+
+def test_slv_leverage_gradient_against_global_scale(orc):
+    """d E y_i / d c of E y_i(L = c L0) at c = 1 equals sum_nodes L0 * dE y_i/dL (bilinear
+    weights sum to one), by central differences with common random numbers."""
+    w = inputs.slv_config(n_paths=2048, steps_per_year=32, T=1.0, n_mat=4, n_strike=4)
+    pb, n = w.problem, 2048
+    e = np.zeros(pb.m)
+    e[9] = 1.0
+    g = orc.vjp(pb, w.theta, e, n)
+    h = 1e-6
+    tp, tm = w.theta.copy(), w.theta.copy()
+    tp[5:] *= 1 + h
+    tm[5:] *= 1 - h
+    fd = (orc.forward(pb, tp, n)[9] - orc.forward(pb, tm, n)[9]) / (2 * h)
+    assert abs(fd - np.dot(w.theta[5:], g[5:])) <= 1e-6 * max(1.0, abs(fd))
+
+
+def test_slv_fd_and_martingale(orc):
+    w = inputs.slv_config(n_paths=1024, steps_per_year=32, T=1.0, n_mat=4, n_strike=4, nt=5, nx=6)
+    pb, n = w.problem, 1024
+    _, G, g = orc.value_and_grad(pb, w.theta, w.C, n)
+    for j in [0, 1, 2, 3, 4, 5, 12, 20, 33]:
+        hh = 1e-6 * max(1.0, abs(w.theta[j]))
+        tp, tm = w.theta.copy(), w.theta.copy()
+        tp[j] += hh
+        tm[j] -= hh
+        fd = (orc.value_and_grad(pb, tp, w.C, n)[1] - orc.value_and_grad(pb, tm, w.C, n)[1]) / (2 * hh)
+        assert abs(fd - g[j]) <= 1e-5 * np.max(np.abs(g)) + 1e-9, (j, fd, g[j])
+    pb0 = replace(pb, K=np.zeros(pb.m))
+    Ey, se = batched(lambda p0, k: orc.forward(pb0, w.theta, k, path0=p0), 1 << 15)
+    assert np.all(np.abs(Ey - pb.S0) < 5 * se)
