@@ -51,7 +51,12 @@ OPS = {"heston": {"forward_sweep": {"fp32": 22, "mufu": 5, "int": 24},
        # adjoint: cell and lerp again 12 FP32, sigma-bar and weights 6, four row-adjoint FMAs 4,
        # d sigma/dx term 2 (shared-memory loads and stores not counted)
        "lv": {"forward_sweep": {"fp32": 21, "mufu": 2, "int": 12},
-              "reverse_sweep": {"fp32": 45, "mufu": 2, "int": 12}}}
+              "reverse_sweep": {"fp32": 45, "mufu": 2, "int": 12}},
+       # Heston SLV: the Heston step plus the leverage lookup (cell, clamp, lerp: 10) and
+       # L^2 vdt, L sq (2) in F; in R the lookup again (10), L-bar and weights (4), four
+       # row-adjoint FMAs (4), the extra L factors of the Heston adjoint (3) and dL/dx (2)
+       "slv": {"forward_sweep": {"fp32": 34, "mufu": 5, "int": 24},
+               "reverse_sweep": {"fp32": 74, "mufu": 5, "int": 24}}}
 
 
 def _ops(model, kernel):
@@ -323,7 +328,7 @@ def main():
     ap.add_argument("--ref-paths", type=int, default=1 << 15)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ppt", type=int, default=0, help="paths per GPU thread (0 = library default)")
-    ap.add_argument("--workload", default="heston", choices=["heston", "lv", "surrogate"],
+    ap.add_argument("--workload", default="heston", choices=["heston", "lv", "slv", "surrogate"],
                     help="heston (the metric's workload), lv (2^22 x 500 local vol) or surrogate "
                          "(one differential-loss training step of the pricing network), for measurement")
     ap.add_argument("--no-calibration", action="store_true", help="skip the surrogate vs plain calibration")
@@ -347,6 +352,8 @@ def main():
         return surrogate_step_bench(args, rank, world)
     if args.workload == "lv":
         w = inputs.lv_config(n_paths=args.paths if args.paths != (1 << 20) else (1 << 22))
+    elif args.workload == "slv":
+        w = inputs.slv_config(n_paths=args.paths)
     else:
         w = inputs.heston_config(n_paths=args.paths)
     if args.ppt or args.ckpt:
@@ -439,8 +446,10 @@ def main():
 
     if rank == 0:
         line = {
-            "metric": METRIC if model == "heston" else METRIC.replace("Heston FT, 2^20 paths x 512 steps, m=64, M=5",
-                                                                      "local vol, 2^22 paths x 500 steps, m=200, M=200"),
+            "metric": METRIC if model == "heston" else METRIC.replace(
+                "Heston FT, 2^20 paths x 512 steps, m=64, M=5",
+                "local vol, 2^22 paths x 500 steps, m=200, M=200" if model == "lv" else
+                "Heston SLV, 2^20 paths x 512 steps, m=64, M=95"),
             "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": ms_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -448,12 +457,12 @@ def main():
                        "ckpt_every": pb.ckpt_every, "paths_per_thread": pb.paths_per_thread or "default",
                        "precision": "fp32 paths, fp64 sums",
                        "l2": "inputs larger than L2: checkpoints %.0f MB per step" %
-                             (P * (S // pb.ckpt_every) * (2 if model == "heston" else 1) * 4 / 1e6)},
+                             (P * (S // pb.ckpt_every) * (1 if model == "lv" else 2) * 4 / 1e6)},
             "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": issue_peak / 1e12,
                          "unit": "Tops/s", "frac": achieved / issue_peak,
                          "traffic": measured_traffic(model, pb.ckpt_every, pb.paths_per_thread or
                                                      (2 if model == "heston" else 1)),
-                         "algorithmic_bytes": P * (S // pb.ckpt_every) * (2 if model == "heston" else 1) * 4,
+                         "algorithmic_bytes": P * (S // pb.ckpt_every) * (1 if model == "lv" else 2) * 4,
                          "kernel": "path_reverse_kernel<%s,f32,K=%d>" % (model, pb.ckpt_every),
                          "ops_per_path_step": _ops(model, "reverse_sweep"),
                          "peak_basis": "SM issue rate 128 thread-ops/clk x %d SMs x %.0f MHz (%s max clock)"

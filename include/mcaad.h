@@ -60,7 +60,8 @@ typedef enum {
 typedef enum {
     MC_MODEL_GBM_PWC = 0,     /* GBM, piecewise-constant vol, log-Euler       */
     MC_MODEL_HESTON_FT = 1,   /* Heston, full-truncation Euler                */
-    MC_MODEL_LV_BILINEAR = 2  /* local vol, bilinear node surface, log-Euler  */
+    MC_MODEL_LV_BILINEAR = 2, /* local vol, bilinear node surface, log-Euler  */
+    MC_MODEL_HESTON_SLV = 3   /* Heston stochastic local vol (leverage surface) */
 } mc_model_kind;
 
 typedef enum { MC_FP64 = 0, MC_FP32 = 1 } mc_precision;
@@ -80,6 +81,10 @@ typedef enum { MC_FP64 = 0, MC_FP32 = 1 } mc_precision;
  *                x_c = x_lo + c (x_hi-x_lo)/(nx-1); sigma(t_n, x_n) bilinear
  *                with flat extrapolation;
  *                x += (r - sigma^2/2) dt + sigma sqrt(dt) z_n.           M = nt*nx
+ *   HESTON_SLV:  theta = (kappa, theta_h, xi, rho, v0, L[j*nx + c]): the
+ *                paper's test model (Heston SLV test paragraph); leverage L
+ *                on the LV node grid, bilinear; v as HESTON_FT and
+ *                x += (r - L^2 v+/2) dt + L sqrt(v+ dt) z1.         M = 5 + nt*nx
  * ckpt_every: checkpoint interval k of the reverse sweep (0 = library
  * default); it must divide every maturity step.
  * paths_per_thread: 1 or 2 independent paths per GPU thread (0 = library

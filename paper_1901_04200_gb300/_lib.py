@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_PKG, "libmcaad.so")
 
 MC_OK, MC_ERR_INVALID_ARG, MC_ERR_CUDA, MC_ERR_OOM, MC_ERR_UNSUPPORTED, MC_ERR_STATE = range(6)
 MC_FP64, MC_FP32 = 0, 1
-KIND = {"gbm": 0, "heston": 1, "lv": 2}
+KIND = {"gbm": 0, "heston": 1, "lv": 2, "slv": 3}
 _STATUS = {1: "MC_ERR_INVALID_ARG", 2: "MC_ERR_CUDA", 3: "MC_ERR_OOM", 4: "MC_ERR_UNSUPPORTED",
            5: "MC_ERR_STATE"}
 
@@ -139,7 +139,7 @@ class _ProblemC:
             self.keep.append(be)
             md.n_buckets = len(be)
             md.bucket_end_host = be.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
-        if pb.kind == "lv":
+        if pb.kind in ("lv", "slv"):
             md.nt, md.nx = int(pb.nt), int(pb.nx)
             md.t_max, md.x_lo, md.x_hi = float(pb.t_max), float(pb.x_lo), float(pb.x_hi)
         if pb.normals is not None:

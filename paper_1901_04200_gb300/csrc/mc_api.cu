@@ -76,6 +76,7 @@ int model_params(const mc_model *md) {
     case MC_MODEL_GBM_PWC: return md->n_buckets;
     case MC_MODEL_HESTON_FT: return 5;
     case MC_MODEL_LV_BILINEAR: return md->nt * md->nx;
+    case MC_MODEL_HESTON_SLV: return 5 + md->nt * md->nx;
     }
     return -1;
 }
@@ -85,6 +86,7 @@ bool kernels_raw(int kind, int precision, int K, int ppt, KernelPair *kp) {
     case kGbm: return gbm_kernels(precision, K, ppt, kp);
     case kHeston: return heston_kernels(precision, K, ppt, kp);
     case kLv: return lv_kernels(precision, K, ppt, kp);
+    case kSlv: return slv_kernels(precision, K, ppt, kp);
     }
     return false;
 }
@@ -111,7 +113,7 @@ mc_status make_plan(const mc_model *md, const mc_instruments *in, Plan &p, std::
         return MC_ERR_INVALID_ARG;
     };
     if (!md || !in) return bad("null model or instruments");
-    if (md->kind < 0 || md->kind > 2) return bad("unknown model kind");
+    if (md->kind < 0 || md->kind > 3) return bad("unknown model kind");
     if (md->precision != MC_FP32 && md->precision != MC_FP64) return bad("unknown precision");
     if (!(md->S0 > 0.0) || !(md->dt > 0.0) || !std::isfinite(md->r)) return bad("need S0 > 0, dt > 0, finite r");
     if (md->n_steps < 1) return bad("n_steps must be >= 1");
@@ -122,7 +124,8 @@ mc_status make_plan(const mc_model *md, const mc_instruments *in, Plan &p, std::
     p.m = in->m;
     p.M = model_params(md);
     if (p.M < 1 || p.M > kMaxParams) return bad("parameter count out of range [1, 256]");
-    p.state_dim = md->kind == MC_MODEL_HESTON_FT ? 2 : 1;
+    const bool lv_grid = md->kind == MC_MODEL_LV_BILINEAR || md->kind == MC_MODEL_HESTON_SLV;
+    p.state_dim = (md->kind == MC_MODEL_HESTON_FT || md->kind == MC_MODEL_HESTON_SLV) ? 2 : 1;
     int n_last = 0, g = 0;
     for (int i = 0; i < in->m; ++i) {
         const int s = in->mat_step_host[i];
@@ -142,7 +145,7 @@ mc_status make_plan(const mc_model *md, const mc_instruments *in, Plan &p, std::
     } else if (md->normals) {
         return bad("a normals table is supported for GBM only");
     }
-    if (md->kind == MC_MODEL_LV_BILINEAR) {
+    if (lv_grid) {
         if (md->nt < 2 || md->nx < 2 || !(md->t_max > 0.0) || !(md->x_hi > md->x_lo))
             return bad("LV needs nt, nx >= 2, t_max > 0, x_hi > x_lo");
         if (md->nx > 32) return bad("LV needs nx <= 32");
@@ -150,8 +153,9 @@ mc_status make_plan(const mc_model *md, const mc_instruments *in, Plan &p, std::
     if (md->paths_per_thread < 0 || md->paths_per_thread > 2) return bad("paths_per_thread must be 0, 1 or 2");
     p.ppt = md->paths_per_thread ? md->paths_per_thread : default_ppt(md->kind, md->precision);
     // segment length: must divide every maturity step
-    const int *ks = md->kind == MC_MODEL_GBM_PWC ? kGbmK : md->kind == MC_MODEL_HESTON_FT ? kHestonK : kLvK;
-    const int nk = md->kind == MC_MODEL_GBM_PWC ? 5 : md->kind == MC_MODEL_HESTON_FT ? 4 : 3;
+    const bool hs_k = md->kind == MC_MODEL_HESTON_FT || md->kind == MC_MODEL_HESTON_SLV;
+    const int *ks = md->kind == MC_MODEL_GBM_PWC ? kGbmK : hs_k ? kHestonK : kLvK;
+    const int nk = md->kind == MC_MODEL_GBM_PWC ? 5 : hs_k ? 4 : 3;
     KernelPair probe;
     p.K = 0;
     if (md->ckpt_every > 0) {
@@ -210,7 +214,7 @@ mc_status make_plan(const mc_model *md, const mc_instruments *in, Plan &p, std::
             p.bucket[n] = b;
         }
     }
-    if (md->kind == MC_MODEL_LV_BILINEAR) {
+    if (lv_grid) {
         // time cell and weight of step n, in FP64 as u_t = (n dt) / (t_max / (nt - 1))
         const double ht = md->t_max / (double)(md->nt - 1);
         p.lv_jt.resize(n_last);
@@ -472,7 +476,7 @@ mc_status mc_context_create(int device, const mc_model *model, const mc_instrume
     pb.normals = model->normals;
     pb.normals_path0 = model->normals_path0;
     pb.normals_rows = model->normals_rows;
-    pb.normals_stride = model->n_steps * (p.kind == kHeston ? 2 : 1);
+    pb.normals_stride = model->n_steps * (p.state_dim == 2 ? 2 : 1);
     *out = ctx;
     return MC_OK;
 }
@@ -831,7 +835,7 @@ extern "C" mc_status mc_forward_static(const mc_model *model, const mc_instrumen
     pb.normals = model->normals;
     pb.normals_path0 = model->normals_path0;
     pb.normals_rows = model->normals_rows;
-    pb.normals_stride = model->n_steps * (p.kind == kHeston ? 2 : 1);
+    pb.normals_stride = model->n_steps * (p.state_dim == 2 ? 2 : 1);
     DevCall cl{};
     cl.theta = theta;
     cl.seed = seed;

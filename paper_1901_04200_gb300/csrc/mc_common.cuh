@@ -107,7 +107,7 @@ __device__ __forceinline__ T warp_sum(T v) {
 
 // ----------------------------------------------------------- parameters ----
 
-enum ModelKind { kGbm = 0, kHeston = 1, kLv = 2 };
+enum ModelKind { kGbm = 0, kHeston = 1, kLv = 2, kSlv = 3 };
 
 // Problem tables fixed at context creation (device pointers into the
 // context's workspace).  Instruments are kept sorted by maturity; maturity
@@ -126,8 +126,8 @@ struct DevProblem {
     const int *grp_seg;         // [n_groups]
     const int *grp_begin;       // [n_groups + 1]
     const int *bucket_of_step;  // GBM [n_seg * K]
-    const int *lv_jt;           // LV   [n_seg * K] time cell of step n
-    const double *lv_a;         // LV   [n_seg * K] time weight of step n
+    const int *lv_jt;           // LV/SLV [n_seg * K] time cell of step n
+    const double *lv_a;         // LV/SLV [n_seg * K] time weight of step n
     int nt, nx;
     double x_lo, hx;
     const double *normals;      // optional GBM table

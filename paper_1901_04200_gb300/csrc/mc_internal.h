@@ -18,6 +18,7 @@ struct KernelPair {
 bool gbm_kernels(int precision, int K, int ppt, KernelPair *out);
 bool heston_kernels(int precision, int K, int ppt, KernelPair *out);
 bool lv_kernels(int precision, int K, int ppt, KernelPair *out);
+bool slv_kernels(int precision, int K, int ppt, KernelPair *out);
 
 // Small kernels (mc_aux.cu).
 cudaError_t launch_finalize_forward(const double *part_y, int nb, int m, double inv_n,

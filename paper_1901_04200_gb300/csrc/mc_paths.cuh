@@ -71,7 +71,7 @@ struct SmemPlan {
             o += (size_t)M * real_bytes;
             o = align_up(o, 16);
             o += (size_t)n_steps * 4;
-        } else if (kind == kLv) {
+        } else if (kind == kLv || kind == kSlv) {
             o += (size_t)n_steps * nx * real_bytes;  // time-interpolated node rows
             o = align_up(o, 16);
             o += (size_t)n_steps * real_bytes;       // time weight a_n
@@ -377,6 +377,112 @@ struct LvModel {
     }
     __device__ static void acc_end(Acc &a, Real, const Par &, const Shared &sh, double *wacc, int lane) {
         flush_rows(a, sh, wacc, lane);
+    }
+};
+
+// Heston stochastic local volatility (the paper's test model): the Heston
+// variance process with full truncation, and x driven by sqrt(v+) times a
+// leverage L(t_n, x_n) interpolated bilinearly on fixed nodes;
+// theta = (kappa, theta_h, xi, rho, v0, L[j*nx + c]).  Per step:
+//   x += (r dt - L^2 vdt / 2) + L sq z1,  v as HestonModel.
+// The leverage surface reuses LvModel's tables, cell logic and per-thread row
+// adjoints (node j*nx + c is parameter 5 + j*nx + c).
+template <typename Real_>
+struct SlvModel {
+    using Real = Real_;
+    using Lv = LvModel<Real_>;
+    using Hs = HestonModel<Real_>;
+    static constexpr int kind = kSlv;
+    static constexpr int DZ = 2, SD = 2;
+    struct State { Real x, v; };
+    struct Tape { Real u, vdt, rs, z1, w; };
+    using Shared = typename Lv::Shared;
+    struct Par {
+        typename Hs::Par h;
+        typename Lv::Par l;
+    };
+    struct Acc {
+        typename Hs::Acc h;
+        typename Lv::Acc l;
+    };
+
+    __device__ static void setup(unsigned char *base, const SmemPlan &sp, const DevProblem &pb,
+                                 const double *theta, int n_steps, Shared &sh, Par &par) {
+        typename Hs::Shared hs;
+        Hs::setup(base, sp, pb, theta, n_steps, hs, par.h);
+        Lv::setup(base, sp, pb, theta + 5, n_steps, sh, par.l);
+    }
+    __device__ static State init(const Par &p) { return State{Real(0), p.h.v0}; }
+    __device__ __forceinline__ static void step(State &s, const Real *z, int n, const Par &p,
+                                                const Shared &sh, Tape *t) {
+        const Real u = (s.x - p.l.x_lo) * p.l.inv_hx;
+        int c;
+        Real b;
+        bool inside;
+        Lv::cell(u, p.l, c, b, inside);
+        const Real *rw = sh.row + n * sh.nx;
+        const Real s0 = rw[c], s1 = rw[c + 1];
+        const Real lev = fma(b, s1 - s0, s0);
+        const Real vdt = fmax(s.v, Real(0)) * p.h.dt;
+        const Real rs = rsqrt_r<Real>(fmax(vdt, tiny_r<Real>()));
+        const Real sq = vdt * rs;
+        const Real z1 = z[0];
+        const Real w = fma(p.h.rho, z1, p.h.rhob * z[1]);
+        s.x = s.x + fma(lev * sq, z1, fma(Real(-0.5) * lev * lev, vdt, p.h.rdt));
+        s.v = s.v + fma(p.h.xi * sq, w, fma(-p.h.kappa, vdt, p.h.kthdt));
+        if (t) {
+            t->u = u;
+            t->vdt = vdt;
+            t->rs = rs;
+            t->z1 = z1;
+            t->w = w;
+        }
+    }
+    __device__ static void acc_begin(Acc &a, int n_last, const Shared &sh) {
+        Hs::acc_begin(a.h, n_last, typename Hs::Shared{});
+        Lv::acc_begin(a.l, n_last, sh);
+    }
+    // Leverage rows flush into parameters 5 + node.
+    __device__ __forceinline__ static void boundary(Acc &a, int n, const Shared &sh, double *wacc, int lane) {
+        Lv::boundary(a.l, n, sh, wacc + 5, lane);
+    }
+    // Adjoint of one step given xb, vb of the state after it:
+    //   L-bar = xb (sq z1 - L vdt) -> bilinear node weights (time weight a_n),
+    //   Heston parameter sums as HestonModel with d x/d sq = L z1,
+    //   vdt-bar = -xb L^2/2 - kappa vb + (xb L z1 + xi vb w) / (2 sq),
+    //   vb_prev = vb + 1{v > 0} dt vdt-bar,  xb_prev = xb + L-bar dL/dx.
+    __device__ __forceinline__ static void adjoint(const Tape &t, int n, Real &xb, Real &vb, Acc &a,
+                                                   const Par &p, const Shared &sh) {
+        int c;
+        Real b;
+        bool inside;
+        Lv::cell(t.u, p.l, c, b, inside);
+        const Real *rw = sh.row + n * sh.nx;
+        const Real s0 = rw[c], s1 = rw[c + 1];
+        const Real ds = s1 - s0;
+        const Real lev = fma(b, ds, s0);
+        const Real sq = t.vdt * t.rs;
+        const Real lb = xb * fma(sq, t.z1, -lev * t.vdt);
+        const Real at = sh.a[n];
+        const Real g1 = lb * b, g0 = lb - g1;
+        Real *r = sh.racc + threadIdx.x;
+        r[(2 * c) * kBlock] = fma(Real(1) - at, g0, r[(2 * c) * kBlock]);
+        r[(2 * c + 1) * kBlock] = fma(at, g0, r[(2 * c + 1) * kBlock]);
+        r[(2 * c + 2) * kBlock] = fma(Real(1) - at, g1, r[(2 * c + 2) * kBlock]);
+        r[(2 * c + 3) * kBlock] = fma(at, g1, r[(2 * c + 3) * kBlock]);
+        const Real vsq = vb * sq;
+        a.h.a = fma(vsq, t.z1, a.h.a);
+        a.h.b = fma(vsq, t.w, a.h.b);
+        a.h.cs += vb;
+        a.h.kb = fma(vb, p.h.thh * p.h.dt - t.vdt, a.h.kb);
+        const Real sqb = fma(xb * lev, t.z1, p.h.xi * vb * t.w);
+        const Real vdtb = fma(Real(0.5) * t.rs, sqb, fma(Real(-0.5) * lev * lev, xb, -p.h.kappa * vb));
+        vb = (t.vdt > Real(0)) ? fma(vdtb, p.h.dt, vb) : vb;
+        if (inside) xb = fma(lb * p.l.inv_hx, ds, xb);
+    }
+    __device__ static void acc_end(Acc &a, Real vb_sum, const Par &p, const Shared &sh, double *wacc, int lane) {
+        Hs::acc_end(a.h, vb_sum, p.h, typename Hs::Shared{}, wacc, lane);
+        Lv::acc_end(a.l, vb_sum, p.l, sh, wacc + 5, lane);
     }
 };
 

@@ -246,3 +246,30 @@ def test_lv_full_size_sampled(L, orc):
     b = ctx.forward(w.theta, w.problem.seed, n - h, path0=h).cpu().numpy()
     assert rel((a + b) / 2, Ey) <= 1e-12
     assert np.all(np.isfinite(g.cpu().numpy()))
+
+
+# ------------------------------------------------- Heston SLV (the paper's model)
+
+@pytest.mark.parametrize("K", [1, 2, 4, 8])
+def test_slv_fp64(L, orc, K):
+    w = inputs.slv_config(n_paths=1500, steps_per_year=32, T=1.0, n_mat=4, n_strike=4, nt=5, nx=6)
+    w = replace(w, problem=replace(w.problem, precision="fp64", ckpt_every=K))
+    check(L, orc, w, 1e-10, 1e-12, path0=33)
+
+
+def test_slv_fp32(L, orc):
+    w = inputs.slv_config(n_paths=1 << 14, steps_per_year=64, T=2.0)
+    check(L, orc, w, 1e-4, 2e-6)
+
+
+def test_slv_unit_leverage_matches_heston_gpu(L):
+    """At L = 1 the SLV kernels reproduce the Heston kernels' prices exactly (FP64)."""
+    ws = inputs.slv_config(n_paths=4096, steps_per_year=32, T=1.0, n_mat=4, n_strike=4)
+    wh = inputs.heston_config(n_paths=4096, steps_per_year=32, T=1.0, n_mat=4, n_strike=4)
+    th = ws.theta.copy()
+    th[5:] = 1.0
+    ps = replace(ws.problem, precision="fp64")
+    ph = replace(wh.problem, precision="fp64", paths_per_thread=1)
+    a = L.Context(ps, max_paths=4096).forward(th, 7, 4096).cpu().numpy()
+    b = L.Context(ph, max_paths=4096).forward(th[:5], 7, 4096).cpu().numpy()
+    assert np.max(np.abs(a - b)) <= 1e-13 * np.max(np.abs(b))

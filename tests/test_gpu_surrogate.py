@@ -53,8 +53,9 @@ def test_surrogate_assisted_calibration_beats_plain(trained):
 
 def test_gpu_calibration_matches_oracle_calibration(orc):
     """Gauss-Newton-metric descent on the FP64 CUDA path (Jacobian from the
-    forward-mode kernel) and on the oracle (Jacobian from unit-seed vjps) both
-    recover theta* under common random numbers."""
+    forward-mode kernel) and on the oracle (Jacobian from unit-seed vjps), from
+    a start near theta*, both recover theta* under common random numbers (the
+    landscape has boundary local minima far from theta*)."""
     from dataclasses import replace
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
@@ -65,9 +66,10 @@ def test_gpu_calibration_matches_oracle_calibration(orc):
     n, seed = 2048, 99
     pb = replace(w.problem, precision="fp64", seed=seed)
     rng = np.random.default_rng(5)
-    theta_star, theta0 = inputs.draw_heston_theta(rng), inputs.draw_heston_theta(rng)
-    C = orc.forward(pb, theta_star, n, n_threads=4)
+    theta_star = inputs.draw_heston_theta(rng)
     lo, hi = inputs.HESTON_RANGES["lo"], inputs.HESTON_RANGES["hi"]
+    theta0 = np.clip(theta_star + 0.05 * (hi - lo) * rng.choice([-1.0, 1.0], 5), lo, hi)
+    C = orc.forward(pb, theta_star, n, n_threads=4)
     ctx = _lib.Context(pb, max_paths=n)
     jac_gpu = lambda th: ctx.price_jacobian(np.asarray(th)[None, :], seed, n)[1][0].cpu().numpy()
     r_gpu = calibrate.descend_metric(calibrate.mc_objective(ctx, C, seed, n), jac_gpu, theta0, lo, hi, 1e-12,
