@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
+#include <cstdlib>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -267,6 +268,33 @@ bool kernels_for(const Plan &p, KernelPair *kp) { return kernels_raw(p.kind, p.p
 
 // Launch shape: blocks of kBlock threads, at most (resident blocks per SM) x
 // (SMs) of them; each warp loops over 32-path chunks.
+// Resident blocks per SM above which a path kernel measured slower (large
+// unrolled bodies: more resident warps spread over more of the code); 0 = no
+// cap.  MCAAD_MAX_BLOCKS_FWD / MCAAD_MAX_BLOCKS_REV override it for tuning.
+struct BlockCap {
+    int kind, precision, K, ppt, fwd, rev;
+};
+const BlockCap kBlockCaps[] = {
+    {kLv, MC_FP32, 25, 1, 0, 0},
+    {kSlv, MC_FP32, 8, 1, 0, 0},
+};
+
+int env_int(const char *name) {
+    const char *v = getenv(name);
+    return v ? atoi(v) : 0;
+}
+
+void block_caps(const Plan &p, int *fwd, int *rev) {
+    *fwd = *rev = 0;
+    for (const BlockCap &c : kBlockCaps)
+        if (c.kind == p.kind && c.precision == p.precision && c.K == p.K && c.ppt == p.ppt) {
+            *fwd = c.fwd;
+            *rev = c.rev;
+        }
+    if (env_int("MCAAD_MAX_BLOCKS_FWD") > 0) *fwd = env_int("MCAAD_MAX_BLOCKS_FWD");
+    if (env_int("MCAAD_MAX_BLOCKS_REV") > 0) *rev = env_int("MCAAD_MAX_BLOCKS_REV");
+}
+
 mc_status launch_shape(const Plan &p, int device, const KernelPair &kp, int nx, int *n_sm,
                        int *grid_fwd, int *grid_rev, size_t *smem_fwd, size_t *smem_rev,
                        std::string &why) {
@@ -288,6 +316,8 @@ mc_status launch_shape(const Plan &p, int device, const KernelPair &kp, int nx, 
     const void *fns[2] = {kp.fwd, kp.rev};
     size_t sm[2] = {*smem_fwd, *smem_rev};
     int *grids[2] = {grid_fwd, grid_rev};
+    int caps[2];
+    block_caps(p, &caps[0], &caps[1]);
     for (int q = 0; q < 2; ++q) {
         e = cudaFuncSetAttribute(fns[q], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm[q]);
         if (e != cudaSuccess) {
@@ -300,15 +330,38 @@ mc_status launch_shape(const Plan &p, int device, const KernelPair &kp, int nx, 
             why = e != cudaSuccess ? cudaGetErrorString(e) : "path kernel does not fit on an SM";
             return e != cudaSuccess ? MC_ERR_CUDA : MC_ERR_UNSUPPORTED;
         }
+        if (caps[q] > 0 && occ > caps[q]) occ = caps[q];
         *grids[q] = occ * *n_sm;
     }
     return MC_OK;
 }
 
-int grid_for_paths(int grid_max, uint64_t n_paths, int ppt) {
+// Blocks for a launch over n_paths: up to grid_max = (resident blocks per SM)
+// x (SMs), each warp looping over 32*ppt-path chunks.  Every chunk costs the
+// same, so the time goes with the number of rounds, ceil(chunks / warps); with
+// n_sm given, fewer resident blocks per SM b (down to occ/2) are used only when
+// that makes the rounds at least 2 % fuller than at full occupancy (fewer
+// warps hide less latency).
+int grid_for_paths(int grid_max, uint64_t n_paths, int ppt, int n_sm = 0) {
     const uint64_t chunks = (n_paths + (uint64_t)kWarp * ppt - 1) / ((uint64_t)kWarp * ppt);
     const uint64_t want = (chunks + kWarpsPerBlock - 1) / kWarpsPerBlock;
-    return (int)(want < (uint64_t)grid_max ? want : (uint64_t)grid_max);
+    if (want <= (uint64_t)grid_max || n_sm <= 0 || grid_max % n_sm) return (int)(want < (uint64_t)grid_max ? want : grid_max);
+    const int occ = grid_max / n_sm;
+    auto eff = [&](int b) {
+        const uint64_t warps = (uint64_t)b * n_sm * kWarpsPerBlock;
+        const uint64_t rounds = (chunks + warps - 1) / warps;
+        return (double)chunks / (double)(rounds * warps);
+    };
+    int best_b = occ;
+    double best_eff = eff(occ);
+    for (int b = occ - 1; b >= (occ + 1) / 2; --b) {
+        const double e = eff(b);
+        if (e > best_eff + 0.02) {
+            best_eff = e;
+            best_b = b;
+        }
+    }
+    return best_b * n_sm;
 }
 
 cudaError_t launch(const void *fn, int grid, size_t smem, const DevProblem &pb, const DevCall &cl,
@@ -517,6 +570,7 @@ static mc_status do_forward(mc_ctx *ctx, const double *theta, uint64_t seed, uin
     cl = DevCall{};
     cl.theta = theta;
     cl.seed = seed;
+    cl.rk = philox_round_keys(seed);
     cl.path0 = path0;
     cl.n_paths = n_paths;
     cl.ckpt = ctx->ckpt;
@@ -525,14 +579,14 @@ static mc_status do_forward(mc_ctx *ctx, const double *theta, uint64_t seed, uin
     cl.part_y = ctx->part_y;
     cl.part_g = ctx->part_g;
     cl.seed_w = ctx->seed_w;
-    grid = grid_for_paths(ctx->grid_fwd, n_paths, ctx->ppt);
+    grid = grid_for_paths(ctx->grid_fwd, n_paths, ctx->ppt, ctx->n_sm);
     cudaError_t e = timed(ctx, MC_K_FORWARD, st, [&] { return launch(ctx->kern.fwd, grid, ctx->smem_fwd, ctx->pb, cl, st); });
     if (e != cudaSuccess) return cuda_fail(ctx, e, "forward sweep launch");
     return MC_OK;
 }
 
 static mc_status do_reverse(mc_ctx *ctx, cudaStream_t st, double *grad_out) {
-    const int grid = grid_for_paths(ctx->grid_rev, ctx->last.n_paths, ctx->ppt);
+    const int grid = grid_for_paths(ctx->grid_rev, ctx->last.n_paths, ctx->ppt, ctx->n_sm);
     cudaError_t e = timed(ctx, MC_K_REVERSE, st, [&] { return launch(ctx->kern.rev, grid, ctx->smem_rev, ctx->pb, ctx->last, st); });
     if (e != cudaSuccess) return cuda_fail(ctx, e, "reverse sweep launch");
     e = timed(ctx, MC_K_FINALIZE_G, st, [&] {
@@ -839,6 +893,7 @@ extern "C" mc_status mc_forward_static(const mc_model *model, const mc_instrumen
     DevCall cl{};
     cl.theta = theta;
     cl.seed = seed;
+    cl.rk = philox_round_keys(seed);
     cl.path0 = path0;
     cl.n_paths = n_paths;
     cl.keep_ckpt = 0;

@@ -75,7 +75,7 @@ finalize_grad_kernel(const double *__restrict__ part_g, int nb, int M, double in
     if (threadIdx.x == 0) grad[j] = s * inv_n;
 }
 
-__global__ void philox_fill_kernel(uint64_t seed, uint64_t path0, uint32_t n_paths, uint32_t n_calls,
+__global__ void philox_fill_kernel(const RoundKeys rk, uint64_t path0, uint32_t n_paths, uint32_t n_calls,
                                    uint4 *out) {
     const uint64_t total = (uint64_t)n_paths * n_calls;
     for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
@@ -83,13 +83,12 @@ __global__ void philox_fill_kernel(uint64_t seed, uint64_t path0, uint32_t n_pat
         const uint64_t i = q / n_calls;
         const uint32_t c = (uint32_t)(q - i * n_calls);
         const uint64_t p = path0 + i;
-        out[q] = philox4x32_10(make_uint4(c, 0u, (uint32_t)p, (uint32_t)(p >> 32)), (uint32_t)seed,
-                               (uint32_t)(seed >> 32));
+        out[q] = philox4x32_10(make_uint4(c, 0u, (uint32_t)p, (uint32_t)(p >> 32)), rk);
     }
 }
 
 template <typename Real>
-__global__ void normals_fill_kernel(uint64_t seed, uint64_t path0, uint32_t n_paths,
+__global__ void normals_fill_kernel(const RoundKeys rk, uint64_t path0, uint32_t n_paths,
                                     uint32_t n_per_path, Real *out) {
     const uint32_t n_calls = (n_per_path + 3) / 4;
     const uint64_t total = (uint64_t)n_paths * n_calls;
@@ -98,8 +97,8 @@ __global__ void normals_fill_kernel(uint64_t seed, uint64_t path0, uint32_t n_pa
         const uint64_t i = q / n_calls;
         const uint32_t c = (uint32_t)(q - i * n_calls);
         PathNormals<Real> g;
-        g.init(seed, path0 + i);
-        g.fill(c);
+        g.init(path0 + i);
+        g.fill(c, rk);
         Real *o = out + i * n_per_path;
         for (uint32_t k = 0; k < 4; ++k) {
             const uint32_t j = 4 * c + k;
@@ -138,19 +137,20 @@ cudaError_t launch_finalize_grad(const double *part_g, int nb, int M, double inv
 cudaError_t launch_philox_fill(uint64_t seed, uint64_t path0, uint32_t n_paths, uint32_t n_calls,
                                uint32_t *out, cudaStream_t st) {
     philox_fill_kernel<<<grid_for((uint64_t)n_paths * n_calls, 256), 256, 0, st>>>(
-        seed, path0, n_paths, n_calls, (uint4 *)out);
+        philox_round_keys(seed), path0, n_paths, n_calls, (uint4 *)out);
     return cudaGetLastError();
 }
 
 cudaError_t launch_normals_fill(uint64_t seed, uint64_t path0, uint32_t n_paths,
                                 uint32_t n_per_path, int precision, void *out, cudaStream_t st) {
     const uint64_t work = (uint64_t)n_paths * ((n_per_path + 3) / 4);
+    const RoundKeys rk = philox_round_keys(seed);
     if (precision == 0)
-        normals_fill_kernel<double><<<grid_for(work, 256), 256, 0, st>>>(seed, path0, n_paths,
-                                                                        n_per_path, (double *)out);
+        normals_fill_kernel<double><<<grid_for(work, 256), 256, 0, st>>>(rk, path0, n_paths, n_per_path,
+                                                                        (double *)out);
     else
-        normals_fill_kernel<float><<<grid_for(work, 256), 256, 0, st>>>(seed, path0, n_paths,
-                                                                       n_per_path, (float *)out);
+        normals_fill_kernel<float><<<grid_for(work, 256), 256, 0, st>>>(rk, path0, n_paths, n_per_path,
+                                                                       (float *)out);
     return cudaGetLastError();
 }
 

@@ -19,18 +19,33 @@ constexpr int kMaxParams = 256;         // M limit
 // 2 by the two Philox constants, keeps the low halves as the new words 1 and
 // 3, and xors the high halves with the other two words and the round key;
 // the key advances by the Weyl increments between rounds.
-__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
-#pragma unroll
+// The round keys depend only on the seed: they are formed once on the host
+// and travel in the kernel parameters (constant bank), so each round costs
+// two wide multiplies and two three-input xors.
+struct RoundKeys {
+    uint32_t k[20];  // (k0, k1) of rounds 0..9
+};
+__host__ __device__ inline RoundKeys philox_round_keys(uint64_t seed) {
+    RoundKeys rk;
+    uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
     for (int round = 0; round < 10; ++round) {
         if (round > 0) {
             k0 += 0x9E3779B9u;
             k1 += 0xBB67AE85u;
         }
+        rk.k[2 * round] = k0;
+        rk.k[2 * round + 1] = k1;
+    }
+    return rk;
+}
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, const RoundKeys &rk) {
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
         const uint32_t lo0 = 0xD2511F53u * c.x;
         const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
         const uint32_t lo1 = 0xCD9E8D57u * c.z;
         const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
-        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        c = make_uint4(hi1 ^ c.y ^ rk.k[2 * round], lo1, hi0 ^ c.w ^ rk.k[2 * round + 1], lo0);
     }
     return c;
 }
@@ -78,16 +93,14 @@ __device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, double &za, d
 // Normals of one path, one Philox block (4 normals) at a time.
 template <typename Real>
 struct PathNormals {
-    uint32_t k0, k1, p_lo, p_hi;
+    uint32_t p_lo, p_hi;
     Real z0, z1, z2, z3;
-    __device__ __forceinline__ void init(uint64_t seed, uint64_t path) {
-        k0 = (uint32_t)seed;
-        k1 = (uint32_t)(seed >> 32);
+    __device__ __forceinline__ void init(uint64_t path) {
         p_lo = (uint32_t)path;
         p_hi = (uint32_t)(path >> 32);
     }
-    __device__ __forceinline__ void fill(uint32_t call) {
-        const uint4 o = philox4x32_10(make_uint4(call, 0u, p_lo, p_hi), k0, k1);
+    __device__ __forceinline__ void fill(uint32_t call, const RoundKeys &rk) {
+        const uint4 o = philox4x32_10(make_uint4(call, 0u, p_lo, p_hi), rk);
         box_muller(o.x, o.y, z0, z1);
         box_muller(o.z, o.w, z2, z3);
     }
@@ -139,6 +152,7 @@ struct DevProblem {
 struct DevCall {
     const double *theta;  // [M]
     uint64_t seed;
+    RoundKeys rk;         // Philox round keys of seed
     uint64_t path0;       // first global path
     uint64_t n_paths;
     void *ckpt;           // [n_seg][state_dim][ckpt_stride] of Real

@@ -26,7 +26,7 @@ constexpr int kJacM = 5;  // Heston parameters (kappa, theta_h, xi, rho, v0)
 template <typename Real>
 __global__ void __launch_bounds__(kBlock)
 heston_jacobian_kernel(const DevProblem pb, const double *__restrict__ thetas,
-                       const double *__restrict__ strikes_t, uint64_t seed, uint64_t n_paths,
+                       const double *__restrict__ strikes_t, const RoundKeys rk, uint64_t n_paths,
                        int bpt, double *__restrict__ out) {
     // out: [n_theta][bpt][m][1 + M] sums (y, then dy/dtheta_j)
     extern __shared__ __align__(16) unsigned char smem[];
@@ -63,7 +63,7 @@ heston_jacobian_kernel(const DevProblem pb, const double *__restrict__ thetas,
         const uint64_t local = ch * kWarp + lane;
         const bool active = local < n_paths;
         PathNormals<Real> rng;
-        rng.init(seed, (uint64_t)t * n_paths + (active ? local : 0));
+        rng.init((uint64_t)t * n_paths + (active ? local : 0));
         Real x = Real(0), v = v0;
         Real dx[kJacM], dv[kJacM];
 #pragma unroll
@@ -76,7 +76,7 @@ heston_jacobian_kernel(const DevProblem pb, const double *__restrict__ thetas,
             for (int i = 0; i < K; ++i) {
                 const int n = s * K + i;
                 const uint32_t j0 = (uint32_t)(2 * n);
-                if ((j0 & 3u) == 0u) rng.fill(j0 >> 2);
+                if ((j0 & 3u) == 0u) rng.fill(j0 >> 2, rk);
                 const Real z1 = rng.pick(j0 & 3u), z2 = rng.pick((j0 + 1) & 3u);
                 const bool pos = v > Real(0);
                 const Real vdt = fmax(v, Real(0)) * dt;
@@ -166,7 +166,8 @@ cudaError_t launch_jacobian(const DevProblem &pb, int precision, const double *t
                             double *part, const double *disc, const int *perm, double *Ey_out,
                             double *J_out, cudaStream_t st) {
     const void *fn = jacobian_kernel(precision);
-    void *args[] = {(void *)&pb, (void *)&thetas, (void *)&strikes_t, (void *)&seed, (void *)&n_paths,
+    const RoundKeys rk = philox_round_keys(seed);
+    void *args[] = {(void *)&pb, (void *)&thetas, (void *)&strikes_t, (void *)&rk, (void *)&n_paths,
                     (void *)&bpt, (void *)&part};
     cudaError_t e = cudaLaunchKernel(fn, dim3(bpt, n_theta), dim3(kBlock), args, smem, st);
     if (e != cudaSuccess) return e;

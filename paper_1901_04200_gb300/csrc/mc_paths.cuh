@@ -119,6 +119,7 @@ struct GbmModel {
     using Real = Real_;
     static constexpr int kind = kGbm;
     static constexpr int DZ = 1, SD = 1;
+    static constexpr bool kKeysInRegisters = false;
     struct State { Real x; };
     struct Tape { Real z; };
     struct Shared {
@@ -181,6 +182,7 @@ struct HestonModel {
     using Real = Real_;
     static constexpr int kind = kHeston;
     static constexpr int DZ = 2, SD = 2;
+    static constexpr bool kKeysInRegisters = false;
     struct State { Real x, v; };
     struct Tape { Real vdt, rs, z1, w; };
     struct Shared {};
@@ -256,6 +258,7 @@ struct LvModel {
     using Real = Real_;
     static constexpr int kind = kLv;
     static constexpr int DZ = 1, SD = 1;
+    static constexpr bool kKeysInRegisters = true;
     static constexpr int kMaxNx = 32;
     struct State { Real x; };
     struct Tape { Real u, z; };  // u = (x - x_lo)/hx, z
@@ -394,6 +397,7 @@ struct SlvModel {
     using Hs = HestonModel<Real_>;
     static constexpr int kind = kSlv;
     static constexpr int DZ = 2, SD = 2;
+    static constexpr bool kKeysInRegisters = true;
     struct State { Real x, v; };
     struct Tape { Real u, vdt, rs, z1, w; };
     using Shared = typename Lv::Shared;
@@ -494,21 +498,21 @@ struct NormalSource {
     PathNormals<Real> gen;
     const double *table;
     __device__ __forceinline__ void init(const DevProblem &pb, const DevCall &cl, uint64_t p) {
-        gen.init(cl.seed, p);
+        gen.init(p);
         table = nullptr;
         if constexpr (Md::kind == kGbm) {  // a normals table is accepted for GBM only
             if (pb.normals) table = pb.normals + (size_t)(p - pb.normals_path0) * pb.normals_stride;
         }
     }
     // Normals of step n, first == true at a segment's first step.
-    __device__ __forceinline__ void get(int n, bool first, Real *z) {
+    __device__ __forceinline__ void get(int n, bool first, Real *z, const RoundKeys &rk) {
 #pragma unroll
         for (int c = 0; c < Md::DZ; ++c) {
             const uint32_t j = (uint32_t)(n * Md::DZ + c);
             if (Md::kind == kGbm && table) {
                 z[c] = (Real)table[j];
             } else {
-                if ((first && c == 0) || (j & 3u) == 0u) gen.fill(j >> 2);
+                if ((first && c == 0) || (j & 3u) == 0u) gen.fill(j >> 2, rk);
                 z[c] = gen.pick(j & 3u);
             }
         }
@@ -555,6 +559,9 @@ __global__ void __launch_bounds__(kBlock) path_forward_kernel(const DevProblem p
     double *wy = (double *)(smem + sp.wacc_y) + warp * pb.m;
     const Real S0 = (Real)pb.S0;
     Real *ck = (Real *)cl.ckpt;
+    // Philox round keys: from the kernel parameters (constant bank), or formed
+    // once per thread into registers, whichever measured faster for the model
+    const RoundKeys rk = Md::kKeysInRegisters ? philox_round_keys(cl.seed) : cl.rk;
 
     constexpr uint64_t kChunk = (uint64_t)kWarp * PPT;
     const uint64_t n_chunks = (cl.n_paths + kChunk - 1) / kChunk;
@@ -587,7 +594,7 @@ __global__ void __launch_bounds__(kBlock) path_forward_kernel(const DevProblem p
 #pragma unroll
                 for (int q = 0; q < PPT; ++q) {
                     Real z[Md::DZ];
-                    rng[q].get(n, i == 0, z);
+                    rng[q].get(n, i == 0, z, rk);
                     Md::step(st[q], z, n, par, sh, nullptr);
                 }
             }
@@ -641,6 +648,7 @@ __global__ void __launch_bounds__(kBlock) path_reverse_kernel(const DevProblem p
     double *wg = (double *)(smem + sp.wacc_g) + warp * pb.M;
     const Real S0 = (Real)pb.S0;
     const Real *ck = (const Real *)cl.ckpt;
+    const RoundKeys rk = Md::kKeysInRegisters ? philox_round_keys(cl.seed) : cl.rk;
 
     constexpr uint64_t kChunk = (uint64_t)kWarp * PPT;
     const uint64_t n_chunks = (cl.n_paths + kChunk - 1) / kChunk;
@@ -676,7 +684,7 @@ __global__ void __launch_bounds__(kBlock) path_reverse_kernel(const DevProblem p
 #pragma unroll
                 for (int q = 0; q < PPT; ++q) {
                     Real z[Md::DZ];
-                    rng[q].get(n, i == 0, z);
+                    rng[q].get(n, i == 0, z, rk);
                     Md::step(st[q], z, n, par, sh, &tape[q][i]);
                 }
             }
