@@ -66,7 +66,7 @@ def _ops(model, kernel):
 # DRAM bytes (read + write) per launch of the dominant kernel, from one ncu
 # capture of the bench command (profiles/heston_fp32_p2e20_s512_value_and_grad.md);
 # reported only while the kernel sources hash to the profiled version.
-MEASURED_TRAFFIC = {("heston", 8, 2): {"bytes": 536916992 + 3986944, "sources": "cce0c5dafaa043b5"}}
+MEASURED_TRAFFIC = {("heston", 8, 2): {"bytes": 536960256 + 4019456, "sources": "1617ec1380f2bd17"}}
 KERNEL_SOURCES = ["mc_common.cuh", "mc_paths.cuh", "mc_paths_heston.cu"]
 
 
