@@ -251,6 +251,8 @@ def calibration_experiment(cases):
         r = calibrate.run_experiment(ctx, sur, theta0, C, seed, P, tol=1e-8, max_evals=300)
         rows.append((r["plain"].converged, r["plain"].evals, r["plain"].seconds, r["mc_phase"].converged,
                      r["mc_phase"].evals, r["surrogate_phase"].seconds + r["mc_phase"].seconds))
+        if sd == 0:
+            verified = calibrate.verify_by_mc(ctx, r["mc_phase"].theta, theta_star, seed + 1, P)
     a = np.array(rows, dtype=float)
     n_samples = n_theta * pb.m
     return {"tol": 1e-8, "paths": P, "cases": cases, "start": "theta*, theta0 drawn in the Heston box (Feller)",
@@ -261,7 +263,8 @@ def calibration_experiment(cases):
                       "median_seconds": float(np.median(a[:, 2]))},
             "surrogate": {"converged": float(a[:, 3].mean()), "median_mc_evals": float(np.median(a[:, 4])),
                           "median_seconds_excl_training": float(np.median(a[:, 5])),
-                          "one_off_seconds": t_data + t_train}}
+                          "one_off_seconds": t_data + t_train},
+            "verified_by_mc": dict(verified, case=0, note="prices at the calibrated theta vs theta*, fresh seed")}
 
 
 def dist_setup(n_gpus):

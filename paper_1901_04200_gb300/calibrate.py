@@ -182,6 +182,21 @@ def surrogate_objective(sur, K, T, C):
     return f
 
 
+def verify_by_mc(ctx, theta, theta_star, seed, n_paths, chunks=4):
+    """Independent check of a calibrated theta: RMS difference of the prices at
+    theta and at theta* over chunks * n_paths fresh paths (a seed the descent
+    never used), and the standard error of that difference."""
+    diffs = []
+    for c in range(chunks):
+        a = ctx.forward(theta, seed, n_paths, path0=c * n_paths).cpu().numpy()
+        b = ctx.forward(theta_star, seed, n_paths, path0=c * n_paths).cpu().numpy()
+        diffs.append(a - b)
+    d = np.mean(diffs, axis=0)
+    se = np.std(diffs, axis=0, ddof=1) / np.sqrt(chunks) if chunks > 1 else np.zeros_like(d)
+    return {"paths": chunks * n_paths, "rms_price_diff": float(np.sqrt(np.mean(d * d))),
+            "max_abs_price_diff": float(np.max(np.abs(d))), "max_stderr": float(np.max(se))}
+
+
 def run_experiment(ctx, sur, theta0, C, seed, n_paths, tol=1e-8, max_evals=500, sur_evals=300):
     """Plain MC-AAD descent vs surrogate-then-MC-AAD descent from theta0 (same optimiser)."""
     lo, hi = inputs.HESTON_RANGES["lo"], inputs.HESTON_RANGES["hi"]

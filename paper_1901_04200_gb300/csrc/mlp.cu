@@ -267,12 +267,16 @@ cudaError_t gemm(const bf16 *A, long long lda, const bf16 *Bm, long long ldb, in
     tc::GemmShape g{A, lda, Bm, ldb, M, N, K, BN, k_slice, err};
     const int kb = (k_slice / tc::kBK) < tc::kMaxKB ? (k_slice / tc::kBK) : tc::kMaxKB;
     const size_t smem = tc::smem_bytes(BN, kb);
-    static bool attr_set = false;  // the largest tile any call uses: BN = 64, four k-blocks
-    if (!attr_set) {
-        cudaError_t r = cudaFuncSetAttribute(gemm_kernel<Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)tc::smem_bytes(kBN, tc::kMaxKB));
+    // the largest tile any call uses (BN = 64, four k-blocks), set once per device
+    static bool attr_set[64] = {false};
+    int dev = 0;
+    cudaError_t r = cudaGetDevice(&dev);
+    if (r != cudaSuccess) return r;
+    if (dev < 0 || dev >= 64 || !attr_set[dev]) {
+        r = cudaFuncSetAttribute(gemm_kernel<Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)tc::smem_bytes(kBN, tc::kMaxKB));
         if (r != cudaSuccess) return r;
-        attr_set = true;
+        if (dev >= 0 && dev < 64) attr_set[dev] = true;
     }
     gemm_kernel<Epi><<<dim3(M / tc::kBM, N / BN, K / k_slice), tc::kThreads, smem, st>>>(g, e);
     return cudaGetLastError();
