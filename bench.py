@@ -337,6 +337,8 @@ def main():
     ap.add_argument("--no-calibration", action="store_true", help="skip the surrogate vs plain calibration")
     ap.add_argument("--calib-cases", type=int, default=4)
     ap.add_argument("--ckpt", type=int, default=0, help="checkpoint interval (0 = workload default)")
+    ap.add_argument("--storage", default="checkpoint", choices=["checkpoint", "full"],
+                    help="reverse sweep: recompute from checkpoints, or read the whole stored tape")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -362,6 +364,7 @@ def main():
     if args.ppt or args.ckpt:
         w.problem.paths_per_thread = args.ppt
         w.problem.ckpt_every = args.ckpt or w.problem.ckpt_every
+    w.problem.storage = args.storage
     pb, P, S = w.problem, w.n_paths, w.problem.last_step
     path0 = rank * P
     dev = torch.device("cuda", torch.cuda.current_device())
@@ -457,6 +460,7 @@ def main():
             "warmup": max(args.warmup, 3), "ms_per_step": ms_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": w.name, "paths_per_gpu": P, "steps": S, "instruments": pb.m, "params": pb.n_params,
+                       "storage": pb.storage,
                        "ckpt_every": pb.ckpt_every, "paths_per_thread": pb.paths_per_thread or "default",
                        "precision": "fp32 paths, fp64 sums",
                        "l2": "inputs larger than L2: checkpoints %.0f MB per step" %

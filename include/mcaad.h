@@ -66,6 +66,13 @@ typedef enum {
 
 typedef enum { MC_FP64 = 0, MC_FP32 = 1 } mc_precision;
 
+/* How the reverse sweep gets the forward sweep's results (two-step algorithm,
+ * step 2): MC_STORAGE_CHECKPOINT stores the state every ckpt_every steps and
+ * re-runs F between checkpoints (cost K_F + K_R per path); MC_STORAGE_FULL
+ * stores every step's tape (K_R only; HBM per path-step: the model's tape
+ * fields x 4 or 8 bytes, written once and read once). */
+typedef enum { MC_STORAGE_CHECKPOINT = 0, MC_STORAGE_FULL = 1 } mc_storage;
+
 /*
  * The stochastic model F (paper: F maps M parameters and N random numbers to
  * the m payoffs of one path; Heston SLV test paragraph: Euler discretisation).
@@ -106,6 +113,7 @@ typedef struct {
     uint64_t normals_path0;
     uint64_t normals_rows;
     int32_t paths_per_thread;
+    int32_t storage;     /* mc_storage */
 } mc_model;
 
 /* European calls y_i = exp(-r T_i) max(S0 e^{x_{n_i}} - K_i, 0), T_i = n_i dt

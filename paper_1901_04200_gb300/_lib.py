@@ -41,6 +41,7 @@ class mc_model(ctypes.Structure):
         ("t_max", ctypes.c_double), ("x_lo", ctypes.c_double), ("x_hi", ctypes.c_double),
         ("normals", ctypes.c_void_p), ("normals_path0", ctypes.c_uint64),
         ("normals_rows", ctypes.c_uint64), ("paths_per_thread", ctypes.c_int32),
+        ("storage", ctypes.c_int32),
     ]
 
 
@@ -134,6 +135,7 @@ class _ProblemC:
         md.n_steps = int(pb.n_steps)
         md.ckpt_every = int(pb.ckpt_every or 0)
         md.paths_per_thread = int(getattr(pb, "paths_per_thread", 0) or 0)
+        md.storage = 1 if getattr(pb, "storage", "checkpoint") == "full" else 0
         if pb.kind == "gbm":
             be = np.ascontiguousarray(pb.bucket_end, dtype=np.int32)
             self.keep.append(be)

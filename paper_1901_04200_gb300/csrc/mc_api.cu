@@ -27,6 +27,8 @@ struct mc_ctx {
     uint64_t max_paths = 0, ckpt_stride = 0;
     int n_sm = 1;
     int grid_fwd = 1, grid_rev = 1, grid_max = 1;
+    int storage = 0;                       // 1: full-storage variant
+    int grid_fwd_st = 1, grid_rev_st = 1;
     size_t smem_fwd = 0, smem_rev = 0;
     KernelPair kern;
     DevProblem pb{};
@@ -35,6 +37,7 @@ struct mc_ctx {
     unsigned char *ws = nullptr;
     size_t ws_bytes = 0;
     void *ckpt = nullptr;
+    void *tape = nullptr, *xmat = nullptr;
     double *part_y = nullptr, *part_g = nullptr, *seed_w = nullptr, *lam2 = nullptr;
     unsigned int *ticket = nullptr;
     // state for mc_vjp
@@ -99,7 +102,7 @@ int default_ppt(int kind, int precision) { return (kind == kHeston && precision 
 
 // Everything a context derives from (model, instruments), computed on the host.
 struct Plan {
-    int kind, precision, K, ppt, n_last, n_seg, m, M, n_groups, state_dim;
+    int kind, precision, K, ppt, n_last, n_seg, m, M, n_groups, state_dim, storage, tape_fields;
     std::vector<int> order;  // sorted position -> caller index
     std::vector<double> strike, disc;
     std::vector<int> perm, grp_seg, grp_begin, bucket, lv_jt;
@@ -152,6 +155,9 @@ mc_status make_plan(const mc_model *md, const mc_instruments *in, Plan &p, std::
         if (md->nx > 32) return bad("LV needs nx <= 32");
     }
     if (md->paths_per_thread < 0 || md->paths_per_thread > 2) return bad("paths_per_thread must be 0, 1 or 2");
+    if (md->storage != MC_STORAGE_CHECKPOINT && md->storage != MC_STORAGE_FULL) return bad("unknown storage mode");
+    p.storage = md->storage;
+    p.tape_fields = md->kind == MC_MODEL_GBM_PWC ? 1 : md->kind == MC_MODEL_HESTON_FT ? 4 : md->kind == MC_MODEL_LV_BILINEAR ? 2 : 5;
     p.ppt = md->paths_per_thread ? md->paths_per_thread : default_ppt(md->kind, md->precision);
     // segment length: must divide every maturity step
     const bool hs_k = md->kind == MC_MODEL_HESTON_FT || md->kind == MC_MODEL_HESTON_SLV;
@@ -237,7 +243,7 @@ mc_status make_plan(const mc_model *md, const mc_instruments *in, Plan &p, std::
 // Workspace carve-out (256-byte aligned pieces).
 struct WsLayout {
     size_t strike, disc, perm, grp_seg, grp_begin, bucket, lv_jt, lv_a, seed_w, lam2, ticket, part_y, part_g,
-        ckpt, total;
+        ckpt, tape, xmat, total;
     WsLayout(const Plan &p, int grid_max, uint64_t ckpt_stride) {
         size_t o = 0;
         auto take = [&](size_t bytes) {
@@ -259,7 +265,9 @@ struct WsLayout {
         part_y = take((size_t)grid_max * p.m * 8);
         part_g = take((size_t)grid_max * p.M * 8);
         const size_t real = p.precision == MC_FP64 ? 8 : 4;
-        ckpt = take((size_t)p.n_seg * p.state_dim * ckpt_stride * real);
+        ckpt = take(p.storage ? 0 : (size_t)p.n_seg * p.state_dim * ckpt_stride * real);
+        tape = take(p.storage ? (size_t)p.n_last * p.tape_fields * ckpt_stride * real : 0);
+        xmat = take(p.storage ? (size_t)p.n_groups * ckpt_stride * real : 0);
         total = o;
     }
 };
@@ -297,7 +305,7 @@ void block_caps(const Plan &p, int *fwd, int *rev) {
 
 mc_status launch_shape(const Plan &p, int device, const KernelPair &kp, int nx, int *n_sm,
                        int *grid_fwd, int *grid_rev, size_t *smem_fwd, size_t *smem_rev,
-                       std::string &why) {
+                       std::string &why, int *grid_fwd_st = nullptr, int *grid_rev_st = nullptr) {
     cudaError_t e = cudaDeviceGetAttribute(n_sm, cudaDevAttrMultiProcessorCount, device);
     if (e != cudaSuccess) {
         why = cudaGetErrorString(e);
@@ -313,12 +321,14 @@ mc_status launch_shape(const Plan &p, int device, const KernelPair &kp, int nx, 
         why = "problem tables exceed shared memory";
         return MC_ERR_UNSUPPORTED;
     }
-    const void *fns[2] = {kp.fwd, kp.rev};
-    size_t sm[2] = {*smem_fwd, *smem_rev};
-    int *grids[2] = {grid_fwd, grid_rev};
-    int caps[2];
+    const bool st = p.storage && grid_fwd_st && grid_rev_st;
+    const void *fns[4] = {kp.fwd, kp.rev, kp.fwd_store, kp.rev_tape};
+    size_t sm[4] = {*smem_fwd, *smem_rev, *smem_fwd, *smem_rev};
+    int *grids[4] = {grid_fwd, grid_rev, grid_fwd_st, grid_rev_st};
+    int caps[4];
     block_caps(p, &caps[0], &caps[1]);
-    for (int q = 0; q < 2; ++q) {
+    caps[2] = caps[3] = 0;
+    for (int q = 0; q < (st ? 4 : 2); ++q) {
         e = cudaFuncSetAttribute(fns[q], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm[q]);
         if (e != cudaSuccess) {
             why = cudaGetErrorString(e);
@@ -409,12 +419,15 @@ mc_status mc_workspace_size(const mc_model *model, const mc_instruments *inst, u
     if (st != MC_OK) return st;
     KernelPair kp;
     if (!kernels_for(p, &kp)) return MC_ERR_UNSUPPORTED;
-    int n_sm, gf, gr;
+    int n_sm, gf, gr, gfs = 0, grs = 0;
     size_t sf, sr;
-    st = launch_shape(p, device, kp, model->nx, &n_sm, &gf, &gr, &sf, &sr, why);
+    st = launch_shape(p, device, kp, model->nx, &n_sm, &gf, &gr, &sf, &sr, why, &gfs, &grs);
     if (st != MC_OK) return st;
     const uint64_t stride = (max_paths + 2 * kWarp - 1) / (2 * kWarp) * (2 * kWarp);
-    *bytes_out = WsLayout(p, gf > gr ? gf : gr, stride).total;
+    int gmax = gf > gr ? gf : gr;
+    gmax = gfs > gmax ? gfs : gmax;
+    gmax = grs > gmax ? grs : gmax;
+    *bytes_out = WsLayout(p, gmax, stride).total;
     return MC_OK;
 }
 
@@ -451,14 +464,19 @@ mc_status mc_context_create(int device, const mc_model *model, const mc_instrume
     ctx->n_seg = p.n_seg;
     ctx->state_dim = p.state_dim;
     ctx->kern = kp;
+    ctx->storage = p.storage;
     st = launch_shape(p, device, kp, model->nx, &ctx->n_sm, &ctx->grid_fwd, &ctx->grid_rev,
-                      &ctx->smem_fwd, &ctx->smem_rev, why);
+                      &ctx->smem_fwd, &ctx->smem_rev, why, &ctx->grid_fwd_st, &ctx->grid_rev_st);
     if (st != MC_OK) {
         fprintf(stderr, "mc_context_create: %s\n", why.c_str());
         delete ctx;
         return st;
     }
     ctx->grid_max = ctx->grid_fwd > ctx->grid_rev ? ctx->grid_fwd : ctx->grid_rev;
+    if (ctx->storage) {
+        ctx->grid_max = ctx->grid_fwd_st > ctx->grid_max ? ctx->grid_fwd_st : ctx->grid_max;
+        ctx->grid_max = ctx->grid_rev_st > ctx->grid_max ? ctx->grid_rev_st : ctx->grid_max;
+    }
     ctx->max_paths = max_paths;
     ctx->ckpt_stride = (max_paths + 2 * kWarp - 1) / (2 * kWarp) * (2 * kWarp);  // whole 64-path chunks
     WsLayout L(p, ctx->grid_max, ctx->ckpt_stride);
@@ -499,6 +517,8 @@ mc_status mc_context_create(int device, const mc_model *model, const mc_instrume
         return MC_ERR_CUDA;
     }
     ctx->ckpt = w + L.ckpt;
+    ctx->tape = w + L.tape;
+    ctx->xmat = w + L.xmat;
     ctx->part_y = (double *)(w + L.part_y);
     ctx->part_g = (double *)(w + L.part_g);
     ctx->seed_w = (double *)(w + L.seed_w);
@@ -579,15 +599,21 @@ static mc_status do_forward(mc_ctx *ctx, const double *theta, uint64_t seed, uin
     cl.part_y = ctx->part_y;
     cl.part_g = ctx->part_g;
     cl.seed_w = ctx->seed_w;
-    grid = grid_for_paths(ctx->grid_fwd, n_paths, ctx->ppt, ctx->n_sm);
-    cudaError_t e = timed(ctx, MC_K_FORWARD, st, [&] { return launch(ctx->kern.fwd, grid, ctx->smem_fwd, ctx->pb, cl, st); });
+    cl.tape = ctx->tape;
+    cl.xmat = ctx->xmat;
+    const bool store = ctx->storage && keep;
+    grid = grid_for_paths(store ? ctx->grid_fwd_st : ctx->grid_fwd, n_paths, ctx->ppt, ctx->n_sm);
+    const void *fn = store ? ctx->kern.fwd_store : ctx->kern.fwd;
+    cudaError_t e = timed(ctx, MC_K_FORWARD, st, [&] { return launch(fn, grid, ctx->smem_fwd, ctx->pb, cl, st); });
     if (e != cudaSuccess) return cuda_fail(ctx, e, "forward sweep launch");
     return MC_OK;
 }
 
 static mc_status do_reverse(mc_ctx *ctx, cudaStream_t st, double *grad_out) {
-    const int grid = grid_for_paths(ctx->grid_rev, ctx->last.n_paths, ctx->ppt, ctx->n_sm);
-    cudaError_t e = timed(ctx, MC_K_REVERSE, st, [&] { return launch(ctx->kern.rev, grid, ctx->smem_rev, ctx->pb, ctx->last, st); });
+    const int grid = grid_for_paths(ctx->storage ? ctx->grid_rev_st : ctx->grid_rev, ctx->last.n_paths, ctx->ppt,
+                                    ctx->n_sm);
+    const void *fn = ctx->storage ? ctx->kern.rev_tape : ctx->kern.rev;
+    cudaError_t e = timed(ctx, MC_K_REVERSE, st, [&] { return launch(fn, grid, ctx->smem_rev, ctx->pb, ctx->last, st); });
     if (e != cudaSuccess) return cuda_fail(ctx, e, "reverse sweep launch");
     e = timed(ctx, MC_K_FINALIZE_G, st, [&] {
         return launch_finalize_grad(ctx->part_g, grid, ctx->M, 1.0 / (double)ctx->last.n_paths, grad_out, st);

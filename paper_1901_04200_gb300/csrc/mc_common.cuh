@@ -161,6 +161,8 @@ struct DevCall {
     double *part_y;       // [gridDim.x][m] per-block payoff sums (sorted order)
     double *part_g;       // [gridDim.x][M] per-block gradient sums
     const double *seed_w; // [m] sorted: lambda_i * disc_i (reverse sweep seeds)
+    void *tape;           // full storage: [n_steps][tape fields][ckpt_stride] of Real
+    void *xmat;           // full storage: [n_groups][ckpt_stride] x at each maturity
 };
 
 }  // namespace mcaad

@@ -9,8 +9,10 @@
 namespace mcaad {
 
 struct KernelPair {
-    const void *fwd = nullptr;
-    const void *rev = nullptr;
+    const void *fwd = nullptr;        // forward sweep, checkpoints every K steps
+    const void *rev = nullptr;        // reverse sweep, recompute from checkpoints
+    const void *fwd_store = nullptr;  // forward sweep storing the whole tape
+    const void *rev_tape = nullptr;   // reverse sweep reading the stored tape
 };
 
 // Path kernels of (kind, precision, segment length K, paths per thread);

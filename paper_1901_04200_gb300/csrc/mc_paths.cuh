@@ -721,4 +721,182 @@ __global__ void __launch_bounds__(kBlock) path_reverse_kernel(const DevProblem p
     }
 }
 
+// ---------------------------------------------------- full-storage variant --
+// The paper's branch for unconstrained memory (two-step algorithm, step 2:
+// "the cost is K_R Cost(F)" when the first step's results are stored): the
+// forward sweep writes every step's tape (the model's Tape fields, SoA
+// [step][field][path], coalesced) and x at each maturity; the reverse sweep
+// streams them back and runs only the adjoint.
+
+template <class Md, int K, int PPT>
+__global__ void __launch_bounds__(kBlock) path_forward_store_kernel(const DevProblem pb, const DevCall cl) {
+    using Real = typename Md::Real;
+    using Tape = typename Md::Tape;
+    constexpr int NF = sizeof(Tape) / sizeof(Real);
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int n_steps = pb.n_seg * K;
+    const SmemPlan sp(Md::kind, sizeof(Real), pb.m, pb.n_groups, pb.M, n_steps, pb.nx, false);
+    load_tables<Md>(smem, sp, pb, false, cl);
+    typename Md::Shared sh;
+    typename Md::Par par;
+    Md::setup(smem, sp, pb, cl.theta, n_steps, sh, par);
+    __syncthreads();
+
+    const Real *strike = (const Real *)(smem + sp.strike);
+    const int *gseg = (const int *)(smem + sp.grp_seg);
+    const int *gbeg = (const int *)(smem + sp.grp_begin);
+    const int warp = threadIdx.x / kWarp, lane = threadIdx.x % kWarp;
+    double *wy = (double *)(smem + sp.wacc_y) + warp * pb.m;
+    const Real S0 = (Real)pb.S0;
+    Real *tp = (Real *)cl.tape;
+    Real *xm = (Real *)cl.xmat;
+    const uint64_t stride = cl.ckpt_stride;
+    const RoundKeys rk = Md::kKeysInRegisters ? philox_round_keys(cl.seed) : cl.rk;
+
+    constexpr uint64_t kChunk = (uint64_t)kWarp * PPT;
+    const uint64_t n_chunks = (cl.n_paths + kChunk - 1) / kChunk;
+    for (uint64_t ch = (uint64_t)blockIdx.x * kWarpsPerBlock + warp; ch < n_chunks;
+         ch += (uint64_t)gridDim.x * kWarpsPerBlock) {
+        uint64_t local[PPT];
+        bool active[PPT];
+        NormalSource<Md> rng[PPT];
+        typename Md::State st[PPT];
+#pragma unroll
+        for (int q = 0; q < PPT; ++q) {
+            local[q] = ch * kChunk + q * kWarp + lane;
+            active[q] = local[q] < cl.n_paths;
+            rng[q].init(pb, cl, cl.path0 + (active[q] ? local[q] : 0));
+            st[q] = Md::init(par);
+        }
+        int g = 0;
+        for (int s = 0; s < pb.n_seg; ++s) {
+#pragma unroll
+            for (int i = 0; i < K; ++i) {
+                const int n = s * K + i;
+#pragma unroll
+                for (int q = 0; q < PPT; ++q) {
+                    Real z[Md::DZ];
+                    rng[q].get(n, i == 0, z, rk);
+                    Tape t;
+                    Md::step(st[q], z, n, par, sh, &t);
+                    const Real *tf = (const Real *)&t;
+#pragma unroll
+                    for (int f = 0; f < NF; ++f) tp[((size_t)n * NF + f) * stride + local[q]] = tf[f];
+                }
+            }
+            if (g < pb.n_groups && gseg[g] == s) {
+                Real S[PPT];
+#pragma unroll
+                for (int q = 0; q < PPT; ++q) {
+                    xm[(size_t)g * stride + local[q]] = st[q].x;
+                    S[q] = S0 * exp_r<Real>(st[q].x);
+                }
+                for (int i0 = gbeg[g]; i0 < gbeg[g + 1]; i0 += kWarp) {
+                    const int cnt = min(kWarp, gbeg[g + 1] - i0);
+                    Real mine = Real(0);
+                    for (int j = 0; j < cnt; ++j) {
+                        Real pay = Real(0);
+#pragma unroll
+                        for (int q = 0; q < PPT; ++q)
+                            pay += active[q] ? fmax(S[q] - strike[i0 + j], Real(0)) : Real(0);
+                        const Real sum = warp_sum(pay);
+                        mine = (lane == j) ? sum : mine;
+                    }
+                    if (lane < cnt) wy[i0 + lane] += (double)mine;
+                }
+                ++g;
+            }
+        }
+    }
+    __syncthreads();
+    const double *wall = (const double *)(smem + sp.wacc_y);
+    for (int i = threadIdx.x; i < pb.m; i += blockDim.x) {
+        double s = 0.0;
+        for (int w = 0; w < kWarpsPerBlock; ++w) s += wall[w * pb.m + i];
+        cl.part_y[(size_t)blockIdx.x * pb.m + i] = s;
+    }
+}
+
+template <class Md, int K, int PPT>
+__global__ void __launch_bounds__(kBlock) path_reverse_tape_kernel(const DevProblem pb, const DevCall cl) {
+    using Real = typename Md::Real;
+    using Tape = typename Md::Tape;
+    constexpr int NF = sizeof(Tape) / sizeof(Real);
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int n_steps = pb.n_seg * K;
+    const SmemPlan sp(Md::kind, sizeof(Real), pb.m, pb.n_groups, pb.M, n_steps, pb.nx, true);
+    load_tables<Md>(smem, sp, pb, true, cl);
+    typename Md::Shared sh;
+    typename Md::Par par;
+    Md::setup(smem, sp, pb, cl.theta, n_steps, sh, par);
+    __syncthreads();
+
+    const Real *strike = (const Real *)(smem + sp.strike);
+    const Real *sw = (const Real *)(smem + sp.seed_w);
+    const int *gseg = (const int *)(smem + sp.grp_seg);
+    const int *gbeg = (const int *)(smem + sp.grp_begin);
+    const int warp = threadIdx.x / kWarp, lane = threadIdx.x % kWarp;
+    double *wg = (double *)(smem + sp.wacc_g) + warp * pb.M;
+    const Real S0 = (Real)pb.S0;
+    const Real *tp = (const Real *)cl.tape;
+    const Real *xm = (const Real *)cl.xmat;
+    const uint64_t stride = cl.ckpt_stride;
+
+    constexpr uint64_t kChunk = (uint64_t)kWarp * PPT;
+    const uint64_t n_chunks = (cl.n_paths + kChunk - 1) / kChunk;
+    for (uint64_t ch = (uint64_t)blockIdx.x * kWarpsPerBlock + warp; ch < n_chunks;
+         ch += (uint64_t)gridDim.x * kWarpsPerBlock) {
+        uint64_t local[PPT];
+        bool active[PPT];
+        Real xb[PPT], vb[PPT];
+#pragma unroll
+        for (int q = 0; q < PPT; ++q) {
+            local[q] = ch * kChunk + q * kWarp + lane;
+            active[q] = local[q] < cl.n_paths;
+            xb[q] = Real(0);
+            vb[q] = Real(0);
+        }
+        typename Md::Acc acc;
+        Md::acc_begin(acc, n_steps, sh);
+        int g = pb.n_groups - 1;
+        for (int s = pb.n_seg - 1; s >= 0; --s) {
+            if (g >= 0 && gseg[g] == s) {
+#pragma unroll
+                for (int q = 0; q < PPT; ++q) {
+                    const Real S = S0 * exp_r<Real>(xm[(size_t)g * stride + local[q]]);
+                    Real seed = Real(0);
+                    for (int i = gbeg[g]; i < gbeg[g + 1]; ++i)
+                        if (S > strike[i]) seed = fma(sw[i], S, seed);
+                    if (active[q]) xb[q] += seed;
+                }
+                --g;
+            }
+#pragma unroll
+            for (int i = K - 1; i >= 0; --i) {
+                const int n = s * K + i;
+                Md::boundary(acc, n, sh, wg, lane);
+#pragma unroll
+                for (int q = 0; q < PPT; ++q) {
+                    Tape t;
+                    Real *tf = (Real *)&t;
+#pragma unroll
+                    for (int f = 0; f < NF; ++f) tf[f] = tp[((size_t)n * NF + f) * stride + local[q]];
+                    Md::adjoint(t, n, xb[q], vb[q], acc, par, sh);
+                }
+            }
+        }
+        Real vb_sum = Real(0);
+#pragma unroll
+        for (int q = 0; q < PPT; ++q) vb_sum += vb[q];
+        Md::acc_end(acc, vb_sum, par, sh, wg, lane);
+    }
+    __syncthreads();
+    const double *wall = (const double *)(smem + sp.wacc_g);
+    for (int j = threadIdx.x; j < pb.M; j += blockDim.x) {
+        double s = 0.0;
+        for (int w = 0; w < kWarpsPerBlock; ++w) s += wall[w * pb.M + j];
+        cl.part_g[(size_t)blockIdx.x * pb.M + j] = s;
+    }
+}
+
 }  // namespace mcaad

@@ -67,6 +67,7 @@ class Problem:
     precision: str = "fp32"
     ckpt_every: int = 0
     paths_per_thread: int = 0
+    storage: str = "checkpoint"  # or "full": the reverse sweep reads every stored step
 
     @property
     def m(self) -> int:

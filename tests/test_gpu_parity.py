@@ -273,3 +273,29 @@ def test_slv_unit_leverage_matches_heston_gpu(L):
     a = L.Context(ps, max_paths=4096).forward(th, 7, 4096).cpu().numpy()
     b = L.Context(ph, max_paths=4096).forward(th[:5], 7, 4096).cpu().numpy()
     assert np.max(np.abs(a - b)) <= 1e-13 * np.max(np.abs(b))
+
+
+# ------------------------------------------- full-storage variant (no recompute)
+
+@pytest.mark.parametrize("kind", ["gbm", "heston", "lv", "slv"])
+def test_full_storage_fp64(L, orc, kind):
+    if kind == "gbm":
+        w = inputs.gbm_config()
+    elif kind == "heston":
+        w = inputs.heston_config(n_paths=2000, steps_per_year=32, T=1.0, n_mat=4, n_strike=5)
+    elif kind == "lv":
+        w = inputs.lv_config(n_paths=1500, n_steps=100, T=2.0, nt=5, nx=6, n_mat=4, n_strike=5)
+    else:
+        w = inputs.slv_config(n_paths=1500, steps_per_year=32, T=1.0, n_mat=4, n_strike=4, nt=5, nx=6)
+    w = replace(w, problem=replace(w.problem, precision="fp64", storage="full"))
+    check(L, orc, w, 1e-10, 1e-12)
+
+
+def test_full_storage_equals_recompute_fp32(L):
+    """Storing the tape or recomputing it gives the same E y and, to FP32 rounding of the
+    re-run segments, the same gradient."""
+    w = inputs.heston_config(n_paths=1 << 15, steps_per_year=64, T=2.0)
+    a = gpu_vg(L, w)
+    b = gpu_vg(L, replace(w, problem=replace(w.problem, storage="full")))
+    assert rel(a[0], b[0]) <= 1e-13
+    assert rel(a[2], b[2]) <= 1e-5
