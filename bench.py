@@ -35,38 +35,53 @@ UNIT = "path-steps/s"
 # Algorithmic ALU operations per path-step, counted from the formulas with
 # ideal fusion (one FMA per a*b+c, one wide multiply for both halves of a
 # 32x32 product, one three-input logic op, one MUFU per log2/sqrt/rsqrt/sin/cos):
-#   Philox-4x32-10: 10 rounds x (2 wide multiplies + 2 xor3) per block of 4
-#     normals -> 20 INT per Heston step (2 normals);
-#   uniforms: 2 x (bit op + or) INT, 2 FADD;
-#   Box-Muller pair: FP32 7 (scale of log, clamp, shift, 2 angle scalings,
-#     2 products), MUFU 4 (lg2, sqrt, sin, cos);
-#   Heston full-truncation step: FP32 13, MUFU 1 (rsqrt);
-#   => F = 22 FP32 + 5 MUFU + 24 INT = 51 ops;
-#   Heston adjoint step R: 17 FP32.
-# Forward kernel runs F; reverse kernel runs F (recompute) + R.
-OPS = {"heston": {"forward_sweep": {"fp32": 22, "mufu": 5, "int": 24},
-                  "reverse_sweep": {"fp32": 39, "mufu": 5, "int": 24}},
-       # local vol, per path-step (one normal): Philox 10 INT + uniform 2 INT, Box-Muller half a
-       # pair (3.5 FP32 + 2 MUFU, 1 FADD), bilinear step 16 FP32 (cell, clamp, lerp, Euler);
-       # adjoint: cell and lerp again 12 FP32, sigma-bar and weights 6, four row-adjoint FMAs 4,
-       # d sigma/dx term 2 (shared-memory loads and stores not counted)
-       "lv": {"forward_sweep": {"fp32": 21, "mufu": 2, "int": 12},
-              "reverse_sweep": {"fp32": 45, "mufu": 2, "int": 12}},
-       # Heston SLV: the Heston step plus the leverage lookup (cell, clamp, lerp: 10) and
-       # L^2 vdt, L sq (2) in F; in R the lookup again (10), L-bar and weights (4), four
-       # row-adjoint FMAs (4), the extra L factors of the Heston adjoint (3) and dL/dx (2)
-       "slv": {"forward_sweep": {"fp32": 34, "mufu": 5, "int": 24},
-               "reverse_sweep": {"fp32": 74, "mufu": 5, "int": 24}}}
+#   "F"    one Euler step with its normals: Philox-4x32-10 (10 rounds x (2 wide
+#          multiplies + 2 xor3) per block of 4 normals), uniforms (bit op + or,
+#          FADD), Box-Muller (FP32 scale of log, clamp, shift, angle scalings,
+#          products; MUFU lg2, sqrt, sin, cos per pair), the model step;
+#   "step" the model step alone (normals given);
+#   "R"    the adjoint of one step.
+# Heston: F = 22 FP32 + 5 MUFU + 24 INT, step = 13 FP32 + rsqrt, R = 17 FP32.
+# Local vol (one normal per step): F = Philox 10 INT + uniform 2 INT, half a
+# Box-Muller pair (3.5 FP32 + 2 MUFU, 1 FADD), bilinear step 16 FP32 (cell, clamp,
+# lerp, Euler); R = cell and lerp again 12, sigma-bar and weights 6, four row-adjoint
+# FMAs 4, d sigma/dx 2 (shared-memory traffic not counted).
+# Heston SLV: the Heston step plus the leverage lookup (10) and L^2 vdt, L sq (2);
+# R adds the lookup again (10), L-bar and weights (4), four row-adjoint FMAs (4), the
+# extra L factors (3) and dL/dx (2) to the Heston adjoint.
+OPS = {"heston": {"F": {"fp32": 22, "mufu": 5, "int": 24}, "step": {"fp32": 13, "mufu": 1}, "R": {"fp32": 17}},
+       "lv": {"F": {"fp32": 21, "mufu": 2, "int": 12}, "step": {"fp32": 16}, "R": {"fp32": 24}},
+       "slv": {"F": {"fp32": 34, "mufu": 5, "int": 24}, "step": {"fp32": 25, "mufu": 1}, "R": {"fp32": 40}}}
+# What each path kernel runs per path-step, by storage mode.
+KERNEL_PARTS = {"checkpoint": {"forward_sweep": ["F"], "reverse_sweep": ["F", "R"]},
+                "normals": {"forward_sweep": ["F"], "reverse_sweep": ["step", "R"]},
+                "full": {"forward_sweep": ["F"], "reverse_sweep": ["R"]}}
+# State words, normals per step and tape words per step of each model.
+DIMS = {"heston": (2, 2, 4), "lv": (1, 1, 2), "slv": (2, 2, 5)}
 
 
-def _ops(model, kernel):
-    return sum(OPS[model][kernel].values())
+def kernel_ops(model, storage, kernel, kind=None):
+    parts = [OPS[model][q] for q in KERNEL_PARTS[storage][kernel]]
+    return sum(v for d in parts for k, v in d.items() if kind is None or k == kind)
 
 
-# DRAM bytes (read + write) per launch of the dominant kernel, from one ncu
-# capture of the bench command (profiles/heston_fp32_p2e20_s512_value_and_grad.md);
-# reported only while the kernel sources hash to the profiled version.
-MEASURED_TRAFFIC = {("heston", 8, 2): {"bytes": 536960256 + 4019456, "sources": "1617ec1380f2bd17"}}
+def kernel_bytes(model, storage, K, S, n_groups):
+    """Algorithmic HBM bytes per path-step of the forward and reverse sweeps (FP32): each
+    kernel writes (forward) or reads (reverse) the same stored data once."""
+    sd, dz, nf = DIMS[model]
+    if storage == "checkpoint":
+        b = 4.0 * sd / K
+    elif storage == "normals":
+        b = 4.0 * sd / K + 4.0 * dz
+    else:
+        b = 4.0 * nf + 4.0 * n_groups / S
+    return {"forward_sweep": b, "reverse_sweep": b}
+
+
+# DRAM bytes (read + write) per launch of a path kernel, from one ncu capture of
+# the bench command (profiles/); reported only while the kernel sources hash to
+# the profiled version.  Key: (model, storage, K, paths per thread, kernel).
+MEASURED_TRAFFIC = {}
 KERNEL_SOURCES = ["mc_common.cuh", "mc_paths.cuh", "mc_paths_heston.cu"]
 
 
@@ -79,8 +94,8 @@ def kernel_sources_hash():
     return h.hexdigest()[:16]
 
 
-def measured_traffic(model, k, ppt):
-    rec = MEASURED_TRAFFIC.get((model, k, ppt))
+def measured_traffic(model, storage, k, ppt, kernel):
+    rec = MEASURED_TRAFFIC.get((model, storage, k, ppt, kernel))
     if rec and rec["sources"] == kernel_sources_hash():
         return rec["bytes"]
     return None
@@ -337,8 +352,9 @@ def main():
     ap.add_argument("--no-calibration", action="store_true", help="skip the surrogate vs plain calibration")
     ap.add_argument("--calib-cases", type=int, default=4)
     ap.add_argument("--ckpt", type=int, default=0, help="checkpoint interval (0 = workload default)")
-    ap.add_argument("--storage", default="checkpoint", choices=["checkpoint", "full"],
-                    help="reverse sweep: recompute from checkpoints, or read the whole stored tape")
+    ap.add_argument("--storage", default="auto", choices=["auto", "checkpoint", "normals", "full"],
+                    help="what the reverse sweep reads: checkpoints (re-run with regenerated normals), "
+                         "checkpoints and stored normals, the whole stored tape, or the library's choice")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -444,10 +460,37 @@ def main():
     sm_mhz_peak = float(peaks.get("sm_max_mhz", 2070.0))
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     issue_peak = 128 * n_sm * sm_mhz_peak * 1e6  # thread-ops/s: 4 warp instructions per SM per clock
-    rev_ms, rev_n = prof["reverse_sweep"]
-    rev_avg = rev_ms / max(rev_n, 1)
+    hbm_peak = float(peaks["hbm_gbs"]) * 1e9
     model = args.workload
-    achieved = P * S * _ops(model, "reverse_sweep") / (rev_avg * 1e-3)
+    storage = ctx.storage
+    K = pb.ckpt_every
+    ppt = pb.paths_per_thread or (2 if model == "heston" else 1)
+    bytes_ps = kernel_bytes(model, storage, K, S, len(set(np.asarray(pb.mat_step).tolist())))
+    kern = {}
+    for kname in ("forward_sweep", "reverse_sweep"):
+        ms, n = prof[kname]
+        t = ms / max(n, 1) * 1e-3
+        ops = kernel_ops(model, storage, kname)
+        a_ops, a_bytes = P * S * ops / t, P * S * bytes_ps[kname] / t
+        kern[kname] = {"ms": t * 1e3, "ops_per_path_step": ops, "bytes_per_path_step": bytes_ps[kname],
+                       "alu_frac": a_ops / issue_peak, "hbm_frac": a_bytes / hbm_peak,
+                       "alu_tops": a_ops / 1e12, "hbm_gbs": a_bytes / 1e9,
+                       "fp32_frac": P * S * kernel_ops(model, storage, kname, "fp32") / t / issue_peak}
+    dom = max(kern, key=lambda k: kern[k]["ms"])
+    d = kern[dom]
+    hbm_bound = d["hbm_frac"] > d["alu_frac"]
+    roofline = {"bound": "hbm" if hbm_bound else "alu",
+                "achieved": d["hbm_gbs"] if hbm_bound else d["alu_tops"],
+                "peak": hbm_peak / 1e9 if hbm_bound else issue_peak / 1e12,
+                "unit": "GB/s" if hbm_bound else "Tops/s",
+                "frac": d["hbm_frac"] if hbm_bound else d["alu_frac"],
+                "traffic": measured_traffic(model, storage, K, ppt, dom),
+                "algorithmic_bytes": P * S * bytes_ps[dom],
+                "kernel": "%s (%s, %s storage, K=%d, %d paths/thread)" % (dom, model, storage, K, ppt),
+                "peak_basis": ("measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs, %s)" % peak_src) if hbm_bound
+                              else "SM issue rate 128 thread-ops/clk x %d SMs x %.0f MHz (%s max clock)"
+                                   % (n_sm, sm_mhz_peak, peak_src),
+                "kernels": kern}
     launches = sum(n for _, n in prof.values())
 
     if rank == 0:
@@ -460,21 +503,12 @@ def main():
             "warmup": max(args.warmup, 3), "ms_per_step": ms_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": w.name, "paths_per_gpu": P, "steps": S, "instruments": pb.m, "params": pb.n_params,
-                       "storage": pb.storage,
+                       "storage": storage,
                        "ckpt_every": pb.ckpt_every, "paths_per_thread": pb.paths_per_thread or "default",
                        "precision": "fp32 paths, fp64 sums",
-                       "l2": "inputs larger than L2: checkpoints %.0f MB per step" %
-                             (P * (S // pb.ckpt_every) * (1 if model == "lv" else 2) * 4 / 1e6)},
-            "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": issue_peak / 1e12,
-                         "unit": "Tops/s", "frac": achieved / issue_peak,
-                         "traffic": measured_traffic(model, pb.ckpt_every, pb.paths_per_thread or
-                                                     (2 if model == "heston" else 1)),
-                         "algorithmic_bytes": P * (S // pb.ckpt_every) * (1 if model == "lv" else 2) * 4,
-                         "kernel": "path_reverse_kernel<%s,f32,K=%d>" % (model, pb.ckpt_every),
-                         "ops_per_path_step": _ops(model, "reverse_sweep"),
-                         "peak_basis": "SM issue rate 128 thread-ops/clk x %d SMs x %.0f MHz (%s max clock)"
-                                       % (n_sm, sm_mhz_peak, peak_src),
-                         "fp32_frac": P * S * OPS[model]["reverse_sweep"]["fp32"] / (rev_avg * 1e-3) / issue_peak},
+                       "l2": "inputs larger than L2: %.0f MB stored and re-read per step" %
+                             (P * S * bytes_ps["forward_sweep"] / 1e6)},
+            "roofline": roofline,
             "kernels_ms_per_step": {k: v[0] / max(v[1], 1) for k, v in prof.items() if v[1]},
             "gpu_launches": launches,
             "e2e": {"value": world * P * S / (e2e_ms * 1e-3), "unit": UNIT,

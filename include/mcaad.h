@@ -67,11 +67,28 @@ typedef enum {
 typedef enum { MC_FP64 = 0, MC_FP32 = 1 } mc_precision;
 
 /* How the reverse sweep gets the forward sweep's results (two-step algorithm,
- * step 2): MC_STORAGE_CHECKPOINT stores the state every ckpt_every steps and
- * re-runs F between checkpoints (cost K_F + K_R per path); MC_STORAGE_FULL
- * stores every step's tape (K_R only; HBM per path-step: the model's tape
- * fields x 4 or 8 bytes, written once and read once). */
-typedef enum { MC_STORAGE_CHECKPOINT = 0, MC_STORAGE_FULL = 1 } mc_storage;
+ * step 2, stored results against recomputation):
+ *   MC_STORAGE_CHECKPOINT  the state every ckpt_every steps; the reverse sweep
+ *                          re-runs F between checkpoints, normals included
+ *                          (cost K_F + K_R per path).
+ *   MC_STORAGE_FULL        every step's tape (K_R only; HBM per path-step: the
+ *                          model's tape fields x 4 or 8 bytes, written once and
+ *                          read once).
+ *   MC_STORAGE_NORMALS     the checkpoints and every normal drawn (1 per step
+ *                          for GBM and LV, 2 for Heston and SLV, x 4 or 8 bytes
+ *                          per path-step); the reverse sweep re-runs the model
+ *                          step between checkpoints on the stored normals.
+ * The three run the same step arithmetic, so E y is the same and the
+ * gradients agree to rounding (the compiler may fuse a multiply and an add
+ * differently in different kernels).  The mode is fixed per context;
+ * mc_workspace_size accounts for the storage it needs. */
+typedef enum {
+    MC_STORAGE_CHECKPOINT = 0,
+    MC_STORAGE_FULL = 1,
+    MC_STORAGE_NORMALS = 2,
+    MC_STORAGE_AUTO = 3 /* NORMALS when the stored normals for max_paths take at most a
+                           quarter of the device's total memory, else CHECKPOINT */
+} mc_storage;
 
 /*
  * The stochastic model F (paper: F maps M parameters and N random numbers to
@@ -150,6 +167,8 @@ const char *mc_last_error(const mc_ctx *ctx);
 /* Parameter count M and instrument count m of a context. */
 int32_t mc_n_params(const mc_ctx *ctx);
 int32_t mc_n_instruments(const mc_ctx *ctx);
+/* The storage mode a context runs (MC_STORAGE_AUTO resolved); -1 for a null context. */
+int32_t mc_storage_mode(const mc_ctx *ctx);
 /* Synchronise `stream` and report any asynchronous CUDA error. */
 mc_status mc_sync(mc_ctx *ctx, void *stream);
 

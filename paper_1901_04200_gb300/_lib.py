@@ -21,6 +21,7 @@ LIB_PATH = os.path.join(_PKG, "libmcaad.so")
 MC_OK, MC_ERR_INVALID_ARG, MC_ERR_CUDA, MC_ERR_OOM, MC_ERR_UNSUPPORTED, MC_ERR_STATE = range(6)
 MC_FP64, MC_FP32 = 0, 1
 KIND = {"gbm": 0, "heston": 1, "lv": 2, "slv": 3}
+STORAGE = {"checkpoint": 0, "full": 1, "normals": 2, "auto": 3}  # mc_storage
 _STATUS = {1: "MC_ERR_INVALID_ARG", 2: "MC_ERR_CUDA", 3: "MC_ERR_OOM", 4: "MC_ERR_UNSUPPORTED",
            5: "MC_ERR_STATE"}
 
@@ -64,6 +65,7 @@ SIGNATURES = [
     ("mc_last_error", ctypes.c_char_p, [_V]),
     ("mc_n_params", _I32, [_V]),
     ("mc_n_instruments", _I32, [_V]),
+    ("mc_storage_mode", _I32, [_V]),
     ("mc_sync", ctypes.c_int, [_V, _V]),
     ("mc_forward", ctypes.c_int, [_V, _V, _U64, _U64, _U64, _V, ctypes.c_int, _V]),
     ("mc_vjp", ctypes.c_int, [_V, _V, _V, _V]),
@@ -135,7 +137,7 @@ class _ProblemC:
         md.n_steps = int(pb.n_steps)
         md.ckpt_every = int(pb.ckpt_every or 0)
         md.paths_per_thread = int(getattr(pb, "paths_per_thread", 0) or 0)
-        md.storage = 1 if getattr(pb, "storage", "checkpoint") == "full" else 0
+        md.storage = STORAGE[getattr(pb, "storage", "auto")]
         if pb.kind == "gbm":
             be = np.ascontiguousarray(pb.bucket_end, dtype=np.int32)
             self.keep.append(be)
@@ -186,6 +188,8 @@ class Context:
         self.handle = h
         self.M = lib.mc_n_params(h)
         self.m = lib.mc_n_instruments(h)
+        # the storage mode the context runs ("auto" resolved by the library)
+        self.storage = {v: k for k, v in STORAGE.items()}[lib.mc_storage_mode(h)]
         self.max_paths = int(max_paths)
 
     def __del__(self):

@@ -20,17 +20,29 @@
 
 using namespace mcaad;
 
+// The path kernels a context launches (chosen by its storage mode) and their
+// shapes: the forward sweep without checkpoints (mc_forward alone), the
+// forward sweep that leaves what the reverse sweep reads, the reverse sweep.
+struct Launch {
+    const void *fwd = nullptr, *fwd_keep = nullptr, *rev = nullptr;
+    int grid_fwd = 1, grid_fwd_keep = 1, grid_rev = 1;  // (resident blocks per SM) x SMs
+    size_t smem_fwd = 0, smem_rev = 0;
+    int grid_max() const {
+        const int g = grid_fwd > grid_fwd_keep ? grid_fwd : grid_fwd_keep;
+        return g > grid_rev ? g : grid_rev;
+    }
+};
+
 struct mc_ctx {
     int device = 0;
     int kind = 0, precision = 0, K = 1, ppt = 1;
     int m = 0, M = 0, n_groups = 0, n_seg = 0, state_dim = 1;
     uint64_t max_paths = 0, ckpt_stride = 0;
     int n_sm = 1;
-    int grid_fwd = 1, grid_rev = 1, grid_max = 1;
-    int storage = 0;                       // 1: full-storage variant
-    int grid_fwd_st = 1, grid_rev_st = 1;
-    size_t smem_fwd = 0, smem_rev = 0;
+    int grid_max = 1;
+    int storage = 0;  // mc_storage
     KernelPair kern;
+    Launch ln;        // the kernels of the storage mode and their launch shapes
     DevProblem pb{};
     // workspace
     bool owns_ws = false;
@@ -102,7 +114,7 @@ int default_ppt(int kind, int precision) { return (kind == kHeston && precision 
 
 // Everything a context derives from (model, instruments), computed on the host.
 struct Plan {
-    int kind, precision, K, ppt, n_last, n_seg, m, M, n_groups, state_dim, storage, tape_fields;
+    int kind, precision, K, ppt, n_last, n_seg, m, M, n_groups, state_dim, storage, tape_fields, dz;
     std::vector<int> order;  // sorted position -> caller index
     std::vector<double> strike, disc;
     std::vector<int> perm, grp_seg, grp_begin, bucket, lv_jt;
@@ -155,8 +167,9 @@ mc_status make_plan(const mc_model *md, const mc_instruments *in, Plan &p, std::
         if (md->nx > 32) return bad("LV needs nx <= 32");
     }
     if (md->paths_per_thread < 0 || md->paths_per_thread > 2) return bad("paths_per_thread must be 0, 1 or 2");
-    if (md->storage != MC_STORAGE_CHECKPOINT && md->storage != MC_STORAGE_FULL) return bad("unknown storage mode");
+    if (md->storage < MC_STORAGE_CHECKPOINT || md->storage > MC_STORAGE_AUTO) return bad("unknown storage mode");
     p.storage = md->storage;
+    p.dz = p.state_dim;  // normals per step: 1 (GBM, LV) or 2 (Heston, SLV)
     p.tape_fields = md->kind == MC_MODEL_GBM_PWC ? 1 : md->kind == MC_MODEL_HESTON_FT ? 4 : md->kind == MC_MODEL_LV_BILINEAR ? 2 : 5;
     p.ppt = md->paths_per_thread ? md->paths_per_thread : default_ppt(md->kind, md->precision);
     // segment length: must divide every maturity step
@@ -265,12 +278,35 @@ struct WsLayout {
         part_y = take((size_t)grid_max * p.m * 8);
         part_g = take((size_t)grid_max * p.M * 8);
         const size_t real = p.precision == MC_FP64 ? 8 : 4;
-        ckpt = take(p.storage ? 0 : (size_t)p.n_seg * p.state_dim * ckpt_stride * real);
-        tape = take(p.storage ? (size_t)p.n_last * p.tape_fields * ckpt_stride * real : 0);
-        xmat = take(p.storage ? (size_t)p.n_groups * ckpt_stride * real : 0);
+        const bool full = p.storage == MC_STORAGE_FULL;
+        ckpt = take(full ? 0 : (size_t)p.n_seg * p.state_dim * ckpt_stride * real);
+        const size_t per_step = full ? p.tape_fields : p.storage == MC_STORAGE_NORMALS ? p.dz : 0;
+        tape = take((size_t)p.n_last * per_step * ckpt_stride * real);
+        xmat = take(full ? (size_t)p.n_groups * ckpt_stride * real : 0);
         total = o;
     }
 };
+
+// MC_STORAGE_AUTO: the stored normals when they take at most a quarter of the
+// device's total memory (a fixed property, so mc_workspace_size and
+// mc_context_create resolve alike), else checkpoints alone.
+mc_status resolve_storage(Plan &p, uint64_t max_paths, int device, std::string &why) {
+    if (p.storage != MC_STORAGE_AUTO) return MC_OK;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaError_t e = cudaSetDevice(device);
+    size_t free_b = 0, total_b = 0;
+    if (e == cudaSuccess) e = cudaMemGetInfo(&free_b, &total_b);
+    cudaSetDevice(prev);
+    if (e != cudaSuccess) {
+        why = cudaGetErrorString(e);
+        return MC_ERR_CUDA;
+    }
+    const uint64_t stride = (max_paths + 2 * kWarp - 1) / (2 * kWarp) * (2 * kWarp);
+    const double normals_bytes = (double)p.n_last * p.dz * (double)stride * (p.precision == MC_FP64 ? 8 : 4);
+    p.storage = normals_bytes <= 0.25 * (double)total_b ? MC_STORAGE_NORMALS : MC_STORAGE_CHECKPOINT;
+    return MC_OK;
+}
 
 bool kernels_for(const Plan &p, KernelPair *kp) { return kernels_raw(p.kind, p.precision, p.K, p.ppt, kp); }
 
@@ -303,9 +339,8 @@ void block_caps(const Plan &p, int *fwd, int *rev) {
     if (env_int("MCAAD_MAX_BLOCKS_REV") > 0) *rev = env_int("MCAAD_MAX_BLOCKS_REV");
 }
 
-mc_status launch_shape(const Plan &p, int device, const KernelPair &kp, int nx, int *n_sm,
-                       int *grid_fwd, int *grid_rev, size_t *smem_fwd, size_t *smem_rev,
-                       std::string &why, int *grid_fwd_st = nullptr, int *grid_rev_st = nullptr) {
+mc_status launch_shape(const Plan &p, int device, const KernelPair &kp, int nx, int *n_sm, Launch &ln,
+                       std::string &why) {
     cudaError_t e = cudaDeviceGetAttribute(n_sm, cudaDevAttrMultiProcessorCount, device);
     if (e != cudaSuccess) {
         why = cudaGetErrorString(e);
@@ -313,22 +348,27 @@ mc_status launch_shape(const Plan &p, int device, const KernelPair &kp, int nx, 
     }
     const int real = p.precision == MC_FP64 ? 8 : 4;
     const int n_steps = p.n_seg * p.K;
-    *smem_fwd = SmemPlan(p.kind, real, p.m, p.n_groups, p.M, n_steps, nx, false).total;
-    *smem_rev = SmemPlan(p.kind, real, p.m, p.n_groups, p.M, n_steps, nx, true).total;
+    const size_t zst = p.storage == MC_STORAGE_NORMALS      ? kp.stage_bytes_z
+                       : p.storage == MC_STORAGE_CHECKPOINT ? kp.stage_bytes_ckpt
+                                                            : 0;
+    ln.smem_fwd = SmemPlan(p.kind, real, p.m, p.n_groups, p.M, n_steps, nx, false).total;
+    ln.smem_rev = SmemPlan(p.kind, real, p.m, p.n_groups, p.M, n_steps, nx, true, zst).total;
     int optin = 0;
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
-    if (*smem_fwd > (size_t)optin || *smem_rev > (size_t)optin) {
+    if (ln.smem_fwd > (size_t)optin || ln.smem_rev > (size_t)optin) {
         why = "problem tables exceed shared memory";
         return MC_ERR_UNSUPPORTED;
     }
-    const bool st = p.storage && grid_fwd_st && grid_rev_st;
-    const void *fns[4] = {kp.fwd, kp.rev, kp.fwd_store, kp.rev_tape};
-    size_t sm[4] = {*smem_fwd, *smem_rev, *smem_fwd, *smem_rev};
-    int *grids[4] = {grid_fwd, grid_rev, grid_fwd_st, grid_rev_st};
-    int caps[4];
-    block_caps(p, &caps[0], &caps[1]);
-    caps[2] = caps[3] = 0;
-    for (int q = 0; q < (st ? 4 : 2); ++q) {
+    ln.fwd = kp.fwd;
+    ln.fwd_keep = p.storage == MC_STORAGE_FULL ? kp.fwd_store : p.storage == MC_STORAGE_NORMALS ? kp.fwd_z : kp.fwd;
+    ln.rev = p.storage == MC_STORAGE_FULL ? kp.rev_tape : p.storage == MC_STORAGE_NORMALS ? kp.rev_z : kp.rev;
+    const void *fns[3] = {ln.fwd, ln.fwd_keep, ln.rev};
+    const size_t sm[3] = {ln.smem_fwd, ln.smem_fwd, ln.smem_rev};
+    int *grids[3] = {&ln.grid_fwd, &ln.grid_fwd_keep, &ln.grid_rev};
+    int cap_fwd, cap_rev;
+    block_caps(p, &cap_fwd, &cap_rev);
+    const int caps[3] = {cap_fwd, cap_fwd, cap_rev};
+    for (int q = 0; q < 3; ++q) {
         e = cudaFuncSetAttribute(fns[q], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm[q]);
         if (e != cudaSuccess) {
             why = cudaGetErrorString(e);
@@ -417,17 +457,16 @@ mc_status mc_workspace_size(const mc_model *model, const mc_instruments *inst, u
     std::string why;
     mc_status st = make_plan(model, inst, p, why);
     if (st != MC_OK) return st;
+    st = resolve_storage(p, max_paths, device, why);
+    if (st != MC_OK) return st;
     KernelPair kp;
     if (!kernels_for(p, &kp)) return MC_ERR_UNSUPPORTED;
-    int n_sm, gf, gr, gfs = 0, grs = 0;
-    size_t sf, sr;
-    st = launch_shape(p, device, kp, model->nx, &n_sm, &gf, &gr, &sf, &sr, why, &gfs, &grs);
+    int n_sm;
+    Launch ln;
+    st = launch_shape(p, device, kp, model->nx, &n_sm, ln, why);
     if (st != MC_OK) return st;
     const uint64_t stride = (max_paths + 2 * kWarp - 1) / (2 * kWarp) * (2 * kWarp);
-    int gmax = gf > gr ? gf : gr;
-    gmax = gfs > gmax ? gfs : gmax;
-    gmax = grs > gmax ? grs : gmax;
-    *bytes_out = WsLayout(p, gmax, stride).total;
+    *bytes_out = WsLayout(p, ln.grid_max(), stride).total;
     return MC_OK;
 }
 
@@ -440,6 +479,7 @@ mc_status mc_context_create(int device, const mc_model *model, const mc_instrume
     Plan p;
     std::string why;
     mc_status st = make_plan(model, inst, p, why);
+    if (st == MC_OK) st = resolve_storage(p, max_paths, device, why);
     if (st != MC_OK) {
         fprintf(stderr, "mc_context_create: %s\n", why.c_str());
         return st;
@@ -465,18 +505,13 @@ mc_status mc_context_create(int device, const mc_model *model, const mc_instrume
     ctx->state_dim = p.state_dim;
     ctx->kern = kp;
     ctx->storage = p.storage;
-    st = launch_shape(p, device, kp, model->nx, &ctx->n_sm, &ctx->grid_fwd, &ctx->grid_rev,
-                      &ctx->smem_fwd, &ctx->smem_rev, why, &ctx->grid_fwd_st, &ctx->grid_rev_st);
+    st = launch_shape(p, device, kp, model->nx, &ctx->n_sm, ctx->ln, why);
     if (st != MC_OK) {
         fprintf(stderr, "mc_context_create: %s\n", why.c_str());
         delete ctx;
         return st;
     }
-    ctx->grid_max = ctx->grid_fwd > ctx->grid_rev ? ctx->grid_fwd : ctx->grid_rev;
-    if (ctx->storage) {
-        ctx->grid_max = ctx->grid_fwd_st > ctx->grid_max ? ctx->grid_fwd_st : ctx->grid_max;
-        ctx->grid_max = ctx->grid_rev_st > ctx->grid_max ? ctx->grid_rev_st : ctx->grid_max;
-    }
+    ctx->grid_max = ctx->ln.grid_max();
     ctx->max_paths = max_paths;
     ctx->ckpt_stride = (max_paths + 2 * kWarp - 1) / (2 * kWarp) * (2 * kWarp);  // whole 64-path chunks
     WsLayout L(p, ctx->grid_max, ctx->ckpt_stride);
@@ -565,6 +600,7 @@ void mc_context_destroy(mc_ctx *ctx) {
 const char *mc_last_error(const mc_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 int32_t mc_n_params(const mc_ctx *ctx) { return ctx ? ctx->M : -1; }
 int32_t mc_n_instruments(const mc_ctx *ctx) { return ctx ? ctx->m : -1; }
+int32_t mc_storage_mode(const mc_ctx *ctx) { return ctx ? ctx->storage : -1; }
 
 mc_status mc_sync(mc_ctx *ctx, void *stream) {
     cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
@@ -601,19 +637,18 @@ static mc_status do_forward(mc_ctx *ctx, const double *theta, uint64_t seed, uin
     cl.seed_w = ctx->seed_w;
     cl.tape = ctx->tape;
     cl.xmat = ctx->xmat;
-    const bool store = ctx->storage && keep;
-    grid = grid_for_paths(store ? ctx->grid_fwd_st : ctx->grid_fwd, n_paths, ctx->ppt, ctx->n_sm);
-    const void *fn = store ? ctx->kern.fwd_store : ctx->kern.fwd;
-    cudaError_t e = timed(ctx, MC_K_FORWARD, st, [&] { return launch(fn, grid, ctx->smem_fwd, ctx->pb, cl, st); });
+    const Launch &ln = ctx->ln;
+    grid = grid_for_paths(keep ? ln.grid_fwd_keep : ln.grid_fwd, n_paths, ctx->ppt, ctx->n_sm);
+    const void *fn = keep ? ln.fwd_keep : ln.fwd;
+    cudaError_t e = timed(ctx, MC_K_FORWARD, st, [&] { return launch(fn, grid, ln.smem_fwd, ctx->pb, cl, st); });
     if (e != cudaSuccess) return cuda_fail(ctx, e, "forward sweep launch");
     return MC_OK;
 }
 
 static mc_status do_reverse(mc_ctx *ctx, cudaStream_t st, double *grad_out) {
-    const int grid = grid_for_paths(ctx->storage ? ctx->grid_rev_st : ctx->grid_rev, ctx->last.n_paths, ctx->ppt,
-                                    ctx->n_sm);
-    const void *fn = ctx->storage ? ctx->kern.rev_tape : ctx->kern.rev;
-    cudaError_t e = timed(ctx, MC_K_REVERSE, st, [&] { return launch(fn, grid, ctx->smem_rev, ctx->pb, ctx->last, st); });
+    const Launch &ln = ctx->ln;
+    const int grid = grid_for_paths(ln.grid_rev, ctx->last.n_paths, ctx->ppt, ctx->n_sm);
+    cudaError_t e = timed(ctx, MC_K_REVERSE, st, [&] { return launch(ln.rev, grid, ln.smem_rev, ctx->pb, ctx->last, st); });
     if (e != cudaSuccess) return cuda_fail(ctx, e, "reverse sweep launch");
     e = timed(ctx, MC_K_FINALIZE_G, st, [&] {
         return launch_finalize_grad(ctx->part_g, grid, ctx->M, 1.0 / (double)ctx->last.n_paths, grad_out, st);
@@ -856,9 +891,11 @@ extern "C" mc_status mc_forward_static(const mc_model *model, const mc_instrumen
         }
         scratch = g_static_ptr[device];
     }
-    int n_sm = 1, grid_fwd = 1, grid_rev = 1;
-    size_t smem_fwd = 0, smem_rev = 0;
-    st = launch_shape(p, device, kp, model->nx, &n_sm, &grid_fwd, &grid_rev, &smem_fwd, &smem_rev, why);
+    int n_sm = 1;
+    Launch ln;
+    st = launch_shape(p, device, kp, model->nx, &n_sm, ln, why);
+    const int grid_fwd = ln.grid_fwd;
+    const size_t smem_fwd = ln.smem_fwd;
     if (st != MC_OK) {
         fprintf(stderr, "mc_forward_static: %s\n", why.c_str());
         return st;

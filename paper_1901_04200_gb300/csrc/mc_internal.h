@@ -13,6 +13,10 @@ struct KernelPair {
     const void *rev = nullptr;        // reverse sweep, recompute from checkpoints
     const void *fwd_store = nullptr;  // forward sweep storing the whole tape
     const void *rev_tape = nullptr;   // reverse sweep reading the stored tape
+    const void *fwd_z = nullptr;      // forward sweep with checkpoints that also stores its normals
+    const void *rev_z = nullptr;      // reverse sweep recomputing from checkpoints on the stored normals
+    size_t stage_bytes_ckpt = 0;      // rev's shared staging buffers per block
+    size_t stage_bytes_z = 0;         // rev_z's shared staging buffers per block
 };
 
 // Path kernels of (kind, precision, segment length K, paths per thread);

@@ -16,8 +16,9 @@
 // end: the warps' sums in warp order -> part_y[block][i].
 //
 // Reverse kernel (step 2, eq. 0711A): per path, segments from last to first:
-// reload the checkpoint, re-run the segment's K steps (regenerating the
-// normals) while recording what the adjoint needs, add the payoff seeds
+// reload the checkpoint (staged in shared memory one segment ahead), re-run
+// the segment's K steps (regenerating the normals, or reading the stored
+// ones) while recording what the adjoint needs, add the payoff seeds
 // lambda_i e^{-rT_i} 1{S>K_i} S of a maturity at the segment end to x-bar,
 // then run the adjoint of the K steps backwards.  Parameter adjoints are
 // summed per thread over its paths in the path precision, then warp-summed
@@ -56,9 +57,10 @@ __host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a -
 
 // Dynamic shared memory of a path kernel, identical on host and device.
 struct SmemPlan {
-    size_t strike, grp_seg, grp_begin, seed_w, wacc_y, wacc_g, model, total;
+    size_t strike, grp_seg, grp_begin, seed_w, wacc_y, wacc_g, model, zstage, total;
+    // zstage_bytes: the reverse sweep's staging buffers for stored normals (0 otherwise)
     __host__ __device__ SmemPlan(int kind, int real_bytes, int m, int n_groups, int M, int n_steps,
-                                 int nx, bool reverse) {
+                                 int nx, bool reverse, size_t zstage_bytes = 0) {
         size_t o = 0;
         strike = o;    o = align_up(o + (size_t)m * real_bytes, 16);
         grp_seg = o;   o = align_up(o + (size_t)n_groups * 4, 16);
@@ -80,6 +82,8 @@ struct SmemPlan {
             o = align_up(o, 16);
             if (reverse) o += (size_t)nx * 2 * real_bytes * kBlock;  // per-thread row adjoints
         }
+        zstage = o = align_up(o, 16);
+        o += zstage_bytes;
         total = align_up(o, 16);
     }
 };
@@ -492,6 +496,61 @@ struct SlvModel {
 
 // ============================================================== kernels ====
 
+// 16-byte asynchronous global -> shared copies (L1 bypassed), grouped per
+// segment; wait_group<N> returns when at most N of the thread's groups are
+// still in flight (a hardware wait, no polling).
+__device__ __forceinline__ void cp_async16(void *dst_smem, const void *src) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst_smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// Reverse-sweep staging.  A warp's segment s needs the checkpoint of its
+// 32*PPT paths (SD * PPT rows of 32 consecutive paths) and, in the
+// stored-normals variant, the segment's normals (K * DZ * PPT rows): the
+// forward sweep then also writes every normal it draws, SoA
+// zt[(n * DZ + c) * stride + path] (one 128-byte line per warp, step and
+// component).  The warp copies segment s-1's rows into its half of a
+// two-buffer shared staging area while it works on segment s, so HBM latency
+// is paid once per chunk instead of once per segment.
+template <class Md, int K, int PPT, bool kZ>
+struct SegStage {
+    using Real = typename Md::Real;
+    static constexpr int RZ = kZ ? K * Md::DZ * PPT : 0;           // normals rows
+    static constexpr int R = RZ + Md::SD * PPT;                     // + checkpoint rows
+    static constexpr int kPerRow = kWarp * (int)sizeof(Real) / 16;  // 16-byte pieces per row
+    static constexpr size_t kWarpBytes = 2 * (size_t)R * kWarp * sizeof(Real);
+    static constexpr size_t kBlockBytes = kWarpBytes * kWarpsPerBlock;
+    __device__ static constexpr int zrow(int i, int c, int q) { return (i * Md::DZ + c) * PPT + q; }
+    __device__ static constexpr int crow(int w, int q) { return RZ + w * PPT + q; }
+    // Copy segment s of the chunk starting at path chunk0 into buffer (s & 1).
+    __device__ __forceinline__ static void issue(Real *stage, const Real *zt, const Real *ck, uint64_t stride,
+                                                 uint64_t chunk0, int s, int lane) {
+        __syncwarp();  // every lane is done with this buffer's previous segment
+        Real *buf = stage + (size_t)(s & 1) * R * kWarp;
+#pragma unroll
+        for (int p0 = 0; p0 < R * kPerRow; p0 += kWarp) {
+            const int p = p0 + lane;
+            if (R * kPerRow % kWarp == 0 || p < R * kPerRow) {
+                const int r = p / kPerRow, part = p - r * kPerRow;
+                const size_t off = part * (16 / sizeof(Real));
+                const int q = r % PPT;  // path slot of the row (RZ is a multiple of PPT)
+                const Real *row;
+                if (r < RZ) {
+                    const int c = (r / PPT) % Md::DZ, i = r / (PPT * Md::DZ);
+                    row = zt + ((size_t)(s * K + i) * Md::DZ + c) * stride;
+                } else {
+                    row = ck + ((size_t)s * Md::SD + (r - RZ) / PPT) * stride;
+                }
+                cp_async16(buf + (size_t)r * kWarp + off, row + chunk0 + (size_t)q * kWarp + off);
+            }
+        }
+        cp_async_commit();
+    }
+};
+
 template <class Md>
 struct NormalSource {
     using Real = typename Md::Real;
@@ -540,7 +599,7 @@ __device__ __forceinline__ void load_tables(unsigned char *base, const SmemPlan 
     }
 }
 
-template <class Md, int K, int PPT>
+template <class Md, int K, int PPT, bool kStoreZ = false>
 __global__ void __launch_bounds__(kBlock) path_forward_kernel(const DevProblem pb, const DevCall cl) {
     using Real = typename Md::Real;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -595,6 +654,11 @@ __global__ void __launch_bounds__(kBlock) path_forward_kernel(const DevProblem p
                 for (int q = 0; q < PPT; ++q) {
                     Real z[Md::DZ];
                     rng[q].get(n, i == 0, z, rk);
+                    if constexpr (kStoreZ) {
+#pragma unroll
+                        for (int c = 0; c < Md::DZ; ++c)
+                            ((Real *)cl.tape)[((size_t)n * Md::DZ + c) * cl.ckpt_stride + local[q]] = z[c];
+                    }
                     Md::step(st[q], z, n, par, sh, nullptr);
                 }
             }
@@ -628,12 +692,13 @@ __global__ void __launch_bounds__(kBlock) path_forward_kernel(const DevProblem p
     }
 }
 
-template <class Md, int K, int PPT>
+template <class Md, int K, int PPT, bool kLoadZ = false>
 __global__ void __launch_bounds__(kBlock) path_reverse_kernel(const DevProblem pb, const DevCall cl) {
     using Real = typename Md::Real;
+    using ZS = SegStage<Md, K, PPT, kLoadZ>;
     extern __shared__ __align__(16) unsigned char smem[];
     const int n_steps = pb.n_seg * K;
-    const SmemPlan sp(Md::kind, sizeof(Real), pb.m, pb.n_groups, pb.M, n_steps, pb.nx, true);
+    const SmemPlan sp(Md::kind, sizeof(Real), pb.m, pb.n_groups, pb.M, n_steps, pb.nx, true, ZS::kBlockBytes);
     load_tables<Md>(smem, sp, pb, true, cl);
     typename Md::Shared sh;
     typename Md::Par par;
@@ -648,7 +713,10 @@ __global__ void __launch_bounds__(kBlock) path_reverse_kernel(const DevProblem p
     double *wg = (double *)(smem + sp.wacc_g) + warp * pb.M;
     const Real S0 = (Real)pb.S0;
     const Real *ck = (const Real *)cl.ckpt;
-    const RoundKeys rk = Md::kKeysInRegisters ? philox_round_keys(cl.seed) : cl.rk;
+    RoundKeys rk;
+    if constexpr (!kLoadZ) rk = Md::kKeysInRegisters ? philox_round_keys(cl.seed) : cl.rk;
+    Real *zstage = (Real *)(smem + sp.zstage) + (size_t)warp * (ZS::kWarpBytes / sizeof(Real));
+    const Real *zt = (const Real *)cl.tape;
 
     constexpr uint64_t kChunk = (uint64_t)kWarp * PPT;
     const uint64_t n_chunks = (cl.n_paths + kChunk - 1) / kChunk;
@@ -662,21 +730,29 @@ __global__ void __launch_bounds__(kBlock) path_reverse_kernel(const DevProblem p
         for (int q = 0; q < PPT; ++q) {
             local[q] = ch * kChunk + q * kWarp + lane;
             active[q] = local[q] < cl.n_paths;
-            rng[q].init(pb, cl, cl.path0 + (active[q] ? local[q] : 0));
+            if constexpr (!kLoadZ) rng[q].init(pb, cl, cl.path0 + (active[q] ? local[q] : 0));
             xb[q] = Real(0);
             vb[q] = Real(0);
         }
+        ZS::issue(zstage, zt, ck, cl.ckpt_stride, ch * kChunk, pb.n_seg - 1, lane);
         typename Md::Acc acc;
         Md::acc_begin(acc, n_steps, sh);
         int g = pb.n_groups - 1;
         for (int s = pb.n_seg - 1; s >= 0; --s) {
+            if (s > 0) {
+                ZS::issue(zstage, zt, ck, cl.ckpt_stride, ch * kChunk, s - 1, lane);
+                cp_async_wait<1>();
+            } else {
+                cp_async_wait<0>();
+            }
+            __syncwarp();  // the other lanes' copies of segment s are visible
+            const Real *sbuf = zstage + (size_t)(s & 1) * ZS::R * kWarp + lane;
             typename Md::State st[PPT];
             typename Md::Tape tape[PPT][K];
 #pragma unroll
             for (int q = 0; q < PPT; ++q) {
-                const Real *c0 = ck + ((size_t)s * Md::SD) * cl.ckpt_stride + local[q];
-                st[q].x = c0[0];
-                if constexpr (Md::SD == 2) st[q].v = c0[cl.ckpt_stride];
+                st[q].x = sbuf[ZS::crow(0, q) * kWarp];
+                if constexpr (Md::SD == 2) st[q].v = sbuf[ZS::crow(1, q) * kWarp];
             }
 #pragma unroll
             for (int i = 0; i < K; ++i) {
@@ -684,7 +760,12 @@ __global__ void __launch_bounds__(kBlock) path_reverse_kernel(const DevProblem p
 #pragma unroll
                 for (int q = 0; q < PPT; ++q) {
                     Real z[Md::DZ];
-                    rng[q].get(n, i == 0, z, rk);
+                    if constexpr (kLoadZ) {
+#pragma unroll
+                        for (int c = 0; c < Md::DZ; ++c) z[c] = sbuf[ZS::zrow(i, c, q) * kWarp];
+                    } else {
+                        rng[q].get(n, i == 0, z, rk);
+                    }
                     Md::step(st[q], z, n, par, sh, &tape[q][i]);
                 }
             }
@@ -897,6 +978,19 @@ __global__ void __launch_bounds__(kBlock) path_reverse_tape_kernel(const DevProb
         for (int w = 0; w < kWarpsPerBlock; ++w) s += wall[w * pb.M + j];
         cl.part_g[(size_t)blockIdx.x * pb.M + j] = s;
     }
+}
+
+// Every variant of (model, K, PPT) for the host's kernel table.
+template <class Md, int K, int PPT, class Table>
+void set_kernels(Table *out) {
+    out->fwd = (const void *)path_forward_kernel<Md, K, PPT>;
+    out->rev = (const void *)path_reverse_kernel<Md, K, PPT>;
+    out->fwd_store = (const void *)path_forward_store_kernel<Md, K, PPT>;
+    out->rev_tape = (const void *)path_reverse_tape_kernel<Md, K, PPT>;
+    out->fwd_z = (const void *)path_forward_kernel<Md, K, PPT, true>;
+    out->rev_z = (const void *)path_reverse_kernel<Md, K, PPT, true>;
+    out->stage_bytes_ckpt = SegStage<Md, K, PPT, false>::kBlockBytes;
+    out->stage_bytes_z = SegStage<Md, K, PPT, true>::kBlockBytes;
 }
 
 }  // namespace mcaad

@@ -1,5 +1,5 @@
 // mc_paths_gbm.cu -- instantiations of the forward and reverse path kernels
-// (checkpoint/recompute and full-storage variants)
+// (checkpoint/recompute, stored-normals and full-storage variants)
 // for the GbmModel model, one per (precision, segment length K, paths per thread).
 #include "mc_internal.h"
 #include "mc_paths.cuh"
@@ -9,38 +9,23 @@ namespace mcaad {
 template <typename Real>
 static bool pick(int K, int ppt, KernelPair *out) {
     if (K == 16 && ppt == 1) {
-        out->fwd = (const void *)path_forward_kernel<GbmModel<Real>, 16, 1>;
-        out->rev = (const void *)path_reverse_kernel<GbmModel<Real>, 16, 1>;
-        out->fwd_store = (const void *)path_forward_store_kernel<GbmModel<Real>, 16, 1>;
-        out->rev_tape = (const void *)path_reverse_tape_kernel<GbmModel<Real>, 16, 1>;
+        set_kernels<GbmModel<Real>, 16, 1>(out);
         return true;
     }
     if (K == 8 && ppt == 1) {
-        out->fwd = (const void *)path_forward_kernel<GbmModel<Real>, 8, 1>;
-        out->rev = (const void *)path_reverse_kernel<GbmModel<Real>, 8, 1>;
-        out->fwd_store = (const void *)path_forward_store_kernel<GbmModel<Real>, 8, 1>;
-        out->rev_tape = (const void *)path_reverse_tape_kernel<GbmModel<Real>, 8, 1>;
+        set_kernels<GbmModel<Real>, 8, 1>(out);
         return true;
     }
     if (K == 4 && ppt == 1) {
-        out->fwd = (const void *)path_forward_kernel<GbmModel<Real>, 4, 1>;
-        out->rev = (const void *)path_reverse_kernel<GbmModel<Real>, 4, 1>;
-        out->fwd_store = (const void *)path_forward_store_kernel<GbmModel<Real>, 4, 1>;
-        out->rev_tape = (const void *)path_reverse_tape_kernel<GbmModel<Real>, 4, 1>;
+        set_kernels<GbmModel<Real>, 4, 1>(out);
         return true;
     }
     if (K == 2 && ppt == 1) {
-        out->fwd = (const void *)path_forward_kernel<GbmModel<Real>, 2, 1>;
-        out->rev = (const void *)path_reverse_kernel<GbmModel<Real>, 2, 1>;
-        out->fwd_store = (const void *)path_forward_store_kernel<GbmModel<Real>, 2, 1>;
-        out->rev_tape = (const void *)path_reverse_tape_kernel<GbmModel<Real>, 2, 1>;
+        set_kernels<GbmModel<Real>, 2, 1>(out);
         return true;
     }
     if (K == 1 && ppt == 1) {
-        out->fwd = (const void *)path_forward_kernel<GbmModel<Real>, 1, 1>;
-        out->rev = (const void *)path_reverse_kernel<GbmModel<Real>, 1, 1>;
-        out->fwd_store = (const void *)path_forward_store_kernel<GbmModel<Real>, 1, 1>;
-        out->rev_tape = (const void *)path_reverse_tape_kernel<GbmModel<Real>, 1, 1>;
+        set_kernels<GbmModel<Real>, 1, 1>(out);
         return true;
     }
     return false;

@@ -1,5 +1,5 @@
 // mc_paths_heston.cu -- instantiations of the forward and reverse path kernels
-// (checkpoint/recompute and full-storage variants)
+// (checkpoint/recompute, stored-normals and full-storage variants)
 // for the HestonModel model, one per (precision, segment length K, paths per thread).
 #include "mc_internal.h"
 #include "mc_paths.cuh"
@@ -9,52 +9,31 @@ namespace mcaad {
 template <typename Real>
 static bool pick(int K, int ppt, KernelPair *out) {
     if (K == 8 && ppt == 1) {
-        out->fwd = (const void *)path_forward_kernel<HestonModel<Real>, 8, 1>;
-        out->rev = (const void *)path_reverse_kernel<HestonModel<Real>, 8, 1>;
-        out->fwd_store = (const void *)path_forward_store_kernel<HestonModel<Real>, 8, 1>;
-        out->rev_tape = (const void *)path_reverse_tape_kernel<HestonModel<Real>, 8, 1>;
+        set_kernels<HestonModel<Real>, 8, 1>(out);
         return true;
     }
     if (K == 4 && ppt == 1) {
-        out->fwd = (const void *)path_forward_kernel<HestonModel<Real>, 4, 1>;
-        out->rev = (const void *)path_reverse_kernel<HestonModel<Real>, 4, 1>;
-        out->fwd_store = (const void *)path_forward_store_kernel<HestonModel<Real>, 4, 1>;
-        out->rev_tape = (const void *)path_reverse_tape_kernel<HestonModel<Real>, 4, 1>;
+        set_kernels<HestonModel<Real>, 4, 1>(out);
         return true;
     }
     if (K == 2 && ppt == 1) {
-        out->fwd = (const void *)path_forward_kernel<HestonModel<Real>, 2, 1>;
-        out->rev = (const void *)path_reverse_kernel<HestonModel<Real>, 2, 1>;
-        out->fwd_store = (const void *)path_forward_store_kernel<HestonModel<Real>, 2, 1>;
-        out->rev_tape = (const void *)path_reverse_tape_kernel<HestonModel<Real>, 2, 1>;
+        set_kernels<HestonModel<Real>, 2, 1>(out);
         return true;
     }
     if (K == 1 && ppt == 1) {
-        out->fwd = (const void *)path_forward_kernel<HestonModel<Real>, 1, 1>;
-        out->rev = (const void *)path_reverse_kernel<HestonModel<Real>, 1, 1>;
-        out->fwd_store = (const void *)path_forward_store_kernel<HestonModel<Real>, 1, 1>;
-        out->rev_tape = (const void *)path_reverse_tape_kernel<HestonModel<Real>, 1, 1>;
+        set_kernels<HestonModel<Real>, 1, 1>(out);
         return true;
     }
     if (K == 8 && ppt == 2) {
-        out->fwd = (const void *)path_forward_kernel<HestonModel<Real>, 8, 2>;
-        out->rev = (const void *)path_reverse_kernel<HestonModel<Real>, 8, 2>;
-        out->fwd_store = (const void *)path_forward_store_kernel<HestonModel<Real>, 8, 2>;
-        out->rev_tape = (const void *)path_reverse_tape_kernel<HestonModel<Real>, 8, 2>;
+        set_kernels<HestonModel<Real>, 8, 2>(out);
         return true;
     }
     if (K == 4 && ppt == 2) {
-        out->fwd = (const void *)path_forward_kernel<HestonModel<Real>, 4, 2>;
-        out->rev = (const void *)path_reverse_kernel<HestonModel<Real>, 4, 2>;
-        out->fwd_store = (const void *)path_forward_store_kernel<HestonModel<Real>, 4, 2>;
-        out->rev_tape = (const void *)path_reverse_tape_kernel<HestonModel<Real>, 4, 2>;
+        set_kernels<HestonModel<Real>, 4, 2>(out);
         return true;
     }
     if (K == 2 && ppt == 2) {
-        out->fwd = (const void *)path_forward_kernel<HestonModel<Real>, 2, 2>;
-        out->rev = (const void *)path_reverse_kernel<HestonModel<Real>, 2, 2>;
-        out->fwd_store = (const void *)path_forward_store_kernel<HestonModel<Real>, 2, 2>;
-        out->rev_tape = (const void *)path_reverse_tape_kernel<HestonModel<Real>, 2, 2>;
+        set_kernels<HestonModel<Real>, 2, 2>(out);
         return true;
     }
     return false;

@@ -1,5 +1,5 @@
 // mc_paths_lv.cu -- instantiations of the forward and reverse path kernels
-// (checkpoint/recompute and full-storage variants)
+// (checkpoint/recompute, stored-normals and full-storage variants)
 // for the LvModel model, one per (precision, segment length K, paths per thread).
 #include "mc_internal.h"
 #include "mc_paths.cuh"
@@ -9,31 +9,19 @@ namespace mcaad {
 template <typename Real>
 static bool pick(int K, int ppt, KernelPair *out) {
     if (K == 25 && ppt == 1) {
-        out->fwd = (const void *)path_forward_kernel<LvModel<Real>, 25, 1>;
-        out->rev = (const void *)path_reverse_kernel<LvModel<Real>, 25, 1>;
-        out->fwd_store = (const void *)path_forward_store_kernel<LvModel<Real>, 25, 1>;
-        out->rev_tape = (const void *)path_reverse_tape_kernel<LvModel<Real>, 25, 1>;
+        set_kernels<LvModel<Real>, 25, 1>(out);
         return true;
     }
     if (K == 5 && ppt == 1) {
-        out->fwd = (const void *)path_forward_kernel<LvModel<Real>, 5, 1>;
-        out->rev = (const void *)path_reverse_kernel<LvModel<Real>, 5, 1>;
-        out->fwd_store = (const void *)path_forward_store_kernel<LvModel<Real>, 5, 1>;
-        out->rev_tape = (const void *)path_reverse_tape_kernel<LvModel<Real>, 5, 1>;
+        set_kernels<LvModel<Real>, 5, 1>(out);
         return true;
     }
     if (K == 1 && ppt == 1) {
-        out->fwd = (const void *)path_forward_kernel<LvModel<Real>, 1, 1>;
-        out->rev = (const void *)path_reverse_kernel<LvModel<Real>, 1, 1>;
-        out->fwd_store = (const void *)path_forward_store_kernel<LvModel<Real>, 1, 1>;
-        out->rev_tape = (const void *)path_reverse_tape_kernel<LvModel<Real>, 1, 1>;
+        set_kernels<LvModel<Real>, 1, 1>(out);
         return true;
     }
     if (K == 5 && ppt == 2) {
-        out->fwd = (const void *)path_forward_kernel<LvModel<Real>, 5, 2>;
-        out->rev = (const void *)path_reverse_kernel<LvModel<Real>, 5, 2>;
-        out->fwd_store = (const void *)path_forward_store_kernel<LvModel<Real>, 5, 2>;
-        out->rev_tape = (const void *)path_reverse_tape_kernel<LvModel<Real>, 5, 2>;
+        set_kernels<LvModel<Real>, 5, 2>(out);
         return true;
     }
     return false;

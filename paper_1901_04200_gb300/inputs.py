@@ -67,7 +67,11 @@ class Problem:
     precision: str = "fp32"
     ckpt_every: int = 0
     paths_per_thread: int = 0
-    storage: str = "checkpoint"  # or "full": the reverse sweep reads every stored step
+    # what the reverse sweep reads: "checkpoint" (states every K steps, re-run with
+    # regenerated normals), "normals" (the checkpoints and every normal drawn),
+    # "full" (every step's tape), "auto" (normals if they fit a quarter of the
+    # device's memory, else checkpoint)
+    storage: str = "auto"
 
     @property
     def m(self) -> int:
@@ -181,8 +185,11 @@ def heston_config(n_paths: int = 1 << 20, steps_per_year: int = 256, T: float = 
 
 def lv_config(n_paths: int = 1 << 22, n_steps: int = 500, T: float = 5.0, nt: int = 20,
               nx: int = 10, n_mat: int = 20, n_strike: int = 10, seed: int = PHILOX_SEED,
-              ckpt_every: int = 25) -> Workload:
-    """Bilinear local-vol surface over (t, ln S/S0); FP32 path arithmetic."""
+              ckpt_every: int = 5, paths_per_thread: int = 2) -> Workload:
+    """Bilinear local-vol surface over (t, ln S/S0); FP32 path arithmetic.  Segments of 5
+    steps with two paths per thread: the fastest launch shape measured on 2^22 x 500
+    (11.0 ms per value and gradient with stored normals, against 14.6 ms at K = 25 with one
+    path per thread)."""
     dt = T / n_steps
     steps = (np.arange(1, n_mat + 1) * (n_steps // n_mat)).astype(np.int32)
     strikes = np.linspace(60.0, 150.0, n_strike)
@@ -195,7 +202,7 @@ def lv_config(n_paths: int = 1 << 22, n_steps: int = 500, T: float = 5.0, nt: in
     C = _bs_targets(100.0, 0.02, K, mat_step * dt, hidden, mat_index)
     pb = Problem(kind="lv", S0=100.0, r=0.02, dt=dt, n_steps=n_steps, K=K, mat_step=mat_step,
                  seed=seed, nt=nt, nx=nx, t_max=T, x_lo=-1.0, x_hi=1.0,
-                 precision="fp32", ckpt_every=ckpt_every)
+                 precision="fp32", ckpt_every=ckpt_every, paths_per_thread=paths_per_thread)
     return Workload("lv_bilinear_m200_s500_fp32", pb, theta, C, n_paths, {"hidden_vol": hidden})
 
 

@@ -98,10 +98,12 @@ def test_gbm_fp64_philox_ragged(L, orc):
     check(L, orc, w, 1e-10, 1e-12, n_paths=1001, path0=(1 << 32) - 500)
 
 
+@pytest.mark.parametrize("storage", ["checkpoint", "normals"])
 @pytest.mark.parametrize("K,ppt", [(1, 1), (2, 1), (4, 1), (8, 1), (2, 2), (4, 2), (8, 2)])
-def test_heston_fp64_all_segment_lengths(L, orc, K, ppt):
+def test_heston_fp64_all_segment_lengths(L, orc, K, ppt, storage):
     w = inputs.heston_config(n_paths=3000, steps_per_year=32, T=1.0, n_mat=4, n_strike=5)
-    w = replace(w, problem=replace(w.problem, precision="fp64", ckpt_every=K, paths_per_thread=ppt))
+    w = replace(w, problem=replace(w.problem, precision="fp64", ckpt_every=K, paths_per_thread=ppt,
+                                   storage=storage))
     check(L, orc, w, 1e-10, 1e-12, n_paths=3000, path0=77)
 
 
@@ -112,10 +114,12 @@ def test_heston_fp64_no_feller(L, orc):
     check(L, orc, w, 1e-9, 1e-12)
 
 
+@pytest.mark.parametrize("storage", ["checkpoint", "normals"])
 @pytest.mark.parametrize("K,ppt", [(1, 1), (5, 1), (25, 1), (5, 2)])
-def test_lv_fp64(L, orc, K, ppt):
+def test_lv_fp64(L, orc, K, ppt, storage):
     w = inputs.lv_config(n_paths=1500, n_steps=100, T=2.0, nt=5, nx=6, n_mat=4, n_strike=5)
-    w = replace(w, problem=replace(w.problem, precision="fp64", ckpt_every=K, paths_per_thread=ppt))
+    w = replace(w, problem=replace(w.problem, precision="fp64", ckpt_every=K, paths_per_thread=ppt,
+                                   storage=storage))
     check(L, orc, w, 1e-10, 1e-12)
 
 
@@ -127,10 +131,11 @@ def test_lv_fp64_clamped_surface(L, orc):
 
 # ------------------------------------------------------------ FP32 paths
 
+@pytest.mark.parametrize("storage", ["checkpoint", "normals"])
 @pytest.mark.parametrize("K,ppt", [(8, 1), (4, 2), (2, 2)])
-def test_heston_fp32_small(L, orc, K, ppt):
+def test_heston_fp32_small(L, orc, K, ppt, storage):
     w = inputs.heston_config(n_paths=1 << 14, steps_per_year=64, T=2.0)
-    w = replace(w, problem=replace(w.problem, ckpt_every=K, paths_per_thread=ppt))
+    w = replace(w, problem=replace(w.problem, ckpt_every=K, paths_per_thread=ppt, storage=storage))
     check(L, orc, w, 1e-4, 2e-6)
 
 
@@ -147,10 +152,11 @@ def test_gbm_fp32(L, orc):
 
 # -------------------------------------------------------------- edge cases
 
+@pytest.mark.parametrize("storage", ["checkpoint", "normals"])
 @pytest.mark.parametrize("n", [1, 31, 33, 4097])
-def test_ragged_path_counts(L, orc, n):
+def test_ragged_path_counts(L, orc, n, storage):
     w = inputs.heston_config(n_paths=n, steps_per_year=16, T=1.0, n_mat=2, n_strike=3)
-    w = replace(w, problem=replace(w.problem, precision="fp64"))
+    w = replace(w, problem=replace(w.problem, precision="fp64", storage=storage))
     check(L, orc, w, 1e-10, 1e-12)
 
 
@@ -223,9 +229,10 @@ def test_deterministic_repeat(L):
 
 @pytest.mark.slow
 def test_heston_full_size(L, orc):
-    """The benchmark workload (2^20 paths x 512 steps, launch shape of the bench) vs the oracle."""
+    """The benchmark workload (2^20 paths x 512 steps, launch shape of the bench) vs the oracle,
+    checkpoint/recompute arm."""
     w = inputs.heston_config()
-    check(L, orc, w, 1e-4, 2e-6)
+    check(L, orc, replace(w, problem=replace(w.problem, storage="checkpoint")), 1e-4, 2e-6)
 
 
 @pytest.mark.slow
@@ -250,10 +257,11 @@ def test_lv_full_size_sampled(L, orc):
 
 # ------------------------------------------------- Heston SLV (the paper's model)
 
+@pytest.mark.parametrize("storage", ["checkpoint", "normals"])
 @pytest.mark.parametrize("K", [1, 2, 4, 8])
-def test_slv_fp64(L, orc, K):
+def test_slv_fp64(L, orc, K, storage):
     w = inputs.slv_config(n_paths=1500, steps_per_year=32, T=1.0, n_mat=4, n_strike=4, nt=5, nx=6)
-    w = replace(w, problem=replace(w.problem, precision="fp64", ckpt_every=K))
+    w = replace(w, problem=replace(w.problem, precision="fp64", ckpt_every=K, storage=storage))
     check(L, orc, w, 1e-10, 1e-12, path0=33)
 
 
@@ -275,27 +283,91 @@ def test_slv_unit_leverage_matches_heston_gpu(L):
     assert np.max(np.abs(a - b)) <= 1e-13 * np.max(np.abs(b))
 
 
-# ------------------------------------------- full-storage variant (no recompute)
+# ------------------------------------- stored variants: full tape, stored normals
+# "full": the forward sweep stores every step's tape and the reverse sweep runs
+# only the adjoint; "normals": the forward sweep stores its normals next to the
+# checkpoints and the reverse sweep re-runs each segment on them.
 
-@pytest.mark.parametrize("kind", ["gbm", "heston", "lv", "slv"])
-def test_full_storage_fp64(L, orc, kind):
+STORED = ["full", "normals"]
+
+
+def small_case(kind, n_paths=None):
     if kind == "gbm":
-        w = inputs.gbm_config()
-    elif kind == "heston":
-        w = inputs.heston_config(n_paths=2000, steps_per_year=32, T=1.0, n_mat=4, n_strike=5)
-    elif kind == "lv":
-        w = inputs.lv_config(n_paths=1500, n_steps=100, T=2.0, nt=5, nx=6, n_mat=4, n_strike=5)
+        return inputs.gbm_config()
+    if kind == "heston":
+        return inputs.heston_config(n_paths=n_paths or 2000, steps_per_year=32, T=1.0, n_mat=4, n_strike=5)
+    if kind == "lv":
+        return inputs.lv_config(n_paths=n_paths or 1500, n_steps=100, T=2.0, nt=5, nx=6, n_mat=4, n_strike=5)
+    return inputs.slv_config(n_paths=n_paths or 1500, steps_per_year=32, T=1.0, n_mat=4, n_strike=4, nt=5, nx=6)
+
+
+def with_pb(w, **kw):
+    return replace(w, problem=replace(w.problem, **kw))
+
+
+@pytest.mark.parametrize("storage", STORED)
+@pytest.mark.parametrize("kind", ["gbm", "heston", "lv", "slv"])
+def test_stored_variants_fp64(L, orc, kind, storage):
+    check(L, orc, with_pb(small_case(kind), precision="fp64", storage=storage), 1e-10, 1e-12)
+
+
+@pytest.mark.parametrize("kind,K,ppt", [("gbm", 1, 1), ("gbm", 16, 1), ("heston", 1, 1), ("heston", 2, 2),
+                                        ("heston", 4, 1), ("heston", 8, 2), ("lv", 1, 1), ("lv", 5, 2),
+                                        ("lv", 25, 1), ("slv", 2, 1), ("slv", 8, 1)])
+def test_stored_normals_staging_shapes_fp64(L, orc, kind, K, ppt):
+    """Every staging geometry: rows per warp K*DZ*PPT from 1 to 32, copies that do not fill
+    the warp's lanes, 256-byte FP64 rows, ragged path counts."""
+    if kind == "gbm":  # one bucket, so that K = 16 divides the only maturity step
+        w = with_pb(inputs.gbm_config(n_paths=1001, n_buckets=8 if K < 16 else 1), normals=None)
     else:
-        w = inputs.slv_config(n_paths=1500, steps_per_year=32, T=1.0, n_mat=4, n_strike=4, nt=5, nx=6)
-    w = replace(w, problem=replace(w.problem, precision="fp64", storage="full"))
-    check(L, orc, w, 1e-10, 1e-12)
+        w = small_case(kind, n_paths=1001)
+    check(L, orc, with_pb(w, precision="fp64", storage="normals", ckpt_every=K, paths_per_thread=ppt),
+          1e-10, 1e-12)
 
 
-def test_full_storage_equals_recompute_fp32(L):
-    """Storing the tape or recomputing it gives the same E y and, to FP32 rounding of the
-    re-run segments, the same gradient."""
-    w = inputs.heston_config(n_paths=1 << 15, steps_per_year=64, T=2.0)
-    a = gpu_vg(L, w)
-    b = gpu_vg(L, replace(w, problem=replace(w.problem, storage="full")))
+@pytest.mark.parametrize("storage", STORED)
+@pytest.mark.parametrize("kind", ["heston", "lv", "slv"])
+def test_stored_equals_recompute_fp32(L, kind, storage):
+    """The stored variants run the same step arithmetic as checkpoint/recompute: the same
+    E y, and the gradient to FP32 rounding of the re-run segments."""
+    if kind == "heston":
+        w = inputs.heston_config(n_paths=1 << 15, steps_per_year=64, T=2.0)
+    elif kind == "lv":
+        w = inputs.lv_config(n_paths=1 << 14)
+    else:
+        w = inputs.slv_config(n_paths=1 << 14, steps_per_year=64, T=2.0)
+    a = gpu_vg(L, with_pb(w, storage="checkpoint"))
+    b = gpu_vg(L, with_pb(w, storage=storage))
     assert rel(a[0], b[0]) <= 1e-13
     assert rel(a[2], b[2]) <= 1e-5
+
+
+@pytest.mark.parametrize("n", [1, 33, 4097])
+def test_stored_normals_ragged_fp32(L, orc, n):
+    w = inputs.heston_config(n_paths=n, steps_per_year=16, T=1.0, n_mat=2, n_strike=3)
+    check(L, orc, with_pb(w, storage="normals"), 1e-4, 2e-6)
+
+
+def test_stored_normals_vjp_after_forward(L, orc):
+    """mc_forward with kept results, then mc_vjp, on the stored normals."""
+    w = with_pb(small_case("lv"), precision="fp64", storage="normals")
+    ctx = L.Context(w.problem, max_paths=w.n_paths)
+    Ey = ctx.forward(w.theta, w.problem.seed, w.n_paths, keep=True).cpu().numpy()
+    ybar = np.linspace(-1.0, 1.0, len(Ey))
+    g = ctx.vjp(ybar).cpu().numpy()
+    assert rel(Ey, orc.forward(w.problem, w.theta, w.n_paths)) <= 1e-12
+    assert rel(g, orc.vjp(w.problem, w.theta, ybar, w.n_paths)) <= 1e-10
+
+
+@pytest.mark.slow
+def test_heston_full_size_stored_normals(L, orc):
+    """The benchmark workload with stored normals (4.3 GB of them) vs the oracle."""
+    check(L, orc, with_pb(inputs.heston_config(), storage="normals"), 1e-4, 2e-6)
+
+
+def test_auto_storage_resolves(L):
+    """"auto" picks the stored normals when they fit a quarter of the device's memory."""
+    w = inputs.heston_config(n_paths=4096, steps_per_year=16, T=1.0, n_mat=2, n_strike=3)
+    assert L.Context(w.problem, max_paths=4096).storage == "normals"
+    for st in ("checkpoint", "normals", "full"):
+        assert L.Context(with_pb(w, storage=st).problem, max_paths=4096).storage == st
