@@ -278,10 +278,12 @@ struct WsLayout {
         part_y = take((size_t)grid_max * p.m * 8);
         part_g = take((size_t)grid_max * p.M * 8);
         const size_t real = p.precision == MC_FP64 ? 8 : 4;
+        // checkpoint tiles (SegTile): per path and segment, the state words and, with
+        // stored normals, the segment's K * dz normals; ckpt_stride covers whole chunks
         const bool full = p.storage == MC_STORAGE_FULL;
-        ckpt = take(full ? 0 : (size_t)p.n_seg * p.state_dim * ckpt_stride * real);
-        const size_t per_step = full ? p.tape_fields : p.storage == MC_STORAGE_NORMALS ? p.dz : 0;
-        tape = take((size_t)p.n_last * per_step * ckpt_stride * real);
+        const size_t per_seg = p.state_dim + (p.storage == MC_STORAGE_NORMALS ? (size_t)p.K * p.dz : 0);
+        ckpt = take(full ? 0 : (size_t)p.n_seg * per_seg * ckpt_stride * real);
+        tape = take(full ? (size_t)p.n_last * p.tape_fields * ckpt_stride * real : 0);
         xmat = take(full ? (size_t)p.n_groups * ckpt_stride * real : 0);
         total = o;
     }

@@ -41,10 +41,12 @@ __host__ __device__ inline RoundKeys philox_round_keys(uint64_t seed) {
 __device__ __forceinline__ uint4 philox4x32_10(uint4 c, const RoundKeys &rk) {
 #pragma unroll
     for (int round = 0; round < 10; ++round) {
-        const uint32_t lo0 = 0xD2511F53u * c.x;
-        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
-        const uint32_t lo1 = 0xCD9E8D57u * c.z;
-        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+        // both halves of each 32 x 32 -> 64-bit product from one wide multiply
+        uint64_t p0, p1;
+        asm("mul.wide.u32 %0, %1, %2;" : "=l"(p0) : "r"(c.x), "r"(0xD2511F53u));
+        asm("mul.wide.u32 %0, %1, %2;" : "=l"(p1) : "r"(c.z), "r"(0xCD9E8D57u));
+        const uint32_t lo0 = (uint32_t)p0, hi0 = (uint32_t)(p0 >> 32);
+        const uint32_t lo1 = (uint32_t)p1, hi1 = (uint32_t)(p1 >> 32);
         c = make_uint4(hi1 ^ c.y ^ rk.k[2 * round], lo1, hi0 ^ c.w ^ rk.k[2 * round + 1], lo0);
     }
     return c;
@@ -155,8 +157,8 @@ struct DevCall {
     RoundKeys rk;         // Philox round keys of seed
     uint64_t path0;       // first global path
     uint64_t n_paths;
-    void *ckpt;           // [n_seg][state_dim][ckpt_stride] of Real
-    uint64_t ckpt_stride; // paths padded to a multiple of 32
+    void *ckpt;           // per-(chunk, segment) tiles of checkpoints (+ normals): SegTile
+    uint64_t ckpt_stride; // paths padded to a multiple of 64 (full-storage tape stride)
     int keep_ckpt;
     double *part_y;       // [gridDim.x][m] per-block payoff sums (sorted order)
     double *part_g;       // [gridDim.x][M] per-block gradient sums

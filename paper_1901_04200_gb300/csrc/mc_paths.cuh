@@ -507,45 +507,44 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-// Reverse-sweep staging.  A warp's segment s needs the checkpoint of its
-// 32*PPT paths (SD * PPT rows of 32 consecutive paths) and, in the
-// stored-normals variant, the segment's normals (K * DZ * PPT rows): the
-// forward sweep then also writes every normal it draws, SoA
-// zt[(n * DZ + c) * stride + path] (one 128-byte line per warp, step and
-// component).  The warp copies segment s-1's rows into its half of a
-// two-buffer shared staging area while it works on segment s, so HBM latency
-// is paid once per chunk instead of once per segment.
+// What the forward sweep leaves for the reverse sweep, in tiles of one warp
+// chunk (32*PPT consecutive paths) and one segment: rows of 32 consecutive
+// paths (one 128-byte line in FP32), first -- in the stored-normals variant --
+// the segment's normals, row (i*DZ + c)*PPT + q for step i, component c,
+// path slot q, then the checkpoint (the state at the segment's start), row
+// RZ + w*PPT + q for state word w.  Tile (chunk, s) starts at
+// (s * n_chunks + chunk) * R * 32 elements (n_chunks: the chunks the
+// workspace holds; the warps of a sweep work on nearby segments, so their
+// tiles are close together), and every store and load of the tile is a
+// compile-time offset from one base.  The reverse sweep copies a
+// warp's tile of segment s-1 into its half of a two-buffer shared staging
+// area (same layout) while it works on segment s, so HBM latency is paid
+// once per chunk instead of once per segment.
 template <class Md, int K, int PPT, bool kZ>
-struct SegStage {
+struct SegTile {
     using Real = typename Md::Real;
     static constexpr int RZ = kZ ? K * Md::DZ * PPT : 0;           // normals rows
     static constexpr int R = RZ + Md::SD * PPT;                     // + checkpoint rows
-    static constexpr int kPerRow = kWarp * (int)sizeof(Real) / 16;  // 16-byte pieces per row
-    static constexpr size_t kWarpBytes = 2 * (size_t)R * kWarp * sizeof(Real);
+    static constexpr int kElems = R * kWarp;                        // elements per tile
+    static constexpr int kPieces = kElems * (int)sizeof(Real) / 16; // 16-byte pieces per tile
+    static constexpr size_t kWarpBytes = 2 * (size_t)kElems * sizeof(Real);
     static constexpr size_t kBlockBytes = kWarpBytes * kWarpsPerBlock;
     __device__ static constexpr int zrow(int i, int c, int q) { return (i * Md::DZ + c) * PPT + q; }
     __device__ static constexpr int crow(int w, int q) { return RZ + w * PPT + q; }
-    // Copy segment s of the chunk starting at path chunk0 into buffer (s & 1).
-    __device__ __forceinline__ static void issue(Real *stage, const Real *zt, const Real *ck, uint64_t stride,
-                                                 uint64_t chunk0, int s, int lane) {
+    __device__ __forceinline__ static Real *tile(void *base, uint64_t chunk, uint64_t n_chunks, int s) {
+        return (Real *)base + ((size_t)s * n_chunks + chunk) * kElems;
+    }
+    // Copy tile (chunk, s) into staging buffer (s & 1).
+    __device__ __forceinline__ static void issue(Real *stage, const void *base, uint64_t chunk, uint64_t n_chunks,
+                                                 int s, int lane) {
         __syncwarp();  // every lane is done with this buffer's previous segment
-        Real *buf = stage + (size_t)(s & 1) * R * kWarp;
+        Real *buf = stage + (size_t)(s & 1) * kElems;
+        const Real *src = tile(const_cast<void *>(base), chunk, n_chunks, s);
+        constexpr int kPer = 16 / (int)sizeof(Real);
 #pragma unroll
-        for (int p0 = 0; p0 < R * kPerRow; p0 += kWarp) {
+        for (int p0 = 0; p0 < kPieces; p0 += kWarp) {
             const int p = p0 + lane;
-            if (R * kPerRow % kWarp == 0 || p < R * kPerRow) {
-                const int r = p / kPerRow, part = p - r * kPerRow;
-                const size_t off = part * (16 / sizeof(Real));
-                const int q = r % PPT;  // path slot of the row (RZ is a multiple of PPT)
-                const Real *row;
-                if (r < RZ) {
-                    const int c = (r / PPT) % Md::DZ, i = r / (PPT * Md::DZ);
-                    row = zt + ((size_t)(s * K + i) * Md::DZ + c) * stride;
-                } else {
-                    row = ck + ((size_t)s * Md::SD + (r - RZ) / PPT) * stride;
-                }
-                cp_async16(buf + (size_t)r * kWarp + off, row + chunk0 + (size_t)q * kWarp + off);
-            }
+            if (kPieces % kWarp == 0 || p < kPieces) cp_async16(buf + p * kPer, src + p * kPer);
         }
         cp_async_commit();
     }
@@ -617,7 +616,7 @@ __global__ void __launch_bounds__(kBlock) path_forward_kernel(const DevProblem p
     const int warp = threadIdx.x / kWarp, lane = threadIdx.x % kWarp;
     double *wy = (double *)(smem + sp.wacc_y) + warp * pb.m;
     const Real S0 = (Real)pb.S0;
-    Real *ck = (Real *)cl.ckpt;
+    using TL = SegTile<Md, K, PPT, kStoreZ>;
     // Philox round keys: from the kernel parameters (constant bank), or formed
     // once per thread into registers, whichever measured faster for the model
     const RoundKeys rk = Md::kKeysInRegisters ? philox_round_keys(cl.seed) : cl.rk;
@@ -639,12 +638,12 @@ __global__ void __launch_bounds__(kBlock) path_forward_kernel(const DevProblem p
         }
         int g = 0;
         for (int s = 0; s < pb.n_seg; ++s) {
+            Real *tl = TL::tile(cl.ckpt, ch, cl.ckpt_stride / kChunk, s) + lane;
             if (cl.keep_ckpt) {
 #pragma unroll
                 for (int q = 0; q < PPT; ++q) {
-                    Real *c0 = ck + ((size_t)s * Md::SD) * cl.ckpt_stride + local[q];
-                    c0[0] = st[q].x;
-                    if constexpr (Md::SD == 2) c0[cl.ckpt_stride] = st[q].v;
+                    tl[TL::crow(0, q) * kWarp] = st[q].x;
+                    if constexpr (Md::SD == 2) tl[TL::crow(1, q) * kWarp] = st[q].v;
                 }
             }
 #pragma unroll
@@ -656,8 +655,7 @@ __global__ void __launch_bounds__(kBlock) path_forward_kernel(const DevProblem p
                     rng[q].get(n, i == 0, z, rk);
                     if constexpr (kStoreZ) {
 #pragma unroll
-                        for (int c = 0; c < Md::DZ; ++c)
-                            ((Real *)cl.tape)[((size_t)n * Md::DZ + c) * cl.ckpt_stride + local[q]] = z[c];
+                        for (int c = 0; c < Md::DZ; ++c) tl[TL::zrow(i, c, q) * kWarp] = z[c];
                     }
                     Md::step(st[q], z, n, par, sh, nullptr);
                 }
@@ -695,7 +693,7 @@ __global__ void __launch_bounds__(kBlock) path_forward_kernel(const DevProblem p
 template <class Md, int K, int PPT, bool kLoadZ = false>
 __global__ void __launch_bounds__(kBlock) path_reverse_kernel(const DevProblem pb, const DevCall cl) {
     using Real = typename Md::Real;
-    using ZS = SegStage<Md, K, PPT, kLoadZ>;
+    using ZS = SegTile<Md, K, PPT, kLoadZ>;
     extern __shared__ __align__(16) unsigned char smem[];
     const int n_steps = pb.n_seg * K;
     const SmemPlan sp(Md::kind, sizeof(Real), pb.m, pb.n_groups, pb.M, n_steps, pb.nx, true, ZS::kBlockBytes);
@@ -712,11 +710,9 @@ __global__ void __launch_bounds__(kBlock) path_reverse_kernel(const DevProblem p
     const int warp = threadIdx.x / kWarp, lane = threadIdx.x % kWarp;
     double *wg = (double *)(smem + sp.wacc_g) + warp * pb.M;
     const Real S0 = (Real)pb.S0;
-    const Real *ck = (const Real *)cl.ckpt;
     RoundKeys rk;
     if constexpr (!kLoadZ) rk = Md::kKeysInRegisters ? philox_round_keys(cl.seed) : cl.rk;
-    Real *zstage = (Real *)(smem + sp.zstage) + (size_t)warp * (ZS::kWarpBytes / sizeof(Real));
-    const Real *zt = (const Real *)cl.tape;
+    Real *zstage = (Real *)(smem + sp.zstage) + (size_t)warp * 2 * ZS::kElems;
 
     constexpr uint64_t kChunk = (uint64_t)kWarp * PPT;
     const uint64_t n_chunks = (cl.n_paths + kChunk - 1) / kChunk;
@@ -734,19 +730,19 @@ __global__ void __launch_bounds__(kBlock) path_reverse_kernel(const DevProblem p
             xb[q] = Real(0);
             vb[q] = Real(0);
         }
-        ZS::issue(zstage, zt, ck, cl.ckpt_stride, ch * kChunk, pb.n_seg - 1, lane);
+        ZS::issue(zstage, cl.ckpt, ch, cl.ckpt_stride / kChunk, pb.n_seg - 1, lane);
         typename Md::Acc acc;
         Md::acc_begin(acc, n_steps, sh);
         int g = pb.n_groups - 1;
         for (int s = pb.n_seg - 1; s >= 0; --s) {
             if (s > 0) {
-                ZS::issue(zstage, zt, ck, cl.ckpt_stride, ch * kChunk, s - 1, lane);
+                ZS::issue(zstage, cl.ckpt, ch, cl.ckpt_stride / kChunk, s - 1, lane);
                 cp_async_wait<1>();
             } else {
                 cp_async_wait<0>();
             }
             __syncwarp();  // the other lanes' copies of segment s are visible
-            const Real *sbuf = zstage + (size_t)(s & 1) * ZS::R * kWarp + lane;
+            const Real *sbuf = zstage + (size_t)(s & 1) * ZS::kElems + lane;
             typename Md::State st[PPT];
             typename Md::Tape tape[PPT][K];
 #pragma unroll
@@ -989,8 +985,8 @@ void set_kernels(Table *out) {
     out->rev_tape = (const void *)path_reverse_tape_kernel<Md, K, PPT>;
     out->fwd_z = (const void *)path_forward_kernel<Md, K, PPT, true>;
     out->rev_z = (const void *)path_reverse_kernel<Md, K, PPT, true>;
-    out->stage_bytes_ckpt = SegStage<Md, K, PPT, false>::kBlockBytes;
-    out->stage_bytes_z = SegStage<Md, K, PPT, true>::kBlockBytes;
+    out->stage_bytes_ckpt = SegTile<Md, K, PPT, false>::kBlockBytes;
+    out->stage_bytes_z = SegTile<Md, K, PPT, true>::kBlockBytes;
 }
 
 }  // namespace mcaad
