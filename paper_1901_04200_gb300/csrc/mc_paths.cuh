@@ -646,19 +646,25 @@ __global__ void __launch_bounds__(kBlock) path_forward_kernel(const DevProblem p
                     if constexpr (Md::SD == 2) tl[TL::crow(1, q) * kWarp] = st[q].v;
                 }
             }
+            // the segment's normals first: its Philox blocks are independent of the state, so
+            // the scheduler can overlap them; then the K dependent Euler steps
+            Real zs[K][PPT][Md::DZ];
 #pragma unroll
             for (int i = 0; i < K; ++i) {
                 const int n = s * K + i;
 #pragma unroll
                 for (int q = 0; q < PPT; ++q) {
-                    Real z[Md::DZ];
-                    rng[q].get(n, i == 0, z, rk);
+                    rng[q].get(n, i == 0, zs[i][q], rk);
                     if constexpr (kStoreZ) {
 #pragma unroll
-                        for (int c = 0; c < Md::DZ; ++c) tl[TL::zrow(i, c, q) * kWarp] = z[c];
+                        for (int c = 0; c < Md::DZ; ++c) tl[TL::zrow(i, c, q) * kWarp] = zs[i][q][c];
                     }
-                    Md::step(st[q], z, n, par, sh, nullptr);
                 }
+            }
+#pragma unroll
+            for (int i = 0; i < K; ++i) {
+#pragma unroll
+                for (int q = 0; q < PPT; ++q) Md::step(st[q], zs[i][q], s * K + i, par, sh, nullptr);
             }
             if (g < pb.n_groups && gseg[g] == s) {
                 Real S[PPT];
