@@ -16,6 +16,7 @@ sweep) are NCCL all-gathers of m + 1 and M + 1 numbers.
 from __future__ import annotations
 
 import argparse
+from dataclasses import replace
 import json
 import math
 import os
@@ -52,6 +53,11 @@ UNIT = "path-steps/s"
 OPS = {"heston": {"F": {"fp32": 22, "mufu": 5, "int": 24}, "step": {"fp32": 13, "mufu": 1}, "R": {"fp32": 17}},
        "lv": {"F": {"fp32": 21, "mufu": 2, "int": 12}, "step": {"fp32": 16}, "R": {"fp32": 24}},
        "slv": {"F": {"fp32": 34, "mufu": 5, "int": 24}, "step": {"fp32": 25, "mufu": 1}, "R": {"fp32": 40}}}
+# Forward-mode tangents of the Heston step (mc_value_and_grad_tangent), per path-step on top of
+# F: shared factors 10 FP32 (the 1{v>0} dt select; the x and v coefficients of d vdt, 2 + 2; the
+# explicit derivatives in kappa, xi, rho, 1 + 1 + 3) and per parameter j the chain d vdt_j, dx_j,
+# dv_j (3), plus the explicit term for j < 4 (1): 10 + 5 x 3 + 4 = 29.
+OPS_TANGENT = {"heston": {"fp32": 29}}
 # What each path kernel runs per path-step, by storage mode.
 KERNEL_PARTS = {"checkpoint": {"forward_sweep": ["F"], "reverse_sweep": ["F", "R"]},
                 "normals": {"forward_sweep": ["F"], "reverse_sweep": ["step", "R"]},
@@ -102,6 +108,62 @@ def measured_traffic(model, storage, k, ppt, kernel):
     if rec and rec["sources"] == kernel_sources_hash():
         return rec["bytes"]
     return None
+
+
+def kernel_rooflines(model, storage, K, ppt, P, S, n_groups, prof, issue_peak, hbm_peak, peak_src, n_sm,
+                     sm_mhz_peak):
+    """Per path kernel: achieved algorithmic ops and bytes per second (CUDA-event durations from
+    the context's profile) against the issue-rate and HBM peaks; the roofline entry of the JSON
+    line for the kernel with the longest time, with the bound of the larger fraction."""
+    if storage == "tangent":
+        table = {"tangent_sweep": (sum(OPS[model]["F"].values()) + sum(OPS_TANGENT[model].values()),
+                                   OPS[model]["F"]["fp32"] + OPS_TANGENT[model]["fp32"], 0.0)}
+    else:
+        by = kernel_bytes(model, storage, K, S, n_groups)
+        table = {k: (kernel_ops(model, storage, k), kernel_ops(model, storage, k, "fp32"), by[k])
+                 for k in ("forward_sweep", "reverse_sweep")}
+    kern = {}
+    for kname, (ops, ops32, byts) in table.items():
+        ms, n = prof[kname]
+        t = ms / max(n, 1) * 1e-3
+        a_ops, a_bytes = P * S * ops / t, P * S * byts / t
+        kern[kname] = {"ms": t * 1e3, "ops_per_path_step": ops, "bytes_per_path_step": byts,
+                       "alu_frac": a_ops / issue_peak, "hbm_frac": a_bytes / hbm_peak,
+                       "alu_tops": a_ops / 1e12, "hbm_gbs": a_bytes / 1e9,
+                       "fp32_frac": P * S * ops32 / t / issue_peak}
+    dom = max(kern, key=lambda k: kern[k]["ms"])
+    d = kern[dom]
+    hbm_bound = d["hbm_frac"] > d["alu_frac"]
+    return {"bound": "hbm" if hbm_bound else "alu",
+            "achieved": d["hbm_gbs"] if hbm_bound else d["alu_tops"],
+            "peak": hbm_peak / 1e9 if hbm_bound else issue_peak / 1e12,
+            "unit": "GB/s" if hbm_bound else "Tops/s",
+            "frac": d["hbm_frac"] if hbm_bound else d["alu_frac"],
+            "traffic": measured_traffic(model, storage, K, ppt, dom),
+            "algorithmic_bytes": P * S * d["bytes_per_path_step"],
+            "kernel": "%s (%s, %s, K=%d, %d paths/thread)" % (dom, model, storage if storage == "tangent"
+                                                               else storage + " storage", K, ppt),
+            "peak_basis": ("measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs, %s)" % peak_src) if hbm_bound
+                          else "SM issue rate 128 thread-ops/clk x %d SMs x %.0f MHz (%s max clock)"
+                               % (n_sm, sm_mhz_peak, peak_src),
+            "kernels": kern}
+
+
+def time_arm(ctx, step, steps, stream):
+    """ms per step (CUDA events on the launching stream, 3 warm-up steps) and the context's
+    per-kernel profile."""
+    import torch
+    for _ in range(3):
+        step()
+    torch.cuda.synchronize()
+    ctx.profile_begin(8 * steps)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps, ctx.profile_end()
 
 
 def load_peaks():
@@ -353,6 +415,8 @@ def main():
                     help="heston (the metric's workload), lv (2^22 x 500 local vol) or surrogate "
                          "(one differential-loss training step of the pricing network), for measurement")
     ap.add_argument("--no-calibration", action="store_true", help="skip the surrogate vs plain calibration")
+    ap.add_argument("--no-arms", action="store_true",
+                    help="skip the recompute and forward-mode comparison arms")
     ap.add_argument("--calib-cases", type=int, default=4)
     ap.add_argument("--ckpt", type=int, default=0, help="checkpoint interval (0 = workload default)")
     ap.add_argument("--storage", default="auto", choices=["auto", "checkpoint", "normals", "full"],
@@ -468,34 +532,14 @@ def main():
     storage = ctx.storage
     K = pb.ckpt_every
     ppt = pb.paths_per_thread or (2 if model == "heston" else 1)
-    bytes_ps = kernel_bytes(model, storage, K, S, len(set(np.asarray(pb.mat_step).tolist())))
-    kern = {}
-    for kname in ("forward_sweep", "reverse_sweep"):
-        ms, n = prof[kname]
-        t = ms / max(n, 1) * 1e-3
-        ops = kernel_ops(model, storage, kname)
-        a_ops, a_bytes = P * S * ops / t, P * S * bytes_ps[kname] / t
-        kern[kname] = {"ms": t * 1e3, "ops_per_path_step": ops, "bytes_per_path_step": bytes_ps[kname],
-                       "alu_frac": a_ops / issue_peak, "hbm_frac": a_bytes / hbm_peak,
-                       "alu_tops": a_ops / 1e12, "hbm_gbs": a_bytes / 1e9,
-                       "fp32_frac": P * S * kernel_ops(model, storage, kname, "fp32") / t / issue_peak}
-    dom = max(kern, key=lambda k: kern[k]["ms"])
-    d = kern[dom]
-    hbm_bound = d["hbm_frac"] > d["alu_frac"]
-    roofline = {"bound": "hbm" if hbm_bound else "alu",
-                "achieved": d["hbm_gbs"] if hbm_bound else d["alu_tops"],
-                "peak": hbm_peak / 1e9 if hbm_bound else issue_peak / 1e12,
-                "unit": "GB/s" if hbm_bound else "Tops/s",
-                "frac": d["hbm_frac"] if hbm_bound else d["alu_frac"],
-                "traffic": measured_traffic(model, storage, K, ppt, dom),
-                "algorithmic_bytes": P * S * bytes_ps[dom],
-                "kernel": "%s (%s, %s storage, K=%d, %d paths/thread)" % (dom, model, storage, K, ppt),
-                "peak_basis": ("measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs, %s)" % peak_src) if hbm_bound
-                              else "SM issue rate 128 thread-ops/clk x %d SMs x %.0f MHz (%s max clock)"
-                                   % (n_sm, sm_mhz_peak, peak_src),
-                "kernels": kern}
+    n_groups = len(set(np.asarray(pb.mat_step).tolist()))
+    bytes_ps = kernel_bytes(model, storage, K, S, n_groups)
+    roof_args = (P, S, n_groups)
+    peak_args = (issue_peak, hbm_peak, peak_src, n_sm, sm_mhz_peak)
+    roofline = kernel_rooflines(model, storage, K, ppt, *roof_args, prof, *peak_args)
     launches = sum(n for _, n in prof.values())
 
+    line = {}
     if rank == 0:
         line = {
             "metric": METRIC if model == "heston" else METRIC.replace(
@@ -518,6 +562,29 @@ def main():
                     "h2d_bytes_per_step": 8 * (ctx.M + ctx.m), "d2h_bytes_per_step": 8 * (1 + ctx.M + ctx.m)},
             "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"]},
         }
+    if world == 1 and not args.no_arms:
+        # the same workload by the design that regenerates the normals and recomputes every
+        # segment (checkpoints only), and for Heston by forward-mode tangents (no reverse sweep)
+        arms = {}
+        if storage != "checkpoint":
+            ctx_r = _lib.Context(replace(pb, storage="checkpoint"), max_paths=P, device=dev)
+            ms_r, prof_r = time_arm(ctx_r, lambda: ctx_r.value_and_grad(theta, C, seed, P, path0=path0, out=out),
+                                    args.steps, stream)
+            arms["recompute_arm"] = {"ms_per_step": ms_r, "value": P * S / (ms_r * 1e-3), "unit": UNIT,
+                                     "storage": "checkpoint",
+                                     "roofline": kernel_rooflines(model, "checkpoint", K, ppt, *roof_args, prof_r,
+                                                                  *peak_args)}
+            del ctx_r
+        if model == "heston":
+            ms_t, prof_t = time_arm(ctx, lambda: ctx.value_and_grad_tangent(theta, C, seed, P, path0=path0,
+                                                                            out=out), args.steps, stream)
+            arms["tangent_arm"] = {"ms_per_step": ms_t, "value": P * S / (ms_t * 1e-3), "unit": UNIT,
+                                   "method": "forward-mode tangents, grad G = J^T lambda",
+                                   "roofline": kernel_rooflines(model, "tangent", K, 1, *roof_args, prof_t,
+                                                                *peak_args)}
+        if rank == 0:
+            line.update(arms)
+    if rank == 0:
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline(w, args.cpu_paths if model == "heston" else args.cpu_paths // 4)
         if not args.no_calibration and world == 1 and model == "heston":

@@ -212,6 +212,23 @@ mc_status mc_price_jacobian(mc_ctx *ctx, const double *thetas, const double *str
                             uint64_t seed, uint64_t n_paths, double *Ey_out, double *J_out, void *scratch,
                             size_t scratch_bytes, void *stream);
 
+/* G and grad G by forward-mode tangents instead of the reverse sweep (Heston
+ * contexts, M = 5): one sweep over global paths [path0, path0 + n_paths) of
+ * `seed` carries d(x, v)/d theta_j along each path and gives E y_i and
+ * J_ij = d E y_i / d theta_j; then lambda = E y - C, G = 1/2 |lambda|^2
+ * (eq. 241118A) and grad G = J^T lambda (the gradient identity, with the
+ * expectation taken per instrument before the contraction with lambda).  The
+ * same estimator as mc_value_and_grad (same paths, normals and kink
+ * conventions); its cost grows with M where the adjoint's does not, and it
+ * stores nothing for a reverse sweep (so mc_vjp does not follow it).
+ * theta, grad_out: FP64 [M]; C: FP64 [m]; G_out: FP64 [1]; Ey_out: FP64 [m]
+ * or NULL; scratch: device buffer of mc_value_and_grad_tangent_scratch_size
+ * bytes, 256-byte aligned. */
+mc_status mc_value_and_grad_tangent_scratch_size(mc_ctx *ctx, uint64_t n_paths, size_t *bytes_out);
+mc_status mc_value_and_grad_tangent(mc_ctx *ctx, const double *theta, const double *C, uint64_t seed,
+                                    uint64_t path0, uint64_t n_paths, double *G_out, double *grad_out,
+                                    double *Ey_out, void *scratch, size_t scratch_bytes, void *stream);
+
 /* The tensor-core GEMM used by the pricing surrogate, as a plain operation:
  * D[s][M][N] (row stride ldd, slice stride M*ldd) = A[:, s*k_slice .. +k_slice)
  * B[:, same]^T for s < K / k_slice, with A [M][lda] and B [N][ldb] BF16 (K
@@ -271,13 +288,14 @@ mc_status mc_normals_fill(uint64_t seed, uint64_t path0, uint32_t n_paths, uint3
  * every kernel the context launches (no counterpart in the paper; it measures
  * the terms of eq. 0711C).  Kernel ids: MC_K_FORWARD (forward sweep),
  * MC_K_FINALIZE_Y (E y / lambda / G), MC_K_SEED (mc_vjp seeds),
- * MC_K_REVERSE (reverse sweep), MC_K_FINALIZE_G (grad G).
+ * MC_K_REVERSE (reverse sweep), MC_K_FINALIZE_G (grad G), MC_K_TANGENT and
+ * MC_K_FINALIZE_T (mc_value_and_grad_tangent).
  * mc_profile_begin creates events for up to max_launches launches (host
  * call).  mc_profile_end waits for the recorded events, writes the summed
  * milliseconds and launch counts per kernel id into ms_out[MC_N_KERNELS] and
  * launches_out[MC_N_KERNELS] (either may be NULL), and stops recording. */
 enum { MC_K_FORWARD = 0, MC_K_FINALIZE_Y = 1, MC_K_SEED = 2, MC_K_REVERSE = 3, MC_K_FINALIZE_G = 4,
-       MC_N_KERNELS = 5 };
+       MC_K_TANGENT = 5, MC_K_FINALIZE_T = 6, MC_N_KERNELS = 7 };
 mc_status mc_profile_begin(mc_ctx *ctx, int32_t max_launches);
 mc_status mc_profile_end(mc_ctx *ctx, double *ms_out, int32_t *launches_out);
 

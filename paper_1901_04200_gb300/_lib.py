@@ -77,6 +77,8 @@ SIGNATURES = [
     ("mc_forward_static", ctypes.c_int, [_P(mc_model), _P(mc_instruments), _V, _U64, _U64, _U64, _V, _V]),
     ("mc_price_jacobian_scratch_size", ctypes.c_int, [_V, _I32, _U64, _P(_SZ)]),
     ("mc_price_jacobian", ctypes.c_int, [_V, _V, _V, _I32, _U64, _U64, _V, _V, _V, _SZ, _V]),
+    ("mc_value_and_grad_tangent_scratch_size", ctypes.c_int, [_V, _U64, _P(_SZ)]),
+    ("mc_value_and_grad_tangent", ctypes.c_int, [_V, _V, _V, _U64, _U64, _U64, _V, _V, _V, _V, _SZ, _V]),
     ("mc_tc_gemm_bf16", ctypes.c_int, [_V, ctypes.c_int64, _V, ctypes.c_int64, _I32, _I32, _I32, _I32, _V,
                                        ctypes.c_int64, _V, _V]),
     ("mlp_n_params", ctypes.c_int64, []),
@@ -90,7 +92,8 @@ SIGNATURES = [
                                      ctypes.c_float, _V]),
     ("mlp_error_flag", ctypes.c_int, [_V, _P(_I32)]),
 ]
-KERNEL_NAMES = ["forward_sweep", "finalize_y", "seed", "reverse_sweep", "finalize_grad"]
+KERNEL_NAMES = ["forward_sweep", "finalize_y", "seed", "reverse_sweep", "finalize_grad", "tangent_sweep",
+                "finalize_tangent"]  # mc_profile kernel ids 0 .. MC_N_KERNELS-1
 
 
 def load():
@@ -237,6 +240,33 @@ class Context:
         self._theta_keep = th
         return G, grad, Ey
 
+    def value_and_grad_tangent(self, theta, C, seed: int, n_paths: int, path0: int = 0, with_ey: bool = True,
+                               stream=None, out=None):
+        """(G [1], grad G [M], E y [m] or None) by forward-mode tangents (mc_value_and_grad_tangent)."""
+        th = self._f64(theta, self.M)
+        Ct = self._f64(C, self.m)
+        if out is None:
+            G = torch.empty(1, dtype=torch.float64, device=self.device)
+            grad = torch.empty(self.M, dtype=torch.float64, device=self.device)
+            Ey = torch.empty(self.m, dtype=torch.float64, device=self.device) if with_ey else None
+        else:
+            G, grad, Ey = out
+        nbytes = ctypes.c_size_t(0)
+        _check(load().mc_value_and_grad_tangent_scratch_size(self.handle, int(n_paths), ctypes.byref(nbytes)),
+               self.handle)
+        key = int(nbytes.value)
+        if getattr(self, "_tan_scratch", None) is None or self._tan_scratch[0] < key:
+            buf = torch.empty(key + 256, dtype=torch.uint8, device=self.device)
+            self._tan_scratch = (key, buf)
+        buf = self._tan_scratch[1]
+        base = (buf.data_ptr() + 255) // 256 * 256
+        _check(load().mc_value_and_grad_tangent(self.handle, _ptr(th), _ptr(Ct), int(seed), int(path0),
+                                                int(n_paths), _ptr(G), _ptr(grad),
+                                                _ptr(Ey) if Ey is not None else None, ctypes.c_void_p(base),
+                                                key, _stream(stream)), self.handle)
+        self._theta_keep = (th, Ct)
+        return G, grad, Ey
+
     def price_jacobian(self, thetas, seed: int, n_paths: int, strikes=None, stream=None):
         """(E y [n_theta, m], J [n_theta, m, 5]) by forward-mode tangents (mc_price_jacobian)."""
         th = torch.as_tensor(thetas, dtype=torch.float64, device=self.device).reshape(-1, self.M).contiguous()
@@ -261,10 +291,11 @@ class Context:
 
     def profile_end(self):
         """{kernel name: (total ms, launches)} for the launches since profile_begin."""
-        ms = (ctypes.c_double * 5)()
-        n = (ctypes.c_int32 * 5)()
+        nk = len(KERNEL_NAMES)
+        ms = (ctypes.c_double * nk)()
+        n = (ctypes.c_int32 * nk)()
         _check(load().mc_profile_end(self.handle, ms, n), self.handle)
-        return {KERNEL_NAMES[k]: (ms[k], n[k]) for k in range(5)}
+        return {KERNEL_NAMES[k]: (ms[k], n[k]) for k in range(nk)}
 
     def sync(self, stream=None):
         _check(load().mc_sync(self.handle, _stream(stream)), self.handle)

@@ -766,9 +766,19 @@ mc_status mc_profile_end(mc_ctx *ctx, double *ms_out, int32_t *launches_out) {
 
 // Blocks per parameter vector: one when there are enough vectors to fill the
 // GPU, otherwise enough to give it about four blocks per SM.
+// Blocks per parameter vector: enough for every SM to hold as many blocks as
+// fit (few vectors: one vector fills the GPU), at most one per 128 paths.
 static int jacobian_bpt(const mc_ctx *ctx, int n_theta, uint64_t n_paths) {
     const uint64_t chunks = (n_paths + kWarp - 1) / kWarp;
-    const uint64_t target = (uint64_t)ctx->n_sm * 4;
+    int occ = 0;
+    const size_t smem = jacobian_smem_bytes(ctx->m, ctx->n_groups, ctx->precision);
+    if (cudaFuncSetAttribute(jacobian_kernel(ctx->precision), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, jacobian_kernel(ctx->precision), kBlock, smem) !=
+            cudaSuccess ||
+        occ < 1)
+        occ = 4;
+    const uint64_t target = (uint64_t)ctx->n_sm * occ;
     uint64_t bpt = (target + n_theta - 1) / (uint64_t)n_theta;
     const uint64_t cap = (chunks + kWarpsPerBlock - 1) / kWarpsPerBlock;
     if (bpt > cap) bpt = cap;
@@ -802,9 +812,56 @@ mc_status mc_price_jacobian(mc_ctx *ctx, const double *thetas, const double *str
                                          (int)smem);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "jacobian shared memory");
     cudaStream_t st = (cudaStream_t)stream;
-    e = launch_jacobian(ctx->pb, ctx->precision, thetas, strikes, n_theta, seed, n_paths, bpt, smem,
+    e = launch_jacobian(ctx->pb, ctx->precision, thetas, strikes, n_theta, seed, 0, n_paths, bpt, smem,
                         (double *)scratch, ctx->pb.disc, ctx->pb.perm, Ey_out, J_out, st);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "jacobian launch");
+    return MC_OK;
+}
+
+// Scratch of mc_value_and_grad_tangent: the jacobian's per-block sums, then
+// E y [m] and J [m][5] (256-byte aligned pieces).
+static size_t tangent_scratch(mc_ctx *ctx, uint64_t n_paths, size_t *off_ey, size_t *off_j) {
+    size_t part = 0;
+    mc_price_jacobian_scratch_size(ctx, 1, n_paths, &part);
+    *off_ey = align_up(part, 256);
+    *off_j = align_up(*off_ey + (size_t)ctx->m * 8, 256);
+    return align_up(*off_j + (size_t)ctx->m * 5 * 8, 256);
+}
+
+mc_status mc_value_and_grad_tangent_scratch_size(mc_ctx *ctx, uint64_t n_paths, size_t *bytes_out) {
+    if (!ctx || !bytes_out || n_paths == 0) return MC_ERR_INVALID_ARG;
+    size_t a, b;
+    *bytes_out = tangent_scratch(ctx, n_paths, &a, &b);
+    return MC_OK;
+}
+
+mc_status mc_value_and_grad_tangent(mc_ctx *ctx, const double *theta, const double *C, uint64_t seed,
+                                    uint64_t path0, uint64_t n_paths, double *G_out, double *grad_out,
+                                    double *Ey_out, void *scratch, size_t scratch_bytes, void *stream) {
+    if (!ctx) return MC_ERR_INVALID_ARG;
+    if (ctx->kind != kHeston) return fail(ctx, MC_ERR_UNSUPPORTED, "forward-mode tangents are built for the Heston model");
+    mc_status s = check_call(ctx, theta, path0, n_paths);
+    if (s != MC_OK) return s;
+    if (!C || !G_out || !grad_out || !scratch || !aligned8(C) || !aligned8(G_out) || !aligned8(grad_out) ||
+        (Ey_out && !aligned8(Ey_out)) || ((uintptr_t)scratch & 255u))
+        return fail(ctx, MC_ERR_INVALID_ARG, "C, G_out, grad_out must be FP64 device pointers, scratch 256-byte aligned");
+    size_t off_ey, off_j;
+    const size_t need = tangent_scratch(ctx, n_paths, &off_ey, &off_j);
+    if (scratch_bytes < need) return fail(ctx, MC_ERR_INVALID_ARG, "scratch needs %zu bytes", need);
+    unsigned char *sc = (unsigned char *)scratch;
+    double *Ey = Ey_out ? Ey_out : (double *)(sc + off_ey);
+    double *J = (double *)(sc + off_j);
+    const int bpt = jacobian_bpt(ctx, 1, n_paths);
+    const size_t smem = jacobian_smem_bytes(ctx->m, ctx->n_groups, ctx->precision);
+    cudaStream_t st = (cudaStream_t)stream;
+    ctx->have_ckpt = false;
+    cudaError_t e = timed(ctx, MC_K_TANGENT, st, [&] {
+        return launch_jacobian(ctx->pb, ctx->precision, theta, nullptr, 1, seed, path0, n_paths, bpt, smem,
+                               (double *)sc, ctx->pb.disc, ctx->pb.perm, Ey, J, st);
+    });
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "tangent sweep launch");
+    e = timed(ctx, MC_K_FINALIZE_T, st, [&] { return launch_tangent_finalize(Ey, J, C, ctx->m, G_out, grad_out, st); });
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "tangent finalize launch");
     return MC_OK;
 }
 

@@ -44,8 +44,10 @@ cudaError_t launch_normals_fill(uint64_t seed, uint64_t path0, uint32_t n_paths,
 size_t jacobian_smem_bytes(int m, int n_groups, int precision);
 const void *jacobian_kernel(int precision);
 cudaError_t launch_jacobian(const DevProblem &pb, int precision, const double *thetas, const double *strikes_t,
-                            int n_theta, uint64_t seed, uint64_t n_paths, int bpt, size_t smem,
+                            int n_theta, uint64_t seed, uint64_t path0, uint64_t n_paths, int bpt, size_t smem,
                             double *part, const double *disc, const int *perm, double *Ey_out,
                             double *J_out, cudaStream_t st);
+cudaError_t launch_tangent_finalize(const double *Ey, const double *J, const double *C, int m, double *G_out,
+                                    double *grad_out, cudaStream_t st);
 
 }  // namespace mcaad

@@ -11,8 +11,8 @@
 // d max(v,0)/dv = 1{v > 0}, the tangent of sqrt(v+ dt) is 0 when v <= 0, the
 // payoff derivative is 1{S > K}.
 //
-// Paths of parameter vector t are the global paths [t P, (t+1) P) with the
-// call's seed, so different t draw independent normals.  Grid (bpt, n_theta):
+// Paths of parameter vector t are the global paths path0 + [t P, (t+1) P)
+// with the call's seed, so different t draw independent normals.  Grid (bpt, n_theta):
 // block (b, t) walks warps over 32-path chunks of its slice of theta t's
 // paths and leaves FP64 sums of y_i and of dy_i/dtheta_j per block
 // (warp sums in the path precision, FP64 above the warp, no atomics).
@@ -26,8 +26,8 @@ constexpr int kJacM = 5;  // Heston parameters (kappa, theta_h, xi, rho, v0)
 template <typename Real>
 __global__ void __launch_bounds__(kBlock)
 heston_jacobian_kernel(const DevProblem pb, const double *__restrict__ thetas,
-                       const double *__restrict__ strikes_t, const RoundKeys rk, uint64_t n_paths,
-                       int bpt, double *__restrict__ out) {
+                       const double *__restrict__ strikes_t, const RoundKeys rk, uint64_t path0,
+                       uint64_t n_paths, int bpt, double *__restrict__ out) {
     // out: [n_theta][bpt][m][1 + M] sums (y, then dy/dtheta_j)
     extern __shared__ __align__(16) unsigned char smem[];
     const int m = pb.m;
@@ -63,7 +63,7 @@ heston_jacobian_kernel(const DevProblem pb, const double *__restrict__ thetas,
         const uint64_t local = ch * kWarp + lane;
         const bool active = local < n_paths;
         PathNormals<Real> rng;
-        rng.init((uint64_t)t * n_paths + (active ? local : 0));
+        rng.init(path0 + (uint64_t)t * n_paths + (active ? local : 0));
         Real x = Real(0), v = v0;
         Real dx[kJacM], dv[kJacM];
 #pragma unroll
@@ -162,13 +162,13 @@ const void *jacobian_kernel(int precision) {
 }
 
 cudaError_t launch_jacobian(const DevProblem &pb, int precision, const double *thetas, const double *strikes_t,
-                            int n_theta, uint64_t seed, uint64_t n_paths, int bpt, size_t smem,
+                            int n_theta, uint64_t seed, uint64_t path0, uint64_t n_paths, int bpt, size_t smem,
                             double *part, const double *disc, const int *perm, double *Ey_out,
                             double *J_out, cudaStream_t st) {
     const void *fn = jacobian_kernel(precision);
     const RoundKeys rk = philox_round_keys(seed);
-    void *args[] = {(void *)&pb, (void *)&thetas, (void *)&strikes_t, (void *)&rk, (void *)&n_paths,
-                    (void *)&bpt, (void *)&part};
+    void *args[] = {(void *)&pb, (void *)&thetas, (void *)&strikes_t, (void *)&rk, (void *)&path0,
+                    (void *)&n_paths, (void *)&bpt, (void *)&part};
     cudaError_t e = cudaLaunchKernel(fn, dim3(bpt, n_theta), dim3(kBlock), args, smem, st);
     if (e != cudaSuccess) return e;
     const uint64_t total = (uint64_t)n_theta * (1 + kJacM) * pb.m;
@@ -176,6 +176,34 @@ cudaError_t launch_jacobian(const DevProblem &pb, int precision, const double *t
     if (grid > 65536) grid = 65536;
     jacobian_finalize_kernel<<<grid, 256, 0, st>>>(part, n_theta, bpt, pb.m, disc, perm, 1.0 / (double)n_paths,
                                                   Ey_out, J_out);
+    return cudaGetLastError();
+}
+
+// G and its gradient from E y and the Jacobian of one parameter vector (the
+// gradient identity with the expectation taken per instrument first):
+// lambda_i = E y_i - C_i, G = 1/2 sum_i lambda_i^2 (eq. 241118A),
+// dG/dtheta_j = sum_i lambda_i dE y_i/dtheta_j.  One warp; each sum runs over
+// i in order.
+__global__ void tangent_finalize_kernel(const double *__restrict__ Ey, const double *__restrict__ J,
+                                        const double *__restrict__ C, int m, double *G_out, double *grad_out) {
+    const int j = threadIdx.x;
+    if (j < kJacM) {
+        double g = 0.0;
+        for (int i = 0; i < m; ++i) g += (Ey[i] - C[i]) * J[(size_t)i * kJacM + j];
+        grad_out[j] = g;
+    } else if (j == kJacM) {
+        double G = 0.0;
+        for (int i = 0; i < m; ++i) {
+            const double l = Ey[i] - C[i];
+            G += l * l;
+        }
+        *G_out = 0.5 * G;
+    }
+}
+
+cudaError_t launch_tangent_finalize(const double *Ey, const double *J, const double *C, int m, double *G_out,
+                                    double *grad_out, cudaStream_t st) {
+    tangent_finalize_kernel<<<1, kWarp, 0, st>>>(Ey, J, C, m, G_out, grad_out);
     return cudaGetLastError();
 }
 

@@ -77,3 +77,38 @@ def test_jacobian_many_thetas_fp32(L, orc):
         assert rel(Ey[t], Eo) <= 2e-6
         gi = orc.vjp(pbt, thetas[t], np.eye(pb.m)[10], n, path0=t * n)
         assert rel(J[t, 10], gi) <= 1e-4
+
+
+# ------------------------------------- G and grad G by forward-mode tangents
+
+@pytest.mark.parametrize("path0", [0, 12345])
+def test_tangent_value_and_grad_fp64_matches_oracle(L, orc, path0):
+    """mc_value_and_grad_tangent = the oracle's two-step G and grad G on the same paths."""
+    w = inputs.heston_config(n_paths=2001, steps_per_year=32, T=1.0, n_mat=4, n_strike=5)
+    pb = replace(w.problem, precision="fp64")
+    ctx = L.Context(pb, max_paths=w.n_paths)
+    G, g, Ey = ctx.value_and_grad_tangent(w.theta, w.C, pb.seed, w.n_paths, path0=path0)
+    Eo, Go, go = orc.value_and_grad(pb, w.theta, w.C, w.n_paths, path0=path0)
+    assert rel(Ey.cpu().numpy(), Eo) <= 1e-12
+    assert abs(G.item() - Go) <= 1e-10 * abs(Go)
+    assert rel(g.cpu().numpy(), go) <= 1e-10
+
+
+def test_tangent_equals_adjoint_fp32(L):
+    """Forward mode and the adjoint give the same estimator: E y to FP32 summation order,
+    the gradient to FP32 rounding of the path arithmetic."""
+    w = inputs.heston_config(n_paths=1 << 16, steps_per_year=64, T=2.0)
+    ctx = L.Context(w.problem, max_paths=w.n_paths)
+    Ga, ga, Ea = [t.cpu().numpy() for t in ctx.value_and_grad(w.theta, w.C, w.problem.seed, w.n_paths)]
+    Gt, gt, Et = [t.cpu().numpy() for t in ctx.value_and_grad_tangent(w.theta, w.C, w.problem.seed, w.n_paths)]
+    assert rel(Et, Ea) <= 1e-6
+    assert rel(gt, ga) <= 1e-4
+    assert abs(Gt[0] - Ga[0]) <= 1e-4 * abs(Ga[0])
+
+
+def test_tangent_rejects_other_models(L):
+    w = inputs.lv_config(n_paths=64, n_steps=100, T=2.0, nt=5, nx=6, n_mat=4, n_strike=5)
+    ctx = L.Context(w.problem, max_paths=64)
+    with pytest.raises(L.McError) as e:
+        ctx.value_and_grad_tangent(w.theta, w.C, w.problem.seed, 64)
+    assert e.value.status == L.MC_ERR_UNSUPPORTED
