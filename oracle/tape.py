@@ -93,6 +93,10 @@ def exp(a: Var) -> Var:
     return a.t._push(e, [(a.idx, e)])
 
 
+def log(a: Var) -> Var:
+    return a.t._push(np.log(a.v), [(a.idx, 1.0 / a.v)])
+
+
 def sqrt(a: Var) -> Var:
     s = np.sqrt(a.v)
     with np.errstate(divide="ignore"):

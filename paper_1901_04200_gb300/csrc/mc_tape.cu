@@ -1,0 +1,724 @@
+// mc_tape.cu -- expected-backward AD of a whole Monte-Carlo program on the
+// GPU (arXiv 1901.04200, Appendix, after Fries).  The program, the rule and
+// the stage structure are described in include/mctape.h.
+//
+// Host plan.  Each node is deterministic (DET) or per-path (PATH).  PARAM and
+// CONST are DET, NORMAL is PATH, an expectation of a PATH node is DET (an
+// expectation of a DET node is the node itself), any other op is PATH if an
+// argument is.  A node's stage is the latest stage at which its arguments
+// are available; an expectation belongs to the stage of its argument and is
+// available from the next one.  Per stage the order det-nodes -> path-nodes
+// -> expectations is topological, so the forward sweep runs per stage
+//   det_forward (one thread) -> path_forward (one thread per path, values to
+//   the tape, per-warp sums of the expectations' arguments) -> expect_finalize
+// and the backward sweep runs the stages in reverse, per stage
+//   path_backward (adds E(D) of each expectation to its argument's per-path
+//   adjoint, then the per-path nodes in reverse; per-warp sums of the
+//   adjoint contributions to deterministic arguments) -> darg_finalize (their
+//   means) -> det_backward (one thread, the deterministic nodes in reverse;
+//   a parameter's adjoint mean is its gradient).
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "mc_common.cuh"
+#include "mctape.h"
+
+using namespace mcaad;
+
+namespace {
+
+constexpr int kMaxNodes = 1 << 24;
+constexpr int kMaxStageSums = 2048;  // expectations, or distinct DET arguments, per stage
+
+// Device form of a node.  References to values: r >= 0 is row r of the
+// per-path tape, r < 0 is deterministic slot -r-1.  la, lb: index of a DET
+// argument among the stage's accumulated DET arguments (backward), -1 else.
+struct DevNode {
+    int op;
+    int ra, rb, rm;
+    int la, lb;
+    double c;
+};
+
+struct StagePlan {
+    std::vector<int> det, path, expect;  // node indices, program order
+    std::vector<int> dargs;              // DET nodes used by the stage's PATH nodes (first use order)
+};
+
+struct TapePlan {
+    int n_nodes = 0, objective = 0, n_params = 0, n_stages = 0, n_rows = 0, n_det = 0;
+    int max_exp = 0, max_darg = 0;
+    std::vector<int> cls;    // 0 DET, 1 PATH
+    std::vector<int> stage;  // stage where the node is computed
+    std::vector<int> ref;    // row (PATH) or -slot-1 (DET)
+    std::vector<StagePlan> st;
+};
+
+__host__ __device__ inline int n_args(int op) {
+    switch (op) {
+    case MC_OP_PARAM:
+    case MC_OP_CONST:
+    case MC_OP_NORMAL:
+        return 0;
+    case MC_OP_ADD:
+    case MC_OP_SUB:
+    case MC_OP_MUL:
+    case MC_OP_DIV:
+        return 2;
+    default:
+        return 1;
+    }
+}
+
+mc_status make_tape_plan(const mc_tape_node *nodes, int n, int objective, int n_params, TapePlan &p,
+                         std::string &why) {
+    char buf[256];
+    auto bad = [&](mc_status s, const char *fmt, ...) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        why = buf;
+        return s;
+    };
+    if (!nodes || n < 1) return bad(MC_ERR_INVALID_ARG, "empty program");
+    if (n > kMaxNodes) return bad(MC_ERR_UNSUPPORTED, "more than %d nodes", kMaxNodes);
+    if (objective < 0 || objective >= n) return bad(MC_ERR_INVALID_ARG, "objective %d outside the program", objective);
+    if (n_params < 0) return bad(MC_ERR_INVALID_ARG, "negative parameter count");
+    p = TapePlan();
+    p.n_nodes = n;
+    p.objective = objective;
+    p.n_params = n_params;
+    p.cls.assign(n, 0);
+    p.stage.assign(n, 0);
+    p.ref.assign(n, 0);
+    std::vector<int> avail(n, 0);
+    for (int i = 0; i < n; ++i) {
+        const mc_tape_node &d = nodes[i];
+        if (d.op < 0 || d.op >= MC_N_OPS) return bad(MC_ERR_INVALID_ARG, "node %d: unknown op %d", i, d.op);
+        const int na = n_args(d.op);
+        const int args[2] = {d.a, d.b};
+        for (int q = 0; q < 2; ++q) {
+            if (q < na) {
+                if (args[q] < 0 || args[q] >= i)
+                    return bad(MC_ERR_INVALID_ARG, "node %d: argument %d does not precede it", i, args[q]);
+            } else if (args[q] != -1) {
+                return bad(MC_ERR_INVALID_ARG, "node %d: op %d takes %d arguments", i, d.op, na);
+            }
+        }
+        if (d.op == MC_OP_PARAM && !(d.c >= 0 && d.c < n_params && d.c == floor(d.c)))
+            return bad(MC_ERR_INVALID_ARG, "node %d: parameter index %g outside [0, %d)", i, d.c, n_params);
+        if (d.op == MC_OP_NORMAL && !(d.c >= 0 && d.c < 4294967296.0 * 4.0 && d.c == floor(d.c)))
+            return bad(MC_ERR_INVALID_ARG, "node %d: bad normal index %g", i, d.c);
+        if (!std::isfinite(d.c)) return bad(MC_ERR_INVALID_ARG, "node %d: non-finite constant", i);
+        if (d.op == MC_OP_PARAM || d.op == MC_OP_CONST) {
+            p.cls[i] = 0;
+            p.stage[i] = avail[i] = 0;
+        } else if (d.op == MC_OP_NORMAL) {
+            p.cls[i] = 1;
+            p.stage[i] = avail[i] = 0;
+        } else if (d.op == MC_OP_EXPECT) {
+            p.cls[i] = 0;
+            if (p.cls[d.a] == 0) {  // E of a deterministic value: the value itself
+                p.stage[i] = avail[i] = avail[d.a];
+            } else {
+                p.stage[i] = p.stage[d.a];
+                avail[i] = p.stage[d.a] + 1;
+            }
+        } else {
+            int cls = 0, s = 0;
+            for (int q = 0; q < na; ++q) {
+                cls |= p.cls[args[q]];
+                s = std::max(s, avail[args[q]]);
+            }
+            p.cls[i] = cls;
+            p.stage[i] = avail[i] = s;
+        }
+    }
+    if (p.cls[objective] != 0) return bad(MC_ERR_INVALID_ARG, "the objective (node %d) is not deterministic", objective);
+    int ns = 1;
+    for (int i = 0; i < n; ++i) ns = std::max(ns, p.stage[i] + 1);
+    p.n_stages = ns;
+    p.st.assign(ns, StagePlan());
+    for (int i = 0; i < n; ++i) {
+        StagePlan &sp = p.st[p.stage[i]];
+        if (p.cls[i] == 1) {
+            p.ref[i] = p.n_rows++;
+            sp.path.push_back(i);
+        } else {
+            p.ref[i] = -(p.n_det++) - 1;
+            const bool exp_of_path = nodes[i].op == MC_OP_EXPECT && p.cls[nodes[i].a] == 1;
+            (exp_of_path ? sp.expect : sp.det).push_back(i);
+        }
+    }
+    for (int s = 0; s < ns; ++s) {
+        StagePlan &sp = p.st[s];
+        for (int i : sp.path) {
+            const int args[2] = {nodes[i].a, nodes[i].b};
+            for (int q = 0; q < n_args(nodes[i].op); ++q)
+                if (p.cls[args[q]] == 0 && std::find(sp.dargs.begin(), sp.dargs.end(), args[q]) == sp.dargs.end())
+                    sp.dargs.push_back(args[q]);
+        }
+        if ((int)sp.expect.size() > kMaxStageSums)
+            return bad(MC_ERR_UNSUPPORTED, "stage %d has %zu expectations (limit %d)", s, sp.expect.size(), kMaxStageSums);
+        if ((int)sp.dargs.size() > kMaxStageSums)
+            return bad(MC_ERR_UNSUPPORTED, "stage %d uses %zu deterministic values per path (limit %d)", s,
+                       sp.dargs.size(), kMaxStageSums);
+        p.max_exp = std::max(p.max_exp, (int)sp.expect.size());
+        p.max_darg = std::max(p.max_darg, (int)sp.dargs.size());
+    }
+    return MC_OK;
+}
+
+// Device node lists: per stage [det | path | expect] blocks, flattened.
+struct DevLists {
+    std::vector<DevNode> all;
+    std::vector<int> det_off, path_off, exp_off, darg_off;  // per stage, + 1 end entry each
+    std::vector<int> darg_slot;                              // flattened: DET slot of each accumulated argument
+};
+
+DevLists make_lists(const mc_tape_node *nodes, const TapePlan &p) {
+    DevLists L;
+    auto dev = [&](int i, const StagePlan *sp) {
+        DevNode d;
+        d.op = nodes[i].op;
+        d.c = nodes[i].c;
+        d.rm = p.ref[i];
+        d.ra = nodes[i].a >= 0 ? p.ref[nodes[i].a] : 0;
+        d.rb = nodes[i].b >= 0 ? p.ref[nodes[i].b] : 0;
+        d.la = d.lb = -1;
+        if (sp) {
+            auto local = [&](int arg) {
+                if (arg < 0 || p.cls[arg] == 1) return -1;
+                return (int)(std::find(sp->dargs.begin(), sp->dargs.end(), arg) - sp->dargs.begin());
+            };
+            d.la = local(nodes[i].a);
+            d.lb = local(nodes[i].b);
+        }
+        return d;
+    };
+    for (int s = 0; s < p.n_stages; ++s) {
+        const StagePlan &sp = p.st[s];
+        L.det_off.push_back((int)L.all.size());
+        for (int i : sp.det) L.all.push_back(dev(i, nullptr));
+        L.path_off.push_back((int)L.all.size());
+        for (int i : sp.path) L.all.push_back(dev(i, &sp));
+        L.exp_off.push_back((int)L.all.size());
+        for (int i : sp.expect) L.all.push_back(dev(i, nullptr));
+        L.darg_off.push_back((int)L.darg_slot.size());
+        for (int i : sp.dargs) L.darg_slot.push_back(-p.ref[i] - 1);
+    }
+    L.det_off.push_back((int)L.all.size());
+    L.path_off.push_back((int)L.all.size());
+    L.exp_off.push_back((int)L.all.size());
+    L.darg_off.push_back((int)L.darg_slot.size());
+    return L;
+}
+
+inline size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+struct TapeWs {
+    size_t nodes, dslot, det, ddet, part, tape, adj, total;
+    TapeWs(const TapePlan &p, size_t n_all, size_t n_dslot, int grid, uint64_t stride) {
+        size_t o = 0;
+        auto take = [&](size_t bytes) {
+            size_t at = o;
+            o = round_up(o + bytes, 256);
+            return at;
+        };
+        nodes = take(n_all * sizeof(DevNode));
+        dslot = take(n_dslot * 4 + 4);
+        det = take((size_t)p.n_det * 8);
+        ddet = take((size_t)p.n_det * 8);
+        part = take((size_t)grid * std::max(1, std::max(p.max_exp, p.max_darg)) * 8);
+        tape = take((size_t)p.n_rows * stride * 8);
+        adj = take((size_t)p.n_rows * stride * 8);
+        total = o;
+    }
+};
+
+// ------------------------------------------------------------- kernels ----
+
+__device__ __forceinline__ double ld(const double *tape, const double *det, int r, uint64_t stride, uint64_t p) {
+    return r >= 0 ? tape[(size_t)r * stride + p] : det[-r - 1];
+}
+
+__device__ __forceinline__ double apply_op(int op, double a, double b, double c) {
+    switch (op) {
+    case MC_OP_ADD: return a + b;
+    case MC_OP_SUB: return a - b;
+    case MC_OP_MUL: return a * b;
+    case MC_OP_DIV: return a / b;
+    case MC_OP_ADDC: return a + c;
+    case MC_OP_MULC: return a * c;
+    case MC_OP_NEG: return -a;
+    case MC_OP_EXP: return exp(a);
+    case MC_OP_LOG: return log(a);
+    case MC_OP_SQRT: return sqrt(a);
+    case MC_OP_RELU: return a > 0.0 ? a : 0.0;
+    case MC_OP_ABS: return fabs(a);
+    default: return a;  // EXPECT of a deterministic value
+    }
+}
+
+// Partial derivatives of node value m = op(a, b) with respect to a and b.
+__device__ __forceinline__ void partials(int op, double a, double b, double m, double c, double &pa, double &pb) {
+    pa = 0.0;
+    pb = 0.0;
+    switch (op) {
+    case MC_OP_ADD: pa = 1.0; pb = 1.0; break;
+    case MC_OP_SUB: pa = 1.0; pb = -1.0; break;
+    case MC_OP_MUL: pa = b; pb = a; break;
+    case MC_OP_DIV: pa = 1.0 / b; pb = -a / (b * b); break;
+    case MC_OP_ADDC: pa = 1.0; break;
+    case MC_OP_MULC: pa = c; break;
+    case MC_OP_NEG: pa = -1.0; break;
+    case MC_OP_EXP: pa = m; break;
+    case MC_OP_LOG: pa = 1.0 / a; break;
+    case MC_OP_SQRT: pa = a > 0.0 ? 0.5 / m : 0.0; break;
+    case MC_OP_RELU: pa = a > 0.0 ? 1.0 : 0.0; break;
+    case MC_OP_ABS: pa = a > 0.0 ? 1.0 : (a < 0.0 ? -1.0 : 0.0); break;
+    case MC_OP_EXPECT: pa = 1.0; break;  // of a deterministic value: identity
+    default: break;
+    }
+}
+
+// Deterministic nodes of a stage, in program order (one thread).
+__global__ void tape_det_forward(const DevNode *__restrict__ nd, int n, const double *__restrict__ theta,
+                                 double *__restrict__ det) {
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    for (int k = 0; k < n; ++k) {
+        const DevNode d = nd[k];
+        double v;
+        if (d.op == MC_OP_PARAM) {
+            v = theta[(int)d.c];
+        } else if (d.op == MC_OP_CONST) {
+            v = d.c;
+        } else {
+            const double a = det[-d.ra - 1];
+            const double b = n_args(d.op) == 2 ? det[-d.rb - 1] : 0.0;
+            v = apply_op(d.op, a, b, d.c);
+        }
+        det[-d.rm - 1] = v;
+    }
+}
+
+// Per-path nodes of a stage, one thread per path; then per-warp FP64 sums of
+// the expectations' arguments (warp shuffle in FP64, lane k%32 adds), per
+// block in warp order -> part[block][k].
+__global__ void __launch_bounds__(kBlock) tape_path_forward(const DevNode *__restrict__ nd, int n,
+                                                            const DevNode *__restrict__ ex, int n_exp,
+                                                            const double *__restrict__ det, double *__restrict__ tape,
+                                                            uint64_t stride, RoundKeys rk, uint64_t path0,
+                                                            uint64_t n_paths, double *__restrict__ part) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    double *wacc = (double *)smem;  // [kWarpsPerBlock][n_exp]
+    for (int q = threadIdx.x; q < kWarpsPerBlock * n_exp; q += blockDim.x) wacc[q] = 0.0;
+    __syncthreads();
+    const int warp = threadIdx.x / kWarp, lane = threadIdx.x % kWarp;
+    const uint64_t chunks = (n_paths + kWarp - 1) / kWarp;
+    for (uint64_t ch = (uint64_t)blockIdx.x * kWarpsPerBlock + warp; ch < chunks;
+         ch += (uint64_t)gridDim.x * kWarpsPerBlock) {
+        const uint64_t p = ch * kWarp + lane;
+        const bool active = p < n_paths;
+        PathNormals<double> rng;
+        rng.init(path0 + (active ? p : 0));
+        uint64_t last_call = ~0ull;
+        for (int k = 0; k < n; ++k) {
+            const DevNode d = nd[k];
+            double v;
+            if (d.op == MC_OP_NORMAL) {
+                const uint64_t j = (uint64_t)d.c;
+                if ((j >> 2) != last_call) {
+                    last_call = j >> 2;
+                    rng.fill((uint32_t)last_call, rk);
+                }
+                v = rng.pick((uint32_t)(j & 3u));
+            } else {
+                const double a = ld(tape, det, d.ra, stride, p);
+                const double b = n_args(d.op) == 2 ? ld(tape, det, d.rb, stride, p) : 0.0;
+                v = apply_op(d.op, a, b, d.c);
+            }
+            tape[(size_t)d.rm * stride + p] = v;
+        }
+        double *wrow = wacc + warp * n_exp;
+        for (int k0 = 0; k0 < n_exp; k0 += kWarp) {
+            const int cnt = min(kWarp, n_exp - k0);
+            double mine = 0.0;
+            for (int j = 0; j < cnt; ++j) {
+                const double v = active ? tape[(size_t)ex[k0 + j].ra * stride + p] : 0.0;
+                const double s = warp_sum(v);
+                mine = lane == j ? s : mine;
+            }
+            if (lane < cnt) wrow[k0 + lane] += mine;
+        }
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < n_exp; k += blockDim.x) {
+        double s = 0.0;
+        for (int w = 0; w < kWarpsPerBlock; ++w) s += wacc[w * n_exp + k];
+        part[(size_t)blockIdx.x * n_exp + k] = s;
+    }
+}
+
+// Expectation k = (sum over blocks in order) / n.
+__global__ void tape_expect_finalize(const double *__restrict__ part, int nb, const DevNode *__restrict__ ex,
+                                     int n_exp, double inv_n, double *__restrict__ det) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n_exp; k += gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int b = 0; b < nb; ++b) s += part[(size_t)b * n_exp + k];
+        det[-ex[k].rm - 1] = s * inv_n;
+    }
+}
+
+// Backward sweep of a stage's per-path nodes: first E(D) of each expectation
+// into its argument's adjoint, then the nodes in reverse; contributions to
+// deterministic arguments are warp-summed into per-warp accumulators.
+__global__ void __launch_bounds__(kBlock) tape_path_backward(const DevNode *__restrict__ nd, int n,
+                                                             const DevNode *__restrict__ ex, int n_exp, int n_darg,
+                                                             const double *__restrict__ det,
+                                                             const double *__restrict__ ddet,
+                                                             const double *__restrict__ tape, double *__restrict__ adj,
+                                                             uint64_t stride, uint64_t n_paths,
+                                                             double *__restrict__ part) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    double *wacc = (double *)smem;  // [kWarpsPerBlock][n_darg]
+    for (int q = threadIdx.x; q < kWarpsPerBlock * n_darg; q += blockDim.x) wacc[q] = 0.0;
+    __syncthreads();
+    const int warp = threadIdx.x / kWarp, lane = threadIdx.x % kWarp;
+    double *wrow = wacc + warp * n_darg;
+    const uint64_t chunks = (n_paths + kWarp - 1) / kWarp;
+    for (uint64_t ch = (uint64_t)blockIdx.x * kWarpsPerBlock + warp; ch < chunks;
+         ch += (uint64_t)gridDim.x * kWarpsPerBlock) {
+        const uint64_t p = ch * kWarp + lane;
+        const bool active = p < n_paths;
+        if (active)
+            for (int k = 0; k < n_exp; ++k) adj[(size_t)ex[k].ra * stride + p] += ddet[-ex[k].rm - 1];
+        for (int k = n - 1; k >= 0; --k) {
+            const DevNode d = nd[k];
+            if (d.op == MC_OP_NORMAL) continue;
+            const double D = active ? adj[(size_t)d.rm * stride + p] : 0.0;
+            const bool two = n_args(d.op) == 2;
+            // only the values the op's partials need (the op is the same on every lane)
+            const bool need_ab = d.op == MC_OP_MUL || d.op == MC_OP_DIV;
+            const bool need_a = need_ab || d.op == MC_OP_LOG || d.op == MC_OP_SQRT || d.op == MC_OP_RELU ||
+                                d.op == MC_OP_ABS;
+            const double a = need_a ? ld(tape, det, d.ra, stride, p) : 0.0;
+            const double b = need_ab ? ld(tape, det, d.rb, stride, p) : 0.0;
+            const double m = (d.op == MC_OP_EXP || d.op == MC_OP_SQRT) ? tape[(size_t)d.rm * stride + p] : 0.0;
+            double pa, pb;
+            partials(d.op, a, b, m, d.c, pa, pb);
+            const double ga = active ? D * pa : 0.0, gb = active ? D * pb : 0.0;
+            if (d.ra >= 0) {
+                if (active) adj[(size_t)d.ra * stride + p] += ga;
+            } else {
+                const double s = warp_sum(ga);
+                if (lane == 0) wrow[d.la] += s;
+            }
+            if (two) {
+                if (d.rb >= 0) {
+                    if (active) adj[(size_t)d.rb * stride + p] += gb;
+                } else {
+                    const double s = warp_sum(gb);
+                    if (lane == 0) wrow[d.lb] += s;
+                }
+            }
+        }
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < n_darg; k += blockDim.x) {
+        double s = 0.0;
+        for (int w = 0; w < kWarpsPerBlock; ++w) s += wacc[w * n_darg + k];
+        part[(size_t)blockIdx.x * n_darg + k] = s;
+    }
+}
+
+// Adjoint means of the stage's deterministic arguments: += (sum over blocks in order) / n.
+__global__ void tape_darg_finalize(const double *__restrict__ part, int nb, const int *__restrict__ slot,
+                                   int n_darg, double inv_n, double *__restrict__ ddet) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n_darg; k += gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int b = 0; b < nb; ++b) s += part[(size_t)b * n_darg + k];
+        ddet[slot[k]] += s * inv_n;
+    }
+}
+
+// Deterministic nodes of a stage in reverse (one thread); a parameter's
+// adjoint mean is added to its gradient component.
+__global__ void tape_det_backward(const DevNode *__restrict__ nd, int n, const double *__restrict__ det,
+                                  double *__restrict__ ddet, double *__restrict__ grad) {
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    for (int k = n - 1; k >= 0; --k) {
+        const DevNode d = nd[k];
+        const double D = ddet[-d.rm - 1];
+        if (d.op == MC_OP_PARAM) {
+            grad[(int)d.c] += D;
+            continue;
+        }
+        if (d.op == MC_OP_CONST) continue;
+        const bool two = n_args(d.op) == 2;
+        const double a = det[-d.ra - 1];
+        const double b = two ? det[-d.rb - 1] : 0.0;
+        double pa, pb;
+        partials(d.op, a, b, det[-d.rm - 1], d.c, pa, pb);
+        ddet[-d.ra - 1] += D * pa;
+        if (two) ddet[-d.rb - 1] += D * pb;
+    }
+}
+
+__global__ void tape_begin_backward(double *__restrict__ ddet, int n_det, int obj_slot, double *__restrict__ grad,
+                                    int n_params) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n_det; k += gridDim.x * blockDim.x)
+        ddet[k] = k == obj_slot ? 1.0 : 0.0;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n_params; k += gridDim.x * blockDim.x) grad[k] = 0.0;
+}
+
+__global__ void tape_copy_value(const double *__restrict__ det, int slot, double *__restrict__ out) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) *out = det[slot];
+}
+
+}  // namespace
+
+struct mc_tape {
+    int device = 0;
+    TapePlan plan;
+    DevLists lists;
+    int grid = 1, n_sm = 1;
+    uint64_t max_paths = 0, stride = 0;
+    size_t smem_fwd = 0, smem_bwd = 0;
+    bool owns_ws = false;
+    unsigned char *ws = nullptr;
+    DevNode *nodes = nullptr;
+    int *dslot = nullptr;
+    double *det = nullptr, *ddet = nullptr, *part = nullptr, *tape = nullptr, *adj = nullptr;
+    uint64_t last_n = 0;
+    std::string err;
+};
+
+namespace {
+
+mc_status tfail(mc_tape *t, mc_status st, const char *fmt, ...) __attribute__((format(printf, 3, 4)));
+mc_status tfail(mc_tape *t, mc_status st, const char *fmt, ...) {
+    if (t) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        t->err = buf;
+    }
+    return st;
+}
+
+uint64_t tape_stride(uint64_t max_paths) { return (max_paths + kWarp - 1) / kWarp * kWarp; }
+
+// Blocks: (resident blocks per SM) x SMs of the heavier path kernel, capped at
+// one block per 4 chunks of 32 paths.
+mc_status tape_launch_shape(int device, const TapePlan &p, uint64_t max_paths, int *grid, int *n_sm,
+                            size_t *smem_fwd, size_t *smem_bwd, std::string &why) {
+    cudaError_t e = cudaDeviceGetAttribute(n_sm, cudaDevAttrMultiProcessorCount, device);
+    if (e != cudaSuccess) {
+        why = cudaGetErrorString(e);
+        return MC_ERR_CUDA;
+    }
+    *smem_fwd = (size_t)kWarpsPerBlock * p.max_exp * 8;
+    *smem_bwd = (size_t)kWarpsPerBlock * p.max_darg * 8;
+    int occ_f = 0, occ_b = 0;
+    e = cudaFuncSetAttribute(tape_path_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem_fwd);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(tape_path_backward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem_bwd);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_f, tape_path_forward, kBlock, *smem_fwd);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_b, tape_path_backward, kBlock, *smem_bwd);
+    if (e != cudaSuccess) {
+        why = cudaGetErrorString(e);
+        return MC_ERR_CUDA;
+    }
+    const int occ = std::max(1, std::min(occ_f, occ_b));
+    const uint64_t want = ((max_paths + kWarp - 1) / kWarp + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    *grid = (int)std::min<uint64_t>((uint64_t)occ * *n_sm, std::max<uint64_t>(want, 1));
+    return MC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+mc_status mc_tape_plan(const mc_tape_node *nodes, int32_t n_nodes, int32_t objective, int32_t n_params,
+                       uint64_t max_paths, int32_t *n_stages, int32_t *n_path_nodes, size_t *workspace) {
+    TapePlan p;
+    std::string why;
+    mc_status st = make_tape_plan(nodes, n_nodes, objective, n_params, p, why);
+    if (st != MC_OK) {
+        fprintf(stderr, "mc_tape_plan: %s\n", why.c_str());
+        return st;
+    }
+    if (n_stages) *n_stages = p.n_stages;
+    if (n_path_nodes) *n_path_nodes = p.n_rows;
+    if (workspace) {
+        if (max_paths == 0) return MC_ERR_INVALID_ARG;
+        // the grid is bounded by one block per 128 paths and by 32 resident blocks on each of 1024 SMs
+        const uint64_t blocks = std::min<uint64_t>((max_paths + kBlock - 1) / kBlock, 32u * 1024u);
+        const DevLists L = make_lists(nodes, p);
+        *workspace = TapeWs(p, L.all.size(), L.darg_slot.size(), (int)blocks, tape_stride(max_paths)).total;
+    }
+    return MC_OK;
+}
+
+mc_status mc_tape_create(int device, const mc_tape_node *nodes, int32_t n_nodes, int32_t objective,
+                         int32_t n_params, uint64_t max_paths, void *workspace, size_t workspace_bytes,
+                         mc_tape **out) {
+    if (!out || max_paths == 0) return MC_ERR_INVALID_ARG;
+    *out = nullptr;
+    mc_tape *t = new (std::nothrow) mc_tape();
+    if (!t) return MC_ERR_OOM;
+    std::string why;
+    mc_status st = make_tape_plan(nodes, n_nodes, objective, n_params, t->plan, why);
+    if (st != MC_OK) {
+        fprintf(stderr, "mc_tape_create: %s\n", why.c_str());
+        delete t;
+        return st;
+    }
+    cudaError_t e = cudaSetDevice(device);
+    if (e != cudaSuccess) {
+        delete t;
+        return MC_ERR_CUDA;
+    }
+    t->device = device;
+    t->max_paths = max_paths;
+    t->stride = tape_stride(max_paths);
+    t->lists = make_lists(nodes, t->plan);
+    st = tape_launch_shape(device, t->plan, max_paths, &t->grid, &t->n_sm, &t->smem_fwd, &t->smem_bwd, why);
+    if (st != MC_OK) {
+        fprintf(stderr, "mc_tape_create: %s\n", why.c_str());
+        delete t;
+        return st;
+    }
+    const uint64_t blocks_cap = std::min<uint64_t>((max_paths + kBlock - 1) / kBlock, 32u * 1024u);
+    if ((uint64_t)t->grid > blocks_cap) t->grid = (int)std::max<uint64_t>(blocks_cap, 1);
+    TapeWs W(t->plan, t->lists.all.size(), t->lists.darg_slot.size(), (int)std::max<uint64_t>(blocks_cap, 1),
+             t->stride);
+    if (workspace) {
+        if (workspace_bytes < W.total || ((uintptr_t)workspace & 255u)) {
+            fprintf(stderr, "mc_tape_create: workspace needs %zu bytes, 256-byte aligned\n", W.total);
+            delete t;
+            return MC_ERR_INVALID_ARG;
+        }
+        t->ws = (unsigned char *)workspace;
+    } else {
+        e = cudaMalloc((void **)&t->ws, W.total);
+        if (e != cudaSuccess) {
+            fprintf(stderr, "mc_tape_create: cudaMalloc(%zu): %s\n", W.total, cudaGetErrorString(e));
+            delete t;
+            return e == cudaErrorMemoryAllocation ? MC_ERR_OOM : MC_ERR_CUDA;
+        }
+        t->owns_ws = true;
+    }
+    t->nodes = (DevNode *)(t->ws + W.nodes);
+    t->dslot = (int *)(t->ws + W.dslot);
+    t->det = (double *)(t->ws + W.det);
+    t->ddet = (double *)(t->ws + W.ddet);
+    t->part = (double *)(t->ws + W.part);
+    t->tape = (double *)(t->ws + W.tape);
+    t->adj = (double *)(t->ws + W.adj);
+    e = cudaMemcpy(t->nodes, t->lists.all.data(), t->lists.all.size() * sizeof(DevNode), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !t->lists.darg_slot.empty())
+        e = cudaMemcpy(t->dslot, t->lists.darg_slot.data(), t->lists.darg_slot.size() * 4, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        fprintf(stderr, "mc_tape_create: upload: %s\n", cudaGetErrorString(e));
+        mc_tape_destroy(t);
+        return MC_ERR_CUDA;
+    }
+    *out = t;
+    return MC_OK;
+}
+
+void mc_tape_destroy(mc_tape *t) {
+    if (!t) return;
+    cudaSetDevice(t->device);
+    if (t->owns_ws && t->ws) cudaFree(t->ws);
+    delete t;
+}
+
+const char *mc_tape_last_error(const mc_tape *t) { return t ? t->err.c_str() : "null tape"; }
+
+mc_status mc_tape_value_and_grad(mc_tape *t, const double *theta, uint64_t seed, uint64_t path0,
+                                 uint64_t n_paths, double *value_out, double *grad_out, void *stream) {
+    if (!t) return MC_ERR_INVALID_ARG;
+    const TapePlan &p = t->plan;
+    if (n_paths == 0 || n_paths > t->max_paths)
+        return tfail(t, MC_ERR_INVALID_ARG, "n_paths=%llu outside [1, max_paths=%llu]", (unsigned long long)n_paths,
+                     (unsigned long long)t->max_paths);
+    if ((p.n_params > 0 && (!theta || ((uintptr_t)theta & 7u))) || !value_out || !grad_out ||
+        ((uintptr_t)value_out & 7u) || ((uintptr_t)grad_out & 7u))
+        return tfail(t, MC_ERR_INVALID_ARG, "theta, value_out and grad_out must be FP64 device pointers");
+    if (path0 + n_paths < path0) return tfail(t, MC_ERR_INVALID_ARG, "path range overflows");
+    cudaStream_t st = (cudaStream_t)stream;
+    const DevLists &L = t->lists;
+    const RoundKeys rk = philox_round_keys(seed);
+    const double inv_n = 1.0 / (double)n_paths;
+    const uint64_t want = ((n_paths + kWarp - 1) / kWarp + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    const int grid = (int)std::min<uint64_t>((uint64_t)t->grid, want);
+    auto ck = [&](const char *what) -> mc_status {
+        const cudaError_t e = cudaGetLastError();
+        return e == cudaSuccess ? MC_OK : tfail(t, MC_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+    };
+    // ---- forward sweep
+    for (int s = 0; s < p.n_stages; ++s) {
+        const int nd = L.path_off[s] - L.det_off[s], np = L.exp_off[s] - L.path_off[s];
+        const int ne = L.det_off[s + 1] - L.exp_off[s];
+        if (nd > 0) tape_det_forward<<<1, 1, 0, st>>>(t->nodes + L.det_off[s], nd, theta, t->det);
+        if (np > 0 || ne > 0)
+            tape_path_forward<<<grid, kBlock, (size_t)kWarpsPerBlock * ne * 8, st>>>(
+                t->nodes + L.path_off[s], np, t->nodes + L.exp_off[s], ne, t->det, t->tape, t->stride, rk, path0,
+                n_paths, t->part);
+        if (ne > 0)
+            tape_expect_finalize<<<(ne + 127) / 128, 128, 0, st>>>(t->part, grid, t->nodes + L.exp_off[s], ne, inv_n,
+                                                                  t->det);
+        mc_status r = ck("forward sweep");
+        if (r != MC_OK) return r;
+    }
+    tape_copy_value<<<1, 1, 0, st>>>(t->det, -p.ref[p.objective] - 1, value_out);
+    // ---- backward sweep
+    if (p.n_rows > 0) {
+        const cudaError_t e = cudaMemsetAsync(t->adj, 0, (size_t)p.n_rows * t->stride * 8, st);
+        if (e != cudaSuccess) return tfail(t, MC_ERR_CUDA, "adjoint reset: %s", cudaGetErrorString(e));
+    }
+    tape_begin_backward<<<(std::max(p.n_det, p.n_params) + 255) / 256 + 1, 256, 0, st>>>(
+        t->ddet, p.n_det, -p.ref[p.objective] - 1, grad_out, p.n_params);
+    for (int s = p.n_stages - 1; s >= 0; --s) {
+        const int nd = L.path_off[s] - L.det_off[s], np = L.exp_off[s] - L.path_off[s];
+        const int ne = L.det_off[s + 1] - L.exp_off[s];
+        const int na = L.darg_off[s + 1] - L.darg_off[s];
+        if (np > 0 || ne > 0)
+            tape_path_backward<<<grid, kBlock, (size_t)kWarpsPerBlock * na * 8, st>>>(
+                t->nodes + L.path_off[s], np, t->nodes + L.exp_off[s], ne, na, t->det, t->ddet, t->tape, t->adj,
+                t->stride, n_paths, t->part);
+        if (na > 0)
+            tape_darg_finalize<<<(na + 127) / 128, 128, 0, st>>>(t->part, grid, t->dslot + L.darg_off[s], na, inv_n,
+                                                                t->ddet);
+        if (nd > 0) tape_det_backward<<<1, 1, 0, st>>>(t->nodes + L.det_off[s], nd, t->det, t->ddet, grad_out);
+        mc_status r = ck("backward sweep");
+        if (r != MC_OK) return r;
+    }
+    t->last_n = n_paths;
+    return MC_OK;
+}
+
+mc_status mc_tape_path_values(mc_tape *t, int32_t node, double *out, void *stream) {
+    if (!t) return MC_ERR_INVALID_ARG;
+    if (node < 0 || node >= t->plan.n_nodes || t->plan.cls[node] != 1 || !out)
+        return tfail(t, MC_ERR_INVALID_ARG, "node %d is not a per-path node", node);
+    if (t->last_n == 0) return tfail(t, MC_ERR_STATE, "no evaluation yet");
+    const cudaError_t e = cudaMemcpyAsync(out, t->tape + (size_t)t->plan.ref[node] * t->stride, t->last_n * 8,
+                                          cudaMemcpyDeviceToDevice, (cudaStream_t)stream);
+    return e == cudaSuccess ? MC_OK : tfail(t, MC_ERR_CUDA, "copy: %s", cudaGetErrorString(e));
+}
+
+}  // extern "C"

@@ -1,0 +1,134 @@
+"""Expected-backward AD on the GPU (include/mctape.h) against the oracle.
+
+The oracle's whole-program tape (oracle/tape.py, the Appendix's rule in FP64
+numpy) differentiates the same program on the same normals; for the Heston
+calibration objective the two-step algorithm (the oracle's C path, and the
+GPU's mc_value_and_grad) gives the same G and gradient (the gradient identity)."""
+from dataclasses import replace
+
+import numpy as np
+import pytest
+
+from paper_1901_04200_gb300 import inputs
+
+import tape_programs as TP
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def T():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1901_04200_gb300 import build as b
+    b.build()
+    from paper_1901_04200_gb300 import tape
+    return tape
+
+
+def rel(a, b):
+    a, b = np.asarray(a, dtype=np.float64), np.asarray(b, dtype=np.float64)
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+@pytest.mark.parametrize("seed,P", [(1, 1000), (2, 33), (3, 4096), (4, 1)])
+def test_random_programs_match_oracle_tape(T, orc, seed, P):
+    ops, obj = TP.random_program(seed)
+    theta = np.random.default_rng(100 + seed).uniform(0.2, 0.8, 4)
+    phil = 0x190104200 + seed
+    Z = orc.normals_fill(phil, 0, P, 6)
+    G_o, g_o, vals = TP.run_oracle(ops, obj, theta, Z)
+    prog, nodes = TP.build_product(ops, T)
+    ctx = T.TapeContext(prog, nodes[obj], 4, max_paths=P)
+    G, g = ctx.value_and_grad(theta, phil, P)
+    assert abs(G.item() - G_o) <= 1e-12 * max(abs(G_o), 1.0)
+    assert rel(g.cpu().numpy(), g_o) <= 1e-10
+    # per-path values of a late per-path node and of the normals
+    for k in (6, 9, len(ops) - 12):
+        op = ops[k][0]
+        if op not in ("param", "const", "expect") and vals[k].v.ndim == 1 and not _is_det(ops, k):
+            assert rel(ctx.path_values(nodes[k]).cpu().numpy(), vals[k].v) <= 1e-12
+
+
+def _is_det(ops, k):
+    op, a, b, _ = ops[k]
+    if op in ("param", "const", "expect"):
+        return True
+    if op == "normal":
+        return False
+    return all(_is_det(ops, x) for x in (a, b) if x >= 0)
+
+
+def test_path_offset_and_partition(T, orc):
+    """Paths [path0, path0 + n): the normals follow the global path index."""
+    ops, obj = TP.random_program(7)
+    theta = np.full(4, 0.5)
+    Z = orc.normals_fill(99, 5000, 700, 6)
+    G_o, g_o, _ = TP.run_oracle(ops, obj, theta, Z)
+    prog, nodes = TP.build_product(ops, T)
+    ctx = T.TapeContext(prog, nodes[obj], 4, max_paths=1000)
+    G, g = ctx.value_and_grad(theta, 99, 700, path0=5000)
+    assert abs(G.item() - G_o) <= 1e-12 * max(abs(G_o), 1.0)
+    assert rel(g.cpu().numpy(), g_o) <= 1e-10
+
+
+def test_expectation_inside_paths_control_variate(T, orc):
+    """G = E[(y - E y)^2] with y = theta0 exp(theta1 z): the expectation feeds every path."""
+    P = 2048
+    ops = [("param", -1, -1, 0), ("param", -1, -1, 1), ("normal", -1, -1, 0)]
+    ops += [("mul", 1, 2, 0.0), ("exp", 3, -1, 0.0), ("mul", 0, 4, 0.0), ("expect", 5, -1, 0.0),
+            ("sub", 5, 6, 0.0), ("mul", 7, 7, 0.0), ("expect", 8, -1, 0.0)]
+    theta = np.array([1.3, 0.4])
+    Z = orc.normals_fill(11, 0, P, 1)
+    G_o, g_o, _ = TP.run_oracle(ops, 9, theta, Z)
+    prog, nodes = TP.build_product(ops, T)
+    ctx = T.TapeContext(prog, nodes[9], 2, max_paths=P)
+    G, g = ctx.value_and_grad(theta, 11, P)
+    assert abs(G.item() - G_o) <= 1e-12 * abs(G_o)
+    assert rel(g.cpu().numpy(), g_o) <= 1e-10
+    # closed form of the sample variance's gradient on these paths
+    z = Z[:, 0]
+    y = theta[0] * np.exp(theta[1] * z)
+    dy0, dy1 = np.exp(theta[1] * z), y * z
+    c = y - y.mean()
+    assert rel(g.cpu().numpy(), [2 * np.mean(c * (dy0 - dy0.mean())), 2 * np.mean(c * (dy1 - dy1.mean()))]) <= 1e-10
+
+
+@pytest.mark.parametrize("n_paths", [1000, 4096])
+def test_heston_objective_equals_two_step(T, orc, n_paths):
+    """The whole-program tape of G and the two-step algorithm agree (gradient identity)."""
+    w = inputs.heston_config(n_paths=n_paths, steps_per_year=16, T=1.0, n_mat=4, n_strike=3)
+    pb = replace(w.problem, precision="fp64", ckpt_every=4)  # maturities at steps 4, 8, 12, 16
+    prog, G = T.heston_objective(pb, w.C)
+    ctx = T.TapeContext(prog, G, 5, max_paths=n_paths)
+    Gt, gt = ctx.value_and_grad(w.theta, pb.seed, n_paths)
+    _, Go, go = orc.value_and_grad(pb, w.theta, w.C, n_paths)
+    assert abs(Gt.item() - Go) <= 1e-10 * abs(Go)
+    assert rel(gt.cpu().numpy(), go) <= 1e-9
+    from paper_1901_04200_gb300 import _lib
+    c2 = _lib.Context(pb, max_paths=n_paths)
+    G2, g2, _ = c2.value_and_grad(w.theta, w.C, pb.seed, n_paths)
+    assert abs(Gt.item() - G2.item()) <= 1e-10 * abs(G2.item())
+    assert rel(gt.cpu().numpy(), g2.cpu().numpy()) <= 1e-9
+
+
+def test_deterministic_repeat(T):
+    ops, obj = TP.random_program(5)
+    prog, nodes = TP.build_product(ops, T)
+    ctx = T.TapeContext(prog, nodes[obj], 4, max_paths=5000)
+    a = [x.cpu().numpy().copy() for x in ctx.value_and_grad(np.full(4, 0.4), 3, 5000)]
+    b = [x.cpu().numpy().copy() for x in ctx.value_and_grad(np.full(4, 0.4), 3, 5000)]
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+def test_call_errors(T):
+    from paper_1901_04200_gb300 import _lib
+    ops, obj = TP.random_program(6)
+    prog, nodes = TP.build_product(ops, T)
+    ctx = T.TapeContext(prog, nodes[obj], 4, max_paths=64)
+    with pytest.raises(_lib.McError):
+        ctx.value_and_grad(np.full(4, 0.4), 3, 65)
+    ctx.value_and_grad(np.full(4, 0.4), 3, 64)
+    with pytest.raises(_lib.McError):
+        ctx.path_values(nodes[obj])
