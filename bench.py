@@ -304,42 +304,6 @@ def surrogate_step_bench(args, rank, world):
             "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"]}}))
 
 
-def tape_bytes(prog, objective):
-    """Algorithmic HBM bytes per path of one value-and-gradient by the expected-backward tape,
-    from the node list with the kernels' access rules (FP64 tape and adjoint arrays [node][path]):
-    forward, a per-path node writes its value and reads its per-path arguments; backward, it
-    reads its adjoint, the values its partials need, and updates the adjoints of its per-path
-    arguments (read + write); an expectation adds to its argument's adjoint (read + write)."""
-    from paper_1901_04200_gb300 import tape as T
-    ops = {v: k for k, v in T.OPS.items()}
-    path = []
-    for op, a, b, _ in prog.nodes:
-        name = ops[op]
-        if name == "normal":
-            path.append(True)
-        elif name in ("param", "const", "expect"):
-            path.append(False)
-        else:
-            path.append(any(path[x] for x in (a, b) if x >= 0))
-    fwd = bwd = 0
-    for i, (op, a, b, _) in enumerate(prog.nodes):
-        name = ops[op]
-        if name == "expect" and path[a]:
-            fwd += 8           # its argument, read back for the per-warp sum
-            bwd += 16
-            continue
-        if not path[i]:
-            continue
-        pa = [x for x in (a, b) if x >= 0 and path[x]]
-        fwd += 8 + 8 * len(pa)
-        if name == "normal":
-            continue
-        need = {"mul": 2, "div": 2, "log": 1, "sqrt": 1, "relu": 1, "abs": 1}.get(name, 0)
-        vals = [x for x in (a, b)[:need] if x >= 0 and path[x]]
-        bwd += 8 + 8 * len(vals) + (8 if name in ("exp", "sqrt") else 0) + 16 * len(pa)
-    return fwd, bwd
-
-
 def tape_bench(args, rank, world):
     """G and grad G of the Heston objective by the expected-backward tape (the whole program,
     expectations included, differentiated by the Appendix's rule)."""
@@ -352,7 +316,7 @@ def tape_bench(args, rank, world):
     pb, S = w.problem, w.problem.last_step
     prog, G = tape.heston_objective(pb, w.C)
     dev = torch.device("cuda", torch.cuda.current_device())
-    ctx = tape.TapeContext(prog, G, 5, max_paths=P, device=dev)
+    ctx = tape.TapeContext(prog, G, 5, max_paths=P, device=dev, precision=args.tape_precision)
     theta = torch.tensor(w.theta, dtype=torch.float64, device=dev)
     out = (torch.empty(1, dtype=torch.float64, device=dev), torch.empty(5, dtype=torch.float64, device=dev))
     path0 = rank * P
@@ -378,8 +342,8 @@ def tape_bench(args, rank, world):
     clk = clocks.stop()
     ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world)
     peaks, src = load_peaks()
-    fwd_b, bwd_b = tape_bytes(prog, G.i)
-    byts = P * (fwd_b + bwd_b)
+    per_path = tape.plan(prog, G, 5, P, args.tape_precision)[4]  # the kernels' HBM bytes per path (mc_tape_plan)
+    byts = P * per_path
     hbm = float(peaks["hbm_gbs"]) * 1e9
     if rank == 0:
         print(json.dumps({
@@ -387,12 +351,13 @@ def tape_bench(args, rank, world):
                       "m=64, M=5)" % (P, S),
             "value": world * P * S / (ms * 1e-3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f32" if args.tape_precision == "fp32" else "f64", "data": "synthetic",
             "config": {"workload": "tape_" + w.name, "paths_per_gpu": P, "steps": S, "nodes": len(prog.nodes),
+                       "precision": args.tape_precision + " per-path values and adjoints, fp64 sums",
                        "l2": "inputs larger than L2: %.1f GB of tape and adjoints" % (byts / 1e9)},
             "roofline": {"bound": "hbm", "achieved": byts / (ms * 1e-3) / 1e9, "peak": hbm / 1e9, "unit": "GB/s",
                          "frac": byts / (ms * 1e-3) / hbm, "traffic": None,
-                         "algorithmic_bytes": byts, "bytes_per_path": {"forward": fwd_b, "backward": bwd_b},
+                         "algorithmic_bytes": byts, "bytes_per_path": per_path,
                          "kernel": "all tape kernels of the step (whole-step time)",
                          "peak_basis": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs, %s)" % src},
             "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"]}}))
@@ -505,7 +470,9 @@ def main():
     ap.add_argument("--ref-paths", type=int, default=1 << 15)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ppt", type=int, default=0, help="paths per GPU thread (0 = library default)")
-    ap.add_argument("--tape-paths", type=int, default=1 << 16, help="paths of the --workload tape run")
+    ap.add_argument("--tape-paths", type=int, default=1 << 18, help="paths of the --workload tape run")
+    ap.add_argument("--tape-precision", default="fp32", choices=["fp32", "fp64"],
+                    help="per-path values and adjoints of the --workload tape run")
     ap.add_argument("--workload", default="heston", choices=["heston", "lv", "slv", "surrogate", "tape"],
                     help="heston (the metric's workload), lv (2^22 x 500 local vol) or surrogate "
                          "(one differential-loss training step of the pricing network), for measurement")

@@ -20,8 +20,9 @@
  * GPU execution: the host cuts the program into stages at the first use of
  * each expectation's value.  Per stage, one thread evaluates the
  * deterministic nodes, one GPU thread per path interprets the per-path nodes
- * (values stored FP64, structure of arrays [node][path] in HBM, so the whole
- * tape of the program is kept), and fixed-order block sums then a fixed-order
+ * (values FP64 or FP32, structure of arrays [node][path] in HBM where needed
+ * later),
+ * and fixed-order block sums then a fixed-order
  * sum over blocks give the stage's expectations.  The backward sweep runs
  * the stages in reverse: per-path adjoints in a second [node][path] array;
  * adjoints of deterministic nodes are means over paths (warp sums, per-warp
@@ -91,18 +92,27 @@ typedef struct {
  * stage's per-path nodes).  Any output pointer may be NULL.
  *   n_stages       stages (expectation boundaries + 1)
  *   n_path_nodes   per-path nodes (rows of the value and adjoint tapes)
- *   workspace      device bytes a context needs for max_paths paths */
+ *   workspace      device bytes a context needs for max_paths paths
+ *   hbm_bytes      HBM bytes per path that one mc_tape_value_and_grad moves:
+ *                  a per-thread shared-memory window holds the last 32
+ *                  per-path values (forward) and adjoints (backward) of a
+ *                  stage, so only values a far or later-stage user, an
+ *                  expectation or a backward partial needs go to the tape */
 mc_status mc_tape_plan(const mc_tape_node *nodes, int32_t n_nodes, int32_t objective, int32_t n_params,
-                       uint64_t max_paths, int32_t *n_stages, int32_t *n_path_nodes, size_t *workspace);
+                       int32_t precision, uint64_t max_paths, int32_t *n_stages, int32_t *n_path_nodes,
+                       size_t *workspace, size_t *hbm_bytes);
 
 typedef struct mc_tape mc_tape;
 
 /* Copy the program to `device` and allocate the tapes for up to max_paths
  * paths (workspace: caller-owned device buffer of mc_tape_plan's bytes,
- * 256-byte aligned, or NULL to let the context allocate).  Synchronous. */
+ * 256-byte aligned, or NULL to let the context allocate).  precision
+ * (mc_precision) is that of the per-path values, adjoints and normals:
+ * MC_FP64, or MC_FP32 with FP64 kept for the deterministic nodes, the
+ * expectations and every sum over paths.  Synchronous. */
 mc_status mc_tape_create(int device, const mc_tape_node *nodes, int32_t n_nodes, int32_t objective,
-                         int32_t n_params, uint64_t max_paths, void *workspace, size_t workspace_bytes,
-                         mc_tape **out);
+                         int32_t n_params, int32_t precision, uint64_t max_paths, void *workspace,
+                         size_t workspace_bytes, mc_tape **out);
 void mc_tape_destroy(mc_tape *t);
 const char *mc_tape_last_error(const mc_tape *t);
 
@@ -113,7 +123,11 @@ mc_status mc_tape_value_and_grad(mc_tape *t, const double *theta, uint64_t seed,
                                  uint64_t n_paths, double *value_out, double *grad_out, void *stream);
 
 /* Per-path value of node `node` on the last evaluated paths (FP64 device
- * [n_paths]); MC_ERR_INVALID_ARG for a deterministic node. */
+ * [n_paths]); MC_ERR_INVALID_ARG for a deterministic node,
+ * MC_ERR_UNSUPPORTED for a per-path node that is not kept on the tape (one
+ * that only users fewer than 32 positions later in its stage read, and that
+ * no backward partial needs; expectation arguments and arguments of
+ * products, quotients, log, sqrt, relu and abs are always kept). */
 mc_status mc_tape_path_values(mc_tape *t, int32_t node, double *out, void *stream);
 
 #ifdef __cplusplus

@@ -79,8 +79,8 @@ SIGNATURES = [
     ("mc_price_jacobian", ctypes.c_int, [_V, _V, _V, _I32, _U64, _U64, _V, _V, _V, _SZ, _V]),
     ("mc_value_and_grad_tangent_scratch_size", ctypes.c_int, [_V, _U64, _P(_SZ)]),
     # expected-backward tape (include/mctape.h); nodes passed as a ctypes array of mc_tape_node
-    ("mc_tape_plan", ctypes.c_int, [_V, _I32, _I32, _I32, _U64, _P(_I32), _P(_I32), _P(_SZ)]),
-    ("mc_tape_create", ctypes.c_int, [ctypes.c_int, _V, _I32, _I32, _I32, _U64, _V, _SZ, _P(_V)]),
+    ("mc_tape_plan", ctypes.c_int, [_V, _I32, _I32, _I32, _I32, _U64, _P(_I32), _P(_I32), _P(_SZ), _P(_SZ)]),
+    ("mc_tape_create", ctypes.c_int, [ctypes.c_int, _V, _I32, _I32, _I32, _I32, _U64, _V, _SZ, _P(_V)]),
     ("mc_tape_destroy", None, [_V]),
     ("mc_tape_last_error", ctypes.c_char_p, [_V]),
     ("mc_tape_value_and_grad", ctypes.c_int, [_V, _V, _U64, _U64, _U64, _V, _V, _V]),

@@ -36,13 +36,27 @@ namespace {
 
 constexpr int kMaxNodes = 1 << 24;
 constexpr int kMaxStageSums = 2048;  // expectations, or distinct DET arguments, per stage
+constexpr int kRing = 32;            // per-thread shared-memory window of recent per-path nodes
+constexpr int kGroup = 8;            // nodes whose HBM loads are issued together (<= kRing)
+constexpr int kTile = 128;           // node descriptors a block stages in shared memory at a time
+
+// Node flags.  kStore: the value goes to the HBM tape (a far or later-stage
+// user, an expectation, or a backward partial needs it from there).  kFar:
+// some user's adjoint contribution goes to the HBM adjoint array (a far or
+// later-stage user, or an expectation), so the backward sweep reads it.
+constexpr int kStore = 1, kFar = 2;
 
 // Device form of a node.  References to values: r >= 0 is row r of the
-// per-path tape, r < 0 is deterministic slot -r-1.  la, lb: index of a DET
-// argument among the stage's accumulated DET arguments (backward), -1 else.
+// per-path tape, r < 0 is deterministic slot -r-1.  sm: the node's slot in
+// the per-thread ring (its position in the stage's per-path list mod kRing);
+// sa, sb: the ring slot of a per-path argument fewer than kRing positions
+// earlier in the same stage (read from the ring, not HBM), -1 else.  la, lb:
+// index of a DET argument among the stage's accumulated DET arguments
+// (backward), -1 else.
 struct DevNode {
-    int op;
+    int op, flags;
     int ra, rb, rm;
+    int sa, sb, sm;
     int la, lb;
     double c;
 };
@@ -182,17 +196,48 @@ struct DevLists {
     std::vector<DevNode> all;
     std::vector<int> det_off, path_off, exp_off, darg_off;  // per stage, + 1 end entry each
     std::vector<int> darg_slot;                              // flattened: DET slot of each accumulated argument
+    std::vector<char> stored;                                // per node: its per-path values are on the tape
 };
 
-DevLists make_lists(const mc_tape_node *nodes, const TapePlan &p) {
+// Whether the backward partials of op need the value of argument q (0: a, 1: b) or the node's own.
+bool needs_arg_value(int op, int q) {
+    if (op == MC_OP_MUL || op == MC_OP_DIV) return true;
+    return q == 0 && (op == MC_OP_LOG || op == MC_OP_SQRT || op == MC_OP_RELU || op == MC_OP_ABS);
+}
+bool needs_own_value(int op) { return op == MC_OP_EXP || op == MC_OP_SQRT; }
+
+DevLists make_lists(const mc_tape_node *nodes, const TapePlan &p, size_t *bytes_per_path = nullptr,
+                    size_t rb = 8) {
     DevLists L;
+    const int n = p.n_nodes;
+    // position of each per-path node in its stage's list; flags from its users
+    std::vector<int> pos(n, -1), flags(n, 0);
+    for (int s = 0; s < p.n_stages; ++s)
+        for (size_t k = 0; k < p.st[s].path.size(); ++k) pos[p.st[s].path[k]] = (int)k;
+    auto near = [&](int user, int arg) {
+        return p.cls[arg] == 1 && p.cls[user] == 1 && p.stage[user] == p.stage[arg] && pos[user] - pos[arg] < kRing;
+    };
+    for (int i = 0; i < n; ++i) {
+        const int args[2] = {nodes[i].a, nodes[i].b};
+        for (int q = 0; q < n_args(nodes[i].op); ++q) {
+            const int a = args[q];
+            if (p.cls[a] != 1) continue;
+            if (!near(i, a)) flags[a] |= kStore | kFar;  // far user, later stage, or an expectation
+            if (needs_arg_value(nodes[i].op, q)) flags[a] |= kStore;
+        }
+        if (p.cls[i] == 1 && needs_own_value(nodes[i].op)) flags[i] |= kStore;
+    }
     auto dev = [&](int i, const StagePlan *sp) {
         DevNode d;
         d.op = nodes[i].op;
+        d.flags = flags[i];
         d.c = nodes[i].c;
         d.rm = p.ref[i];
         d.ra = nodes[i].a >= 0 ? p.ref[nodes[i].a] : 0;
         d.rb = nodes[i].b >= 0 ? p.ref[nodes[i].b] : 0;
+        d.sm = pos[i] >= 0 ? pos[i] % kRing : -1;
+        d.sa = nodes[i].a >= 0 && near(i, nodes[i].a) ? pos[nodes[i].a] % kRing : -1;
+        d.sb = nodes[i].b >= 0 && near(i, nodes[i].b) ? pos[nodes[i].b] % kRing : -1;
         d.la = d.lb = -1;
         if (sp) {
             auto local = [&](int arg) {
@@ -204,6 +249,31 @@ DevLists make_lists(const mc_tape_node *nodes, const TapePlan &p) {
         }
         return d;
     };
+    L.stored.assign(n, 0);
+    for (int i = 0; i < n; ++i) L.stored[i] = p.cls[i] == 1 && (flags[i] & kStore);
+    if (bytes_per_path) {
+        // HBM bytes per path of one value and gradient under the kernels' rules (FP64)
+        size_t b = 0;
+        for (int i = 0; i < n; ++i) {
+            const int op = nodes[i].op;
+            if (op == MC_OP_EXPECT) {
+                if (p.cls[nodes[i].a] == 1) b += 3 * rb;  // argument read for the sum; E(D) added to its adjoint
+                continue;
+            }
+            if (p.cls[i] != 1) continue;
+            if (flags[i] & kStore) b += rb;          // forward: value to the tape
+            if (flags[i] & kFar) b += rb;            // backward: adjoint from HBM
+            if (needs_own_value(op)) b += rb;        // backward: own value
+            const int args[2] = {nodes[i].a, nodes[i].b};
+            for (int q = 0; q < n_args(op); ++q) {
+                const int a = args[q];
+                if (p.cls[a] != 1) continue;
+                if (!near(i, a)) b += 3 * rb;        // forward load; backward adjoint update
+                if (needs_arg_value(op, q)) b += rb; // backward: argument value
+            }
+        }
+        *bytes_per_path = b;
+    }
     for (int s = 0; s < p.n_stages; ++s) {
         const StagePlan &sp = p.st[s];
         L.det_off.push_back((int)L.all.size());
@@ -226,7 +296,7 @@ inline size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 struct TapeWs {
     size_t nodes, dslot, det, ddet, part, tape, adj, total;
-    TapeWs(const TapePlan &p, size_t n_all, size_t n_dslot, int grid, uint64_t stride) {
+    TapeWs(const TapePlan &p, size_t n_all, size_t n_dslot, int grid, uint64_t stride, size_t rb) {
         size_t o = 0;
         auto take = [&](size_t bytes) {
             size_t at = o;
@@ -238,19 +308,28 @@ struct TapeWs {
         det = take((size_t)p.n_det * 8);
         ddet = take((size_t)p.n_det * 8);
         part = take((size_t)grid * std::max(1, std::max(p.max_exp, p.max_darg)) * 8);
-        tape = take((size_t)p.n_rows * stride * 8);
-        adj = take((size_t)p.n_rows * stride * 8);
+        tape = take((size_t)p.n_rows * stride * rb);
+        adj = take((size_t)p.n_rows * stride * rb);
         total = o;
     }
 };
 
 // ------------------------------------------------------------- kernels ----
 
-__device__ __forceinline__ double ld(const double *tape, const double *det, int r, uint64_t stride, uint64_t p) {
-    return r >= 0 ? tape[(size_t)r * stride + p] : det[-r - 1];
+template <typename Real>
+__device__ __forceinline__ Real ld(const Real *tape, const double *det, int r, uint64_t stride, uint64_t p) {
+    return r >= 0 ? tape[(size_t)r * stride + p] : (Real)det[-r - 1];
 }
 
-__device__ __forceinline__ double apply_op(int op, double a, double b, double c) {
+__device__ __forceinline__ float exp_t(float x) { return expf(x); }
+__device__ __forceinline__ double exp_t(double x) { return exp(x); }
+__device__ __forceinline__ float log_t(float x) { return logf(x); }
+__device__ __forceinline__ double log_t(double x) { return log(x); }
+__device__ __forceinline__ float sqrt_t(float x) { return sqrtf(x); }
+__device__ __forceinline__ double sqrt_t(double x) { return sqrt(x); }
+
+template <typename T>
+__device__ __forceinline__ T apply_op(int op, T a, T b, T c) {
     switch (op) {
     case MC_OP_ADD: return a + b;
     case MC_OP_SUB: return a - b;
@@ -259,35 +338,45 @@ __device__ __forceinline__ double apply_op(int op, double a, double b, double c)
     case MC_OP_ADDC: return a + c;
     case MC_OP_MULC: return a * c;
     case MC_OP_NEG: return -a;
-    case MC_OP_EXP: return exp(a);
-    case MC_OP_LOG: return log(a);
-    case MC_OP_SQRT: return sqrt(a);
-    case MC_OP_RELU: return a > 0.0 ? a : 0.0;
-    case MC_OP_ABS: return fabs(a);
+    case MC_OP_EXP: return exp_t(a);
+    case MC_OP_LOG: return log_t(a);
+    case MC_OP_SQRT: return sqrt_t(a);
+    case MC_OP_RELU: return a > T(0) ? a : T(0);
+    case MC_OP_ABS: return a < T(0) ? -a : a;
     default: return a;  // EXPECT of a deterministic value
     }
 }
 
 // Partial derivatives of node value m = op(a, b) with respect to a and b.
-__device__ __forceinline__ void partials(int op, double a, double b, double m, double c, double &pa, double &pb) {
-    pa = 0.0;
-    pb = 0.0;
+template <typename T>
+__device__ __forceinline__ void partials(int op, T a, T b, T m, T c, T &pa, T &pb) {
+    pa = T(0);
+    pb = T(0);
     switch (op) {
-    case MC_OP_ADD: pa = 1.0; pb = 1.0; break;
-    case MC_OP_SUB: pa = 1.0; pb = -1.0; break;
+    case MC_OP_ADD: pa = T(1); pb = T(1); break;
+    case MC_OP_SUB: pa = T(1); pb = T(-1); break;
     case MC_OP_MUL: pa = b; pb = a; break;
-    case MC_OP_DIV: pa = 1.0 / b; pb = -a / (b * b); break;
-    case MC_OP_ADDC: pa = 1.0; break;
+    case MC_OP_DIV: pa = T(1) / b; pb = -a / (b * b); break;
+    case MC_OP_ADDC: pa = T(1); break;
     case MC_OP_MULC: pa = c; break;
-    case MC_OP_NEG: pa = -1.0; break;
+    case MC_OP_NEG: pa = T(-1); break;
     case MC_OP_EXP: pa = m; break;
-    case MC_OP_LOG: pa = 1.0 / a; break;
-    case MC_OP_SQRT: pa = a > 0.0 ? 0.5 / m : 0.0; break;
-    case MC_OP_RELU: pa = a > 0.0 ? 1.0 : 0.0; break;
-    case MC_OP_ABS: pa = a > 0.0 ? 1.0 : (a < 0.0 ? -1.0 : 0.0); break;
-    case MC_OP_EXPECT: pa = 1.0; break;  // of a deterministic value: identity
+    case MC_OP_LOG: pa = T(1) / a; break;
+    case MC_OP_SQRT: pa = a > T(0) ? T(0.5) / m : T(0); break;
+    case MC_OP_RELU: pa = a > T(0) ? T(1) : T(0); break;
+    case MC_OP_ABS: pa = a > T(0) ? T(1) : (a < T(0) ? T(-1) : T(0)); break;
+    case MC_OP_EXPECT: pa = T(1); break;  // of a deterministic value: identity
     default: break;
     }
+}
+
+// The block's copy of descriptors nd[k0 .. k0 + cnt) into shared memory (16-byte words).
+__device__ __forceinline__ void stage_tile(DevNode *tile, const DevNode *__restrict__ nd, int k0, int cnt) {
+    static_assert(sizeof(DevNode) % 16 == 0, "descriptor size");
+    constexpr int kWords = (int)(sizeof(DevNode) / 16);
+    const int4 *src = (const int4 *)(nd + k0);
+    int4 *dst = (int4 *)tile;
+    for (int q = threadIdx.x; q < cnt * kWords; q += blockDim.x) dst[q] = src[q];
 }
 
 // Deterministic nodes of a stage, in program order (one thread).
@@ -304,60 +393,93 @@ __global__ void tape_det_forward(const DevNode *__restrict__ nd, int n, const do
         } else {
             const double a = det[-d.ra - 1];
             const double b = n_args(d.op) == 2 ? det[-d.rb - 1] : 0.0;
-            v = apply_op(d.op, a, b, d.c);
+            v = apply_op<double>(d.op, a, b, d.c);
         }
         det[-d.rm - 1] = v;
     }
 }
 
-// Per-path nodes of a stage, one thread per path; then per-warp FP64 sums of
-// the expectations' arguments (warp shuffle in FP64, lane k%32 adds), per
-// block in warp order -> part[block][k].
+// Per-path nodes of a stage, one thread per path.  Each thread keeps its last
+// kRing per-path values in shared memory (ring[slot][thread]); arguments
+// further back, of earlier stages, or deterministic ones are loaded for a
+// group of kGroup nodes at once before the group is computed.  Values flagged
+// kStore also go to the HBM tape.  Then per-warp FP64 sums of the
+// expectations' arguments (warp shuffle, lane k%32 adds), per block in warp
+// order -> part[block][k].
+template <typename Real>
 __global__ void __launch_bounds__(kBlock) tape_path_forward(const DevNode *__restrict__ nd, int n,
                                                             const DevNode *__restrict__ ex, int n_exp,
-                                                            const double *__restrict__ det, double *__restrict__ tape,
+                                                            const double *__restrict__ det, Real *__restrict__ tape,
                                                             uint64_t stride, RoundKeys rk, uint64_t path0,
                                                             uint64_t n_paths, double *__restrict__ part) {
     extern __shared__ __align__(16) unsigned char smem[];
-    double *wacc = (double *)smem;  // [kWarpsPerBlock][n_exp]
+    DevNode *tile = (DevNode *)smem;                                     // [kTile] descriptors
+    unsigned char *after = smem + (size_t)kTile * sizeof(DevNode);
+    Real *ring = (Real *)after + threadIdx.x;                                 // [kRing][kBlock]
+    double *wacc = (double *)(after + (size_t)kRing * kBlock * sizeof(Real));  // [kWarpsPerBlock][n_exp]
     for (int q = threadIdx.x; q < kWarpsPerBlock * n_exp; q += blockDim.x) wacc[q] = 0.0;
     __syncthreads();
     const int warp = threadIdx.x / kWarp, lane = threadIdx.x % kWarp;
     const uint64_t chunks = (n_paths + kWarp - 1) / kWarp;
-    for (uint64_t ch = (uint64_t)blockIdx.x * kWarpsPerBlock + warp; ch < chunks;
-         ch += (uint64_t)gridDim.x * kWarpsPerBlock) {
+    // the block's warps take chunks base + warp in lockstep (block-uniform loop: they share the tiles)
+    for (uint64_t base = (uint64_t)blockIdx.x * kWarpsPerBlock; base < chunks;
+         base += (uint64_t)gridDim.x * kWarpsPerBlock) {
+        const uint64_t ch = base + warp;
+        const bool live = ch < chunks;  // a warp past the last chunk only takes part in the tiles
         const uint64_t p = ch * kWarp + lane;
-        const bool active = p < n_paths;
-        PathNormals<double> rng;
+        const bool active = live && p < n_paths;
+        PathNormals<Real> rng;
         rng.init(path0 + (active ? p : 0));
         uint64_t last_call = ~0ull;
-        for (int k = 0; k < n; ++k) {
-            const DevNode d = nd[k];
-            double v;
-            if (d.op == MC_OP_NORMAL) {
-                const uint64_t j = (uint64_t)d.c;
-                if ((j >> 2) != last_call) {
-                    last_call = j >> 2;
-                    rng.fill((uint32_t)last_call, rk);
+        for (int t0 = 0; t0 < n; t0 += kTile) {
+        const int tn = min(kTile, n - t0);
+        __syncthreads();  // the previous tile is consumed
+        stage_tile(tile, nd, t0, tn);
+        __syncthreads();
+        for (int k0 = 0; k0 < tn; k0 += kGroup) {
+            Real fa[kGroup], fb[kGroup];
+#pragma unroll
+            for (int g = 0; g < kGroup; ++g) {
+                fa[g] = fb[g] = Real(0);
+                if (live && k0 + g < tn) {
+                    const DevNode &d = tile[k0 + g];
+                    const int na = d.op == MC_OP_NORMAL ? 0 : n_args(d.op);
+                    if (na >= 1 && d.sa < 0) fa[g] = ld(tape, det, d.ra, stride, p);
+                    if (na == 2 && d.sb < 0) fb[g] = ld(tape, det, d.rb, stride, p);
                 }
-                v = rng.pick((uint32_t)(j & 3u));
-            } else {
-                const double a = ld(tape, det, d.ra, stride, p);
-                const double b = n_args(d.op) == 2 ? ld(tape, det, d.rb, stride, p) : 0.0;
-                v = apply_op(d.op, a, b, d.c);
             }
-            tape[(size_t)d.rm * stride + p] = v;
+#pragma unroll
+            for (int g = 0; g < kGroup; ++g) {
+                if (k0 + g >= tn) break;
+                const DevNode &d = tile[k0 + g];
+                Real v;
+                if (d.op == MC_OP_NORMAL) {
+                    const uint64_t j = (uint64_t)d.c;
+                    if ((j >> 2) != last_call) {
+                        last_call = j >> 2;
+                        rng.fill((uint32_t)last_call, rk);
+                    }
+                    v = rng.pick((uint32_t)(j & 3u));
+                } else {
+                    const Real a = d.sa >= 0 ? ring[d.sa * kBlock] : fa[g];
+                    const Real b = d.sb >= 0 ? ring[d.sb * kBlock] : fb[g];
+                    v = apply_op<Real>(d.op, a, b, (Real)d.c);
+                }
+                ring[d.sm * kBlock] = v;
+                if (live && (d.flags & kStore)) tape[(size_t)d.rm * stride + p] = v;
+            }
+        }
         }
         double *wrow = wacc + warp * n_exp;
         for (int k0 = 0; k0 < n_exp; k0 += kWarp) {
             const int cnt = min(kWarp, n_exp - k0);
-            double mine = 0.0;
+            Real mine = Real(0);
             for (int j = 0; j < cnt; ++j) {
-                const double v = active ? tape[(size_t)ex[k0 + j].ra * stride + p] : 0.0;
-                const double s = warp_sum(v);
+                const Real v = active ? tape[(size_t)ex[k0 + j].ra * stride + p] : Real(0);
+                const Real s = warp_sum(v);
                 mine = lane == j ? s : mine;
             }
-            if (lane < cnt) wrow[k0 + lane] += mine;
+            if (lane < cnt) wrow[k0 + lane] += (double)mine;
         }
     }
     __syncthreads();
@@ -379,57 +501,95 @@ __global__ void tape_expect_finalize(const double *__restrict__ part, int nb, co
 }
 
 // Backward sweep of a stage's per-path nodes: first E(D) of each expectation
-// into its argument's adjoint, then the nodes in reverse; contributions to
-// deterministic arguments are warp-summed into per-warp accumulators.
+// into its argument's adjoint (HBM), then the nodes in reverse.  A node's
+// adjoint is the sum of its near users' contributions, kept in a per-thread
+// shared-memory ring like the forward values, and (flag kFar) of the far
+// users' contributions in the HBM adjoint array.  The values the partials
+// need are loaded from the tape for a group of kGroup nodes at once;
+// contributions to deterministic arguments are warp-summed into per-warp
+// accumulators.
+template <typename Real>
 __global__ void __launch_bounds__(kBlock) tape_path_backward(const DevNode *__restrict__ nd, int n,
                                                              const DevNode *__restrict__ ex, int n_exp, int n_darg,
                                                              const double *__restrict__ det,
                                                              const double *__restrict__ ddet,
-                                                             const double *__restrict__ tape, double *__restrict__ adj,
+                                                             const Real *__restrict__ tape, Real *__restrict__ adj,
                                                              uint64_t stride, uint64_t n_paths,
                                                              double *__restrict__ part) {
     extern __shared__ __align__(16) unsigned char smem[];
-    double *wacc = (double *)smem;  // [kWarpsPerBlock][n_darg]
+    DevNode *tile = (DevNode *)smem;                                     // [kTile] descriptors
+    unsigned char *after = smem + (size_t)kTile * sizeof(DevNode);
+    Real *ring = (Real *)after + threadIdx.x;                                 // [kRing][kBlock] adjoints
+    double *wacc = (double *)(after + (size_t)kRing * kBlock * sizeof(Real));  // [kWarpsPerBlock][n_darg]
     for (int q = threadIdx.x; q < kWarpsPerBlock * n_darg; q += blockDim.x) wacc[q] = 0.0;
     __syncthreads();
     const int warp = threadIdx.x / kWarp, lane = threadIdx.x % kWarp;
     double *wrow = wacc + warp * n_darg;
     const uint64_t chunks = (n_paths + kWarp - 1) / kWarp;
-    for (uint64_t ch = (uint64_t)blockIdx.x * kWarpsPerBlock + warp; ch < chunks;
-         ch += (uint64_t)gridDim.x * kWarpsPerBlock) {
+    for (uint64_t base = (uint64_t)blockIdx.x * kWarpsPerBlock; base < chunks;
+         base += (uint64_t)gridDim.x * kWarpsPerBlock) {
+        const uint64_t ch = base + warp;
+        const bool live = ch < chunks;
         const uint64_t p = ch * kWarp + lane;
-        const bool active = p < n_paths;
+        const bool active = live && p < n_paths;
+#pragma unroll
+        for (int q = 0; q < kRing; ++q) ring[q * kBlock] = Real(0);
         if (active)
-            for (int k = 0; k < n_exp; ++k) adj[(size_t)ex[k].ra * stride + p] += ddet[-ex[k].rm - 1];
-        for (int k = n - 1; k >= 0; --k) {
-            const DevNode d = nd[k];
-            if (d.op == MC_OP_NORMAL) continue;
-            const double D = active ? adj[(size_t)d.rm * stride + p] : 0.0;
-            const bool two = n_args(d.op) == 2;
-            // only the values the op's partials need (the op is the same on every lane)
-            const bool need_ab = d.op == MC_OP_MUL || d.op == MC_OP_DIV;
-            const bool need_a = need_ab || d.op == MC_OP_LOG || d.op == MC_OP_SQRT || d.op == MC_OP_RELU ||
-                                d.op == MC_OP_ABS;
-            const double a = need_a ? ld(tape, det, d.ra, stride, p) : 0.0;
-            const double b = need_ab ? ld(tape, det, d.rb, stride, p) : 0.0;
-            const double m = (d.op == MC_OP_EXP || d.op == MC_OP_SQRT) ? tape[(size_t)d.rm * stride + p] : 0.0;
-            double pa, pb;
-            partials(d.op, a, b, m, d.c, pa, pb);
-            const double ga = active ? D * pa : 0.0, gb = active ? D * pb : 0.0;
-            if (d.ra >= 0) {
-                if (active) adj[(size_t)d.ra * stride + p] += ga;
-            } else {
-                const double s = warp_sum(ga);
-                if (lane == 0) wrow[d.la] += s;
-            }
-            if (two) {
-                if (d.rb >= 0) {
-                    if (active) adj[(size_t)d.rb * stride + p] += gb;
-                } else {
-                    const double s = warp_sum(gb);
-                    if (lane == 0) wrow[d.lb] += s;
+            for (int k = 0; k < n_exp; ++k) adj[(size_t)ex[k].ra * stride + p] += (Real)ddet[-ex[k].rm - 1];
+        for (int t1 = n; t1 > 0; t1 -= kTile) {
+        const int t0 = max(0, t1 - kTile), tn = t1 - t0;
+        __syncthreads();  // the previous tile is consumed
+        stage_tile(tile, nd, t0, tn);
+        __syncthreads();
+        for (int k0 = tn - 1; k0 >= 0; k0 -= kGroup) {
+            Real va[kGroup], vb[kGroup], vm[kGroup], dg[kGroup];
+#pragma unroll
+            for (int g = 0; g < kGroup; ++g) {
+                va[g] = vb[g] = vm[g] = dg[g] = Real(0);
+                if (live && k0 - g >= 0) {
+                    const DevNode &d = tile[k0 - g];
+                    if (d.op != MC_OP_NORMAL) {
+                        const bool need_ab = d.op == MC_OP_MUL || d.op == MC_OP_DIV;
+                        const bool need_a = need_ab || d.op == MC_OP_LOG || d.op == MC_OP_SQRT ||
+                                            d.op == MC_OP_RELU || d.op == MC_OP_ABS;
+                        if (need_a) va[g] = ld(tape, det, d.ra, stride, p);
+                        if (need_ab) vb[g] = ld(tape, det, d.rb, stride, p);
+                        if (d.op == MC_OP_EXP || d.op == MC_OP_SQRT) vm[g] = tape[(size_t)d.rm * stride + p];
+                    }
+                    if ((d.flags & kFar) && active) dg[g] = adj[(size_t)d.rm * stride + p];
                 }
             }
+#pragma unroll
+            for (int g = 0; g < kGroup; ++g) {
+                if (k0 - g < 0) break;
+                const DevNode &d = tile[k0 - g];
+                const Real D = active ? ring[d.sm * kBlock] + dg[g] : Real(0);
+                ring[d.sm * kBlock] = Real(0);
+                if (d.op == MC_OP_NORMAL) continue;
+                const bool two = n_args(d.op) == 2;
+                Real pa, pb;
+                partials<Real>(d.op, va[g], vb[g], vm[g], (Real)d.c, pa, pb);
+                const Real ga = active ? D * pa : Real(0), gb = active ? D * pb : Real(0);
+                if (d.sa >= 0) {
+                    ring[d.sa * kBlock] += ga;
+                } else if (d.ra >= 0) {
+                    if (active) adj[(size_t)d.ra * stride + p] += ga;
+                } else {
+                    const Real sum = warp_sum(ga);
+                    if (lane == 0) wrow[d.la] += (double)sum;
+                }
+                if (two) {
+                    if (d.sb >= 0) {
+                        ring[d.sb * kBlock] += gb;
+                    } else if (d.rb >= 0) {
+                        if (active) adj[(size_t)d.rb * stride + p] += gb;
+                    } else {
+                        const Real sum = warp_sum(gb);
+                        if (lane == 0) wrow[d.lb] += (double)sum;
+                    }
+                }
+            }
+        }
         }
     }
     __syncthreads();
@@ -467,7 +627,7 @@ __global__ void tape_det_backward(const DevNode *__restrict__ nd, int n, const d
         const double a = det[-d.ra - 1];
         const double b = two ? det[-d.rb - 1] : 0.0;
         double pa, pb;
-        partials(d.op, a, b, det[-d.rm - 1], d.c, pa, pb);
+        partials<double>(d.op, a, b, det[-d.rm - 1], d.c, pa, pb);
         ddet[-d.ra - 1] += D * pa;
         if (two) ddet[-d.rb - 1] += D * pb;
     }
@@ -484,10 +644,15 @@ __global__ void tape_copy_value(const double *__restrict__ det, int slot, double
     if (blockIdx.x == 0 && threadIdx.x == 0) *out = det[slot];
 }
 
+__global__ void tape_widen(const float *__restrict__ in, uint64_t n, double *__restrict__ out) {
+    for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (uint64_t)gridDim.x * blockDim.x)
+        out[k] = in[k];
+}
+
 }  // namespace
 
 struct mc_tape {
-    int device = 0;
+    int device = 0, precision = MC_FP64;
     TapePlan plan;
     DevLists lists;
     int grid = 1, n_sm = 1;
@@ -497,7 +662,8 @@ struct mc_tape {
     unsigned char *ws = nullptr;
     DevNode *nodes = nullptr;
     int *dslot = nullptr;
-    double *det = nullptr, *ddet = nullptr, *part = nullptr, *tape = nullptr, *adj = nullptr;
+    double *det = nullptr, *ddet = nullptr, *part = nullptr;
+    void *tape = nullptr, *adj = nullptr;  // [n_rows][stride] of FP64 or FP32
     uint64_t last_n = 0;
     std::string err;
 };
@@ -521,6 +687,7 @@ uint64_t tape_stride(uint64_t max_paths) { return (max_paths + kWarp - 1) / kWar
 
 // Blocks: (resident blocks per SM) x SMs of the heavier path kernel, capped at
 // one block per 4 chunks of 32 paths.
+template <typename Real>
 mc_status tape_launch_shape(int device, const TapePlan &p, uint64_t max_paths, int *grid, int *n_sm,
                             size_t *smem_fwd, size_t *smem_bwd, std::string &why) {
     cudaError_t e = cudaDeviceGetAttribute(n_sm, cudaDevAttrMultiProcessorCount, device);
@@ -528,14 +695,18 @@ mc_status tape_launch_shape(int device, const TapePlan &p, uint64_t max_paths, i
         why = cudaGetErrorString(e);
         return MC_ERR_CUDA;
     }
-    *smem_fwd = (size_t)kWarpsPerBlock * p.max_exp * 8;
-    *smem_bwd = (size_t)kWarpsPerBlock * p.max_darg * 8;
+    const size_t fixed = (size_t)kTile * sizeof(DevNode) + (size_t)kRing * kBlock * sizeof(Real);
+    *smem_fwd = fixed + (size_t)kWarpsPerBlock * p.max_exp * 8;
+    *smem_bwd = fixed + (size_t)kWarpsPerBlock * p.max_darg * 8;
     int occ_f = 0, occ_b = 0;
-    e = cudaFuncSetAttribute(tape_path_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem_fwd);
+    e = cudaFuncSetAttribute(tape_path_forward<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem_fwd);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(tape_path_backward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem_bwd);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_f, tape_path_forward, kBlock, *smem_fwd);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_b, tape_path_backward, kBlock, *smem_bwd);
+        e = cudaFuncSetAttribute(tape_path_backward<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)*smem_bwd);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_f, tape_path_forward<Real>, kBlock, *smem_fwd);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_b, tape_path_backward<Real>, kBlock, *smem_bwd);
     if (e != cudaSuccess) {
         why = cudaGetErrorString(e);
         return MC_ERR_CUDA;
@@ -548,10 +719,74 @@ mc_status tape_launch_shape(int device, const TapePlan &p, uint64_t max_paths, i
 
 }  // namespace
 
+namespace {
+
+// One value and gradient: the forward stages, then the backward stages in reverse.
+template <typename Real>
+mc_status run_tape(mc_tape *t, const double *theta, uint64_t seed, uint64_t path0, uint64_t n_paths,
+                   double *value_out, double *grad_out, cudaStream_t st) {
+    const TapePlan &p = t->plan;
+    const DevLists &L = t->lists;
+    const RoundKeys rk = philox_round_keys(seed);
+    const double inv_n = 1.0 / (double)n_paths;
+    const uint64_t want = ((n_paths + kWarp - 1) / kWarp + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    const int grid = (int)std::min<uint64_t>((uint64_t)t->grid, want);
+    Real *tape = (Real *)t->tape, *adj = (Real *)t->adj;
+    const size_t ring = (size_t)kTile * sizeof(DevNode) + (size_t)kRing * kBlock * sizeof(Real);
+    auto ck = [&](const char *what) -> mc_status {
+        const cudaError_t e = cudaGetLastError();
+        return e == cudaSuccess ? MC_OK : tfail(t, MC_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+    };
+    // ---- forward sweep
+    for (int s = 0; s < p.n_stages; ++s) {
+        const int nd = L.path_off[s] - L.det_off[s], np = L.exp_off[s] - L.path_off[s];
+        const int ne = L.det_off[s + 1] - L.exp_off[s];
+        if (nd > 0) tape_det_forward<<<1, 1, 0, st>>>(t->nodes + L.det_off[s], nd, theta, t->det);
+        if (np > 0 || ne > 0)
+            tape_path_forward<Real><<<grid, kBlock, ring + (size_t)kWarpsPerBlock * ne * 8, st>>>(
+                t->nodes + L.path_off[s], np, t->nodes + L.exp_off[s], ne, t->det, tape, t->stride, rk, path0,
+                n_paths, t->part);
+        if (ne > 0)
+            tape_expect_finalize<<<(ne + 127) / 128, 128, 0, st>>>(t->part, grid, t->nodes + L.exp_off[s], ne, inv_n,
+                                                                  t->det);
+        mc_status r = ck("forward sweep");
+        if (r != MC_OK) return r;
+    }
+    tape_copy_value<<<1, 1, 0, st>>>(t->det, -p.ref[p.objective] - 1, value_out);
+    // ---- backward sweep
+    if (p.n_rows > 0) {
+        const cudaError_t e = cudaMemsetAsync(adj, 0, (size_t)p.n_rows * t->stride * sizeof(Real), st);
+        if (e != cudaSuccess) return tfail(t, MC_ERR_CUDA, "adjoint reset: %s", cudaGetErrorString(e));
+    }
+    tape_begin_backward<<<(std::max(p.n_det, p.n_params) + 255) / 256 + 1, 256, 0, st>>>(
+        t->ddet, p.n_det, -p.ref[p.objective] - 1, grad_out, p.n_params);
+    for (int s = p.n_stages - 1; s >= 0; --s) {
+        const int nd = L.path_off[s] - L.det_off[s], np = L.exp_off[s] - L.path_off[s];
+        const int ne = L.det_off[s + 1] - L.exp_off[s];
+        const int na = L.darg_off[s + 1] - L.darg_off[s];
+        if (np > 0 || ne > 0)
+            tape_path_backward<Real><<<grid, kBlock, ring + (size_t)kWarpsPerBlock * na * 8, st>>>(
+                t->nodes + L.path_off[s], np, t->nodes + L.exp_off[s], ne, na, t->det, t->ddet, tape, adj, t->stride,
+                n_paths, t->part);
+        if (na > 0)
+            tape_darg_finalize<<<(na + 127) / 128, 128, 0, st>>>(t->part, grid, t->dslot + L.darg_off[s], na, inv_n,
+                                                                t->ddet);
+        if (nd > 0) tape_det_backward<<<1, 1, 0, st>>>(t->nodes + L.det_off[s], nd, t->det, t->ddet, grad_out);
+        mc_status r = ck("backward sweep");
+        if (r != MC_OK) return r;
+    }
+    return MC_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 mc_status mc_tape_plan(const mc_tape_node *nodes, int32_t n_nodes, int32_t objective, int32_t n_params,
-                       uint64_t max_paths, int32_t *n_stages, int32_t *n_path_nodes, size_t *workspace) {
+                       int32_t precision, uint64_t max_paths, int32_t *n_stages, int32_t *n_path_nodes,
+                       size_t *workspace, size_t *hbm_bytes) {
+    if (precision != MC_FP32 && precision != MC_FP64) return MC_ERR_INVALID_ARG;
+    const size_t rb = precision == MC_FP64 ? 8 : 4;
     TapePlan p;
     std::string why;
     mc_status st = make_tape_plan(nodes, n_nodes, objective, n_params, p, why);
@@ -561,20 +796,22 @@ mc_status mc_tape_plan(const mc_tape_node *nodes, int32_t n_nodes, int32_t objec
     }
     if (n_stages) *n_stages = p.n_stages;
     if (n_path_nodes) *n_path_nodes = p.n_rows;
+    if (hbm_bytes) make_lists(nodes, p, hbm_bytes, rb);
     if (workspace) {
         if (max_paths == 0) return MC_ERR_INVALID_ARG;
         // the grid is bounded by one block per 128 paths and by 32 resident blocks on each of 1024 SMs
         const uint64_t blocks = std::min<uint64_t>((max_paths + kBlock - 1) / kBlock, 32u * 1024u);
         const DevLists L = make_lists(nodes, p);
-        *workspace = TapeWs(p, L.all.size(), L.darg_slot.size(), (int)blocks, tape_stride(max_paths)).total;
+        *workspace = TapeWs(p, L.all.size(), L.darg_slot.size(), (int)blocks, tape_stride(max_paths), rb).total;
     }
     return MC_OK;
 }
 
 mc_status mc_tape_create(int device, const mc_tape_node *nodes, int32_t n_nodes, int32_t objective,
-                         int32_t n_params, uint64_t max_paths, void *workspace, size_t workspace_bytes,
-                         mc_tape **out) {
-    if (!out || max_paths == 0) return MC_ERR_INVALID_ARG;
+                         int32_t n_params, int32_t precision, uint64_t max_paths, void *workspace,
+                         size_t workspace_bytes, mc_tape **out) {
+    if (!out || max_paths == 0 || (precision != MC_FP32 && precision != MC_FP64)) return MC_ERR_INVALID_ARG;
+    const size_t rb = precision == MC_FP64 ? 8 : 4;
     *out = nullptr;
     mc_tape *t = new (std::nothrow) mc_tape();
     if (!t) return MC_ERR_OOM;
@@ -591,10 +828,13 @@ mc_status mc_tape_create(int device, const mc_tape_node *nodes, int32_t n_nodes,
         return MC_ERR_CUDA;
     }
     t->device = device;
+    t->precision = precision;
     t->max_paths = max_paths;
     t->stride = tape_stride(max_paths);
     t->lists = make_lists(nodes, t->plan);
-    st = tape_launch_shape(device, t->plan, max_paths, &t->grid, &t->n_sm, &t->smem_fwd, &t->smem_bwd, why);
+    st = precision == MC_FP64
+             ? tape_launch_shape<double>(device, t->plan, max_paths, &t->grid, &t->n_sm, &t->smem_fwd, &t->smem_bwd, why)
+             : tape_launch_shape<float>(device, t->plan, max_paths, &t->grid, &t->n_sm, &t->smem_fwd, &t->smem_bwd, why);
     if (st != MC_OK) {
         fprintf(stderr, "mc_tape_create: %s\n", why.c_str());
         delete t;
@@ -603,7 +843,7 @@ mc_status mc_tape_create(int device, const mc_tape_node *nodes, int32_t n_nodes,
     const uint64_t blocks_cap = std::min<uint64_t>((max_paths + kBlock - 1) / kBlock, 32u * 1024u);
     if ((uint64_t)t->grid > blocks_cap) t->grid = (int)std::max<uint64_t>(blocks_cap, 1);
     TapeWs W(t->plan, t->lists.all.size(), t->lists.darg_slot.size(), (int)std::max<uint64_t>(blocks_cap, 1),
-             t->stride);
+             t->stride, rb);
     if (workspace) {
         if (workspace_bytes < W.total || ((uintptr_t)workspace & 255u)) {
             fprintf(stderr, "mc_tape_create: workspace needs %zu bytes, 256-byte aligned\n", W.total);
@@ -625,8 +865,8 @@ mc_status mc_tape_create(int device, const mc_tape_node *nodes, int32_t n_nodes,
     t->det = (double *)(t->ws + W.det);
     t->ddet = (double *)(t->ws + W.ddet);
     t->part = (double *)(t->ws + W.part);
-    t->tape = (double *)(t->ws + W.tape);
-    t->adj = (double *)(t->ws + W.adj);
+    t->tape = t->ws + W.tape;
+    t->adj = t->ws + W.adj;
     e = cudaMemcpy(t->nodes, t->lists.all.data(), t->lists.all.size() * sizeof(DevNode), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && !t->lists.darg_slot.empty())
         e = cudaMemcpy(t->dslot, t->lists.darg_slot.data(), t->lists.darg_slot.size() * 4, cudaMemcpyHostToDevice);
@@ -659,66 +899,31 @@ mc_status mc_tape_value_and_grad(mc_tape *t, const double *theta, uint64_t seed,
         ((uintptr_t)value_out & 7u) || ((uintptr_t)grad_out & 7u))
         return tfail(t, MC_ERR_INVALID_ARG, "theta, value_out and grad_out must be FP64 device pointers");
     if (path0 + n_paths < path0) return tfail(t, MC_ERR_INVALID_ARG, "path range overflows");
-    cudaStream_t st = (cudaStream_t)stream;
-    const DevLists &L = t->lists;
-    const RoundKeys rk = philox_round_keys(seed);
-    const double inv_n = 1.0 / (double)n_paths;
-    const uint64_t want = ((n_paths + kWarp - 1) / kWarp + kWarpsPerBlock - 1) / kWarpsPerBlock;
-    const int grid = (int)std::min<uint64_t>((uint64_t)t->grid, want);
-    auto ck = [&](const char *what) -> mc_status {
-        const cudaError_t e = cudaGetLastError();
-        return e == cudaSuccess ? MC_OK : tfail(t, MC_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
-    };
-    // ---- forward sweep
-    for (int s = 0; s < p.n_stages; ++s) {
-        const int nd = L.path_off[s] - L.det_off[s], np = L.exp_off[s] - L.path_off[s];
-        const int ne = L.det_off[s + 1] - L.exp_off[s];
-        if (nd > 0) tape_det_forward<<<1, 1, 0, st>>>(t->nodes + L.det_off[s], nd, theta, t->det);
-        if (np > 0 || ne > 0)
-            tape_path_forward<<<grid, kBlock, (size_t)kWarpsPerBlock * ne * 8, st>>>(
-                t->nodes + L.path_off[s], np, t->nodes + L.exp_off[s], ne, t->det, t->tape, t->stride, rk, path0,
-                n_paths, t->part);
-        if (ne > 0)
-            tape_expect_finalize<<<(ne + 127) / 128, 128, 0, st>>>(t->part, grid, t->nodes + L.exp_off[s], ne, inv_n,
-                                                                  t->det);
-        mc_status r = ck("forward sweep");
-        if (r != MC_OK) return r;
-    }
-    tape_copy_value<<<1, 1, 0, st>>>(t->det, -p.ref[p.objective] - 1, value_out);
-    // ---- backward sweep
-    if (p.n_rows > 0) {
-        const cudaError_t e = cudaMemsetAsync(t->adj, 0, (size_t)p.n_rows * t->stride * 8, st);
-        if (e != cudaSuccess) return tfail(t, MC_ERR_CUDA, "adjoint reset: %s", cudaGetErrorString(e));
-    }
-    tape_begin_backward<<<(std::max(p.n_det, p.n_params) + 255) / 256 + 1, 256, 0, st>>>(
-        t->ddet, p.n_det, -p.ref[p.objective] - 1, grad_out, p.n_params);
-    for (int s = p.n_stages - 1; s >= 0; --s) {
-        const int nd = L.path_off[s] - L.det_off[s], np = L.exp_off[s] - L.path_off[s];
-        const int ne = L.det_off[s + 1] - L.exp_off[s];
-        const int na = L.darg_off[s + 1] - L.darg_off[s];
-        if (np > 0 || ne > 0)
-            tape_path_backward<<<grid, kBlock, (size_t)kWarpsPerBlock * na * 8, st>>>(
-                t->nodes + L.path_off[s], np, t->nodes + L.exp_off[s], ne, na, t->det, t->ddet, t->tape, t->adj,
-                t->stride, n_paths, t->part);
-        if (na > 0)
-            tape_darg_finalize<<<(na + 127) / 128, 128, 0, st>>>(t->part, grid, t->dslot + L.darg_off[s], na, inv_n,
-                                                                t->ddet);
-        if (nd > 0) tape_det_backward<<<1, 1, 0, st>>>(t->nodes + L.det_off[s], nd, t->det, t->ddet, grad_out);
-        mc_status r = ck("backward sweep");
-        if (r != MC_OK) return r;
-    }
-    t->last_n = n_paths;
-    return MC_OK;
+    const mc_status r = t->precision == MC_FP64
+                            ? run_tape<double>(t, theta, seed, path0, n_paths, value_out, grad_out, (cudaStream_t)stream)
+                            : run_tape<float>(t, theta, seed, path0, n_paths, value_out, grad_out, (cudaStream_t)stream);
+    if (r == MC_OK) t->last_n = n_paths;
+    return r;
 }
 
 mc_status mc_tape_path_values(mc_tape *t, int32_t node, double *out, void *stream) {
     if (!t) return MC_ERR_INVALID_ARG;
-    if (node < 0 || node >= t->plan.n_nodes || t->plan.cls[node] != 1 || !out)
-        return tfail(t, MC_ERR_INVALID_ARG, "node %d is not a per-path node", node);
+    if (node < 0 || node >= t->plan.n_nodes || t->plan.cls[node] != 1 || !out || ((uintptr_t)out & 7u))
+        return tfail(t, MC_ERR_INVALID_ARG, "node %d is not a per-path node, or out is not FP64-aligned", node);
+    if (!t->lists.stored[node])
+        return tfail(t, MC_ERR_UNSUPPORTED, "node %d is not kept on the tape (nothing reads it from there)", node);
     if (t->last_n == 0) return tfail(t, MC_ERR_STATE, "no evaluation yet");
-    const cudaError_t e = cudaMemcpyAsync(out, t->tape + (size_t)t->plan.ref[node] * t->stride, t->last_n * 8,
-                                          cudaMemcpyDeviceToDevice, (cudaStream_t)stream);
-    return e == cudaSuccess ? MC_OK : tfail(t, MC_ERR_CUDA, "copy: %s", cudaGetErrorString(e));
+    const size_t rb = t->precision == MC_FP64 ? 8 : 4;
+    const unsigned char *row = (const unsigned char *)t->tape + (size_t)t->plan.ref[node] * t->stride * rb;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (t->precision == MC_FP64) {
+        const cudaError_t e = cudaMemcpyAsync(out, row, t->last_n * 8, cudaMemcpyDeviceToDevice, st);
+        return e == cudaSuccess ? MC_OK : tfail(t, MC_ERR_CUDA, "copy: %s", cudaGetErrorString(e));
+    }
+    const int blocks = (int)std::min<uint64_t>((t->last_n + 255) / 256, 4096);
+    tape_widen<<<blocks, 256, 0, st>>>((const float *)row, t->last_n, out);
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? MC_OK : tfail(t, MC_ERR_CUDA, "widen: %s", cudaGetErrorString(e));
 }
 
 }  // extern "C"

@@ -108,19 +108,25 @@ def expect(a: Node) -> Node:
     return a.prog.node("expect", a.i)
 
 
-def plan(prog: Program, objective: Node, n_params: int, max_paths: int = 1):
-    """(stages, per-path nodes, workspace bytes) from mc_tape_plan (host only)."""
+PRECISION = {"fp64": 0, "fp32": 1}  # mc_precision
+
+
+def plan(prog: Program, objective: Node, n_params: int, max_paths: int = 1, precision: str = "fp64"):
+    """(status, stages, per-path nodes, workspace bytes, HBM bytes per path of one value and
+    gradient) from mc_tape_plan (host only)."""
     from . import _lib
-    ns, nr, ws = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_size_t(0)
-    st = _lib.load().mc_tape_plan(prog.c_nodes(), len(prog.nodes), objective.i, n_params, max_paths,
-                                  ctypes.byref(ns), ctypes.byref(nr), ctypes.byref(ws))
-    return st, ns.value, nr.value, ws.value
+    ns, nr, ws, hb = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_size_t(0), ctypes.c_size_t(0)
+    st = _lib.load().mc_tape_plan(prog.c_nodes(), len(prog.nodes), objective.i, n_params, PRECISION[precision], max_paths,
+                                  ctypes.byref(ns), ctypes.byref(nr), ctypes.byref(ws), ctypes.byref(hb))
+    return st, ns.value, nr.value, ws.value, hb.value
 
 
 class TapeContext:
-    """A program on one GPU with tapes for up to max_paths paths (mc_tape_create)."""
+    """A program on one GPU with tapes for up to max_paths paths (mc_tape_create); precision
+    "fp64" or "fp32" (per-path values, adjoints and normals; sums over paths stay FP64)."""
 
-    def __init__(self, prog: Program, objective: Node, n_params: int, max_paths: int, device=None):
+    def __init__(self, prog: Program, objective: Node, n_params: int, max_paths: int, device=None,
+                 precision: str = "fp64"):
         import torch
         from . import _lib
         self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
@@ -129,7 +135,8 @@ class TapeContext:
         lib = _lib.load()
         h = ctypes.c_void_p()
         _lib._check(lib.mc_tape_create(self.device.index, prog.c_nodes(), len(prog.nodes), objective.i,
-                                       self.n_params, int(max_paths), None, 0, ctypes.byref(h)),
+                                       self.n_params, PRECISION[precision], int(max_paths), None, 0,
+                                       ctypes.byref(h)),
                     what="mc_tape_create rejected the program")
         self.handle = h
         self._destroy = lib.mc_tape_destroy  # kept: no imports while the interpreter shuts down

@@ -44,11 +44,15 @@ def test_random_programs_match_oracle_tape(T, orc, seed, P):
     G, g = ctx.value_and_grad(theta, phil, P)
     assert abs(G.item() - G_o) <= 1e-12 * max(abs(G_o), 1.0)
     assert rel(g.cpu().numpy(), g_o) <= 1e-10
-    # per-path values of a late per-path node and of the normals
-    for k in (6, 9, len(ops) - 12):
-        op = ops[k][0]
-        if op not in ("param", "const", "expect") and vals[k].v.ndim == 1 and not _is_det(ops, k):
-            assert rel(ctx.path_values(nodes[k]).cpu().numpy(), vals[k].v) <= 1e-12
+    # per-path values of nodes always kept on the tape: expectation arguments and arguments of
+    # products (other per-path nodes may live only in the shared-memory window)
+    kept = {a for op, a, b, _ in ops if op == "expect"} | {x for op, a, b, _ in ops if op == "mul" for x in (a, b)}
+    checked = 0
+    for k in sorted(kept):
+        if not _is_det(ops, k):
+            assert rel(ctx.path_values(nodes[k]).cpu().numpy(), vals[k].v) <= 1e-12, k
+            checked += 1
+    assert checked >= 6
 
 
 def _is_det(ops, k):
@@ -132,3 +136,47 @@ def test_call_errors(T):
     ctx.value_and_grad(np.full(4, 0.4), 3, 64)
     with pytest.raises(_lib.McError):
         ctx.path_values(nodes[obj])
+    # a per-path node read only by the next node, through an addition, is not kept
+    p2 = T.Program()
+    z = p2.normal(0)
+    u = z + 1.0
+    G = T.expect(u * u)
+    c2 = T.TapeContext(p2, G, 0, max_paths=64)
+    c2.value_and_grad(np.zeros(1), 3, 64)
+    with pytest.raises(_lib.McError) as e:
+        c2.path_values(z)
+    assert e.value.status == _lib.MC_ERR_UNSUPPORTED
+    from oracle import normals_fill
+    assert np.allclose(c2.path_values(u).cpu().numpy(), normals_fill(3, 0, 64, 1)[:, 0] + 1.0, rtol=0, atol=1e-14)
+
+
+# ---------------------------------------------------------------- FP32 tape
+
+@pytest.mark.parametrize("seed", [1, 3])
+def test_random_programs_fp32(T, orc, seed):
+    """FP32 per-path values and adjoints, FP64 sums: within FP32 rounding of the FP64 oracle."""
+    P = 3000
+    ops, obj = TP.random_program(seed)
+    theta = np.random.default_rng(100 + seed).uniform(0.2, 0.8, 4)
+    phil = 0x190104200 + seed
+    Z = orc.normals_fill(phil, 0, P, 6)
+    G_o, g_o, _ = TP.run_oracle(ops, obj, theta, Z)
+    prog, nodes = TP.build_product(ops, T)
+    ctx = T.TapeContext(prog, nodes[obj], 4, max_paths=P, precision="fp32")
+    G, g = ctx.value_and_grad(theta, phil, P)
+    assert abs(G.item() - G_o) <= 1e-5 * max(abs(G_o), 1.0)
+    assert rel(g.cpu().numpy(), g_o) <= 1e-4
+
+
+def test_heston_objective_fp32_equals_two_step_fp32(T):
+    """The FP32 tape of the Heston objective and the FP32 two-step kernels (same FP32 normals)."""
+    w = inputs.heston_config(n_paths=1 << 14, steps_per_year=64, T=2.0)
+    pb = w.problem
+    prog, G = T.heston_objective(pb, w.C)
+    ctx = T.TapeContext(prog, G, 5, max_paths=w.n_paths, precision="fp32")
+    Gt, gt = ctx.value_and_grad(w.theta, pb.seed, w.n_paths)
+    from paper_1901_04200_gb300 import _lib
+    c2 = _lib.Context(pb, max_paths=w.n_paths)
+    G2, g2, _ = c2.value_and_grad(w.theta, w.C, pb.seed, w.n_paths)
+    assert abs(Gt.item() - G2.item()) <= 1e-5 * abs(G2.item())
+    assert rel(gt.cpu().numpy(), g2.cpu().numpy()) <= 1e-4

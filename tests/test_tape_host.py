@@ -18,9 +18,11 @@ def built():
 def test_heston_program_has_two_stages():
     w = inputs.heston_config(n_paths=64, steps_per_year=8, T=1.0, n_mat=2, n_strike=2)
     prog, G = tape.heston_objective(w.problem, w.C)
-    st, ns, nrows, ws = tape.plan(prog, G, 5, 1000)
+    st, ns, nrows, ws, hb = tape.plan(prog, G, 5, 1000)
     assert st == _lib.MC_OK and ns == 2
     assert 0 < nrows < len(prog.nodes) and ws >= 2 * nrows * 1024 * 8
+    # the shared-memory window keeps most values and adjoints out of HBM
+    assert 0 < hb < 3 * 8 * nrows
 
 
 def test_stages_follow_expectation_use():
