@@ -655,7 +655,7 @@ struct mc_tape {
     int device = 0, precision = MC_FP64;
     TapePlan plan;
     DevLists lists;
-    int grid = 1, n_sm = 1;
+    int grid_f = 1, grid_b = 1, n_sm = 1;  // blocks of the path forward / backward kernels
     uint64_t max_paths = 0, stride = 0;
     size_t smem_fwd = 0, smem_bwd = 0;
     bool owns_ws = false;
@@ -688,7 +688,7 @@ uint64_t tape_stride(uint64_t max_paths) { return (max_paths + kWarp - 1) / kWar
 // Blocks: (resident blocks per SM) x SMs of the heavier path kernel, capped at
 // one block per 4 chunks of 32 paths.
 template <typename Real>
-mc_status tape_launch_shape(int device, const TapePlan &p, uint64_t max_paths, int *grid, int *n_sm,
+mc_status tape_launch_shape(int device, const TapePlan &p, uint64_t max_paths, int *grid_f, int *grid_b, int *n_sm,
                             size_t *smem_fwd, size_t *smem_bwd, std::string &why) {
     cudaError_t e = cudaDeviceGetAttribute(n_sm, cudaDevAttrMultiProcessorCount, device);
     if (e != cudaSuccess) {
@@ -711,9 +711,9 @@ mc_status tape_launch_shape(int device, const TapePlan &p, uint64_t max_paths, i
         why = cudaGetErrorString(e);
         return MC_ERR_CUDA;
     }
-    const int occ = std::max(1, std::min(occ_f, occ_b));
-    const uint64_t want = ((max_paths + kWarp - 1) / kWarp + kWarpsPerBlock - 1) / kWarpsPerBlock;
-    *grid = (int)std::min<uint64_t>((uint64_t)occ * *n_sm, std::max<uint64_t>(want, 1));
+    const uint64_t want = std::max<uint64_t>(((max_paths + kWarp - 1) / kWarp + kWarpsPerBlock - 1) / kWarpsPerBlock, 1);
+    *grid_f = (int)std::min<uint64_t>((uint64_t)std::max(occ_f, 1) * *n_sm, want);
+    *grid_b = (int)std::min<uint64_t>((uint64_t)std::max(occ_b, 1) * *n_sm, want);
     return MC_OK;
 }
 
@@ -730,7 +730,8 @@ mc_status run_tape(mc_tape *t, const double *theta, uint64_t seed, uint64_t path
     const RoundKeys rk = philox_round_keys(seed);
     const double inv_n = 1.0 / (double)n_paths;
     const uint64_t want = ((n_paths + kWarp - 1) / kWarp + kWarpsPerBlock - 1) / kWarpsPerBlock;
-    const int grid = (int)std::min<uint64_t>((uint64_t)t->grid, want);
+    const int grid_f = (int)std::min<uint64_t>((uint64_t)t->grid_f, want);
+    const int grid_b = (int)std::min<uint64_t>((uint64_t)t->grid_b, want);
     Real *tape = (Real *)t->tape, *adj = (Real *)t->adj;
     const size_t ring = (size_t)kTile * sizeof(DevNode) + (size_t)kRing * kBlock * sizeof(Real);
     auto ck = [&](const char *what) -> mc_status {
@@ -743,11 +744,11 @@ mc_status run_tape(mc_tape *t, const double *theta, uint64_t seed, uint64_t path
         const int ne = L.det_off[s + 1] - L.exp_off[s];
         if (nd > 0) tape_det_forward<<<1, 1, 0, st>>>(t->nodes + L.det_off[s], nd, theta, t->det);
         if (np > 0 || ne > 0)
-            tape_path_forward<Real><<<grid, kBlock, ring + (size_t)kWarpsPerBlock * ne * 8, st>>>(
+            tape_path_forward<Real><<<grid_f, kBlock, ring + (size_t)kWarpsPerBlock * ne * 8, st>>>(
                 t->nodes + L.path_off[s], np, t->nodes + L.exp_off[s], ne, t->det, tape, t->stride, rk, path0,
                 n_paths, t->part);
         if (ne > 0)
-            tape_expect_finalize<<<(ne + 127) / 128, 128, 0, st>>>(t->part, grid, t->nodes + L.exp_off[s], ne, inv_n,
+            tape_expect_finalize<<<(ne + 127) / 128, 128, 0, st>>>(t->part, grid_f, t->nodes + L.exp_off[s], ne, inv_n,
                                                                   t->det);
         mc_status r = ck("forward sweep");
         if (r != MC_OK) return r;
@@ -765,11 +766,11 @@ mc_status run_tape(mc_tape *t, const double *theta, uint64_t seed, uint64_t path
         const int ne = L.det_off[s + 1] - L.exp_off[s];
         const int na = L.darg_off[s + 1] - L.darg_off[s];
         if (np > 0 || ne > 0)
-            tape_path_backward<Real><<<grid, kBlock, ring + (size_t)kWarpsPerBlock * na * 8, st>>>(
+            tape_path_backward<Real><<<grid_b, kBlock, ring + (size_t)kWarpsPerBlock * na * 8, st>>>(
                 t->nodes + L.path_off[s], np, t->nodes + L.exp_off[s], ne, na, t->det, t->ddet, tape, adj, t->stride,
                 n_paths, t->part);
         if (na > 0)
-            tape_darg_finalize<<<(na + 127) / 128, 128, 0, st>>>(t->part, grid, t->dslot + L.darg_off[s], na, inv_n,
+            tape_darg_finalize<<<(na + 127) / 128, 128, 0, st>>>(t->part, grid_b, t->dslot + L.darg_off[s], na, inv_n,
                                                                 t->ddet);
         if (nd > 0) tape_det_backward<<<1, 1, 0, st>>>(t->nodes + L.det_off[s], nd, t->det, t->ddet, grad_out);
         mc_status r = ck("backward sweep");
@@ -833,15 +834,18 @@ mc_status mc_tape_create(int device, const mc_tape_node *nodes, int32_t n_nodes,
     t->stride = tape_stride(max_paths);
     t->lists = make_lists(nodes, t->plan);
     st = precision == MC_FP64
-             ? tape_launch_shape<double>(device, t->plan, max_paths, &t->grid, &t->n_sm, &t->smem_fwd, &t->smem_bwd, why)
-             : tape_launch_shape<float>(device, t->plan, max_paths, &t->grid, &t->n_sm, &t->smem_fwd, &t->smem_bwd, why);
+             ? tape_launch_shape<double>(device, t->plan, max_paths, &t->grid_f, &t->grid_b, &t->n_sm, &t->smem_fwd,
+                                         &t->smem_bwd, why)
+             : tape_launch_shape<float>(device, t->plan, max_paths, &t->grid_f, &t->grid_b, &t->n_sm, &t->smem_fwd,
+                                        &t->smem_bwd, why);
     if (st != MC_OK) {
         fprintf(stderr, "mc_tape_create: %s\n", why.c_str());
         delete t;
         return st;
     }
     const uint64_t blocks_cap = std::min<uint64_t>((max_paths + kBlock - 1) / kBlock, 32u * 1024u);
-    if ((uint64_t)t->grid > blocks_cap) t->grid = (int)std::max<uint64_t>(blocks_cap, 1);
+    if ((uint64_t)t->grid_f > blocks_cap) t->grid_f = (int)std::max<uint64_t>(blocks_cap, 1);
+    if ((uint64_t)t->grid_b > blocks_cap) t->grid_b = (int)std::max<uint64_t>(blocks_cap, 1);
     TapeWs W(t->plan, t->lists.all.size(), t->lists.darg_slot.size(), (int)std::max<uint64_t>(blocks_cap, 1),
              t->stride, rb);
     if (workspace) {
