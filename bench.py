@@ -241,6 +241,38 @@ def cpu_baseline(workload, n_paths, threads=None):
             "sample": "%d of the workload's paths x %d steps, FP64, value+grad, %.1f s wall" % (n_paths, steps, dt)}
 
 
+def cpu_baseline_tape(pb, theta, C, n_paths):
+    """The oracle's whole-program tape (FP64 numpy) on a bounded sample of the same program."""
+    import oracle
+    from oracle import tape as otape
+    Z = oracle.normals_fill(pb.seed, 0, n_paths, 2 * pb.n_steps)
+    t0 = time.perf_counter()
+    otape.full_tape_value_and_grad(pb, theta, C, Z)
+    dt = time.perf_counter() - t0
+    return {"value": n_paths * pb.last_step / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d paths x %d steps through the oracle's whole-program tape (FP64 numpy), %.1f s wall"
+                      % (n_paths, pb.last_step, dt)}
+
+
+def cpu_baseline_surrogate(B=4096, steps=3):
+    """The oracle MLP's differential-loss gradient and Adam step (FP64 numpy) at the same batch."""
+    import numpy as np
+    from oracle import mlp as omlp
+    rng = np.random.default_rng(0)
+    pv = omlp.flatten(omlp.init_params(0))
+    X = rng.uniform(-1, 1, (B, 7))
+    y = rng.uniform(0, 0.3, B)
+    dy = rng.standard_normal((B, 5)) * 0.05
+    m, v = np.zeros_like(pv), np.zeros_like(pv)
+    t0 = time.perf_counter()
+    for t in range(1, steps + 1):
+        _, g, _, _ = omlp.loss_grad(omlp.unflatten(pv), X, y, dy, 1.0)
+        pv, m, v = omlp.adam(pv, omlp.flatten(g), m, v, t, 1e-4)
+    dt = (time.perf_counter() - t0) / steps
+    return {"value": B / dt, "unit": "samples/s", "cores": os.cpu_count() or 1, "kind": "oracle",
+            "sample": "%d training steps at batch %d, FP64 numpy (BLAS threads), %.2f s per step" % (steps, B, dt)}
+
+
 def surrogate_flops_per_step(B=4096):
     """Dense FLOPs of the tensor-core GEMMs of one training step (2 M N K each,
     padded shapes as launched)."""
@@ -290,7 +322,9 @@ def surrogate_step_bench(args, rank, world):
     peaks, src = load_peaks()
     flops = surrogate_flops_per_step(B)
     if rank == 0:
+        base = cpu_baseline_surrogate(B) if (world == 1 and not args.no_cpu_baseline) else None
         print(json.dumps({
+            "cpu_baseline": base,
             "metric": "surrogate training samples/s (MLP 7->256x4->1, differential loss, batch 4096)",
             "value": world * B / (ms * 1e-3), "unit": "samples/s", "n_gpus": world, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -346,7 +380,9 @@ def tape_bench(args, rank, world):
     byts = P * per_path
     hbm = float(peaks["hbm_gbs"]) * 1e9
     if rank == 0:
+        base = cpu_baseline_tape(pb, w.theta, w.C, 4096) if (world == 1 and not args.no_cpu_baseline) else None
         print(json.dumps({
+            "cpu_baseline": base,
             "metric": "G+grad G path-steps/s by the expected-backward tape (Heston FT, %d paths x %d steps, "
                       "m=64, M=5)" % (P, S),
             "value": world * P * S / (ms * 1e-3), "unit": UNIT, "n_gpus": world, "steps": args.steps,

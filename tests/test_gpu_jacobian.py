@@ -112,3 +112,14 @@ def test_tangent_rejects_other_models(L):
     with pytest.raises(L.McError) as e:
         ctx.value_and_grad_tangent(w.theta, w.C, w.problem.seed, 64)
     assert e.value.status == L.MC_ERR_UNSUPPORTED
+
+
+@pytest.mark.slow
+def test_tangent_full_size_equals_adjoint(L):
+    """The bench's forward-mode arm (2^20 x 512) against the adjoint on the same paths."""
+    w = inputs.heston_config()
+    ctx = L.Context(w.problem, max_paths=w.n_paths)
+    Ga, ga, Ea = [t.cpu().numpy() for t in ctx.value_and_grad(w.theta, w.C, w.problem.seed, w.n_paths)]
+    Gt, gt, Et = [t.cpu().numpy() for t in ctx.value_and_grad_tangent(w.theta, w.C, w.problem.seed, w.n_paths)]
+    assert rel(Et, Ea) <= 1e-6
+    assert rel(gt, ga) <= 1e-4

@@ -371,3 +371,33 @@ def test_auto_storage_resolves(L):
     assert L.Context(w.problem, max_paths=4096).storage == "normals"
     for st in ("checkpoint", "normals", "full"):
         assert L.Context(with_pb(w, storage=st).problem, max_paths=4096).storage == st
+
+
+@pytest.mark.slow
+def test_slv_full_size_sampled(L, orc):
+    """Heston SLV at the bench's size (2^20 x 512, M = 95, stored normals): a 2^12-path slice at
+    the top of the range vs the oracle, and the full run equals the size-weighted combination of
+    its two halves."""
+    w = inputs.slv_config()
+    n = w.n_paths
+    ctx = L.Context(w.problem, max_paths=n)
+    assert ctx.storage == "normals"
+    p0 = n - (1 << 12)
+    Ey_s = ctx.forward(w.theta, w.problem.seed, 1 << 12, path0=p0).cpu().numpy()
+    assert rel(Ey_s, orc.forward(w.problem, w.theta, 1 << 12, path0=p0)) <= 2e-6
+    G, g, Ey = ctx.value_and_grad(w.theta, w.C, w.problem.seed, n)
+    Ey, g = Ey.cpu().numpy(), g.cpu().numpy()
+    h = n // 2
+    ga = ctx.value_and_grad(w.theta, w.C, w.problem.seed, h)[1].cpu().numpy()
+    gb = ctx.value_and_grad(w.theta, w.C, w.problem.seed, n - h, path0=h)[1].cpu().numpy()
+    a = ctx.forward(w.theta, w.problem.seed, h).cpu().numpy()
+    b = ctx.forward(w.theta, w.problem.seed, n - h, path0=h).cpu().numpy()
+    assert rel((a + b) / 2, Ey) <= 1e-12
+    assert np.all(np.isfinite(g))
+    # the gradient is linear in lambda: rebuild it from the halves' vjp with the full run's lambda
+    lam = Ey - w.C
+    ctx.forward(w.theta, w.problem.seed, h, keep=True)
+    va = ctx.vjp(lam).cpu().numpy()
+    ctx.forward(w.theta, w.problem.seed, n - h, path0=h, keep=True)
+    vb = ctx.vjp(lam).cpu().numpy()
+    assert rel((va + vb) / 2, g) <= 1e-5

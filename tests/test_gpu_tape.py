@@ -180,3 +180,17 @@ def test_heston_objective_fp32_equals_two_step_fp32(T):
     G2, g2, _ = c2.value_and_grad(w.theta, w.C, pb.seed, w.n_paths)
     assert abs(Gt.item() - G2.item()) <= 1e-5 * abs(G2.item())
     assert rel(gt.cpu().numpy(), g2.cpu().numpy()) <= 1e-4
+
+
+@pytest.mark.slow
+def test_heston_tape_bench_size_equals_two_step(T):
+    """The bench's tape run (2^18 paths x 512 steps, FP32) against the FP32 two-step kernels."""
+    w = inputs.heston_config(n_paths=1 << 18)
+    prog, G = T.heston_objective(w.problem, w.C)
+    ctx = T.TapeContext(prog, G, 5, max_paths=w.n_paths, precision="fp32")
+    Gt, gt = ctx.value_and_grad(w.theta, w.problem.seed, w.n_paths)
+    from paper_1901_04200_gb300 import _lib
+    c2 = _lib.Context(w.problem, max_paths=w.n_paths)
+    G2, g2, _ = c2.value_and_grad(w.theta, w.C, w.problem.seed, w.n_paths)
+    assert abs(Gt.item() - G2.item()) <= 1e-5 * abs(G2.item())
+    assert rel(gt.cpu().numpy(), g2.cpu().numpy()) <= 1e-4
