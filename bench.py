@@ -351,6 +351,9 @@ def tape_bench(args, rank, world):
     prog, G = tape.heston_objective(pb, w.C)
     dev = torch.device("cuda", torch.cuda.current_device())
     ctx = tape.TapeContext(prog, G, 5, max_paths=P, device=dev, precision=args.tape_precision)
+    compile_s, per_path = None, tape.plan(prog, G, 5, P, args.tape_precision)[4]  # interpreter HBM bytes per path
+    if not args.tape_interpret:
+        compile_s, per_path = ctx.compile(seg_nodes=args.tape_seg)  # outside the timed region
     theta = torch.tensor(w.theta, dtype=torch.float64, device=dev)
     out = (torch.empty(1, dtype=torch.float64, device=dev), torch.empty(5, dtype=torch.float64, device=dev))
     path0 = rank * P
@@ -376,7 +379,6 @@ def tape_bench(args, rank, world):
     clk = clocks.stop()
     ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world)
     peaks, src = load_peaks()
-    per_path = tape.plan(prog, G, 5, P, args.tape_precision)[4]  # the kernels' HBM bytes per path (mc_tape_plan)
     byts = P * per_path
     hbm = float(peaks["hbm_gbs"]) * 1e9
     if rank == 0:
@@ -390,6 +392,9 @@ def tape_bench(args, rank, world):
             "vs_baseline": None, "dtype": "f32" if args.tape_precision == "fp32" else "f64", "data": "synthetic",
             "config": {"workload": "tape_" + w.name, "paths_per_gpu": P, "steps": S, "nodes": len(prog.nodes),
                        "precision": args.tape_precision + " per-path values and adjoints, fp64 sums",
+                       "execution": "interpreter" if args.tape_interpret else
+                                    "compiled (segments of %s nodes, %.1f s run-time compilation)"
+                                    % (args.tape_seg or 384, compile_s),
                        "l2": "inputs larger than L2: %.1f GB of tape and adjoints" % (byts / 1e9)},
             "roofline": {"bound": "hbm", "achieved": byts / (ms * 1e-3) / 1e9, "peak": hbm / 1e9, "unit": "GB/s",
                          "frac": byts / (ms * 1e-3) / hbm, "traffic": None,
@@ -509,6 +514,9 @@ def main():
     ap.add_argument("--tape-paths", type=int, default=1 << 18, help="paths of the --workload tape run")
     ap.add_argument("--tape-precision", default="fp32", choices=["fp32", "fp64"],
                     help="per-path values and adjoints of the --workload tape run")
+    ap.add_argument("--tape-interpret", action="store_true",
+                    help="--workload tape: run the interpreter instead of the compiled program")
+    ap.add_argument("--tape-seg", type=int, default=0, help="--workload tape: nodes per compiled segment")
     ap.add_argument("--workload", default="heston", choices=["heston", "lv", "slv", "surrogate", "tape"],
                     help="heston (the metric's workload), lv (2^22 x 500 local vol) or surrogate "
                          "(one differential-loss training step of the pricing network), for measurement")

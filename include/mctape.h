@@ -122,6 +122,23 @@ const char *mc_tape_last_error(const mc_tape *t);
 mc_status mc_tape_value_and_grad(mc_tape *t, const double *theta, uint64_t seed, uint64_t path0,
                                  uint64_t n_paths, double *value_out, double *grad_out, void *stream);
 
+/* Compile the program (the GPU analogue of a tape compiler): each stage's
+ * per-path nodes are cut into segments of seg_nodes consecutive nodes (0: 384)
+ * and every segment becomes a straight-line forward kernel (values in
+ * registers) and a straight-line backward kernel (adjoints in registers),
+ * compiled at run time for sm_103a by NVRTC on `threads` host threads (0: all
+ * cores), without FMA contraction, and loaded on the tape's device.  Values
+ * cross a segment or stage boundary, and feed expectations and backward
+ * partials, through the HBM tape; the rest of the evaluation (deterministic
+ * nodes, expectations, fixed-order sums) is unchanged, so the results agree
+ * with the interpreter's to the rounding of the reordered sums.  Later
+ * mc_tape_value_and_grad calls run the compiled kernels.  Allocates a small
+ * device table.  seconds_out: wall time of the compilation (or NULL);
+ * hbm_bytes_out: HBM bytes per path of one compiled value and gradient (or
+ * NULL).  MC_ERR_UNSUPPORTED if the run-time compiler fails (mc_tape_last_error
+ * has the start of its log; the tape keeps interpreting). */
+mc_status mc_tape_compile(mc_tape *t, int32_t seg_nodes, int32_t threads, double *seconds_out, size_t *hbm_bytes_out);
+
 /* Per-path value of node `node` on the last evaluated paths (FP64 device
  * [n_paths]); MC_ERR_INVALID_ARG for a deterministic node,
  * MC_ERR_UNSUPPORTED for a per-path node that is not kept on the tape (one

@@ -21,7 +21,21 @@ LIB = os.path.join(PKG, "libmcaad.so")
 BUILD = os.path.join(PKG, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
-              "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]
+              "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC, "-I", BUILD]
+
+
+def _embed_common_header():
+    """The tape compiler hands mc_common.cuh (Philox, Box-Muller, warp sums) to the run-time
+    compiler, so the compiled programs draw exactly the library's normals: embed its text."""
+    with open(os.path.join(CSRC, "mc_common.cuh")) as f:
+        text = f.read()
+    assert ")MCSRC" not in text
+    out = os.path.join(BUILD, "mc_common_src.h")
+    body = '// generated by build.py from csrc/mc_common.cuh\nstatic const char kMcCommonSrc[] = R"MCSRC(' + \
+        text + ')MCSRC";\n'
+    if not os.path.exists(out) or open(out).read() != body:
+        with open(out, "w") as f:
+            f.write(body)
 
 
 def _nvcc() -> str:
@@ -51,6 +65,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
     if not force and up_to_date():
         return LIB
     os.makedirs(BUILD, exist_ok=True)
+    _embed_common_header()
     nvcc = _nvcc()
     flags = NVCC_FLAGS + list(extra_flags or [])
 
@@ -68,7 +83,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
     with cf.ThreadPoolExecutor(max_workers=min(len(srcs), os.cpu_count() or 4)) as ex:
         objs = list(ex.map(compile_one, srcs))
     tmp = LIB + ".%d.tmp" % os.getpid()
-    cmd = [nvcc] + ARCH + ["-shared", "--cudart", "shared", "-o", tmp] + objs + \
+    cmd = [nvcc] + ARCH + ["-shared", "--cudart", "shared", "-o", tmp] + objs + ["-lnvrtc"] + \
         ["-Xlinker", "-rpath," + os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "lib64")]
     res = subprocess.run(cmd, capture_output=True, text=True)
     if res.returncode != 0:

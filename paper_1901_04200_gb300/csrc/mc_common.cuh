@@ -2,8 +2,15 @@
 // Philox-4x32-10 (Salmon et al., SC'11), the uniform map, Box-Muller, warp
 // sums, and the parameter blocks handed to every kernel by value.
 #pragma once
+#ifdef __CUDACC_RTC__
+// compiled at run time (the tape compiler embeds this header): no system headers
+typedef unsigned int uint32_t;
+typedef unsigned long long uint64_t;
+typedef unsigned long size_t;
+#else
 #include <cuda_runtime.h>
 #include <stdint.h>
+#endif
 
 namespace mcaad {
 

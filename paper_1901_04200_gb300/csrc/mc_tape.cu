@@ -22,12 +22,19 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <nvrtc.h>
+
 #include <algorithm>
+#include <atomic>
+#include <chrono>
 #include <cmath>
+#include <sstream>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "mc_common.cuh"
+#include "mc_common_src.h"  // kMcCommonSrc: this header's text, for the run-time compiler
 #include "mctape.h"
 
 using namespace mcaad;
@@ -651,8 +658,39 @@ __global__ void tape_widen(const float *__restrict__ in, uint64_t n, double *__r
 
 }  // namespace
 
+// ------------------------------------------------------- tape compiler ----
+// A stage's per-path nodes are cut into segments of consecutive nodes; each
+// segment becomes two straight-line kernels (forward: values in registers;
+// backward: adjoints in registers) compiled at run time.  A value crosses a
+// segment or stage boundary, or feeds an expectation or a backward partial,
+// through the HBM tape; an adjoint contribution to a node outside the segment
+// goes to the HBM adjoint array.
+struct JitSeg {
+    int stage = 0;
+    std::vector<int> nodes;  // per-path nodes, program order
+    std::vector<int> dargs;  // deterministic nodes they use, first-use order
+    int darg_off = 0;        // offset of this segment's DET slots in the device list
+    std::string src, log;
+    std::vector<char> cubin;
+    cudaLibrary_t lib = nullptr;
+    cudaKernel_t fwd = nullptr, bwd = nullptr;
+    int grid_f = 1, grid_b = 1;
+    size_t smem_b = 0;
+};
+
+struct JitPlan {
+    std::vector<JitSeg> segs;           // stage order, then program order
+    std::vector<int> seg_begin;         // per stage: first segment; + end entry
+    std::vector<char> store, far;       // per node, compiled mode
+    std::vector<int> dslot;             // DET slot of every segment's accumulated arguments
+    int *dslot_dev = nullptr;
+    size_t bytes_per_path = 0;
+};
+
 struct mc_tape {
     int device = 0, precision = MC_FP64;
+    std::vector<mc_tape_node> src_nodes;  // the program as given (for the tape compiler)
+    JitPlan *jit = nullptr;               // compiled program, or null (interpreter)
     TapePlan plan;
     DevLists lists;
     int grid_f = 1, grid_b = 1, n_sm = 1;  // blocks of the path forward / backward kernels
@@ -781,6 +819,374 @@ mc_status run_tape(mc_tape *t, const double *theta, uint64_t seed, uint64_t path
 
 }  // namespace
 
+namespace {
+
+// ------------------------------------------------ tape compiler: plan ----
+
+JitPlan *make_jit_plan(const std::vector<mc_tape_node> &nodes, const TapePlan &p, int seg_nodes, size_t rb) {
+    JitPlan *J = new JitPlan;
+    const int n = p.n_nodes;
+    std::vector<int> seg_of(n, -1);
+    for (int s = 0; s < p.n_stages; ++s) {
+        J->seg_begin.push_back((int)J->segs.size());
+        const std::vector<int> &path = p.st[s].path;
+        for (size_t k0 = 0; k0 < path.size(); k0 += (size_t)seg_nodes) {
+            JitSeg sg;
+            sg.stage = s;
+            for (size_t k = k0; k < std::min(path.size(), k0 + (size_t)seg_nodes); ++k) {
+                sg.nodes.push_back(path[k]);
+                seg_of[path[k]] = (int)J->segs.size();
+            }
+            J->segs.push_back(std::move(sg));
+        }
+    }
+    J->seg_begin.push_back((int)J->segs.size());
+    J->store.assign(n, 0);
+    J->far.assign(n, 0);
+    for (int i = 0; i < n; ++i) {
+        const int args[2] = {nodes[i].a, nodes[i].b};
+        for (int q = 0; q < n_args(nodes[i].op); ++q) {
+            const int a = args[q];
+            if (p.cls[a] != 1) continue;
+            if (!(p.cls[i] == 1 && seg_of[i] == seg_of[a])) J->store[a] = J->far[a] = 1;  // outside user
+            if (needs_arg_value(nodes[i].op, q)) J->store[a] = 1;
+        }
+        if (p.cls[i] == 1 && needs_own_value(nodes[i].op)) J->store[i] = 1;
+    }
+    size_t b = 0;
+    for (int i = 0; i < n; ++i)
+        if (nodes[i].op == MC_OP_EXPECT && p.cls[nodes[i].a] == 1) b += 3 * rb;
+    for (size_t k = 0; k < J->segs.size(); ++k) {
+        JitSeg &sg = J->segs[k];
+        sg.darg_off = (int)J->dslot.size();
+        std::vector<int> fwd_loads, bwd_loads, far_rows;
+        auto add = [](std::vector<int> &v, int x) {
+            if (std::find(v.begin(), v.end(), x) == v.end()) v.push_back(x);
+        };
+        for (int i : sg.nodes) {
+            const int args[2] = {nodes[i].a, nodes[i].b};
+            if (J->store[i]) b += rb;
+            if (J->far[i]) b += rb;
+            if (needs_own_value(nodes[i].op)) add(bwd_loads, i);
+            for (int q = 0; q < n_args(nodes[i].op); ++q) {
+                const int a = args[q];
+                if (p.cls[a] == 0) {
+                    add(sg.dargs, a);
+                    continue;
+                }
+                if (seg_of[a] != (int)k) {
+                    add(fwd_loads, a);
+                    add(far_rows, a);
+                }
+                if (needs_arg_value(nodes[i].op, q)) add(bwd_loads, a);
+            }
+        }
+        b += rb * (fwd_loads.size() + bwd_loads.size()) + 2 * rb * far_rows.size();
+        for (int d : sg.dargs) J->dslot.push_back(-p.ref[d] - 1);
+    }
+    J->bytes_per_path = b;
+    return J;
+}
+
+// ---------------------------------------------- tape compiler: codegen ----
+
+std::string lit(double c) {
+    char buf[64];
+    snprintf(buf, sizeof buf, "%.17g", c);
+    std::string t(buf);
+    if (t.find_first_of(".eE") == std::string::npos) t += ".0";
+    return "R(" + t + ")";
+}
+
+std::string gen_segment(const std::vector<mc_tape_node> &nodes, const TapePlan &p, const JitPlan &J, int k,
+                        int precision) {
+    const JitSeg &sg = J.segs[k];
+    const bool f64 = precision == MC_FP64;
+    std::vector<int> local(p.n_nodes, -1);
+    for (size_t q = 0; q < sg.nodes.size(); ++q) local[sg.nodes[q]] = (int)q;
+    std::vector<int> dl(p.n_nodes, -1);
+    for (size_t q = 0; q < sg.dargs.size(); ++q) dl[sg.dargs[q]] = (int)q;
+    auto det_ref = [&](int a) { return "R(det[" + std::to_string(-p.ref[a] - 1) + "])"; };
+    std::ostringstream o;
+    o << "#include \"mc_common.cuh\"\ntypedef " << (f64 ? "double" : "float") << " R;\ntypedef unsigned long long u64;\n";
+
+    // forward: values in registers; loads of values from outside the segment at first use
+    o << "extern \"C\" __global__ void __launch_bounds__(128) fwd(const double *__restrict__ det, R *__restrict__ tape,"
+         " u64 stride, mcaad::RoundKeys rk, u64 path0, u64 n_paths) {\n"
+         " const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;\n"
+         " const u64 chunks = (n_paths + 31) / 32;\n"
+         " for (u64 ch = (u64)blockIdx.x * 4 + warp; ch < chunks; ch += (u64)gridDim.x * 4) {\n"
+         "  const u64 p = ch * 32 + lane;\n"
+         "  const bool active = p < n_paths;\n"
+         "  R *tp = tape + p;\n"
+         "  mcaad::PathNormals<R> rng;\n"
+         "  rng.init(path0 + (active ? p : 0));\n";
+    {
+        std::vector<char> loaded(p.n_nodes, 0);
+        long long call = -1;
+        auto val = [&](int a) -> std::string {
+            if (p.cls[a] == 0) return det_ref(a);
+            if (local[a] >= 0) return "v" + std::to_string(local[a]);
+            if (!loaded[a]) {
+                o << "  const R w" << p.ref[a] << " = tp[(u64)" << p.ref[a] << " * stride];\n";
+                loaded[a] = 1;
+            }
+            return "w" + std::to_string(p.ref[a]);
+        };
+        for (size_t q = 0; q < sg.nodes.size(); ++q) {
+            const int i = sg.nodes[q];
+            const mc_tape_node &d = nodes[i];
+            const std::string A = n_args(d.op) >= 1 ? val(d.a) : std::string();
+            const std::string B = n_args(d.op) == 2 ? val(d.b) : std::string();
+            std::string e;
+            switch (d.op) {
+            case MC_OP_NORMAL: {
+                const unsigned long long j = (unsigned long long)d.c;
+                if ((long long)(j >> 2) != call) {
+                    call = (long long)(j >> 2);
+                    o << "  rng.fill(" << call << "u, rk);\n";
+                }
+                e = "rng.z" + std::to_string(j & 3u);
+                break;
+            }
+            case MC_OP_ADD: e = A + " + " + B; break;
+            case MC_OP_SUB: e = A + " - " + B; break;
+            case MC_OP_MUL: e = A + " * " + B; break;
+            case MC_OP_DIV: e = A + " / " + B; break;
+            case MC_OP_ADDC: e = A + " + " + lit(d.c); break;
+            case MC_OP_MULC: e = A + " * " + lit(d.c); break;
+            case MC_OP_NEG: e = "-" + A; break;
+            case MC_OP_EXP: e = std::string(f64 ? "exp(" : "expf(") + A + ")"; break;
+            case MC_OP_LOG: e = std::string(f64 ? "log(" : "logf(") + A + ")"; break;
+            case MC_OP_SQRT: e = std::string(f64 ? "sqrt(" : "sqrtf(") + A + ")"; break;
+            case MC_OP_RELU: e = "(" + A + " > R(0) ? " + A + " : R(0))"; break;
+            case MC_OP_ABS: e = "(" + A + " < R(0) ? -" + A + " : " + A + ")"; break;
+            default: e = A; break;
+            }
+            o << "  const R v" << q << " = " << e << ";\n";
+            if (J.store[i]) o << "  tp[(u64)" << p.ref[i] << " * stride] = v" << q << ";\n";
+        }
+    }
+    o << " }\n}\n";
+
+    // backward: adjoints of the segment's nodes in registers; values its partials need loaded
+    // from the tape; contributions to nodes outside summed per row and added once
+    std::vector<int> far_rows;
+    for (int i : sg.nodes) {
+        const int args[2] = {nodes[i].a, nodes[i].b};
+        for (int q = 0; q < n_args(nodes[i].op); ++q) {
+            const int a = args[q];
+            if (p.cls[a] == 1 && local[a] < 0 && std::find(far_rows.begin(), far_rows.end(), a) == far_rows.end())
+                far_rows.push_back(a);
+        }
+    }
+    o << "extern \"C\" __global__ void __launch_bounds__(128) bwd(const double *__restrict__ det,"
+         " const R *__restrict__ tape, R *__restrict__ adj, u64 stride, u64 n_paths, double *__restrict__ part,"
+         " int n_darg) {\n"
+         " extern __shared__ double wacc[];\n"
+         " for (int q = threadIdx.x; q < 4 * n_darg; q += blockDim.x) wacc[q] = 0.0;\n"
+         " __syncthreads();\n"
+         " const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;\n"
+         " double *wrow = wacc + warp * n_darg;\n"
+         " const u64 chunks = (n_paths + 31) / 32;\n"
+         " for (u64 ch = (u64)blockIdx.x * 4 + warp; ch < chunks; ch += (u64)gridDim.x * 4) {\n"
+         "  const u64 p = ch * 32 + lane;\n"
+         "  const bool active = p < n_paths;\n"
+         "  const R *tv = tape + p;\n"
+         "  R *ta = adj + p;\n";
+    for (size_t q = 0; q < sg.nodes.size(); ++q) o << "  R a" << q << " = R(0);\n";
+    for (int a : far_rows) o << "  R f" << p.ref[a] << " = R(0);\n";
+    {
+        std::vector<char> vloaded(p.n_nodes, 0);
+        auto value = [&](int a) -> std::string {
+            if (p.cls[a] == 0) return det_ref(a);
+            if (!vloaded[a]) {
+                o << "  const R u" << p.ref[a] << " = tv[(u64)" << p.ref[a] << " * stride];\n";
+                vloaded[a] = 1;
+            }
+            return "u" + std::to_string(p.ref[a]);
+        };
+        auto contrib = [&](int a, const std::string &g) {
+            if (p.cls[a] == 0)
+                o << "  { const R s = mcaad::warp_sum(" << g << "); if (lane == 0) wrow[" << dl[a] << "] += (double)s; }\n";
+            else if (local[a] >= 0)
+                o << "  a" << local[a] << " += " << g << ";\n";
+            else
+                o << "  f" << p.ref[a] << " += " << g << ";\n";
+        };
+        for (int q = (int)sg.nodes.size() - 1; q >= 0; --q) {
+            const int i = sg.nodes[q];
+            const mc_tape_node &d = nodes[i];
+            const std::string D = "D" + std::to_string(q);
+            if (J.far[i])
+                o << "  const R " << D << " = active ? a" << q << " + ta[(u64)" << p.ref[i] << " * stride] : R(0);\n";
+            else
+                o << "  const R " << D << " = active ? a" << q << " : R(0);\n";
+            switch (d.op) {
+            case MC_OP_NORMAL: break;
+            case MC_OP_ADD: contrib(d.a, D); contrib(d.b, D); break;
+            case MC_OP_SUB: contrib(d.a, D); contrib(d.b, "-" + D); break;
+            case MC_OP_MUL: {
+                const std::string va = value(d.a), vb = value(d.b);
+                contrib(d.a, D + " * " + vb);
+                contrib(d.b, D + " * " + va);
+                break;
+            }
+            case MC_OP_DIV: {
+                const std::string va = value(d.a), vb = value(d.b);
+                contrib(d.a, D + " * (R(1) / " + vb + ")");
+                contrib(d.b, D + " * (-" + va + " / (" + vb + " * " + vb + "))");
+                break;
+            }
+            case MC_OP_ADDC: contrib(d.a, D); break;
+            case MC_OP_MULC: contrib(d.a, D + " * " + lit(d.c)); break;
+            case MC_OP_NEG: contrib(d.a, "-" + D); break;
+            case MC_OP_EXP: contrib(d.a, D + " * " + value(i)); break;
+            case MC_OP_LOG: contrib(d.a, D + " * (R(1) / " + value(d.a) + ")"); break;
+            case MC_OP_SQRT: {
+                const std::string va = value(d.a), m = value(i);
+                contrib(d.a, D + " * (" + va + " > R(0) ? R(0.5) / " + m + " : R(0))");
+                break;
+            }
+            case MC_OP_RELU: {
+                const std::string va = value(d.a);
+                contrib(d.a, D + " * (" + va + " > R(0) ? R(1) : R(0))");
+                break;
+            }
+            case MC_OP_ABS: {
+                const std::string va = value(d.a);
+                contrib(d.a, D + " * (" + va + " > R(0) ? R(1) : (" + va + " < R(0) ? R(-1) : R(0)))");
+                break;
+            }
+            default: break;
+            }
+        }
+    }
+    for (int a : far_rows) o << "  if (active) ta[(u64)" << p.ref[a] << " * stride] += f" << p.ref[a] << ";\n";
+    o << " }\n"
+         " __syncthreads();\n"
+         " for (int k = threadIdx.x; k < n_darg; k += blockDim.x) {\n"
+         "  double s = 0.0;\n"
+         "  for (int w = 0; w < 4; ++w) s += wacc[w * n_darg + k];\n"
+         "  part[(u64)blockIdx.x * n_darg + k] = s;\n"
+         " }\n}\n";
+    return o.str();
+}
+
+bool rtc_compile(JitSeg &sg) {
+    nvrtcProgram prog;
+    const char *hdr[] = {kMcCommonSrc};
+    const char *hdr_name[] = {"mc_common.cuh"};
+    if (nvrtcCreateProgram(&prog, sg.src.c_str(), "tape_segment.cu", 1, hdr, hdr_name) != NVRTC_SUCCESS) {
+        sg.log = "nvrtcCreateProgram failed";
+        return false;
+    }
+    const char *opts[] = {"--gpu-architecture=sm_103a", "-std=c++17", "--fmad=false"};
+    const nvrtcResult r = nvrtcCompileProgram(prog, 3, opts);
+    size_t ls = 0;
+    nvrtcGetProgramLogSize(prog, &ls);
+    sg.log.assign(ls, '\0');
+    if (ls) nvrtcGetProgramLog(prog, &sg.log[0]);
+    bool ok = r == NVRTC_SUCCESS;
+    if (ok) {
+        size_t cs = 0;
+        ok = nvrtcGetCUBINSize(prog, &cs) == NVRTC_SUCCESS && cs > 0;
+        if (ok) {
+            sg.cubin.resize(cs);
+            ok = nvrtcGetCUBIN(prog, sg.cubin.data()) == NVRTC_SUCCESS;
+        }
+    }
+    nvrtcDestroyProgram(&prog);
+    return ok;
+}
+
+void jit_free(JitPlan *J) {
+    if (!J) return;
+    for (JitSeg &sg : J->segs)
+        if (sg.lib) cudaLibraryUnload(sg.lib);
+    if (J->dslot_dev) cudaFree(J->dslot_dev);
+    delete J;
+}
+
+// One value and gradient with the compiled segments (the deterministic nodes,
+// the expectations' sums and adds, and the finalize steps as in the interpreter).
+template <typename Real>
+mc_status run_tape_jit(mc_tape *t, const double *theta, uint64_t seed, uint64_t path0, uint64_t n_paths,
+                       double *value_out, double *grad_out, cudaStream_t st) {
+    const TapePlan &p = t->plan;
+    const DevLists &L = t->lists;
+    const JitPlan &J = *t->jit;
+    RoundKeys rk = philox_round_keys(seed);
+    const double inv_n = 1.0 / (double)n_paths;
+    const uint64_t want = ((n_paths + kWarp - 1) / kWarp + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    const int grid_f = (int)std::min<uint64_t>((uint64_t)t->grid_f, want);
+    const int grid_b = (int)std::min<uint64_t>((uint64_t)t->grid_b, want);
+    Real *tape = (Real *)t->tape, *adj = (Real *)t->adj;
+    uint64_t stride = t->stride;
+    const size_t ring = (size_t)kTile * sizeof(DevNode) + (size_t)kRing * kBlock * sizeof(Real);
+    auto ck = [&](const char *what) -> mc_status {
+        const cudaError_t e = cudaGetLastError();
+        return e == cudaSuccess ? MC_OK : tfail(t, MC_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+    };
+    for (int s = 0; s < p.n_stages; ++s) {
+        const int nd = L.path_off[s] - L.det_off[s];
+        const int ne = L.det_off[s + 1] - L.exp_off[s];
+        if (nd > 0) tape_det_forward<<<1, 1, 0, st>>>(t->nodes + L.det_off[s], nd, theta, t->det);
+        for (int k = J.seg_begin[s]; k < J.seg_begin[s + 1]; ++k) {
+            const JitSeg &sg = J.segs[k];
+            const double *det = t->det;
+            void *args[] = {(void *)&det, (void *)&tape, (void *)&stride, (void *)&rk, (void *)&path0, (void *)&n_paths};
+            const int g = (int)std::min<uint64_t>((uint64_t)sg.grid_f, want);
+            const cudaError_t e = cudaLaunchKernel((const void *)sg.fwd, dim3(g), dim3(kBlock), args, 0, st);
+            if (e != cudaSuccess) return tfail(t, MC_ERR_CUDA, "compiled forward: %s", cudaGetErrorString(e));
+        }
+        if (ne > 0) {  // the expectations' sums, read back from the tape
+            tape_path_forward<Real><<<grid_f, kBlock, ring + (size_t)kWarpsPerBlock * ne * 8, st>>>(
+                t->nodes + L.path_off[s], 0, t->nodes + L.exp_off[s], ne, t->det, tape, stride, rk, path0, n_paths,
+                t->part);
+            tape_expect_finalize<<<(ne + 127) / 128, 128, 0, st>>>(t->part, grid_f, t->nodes + L.exp_off[s], ne, inv_n,
+                                                                  t->det);
+        }
+        mc_status r = ck("forward sweep");
+        if (r != MC_OK) return r;
+    }
+    tape_copy_value<<<1, 1, 0, st>>>(t->det, -p.ref[p.objective] - 1, value_out);
+    if (p.n_rows > 0) {
+        const cudaError_t e = cudaMemsetAsync(adj, 0, (size_t)p.n_rows * stride * sizeof(Real), st);
+        if (e != cudaSuccess) return tfail(t, MC_ERR_CUDA, "adjoint reset: %s", cudaGetErrorString(e));
+    }
+    tape_begin_backward<<<(std::max(p.n_det, p.n_params) + 255) / 256 + 1, 256, 0, st>>>(
+        t->ddet, p.n_det, -p.ref[p.objective] - 1, grad_out, p.n_params);
+    for (int s = p.n_stages - 1; s >= 0; --s) {
+        const int nd = L.path_off[s] - L.det_off[s];
+        const int ne = L.det_off[s + 1] - L.exp_off[s];
+        if (ne > 0)  // E(D) of each expectation into its argument's adjoint
+            tape_path_backward<Real><<<grid_b, kBlock, ring, st>>>(t->nodes + L.path_off[s], 0, t->nodes + L.exp_off[s],
+                                                                   ne, 0, t->det, t->ddet, tape, adj, stride, n_paths,
+                                                                   t->part);
+        for (int k = J.seg_begin[s + 1] - 1; k >= J.seg_begin[s]; --k) {
+            const JitSeg &sg = J.segs[k];
+            const double *det = t->det;
+            double *part = t->part;
+            int na = (int)sg.dargs.size();
+            void *args[] = {(void *)&det, (void *)&tape, (void *)&adj, (void *)&stride, (void *)&n_paths, (void *)&part,
+                            (void *)&na};
+            const int g = (int)std::min<uint64_t>((uint64_t)sg.grid_b, want);
+            const cudaError_t e = cudaLaunchKernel((const void *)sg.bwd, dim3(g), dim3(kBlock), args, sg.smem_b, st);
+            if (e != cudaSuccess) return tfail(t, MC_ERR_CUDA, "compiled backward: %s", cudaGetErrorString(e));
+            if (na > 0)
+                tape_darg_finalize<<<(na + 127) / 128, 128, 0, st>>>(t->part, g, J.dslot_dev + sg.darg_off, na, inv_n,
+                                                                    t->ddet);
+        }
+        if (nd > 0) tape_det_backward<<<1, 1, 0, st>>>(t->nodes + L.det_off[s], nd, t->det, t->ddet, grad_out);
+        mc_status r = ck("backward sweep");
+        if (r != MC_OK) return r;
+    }
+    return MC_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 mc_status mc_tape_plan(const mc_tape_node *nodes, int32_t n_nodes, int32_t objective, int32_t n_params,
@@ -830,6 +1236,7 @@ mc_status mc_tape_create(int device, const mc_tape_node *nodes, int32_t n_nodes,
     }
     t->device = device;
     t->precision = precision;
+    t->src_nodes.assign(nodes, nodes + n_nodes);
     t->max_paths = max_paths;
     t->stride = tape_stride(max_paths);
     t->lists = make_lists(nodes, t->plan);
@@ -886,6 +1293,7 @@ mc_status mc_tape_create(int device, const mc_tape_node *nodes, int32_t n_nodes,
 void mc_tape_destroy(mc_tape *t) {
     if (!t) return;
     cudaSetDevice(t->device);
+    jit_free(t->jit);
     if (t->owns_ws && t->ws) cudaFree(t->ws);
     delete t;
 }
@@ -903,9 +1311,14 @@ mc_status mc_tape_value_and_grad(mc_tape *t, const double *theta, uint64_t seed,
         ((uintptr_t)value_out & 7u) || ((uintptr_t)grad_out & 7u))
         return tfail(t, MC_ERR_INVALID_ARG, "theta, value_out and grad_out must be FP64 device pointers");
     if (path0 + n_paths < path0) return tfail(t, MC_ERR_INVALID_ARG, "path range overflows");
-    const mc_status r = t->precision == MC_FP64
-                            ? run_tape<double>(t, theta, seed, path0, n_paths, value_out, grad_out, (cudaStream_t)stream)
-                            : run_tape<float>(t, theta, seed, path0, n_paths, value_out, grad_out, (cudaStream_t)stream);
+    cudaStream_t st = (cudaStream_t)stream;
+    mc_status r;
+    if (t->jit)
+        r = t->precision == MC_FP64 ? run_tape_jit<double>(t, theta, seed, path0, n_paths, value_out, grad_out, st)
+                                    : run_tape_jit<float>(t, theta, seed, path0, n_paths, value_out, grad_out, st);
+    else
+        r = t->precision == MC_FP64 ? run_tape<double>(t, theta, seed, path0, n_paths, value_out, grad_out, st)
+                                    : run_tape<float>(t, theta, seed, path0, n_paths, value_out, grad_out, st);
     if (r == MC_OK) t->last_n = n_paths;
     return r;
 }
@@ -914,7 +1327,7 @@ mc_status mc_tape_path_values(mc_tape *t, int32_t node, double *out, void *strea
     if (!t) return MC_ERR_INVALID_ARG;
     if (node < 0 || node >= t->plan.n_nodes || t->plan.cls[node] != 1 || !out || ((uintptr_t)out & 7u))
         return tfail(t, MC_ERR_INVALID_ARG, "node %d is not a per-path node, or out is not FP64-aligned", node);
-    if (!t->lists.stored[node])
+    if (!(t->jit ? t->jit->store[node] : t->lists.stored[node]))
         return tfail(t, MC_ERR_UNSUPPORTED, "node %d is not kept on the tape (nothing reads it from there)", node);
     if (t->last_n == 0) return tfail(t, MC_ERR_STATE, "no evaluation yet");
     const size_t rb = t->precision == MC_FP64 ? 8 : 4;
@@ -928,6 +1341,69 @@ mc_status mc_tape_path_values(mc_tape *t, int32_t node, double *out, void *strea
     tape_widen<<<blocks, 256, 0, st>>>((const float *)row, t->last_n, out);
     const cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? MC_OK : tfail(t, MC_ERR_CUDA, "widen: %s", cudaGetErrorString(e));
+}
+
+mc_status mc_tape_compile(mc_tape *t, int32_t seg_nodes, int32_t threads, double *seconds_out,
+                          size_t *hbm_bytes_out) {
+    if (!t) return MC_ERR_INVALID_ARG;
+    if (seg_nodes <= 0) seg_nodes = 384;
+    if (threads <= 0) threads = (int)std::max(1u, std::thread::hardware_concurrency());
+    const auto t0 = std::chrono::steady_clock::now();
+    const size_t rb = t->precision == MC_FP64 ? 8 : 4;
+    JitPlan *J = make_jit_plan(t->src_nodes, t->plan, seg_nodes, rb);
+    const int nseg = (int)J->segs.size();
+    for (int k = 0; k < nseg; ++k) J->segs[k].src = gen_segment(t->src_nodes, t->plan, *J, k, t->precision);
+    std::atomic<int> next(0), failed(-1);
+    auto work = [&]() {
+        for (int k = next++; k < nseg; k = next++)
+            if (!rtc_compile(J->segs[k])) failed = k;
+    };
+    std::vector<std::thread> pool;
+    for (int q = 0; q < std::min(threads, std::max(nseg, 1)); ++q) pool.emplace_back(work);
+    for (std::thread &th : pool) th.join();
+    if (failed >= 0) {
+        const std::string head = J->segs[failed].log.substr(0, 400);
+        jit_free(J);
+        return tfail(t, MC_ERR_UNSUPPORTED, "run-time compilation of segment %d failed: %s", (int)failed, head.c_str());
+    }
+    cudaSetDevice(t->device);
+    for (JitSeg &sg : J->segs) {
+        cudaError_t e = cudaLibraryLoadData(&sg.lib, sg.cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
+        if (e == cudaSuccess) e = cudaLibraryGetKernel(&sg.fwd, sg.lib, "fwd");
+        if (e == cudaSuccess) e = cudaLibraryGetKernel(&sg.bwd, sg.lib, "bwd");
+        sg.smem_b = (size_t)kWarpsPerBlock * sg.dargs.size() * 8;
+        if (e == cudaSuccess && sg.smem_b > 48 * 1024)
+            e = cudaFuncSetAttribute((const void *)sg.bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sg.smem_b);
+        int occ_f = 0, occ_b = 0;
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_f, (const void *)sg.fwd, kBlock, 0);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_b, (const void *)sg.bwd, kBlock, sg.smem_b);
+        if (e != cudaSuccess) {
+            jit_free(J);
+            return tfail(t, MC_ERR_CUDA, "loading a compiled segment: %s", cudaGetErrorString(e));
+        }
+        const uint64_t cap = std::min<uint64_t>((t->max_paths + kBlock - 1) / kBlock, 32u * 1024u);
+        sg.grid_f = (int)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)std::max(occ_f, 1) * t->n_sm, cap));
+        sg.grid_b = (int)std::max<uint64_t>(1, std::min<uint64_t>((uint64_t)std::max(occ_b, 1) * t->n_sm, cap));
+        sg.cubin.clear();
+        sg.cubin.shrink_to_fit();
+        sg.src.clear();
+    }
+    if (!J->dslot.empty()) {
+        cudaError_t e = cudaMalloc((void **)&J->dslot_dev, J->dslot.size() * 4);
+        if (e == cudaSuccess) e = cudaMemcpy(J->dslot_dev, J->dslot.data(), J->dslot.size() * 4, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            jit_free(J);
+            return tfail(t, MC_ERR_CUDA, "segment tables: %s", cudaGetErrorString(e));
+        }
+    }
+    jit_free(t->jit);
+    t->jit = J;
+    t->last_n = 0;
+    if (seconds_out)
+        *seconds_out = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (hbm_bytes_out) *hbm_bytes_out = J->bytes_per_path;
+    return MC_OK;
 }
 
 }  // extern "C"

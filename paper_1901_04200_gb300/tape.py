@@ -172,6 +172,15 @@ class TapeContext:
         self._n = int(n_paths)
         return val, grad[:self.n_params]
 
+    def compile(self, seg_nodes: int = 0, threads: int = 0):
+        """Compile the program into straight-line kernels (mc_tape_compile); returns
+        (compile seconds, HBM bytes per path of one compiled value and gradient)."""
+        from . import _lib
+        sec, hb = ctypes.c_double(0.0), ctypes.c_size_t(0)
+        self._check(_lib.load().mc_tape_compile(self.handle, int(seg_nodes), int(threads), ctypes.byref(sec),
+                                                ctypes.byref(hb)))
+        return sec.value, hb.value
+
     def path_values(self, node: Node, stream=None):
         """Per-path values of a per-path node on the last evaluated paths."""
         import torch

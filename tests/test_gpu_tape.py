@@ -194,3 +194,45 @@ def test_heston_tape_bench_size_equals_two_step(T):
     G2, g2, _ = c2.value_and_grad(w.theta, w.C, w.problem.seed, w.n_paths)
     assert abs(Gt.item() - G2.item()) <= 1e-5 * abs(G2.item())
     assert rel(gt.cpu().numpy(), g2.cpu().numpy()) <= 1e-4
+
+
+# ------------------------------------------------------ compiled programs
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
+@pytest.mark.parametrize("seed,seg", [(1, 40), (3, 7), (4, 1000)])
+def test_compiled_equals_interpreter_and_oracle(T, orc, seed, seg, precision, tol):
+    """mc_tape_compile: straight-line segment kernels give the interpreter's results (to the
+    rounding of reordered sums) and the oracle's."""
+    P = 3000
+    ops, obj = TP.random_program(seed)
+    theta = np.random.default_rng(100 + seed).uniform(0.2, 0.8, 4)
+    phil = 0x190104200 + seed
+    prog, nodes = TP.build_product(ops, T)
+    a = T.TapeContext(prog, nodes[obj], 4, max_paths=P, precision=precision)
+    Ga, ga = a.value_and_grad(theta, phil, P)
+    b = T.TapeContext(prog, nodes[obj], 4, max_paths=P, precision=precision)
+    sec, hb = b.compile(seg_nodes=seg)
+    assert sec > 0 and hb > 0
+    Gb, gb = b.value_and_grad(theta, phil, P)
+    assert abs(Gb.item() - Ga.item()) <= tol * max(abs(Ga.item()), 1.0)
+    assert rel(gb.cpu().numpy(), ga.cpu().numpy()) <= 10 * tol
+    if precision == "fp64":
+        Z = orc.normals_fill(phil, 0, P, 6)
+        G_o, g_o, vals = TP.run_oracle(ops, obj, theta, Z)
+        assert abs(Gb.item() - G_o) <= 1e-12 * max(abs(G_o), 1.0)
+        assert rel(gb.cpu().numpy(), g_o) <= 1e-10
+        for k in sorted({x for op, x, _, _ in ops if op == "expect"}):
+            if not _is_det(ops, k):
+                assert rel(b.path_values(nodes[k]).cpu().numpy(), vals[k].v) <= 1e-12
+
+
+def test_compiled_heston_objective_equals_two_step(T, orc):
+    w = inputs.heston_config(n_paths=2000, steps_per_year=16, T=1.0, n_mat=4, n_strike=3)
+    pb = replace(w.problem, precision="fp64", ckpt_every=4)
+    prog, G = T.heston_objective(pb, w.C)
+    ctx = T.TapeContext(prog, G, 5, max_paths=2000)
+    ctx.compile(seg_nodes=64)
+    Gt, gt = ctx.value_and_grad(w.theta, pb.seed, 2000, path0=77)
+    _, Go, go = orc.value_and_grad(pb, w.theta, w.C, 2000, path0=77)
+    assert abs(Gt.item() - Go) <= 1e-10 * abs(Go)
+    assert rel(gt.cpu().numpy(), go) <= 1e-9
