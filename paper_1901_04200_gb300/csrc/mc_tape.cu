@@ -386,23 +386,38 @@ __device__ __forceinline__ void stage_tile(DevNode *tile, const DevNode *__restr
     for (int q = threadIdx.x; q < cnt * kWords; q += blockDim.x) dst[q] = src[q];
 }
 
-// Deterministic nodes of a stage, in program order (one thread).
+// Deterministic nodes of a stage, in program order, by one thread; the block
+// first stages the deterministic values in shared memory when they fit
+// (in_smem), so the walk's dependent loads do not go to L2.
+constexpr int kDetSmemBytes = 48 * 1024;
+
 __global__ void tape_det_forward(const DevNode *__restrict__ nd, int n, const double *__restrict__ theta,
-                                 double *__restrict__ det) {
-    if (blockIdx.x != 0 || threadIdx.x != 0) return;
-    for (int k = 0; k < n; ++k) {
-        const DevNode d = nd[k];
-        double v;
-        if (d.op == MC_OP_PARAM) {
-            v = theta[(int)d.c];
-        } else if (d.op == MC_OP_CONST) {
-            v = d.c;
-        } else {
-            const double a = det[-d.ra - 1];
-            const double b = n_args(d.op) == 2 ? det[-d.rb - 1] : 0.0;
-            v = apply_op<double>(d.op, a, b, d.c);
+                                 double *__restrict__ det, int n_det, int in_smem) {
+    extern __shared__ double sdet[];
+    double *V = in_smem ? sdet : det;
+    if (in_smem) {
+        for (int q = threadIdx.x; q < n_det; q += blockDim.x) sdet[q] = det[q];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < n; ++k) {
+            const DevNode d = nd[k];
+            double v;
+            if (d.op == MC_OP_PARAM) {
+                v = theta[(int)d.c];
+            } else if (d.op == MC_OP_CONST) {
+                v = d.c;
+            } else {
+                const double a = V[-d.ra - 1];
+                const double b = n_args(d.op) == 2 ? V[-d.rb - 1] : 0.0;
+                v = apply_op<double>(d.op, a, b, d.c);
+            }
+            V[-d.rm - 1] = v;
         }
-        det[-d.rm - 1] = v;
+    }
+    if (in_smem) {
+        __syncthreads();
+        for (int q = threadIdx.x; q < n_det; q += blockDim.x) det[q] = sdet[q];
     }
 }
 
@@ -497,13 +512,17 @@ __global__ void __launch_bounds__(kBlock) tape_path_forward(const DevNode *__res
     }
 }
 
-// Expectation k = (sum over blocks in order) / n.
+// Expectation k = (sum over blocks) / n: one warp per expectation, lane l
+// sums blocks l, l + 32, ... in order, then a fixed shuffle tree.
 __global__ void tape_expect_finalize(const double *__restrict__ part, int nb, const DevNode *__restrict__ ex,
                                      int n_exp, double inv_n, double *__restrict__ det) {
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n_exp; k += gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x % kWarp;
+    const int warps = gridDim.x * blockDim.x / kWarp;
+    for (int k = (blockIdx.x * blockDim.x + threadIdx.x) / kWarp; k < n_exp; k += warps) {
         double s = 0.0;
-        for (int b = 0; b < nb; ++b) s += part[(size_t)b * n_exp + k];
-        det[-ex[k].rm - 1] = s * inv_n;
+        for (int b = lane; b < nb; b += kWarp) s += part[(size_t)b * n_exp + k];
+        s = warp_sum(s);
+        if (lane == 0) det[-ex[k].rm - 1] = s * inv_n;
     }
 }
 
@@ -607,37 +626,76 @@ __global__ void __launch_bounds__(kBlock) tape_path_backward(const DevNode *__re
     }
 }
 
-// Adjoint means of the stage's deterministic arguments: += (sum over blocks in order) / n.
+// Adjoint means of the stage's deterministic arguments: += (sum over blocks) / n,
+// one warp per argument as in tape_expect_finalize.
 __global__ void tape_darg_finalize(const double *__restrict__ part, int nb, const int *__restrict__ slot,
                                    int n_darg, double inv_n, double *__restrict__ ddet) {
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n_darg; k += gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x % kWarp;
+    const int warps = gridDim.x * blockDim.x / kWarp;
+    for (int k = (blockIdx.x * blockDim.x + threadIdx.x) / kWarp; k < n_darg; k += warps) {
         double s = 0.0;
-        for (int b = 0; b < nb; ++b) s += part[(size_t)b * n_darg + k];
-        ddet[slot[k]] += s * inv_n;
+        for (int b = lane; b < nb; b += kWarp) s += part[(size_t)b * n_darg + k];
+        s = warp_sum(s);
+        if (lane == 0) ddet[slot[k]] += s * inv_n;
     }
 }
 
-// Deterministic nodes of a stage in reverse (one thread); a parameter's
-// adjoint mean is added to its gradient component.
+// Deterministic nodes of a stage in reverse, by one thread (values and
+// adjoints staged in shared memory when they fit); a parameter's adjoint mean
+// is added to its gradient component.
 __global__ void tape_det_backward(const DevNode *__restrict__ nd, int n, const double *__restrict__ det,
-                                  double *__restrict__ ddet, double *__restrict__ grad) {
-    if (blockIdx.x != 0 || threadIdx.x != 0) return;
-    for (int k = n - 1; k >= 0; --k) {
-        const DevNode d = nd[k];
-        const double D = ddet[-d.rm - 1];
-        if (d.op == MC_OP_PARAM) {
-            grad[(int)d.c] += D;
-            continue;
+                                  double *__restrict__ ddet, double *__restrict__ grad, int n_det, int in_smem) {
+    extern __shared__ double sdet[];
+    const double *V = in_smem ? sdet : det;
+    double *A = in_smem ? sdet + n_det : ddet;
+    if (in_smem) {
+        for (int q = threadIdx.x; q < n_det; q += blockDim.x) {
+            sdet[q] = det[q];
+            sdet[n_det + q] = ddet[q];
         }
-        if (d.op == MC_OP_CONST) continue;
-        const bool two = n_args(d.op) == 2;
-        const double a = det[-d.ra - 1];
-        const double b = two ? det[-d.rb - 1] : 0.0;
-        double pa, pb;
-        partials<double>(d.op, a, b, det[-d.rm - 1], d.c, pa, pb);
-        ddet[-d.ra - 1] += D * pa;
-        if (two) ddet[-d.rb - 1] += D * pb;
+        __syncthreads();
     }
+    if (threadIdx.x == 0) {
+        for (int k = n - 1; k >= 0; --k) {
+            const DevNode d = nd[k];
+            const double D = A[-d.rm - 1];
+            if (d.op == MC_OP_PARAM) {
+                grad[(int)d.c] += D;
+                continue;
+            }
+            if (d.op == MC_OP_CONST) continue;
+            const bool two = n_args(d.op) == 2;
+            const double a = V[-d.ra - 1];
+            const double b = two ? V[-d.rb - 1] : 0.0;
+            double pa, pb;
+            partials<double>(d.op, a, b, V[-d.rm - 1], d.c, pa, pb);
+            A[-d.ra - 1] += D * pa;
+            if (two) A[-d.rb - 1] += D * pb;
+        }
+    }
+    if (in_smem) {
+        __syncthreads();
+        for (int q = threadIdx.x; q < n_det; q += blockDim.x) ddet[q] = sdet[n_det + q];
+    }
+}
+
+// Launchers (shared by the interpreter and the compiled program).
+void launch_det_forward(const DevNode *nd, int n, const double *theta, double *det, int n_det, cudaStream_t st) {
+    const bool sm = (size_t)n_det * 8 <= (size_t)kDetSmemBytes;
+    tape_det_forward<<<1, kBlock, sm ? (size_t)n_det * 8 : 0, st>>>(nd, n, theta, det, n_det, sm ? 1 : 0);
+}
+void launch_det_backward(const DevNode *nd, int n, const double *det, double *ddet, double *grad, int n_det,
+                         cudaStream_t st) {
+    const bool sm = (size_t)n_det * 16 <= (size_t)kDetSmemBytes;
+    tape_det_backward<<<1, kBlock, sm ? (size_t)n_det * 16 : 0, st>>>(nd, n, det, ddet, grad, n_det, sm ? 1 : 0);
+}
+void launch_expect_finalize(const double *part, int nb, const DevNode *ex, int n_exp, double inv_n, double *det,
+                            cudaStream_t st) {
+    tape_expect_finalize<<<(n_exp * kWarp + kBlock - 1) / kBlock, kBlock, 0, st>>>(part, nb, ex, n_exp, inv_n, det);
+}
+void launch_darg_finalize(const double *part, int nb, const int *slot, int n_darg, double inv_n, double *ddet,
+                          cudaStream_t st) {
+    tape_darg_finalize<<<(n_darg * kWarp + kBlock - 1) / kBlock, kBlock, 0, st>>>(part, nb, slot, n_darg, inv_n, ddet);
 }
 
 __global__ void tape_begin_backward(double *__restrict__ ddet, int n_det, int obj_slot, double *__restrict__ grad,
@@ -780,14 +838,13 @@ mc_status run_tape(mc_tape *t, const double *theta, uint64_t seed, uint64_t path
     for (int s = 0; s < p.n_stages; ++s) {
         const int nd = L.path_off[s] - L.det_off[s], np = L.exp_off[s] - L.path_off[s];
         const int ne = L.det_off[s + 1] - L.exp_off[s];
-        if (nd > 0) tape_det_forward<<<1, 1, 0, st>>>(t->nodes + L.det_off[s], nd, theta, t->det);
+        if (nd > 0) launch_det_forward(t->nodes + L.det_off[s], nd, theta, t->det, p.n_det, st);
         if (np > 0 || ne > 0)
             tape_path_forward<Real><<<grid_f, kBlock, ring + (size_t)kWarpsPerBlock * ne * 8, st>>>(
                 t->nodes + L.path_off[s], np, t->nodes + L.exp_off[s], ne, t->det, tape, t->stride, rk, path0,
                 n_paths, t->part);
         if (ne > 0)
-            tape_expect_finalize<<<(ne + 127) / 128, 128, 0, st>>>(t->part, grid_f, t->nodes + L.exp_off[s], ne, inv_n,
-                                                                  t->det);
+            launch_expect_finalize(t->part, grid_f, t->nodes + L.exp_off[s], ne, inv_n, t->det, st);
         mc_status r = ck("forward sweep");
         if (r != MC_OK) return r;
     }
@@ -808,9 +865,8 @@ mc_status run_tape(mc_tape *t, const double *theta, uint64_t seed, uint64_t path
                 t->nodes + L.path_off[s], np, t->nodes + L.exp_off[s], ne, na, t->det, t->ddet, tape, adj, t->stride,
                 n_paths, t->part);
         if (na > 0)
-            tape_darg_finalize<<<(na + 127) / 128, 128, 0, st>>>(t->part, grid_b, t->dslot + L.darg_off[s], na, inv_n,
-                                                                t->ddet);
-        if (nd > 0) tape_det_backward<<<1, 1, 0, st>>>(t->nodes + L.det_off[s], nd, t->det, t->ddet, grad_out);
+            launch_darg_finalize(t->part, grid_b, t->dslot + L.darg_off[s], na, inv_n, t->ddet, st);
+        if (nd > 0) launch_det_backward(t->nodes + L.det_off[s], nd, t->det, t->ddet, grad_out, p.n_det, st);
         mc_status r = ck("backward sweep");
         if (r != MC_OK) return r;
     }
@@ -970,7 +1026,8 @@ std::string gen_segment(const std::vector<mc_tape_node> &nodes, const TapePlan &
     o << " }\n}\n";
 
     // backward: adjoints of the segment's nodes in registers; values its partials need loaded
-    // from the tape; contributions to nodes outside summed per row and added once
+    // from the tape; contributions to nodes outside summed per row and added once; those to
+    // deterministic arguments summed per thread, warp-summed once per chunk
     std::vector<int> far_rows;
     for (int i : sg.nodes) {
         const int args[2] = {nodes[i].a, nodes[i].b};
@@ -996,6 +1053,7 @@ std::string gen_segment(const std::vector<mc_tape_node> &nodes, const TapePlan &
          "  R *ta = adj + p;\n";
     for (size_t q = 0; q < sg.nodes.size(); ++q) o << "  R a" << q << " = R(0);\n";
     for (int a : far_rows) o << "  R f" << p.ref[a] << " = R(0);\n";
+    for (size_t l = 0; l < sg.dargs.size(); ++l) o << "  R g" << l << " = R(0);\n";
     {
         std::vector<char> vloaded(p.n_nodes, 0);
         auto value = [&](int a) -> std::string {
@@ -1008,7 +1066,7 @@ std::string gen_segment(const std::vector<mc_tape_node> &nodes, const TapePlan &
         };
         auto contrib = [&](int a, const std::string &g) {
             if (p.cls[a] == 0)
-                o << "  { const R s = mcaad::warp_sum(" << g << "); if (lane == 0) wrow[" << dl[a] << "] += (double)s; }\n";
+                o << "  g" << dl[a] << " += " << g << ";\n";
             else if (local[a] >= 0)
                 o << "  a" << local[a] << " += " << g << ";\n";
             else
@@ -1063,6 +1121,8 @@ std::string gen_segment(const std::vector<mc_tape_node> &nodes, const TapePlan &
         }
     }
     for (int a : far_rows) o << "  if (active) ta[(u64)" << p.ref[a] << " * stride] += f" << p.ref[a] << ";\n";
+    for (size_t l = 0; l < sg.dargs.size(); ++l)
+        o << "  { const R s = mcaad::warp_sum(g" << l << "); if (lane == 0) wrow[" << l << "] += (double)s; }\n";
     o << " }\n"
          " __syncthreads();\n"
          " for (int k = threadIdx.x; k < n_darg; k += blockDim.x) {\n"
@@ -1131,7 +1191,7 @@ mc_status run_tape_jit(mc_tape *t, const double *theta, uint64_t seed, uint64_t 
     for (int s = 0; s < p.n_stages; ++s) {
         const int nd = L.path_off[s] - L.det_off[s];
         const int ne = L.det_off[s + 1] - L.exp_off[s];
-        if (nd > 0) tape_det_forward<<<1, 1, 0, st>>>(t->nodes + L.det_off[s], nd, theta, t->det);
+        if (nd > 0) launch_det_forward(t->nodes + L.det_off[s], nd, theta, t->det, p.n_det, st);
         for (int k = J.seg_begin[s]; k < J.seg_begin[s + 1]; ++k) {
             const JitSeg &sg = J.segs[k];
             const double *det = t->det;
@@ -1144,8 +1204,7 @@ mc_status run_tape_jit(mc_tape *t, const double *theta, uint64_t seed, uint64_t 
             tape_path_forward<Real><<<grid_f, kBlock, ring + (size_t)kWarpsPerBlock * ne * 8, st>>>(
                 t->nodes + L.path_off[s], 0, t->nodes + L.exp_off[s], ne, t->det, tape, stride, rk, path0, n_paths,
                 t->part);
-            tape_expect_finalize<<<(ne + 127) / 128, 128, 0, st>>>(t->part, grid_f, t->nodes + L.exp_off[s], ne, inv_n,
-                                                                  t->det);
+            launch_expect_finalize(t->part, grid_f, t->nodes + L.exp_off[s], ne, inv_n, t->det, st);
         }
         mc_status r = ck("forward sweep");
         if (r != MC_OK) return r;
@@ -1175,10 +1234,9 @@ mc_status run_tape_jit(mc_tape *t, const double *theta, uint64_t seed, uint64_t 
             const cudaError_t e = cudaLaunchKernel((const void *)sg.bwd, dim3(g), dim3(kBlock), args, sg.smem_b, st);
             if (e != cudaSuccess) return tfail(t, MC_ERR_CUDA, "compiled backward: %s", cudaGetErrorString(e));
             if (na > 0)
-                tape_darg_finalize<<<(na + 127) / 128, 128, 0, st>>>(t->part, g, J.dslot_dev + sg.darg_off, na, inv_n,
-                                                                    t->ddet);
+                launch_darg_finalize(t->part, g, J.dslot_dev + sg.darg_off, na, inv_n, t->ddet, st);
         }
-        if (nd > 0) tape_det_backward<<<1, 1, 0, st>>>(t->nodes + L.det_off[s], nd, t->det, t->ddet, grad_out);
+        if (nd > 0) launch_det_backward(t->nodes + L.det_off[s], nd, t->det, t->ddet, grad_out, p.n_det, st);
         mc_status r = ck("backward sweep");
         if (r != MC_OK) return r;
     }
