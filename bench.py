@@ -484,7 +484,12 @@ def run_reference(args):
         return
     from paper_1901_04200_gb300 import inputs
     w = inputs.heston_config()
-    n = args.ref_paths
+    # size the per-step sample from a short probe of the host's rate, so the whole run
+    # (warm-ups at an eighth of the sample) takes about --ref-seconds
+    rate = cpu_baseline(w, 2048)["value"]
+    budget_steps = args.steps + args.warmup / 8.0
+    n = int(rate * args.ref_seconds / max(budget_steps, 1.0) / w.problem.last_step) // 1024 * 1024
+    n = max(1024, min(n, args.ref_paths))
     for _ in range(args.warmup):
         cpu_baseline(w, max(n // 8, 256))
     vals = [cpu_baseline(w, n) for _ in range(args.steps)]
@@ -508,7 +513,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--paths", type=int, default=1 << 20)
     ap.add_argument("--cpu-paths", type=int, default=1 << 16)
-    ap.add_argument("--ref-paths", type=int, default=1 << 15)
+    ap.add_argument("--ref-paths", type=int, default=1 << 15, help="--impl reference: largest sample per step")
+    ap.add_argument("--ref-seconds", type=float, default=90.0,
+                    help="--impl reference: host time the whole run is sized for")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ppt", type=int, default=0, help="paths per GPU thread (0 = library default)")
     ap.add_argument("--tape-paths", type=int, default=1 << 18, help="paths of the --workload tape run")
