@@ -227,18 +227,29 @@ class ClockSampler:
         return out
 
 
-def cpu_baseline(workload, n_paths, threads=None):
-    """The FP64 oracle's value_and_grad on a bounded sample of the same workload."""
+def cpu_baseline(workload, n_paths, threads=None, keep=None):
+    """The FP64 oracle's value_and_grad on a bounded sample of the same workload (paths
+    [0, n_paths)); its (E y, G, grad G) go to keep[0] when a list is given."""
     import oracle
     oracle.build()
     threads = threads or os.cpu_count() or 1
     pb = workload.problem
     t0 = time.perf_counter()
-    oracle.value_and_grad(pb, workload.theta, workload.C, n_paths, n_threads=threads)
+    res = oracle.value_and_grad(pb, workload.theta, workload.C, n_paths, n_threads=threads)
     dt = time.perf_counter() - t0
+    if keep is not None:
+        keep.append(res)
     steps = pb.last_step
     return {"value": n_paths * steps / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": "%d of the workload's paths x %d steps, FP64, value+grad, %.1f s wall" % (n_paths, steps, dt)}
+
+
+def oracle_single_path_cost(workload, n_paths=512):
+    """Cost(F) of the paper's table: seconds of the oracle's forward sweep per path on one core."""
+    import oracle
+    t0 = time.perf_counter()
+    oracle.forward(workload.problem, workload.theta, n_paths, n_threads=1)
+    return (time.perf_counter() - t0) / n_paths
 
 
 def cpu_baseline_tape(pb, theta, C, n_paths):
@@ -701,7 +712,23 @@ def main():
             line.update(arms)
     if rank == 0:
         if not args.no_cpu_baseline and world == 1:
-            line["cpu_baseline"] = cpu_baseline(w, args.cpu_paths if model == "heston" else args.cpu_paths // 4)
+            n_cpu = args.cpu_paths if model == "heston" else args.cpu_paths // 4
+            keep = []
+            line["cpu_baseline"] = cpu_baseline(w, n_cpu, keep=keep)
+            # the FP32 path's error against the FP64 oracle, per result, on the same paths
+            Ey_o, G_o, g_o = keep[0]
+            Gs, gs, Eys = (x.cpu().numpy() for x in ctx.value_and_grad(theta, C, seed, n_cpu))
+            line["precision"] = {
+                "sample": "paths [0, %d) of the workload: GPU FP32 paths and FP64 sums vs the FP64 oracle" % n_cpu,
+                "Ey_max_rel": float(np.max(np.abs(Eys - Ey_o)) / np.max(np.abs(Ey_o))),
+                "G_rel": float(abs(Gs[0] - G_o) / abs(G_o)),
+                "grad_normwise_rel": float(np.max(np.abs(gs - g_o)) / np.max(np.abs(g_o)))}
+            # the GPU analogues of the paper's cost table (eq. 1311A with c = one GPU)
+            cost_f = oracle_single_path_cost(w)
+            kf, kr = roofline["kernels"]["forward_sweep"]["ms"] * 1e-3, roofline["kernels"]["reverse_sweep"]["ms"] * 1e-3
+            line["paper_table"] = {"cost_F_one_core_s": cost_f, "K_F_over_c": kf / (P * cost_f),
+                                   "K_R_over_c": kr / (P * cost_f), "cost_G_over_P_cost_F": ms_step * 1e-3 / (P * cost_f),
+                                   "note": "Cost(F): the oracle's FP64 forward sweep of one path on one host core"}
         if not args.no_calibration and world == 1 and model == "heston":
             line["calibration"] = calibration_experiment(args.calib_cases)
         print(json.dumps(line))

@@ -83,9 +83,9 @@ __device__ __forceinline__ float sqrt_approx(float x) {
 __device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, float &za, float &zb) {
     const float ua = uniform_f32(a);
     const float ub = uniform_f32(b);
-    const float rad = sqrt_approx(fmaxf(-2.0f * __logf(ua), 0.0f));
+    const float rad = sqrt_approx(fmaxf(-1.38629436111989061f * __log2f(ua), 0.0f));  // -2 ln u = (-2 ln 2) log2 u
     float s, c;
-    __sincosf(6.28318530717958648f * (ub - 0.5f), &s, &c);
+    __sincosf(fmaf(6.28318530717958648f, ub, -3.14159265358979324f), &s, &c);  // 2 pi u_b - pi, one rounding
     za = -rad * c;
     zb = -rad * s;
 }

@@ -311,9 +311,10 @@ struct LvModel {
 
     // Cell c = clamp(floor(u), 0, nx-2) and weight b = clamp(u - c, 0, 1).
     __device__ __forceinline__ static void cell(Real u, const Par &p, int &c, Real &b, bool &inside) {
-        const Real f = floor(u);
-        c = (int)fmin(fmax(f, Real(0)), (Real)p.nxm2);
-        const Real bb = u - (Real)c;
+        // the clamped floor stays a float: u - f needs no int-to-float conversion
+        const Real f = fmin(fmax(floor(u), Real(0)), (Real)p.nxm2);
+        c = (int)f;
+        const Real bb = u - f;
         inside = (bb >= Real(0)) && (bb <= Real(1));
         b = fmin(fmax(bb, Real(0)), Real(1));
     }
