@@ -10,8 +10,10 @@
 // sweep's tape lives in registers).  Every maturity lies on a segment end.
 //
 // Forward kernel (step 1, eq. 1211A): per segment, optionally store the state
-// (checkpoint, SoA [seg][state][path], coalesced), run K Euler steps with
-// Philox normals, and at a maturity sum the undiscounted call payoffs of the
+// (checkpoint) and, in the stored-normals variant, the segment's normals into
+// the warp chunk's tile (SegTile below: rows of 32 consecutive paths), run K
+// Euler steps with Philox normals, and at a maturity sum the undiscounted call
+// payoffs of the
 // warp's 32 paths (FP32 warp sum) into per-warp FP64 accumulators.  Block
 // end: the warps' sums in warp order -> part_y[block][i].
 //
