@@ -278,11 +278,15 @@ struct WsLayout {
         part_y = take((size_t)grid_max * p.m * 8);
         part_g = take((size_t)grid_max * p.M * 8);
         const size_t real = p.precision == MC_FP64 ? 8 : 4;
-        // checkpoint tiles (SegTile): per path and segment, the state words and, with
-        // stored normals, the segment's K * dz normals; ckpt_stride covers whole chunks
+        // checkpoint tiles (SegTile): per warp chunk of 32*ppt paths and segment, the state
+        // words and, with stored normals, the segment's K * dz normals of each path, in rows of
+        // 32 paths padded to whole 16-byte groups; ckpt_stride covers whole chunks
         const bool full = p.storage == MC_STORAGE_FULL;
-        const size_t per_seg = p.state_dim + (p.storage == MC_STORAGE_NORMALS ? (size_t)p.K * p.dz : 0);
-        ckpt = take(full ? 0 : (size_t)p.n_seg * per_seg * ckpt_stride * real);
+        const size_t rows = (size_t)p.ppt * (p.state_dim + (p.storage == MC_STORAGE_NORMALS ? (size_t)p.K * p.dz : 0));
+        const size_t group = 16 / real;
+        const size_t rows_padded = (rows + group - 1) / group * group;
+        const size_t chunks = ckpt_stride / (32 * (size_t)p.ppt);
+        ckpt = take(full ? 0 : (size_t)p.n_seg * chunks * rows_padded * 32 * real);
         tape = take(full ? (size_t)p.n_last * p.tape_fields * ckpt_stride * real : 0);
         xmat = take(full ? (size_t)p.n_groups * ckpt_stride * real : 0);
         total = o;

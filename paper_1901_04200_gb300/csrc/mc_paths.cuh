@@ -510,30 +510,63 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
+// 16-byte vectors of the path precision (4 floats or 2 doubles).
+template <typename Real>
+struct Vec16;
+template <>
+struct Vec16<float> {
+    using T = float4;
+    __device__ static T make(const float *v) { return make_float4(v[0], v[1], v[2], v[3]); }
+    __device__ static float get(const T &x, int k) { return k == 0 ? x.x : k == 1 ? x.y : k == 2 ? x.z : x.w; }
+};
+template <>
+struct Vec16<double> {
+    using T = double2;
+    __device__ static T make(const double *v) { return make_double2(v[0], v[1]); }
+    __device__ static double get(const T &x, int k) { return k == 0 ? x.x : x.y; }
+};
+
 // What the forward sweep leaves for the reverse sweep, in tiles of one warp
-// chunk (32*PPT consecutive paths) and one segment: rows of 32 consecutive
-// paths (one 128-byte line in FP32), first -- in the stored-normals variant --
-// the segment's normals, row (i*DZ + c)*PPT + q for step i, component c,
-// path slot q, then the checkpoint (the state at the segment's start), row
-// RZ + w*PPT + q for state word w.  Tile (chunk, s) starts at
-// (s * n_chunks + chunk) * R * 32 elements (n_chunks: the chunks the
-// workspace holds; the warps of a sweep work on nearby segments, so their
-// tiles are close together), and every store and load of the tile is a
-// compile-time offset from one base.  The reverse sweep copies a
+// chunk (32*PPT consecutive paths) and one segment.  Rows: first -- in the
+// stored-normals variant -- the segment's normals, row (i*DZ + c)*PPT + q for
+// step i, component c, path slot q, then the checkpoint (the state at the
+// segment's start), row RZ + w*PPT + q for state word w, padded to whole
+// groups of G = 16 / sizeof(Real) rows.  Within a tile, lane l's G rows of
+// group g are one 16-byte vector at ((g * 32) + l) * G: the forward sweep
+// writes a group with one vector store per lane (a warp writes 512
+// contiguous bytes) and the reverse sweep reads it with one vector load.
+// Tile (chunk, s) starts at (s * n_chunks + chunk) * Rp * 32 elements
+// (n_chunks: the chunks the workspace holds; the warps of a sweep work on
+// nearby segments, so their tiles are close together), and every store and
+// load of the tile is a compile-time offset from one base.  The reverse sweep copies a
 // warp's tile of segment s-1 into its half of a two-buffer shared staging
 // area (same layout) while it works on segment s, so HBM latency is paid
 // once per chunk instead of once per segment.
 template <class Md, int K, int PPT, bool kZ>
 struct SegTile {
     using Real = typename Md::Real;
+    using V = Vec16<Real>;
     static constexpr int RZ = kZ ? K * Md::DZ * PPT : 0;           // normals rows
     static constexpr int R = RZ + Md::SD * PPT;                     // + checkpoint rows
-    static constexpr int kElems = R * kWarp;                        // elements per tile
+    static constexpr int kG = 16 / (int)sizeof(Real);               // rows per vector group
+    static constexpr int Rp = (R + kG - 1) / kG * kG;               // rows padded to whole groups
+    static constexpr int kElems = Rp * kWarp;                       // elements per tile
     static constexpr int kPieces = kElems * (int)sizeof(Real) / 16; // 16-byte pieces per tile
     static constexpr size_t kWarpBytes = 2 * (size_t)kElems * sizeof(Real);
     static constexpr size_t kBlockBytes = kWarpBytes * kWarpsPerBlock;
     __device__ static constexpr int zrow(int i, int c, int q) { return (i * Md::DZ + c) * PPT + q; }
     __device__ static constexpr int crow(int w, int q) { return RZ + w * PPT + q; }
+    // group g of this lane (tile or staging buffer base, lane)
+    __device__ __forceinline__ static typename V::T *group(Real *t, int g, int lane) {
+        return (typename V::T *)(t + ((size_t)g * kWarp + lane) * kG);
+    }
+    __device__ __forceinline__ static const typename V::T *group(const Real *t, int g, int lane) {
+        return (const typename V::T *)(t + ((size_t)g * kWarp + lane) * kG);
+    }
+    // row r of this lane from a tile or staging buffer (the group is one vector load)
+    __device__ __forceinline__ static Real row(const Real *t, int r, int lane) {
+        return V::get(*group(t, r / kG, lane), r % kG);
+    }
     __device__ __forceinline__ static Real *tile(void *base, uint64_t chunk, uint64_t n_chunks, int s) {
         return (Real *)base + ((size_t)s * n_chunks + chunk) * kElems;
     }
@@ -641,27 +674,42 @@ __global__ void __launch_bounds__(kBlock) path_forward_kernel(const DevProblem p
         }
         int g = 0;
         for (int s = 0; s < pb.n_seg; ++s) {
-            Real *tl = TL::tile(cl.ckpt, ch, cl.ckpt_stride / kChunk, s) + lane;
+            // the segment's normals first: its Philox blocks are independent of the state, so
+            // the scheduler can overlap them; then the K dependent Euler steps.  The tile's
+            // groups (normals when kept, checkpoint) go out as soon as all their rows exist.
+            Real zs[K][PPT][Md::DZ];
+            Real *tl = TL::tile(cl.ckpt, ch, cl.ckpt_stride / kChunk, s);
+            auto store_group = [&](int g0) {
+                Real v[TL::kG];
+#pragma unroll
+                for (int k = 0; k < TL::kG; ++k) {
+                    const int r = g0 + k;
+                    if (r < TL::RZ) {
+                        v[k] = zs[r / (Md::DZ * PPT)][r % PPT][(r / PPT) % Md::DZ];
+                    } else if (r < TL::R) {
+                        const int w = (r - TL::RZ) / PPT, q = (r - TL::RZ) % PPT;
+                        if constexpr (Md::SD == 2) v[k] = w == 0 ? st[q].x : st[q].v;
+                        else v[k] = st[q].x;
+                    } else {
+                        v[k] = Real(0);
+                    }
+                }
+                *TL::group(tl, g0 / TL::kG, lane) = TL::V::make(v);
+            };
             if (cl.keep_ckpt) {
 #pragma unroll
-                for (int q = 0; q < PPT; ++q) {
-                    tl[TL::crow(0, q) * kWarp] = st[q].x;
-                    if constexpr (Md::SD == 2) tl[TL::crow(1, q) * kWarp] = st[q].v;
-                }
+                for (int g0 = 0; g0 < TL::Rp; g0 += TL::kG)
+                    if (g0 >= TL::RZ) store_group(g0);  // checkpoint (and padding) only
             }
-            // the segment's normals first: its Philox blocks are independent of the state, so
-            // the scheduler can overlap them; then the K dependent Euler steps
-            Real zs[K][PPT][Md::DZ];
 #pragma unroll
             for (int i = 0; i < K; ++i) {
                 const int n = s * K + i;
 #pragma unroll
-                for (int q = 0; q < PPT; ++q) {
-                    rng[q].get(n, i == 0, zs[i][q], rk);
-                    if constexpr (kStoreZ) {
+                for (int q = 0; q < PPT; ++q) rng[q].get(n, i == 0, zs[i][q], rk);
+                if (cl.keep_ckpt) {
 #pragma unroll
-                        for (int c = 0; c < Md::DZ; ++c) tl[TL::zrow(i, c, q) * kWarp] = zs[i][q][c];
-                    }
+                    for (int g0 = 0; g0 < TL::RZ; g0 += TL::kG)  // groups whose last normals row is step i's
+                        if ((min(g0 + TL::kG, TL::RZ) - 1) / (Md::DZ * PPT) == i) store_group(g0);
                 }
             }
 #pragma unroll
@@ -751,13 +799,13 @@ __global__ void __launch_bounds__(kBlock) path_reverse_kernel(const DevProblem p
                 cp_async_wait<0>();
             }
             __syncwarp();  // the other lanes' copies of segment s are visible
-            const Real *sbuf = zstage + (size_t)(s & 1) * ZS::kElems + lane;
+            const Real *sbuf = zstage + (size_t)(s & 1) * ZS::kElems;
             typename Md::State st[PPT];
             typename Md::Tape tape[PPT][K];
 #pragma unroll
             for (int q = 0; q < PPT; ++q) {
-                st[q].x = sbuf[ZS::crow(0, q) * kWarp];
-                if constexpr (Md::SD == 2) st[q].v = sbuf[ZS::crow(1, q) * kWarp];
+                st[q].x = ZS::row(sbuf, ZS::crow(0, q), lane);
+                if constexpr (Md::SD == 2) st[q].v = ZS::row(sbuf, ZS::crow(1, q), lane);
             }
 #pragma unroll
             for (int i = 0; i < K; ++i) {
@@ -767,7 +815,7 @@ __global__ void __launch_bounds__(kBlock) path_reverse_kernel(const DevProblem p
                     Real z[Md::DZ];
                     if constexpr (kLoadZ) {
 #pragma unroll
-                        for (int c = 0; c < Md::DZ; ++c) z[c] = sbuf[ZS::zrow(i, c, q) * kWarp];
+                        for (int c = 0; c < Md::DZ; ++c) z[c] = ZS::row(sbuf, ZS::zrow(i, c, q), lane);
                     } else {
                         rng[q].get(n, i == 0, z, rk);
                     }
