@@ -111,8 +111,10 @@ typedef enum {
  *                x += (r - L^2 v+/2) dt + L sqrt(v+ dt) z1.         M = 5 + nt*nx
  * ckpt_every: checkpoint interval k of the reverse sweep (0 = library
  * default); it must divide every maturity step.
- * paths_per_thread: 1 or 2 independent paths per GPU thread (0 = library
- * default); results agree to rounding of the FP32 warp sums.
+ * paths_per_thread: independent paths per GPU thread, 1 to 4 where that
+ * (model, precision, ckpt_every) combination is built (MC_ERR_UNSUPPORTED
+ * otherwise; 0 = library default); results agree to rounding of the FP32
+ * warp sums.
  * normals: optional device FP64 table [rows][n_steps * normals_per_step]
  * (row = global path - normals_path0) used instead of Philox; GBM only.
  */

@@ -112,6 +112,13 @@ bool kernels_raw(int kind, int precision, int K, int ppt, KernelPair *kp) {
 // 2.93 ms per value-and-gradient on 2^20 x 512 paths).
 int default_ppt(int kind, int precision) { return (kind == kHeston && precision == MC_FP32) ? 2 : 1; }
 
+// Path stride of the workspace arrays: whole pairs of warp chunks (64 * ppt paths), so the
+// segment tiles of every chunk of a call fit.
+uint64_t path_stride(uint64_t max_paths, int ppt) {
+    const uint64_t q = 2 * (uint64_t)kWarp * (uint64_t)ppt;
+    return (max_paths + q - 1) / q * q;
+}
+
 // Everything a context derives from (model, instruments), computed on the host.
 struct Plan {
     int kind, precision, K, ppt, n_last, n_seg, m, M, n_groups, state_dim, storage, tape_fields, dz;
@@ -166,7 +173,7 @@ mc_status make_plan(const mc_model *md, const mc_instruments *in, Plan &p, std::
             return bad("LV needs nt, nx >= 2, t_max > 0, x_hi > x_lo");
         if (md->nx > 32) return bad("LV needs nx <= 32");
     }
-    if (md->paths_per_thread < 0 || md->paths_per_thread > 2) return bad("paths_per_thread must be 0, 1 or 2");
+    if (md->paths_per_thread < 0 || md->paths_per_thread > 4) return bad("paths_per_thread must be in [0, 4]");
     if (md->storage < MC_STORAGE_CHECKPOINT || md->storage > MC_STORAGE_AUTO) return bad("unknown storage mode");
     p.storage = md->storage;
     p.dz = p.state_dim;  // normals per step: 1 (GBM, LV) or 2 (Heston, SLV)
@@ -308,7 +315,7 @@ mc_status resolve_storage(Plan &p, uint64_t max_paths, int device, std::string &
         why = cudaGetErrorString(e);
         return MC_ERR_CUDA;
     }
-    const uint64_t stride = (max_paths + 2 * kWarp - 1) / (2 * kWarp) * (2 * kWarp);
+    const uint64_t stride = path_stride(max_paths, p.ppt);
     const double normals_bytes = (double)p.n_last * p.dz * (double)stride * (p.precision == MC_FP64 ? 8 : 4);
     p.storage = normals_bytes <= 0.25 * (double)total_b ? MC_STORAGE_NORMALS : MC_STORAGE_CHECKPOINT;
     return MC_OK;
@@ -471,7 +478,7 @@ mc_status mc_workspace_size(const mc_model *model, const mc_instruments *inst, u
     Launch ln;
     st = launch_shape(p, device, kp, model->nx, &n_sm, ln, why);
     if (st != MC_OK) return st;
-    const uint64_t stride = (max_paths + 2 * kWarp - 1) / (2 * kWarp) * (2 * kWarp);
+    const uint64_t stride = path_stride(max_paths, p.ppt);
     *bytes_out = WsLayout(p, ln.grid_max(), stride).total;
     return MC_OK;
 }
@@ -519,7 +526,7 @@ mc_status mc_context_create(int device, const mc_model *model, const mc_instrume
     }
     ctx->grid_max = ctx->ln.grid_max();
     ctx->max_paths = max_paths;
-    ctx->ckpt_stride = (max_paths + 2 * kWarp - 1) / (2 * kWarp) * (2 * kWarp);  // whole 64-path chunks
+    ctx->ckpt_stride = path_stride(max_paths, p.ppt);
     WsLayout L(p, ctx->grid_max, ctx->ckpt_stride);
     if (workspace) {
         if (workspace_bytes < L.total || ((uintptr_t)workspace & 255u)) {

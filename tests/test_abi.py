@@ -85,3 +85,11 @@ def test_fill_hooks_reject_bad_arguments(lib):
     from paper_1901_04200_gb300 import _lib
     assert lib.mc_philox_fill(1, 0, 0, 4, None, None) == _lib.MC_ERR_INVALID_ARG
     assert lib.mc_normals_fill(1, 0, 4, 4, 7, ctypes.c_void_p(256), None) == _lib.MC_ERR_INVALID_ARG
+
+
+def test_unbuilt_paths_per_thread_is_unsupported(lib):
+    """paths_per_thread up to 4 is accepted by the ABI; a combination without kernels is refused."""
+    from paper_1901_04200_gb300 import _lib
+    pb = inputs.heston_config(n_paths=64, steps_per_year=16, T=1.0, n_mat=2, n_strike=2).problem
+    assert _ws(lib, replace(pb, paths_per_thread=4, ckpt_every=4)) == _lib.MC_ERR_UNSUPPORTED
+    assert _ws(lib, replace(pb, paths_per_thread=5)) == _lib.MC_ERR_INVALID_ARG
