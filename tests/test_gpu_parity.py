@@ -401,3 +401,32 @@ def test_slv_full_size_sampled(L, orc):
     ctx.forward(w.theta, w.problem.seed, n - h, path0=h, keep=True)
     vb = ctx.vjp(lam).cpu().numpy()
     assert rel((va + vb) / 2, g) <= 1e-5
+
+
+# ------------------------------------------------------------- size limits
+
+@pytest.mark.parametrize("storage", ["checkpoint", "normals"])
+def test_heston_1024_instruments_fp64(L, orc, storage):
+    """The instrument limit (m = 1024: 8 maturities x 128 strikes) against the oracle."""
+    w = inputs.heston_config(n_paths=700, steps_per_year=16, T=1.0, n_mat=8, n_strike=128)
+    assert w.problem.m == 1024
+    check(L, orc, replace(w, problem=replace(w.problem, precision="fp64", ckpt_every=2, storage=storage)),
+          1e-10, 1e-12)
+
+
+@pytest.mark.parametrize("storage", ["checkpoint", "normals"])
+def test_lv_256_parameters_fp64(L, orc, storage):
+    """The parameter limit (M = 256: an 8 x 32 node surface, the 32-node axis limit) against the oracle."""
+    w = inputs.lv_config(n_paths=900, n_steps=100, T=2.0, nt=8, nx=32, n_mat=4, n_strike=5)
+    assert w.problem.n_params == 256
+    check(L, orc, replace(w, problem=replace(w.problem, precision="fp64", storage=storage)), 1e-10, 1e-12)
+
+
+def test_beyond_limits_rejected(L):
+    w = inputs.heston_config(n_paths=64, steps_per_year=16, T=1.0, n_mat=8, n_strike=129)
+    with pytest.raises(L.McError) as e:
+        L.Context(w.problem, max_paths=64)
+    assert e.value.status == L.MC_ERR_INVALID_ARG
+    w = inputs.lv_config(n_paths=64, n_steps=100, T=2.0, nt=9, nx=32, n_mat=4, n_strike=5)
+    with pytest.raises(L.McError):
+        L.Context(w.problem, max_paths=64)

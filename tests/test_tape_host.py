@@ -95,3 +95,15 @@ def test_oracle_tape_log_by_finite_differences():
     fd = (value(0.8 + h)[0].v[0] - value(0.8 - h)[0].v[0]) / (2 * h)
     assert math.isclose(g, fd, rel_tol=1e-8)
     assert math.isclose(g, np.mean(1.0 / (0.8 + z * z)), rel_tol=1e-14)
+
+
+def test_stage_limits():
+    """More than 2048 expectations in one stage is refused as unsupported, 2048 is accepted."""
+    for n, want in [(2048, _lib.MC_OK), (2049, _lib.MC_ERR_UNSUPPORTED)]:
+        p = tape.Program()
+        z = p.normal(0)
+        G = None
+        for k in range(n):
+            e = tape.expect(z * float(k + 1))
+            G = e if G is None else G + e
+        assert tape.plan(p, G, 0)[0] == want
