@@ -778,9 +778,10 @@ mc_status mc_profile_end(mc_ctx *ctx, double *ms_out, int32_t *launches_out) {
 // Blocks per parameter vector: one when there are enough vectors to fill the
 // GPU, otherwise enough to give it about four blocks per SM.
 // Blocks per parameter vector: enough for every SM to hold as many blocks as
-// fit (few vectors: one vector fills the GPU), at most one per 128 paths.
+// fit (few vectors: one vector fills the GPU), at most one per four warp chunks.
 static int jacobian_bpt(const mc_ctx *ctx, int n_theta, uint64_t n_paths) {
-    const uint64_t chunks = (n_paths + kWarp - 1) / kWarp;
+    const uint64_t chunk = (uint64_t)kWarp * jacobian_ppt(ctx->precision);
+    const uint64_t chunks = (n_paths + chunk - 1) / chunk;
     int occ = 0;
     const size_t smem = jacobian_smem_bytes(ctx->m, ctx->n_groups, ctx->precision);
     if (cudaFuncSetAttribute(jacobian_kernel(ctx->precision), cudaFuncAttributeMaxDynamicSharedMemorySize,

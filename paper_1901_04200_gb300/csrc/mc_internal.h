@@ -43,6 +43,7 @@ cudaError_t launch_normals_fill(uint64_t seed, uint64_t path0, uint32_t n_paths,
 // Forward-mode Jacobian (mc_jacobian.cu).
 size_t jacobian_smem_bytes(int m, int n_groups, int precision);
 const void *jacobian_kernel(int precision);
+int jacobian_ppt(int precision);  // paths per thread of jacobian_kernel
 cudaError_t launch_jacobian(const DevProblem &pb, int precision, const double *thetas, const double *strikes_t,
                             int n_theta, uint64_t seed, uint64_t path0, uint64_t n_paths, int bpt, size_t smem,
                             double *part, const double *disc, const int *perm, double *Ey_out,

@@ -13,9 +13,11 @@
 //
 // Paths of parameter vector t are the global paths path0 + [t P, (t+1) P)
 // with the call's seed, so different t draw independent normals.  Grid (bpt, n_theta):
-// block (b, t) walks warps over 32-path chunks of its slice of theta t's
-// paths and leaves FP64 sums of y_i and of dy_i/dtheta_j per block
-// (warp sums in the path precision, FP64 above the warp, no atomics).
+// block (b, t) walks warps over chunks of 32 * PPT paths of its slice of
+// theta t's paths (PPT independent recursions per thread: two in FP32, one in
+// FP64) and leaves FP64 sums of y_i and of dy_i/dtheta_j per block (per-thread
+// sums over its paths and warp sums in the path precision, FP64 above the
+// warp, no atomics).
 #include "mc_internal.h"
 #include "mc_paths.cuh"
 
@@ -23,7 +25,7 @@ namespace mcaad {
 
 constexpr int kJacM = 5;  // Heston parameters (kappa, theta_h, xi, rho, v0)
 
-template <typename Real>
+template <typename Real, int PPT>
 __global__ void __launch_bounds__(kBlock)
 heston_jacobian_kernel(const DevProblem pb, const double *__restrict__ thetas,
                        const double *__restrict__ strikes_t, const RoundKeys rk, uint64_t path0,
@@ -45,7 +47,7 @@ heston_jacobian_kernel(const DevProblem pb, const double *__restrict__ thetas,
     for (int q = threadIdx.x; q < kWarpsPerBlock * W; q += blockDim.x) wacc[q] = 0.0;
     const double *th = thetas + (size_t)t * kJacM;
     const double kappa_d = th[0], thh_d = th[1], xi_d = th[2], rho_d = th[3];
-    const Real kappa = (Real)kappa_d, thh = (Real)thh_d, xi = (Real)xi_d, rho = (Real)rho_d;
+    const Real kappa = (Real)kappa_d, xi = (Real)xi_d, rho = (Real)rho_d;
     const Real rhob = (Real)sqrt(1.0 - rho_d * rho_d);
     const Real rho_over_rhob = (Real)(rho_d / sqrt(1.0 - rho_d * rho_d));
     const Real v0 = (Real)th[4];
@@ -57,60 +59,76 @@ heston_jacobian_kernel(const DevProblem pb, const double *__restrict__ thetas,
     const int warp = threadIdx.x / kWarp, lane = threadIdx.x % kWarp;
     double *wrow = wacc + warp * W;
     const int K = pb.K;
-    const uint64_t chunks = (n_paths + kWarp - 1) / kWarp;
+    constexpr uint64_t kChunk = (uint64_t)kWarp * PPT;  // lane l carries paths chunk*kChunk + q*32 + l
+    const uint64_t chunks = (n_paths + kChunk - 1) / kChunk;
     for (uint64_t ch = (uint64_t)blockIdx.x * kWarpsPerBlock + warp; ch < chunks;
          ch += (uint64_t)bpt * kWarpsPerBlock) {
-        const uint64_t local = ch * kWarp + lane;
-        const bool active = local < n_paths;
-        PathNormals<Real> rng;
-        rng.init(path0 + (uint64_t)t * n_paths + (active ? local : 0));
-        Real x = Real(0), v = v0;
-        Real dx[kJacM], dv[kJacM];
+        bool active[PPT];
+        PathNormals<Real> rng[PPT];
+        Real x[PPT], v[PPT], dx[PPT][kJacM], dv[PPT][kJacM];
 #pragma unroll
-        for (int j = 0; j < kJacM; ++j) {
-            dx[j] = Real(0);
-            dv[j] = (j == 4) ? Real(1) : Real(0);
+        for (int q = 0; q < PPT; ++q) {
+            const uint64_t local = ch * kChunk + q * kWarp + lane;
+            active[q] = local < n_paths;
+            rng[q].init(path0 + (uint64_t)t * n_paths + (active[q] ? local : 0));
+            x[q] = Real(0);
+            v[q] = v0;
+#pragma unroll
+            for (int j = 0; j < kJacM; ++j) {
+                dx[q][j] = Real(0);
+                dv[q][j] = (j == 4) ? Real(1) : Real(0);
+            }
         }
         int g = 0;
         for (int s = 0; s < pb.n_seg; ++s) {
             for (int i = 0; i < K; ++i) {
                 const int n = s * K + i;
                 const uint32_t j0 = (uint32_t)(2 * n);
-                if ((j0 & 3u) == 0u) rng.fill(j0 >> 2, rk);
-                const Real z1 = rng.pick(j0 & 3u), z2 = rng.pick((j0 + 1) & 3u);
-                const bool pos = v > Real(0);
-                const Real vdt = fmax(v, Real(0)) * dt;
-                const Real rs = rsqrt_r<Real>(fmax(vdt, tiny_r<Real>()));
-                const Real sq = vdt * rs;
-                const Real w = fma(rho, z1, rhob * z2);
-                // tangents: d vdt = 1{v>0} dt dv; d sq = rs/2 d vdt
-                const Real dts = pos ? dt : Real(0);
-                const Real cx = Real(0.5) * fma(rs, z1, Real(-1));   // dx'/d vdt
-                const Real cv = fma(Real(0.5) * xi * rs, w, -kappa);  // dv'/d vdt
-                const Real e_kappa = thdt - vdt, e_th = kdt, e_xi = sq * w;
-                const Real e_rho = xi * sq * fma(-rho_over_rhob, z2, z1);
 #pragma unroll
-                for (int j = 0; j < kJacM; ++j) {
-                    const Real dvdt = dts * dv[j];
-                    dx[j] = fma(cx, dvdt, dx[j]);
-                    Real e = Real(0);
-                    if (j == 0) e = e_kappa;
-                    if (j == 1) e = e_th;
-                    if (j == 2) e = e_xi;
-                    if (j == 3) e = e_rho;
-                    dv[j] = fma(cv, dvdt, dv[j]) + e;
+                for (int q = 0; q < PPT; ++q) {
+                    if ((j0 & 3u) == 0u) rng[q].fill(j0 >> 2, rk);
+                    const Real z1 = rng[q].pick(j0 & 3u), z2 = rng[q].pick((j0 + 1) & 3u);
+                    const bool pos = v[q] > Real(0);
+                    const Real vdt = fmax(v[q], Real(0)) * dt;
+                    const Real rs = rsqrt_r<Real>(fmax(vdt, tiny_r<Real>()));
+                    const Real sq = vdt * rs;
+                    const Real w = fma(rho, z1, rhob * z2);
+                    // tangents: d vdt = 1{v>0} dt dv; d sq = rs/2 d vdt
+                    const Real dts = pos ? dt : Real(0);
+                    const Real cx = Real(0.5) * fma(rs, z1, Real(-1));   // dx'/d vdt
+                    const Real cv = fma(Real(0.5) * xi * rs, w, -kappa);  // dv'/d vdt
+                    const Real e_kappa = thdt - vdt, e_th = kdt, e_xi = sq * w;
+                    const Real e_rho = xi * sq * fma(-rho_over_rhob, z2, z1);
+#pragma unroll
+                    for (int j = 0; j < kJacM; ++j) {
+                        const Real dvdt = dts * dv[q][j];
+                        dx[q][j] = fma(cx, dvdt, dx[q][j]);
+                        Real e = Real(0);
+                        if (j == 0) e = e_kappa;
+                        if (j == 1) e = e_th;
+                        if (j == 2) e = e_xi;
+                        if (j == 3) e = e_rho;
+                        dv[q][j] = fma(cv, dvdt, dv[q][j]) + e;
+                    }
+                    x[q] = x[q] + fma(sq, z1, fma(Real(-0.5), vdt, rdt));
+                    v[q] = v[q] + fma(xi * sq, w, fma(-kappa, vdt, kthdt));
                 }
-                x = x + fma(sq, z1, fma(Real(-0.5), vdt, rdt));
-                v = v + fma(xi * sq, w, fma(-kappa, vdt, kthdt));
             }
             if (g < pb.n_groups && gseg[g] == s) {
-                const Real S = S0 * exp_r<Real>(x);
-                for (int i = gbeg[g]; i < gbeg[g + 1]; ++i) {
-                    const bool itm = active && S > strike[i];
-                    Real vals[1 + kJacM];
-                    vals[0] = itm ? S - strike[i] : Real(0);
+                Real S[PPT];
 #pragma unroll
-                    for (int j = 0; j < kJacM; ++j) vals[1 + j] = itm ? S * dx[j] : Real(0);
+                for (int q = 0; q < PPT; ++q) S[q] = S0 * exp_r<Real>(x[q]);
+                for (int i = gbeg[g]; i < gbeg[g + 1]; ++i) {
+                    Real vals[1 + kJacM];
+#pragma unroll
+                    for (int k = 0; k <= kJacM; ++k) vals[k] = Real(0);
+#pragma unroll
+                    for (int q = 0; q < PPT; ++q) {
+                        const bool itm = active[q] && S[q] > strike[i];
+                        vals[0] += itm ? S[q] - strike[i] : Real(0);
+#pragma unroll
+                        for (int j = 0; j < kJacM; ++j) vals[1 + j] += itm ? S[q] * dx[q][j] : Real(0);
+                    }
                     warp_flush_n(wrow, i * (1 + kJacM), vals, lane);
                 }
                 ++g;
@@ -156,9 +174,13 @@ size_t jacobian_smem_bytes(int m, int n_groups, int precision) {
     return o + (size_t)kWarpsPerBlock * (1 + kJacM) * m * 8;
 }
 
+// Paths per thread of the forward-mode kernel: two independent recursions in
+// FP32 (as the path sweeps), one in FP64.
+int jacobian_ppt(int precision) { return precision == 0 ? 1 : 2; }
+
 const void *jacobian_kernel(int precision) {
-    return precision == 0 ? (const void *)heston_jacobian_kernel<double>
-                          : (const void *)heston_jacobian_kernel<float>;
+    return precision == 0 ? (const void *)heston_jacobian_kernel<double, 1>
+                          : (const void *)heston_jacobian_kernel<float, 2>;
 }
 
 cudaError_t launch_jacobian(const DevProblem &pb, int precision, const double *thetas, const double *strikes_t,
