@@ -364,7 +364,7 @@ def tape_bench(args, rank, world):
     ctx = tape.TapeContext(prog, G, 5, max_paths=P, device=dev, precision=args.tape_precision)
     compile_s, per_path = None, tape.plan(prog, G, 5, P, args.tape_precision)[4]  # interpreter HBM bytes per path
     if not args.tape_interpret:
-        compile_s, per_path = ctx.compile(seg_nodes=args.tape_seg)  # outside the timed region
+        compile_s, per_path = ctx.compile(seg_nodes=args.tape_seg, recompute=args.tape_recompute)  # untimed
     theta = torch.tensor(w.theta, dtype=torch.float64, device=dev)
     out = (torch.empty(1, dtype=torch.float64, device=dev), torch.empty(5, dtype=torch.float64, device=dev))
     path0 = rank * P
@@ -404,8 +404,9 @@ def tape_bench(args, rank, world):
             "config": {"workload": "tape_" + w.name, "paths_per_gpu": P, "steps": S, "nodes": len(prog.nodes),
                        "precision": args.tape_precision + " per-path values and adjoints, fp64 sums",
                        "execution": "interpreter" if args.tape_interpret else
-                                    "compiled (segments of %s nodes, %.1f s run-time compilation)"
-                                    % (args.tape_seg or 384, compile_s),
+                                    "compiled (segments of %s nodes%s, %.1f s run-time compilation)"
+                                    % (args.tape_seg or 384, ", backward recomputes" if args.tape_recompute else "",
+                                       compile_s),
                        "l2": "inputs larger than L2: %.1f GB of tape and adjoints" % (byts / 1e9)},
             "roofline": {"bound": "hbm", "achieved": byts / (ms * 1e-3) / 1e9, "peak": hbm / 1e9, "unit": "GB/s",
                          "frac": byts / (ms * 1e-3) / hbm, "traffic": None,
@@ -544,6 +545,8 @@ def main():
     ap.add_argument("--tape-interpret", action="store_true",
                     help="--workload tape: run the interpreter instead of the compiled program")
     ap.add_argument("--tape-seg", type=int, default=0, help="--workload tape: nodes per compiled segment")
+    ap.add_argument("--tape-recompute", action="store_true",
+                    help="--workload tape: compiled backward kernels re-run their segment's forward")
     ap.add_argument("--workload", default="heston", choices=["heston", "lv", "slv", "surrogate", "tape"],
                     help="heston (the metric's workload), lv (2^22 x 500 local vol) or surrogate "
                          "(one differential-loss training step of the pricing network), for measurement")

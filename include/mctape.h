@@ -129,7 +129,10 @@ mc_status mc_tape_value_and_grad(mc_tape *t, const double *theta, uint64_t seed,
  * compiled at run time for sm_103a by NVRTC on `threads` host threads (0: all
  * cores), without FMA contraction, and loaded on the tape's device.  Values
  * cross a segment or stage boundary, and feed expectations and backward
- * partials, through the HBM tape; the rest of the evaluation (deterministic
+ * partials, through the HBM tape (with recompute != 0, the backward kernel
+ * first re-runs its segment's forward code, normals included, so only values
+ * crossing a segment or stage boundary or feeding an expectation use the
+ * tape); the rest of the evaluation (deterministic
  * nodes, expectations, fixed-order sums) is unchanged, so the results agree
  * with the interpreter's to the rounding of the reordered sums.  Later
  * mc_tape_value_and_grad calls run the compiled kernels.  Allocates a small
@@ -137,7 +140,8 @@ mc_status mc_tape_value_and_grad(mc_tape *t, const double *theta, uint64_t seed,
  * hbm_bytes_out: HBM bytes per path of one compiled value and gradient (or
  * NULL).  MC_ERR_UNSUPPORTED if the run-time compiler fails (mc_tape_last_error
  * has the start of its log; the tape keeps interpreting). */
-mc_status mc_tape_compile(mc_tape *t, int32_t seg_nodes, int32_t threads, double *seconds_out, size_t *hbm_bytes_out);
+mc_status mc_tape_compile(mc_tape *t, int32_t seg_nodes, int32_t recompute, int32_t threads, double *seconds_out,
+                          size_t *hbm_bytes_out);
 
 /* Per-path value of node `node` on the last evaluated paths (FP64 device
  * [n_paths]); MC_ERR_INVALID_ARG for a deterministic node,

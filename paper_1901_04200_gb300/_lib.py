@@ -85,7 +85,7 @@ SIGNATURES = [
     ("mc_tape_last_error", ctypes.c_char_p, [_V]),
     ("mc_tape_value_and_grad", ctypes.c_int, [_V, _V, _U64, _U64, _U64, _V, _V, _V]),
     ("mc_tape_path_values", ctypes.c_int, [_V, _I32, _V, _V]),
-    ("mc_tape_compile", ctypes.c_int, [_V, _I32, _I32, _P(ctypes.c_double), _P(_SZ)]),
+    ("mc_tape_compile", ctypes.c_int, [_V, _I32, _I32, _I32, _P(ctypes.c_double), _P(_SZ)]),
     ("mc_value_and_grad_tangent", ctypes.c_int, [_V, _V, _V, _U64, _U64, _U64, _V, _V, _V, _V, _SZ, _V]),
     ("mc_tc_gemm_bf16", ctypes.c_int, [_V, ctypes.c_int64, _V, ctypes.c_int64, _I32, _I32, _I32, _I32, _V,
                                        ctypes.c_int64, _V, _V]),

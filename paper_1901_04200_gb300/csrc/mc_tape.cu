@@ -737,6 +737,7 @@ struct JitSeg {
 };
 
 struct JitPlan {
+    bool recompute = false;             // backward kernels re-run their segment's forward
     std::vector<JitSeg> segs;           // stage order, then program order
     std::vector<int> seg_begin;         // per stage: first segment; + end entry
     std::vector<char> store, far;       // per node, compiled mode
@@ -879,8 +880,10 @@ namespace {
 
 // ------------------------------------------------ tape compiler: plan ----
 
-JitPlan *make_jit_plan(const std::vector<mc_tape_node> &nodes, const TapePlan &p, int seg_nodes, size_t rb) {
+JitPlan *make_jit_plan(const std::vector<mc_tape_node> &nodes, const TapePlan &p, int seg_nodes, size_t rb,
+                       bool recompute) {
     JitPlan *J = new JitPlan;
+    J->recompute = recompute;
     const int n = p.n_nodes;
     std::vector<int> seg_of(n, -1);
     for (int s = 0; s < p.n_stages; ++s) {
@@ -905,9 +908,9 @@ JitPlan *make_jit_plan(const std::vector<mc_tape_node> &nodes, const TapePlan &p
             const int a = args[q];
             if (p.cls[a] != 1) continue;
             if (!(p.cls[i] == 1 && seg_of[i] == seg_of[a])) J->store[a] = J->far[a] = 1;  // outside user
-            if (needs_arg_value(nodes[i].op, q)) J->store[a] = 1;
+            if (!recompute && needs_arg_value(nodes[i].op, q)) J->store[a] = 1;
         }
-        if (p.cls[i] == 1 && needs_own_value(nodes[i].op)) J->store[i] = 1;
+        if (!recompute && p.cls[i] == 1 && needs_own_value(nodes[i].op)) J->store[i] = 1;
     }
     size_t b = 0;
     for (int i = 0; i < n; ++i)
@@ -937,7 +940,8 @@ JitPlan *make_jit_plan(const std::vector<mc_tape_node> &nodes, const TapePlan &p
                 if (needs_arg_value(nodes[i].op, q)) add(bwd_loads, a);
             }
         }
-        b += rb * (fwd_loads.size() + bwd_loads.size()) + 2 * rb * far_rows.size();
+        // with recompute the backward kernel loads what the forward kernel loads, and nothing more
+        b += rb * (fwd_loads.size() + (recompute ? fwd_loads.size() : bwd_loads.size())) + 2 * rb * far_rows.size();
         for (int d : sg.dargs) J->dslot.push_back(-p.ref[d] - 1);
     }
     J->bytes_per_path = b;
@@ -966,25 +970,16 @@ std::string gen_segment(const std::vector<mc_tape_node> &nodes, const TapePlan &
     std::ostringstream o;
     o << "#include \"mc_common.cuh\"\ntypedef " << (f64 ? "double" : "float") << " R;\ntypedef unsigned long long u64;\n";
 
-    // forward: values in registers; loads of values from outside the segment at first use
-    o << "extern \"C\" __global__ void __launch_bounds__(128) fwd(const double *__restrict__ det, R *__restrict__ tape,"
-         " u64 stride, mcaad::RoundKeys rk, u64 path0, u64 n_paths) {\n"
-         " const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;\n"
-         " const u64 chunks = (n_paths + 31) / 32;\n"
-         " for (u64 ch = (u64)blockIdx.x * 4 + warp; ch < chunks; ch += (u64)gridDim.x * 4) {\n"
-         "  const u64 p = ch * 32 + lane;\n"
-         "  const bool active = p < n_paths;\n"
-         "  R *tp = tape + p;\n"
-         "  mcaad::PathNormals<R> rng;\n"
-         "  rng.init(path0 + (active ? p : 0));\n";
-    {
+    // The segment's forward body: values in registers; values from outside the segment loaded
+    // at first use through `ptr` (w<row>); with `stores`, values flagged kept go to the tape.
+    auto emit_forward = [&](bool stores, const char *ptr) {
         std::vector<char> loaded(p.n_nodes, 0);
         long long call = -1;
         auto val = [&](int a) -> std::string {
             if (p.cls[a] == 0) return det_ref(a);
             if (local[a] >= 0) return "v" + std::to_string(local[a]);
             if (!loaded[a]) {
-                o << "  const R w" << p.ref[a] << " = tp[(u64)" << p.ref[a] << " * stride];\n";
+                o << "  const R w" << p.ref[a] << " = " << ptr << "[(u64)" << p.ref[a] << " * stride];\n";
                 loaded[a] = 1;
             }
             return "w" + std::to_string(p.ref[a]);
@@ -1020,9 +1015,22 @@ std::string gen_segment(const std::vector<mc_tape_node> &nodes, const TapePlan &
             default: e = A; break;
             }
             o << "  const R v" << q << " = " << e << ";\n";
-            if (J.store[i]) o << "  tp[(u64)" << p.ref[i] << " * stride] = v" << q << ";\n";
+            if (stores && J.store[i]) o << "  " << ptr << "[(u64)" << p.ref[i] << " * stride] = v" << q << ";\n";
         }
-    }
+    };
+
+    // forward kernel
+    o << "extern \"C\" __global__ void __launch_bounds__(128) fwd(const double *__restrict__ det, R *__restrict__ tape,"
+         " u64 stride, mcaad::RoundKeys rk, u64 path0, u64 n_paths) {\n"
+         " const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;\n"
+         " const u64 chunks = (n_paths + 31) / 32;\n"
+         " for (u64 ch = (u64)blockIdx.x * 4 + warp; ch < chunks; ch += (u64)gridDim.x * 4) {\n"
+         "  const u64 p = ch * 32 + lane;\n"
+         "  const bool active = p < n_paths;\n"
+         "  R *tp = tape + p;\n"
+         "  mcaad::PathNormals<R> rng;\n"
+         "  rng.init(path0 + (active ? p : 0));\n";
+    emit_forward(true, "tp");
     o << " }\n}\n";
 
     // backward: adjoints of the segment's nodes in registers; values its partials need loaded
@@ -1039,7 +1047,7 @@ std::string gen_segment(const std::vector<mc_tape_node> &nodes, const TapePlan &
     }
     o << "extern \"C\" __global__ void __launch_bounds__(128) bwd(const double *__restrict__ det,"
          " const R *__restrict__ tape, R *__restrict__ adj, u64 stride, u64 n_paths, double *__restrict__ part,"
-         " int n_darg) {\n"
+         " int n_darg, mcaad::RoundKeys rk, u64 path0) {\n"
          " extern __shared__ double wacc[];\n"
          " for (int q = threadIdx.x; q < 4 * n_darg; q += blockDim.x) wacc[q] = 0.0;\n"
          " __syncthreads();\n"
@@ -1051,6 +1059,10 @@ std::string gen_segment(const std::vector<mc_tape_node> &nodes, const TapePlan &
          "  const bool active = p < n_paths;\n"
          "  const R *tv = tape + p;\n"
          "  R *ta = adj + p;\n";
+    if (J.recompute) {  // the segment's values, re-run in registers: the partials need no tape loads
+        o << "  mcaad::PathNormals<R> rng;\n  rng.init(path0 + (active ? p : 0));\n";
+        emit_forward(false, "tv");
+    }
     for (size_t q = 0; q < sg.nodes.size(); ++q) o << "  R a" << q << " = R(0);\n";
     for (int a : far_rows) o << "  R f" << p.ref[a] << " = R(0);\n";
     for (size_t l = 0; l < sg.dargs.size(); ++l) o << "  R g" << l << " = R(0);\n";
@@ -1058,6 +1070,7 @@ std::string gen_segment(const std::vector<mc_tape_node> &nodes, const TapePlan &
         std::vector<char> vloaded(p.n_nodes, 0);
         auto value = [&](int a) -> std::string {
             if (p.cls[a] == 0) return det_ref(a);
+            if (J.recompute) return local[a] >= 0 ? "v" + std::to_string(local[a]) : "w" + std::to_string(p.ref[a]);
             if (!vloaded[a]) {
                 o << "  const R u" << p.ref[a] << " = tv[(u64)" << p.ref[a] << " * stride];\n";
                 vloaded[a] = 1;
@@ -1228,8 +1241,8 @@ mc_status run_tape_jit(mc_tape *t, const double *theta, uint64_t seed, uint64_t 
             const double *det = t->det;
             double *part = t->part;
             int na = (int)sg.dargs.size();
-            void *args[] = {(void *)&det, (void *)&tape, (void *)&adj, (void *)&stride, (void *)&n_paths, (void *)&part,
-                            (void *)&na};
+            void *args[] = {(void *)&det, (void *)&tape,  (void *)&adj, (void *)&stride, (void *)&n_paths,
+                            (void *)&part, (void *)&na,   (void *)&rk,  (void *)&path0};
             const int g = (int)std::min<uint64_t>((uint64_t)sg.grid_b, want);
             const cudaError_t e = cudaLaunchKernel((const void *)sg.bwd, dim3(g), dim3(kBlock), args, sg.smem_b, st);
             if (e != cudaSuccess) return tfail(t, MC_ERR_CUDA, "compiled backward: %s", cudaGetErrorString(e));
@@ -1401,14 +1414,14 @@ mc_status mc_tape_path_values(mc_tape *t, int32_t node, double *out, void *strea
     return e == cudaSuccess ? MC_OK : tfail(t, MC_ERR_CUDA, "widen: %s", cudaGetErrorString(e));
 }
 
-mc_status mc_tape_compile(mc_tape *t, int32_t seg_nodes, int32_t threads, double *seconds_out,
+mc_status mc_tape_compile(mc_tape *t, int32_t seg_nodes, int32_t recompute, int32_t threads, double *seconds_out,
                           size_t *hbm_bytes_out) {
     if (!t) return MC_ERR_INVALID_ARG;
     if (seg_nodes <= 0) seg_nodes = 384;
     if (threads <= 0) threads = (int)std::max(1u, std::thread::hardware_concurrency());
     const auto t0 = std::chrono::steady_clock::now();
     const size_t rb = t->precision == MC_FP64 ? 8 : 4;
-    JitPlan *J = make_jit_plan(t->src_nodes, t->plan, seg_nodes, rb);
+    JitPlan *J = make_jit_plan(t->src_nodes, t->plan, seg_nodes, rb, recompute != 0);
     const int nseg = (int)J->segs.size();
     for (int k = 0; k < nseg; ++k) J->segs[k].src = gen_segment(t->src_nodes, t->plan, *J, k, t->precision);
     std::atomic<int> next(0), failed(-1);

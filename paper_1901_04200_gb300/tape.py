@@ -172,13 +172,14 @@ class TapeContext:
         self._n = int(n_paths)
         return val, grad[:self.n_params]
 
-    def compile(self, seg_nodes: int = 0, threads: int = 0):
-        """Compile the program into straight-line kernels (mc_tape_compile); returns
+    def compile(self, seg_nodes: int = 0, recompute: bool = False, threads: int = 0):
+        """Compile the program into straight-line kernels (mc_tape_compile); with recompute the
+        backward kernels re-run their segment's forward instead of reloading values.  Returns
         (compile seconds, HBM bytes per path of one compiled value and gradient)."""
         from . import _lib
         sec, hb = ctypes.c_double(0.0), ctypes.c_size_t(0)
-        self._check(_lib.load().mc_tape_compile(self.handle, int(seg_nodes), int(threads), ctypes.byref(sec),
-                                                ctypes.byref(hb)))
+        self._check(_lib.load().mc_tape_compile(self.handle, int(seg_nodes), 1 if recompute else 0, int(threads),
+                                                ctypes.byref(sec), ctypes.byref(hb)))
         return sec.value, hb.value
 
     def path_values(self, node: Node, stream=None):

@@ -198,9 +198,10 @@ def test_heston_tape_bench_size_equals_two_step(T):
 
 # ------------------------------------------------------ compiled programs
 
+@pytest.mark.parametrize("recompute", [False, True])
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
 @pytest.mark.parametrize("seed,seg", [(1, 40), (3, 7), (4, 1000)])
-def test_compiled_equals_interpreter_and_oracle(T, orc, seed, seg, precision, tol):
+def test_compiled_equals_interpreter_and_oracle(T, orc, seed, seg, precision, tol, recompute):
     """mc_tape_compile: straight-line segment kernels give the interpreter's results (to the
     rounding of reordered sums) and the oracle's."""
     P = 3000
@@ -211,7 +212,7 @@ def test_compiled_equals_interpreter_and_oracle(T, orc, seed, seg, precision, to
     a = T.TapeContext(prog, nodes[obj], 4, max_paths=P, precision=precision)
     Ga, ga = a.value_and_grad(theta, phil, P)
     b = T.TapeContext(prog, nodes[obj], 4, max_paths=P, precision=precision)
-    sec, hb = b.compile(seg_nodes=seg)
+    sec, hb = b.compile(seg_nodes=seg, recompute=recompute)
     assert sec > 0 and hb > 0
     Gb, gb = b.value_and_grad(theta, phil, P)
     assert abs(Gb.item() - Ga.item()) <= tol * max(abs(Ga.item()), 1.0)
@@ -231,7 +232,7 @@ def test_compiled_heston_objective_equals_two_step(T, orc):
     pb = replace(w.problem, precision="fp64", ckpt_every=4)
     prog, G = T.heston_objective(pb, w.C)
     ctx = T.TapeContext(prog, G, 5, max_paths=2000)
-    ctx.compile(seg_nodes=64)
+    ctx.compile(seg_nodes=64, recompute=True)
     Gt, gt = ctx.value_and_grad(w.theta, pb.seed, 2000, path0=77)
     _, Go, go = orc.value_and_grad(pb, w.theta, w.C, 2000, path0=77)
     assert abs(Gt.item() - Go) <= 1e-10 * abs(Go)
