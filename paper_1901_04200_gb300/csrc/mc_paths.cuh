@@ -598,7 +598,12 @@ struct NormalSource {
             if (pb.normals) table = pb.normals + (size_t)(p - pb.normals_path0) * pb.normals_stride;
         }
     }
-    // Normals of step n, first == true at a segment's first step.
+    // Normals of step n.  first: the Philox block holding the step's first normal
+    // may not be loaded -- a path's first step, or a segment's first step where
+    // segments are visited out of order (the recompute of the reverse sweep); a
+    // forward sweep reuses the block across its segments, which for segments
+    // that do not start on a block boundary (local vol, K = 5) saves a block
+    // per segment.
     __device__ __forceinline__ void get(int n, bool first, Real *z, const RoundKeys &rk) {
 #pragma unroll
         for (int c = 0; c < Md::DZ; ++c) {
@@ -705,7 +710,7 @@ __global__ void __launch_bounds__(kBlock) path_forward_kernel(const DevProblem p
             for (int i = 0; i < K; ++i) {
                 const int n = s * K + i;
 #pragma unroll
-                for (int q = 0; q < PPT; ++q) rng[q].get(n, i == 0, zs[i][q], rk);
+                for (int q = 0; q < PPT; ++q) rng[q].get(n, s == 0 && i == 0, zs[i][q], rk);
                 if (cl.keep_ckpt) {
 #pragma unroll
                     for (int g0 = 0; g0 < TL::RZ; g0 += TL::kG)  // groups whose last normals row is step i's
@@ -910,7 +915,7 @@ __global__ void __launch_bounds__(kBlock) path_forward_store_kernel(const DevPro
 #pragma unroll
                 for (int q = 0; q < PPT; ++q) {
                     Real z[Md::DZ];
-                    rng[q].get(n, i == 0, z, rk);
+                    rng[q].get(n, s == 0 && i == 0, z, rk);
                     Tape t;
                     Md::step(st[q], z, n, par, sh, &t);
                     const Real *tf = (const Real *)&t;
