@@ -82,7 +82,7 @@ struct SmemPlan {
             o = align_up(o, 16);
             o += (size_t)n_steps * 4;                // time cell jt_n
             o = align_up(o, 16);
-            if (reverse) o += (size_t)nx * 2 * real_bytes * kBlock;  // per-thread row adjoints
+            if (reverse) o += (size_t)nx * 2 * real_bytes * kBlock;  // per-thread node adjoints
         }
         zstage = o = align_up(o, 16);
         o += zstage_bytes;
@@ -272,11 +272,13 @@ struct LvModel {
         const Real *row;  // [n_steps][nx]
         const Real *a;    // [n_steps]
         const int *jt;    // [n_steps]
-        Real *racc;       // [nx][2][kBlock] per-thread row adjoints (reverse)
+        Real *racc;       // reverse: [nx][kBlock][2] per-thread node adjoints of rows jt, jt+1
         int nx;
     };
     struct Par { Real rdt, dt, sdt, x_lo, inv_hx; int nxm2; };
-    struct Acc { int jt; };
+    // jt: the time row being accumulated; at, oma: a_n and 1 - a_n of the step
+    // whose adjoints run next
+    struct Acc { int jt; Real at, oma; };
 
     __device__ static void setup(unsigned char *base, const SmemPlan &sp, const DevProblem &pb,
                                  const double *theta, int n_steps, Shared &sh, Par &par) {
@@ -336,24 +338,46 @@ struct LvModel {
             t->z = z[0];
         }
     }
+    // Node k's pair (row jt, row jt+1) of thread t: one 2-vector at (k * kBlock + t) * 2.
+    __device__ __forceinline__ static Real *acc_slot(const Shared &sh, int k) {
+        return sh.racc + (k * kBlock + (int)threadIdx.x) * 2;
+    }
+    __device__ __forceinline__ static void add_node(const Shared &sh, const Acc &a, int k, Real g) {
+        Real *r = acc_slot(sh, k);
+        if constexpr (sizeof(Real) == 4) {
+            float2 v = *(float2 *)r;
+            v.x = fma(a.oma, g, v.x);
+            v.y = fma(a.at, g, v.y);
+            *(float2 *)r = v;
+        } else {
+            double2 v = *(double2 *)r;
+            v.x = fma(a.oma, g, v.x);
+            v.y = fma(a.at, g, v.y);
+            *(double2 *)r = v;
+        }
+    }
     __device__ static void acc_begin(Acc &a, int n_last, const Shared &sh) {
         a.jt = sh.jt[n_last - 1];
-        Real *r = sh.racc;
-        for (int q = 0; q < 2 * sh.nx; ++q) r[q * kBlock + threadIdx.x] = Real(0);
+        a.at = a.oma = Real(0);
+        for (int k = 0; k < sh.nx; ++k) {
+            Real *r = acc_slot(sh, k);
+            r[0] = r[1] = Real(0);
+        }
     }
     // Rows jt and jt+1 are the contiguous node range [jt*nx, (jt+2)*nx).
     __device__ __noinline__ static void flush_rows(Acc &a, const Shared &sh, double *wacc, int lane) {
-        Real *r = sh.racc + threadIdx.x;
         const int nx = sh.nx;
-        for (int row = 0; row < 2; ++row) {
-            Real mine = Real(0);
-            for (int c = 0; c < nx; ++c) {
-                Real *q = r + (2 * c + row) * kBlock;
-                const Real s = warp_sum(*q);
-                *q = Real(0);
-                mine = (lane == c) ? s : mine;
-            }
-            if (lane < nx) wacc[(a.jt + row) * nx + lane] += (double)mine;
+        Real mine0 = Real(0), mine1 = Real(0);
+        for (int k = 0; k < nx; ++k) {
+            Real *r = acc_slot(sh, k);
+            const Real s0 = warp_sum(r[0]), s1 = warp_sum(r[1]);
+            r[0] = r[1] = Real(0);
+            mine0 = (lane == k) ? s0 : mine0;
+            mine1 = (lane == k) ? s1 : mine1;
+        }
+        if (lane < nx) {
+            wacc[a.jt * nx + lane] += (double)mine0;
+            wacc[(a.jt + 1) * nx + lane] += (double)mine1;
         }
     }
     __device__ __forceinline__ static void boundary(Acc &a, int n, const Shared &sh, double *wacc, int lane) {
@@ -362,10 +386,12 @@ struct LvModel {
             flush_rows(a, sh, wacc, lane);
             a.jt = jt;
         }
+        a.at = sh.a[n];
+        a.oma = Real(1) - a.at;
     }
     // sigma-bar = xb (sqrt(dt) z - sigma dt); node adjoints sigma-bar times the
     // bilinear weights; xb += sigma-bar d sigma/dx (0 where x is clamped).
-    __device__ __forceinline__ static void adjoint(const Tape &t, int n, Real &xb, Real &, Acc &,
+    __device__ __forceinline__ static void adjoint(const Tape &t, int n, Real &xb, Real &, Acc &a,
                                                    const Par &p, const Shared &sh) {
         int c;
         Real b;
@@ -376,13 +402,9 @@ struct LvModel {
         const Real ds = s1 - s0;
         const Real sig = fma(b, ds, s0);
         const Real sb = xb * fma(p.sdt, t.z, -sig * p.dt);
-        const Real at = sh.a[n];
         const Real g1 = sb * b, g0 = sb - g1;
-        Real *r = sh.racc + threadIdx.x;
-        r[(2 * c) * kBlock] = fma(Real(1) - at, g0, r[(2 * c) * kBlock]);
-        r[(2 * c + 1) * kBlock] = fma(at, g0, r[(2 * c + 1) * kBlock]);
-        r[(2 * c + 2) * kBlock] = fma(Real(1) - at, g1, r[(2 * c + 2) * kBlock]);
-        r[(2 * c + 3) * kBlock] = fma(at, g1, r[(2 * c + 3) * kBlock]);
+        add_node(sh, a, c, g0);
+        add_node(sh, a, c + 1, g1);
         if (inside) xb = fma(sb * p.inv_hx, ds, xb);
     }
     __device__ static void acc_end(Acc &a, Real, const Par &, const Shared &sh, double *wacc, int lane) {
@@ -474,13 +496,9 @@ struct SlvModel {
         const Real lev = fma(b, ds, s0);
         const Real sq = t.vdt * t.rs;
         const Real lb = xb * fma(sq, t.z1, -lev * t.vdt);
-        const Real at = sh.a[n];
         const Real g1 = lb * b, g0 = lb - g1;
-        Real *r = sh.racc + threadIdx.x;
-        r[(2 * c) * kBlock] = fma(Real(1) - at, g0, r[(2 * c) * kBlock]);
-        r[(2 * c + 1) * kBlock] = fma(at, g0, r[(2 * c + 1) * kBlock]);
-        r[(2 * c + 2) * kBlock] = fma(Real(1) - at, g1, r[(2 * c + 2) * kBlock]);
-        r[(2 * c + 3) * kBlock] = fma(at, g1, r[(2 * c + 3) * kBlock]);
+        Lv::add_node(sh, a.l, c, g0);
+        Lv::add_node(sh, a.l, c + 1, g1);
         const Real vsq = vb * sq;
         a.h.a = fma(vsq, t.z1, a.h.a);
         a.h.b = fma(vsq, t.w, a.h.b);
