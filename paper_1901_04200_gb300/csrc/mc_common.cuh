@@ -69,10 +69,27 @@ __device__ __forceinline__ double uniform_f64(uint32_t w) {
     return ((double)(w >> 9) + 0.5) * (1.0 / 8388608.0);
 }
 
+// The hardware approximations in their flush-to-zero forms: every argument
+// they get on the path is a normal number (or zero), where the two forms agree,
+// and the flush-to-zero form needs no rescaling around the instruction.
 __device__ __forceinline__ float sqrt_approx(float x) {
     float r;
     asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
     return r;
+}
+__device__ __forceinline__ float rsqrt_approx(float x) {
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float log2_approx(float x) {
+    float r;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ void sincos_approx(float x, float &s, float &c) {
+    asm("sin.approx.ftz.f32 %0, %1;" : "=f"(s) : "f"(x));
+    asm("cos.approx.ftz.f32 %0, %1;" : "=f"(c) : "f"(x));
 }
 
 // Box-Muller on one pair of uniforms: rad = sqrt(-2 ln u_a),
@@ -80,12 +97,13 @@ __device__ __forceinline__ float sqrt_approx(float x) {
 // angle as 2 pi (u_b - 1/2) + pi, i.e. negates cos and sin of an argument in
 // (-pi, pi), where the fast hardware sine/cosine are accurate; u_b - 1/2 is
 // exact.  -2 ln u_a is clamped at 0 against the approximate log near u = 1.
+// u_a >= 2^-24 is normal; the angle is 0 or at least 2 pi 2^-24 in magnitude.
 __device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, float &za, float &zb) {
     const float ua = uniform_f32(a);
     const float ub = uniform_f32(b);
-    const float rad = sqrt_approx(fmaxf(-1.38629436111989061f * __log2f(ua), 0.0f));  // -2 ln u = (-2 ln 2) log2 u
+    const float rad = sqrt_approx(fmaxf(-1.38629436111989061f * log2_approx(ua), 0.0f));  // -2 ln u = (-2 ln 2) log2 u
     float s, c;
-    __sincosf(fmaf(6.28318530717958648f, ub, -3.14159265358979324f), &s, &c);  // 2 pi u_b - pi, one rounding
+    sincos_approx(fmaf(6.28318530717958648f, ub, -3.14159265358979324f), s, c);  // 2 pi u_b - pi, one rounding
     za = -rad * c;
     zb = -rad * s;
 }

@@ -35,7 +35,7 @@ namespace mcaad {
 template <typename T>
 __device__ __forceinline__ T rsqrt_r(T x);
 template <>
-__device__ __forceinline__ float rsqrt_r<float>(float x) { return rsqrtf(x); }
+__device__ __forceinline__ float rsqrt_r<float>(float x) { return rsqrt_approx(x); }  // x >= 1e-30 where used
 template <>
 __device__ __forceinline__ double rsqrt_r<double>(double x) { return rsqrt(x); }
 
