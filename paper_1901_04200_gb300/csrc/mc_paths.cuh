@@ -313,11 +313,22 @@ struct LvModel {
     }
     __device__ static State init(const Par &) { return State{Real(0)}; }
 
-    // Cell c = clamp(floor(u), 0, nx-2) and weight b = clamp(u - c, 0, 1).
+    // Cell c = clamp(floor(u), 0, nx-2) = floor(clamp(u, 0, nx-2)) and weight
+    // b = clamp(u - c, 0, 1).  In FP32 the floor of the clamped u (in [0, 30])
+    // comes from one addition of 1.5 2^23 rounded toward minus infinity: the
+    // sum's last place is 1, so it holds 1.5 2^23 + floor, its low bits are the
+    // integer, and subtracting 1.5 2^23 again is exact -- no conversion
+    // instructions.
     __device__ __forceinline__ static void cell(Real u, const Par &p, int &c, Real &b, bool &inside) {
-        // the clamped floor stays a float: u - f needs no int-to-float conversion
-        const Real f = fmin(fmax(floor(u), Real(0)), (Real)p.nxm2);
-        c = (int)f;
+        Real f;
+        if constexpr (sizeof(Real) == 4) {
+            const float r = __fadd_rd(fminf(fmaxf(u, 0.0f), (float)p.nxm2), 12582912.0f);
+            f = r - 12582912.0f;
+            c = __float_as_int(r) - 0x4B400000;
+        } else {
+            f = fmin(fmax(floor(u), Real(0)), (Real)p.nxm2);
+            c = (int)f;
+        }
         const Real bb = u - f;
         inside = (bb >= Real(0)) && (bb <= Real(1));
         b = fmin(fmax(bb, Real(0)), Real(1));
@@ -679,6 +690,9 @@ __global__ void __launch_bounds__(kBlock) path_forward_kernel(const DevProblem p
     // Philox round keys: from the kernel parameters (constant bank), or formed
     // once per thread into registers, whichever measured faster for the model
     const RoundKeys rk = Md::kKeysInRegisters ? philox_round_keys(cl.seed) : cl.rk;
+    // The stored-normals variant always keeps its tiles: a compile-time
+    // condition leaves each unrolled segment one branch-free block to schedule.
+    const bool keep = kStoreZ || cl.keep_ckpt;
 
     constexpr uint64_t kChunk = (uint64_t)kWarp * PPT;
     const uint64_t n_chunks = (cl.n_paths + kChunk - 1) / kChunk;
@@ -719,7 +733,7 @@ __global__ void __launch_bounds__(kBlock) path_forward_kernel(const DevProblem p
                 }
                 *TL::group(tl, g0 / TL::kG, lane) = TL::V::make(v);
             };
-            if (cl.keep_ckpt) {
+            if (keep) {
 #pragma unroll
                 for (int g0 = 0; g0 < TL::Rp; g0 += TL::kG)
                     if (g0 >= TL::RZ) store_group(g0);  // checkpoint (and padding) only
@@ -729,7 +743,7 @@ __global__ void __launch_bounds__(kBlock) path_forward_kernel(const DevProblem p
                 const int n = s * K + i;
 #pragma unroll
                 for (int q = 0; q < PPT; ++q) rng[q].get(n, s == 0 && i == 0, zs[i][q], rk);
-                if (cl.keep_ckpt) {
+                if (keep) {
 #pragma unroll
                     for (int g0 = 0; g0 < TL::RZ; g0 += TL::kG)  // groups whose last normals row is step i's
                         if ((min(g0 + TL::kG, TL::RZ) - 1) / (Md::DZ * PPT) == i) store_group(g0);
