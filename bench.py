@@ -544,9 +544,11 @@ def main():
                     help="per-path values and adjoints of the --workload tape run")
     ap.add_argument("--tape-interpret", action="store_true",
                     help="--workload tape: run the interpreter instead of the compiled program")
-    ap.add_argument("--tape-seg", type=int, default=0, help="--workload tape: nodes per compiled segment")
-    ap.add_argument("--tape-recompute", action="store_true",
-                    help="--workload tape: compiled backward kernels re-run their segment's forward")
+    ap.add_argument("--tape-seg", type=int, default=1024,
+                    help="--workload tape: nodes per compiled segment (0 = library default, 384)")
+    ap.add_argument("--tape-store", dest="tape_recompute", action="store_false",
+                    help="--workload tape: compiled backward kernels read every value they need from the "
+                         "tape; by default they re-run their segment's forward, which measured faster")
     ap.add_argument("--workload", default="heston", choices=["heston", "lv", "slv", "surrogate", "tape"],
                     help="heston (the metric's workload), lv (2^22 x 500 local vol) or surrogate "
                          "(one differential-loss training step of the pricing network), for measurement")
