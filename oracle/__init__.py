@@ -8,7 +8,7 @@ called through ctypes.  A problem is any object with the attributes of
 ``paper_1901_04200_gb300.inputs.Problem`` (read by duck typing, so this package
 imports nothing from the product).
 
-Readings of the paper that this oracle fixes (all also listed in the design doc):
+Readings of the paper that this oracle fixes:
 state x = ln(S/S0); call payoffs discounted with exp(-r T); payoff kink
 derivative 1{S > K}; Heston full truncation with derivative 1{v > 0} of
 max(v, 0); local volatility bilinear with flat extrapolation; normals from
