@@ -615,6 +615,9 @@ struct SegTile {
     }
 };
 
+// Segments of n normals per path that together fill whole Philox blocks of four.
+__host__ __device__ constexpr int philox_period_segments(int n) { return n % 4 == 0 ? 1 : n % 2 == 0 ? 2 : 4; }
+
 template <class Md>
 struct NormalSource {
     using Real = typename Md::Real;
@@ -710,68 +713,77 @@ __global__ void __launch_bounds__(kBlock) path_forward_kernel(const DevProblem p
             st[q] = Md::init(par);
         }
         int g = 0;
-        for (int s = 0; s < pb.n_seg; ++s) {
-            // the segment's normals first: its Philox blocks are independent of the state, so
-            // the scheduler can overlap them; then the K dependent Euler steps.  The tile's
-            // groups (normals when kept, checkpoint) go out as soon as all their rows exist.
-            Real zs[K][PPT][Md::DZ];
-            Real *tl = TL::tile(cl.ckpt, ch, cl.ckpt_stride / kChunk, s);
-            auto store_group = [&](int g0) {
-                Real v[TL::kG];
+        // Segments in groups of kPeriod whose normals fill whole Philox blocks, so
+        // that each normal's block refill and lane are compile-time constants
+        // (local vol, K = 5: four segments per 20 normals; Heston: one segment).
+        constexpr int kPeriod = philox_period_segments(K * Md::DZ);
+        for (int sg = 0; sg * kPeriod < pb.n_seg; ++sg) {
 #pragma unroll
-                for (int k = 0; k < TL::kG; ++k) {
-                    const int r = g0 + k;
-                    if (r < TL::RZ) {
-                        v[k] = zs[r / (Md::DZ * PPT)][r % PPT][(r / PPT) % Md::DZ];
-                    } else if (r < TL::R) {
-                        const int w = (r - TL::RZ) / PPT, q = (r - TL::RZ) % PPT;
-                        if constexpr (Md::SD == 2) v[k] = w == 0 ? st[q].x : st[q].v;
-                        else v[k] = st[q].x;
-                    } else {
-                        v[k] = Real(0);
+            for (int ss = 0; ss < kPeriod; ++ss) {
+                const int s = sg * kPeriod + ss;
+                if (kPeriod > 1 && s >= pb.n_seg) break;
+                // the segment's normals first: its Philox blocks are independent of the state, so
+                // the scheduler can overlap them; then the K dependent Euler steps.  The tile's
+                // groups (normals when kept, checkpoint) go out as soon as all their rows exist.
+                Real zs[K][PPT][Md::DZ];
+                Real *tl = TL::tile(cl.ckpt, ch, cl.ckpt_stride / kChunk, s);
+                auto store_group = [&](int g0) {
+                    Real v[TL::kG];
+#pragma unroll
+                    for (int k = 0; k < TL::kG; ++k) {
+                        const int r = g0 + k;
+                        if (r < TL::RZ) {
+                            v[k] = zs[r / (Md::DZ * PPT)][r % PPT][(r / PPT) % Md::DZ];
+                        } else if (r < TL::R) {
+                            const int w = (r - TL::RZ) / PPT, q = (r - TL::RZ) % PPT;
+                            if constexpr (Md::SD == 2) v[k] = w == 0 ? st[q].x : st[q].v;
+                            else v[k] = st[q].x;
+                        } else {
+                            v[k] = Real(0);
+                        }
                     }
-                }
-                *TL::group(tl, g0 / TL::kG, lane) = TL::V::make(v);
-            };
-            if (keep) {
-#pragma unroll
-                for (int g0 = 0; g0 < TL::Rp; g0 += TL::kG)
-                    if (g0 >= TL::RZ) store_group(g0);  // checkpoint (and padding) only
-            }
-#pragma unroll
-            for (int i = 0; i < K; ++i) {
-                const int n = s * K + i;
-#pragma unroll
-                for (int q = 0; q < PPT; ++q) rng[q].get(n, s == 0 && i == 0, zs[i][q], rk);
+                    *TL::group(tl, g0 / TL::kG, lane) = TL::V::make(v);
+                };
                 if (keep) {
 #pragma unroll
-                    for (int g0 = 0; g0 < TL::RZ; g0 += TL::kG)  // groups whose last normals row is step i's
-                        if ((min(g0 + TL::kG, TL::RZ) - 1) / (Md::DZ * PPT) == i) store_group(g0);
+                    for (int g0 = 0; g0 < TL::Rp; g0 += TL::kG)
+                        if (g0 >= TL::RZ) store_group(g0);  // checkpoint (and padding) only
                 }
-            }
 #pragma unroll
-            for (int i = 0; i < K; ++i) {
+                for (int i = 0; i < K; ++i) {
+                    const int n = s * K + i;
 #pragma unroll
-                for (int q = 0; q < PPT; ++q) Md::step(st[q], zs[i][q], s * K + i, par, sh, nullptr);
-            }
-            if (g < pb.n_groups && gseg[g] == s) {
-                Real S[PPT];
+                    for (int q = 0; q < PPT; ++q) rng[q].get(n, s == 0 && i == 0, zs[i][q], rk);
+                    if (keep) {
 #pragma unroll
-                for (int q = 0; q < PPT; ++q) S[q] = S0 * exp_r<Real>(st[q].x);
-                for (int i0 = gbeg[g]; i0 < gbeg[g + 1]; i0 += kWarp) {
-                    const int cnt = min(kWarp, gbeg[g + 1] - i0);
-                    Real mine = Real(0);
-                    for (int j = 0; j < cnt; ++j) {
-                        Real pay = Real(0);
-#pragma unroll
-                        for (int q = 0; q < PPT; ++q)
-                            pay += active[q] ? fmax(S[q] - strike[i0 + j], Real(0)) : Real(0);
-                        const Real sum = warp_sum(pay);
-                        mine = (lane == j) ? sum : mine;
+                        for (int g0 = 0; g0 < TL::RZ; g0 += TL::kG)  // groups whose last normals row is step i's
+                            if ((min(g0 + TL::kG, TL::RZ) - 1) / (Md::DZ * PPT) == i) store_group(g0);
                     }
-                    if (lane < cnt) wy[i0 + lane] += (double)mine;
                 }
-                ++g;
+#pragma unroll
+                for (int i = 0; i < K; ++i) {
+#pragma unroll
+                    for (int q = 0; q < PPT; ++q) Md::step(st[q], zs[i][q], s * K + i, par, sh, nullptr);
+                }
+                if (g < pb.n_groups && gseg[g] == s) {
+                    Real S[PPT];
+#pragma unroll
+                    for (int q = 0; q < PPT; ++q) S[q] = S0 * exp_r<Real>(st[q].x);
+                    for (int i0 = gbeg[g]; i0 < gbeg[g + 1]; i0 += kWarp) {
+                        const int cnt = min(kWarp, gbeg[g + 1] - i0);
+                        Real mine = Real(0);
+                        for (int j = 0; j < cnt; ++j) {
+                            Real pay = Real(0);
+#pragma unroll
+                            for (int q = 0; q < PPT; ++q)
+                                pay += active[q] ? fmax(S[q] - strike[i0 + j], Real(0)) : Real(0);
+                            const Real sum = warp_sum(pay);
+                            mine = (lane == j) ? sum : mine;
+                        }
+                        if (lane < cnt) wy[i0 + lane] += (double)mine;
+                    }
+                    ++g;
+                }
             }
         }
     }
