@@ -98,6 +98,14 @@ def test_gbm_fp64_philox_ragged(L, orc):
     check(L, orc, w, 1e-10, 1e-12, n_paths=1001, path0=(1 << 32) - 500)
 
 
+@pytest.mark.parametrize("n_steps", [7, 14])
+def test_gbm_fp64_philox_partial_period(L, orc, n_steps):
+    """Seven segments of one step (groups of four per Philox block) or two steps (groups of two)."""
+    w = inputs.gbm_config(n_paths=16, n_steps=n_steps, n_buckets=7)
+    w = replace(w, problem=replace(w.problem, normals=None))
+    check(L, orc, w, 1e-10, 1e-12, n_paths=777)
+
+
 @pytest.mark.parametrize("storage", ["checkpoint", "normals"])
 @pytest.mark.parametrize("K,ppt", [(1, 1), (2, 1), (4, 1), (8, 1), (2, 2), (4, 2), (8, 2)])
 def test_heston_fp64_all_segment_lengths(L, orc, K, ppt, storage):
@@ -118,6 +126,17 @@ def test_heston_fp64_no_feller(L, orc):
 @pytest.mark.parametrize("K,ppt", [(1, 1), (5, 1), (25, 1), (5, 2)])
 def test_lv_fp64(L, orc, K, ppt, storage):
     w = inputs.lv_config(n_paths=1500, n_steps=100, T=2.0, nt=5, nx=6, n_mat=4, n_strike=5)
+    w = replace(w, problem=replace(w.problem, precision="fp64", ckpt_every=K, paths_per_thread=ppt,
+                                   storage=storage))
+    check(L, orc, w, 1e-10, 1e-12)
+
+
+@pytest.mark.parametrize("storage", ["checkpoint", "normals"])
+@pytest.mark.parametrize("K,ppt", [(1, 1), (5, 1), (5, 2)])
+def test_lv_fp64_partial_philox_period(L, orc, K, ppt, storage):
+    """95 steps: 19 segments at K = 5 and 95 at K = 1, so the forward sweep's last group of
+    segments (four per Philox period of 20 or 4 normals) is partial."""
+    w = inputs.lv_config(n_paths=1100, n_steps=95, T=1.9, nt=5, nx=6, n_mat=19, n_strike=2)
     w = replace(w, problem=replace(w.problem, precision="fp64", ckpt_every=K, paths_per_thread=ppt,
                                    storage=storage))
     check(L, orc, w, 1e-10, 1e-12)
