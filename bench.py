@@ -544,7 +544,7 @@ def main():
                     help="per-path values and adjoints of the --workload tape run")
     ap.add_argument("--tape-interpret", action="store_true",
                     help="--workload tape: run the interpreter instead of the compiled program")
-    ap.add_argument("--tape-seg", type=int, default=1024,
+    ap.add_argument("--tape-seg", type=int, default=768,
                     help="--workload tape: nodes per compiled segment (0 = library default, 384)")
     ap.add_argument("--tape-store", dest="tape_recompute", action="store_false",
                     help="--workload tape: compiled backward kernels read every value they need from the "

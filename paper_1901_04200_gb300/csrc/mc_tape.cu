@@ -204,6 +204,7 @@ struct DevLists {
     std::vector<int> det_off, path_off, exp_off, darg_off;  // per stage, + 1 end entry each
     std::vector<int> darg_slot;                              // flattened: DET slot of each accumulated argument
     std::vector<char> stored;                                // per node: its per-path values are on the tape
+    std::vector<int> far_rows;                               // tape rows whose adjoints accumulate in HBM
 };
 
 // Whether the backward partials of op need the value of argument q (0: a, 1: b) or the node's own.
@@ -257,7 +258,10 @@ DevLists make_lists(const mc_tape_node *nodes, const TapePlan &p, size_t *bytes_
         return d;
     };
     L.stored.assign(n, 0);
-    for (int i = 0; i < n; ++i) L.stored[i] = p.cls[i] == 1 && (flags[i] & kStore);
+    for (int i = 0; i < n; ++i) {
+        L.stored[i] = p.cls[i] == 1 && (flags[i] & kStore);
+        if (p.cls[i] == 1 && (flags[i] & kFar)) L.far_rows.push_back(p.ref[i]);
+    }
     if (bytes_per_path) {
         // HBM bytes per path of one value and gradient under the kernels' rules (FP64)
         size_t b = 0;
@@ -302,8 +306,8 @@ DevLists make_lists(const mc_tape_node *nodes, const TapePlan &p, size_t *bytes_
 inline size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 struct TapeWs {
-    size_t nodes, dslot, det, ddet, part, tape, adj, total;
-    TapeWs(const TapePlan &p, size_t n_all, size_t n_dslot, int grid, uint64_t stride, size_t rb) {
+    size_t nodes, dslot, frows, det, ddet, part, tape, adj, total;
+    TapeWs(const TapePlan &p, size_t n_all, size_t n_dslot, size_t n_far, int grid, uint64_t stride, size_t rb) {
         size_t o = 0;
         auto take = [&](size_t bytes) {
             size_t at = o;
@@ -312,6 +316,7 @@ struct TapeWs {
         };
         nodes = take(n_all * sizeof(DevNode));
         dslot = take(n_dslot * 4 + 4);
+        frows = take(n_far * 4 + 4);
         det = take((size_t)p.n_det * 8);
         ddet = take((size_t)p.n_det * 8);
         part = take((size_t)grid * std::max(1, std::max(p.max_exp, p.max_darg)) * 8);
@@ -386,33 +391,42 @@ __device__ __forceinline__ void stage_tile(DevNode *tile, const DevNode *__restr
     for (int q = threadIdx.x; q < cnt * kWords; q += blockDim.x) dst[q] = src[q];
 }
 
-// Deterministic nodes of a stage, in program order, by one thread; the block
-// first stages the deterministic values in shared memory when they fit
-// (in_smem), so the walk's dependent loads do not go to L2.
-constexpr int kDetSmemBytes = 48 * 1024;
+// Deterministic nodes of a stage, in program order, by one thread.  The block
+// stages the node descriptors in shared memory, kDetTile at a time, and the
+// deterministic values too when they fit (in_smem), so the walk's dependent
+// loads do not go to L2.
+constexpr int kDetTile = 256;
+constexpr size_t kDetTileBytes = (size_t)kDetTile * sizeof(DevNode);
+constexpr int kDetSmemBytes = 36 * 1024;  // values; with the tile within the default 48 KB
 
 __global__ void tape_det_forward(const DevNode *__restrict__ nd, int n, const double *__restrict__ theta,
                                  double *__restrict__ det, int n_det, int in_smem) {
-    extern __shared__ double sdet[];
+    extern __shared__ __align__(16) unsigned char dsm[];
+    DevNode *tile = (DevNode *)dsm;
+    double *sdet = (double *)(dsm + kDetTileBytes);
     double *V = in_smem ? sdet : det;
-    if (in_smem) {
+    if (in_smem)
         for (int q = threadIdx.x; q < n_det; q += blockDim.x) sdet[q] = det[q];
+    for (int t0 = 0; t0 < n; t0 += kDetTile) {
+        const int tn = min(kDetTile, n - t0);
+        __syncthreads();  // values staged; the previous tile consumed
+        stage_tile(tile, nd, t0, tn);
         __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        for (int k = 0; k < n; ++k) {
-            const DevNode d = nd[k];
-            double v;
-            if (d.op == MC_OP_PARAM) {
-                v = theta[(int)d.c];
-            } else if (d.op == MC_OP_CONST) {
-                v = d.c;
-            } else {
-                const double a = V[-d.ra - 1];
-                const double b = n_args(d.op) == 2 ? V[-d.rb - 1] : 0.0;
-                v = apply_op<double>(d.op, a, b, d.c);
+        if (threadIdx.x == 0) {
+            for (int k = 0; k < tn; ++k) {
+                const DevNode &d = tile[k];
+                double v;
+                if (d.op == MC_OP_PARAM) {
+                    v = theta[(int)d.c];
+                } else if (d.op == MC_OP_CONST) {
+                    v = d.c;
+                } else {
+                    const double a = V[-d.ra - 1];
+                    const double b = n_args(d.op) == 2 ? V[-d.rb - 1] : 0.0;
+                    v = apply_op<double>(d.op, a, b, d.c);
+                }
+                V[-d.rm - 1] = v;
             }
-            V[-d.rm - 1] = v;
         }
     }
     if (in_smem) {
@@ -645,32 +659,38 @@ __global__ void tape_darg_finalize(const double *__restrict__ part, int nb, cons
 // is added to its gradient component.
 __global__ void tape_det_backward(const DevNode *__restrict__ nd, int n, const double *__restrict__ det,
                                   double *__restrict__ ddet, double *__restrict__ grad, int n_det, int in_smem) {
-    extern __shared__ double sdet[];
+    extern __shared__ __align__(16) unsigned char dsm[];
+    DevNode *tile = (DevNode *)dsm;
+    double *sdet = (double *)(dsm + kDetTileBytes);
     const double *V = in_smem ? sdet : det;
     double *A = in_smem ? sdet + n_det : ddet;
-    if (in_smem) {
+    if (in_smem)
         for (int q = threadIdx.x; q < n_det; q += blockDim.x) {
             sdet[q] = det[q];
             sdet[n_det + q] = ddet[q];
         }
+    for (int t1 = n; t1 > 0; t1 -= kDetTile) {
+        const int t0 = max(0, t1 - kDetTile), tn = t1 - t0;
+        __syncthreads();  // values staged; the previous tile consumed
+        stage_tile(tile, nd, t0, tn);
         __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        for (int k = n - 1; k >= 0; --k) {
-            const DevNode d = nd[k];
-            const double D = A[-d.rm - 1];
-            if (d.op == MC_OP_PARAM) {
-                grad[(int)d.c] += D;
-                continue;
+        if (threadIdx.x == 0) {
+            for (int k = tn - 1; k >= 0; --k) {
+                const DevNode &d = tile[k];
+                const double D = A[-d.rm - 1];
+                if (d.op == MC_OP_PARAM) {
+                    grad[(int)d.c] += D;
+                    continue;
+                }
+                if (d.op == MC_OP_CONST) continue;
+                const bool two = n_args(d.op) == 2;
+                const double a = V[-d.ra - 1];
+                const double b = two ? V[-d.rb - 1] : 0.0;
+                double pa, pb;
+                partials<double>(d.op, a, b, V[-d.rm - 1], d.c, pa, pb);
+                A[-d.ra - 1] += D * pa;
+                if (two) A[-d.rb - 1] += D * pb;
             }
-            if (d.op == MC_OP_CONST) continue;
-            const bool two = n_args(d.op) == 2;
-            const double a = V[-d.ra - 1];
-            const double b = two ? V[-d.rb - 1] : 0.0;
-            double pa, pb;
-            partials<double>(d.op, a, b, V[-d.rm - 1], d.c, pa, pb);
-            A[-d.ra - 1] += D * pa;
-            if (two) A[-d.rb - 1] += D * pb;
         }
     }
     if (in_smem) {
@@ -682,12 +702,14 @@ __global__ void tape_det_backward(const DevNode *__restrict__ nd, int n, const d
 // Launchers (shared by the interpreter and the compiled program).
 void launch_det_forward(const DevNode *nd, int n, const double *theta, double *det, int n_det, cudaStream_t st) {
     const bool sm = (size_t)n_det * 8 <= (size_t)kDetSmemBytes;
-    tape_det_forward<<<1, kBlock, sm ? (size_t)n_det * 8 : 0, st>>>(nd, n, theta, det, n_det, sm ? 1 : 0);
+    tape_det_forward<<<1, kBlock, kDetTileBytes + (sm ? (size_t)n_det * 8 : 0), st>>>(nd, n, theta, det, n_det,
+                                                                                       sm ? 1 : 0);
 }
 void launch_det_backward(const DevNode *nd, int n, const double *det, double *ddet, double *grad, int n_det,
                          cudaStream_t st) {
     const bool sm = (size_t)n_det * 16 <= (size_t)kDetSmemBytes;
-    tape_det_backward<<<1, kBlock, sm ? (size_t)n_det * 16 : 0, st>>>(nd, n, det, ddet, grad, n_det, sm ? 1 : 0);
+    tape_det_backward<<<1, kBlock, kDetTileBytes + (sm ? (size_t)n_det * 16 : 0), st>>>(nd, n, det, ddet, grad,
+                                                                                        n_det, sm ? 1 : 0);
 }
 void launch_expect_finalize(const double *part, int nb, const DevNode *ex, int n_exp, double inv_n, double *det,
                             cudaStream_t st) {
@@ -707,6 +729,28 @@ __global__ void tape_begin_backward(double *__restrict__ ddet, int n_det, int ob
 
 __global__ void tape_copy_value(const double *__restrict__ det, int slot, double *__restrict__ out) {
     if (blockIdx.x == 0 && threadIdx.x == 0) *out = det[slot];
+}
+
+// Zero, for the evaluated paths, the adjoint rows that accumulate contributions
+// in HBM (nodes with a far or later-stage user or an expectation); no other
+// row of the adjoint array is read.  Block row y walks rows y, y + gridDim.y, ...
+template <typename Real>
+__global__ void tape_zero_rows(Real *__restrict__ adj, const int *__restrict__ rows, int n_rows, uint64_t stride,
+                               uint64_t n_paths) {
+    for (int r = blockIdx.y; r < n_rows; r += gridDim.y) {
+        Real *row = adj + (size_t)rows[r] * stride;
+        for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n_paths;
+             q += (uint64_t)gridDim.x * blockDim.x)
+            row[q] = Real(0);
+    }
+}
+
+template <typename Real>
+void launch_zero_rows(Real *adj, const int *rows, int n_rows, uint64_t stride, uint64_t n_paths, cudaStream_t st) {
+    if (n_rows <= 0) return;
+    const int gx = (int)std::min<uint64_t>((n_paths + 1023) / 1024, 1024);
+    const int gy = std::min(n_rows, 1024);
+    tape_zero_rows<Real><<<dim3(gx, gy), 256, 0, st>>>(adj, rows, n_rows, stride, n_paths);
 }
 
 __global__ void tape_widen(const float *__restrict__ in, uint64_t n, double *__restrict__ out) {
@@ -743,6 +787,8 @@ struct JitPlan {
     std::vector<char> store, far;       // per node, compiled mode
     std::vector<int> dslot;             // DET slot of every segment's accumulated arguments
     int *dslot_dev = nullptr;
+    std::vector<int> far_rows;          // tape rows whose adjoints accumulate in HBM (far nodes)
+    int *frows_dev = nullptr;
     size_t bytes_per_path = 0;
 };
 
@@ -759,6 +805,7 @@ struct mc_tape {
     unsigned char *ws = nullptr;
     DevNode *nodes = nullptr;
     int *dslot = nullptr;
+    int *frows = nullptr;  // the interpreter's HBM-accumulated adjoint rows (lists.far_rows)
     double *det = nullptr, *ddet = nullptr, *part = nullptr;
     void *tape = nullptr, *adj = nullptr;  // [n_rows][stride] of FP64 or FP32
     uint64_t last_n = 0;
@@ -851,10 +898,7 @@ mc_status run_tape(mc_tape *t, const double *theta, uint64_t seed, uint64_t path
     }
     tape_copy_value<<<1, 1, 0, st>>>(t->det, -p.ref[p.objective] - 1, value_out);
     // ---- backward sweep
-    if (p.n_rows > 0) {
-        const cudaError_t e = cudaMemsetAsync(adj, 0, (size_t)p.n_rows * t->stride * sizeof(Real), st);
-        if (e != cudaSuccess) return tfail(t, MC_ERR_CUDA, "adjoint reset: %s", cudaGetErrorString(e));
-    }
+    launch_zero_rows<Real>(adj, t->frows, (int)L.far_rows.size(), t->stride, n_paths, st);
     tape_begin_backward<<<(std::max(p.n_det, p.n_params) + 255) / 256 + 1, 256, 0, st>>>(
         t->ddet, p.n_det, -p.ref[p.objective] - 1, grad_out, p.n_params);
     for (int s = p.n_stages - 1; s >= 0; --s) {
@@ -912,6 +956,8 @@ JitPlan *make_jit_plan(const std::vector<mc_tape_node> &nodes, const TapePlan &p
         }
         if (!recompute && p.cls[i] == 1 && needs_own_value(nodes[i].op)) J->store[i] = 1;
     }
+    for (int i = 0; i < n; ++i)
+        if (J->far[i]) J->far_rows.push_back(p.ref[i]);
     size_t b = 0;
     for (int i = 0; i < n; ++i)
         if (nodes[i].op == MC_OP_EXPECT && p.cls[nodes[i].a] == 1) b += 3 * rb;
@@ -1178,6 +1224,7 @@ void jit_free(JitPlan *J) {
     for (JitSeg &sg : J->segs)
         if (sg.lib) cudaLibraryUnload(sg.lib);
     if (J->dslot_dev) cudaFree(J->dslot_dev);
+    if (J->frows_dev) cudaFree(J->frows_dev);
     delete J;
 }
 
@@ -1223,10 +1270,7 @@ mc_status run_tape_jit(mc_tape *t, const double *theta, uint64_t seed, uint64_t 
         if (r != MC_OK) return r;
     }
     tape_copy_value<<<1, 1, 0, st>>>(t->det, -p.ref[p.objective] - 1, value_out);
-    if (p.n_rows > 0) {
-        const cudaError_t e = cudaMemsetAsync(adj, 0, (size_t)p.n_rows * stride * sizeof(Real), st);
-        if (e != cudaSuccess) return tfail(t, MC_ERR_CUDA, "adjoint reset: %s", cudaGetErrorString(e));
-    }
+    launch_zero_rows<Real>(adj, J.frows_dev, (int)J.far_rows.size(), stride, n_paths, st);
     tape_begin_backward<<<(std::max(p.n_det, p.n_params) + 255) / 256 + 1, 256, 0, st>>>(
         t->ddet, p.n_det, -p.ref[p.objective] - 1, grad_out, p.n_params);
     for (int s = p.n_stages - 1; s >= 0; --s) {
@@ -1280,7 +1324,8 @@ mc_status mc_tape_plan(const mc_tape_node *nodes, int32_t n_nodes, int32_t objec
         // the grid is bounded by one block per 128 paths and by 32 resident blocks on each of 1024 SMs
         const uint64_t blocks = std::min<uint64_t>((max_paths + kBlock - 1) / kBlock, 32u * 1024u);
         const DevLists L = make_lists(nodes, p);
-        *workspace = TapeWs(p, L.all.size(), L.darg_slot.size(), (int)blocks, tape_stride(max_paths), rb).total;
+        *workspace = TapeWs(p, L.all.size(), L.darg_slot.size(), L.far_rows.size(), (int)blocks,
+                            tape_stride(max_paths), rb).total;
     }
     return MC_OK;
 }
@@ -1324,8 +1369,8 @@ mc_status mc_tape_create(int device, const mc_tape_node *nodes, int32_t n_nodes,
     const uint64_t blocks_cap = std::min<uint64_t>((max_paths + kBlock - 1) / kBlock, 32u * 1024u);
     if ((uint64_t)t->grid_f > blocks_cap) t->grid_f = (int)std::max<uint64_t>(blocks_cap, 1);
     if ((uint64_t)t->grid_b > blocks_cap) t->grid_b = (int)std::max<uint64_t>(blocks_cap, 1);
-    TapeWs W(t->plan, t->lists.all.size(), t->lists.darg_slot.size(), (int)std::max<uint64_t>(blocks_cap, 1),
-             t->stride, rb);
+    TapeWs W(t->plan, t->lists.all.size(), t->lists.darg_slot.size(), t->lists.far_rows.size(),
+             (int)std::max<uint64_t>(blocks_cap, 1), t->stride, rb);
     if (workspace) {
         if (workspace_bytes < W.total || ((uintptr_t)workspace & 255u)) {
             fprintf(stderr, "mc_tape_create: workspace needs %zu bytes, 256-byte aligned\n", W.total);
@@ -1344,6 +1389,7 @@ mc_status mc_tape_create(int device, const mc_tape_node *nodes, int32_t n_nodes,
     }
     t->nodes = (DevNode *)(t->ws + W.nodes);
     t->dslot = (int *)(t->ws + W.dslot);
+    t->frows = (int *)(t->ws + W.frows);
     t->det = (double *)(t->ws + W.det);
     t->ddet = (double *)(t->ws + W.ddet);
     t->part = (double *)(t->ws + W.part);
@@ -1352,6 +1398,8 @@ mc_status mc_tape_create(int device, const mc_tape_node *nodes, int32_t n_nodes,
     e = cudaMemcpy(t->nodes, t->lists.all.data(), t->lists.all.size() * sizeof(DevNode), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && !t->lists.darg_slot.empty())
         e = cudaMemcpy(t->dslot, t->lists.darg_slot.data(), t->lists.darg_slot.size() * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !t->lists.far_rows.empty())
+        e = cudaMemcpy(t->frows, t->lists.far_rows.data(), t->lists.far_rows.size() * 4, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         fprintf(stderr, "mc_tape_create: upload: %s\n", cudaGetErrorString(e));
         mc_tape_destroy(t);
@@ -1463,6 +1511,15 @@ mc_status mc_tape_compile(mc_tape *t, int32_t seg_nodes, int32_t recompute, int3
     if (!J->dslot.empty()) {
         cudaError_t e = cudaMalloc((void **)&J->dslot_dev, J->dslot.size() * 4);
         if (e == cudaSuccess) e = cudaMemcpy(J->dslot_dev, J->dslot.data(), J->dslot.size() * 4, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            jit_free(J);
+            return tfail(t, MC_ERR_CUDA, "segment tables: %s", cudaGetErrorString(e));
+        }
+    }
+    if (!J->far_rows.empty()) {
+        cudaError_t e = cudaMalloc((void **)&J->frows_dev, J->far_rows.size() * 4);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(J->frows_dev, J->far_rows.data(), J->far_rows.size() * 4, cudaMemcpyHostToDevice);
         if (e != cudaSuccess) {
             jit_free(J);
             return tfail(t, MC_ERR_CUDA, "segment tables: %s", cudaGetErrorString(e));
