@@ -28,7 +28,9 @@ constexpr int kMaxParams = 256;         // M limit
 // the key advances by the Weyl increments between rounds.
 // The round keys depend only on the seed: they are formed once on the host
 // and travel in the kernel parameters (constant bank), so each round costs
-// four 32-bit multiplies (low and high halves) and two three-input xors.
+// two 32 x 32 -> 64-bit products and two three-input xors.  kWide: each
+// product from one wide multiply, else from a low and a high 32-bit multiply
+// (the same bits; which issues faster depends on the surrounding kernel).
 struct RoundKeys {
     uint32_t k[20];  // (k0, k1) of rounds 0..9
 };
@@ -45,13 +47,25 @@ __host__ __device__ inline RoundKeys philox_round_keys(uint64_t seed) {
     }
     return rk;
 }
+template <bool kWide = true>
 __device__ __forceinline__ uint4 philox4x32_10(uint4 c, const RoundKeys &rk) {
 #pragma unroll
     for (int round = 0; round < 10; ++round) {
-        // the halves of each 32 x 32 -> 64-bit product as two 32-bit multiplies: as fast as
-        // one wide multiply with the keys in the constant bank, faster with them in registers
-        const uint32_t lo0 = c.x * 0xD2511F53u, hi0 = __umulhi(c.x, 0xD2511F53u);
-        const uint32_t lo1 = c.z * 0xCD9E8D57u, hi1 = __umulhi(c.z, 0xCD9E8D57u);
+        uint32_t lo0, hi0, lo1, hi1;
+        if constexpr (kWide) {
+            uint64_t p0, p1;
+            asm("mul.wide.u32 %0, %1, %2;" : "=l"(p0) : "r"(c.x), "r"(0xD2511F53u));
+            asm("mul.wide.u32 %0, %1, %2;" : "=l"(p1) : "r"(c.z), "r"(0xCD9E8D57u));
+            lo0 = (uint32_t)p0;
+            hi0 = (uint32_t)(p0 >> 32);
+            lo1 = (uint32_t)p1;
+            hi1 = (uint32_t)(p1 >> 32);
+        } else {
+            lo0 = c.x * 0xD2511F53u;
+            hi0 = __umulhi(c.x, 0xD2511F53u);
+            lo1 = c.z * 0xCD9E8D57u;
+            hi1 = __umulhi(c.z, 0xCD9E8D57u);
+        }
         c = make_uint4(hi1 ^ c.y ^ rk.k[2 * round], lo1, hi0 ^ c.w ^ rk.k[2 * round + 1], lo0);
     }
     return c;
@@ -124,8 +138,9 @@ struct PathNormals {
         p_lo = (uint32_t)path;
         p_hi = (uint32_t)(path >> 32);
     }
+    template <bool kWide = true>
     __device__ __forceinline__ void fill(uint32_t call, const RoundKeys &rk) {
-        const uint4 o = philox4x32_10(make_uint4(call, 0u, p_lo, p_hi), rk);
+        const uint4 o = philox4x32_10<kWide>(make_uint4(call, 0u, p_lo, p_hi), rk);
         box_muller(o.x, o.y, z0, z1);
         box_muller(o.z, o.w, z2, z3);
     }

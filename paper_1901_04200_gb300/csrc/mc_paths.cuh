@@ -126,6 +126,7 @@ struct GbmModel {
     static constexpr int kind = kGbm;
     static constexpr int DZ = 1, SD = 1;
     static constexpr bool kKeysInRegisters = false;
+    static constexpr bool kPhiloxWide = true;   // Philox by wide multiplies
     struct State { Real x; };
     struct Tape { Real z; };
     struct Shared {
@@ -189,6 +190,7 @@ struct HestonModel {
     static constexpr int kind = kHeston;
     static constexpr int DZ = 2, SD = 2;
     static constexpr bool kKeysInRegisters = false;
+    static constexpr bool kPhiloxWide = true;   // Philox by wide multiplies
     struct State { Real x, v; };
     struct Tape { Real vdt, rs, z1, w; };
     struct Shared {};
@@ -265,6 +267,7 @@ struct LvModel {
     static constexpr int kind = kLv;
     static constexpr int DZ = 1, SD = 1;
     static constexpr bool kKeysInRegisters = true;
+    static constexpr bool kPhiloxWide = false;  // Philox by low and high multiplies: measured faster here
     static constexpr int kMaxNx = 32;
     struct State { Real x; };
     struct Tape { Real u, z; };  // u = (x - x_lo)/hx, z
@@ -438,6 +441,7 @@ struct SlvModel {
     static constexpr int kind = kSlv;
     static constexpr int DZ = 2, SD = 2;
     static constexpr bool kKeysInRegisters = true;
+    static constexpr bool kPhiloxWide = true;   // Philox by wide multiplies
     struct State { Real x, v; };
     struct Tape { Real u, vdt, rs, z1, w; };
     using Shared = typename Lv::Shared;
@@ -643,7 +647,7 @@ struct NormalSource {
             if (Md::kind == kGbm && table) {
                 z[c] = (Real)table[j];
             } else {
-                if ((first && c == 0) || (j & 3u) == 0u) gen.fill(j >> 2, rk);
+                if ((first && c == 0) || (j & 3u) == 0u) gen.template fill<Md::kPhiloxWide>(j >> 2, rk);
                 z[c] = gen.pick(j & 3u);
             }
         }
