@@ -88,8 +88,8 @@ def kernel_bytes(model, storage, K, S, n_groups):
 # the bench command (profiles/); reported only while the kernel sources hash to
 # the profiled version.  Key: (model, storage, K, paths per thread, kernel).
 MEASURED_TRAFFIC = {
-    ("heston", "normals", 8, 2, "forward_sweep"): {"bytes": 103424 + 4770169856, "sources": "e86b786da6f7d42d"},
-    ("heston", "normals", 8, 2, "reverse_sweep"): {"bytes": 4831948800 + 313856, "sources": "e86b786da6f7d42d"},
+    ("heston", "normals", 8, 2, "forward_sweep"): {"bytes": 95232 + 4770265856, "sources": "55e5461dd5bc99fa"},
+    ("heston", "normals", 8, 2, "reverse_sweep"): {"bytes": 4831930880 + 521984, "sources": "55e5461dd5bc99fa"},
 }
 KERNEL_SOURCES = ["mc_common.cuh", "mc_paths.cuh", "mc_paths_heston.cu"]
 
