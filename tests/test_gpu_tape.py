@@ -126,6 +126,32 @@ def test_deterministic_repeat(T):
     assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
 
 
+@pytest.mark.parametrize("mode", ["interpret", "compiled", "compiled_recompute"])
+def test_reused_context_fewer_paths(T, orc, mode):
+    """A context evaluated again with fewer paths, another seed and other parameters gives a
+    fresh context's result and the oracle's: before each backward sweep every adjoint row that
+    accumulates in HBM is cleared for the evaluated paths."""
+    ops, obj = TP.random_program(3)
+    prog, nodes = TP.build_product(ops, T)
+
+    def make():
+        c = T.TapeContext(prog, nodes[obj], 4, max_paths=3000)
+        if mode != "interpret":
+            c.compile(seg_nodes=7, recompute=(mode == "compiled_recompute"))
+        return c
+
+    used = make()
+    used.value_and_grad(np.full(4, 0.7), 0x1234, 3000)
+    theta = np.random.default_rng(7).uniform(0.2, 0.8, 4)
+    G1, g1 = used.value_and_grad(theta, 0x5678, 1234)
+    G2, g2 = make().value_and_grad(theta, 0x5678, 1234)
+    assert G1.item() == G2.item() and np.array_equal(g1.cpu().numpy(), g2.cpu().numpy())
+    Z = orc.normals_fill(0x5678, 0, 1234, 6)
+    G_o, g_o, _ = TP.run_oracle(ops, obj, theta, Z)
+    assert abs(G1.item() - G_o) <= 1e-12 * max(abs(G_o), 1.0)
+    assert rel(g1.cpu().numpy(), g_o) <= 1e-10
+
+
 def test_call_errors(T):
     from paper_1901_04200_gb300 import _lib
     ops, obj = TP.random_program(6)
