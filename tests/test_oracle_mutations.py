@@ -1,0 +1,108 @@
+"""The oracle's pins catch plausible mistakes.
+
+Each case copies the oracle (and the tests) into a temporary directory, plants
+one mistake in the copy's source (the C path code or the numpy MLP), and runs
+the pins that must catch it against the copy: they must fail.  The unmodified
+copy passes the same pins, so the failures come from the planted mistakes.
+Nothing here touches the oracle in the repository.
+"""
+import os
+import shutil
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = "mcaad_oracle.c"
+PINS = "tests/test_oracle_pins.py::"
+MLP_FD = "tests/test_oracle_mlp.py::test_loss_grad_fd[0.7]"
+
+# (mistake, oracle file, text in it, replacement, pins that must fail)
+MUTATIONS = [
+    ("GBM drift term dropped",
+     SRC,
+     "s1[0] = s[0] + (r - 0.5 * vol * vol) * dt + vol * sdt * z[n];",
+     "s1[0] = s[0] + r * dt + vol * sdt * z[n];",
+     [PINS + "test_gbm_matches_black_scholes"]),
+    ("Heston correlation: wrong sign of the independent part",
+     SRC,
+     "double w = rho * z1 + sqrt(1.0 - rho * rho) * z2;\n            s1[0] = x + (r - 0.5 * vp) * dt + sq * z1;",
+     "double w = rho * z1 - sqrt(1.0 - rho * rho) * z2;\n            s1[0] = x + (r - 0.5 * vp) * dt + sq * z1;",
+     [PINS + "test_two_step_equals_full_tape_fries[heston]"]),
+    ("Heston adjoint: kappa term dropped",
+     SRC,
+     "double w = rho * z1 + rhob * z2;\n            g[0] += vb * (th - vp) * dt;",
+     "double w = rho * z1 + rhob * z2;\n            g[0] += 0.0;",
+     [PINS + "test_two_step_equals_full_tape_fries[heston]"]),
+    ("local vol adjoint: d sigma / dx term dropped",
+     SRC,
+     "xb = xb + sb * e.dsdx;",
+     "xb = xb;",
+     [PINS + "test_two_step_equals_full_tape_fries[lv]"]),
+    ("local vol: wrong bilinear node weight",
+     SRC,
+     "e.wgt[1] = (1.0 - a) * b;",
+     "e.wgt[1] = a * b;",
+     [PINS + "test_two_step_equals_full_tape_fries[lv]"]),
+    ("Philox: wrong key increment",
+     SRC,
+     "k0 += 0x9E3779B9u;",
+     "k0 += 0x9E3779B7u;",
+     ["tests/test_oracle_philox.py::test_philox_matches_curand_host"]),
+    ("payoff discount dropped",
+     SRC,
+     "y[i] = disc * (S > pb->K[i] ? S - pb->K[i] : 0.0);",
+     "y[i] = (S > pb->K[i] ? S - pb->K[i] : 0.0);",
+     [PINS + "test_gbm_matches_black_scholes"]),
+    ("MLP double backward: silu'' term dropped",
+     "mlp.py",
+     "zbar_t[l] = pbar * g[l] * d2silu(z[l])",
+     "zbar_t[l] = 0.0 * pbar",
+     [MLP_FD]),
+    ("MLP double backward: w5 tangent term dropped",
+     "mlp.py",
+     'grads["w5"] += gbar.sum(axis=0)\n',
+     "\n",
+     [MLP_FD]),
+    ("MLP double backward: tangent weight gradient dropped",
+     "mlp.py",
+     'grads["W%d" % l] += _mm(pl[l].T, gbar, bf16)\n',
+     "\n",
+     [MLP_FD]),
+]
+
+
+def _copy(dst):
+    """Oracle and tests copied (the copy builds its own library), the package linked."""
+    skip = shutil.ignore_patterns("*.so", "*.tmp", "__pycache__", ".pytest_cache")
+    shutil.copytree(os.path.join(ROOT, "oracle"), os.path.join(dst, "oracle"), ignore=skip)
+    shutil.copytree(os.path.join(ROOT, "tests"), os.path.join(dst, "tests"), ignore=skip)
+    os.symlink(os.path.join(ROOT, "paper_1901_04200_gb300"), os.path.join(dst, "paper_1901_04200_gb300"))
+
+
+def _run_pins(cwd, nodes):
+    env = dict(os.environ, PYTHONDONTWRITEBYTECODE="1")
+    cmd = [sys.executable, "-m", "pytest", "-q", "-p", "no:cacheprovider", "-m", "not gpu"] + nodes
+    return subprocess.run(cmd, cwd=cwd, env=env, capture_output=True, text=True, timeout=600)
+
+
+def test_unmodified_copy_passes_the_pins(tmp_path):
+    _copy(str(tmp_path))
+    nodes = sorted({n for m in MUTATIONS for n in m[4]})
+    res = _run_pins(str(tmp_path), nodes)
+    assert res.returncode == 0, res.stdout[-2000:] + res.stderr[-2000:]
+
+
+@pytest.mark.parametrize("mistake,fname,old,new,nodes", MUTATIONS, ids=[m[0] for m in MUTATIONS])
+def test_planted_mistake_fails_a_pin(tmp_path, mistake, fname, old, new, nodes):
+    _copy(str(tmp_path))
+    path = os.path.join(str(tmp_path), "oracle", fname)
+    with open(path) as f:
+        src = f.read()
+    assert src.count(old) == 1, "the oracle's source changed: update this mutation (%s)" % mistake
+    with open(path, "w") as f:
+        f.write(src.replace(old, new))
+    res = _run_pins(str(tmp_path), nodes)
+    # pytest exits 1 when tests ran and some failed
+    assert res.returncode == 1 and " failed" in res.stdout, (mistake, res.stdout[-2000:] + res.stderr[-2000:])
