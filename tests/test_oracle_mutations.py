@@ -1,10 +1,10 @@
 """The oracle's pins catch plausible mistakes.
 
 Each case copies the oracle (and the tests) into a temporary directory, plants
-one mistake in the copy's source (the C path code or the numpy MLP), and runs
-the pins that must catch it against the copy: they must fail.  The unmodified
-copy passes the same pins, so the failures come from the planted mistakes.
-Nothing here touches the oracle in the repository.
+one mistake in the copy's source (the C path code, the numpy MLP or the
+whole-program tape), and runs the pins that must catch it against the copy:
+they must fail.  The unmodified copy passes the same pins, so the failures come
+from the planted mistakes.  Nothing here touches the oracle in the repository.
 """
 import os
 import shutil
@@ -70,6 +70,16 @@ MUTATIONS = [
      'grads["W%d" % l] += _mm(pl[l].T, gbar, bf16)\n',
      "\n",
      [MLP_FD]),
+    ("tape oracle: expectation adjoint not averaged over the paths",
+     "tape.py",
+     "D[j] = D[j] + np.mean(D[m])",
+     "D[j] = D[j] + D[m]",
+     ["tests/test_tape_host.py::test_oracle_tape_product_of_expectations"]),
+    ("tape oracle: product partials swapped",
+     "tape.py",
+     "[(self.idx, o.v), (o.idx, self.v)]",
+     "[(self.idx, self.v), (o.idx, o.v)]",
+     [PINS + "test_two_step_equals_full_tape_fries[heston]"]),
 ]
 
 

@@ -97,6 +97,23 @@ def test_oracle_tape_log_by_finite_differences():
     assert math.isclose(g, np.mean(1.0 / (0.8 + z * z)), rel_tol=1e-14)
 
 
+def test_oracle_tape_product_of_expectations():
+    """G = E[Y E[X]] with X = theta a, Y = theta b: G = theta^2 mean(a) mean(b), so dG/dtheta =
+    2 theta mean(a) mean(b).  The adjoint reaching E[X] differs from path to path (Y), so the
+    expectation's rule must take its mean over the paths."""
+    from oracle import tape as T
+    rng = np.random.default_rng(11)
+    a, b = rng.standard_normal(301), rng.uniform(0.5, 1.5, 301)
+    tp = T.Tape(len(a))
+    th = tp.input(0.7)
+    ex = T.expectation(th * tp.const(a))
+    out = T.expectation((th * tp.const(b)) * ex)
+    D = tp.backward(out)
+    g = np.mean(D[th.idx])
+    assert math.isclose(out.v[0], 0.7 * 0.7 * np.mean(a) * np.mean(b), rel_tol=1e-12)
+    assert math.isclose(g, 2 * 0.7 * np.mean(a) * np.mean(b), rel_tol=1e-12)
+
+
 def test_stage_limits():
     """More than 2048 expectations in one stage is refused as unsupported, 2048 is accepted."""
     for n, want in [(2048, _lib.MC_OK), (2049, _lib.MC_ERR_UNSUPPORTED)]:
