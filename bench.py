@@ -110,27 +110,43 @@ def measured_traffic(model, storage, k, ppt, kernel):
     return None
 
 
+# Per-SM thread-operation rates per clock of the pipes the path kernels use (the CUDA
+# throughput table for compute capability 10.x): FP32 add/multiply/FMA 128, 32-bit integer and
+# logical operations 64, special functions (lg2, sqrt, rsqrt, sin, cos) 16; instruction issue
+# (four warp instructions) 128.
+PIPE_RATES = {"issue": 128, "fp32": 128, "int": 64, "mufu": 16}
+
+
 def kernel_rooflines(model, storage, K, ppt, P, S, n_groups, prof, issue_peak, hbm_peak, peak_src, n_sm,
                      sm_mhz_peak):
     """Per path kernel: achieved algorithmic ops and bytes per second (CUDA-event durations from
-    the context's profile) against the issue-rate and HBM peaks; the roofline entry of the JSON
-    line for the kernel with the longest time, with the bound of the larger fraction."""
+    the context's profile) against the issue-rate and HBM peaks, and each ALU pipe's fraction of
+    its own rate (the per-pipe roofline: the pipe with the largest fraction binds); the roofline
+    entry of the JSON line for the kernel with the longest time, with the bound of the larger of
+    its issue and HBM fractions."""
     if storage == "tangent":
-        table = {"tangent_sweep": (sum(OPS[model]["F"].values()) + sum(OPS_TANGENT[model].values()),
-                                   OPS[model]["F"]["fp32"] + OPS_TANGENT[model]["fp32"], 0.0)}
+        f = OPS[model]["F"]
+        table = {"tangent_sweep": ({"fp32": f["fp32"] + OPS_TANGENT[model]["fp32"], "int": f["int"],
+                                    "mufu": f["mufu"]}, 0.0)}
     else:
         by = kernel_bytes(model, storage, K, S, n_groups)
-        table = {k: (kernel_ops(model, storage, k), kernel_ops(model, storage, k, "fp32"), by[k])
+        table = {k: ({kind: kernel_ops(model, storage, k, kind) for kind in ("fp32", "int", "mufu")}, by[k])
                  for k in ("forward_sweep", "reverse_sweep")}
+    clock = n_sm * sm_mhz_peak * 1e6
     kern = {}
-    for kname, (ops, ops32, byts) in table.items():
+    for kname, (by_kind, byts) in table.items():
+        ops = sum(by_kind.values())
         ms, n = prof[kname]
         t = ms / max(n, 1) * 1e-3
         a_ops, a_bytes = P * S * ops / t, P * S * byts / t
+        pipes = {"issue": a_ops / (PIPE_RATES["issue"] * clock)}
+        pipes.update({kind: P * S * v / t / (PIPE_RATES[kind] * clock) for kind, v in by_kind.items()})
         kern[kname] = {"ms": t * 1e3, "ops_per_path_step": ops, "bytes_per_path_step": byts,
                        "alu_frac": a_ops / issue_peak, "hbm_frac": a_bytes / hbm_peak,
                        "alu_tops": a_ops / 1e12, "hbm_gbs": a_bytes / 1e9,
-                       "fp32_frac": P * S * ops32 / t / issue_peak}
+                       "fp32_frac": P * S * by_kind["fp32"] / t / issue_peak,
+                       "ops_by_pipe": by_kind, "pipe_fracs": pipes,
+                       "alu_pipe_bound": max(pipes, key=pipes.get)}
     dom = max(kern, key=lambda k: kern[k]["ms"])
     d = kern[dom]
     hbm_bound = d["hbm_frac"] > d["alu_frac"]

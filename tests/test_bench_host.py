@@ -1,0 +1,65 @@
+"""Host-side arithmetic of bench.py's roofline entries (no GPU)."""
+import math
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+N_SM, MHZ = 152, 2070.0
+ISSUE = 128 * N_SM * MHZ * 1e6
+HBM = 6800.3e9
+
+
+def test_algorithmic_bytes_per_path_step():
+    """Stored normals: two normals and a checkpoint of two words every K steps, 4 B each."""
+    assert bench.kernel_bytes("heston", "normals", 8, 512, 8)["forward_sweep"] == 4.0 * 2 / 8 + 8.0
+    assert bench.kernel_bytes("heston", "checkpoint", 8, 512, 8)["reverse_sweep"] == 1.0
+    assert bench.kernel_bytes("lv", "normals", 5, 500, 20)["forward_sweep"] == 4.0 / 5 + 4.0
+    # full tape: four Heston fields per step and x at each of 8 maturity steps out of 512
+    assert bench.kernel_bytes("heston", "full", 8, 512, 8)["forward_sweep"] == 16.0 + 4.0 * 8 / 512
+
+
+@pytest.mark.parametrize("storage", ["normals", "checkpoint"])
+def test_pipe_fractions(storage):
+    P, S = 1 << 20, 512
+    prof = {"forward_sweep": (11.3, 10), "reverse_sweep": (7.7, 10)}
+    r = bench.kernel_rooflines("heston", storage, 8, 2, P, S, 8, prof, ISSUE, HBM, "measured", N_SM, MHZ)
+    for name, k in r["kernels"].items():
+        t = k["ms"] * 1e-3
+        by = k["ops_by_pipe"]
+        assert sum(by.values()) == k["ops_per_path_step"] == bench.kernel_ops("heston", storage, name)
+        assert math.isclose(k["pipe_fracs"]["issue"], k["alu_frac"], rel_tol=1e-12)
+        for kind, v in by.items():
+            want = P * S * v / t / (bench.PIPE_RATES[kind] * N_SM * MHZ * 1e6)
+            assert math.isclose(k["pipe_fracs"][kind], want, rel_tol=1e-12)
+        assert k["alu_pipe_bound"] == max(k["pipe_fracs"], key=k["pipe_fracs"].get)
+    dom = r["kernels"]["forward_sweep"]  # the longer kernel
+    assert r["frac"] == max(dom["alu_frac"], dom["hbm_frac"])
+    assert r["bound"] == ("hbm" if dom["hbm_frac"] > dom["alu_frac"] else "alu")
+
+
+def test_tangent_sweep_counts_f_and_the_tangents():
+    prof = {"tangent_sweep": (19.1, 10)}
+    r = bench.kernel_rooflines("heston", "tangent", 8, 1, 1 << 20, 512, 8, prof, ISSUE, HBM, "measured",
+                               N_SM, MHZ)
+    k = r["kernels"]["tangent_sweep"]
+    assert k["ops_per_path_step"] == sum(bench.OPS["heston"]["F"].values()) + bench.OPS_TANGENT["heston"]["fp32"]
+    assert r["bound"] == "alu" and k["bytes_per_path_step"] == 0.0
+
+
+def test_measured_traffic_only_for_the_profiled_sources(monkeypatch):
+    """The stored DRAM bytes are reported while the kernel sources hash to the captured version,
+    and null once they differ."""
+    key = ("heston", "normals", 8, 2, "forward_sweep")
+    rec = bench.MEASURED_TRAFFIC[key]
+    monkeypatch.setattr(bench, "kernel_sources_hash", lambda: rec["sources"])
+    assert bench.measured_traffic(*key) == rec["bytes"]
+    assert bench.measured_traffic("heston", "normals", 4, 2, "forward_sweep") is None
+    monkeypatch.setattr(bench, "kernel_sources_hash", lambda: "another version")
+    assert bench.measured_traffic(*key) is None
