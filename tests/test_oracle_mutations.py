@@ -55,6 +55,21 @@ MUTATIONS = [
      "y[i] = disc * (S > pb->K[i] ? S - pb->K[i] : 0.0);",
      "y[i] = (S > pb->K[i] ? S - pb->K[i] : 0.0);",
      [PINS + "test_gbm_matches_black_scholes"]),
+    ("Heston adjoint: xi term of the variance adjoint dropped",
+     SRC,
+     "if (vp > 0.0) vpb += (xb * z1 + vb * xi * w) * dt / (2.0 * sq);",
+     "if (vp > 0.0) vpb += (xb * z1) * dt / (2.0 * sq);",
+     [PINS + "test_two_step_equals_full_tape_fries[heston]"]),
+    ("SLV adjoint: leverage drift term dropped",
+     SRC,
+     "double levb = xb * (-lev * vp * dt + sq * z1);",
+     "double levb = xb * (sq * z1);",
+     [PINS + "test_slv_two_step_equals_full_tape"]),
+    ("Box-Muller: cosine and sine swapped",
+     SRC,
+     "return (j & 1) ? rad * sin(ORC_TWO_PI * ub) : rad * cos(ORC_TWO_PI * ub);",
+     "return (j & 1) ? rad * cos(ORC_TWO_PI * ub) : rad * sin(ORC_TWO_PI * ub);",
+     ["tests/test_oracle_philox.py::test_box_muller_structure"]),
     ("MLP double backward: silu'' term dropped",
      "mlp.py",
      "zbar_t[l] = pbar * g[l] * d2silu(z[l])",
