@@ -101,6 +101,9 @@ typedef enum {
  *                x += (r - v+/2) dt + sqrt(v+ dt) z1;
  *                v += kappa (theta_h - v+) dt + xi sqrt(v+ dt) (rho z1 + sqrt(1-rho^2) z2),
  *                z1, z2 = normals 2n, 2n+1; v starts at v0.             M = 5
+ *                The gradient needs |rho| < 1: d sqrt(1-rho^2)/d rho is unbounded
+ *                at |rho| = 1, where the rho component is not finite (theta
+ *                lives on the device and is not checked on the host).
  *   LV_BILINEAR: theta[j*nx + c] = sigma at t_j = j t_max/(nt-1),
  *                x_c = x_lo + c (x_hi-x_lo)/(nx-1); sigma(t_n, x_n) bilinear
  *                with flat extrapolation;
