@@ -220,6 +220,10 @@ def test_call_argument_errors(L):
     with pytest.raises(L.McError) as e:
         ctx.forward(w.theta, 1, 65)
     assert e.value.status == L.MC_ERR_INVALID_ARG
+    for call in (lambda: ctx.forward(w.theta, 1, 0), lambda: ctx.value_and_grad(w.theta, w.C, 1, 0)):
+        with pytest.raises(L.McError) as e:  # no paths: an empty estimator
+            call()
+        assert e.value.status == L.MC_ERR_INVALID_ARG
 
 
 @pytest.mark.parametrize("split,tol", [(6016, 1e-13), (6000, 1e-7)])
