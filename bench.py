@@ -211,7 +211,7 @@ class ClockSampler:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
                                           "--format=csv,noheader,nounits", "-lms", "200"],
                                          stdout=self.fh, stderr=subprocess.DEVNULL)
-        except Exception:
+        except OSError:  # no nvidia-smi: the line reports no clock samples
             self.proc = None
 
     def stop(self):
@@ -221,8 +221,9 @@ class ClockSampler:
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
-        except Exception:
+        except subprocess.TimeoutExpired:
             self.proc.kill()
+            self.proc.wait()
         self.fh.close()
         rows = []
         with open(self.path) as f:
