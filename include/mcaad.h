@@ -163,7 +163,9 @@ mc_status mc_workspace_size(const mc_model *model, const mc_instruments *inst,
  * The model's `normals` table pointer, if any, must stay valid for the
  * context's life.  Synchronous.  Errors: MC_ERR_INVALID_ARG (bad model,
  * maturities not multiples of ckpt_every, workspace too small or misaligned),
- * MC_ERR_OOM, MC_ERR_CUDA. */
+ * MC_ERR_OOM, MC_ERR_CUDA.  Tuning: the environment variables
+ * MCAAD_MAX_BLOCKS_FWD / MCAAD_MAX_BLOCKS_REV (positive integers), read here,
+ * cap the resident blocks per SM of the forward / reverse path kernels. */
 mc_status mc_context_create(int device, const mc_model *model, const mc_instruments *inst,
                             uint64_t max_paths, void *workspace, size_t workspace_bytes,
                             mc_ctx **out);

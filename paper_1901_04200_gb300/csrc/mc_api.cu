@@ -324,32 +324,17 @@ mc_status resolve_storage(Plan &p, uint64_t max_paths, int device, std::string &
 bool kernels_for(const Plan &p, KernelPair *kp) { return kernels_raw(p.kind, p.precision, p.K, p.ppt, kp); }
 
 // Launch shape: blocks of kBlock threads, at most (resident blocks per SM) x
-// (SMs) of them; each warp loops over 32-path chunks.
-// Resident blocks per SM above which a path kernel measured slower (large
-// unrolled bodies: more resident warps spread over more of the code); 0 = no
-// cap.  MCAAD_MAX_BLOCKS_FWD / MCAAD_MAX_BLOCKS_REV override it for tuning.
-struct BlockCap {
-    int kind, precision, K, ppt, fwd, rev;
-};
-const BlockCap kBlockCaps[] = {
-    {kLv, MC_FP32, 25, 1, 0, 0},
-    {kSlv, MC_FP32, 8, 1, 0, 0},
-};
-
+// (SMs) of them; each warp loops over 32-path chunks.  The environment
+// variables MCAAD_MAX_BLOCKS_FWD / MCAAD_MAX_BLOCKS_REV (positive integers) cap
+// the resident blocks per SM of the forward / reverse path kernels, for tuning.
 int env_int(const char *name) {
     const char *v = getenv(name);
     return v ? atoi(v) : 0;
 }
 
-void block_caps(const Plan &p, int *fwd, int *rev) {
-    *fwd = *rev = 0;
-    for (const BlockCap &c : kBlockCaps)
-        if (c.kind == p.kind && c.precision == p.precision && c.K == p.K && c.ppt == p.ppt) {
-            *fwd = c.fwd;
-            *rev = c.rev;
-        }
-    if (env_int("MCAAD_MAX_BLOCKS_FWD") > 0) *fwd = env_int("MCAAD_MAX_BLOCKS_FWD");
-    if (env_int("MCAAD_MAX_BLOCKS_REV") > 0) *rev = env_int("MCAAD_MAX_BLOCKS_REV");
+void block_caps(int *fwd, int *rev) {
+    *fwd = env_int("MCAAD_MAX_BLOCKS_FWD") > 0 ? env_int("MCAAD_MAX_BLOCKS_FWD") : 0;
+    *rev = env_int("MCAAD_MAX_BLOCKS_REV") > 0 ? env_int("MCAAD_MAX_BLOCKS_REV") : 0;
 }
 
 mc_status launch_shape(const Plan &p, int device, const KernelPair &kp, int nx, int *n_sm, Launch &ln,
@@ -379,7 +364,7 @@ mc_status launch_shape(const Plan &p, int device, const KernelPair &kp, int nx, 
     const size_t sm[3] = {ln.smem_fwd, ln.smem_fwd, ln.smem_rev};
     int *grids[3] = {&ln.grid_fwd, &ln.grid_fwd_keep, &ln.grid_rev};
     int cap_fwd, cap_rev;
-    block_caps(p, &cap_fwd, &cap_rev);
+    block_caps(&cap_fwd, &cap_rev);
     const int caps[3] = {cap_fwd, cap_fwd, cap_rev};
     for (int q = 0; q < 3; ++q) {
         e = cudaFuncSetAttribute(fns[q], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm[q]);
