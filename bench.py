@@ -550,7 +550,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--paths", type=int, default=1 << 20)
-    ap.add_argument("--cpu-paths", type=int, default=1 << 16)
+    ap.add_argument("--cpu-paths", type=int, default=1 << 17)
     ap.add_argument("--ref-paths", type=int, default=1 << 15, help="--impl reference: largest sample per step")
     ap.add_argument("--ref-seconds", type=float, default=90.0,
                     help="--impl reference: host time the whole run is sized for")
