@@ -10,7 +10,7 @@
  * What it computes, in the paper's order:
  *   forward algorithm F (paper, definition of F: M parameters plus N random
  *     variables -> m payoffs of one path) for three SDE discretisations
- *     (paper, Heston SLV model paragraph: "standard Euler discretization"):
+ *     (paper, Heston SLV model paragraph: an Euler scheme):
  *       GBM with piecewise-constant volatility (log-Euler),
  *       Heston with full-truncation Euler,
  *       local volatility on a bilinear node surface (log-Euler),
@@ -18,8 +18,8 @@
  *       Heston variance process times a leverage surface L(t, S) on fixed
  *       nodes, interpolated bilinearly; full-truncation Euler);
  *     every state of a path is stored (no checkpointing);
- *   Monte Carlo mean E y_i = (1/P) sum_p y_i(omega_p) (paper, "Some remarks
- *     on the Monte-Carlo simulations");
+ *   Monte Carlo mean E y_i = (1/P) sum_p y_i(omega_p) (paper, Monte-Carlo
+ *     remarks);
  *   lambda_i = E y_i - C_i and G (eq. 241118A; two-step algorithm, step 2);
  *   per path, the reverse algorithm R seeded with lambda (eq. 0711A), written
  *     by hand backwards over the stored states, and the sum over paths

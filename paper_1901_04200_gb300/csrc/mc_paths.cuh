@@ -12,8 +12,8 @@
 // Forward kernel (step 1, eq. 1211A): per segment, optionally store the state
 // (checkpoint) and, in the stored-normals variant, the segment's normals into
 // the warp chunk's tile (SegTile below: rows of 32 consecutive paths), run K
-// Euler steps with Philox normals, and at a maturity sum the undiscounted call
-// payoffs of the
+// Euler steps with Philox normals (segments visited in groups that fill whole
+// Philox blocks), and at a maturity sum the undiscounted call payoffs of the
 // warp's 32 paths (FP32 warp sum) into per-warp FP64 accumulators.  Block
 // end: the warps' sums in warp order -> part_y[block][i].
 //
@@ -910,10 +910,10 @@ __global__ void __launch_bounds__(kBlock) path_reverse_kernel(const DevProblem p
 
 // ---------------------------------------------------- full-storage variant --
 // The paper's branch for unconstrained memory (two-step algorithm, step 2:
-// "the cost is K_R Cost(F)" when the first step's results are stored): the
-// forward sweep writes every step's tape (the model's Tape fields, SoA
-// [step][field][path], coalesced) and x at each maturity; the reverse sweep
-// streams them back and runs only the adjoint.
+// with the first step's intermediate values kept, the reverse sweep costs
+// K_R Cost(F) alone): the forward sweep writes every step's tape (the model's
+// Tape fields, SoA [step][field][path], coalesced) and x at each maturity; the
+// reverse sweep streams them back and runs only the adjoint.
 
 template <class Md, int K, int PPT>
 __global__ void __launch_bounds__(kBlock) path_forward_store_kernel(const DevProblem pb, const DevCall cl) {
