@@ -45,6 +45,16 @@ MUTATIONS = [
      "e.wgt[1] = (1.0 - a) * b;",
      "e.wgt[1] = a * b;",
      [PINS + "test_two_step_equals_full_tape_fries[lv]"]),
+    ("local vol: sigma at the step's end instead of its start",
+     SRC,
+     "double ut = ((double)n * pb->dt) / ht;",
+     "double ut = ((double)(n + 1) * pb->dt) / ht;",
+     [PINS + "test_two_step_equals_full_tape_fries[lv]"]),
+    ("GBM: a bucket's end step counted in the bucket",
+     SRC,
+     "while (n >= pb->bucket_end[b]) ++b;",
+     "while (n > pb->bucket_end[b]) ++b;",
+     [PINS + "test_two_step_equals_full_tape_fries[gbm]"]),
     ("Philox: wrong key increment",
      SRC,
      "k0 += 0x9E3779B9u;",
