@@ -281,7 +281,9 @@ mc_status mlp_adam_step(mlp_ctx *ctx, float *params, const float *grads, float *
 /* Host copy of the tensor-core wait-expiry flag (0 = every wait completed). Synchronous. */
 mc_status mlp_error_flag(mlp_ctx *ctx, int32_t *flag_host);
 
-/* Test hooks for the generator.  mc_philox_fill: out uint32
+/* Test hooks for the generator of F's N random inputs (definition of F; the
+ * paper names no generator: Philox-4x32-10 and Box-Muller as described at the
+ * top of this file).  mc_philox_fill: out uint32
  * [n_paths][n_calls][4], block (call c, path path0+i).  mc_normals_fill:
  * out [n_paths][n_per_path] of normals 0.. of each path, FP64 when
  * precision == MC_FP64 (double*), else FP32 (float*), computed exactly as the

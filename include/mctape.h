@@ -83,7 +83,8 @@ typedef struct {
     double c;     /* PARAM: parameter index; CONST, ADDC, MULC: the constant; NORMAL: normal index */
 } mc_tape_node;
 
-/* Plan facts of a program, computed on the host (no GPU needed): checks the
+/* Plan facts of a program, computed on the host (no GPU needed; the stages are
+ * cut where an expectation's value is first used, Appendix): checks the
  * program (MC_ERR_INVALID_ARG for an argument index out of range or not
  * preceding its node, an unknown op, a parameter index outside [0,
  * n_params), a negative normal index, an objective that is not
@@ -117,7 +118,9 @@ void mc_tape_destroy(mc_tape *t);
 const char *mc_tape_last_error(const mc_tape *t);
 
 /* The objective and its gradient over global paths [path0, path0 + n_paths)
- * of `seed`.  theta: FP64 device [n_params]; value_out: FP64 device [1];
+ * of `seed`: the forward stages, then the backward sweep by the Appendix's
+ * rule (expected backward AD after Fries), as described at the top of this
+ * file.  theta: FP64 device [n_params]; value_out: FP64 device [1];
  * grad_out: FP64 device [n_params].  Stream-ordered on `stream`. */
 mc_status mc_tape_value_and_grad(mc_tape *t, const double *theta, uint64_t seed, uint64_t path0,
                                  uint64_t n_paths, double *value_out, double *grad_out, void *stream);
