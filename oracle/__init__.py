@@ -86,6 +86,7 @@ def _lib_handle():
             lib.orc_forward.argtypes = [P(_Problem), P(d), u64, u64, i, P(d)]
             lib.orc_vjp.argtypes = [P(_Problem), P(d), P(d), u64, u64, i, P(d)]
             lib.orc_value_and_grad.argtypes = [P(_Problem), P(d), P(d), u64, u64, i, P(d), P(d), P(d)]
+            lib.orc_states_at.argtypes = [P(_Problem), P(d), u64, u64, i, i, P(d)]
             _lib = lib
     return _lib
 
@@ -252,3 +253,14 @@ def value_and_grad(pb, theta, C, n_paths, path0=0, n_threads=None):
                               _dptr(Ey), ctypes.byref(G), _dptr(grad)):
         raise ValueError("oracle: invalid problem")
     return Ey, G.value, grad
+
+
+def states_at(pb, theta, step, n_paths, path0=0, n_threads=None):
+    """State after `step` steps of each path: [n_paths, state_dim] (x, and v for Heston/SLV)."""
+    lib = _lib_handle()
+    b = _Bound(pb)
+    th = np.ascontiguousarray(theta, dtype=np.float64)
+    out = np.zeros((n_paths, lib.orc_state_dim(b.ref)))
+    if lib.orc_states_at(b.ref, _dptr(th), path0, n_paths, int(step), _threads(n_threads), _dptr(out)):
+        raise ValueError("oracle: invalid problem")
+    return out

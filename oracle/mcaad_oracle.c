@@ -481,3 +481,62 @@ int orc_value_and_grad(const orc_problem *pb, const double *theta, const double 
     free(lambda);
     return rc;
 }
+
+/* State after `step` steps of each path in [path0, path0+n_paths): out is
+ * [n_paths][state_dim] (x = ln(S/S0), and v for the variance models).  Plain
+ * read-out of F's stored states, for pins of the one-step dynamics. */
+typedef struct {
+    const orc_problem *pb;
+    const double *theta;
+    uint64_t path0, n_paths;
+    int step;
+    double *out;
+    uint64_t next;
+    pthread_mutex_t lock;
+} states_job;
+
+static void *states_worker(void *arg)
+{
+    states_job *jb = (states_job *)arg;
+    const orc_problem *pb = jb->pb;
+    int nl = orc_last_step(pb);
+    int sd = orc_state_dim(pb), dz = orc_normals_per_step(pb);
+    double *states = (double *)malloc(sizeof(double) * (size_t)(nl + 1) * sd);
+    double *z = (double *)malloc(sizeof(double) * (size_t)(nl > 0 ? nl : 1) * dz);
+    double *y = (double *)malloc(sizeof(double) * (size_t)pb->m);
+    for (;;) {
+        pthread_mutex_lock(&jb->lock);
+        uint64_t ch = jb->next++;
+        pthread_mutex_unlock(&jb->lock);
+        uint64_t a = ch * ORC_CHUNK;
+        if (a >= jb->n_paths) break;
+        uint64_t b = a + ORC_CHUNK;
+        if (b > jb->n_paths) b = jb->n_paths;
+        for (uint64_t q = a; q < b; ++q) {
+            orc_path_forward(pb, jb->theta, jb->path0 + q, states, z, y);
+            for (int c = 0; c < sd; ++c)
+                jb->out[q * (uint64_t)sd + c] = states[(size_t)jb->step * sd + c];
+        }
+    }
+    free(states); free(z); free(y);
+    return NULL;
+}
+
+int orc_states_at(const orc_problem *pb, const double *theta, uint64_t path0, uint64_t n_paths,
+                  int step, int n_threads, double *out)
+{
+    if (orc_check(pb, theta) || n_paths == 0) return ORC_ERR;
+    if (step < 0 || step > orc_last_step(pb)) return ORC_ERR;
+    states_job jb;
+    memset(&jb, 0, sizeof(jb));
+    jb.pb = pb; jb.theta = theta; jb.path0 = path0; jb.n_paths = n_paths;
+    jb.step = step; jb.out = out;
+    pthread_mutex_init(&jb.lock, NULL);
+    if (n_threads < 1) n_threads = 1;
+    pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * (size_t)n_threads);
+    for (int t = 0; t < n_threads; ++t) pthread_create(&th[t], NULL, states_worker, &jb);
+    for (int t = 0; t < n_threads; ++t) pthread_join(th[t], NULL);
+    free(th);
+    pthread_mutex_destroy(&jb.lock);
+    return ORC_OK;
+}

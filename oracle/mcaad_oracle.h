@@ -68,6 +68,8 @@ int orc_vjp(const orc_problem *pb, const double *theta, const double *ybar, uint
 int orc_value_and_grad(const orc_problem *pb, const double *theta, const double *C,
                        uint64_t path0, uint64_t n_paths, int n_threads,
                        double *Ey, double *G, double *grad);
+int orc_states_at(const orc_problem *pb, const double *theta, uint64_t path0, uint64_t n_paths,
+                  int step, int n_threads, double *out);
 
 #ifdef __cplusplus
 }

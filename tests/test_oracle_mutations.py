@@ -108,12 +108,51 @@ MUTATIONS = [
 ]
 
 
+TAPE = "tape.py"
+MOMENTS = PINS + "test_one_step_conditional_moments"
+CF = PINS + "test_heston_matches_characteristic_function_price"
+CONSISTENCY = [PINS + "test_two_step_equals_full_tape_fries[heston]", PINS + "test_slv_two_step_equals_full_tape",
+               PINS + "test_fd_common_random_numbers[heston]"]
+
+# Mistakes in the model itself, made the same way in the C forward sweep, the C adjoint and the
+# whole-program tape: the pins that compare the oracle with itself (two-step against the tape,
+# finite differences) still pass, so only the pins of the dynamics against the mathematics can
+# catch them.  (mistake, [(file, text, replacement, occurrences)], pins that must fail)
+CONSISTENT_MUTATIONS = [
+    ("Heston and SLV: rho and sqrt(1 - rho^2) swapped",
+     [(SRC, "double w = rho * z1 + sqrt(1.0 - rho * rho) * z2;",
+       "double w = sqrt(1.0 - rho * rho) * z1 + rho * z2;", 2),
+      (SRC, "double w = rho * z1 + rhob * z2;", "double w = rhob * z1 + rho * z2;", 2),
+      (SRC, "g[3] += vb * xi * sq * (z1 - rho / rhob * z2);",
+       "g[3] += vb * xi * sq * (-rho / rhob * z1 + z2);", 2),
+      (TAPE, "w = rho * z1 + rhob * z2", "w = rhob * z1 + rho * z2", 2)],
+     [MOMENTS, CF]),
+    ("Heston and SLV: xi v+ dt in place of xi sqrt(v+ dt)",
+     [(SRC, "s1[1] = v + kappa * (th - vp) * dt + xi * sq * w;",
+       "s1[1] = v + kappa * (th - vp) * dt + xi * vp * dt * w;", 2),
+      (SRC, "g[2] += vb * sq * w;", "g[2] += vb * vp * dt * w;", 2),
+      (SRC, "g[3] += vb * xi * sq * (z1 - rho / rhob * z2);",
+       "g[3] += vb * xi * vp * dt * (z1 - rho / rhob * z2);", 2),
+      (SRC, "double vpb = xb * (-0.5 * dt) + vb * (-kappa * dt);",
+       "double vpb = xb * (-0.5 * dt) + vb * (-kappa * dt) + vb * xi * w * dt;", 1),
+      (SRC, "if (vp > 0.0) vpb += (xb * z1 + vb * xi * w) * dt / (2.0 * sq);",
+       "if (vp > 0.0) vpb += (xb * z1) * dt / (2.0 * sq);", 1),
+      (SRC, "double vpb = xb * (-0.5 * lev * lev * dt) + vb * (-kappa * dt);",
+       "double vpb = xb * (-0.5 * lev * lev * dt) + vb * (-kappa * dt) + vb * xi * w * dt;", 1),
+      (SRC, "if (vp > 0.0) vpb += (xb * lev * z1 + vb * xi * w) * dt / (2.0 * sq);",
+       "if (vp > 0.0) vpb += (xb * lev * z1) * dt / (2.0 * sq);", 1),
+      (TAPE, "v = v + kappa * (thh - vp) * dt + xi * sq * w", "v = v + kappa * (thh - vp) * dt + xi * vp * dt * w", 2)],
+     [MOMENTS, CF]),
+]
+
+
 def _copy(dst):
     """Oracle and tests copied (the copy builds its own library), the package linked."""
     skip = shutil.ignore_patterns("*.so", "*.tmp", "__pycache__", ".pytest_cache")
     shutil.copytree(os.path.join(ROOT, "oracle"), os.path.join(dst, "oracle"), ignore=skip)
     shutil.copytree(os.path.join(ROOT, "tests"), os.path.join(dst, "tests"), ignore=skip)
     os.symlink(os.path.join(ROOT, "paper_1901_04200_gb300"), os.path.join(dst, "paper_1901_04200_gb300"))
+    os.symlink(os.path.join(ROOT, "include"), os.path.join(dst, "include"))
 
 
 def _run_pins(cwd, nodes):
@@ -124,7 +163,8 @@ def _run_pins(cwd, nodes):
 
 def test_unmodified_copy_passes_the_pins(tmp_path):
     _copy(str(tmp_path))
-    nodes = sorted({n for m in MUTATIONS for n in m[4]})
+    nodes = sorted({n for m in MUTATIONS for n in m[4]} | {n for m in CONSISTENT_MUTATIONS for n in m[2]}
+                   | set(CONSISTENCY))
     res = _run_pins(str(tmp_path), nodes)
     assert res.returncode == 0, res.stdout[-2000:] + res.stderr[-2000:]
 
@@ -141,3 +181,25 @@ def test_planted_mistake_fails_a_pin(tmp_path, mistake, fname, old, new, nodes):
     res = _run_pins(str(tmp_path), nodes)
     # pytest exits 1 when tests ran and some failed
     assert res.returncode == 1 and " failed" in res.stdout, (mistake, res.stdout[-2000:] + res.stderr[-2000:])
+
+
+def _plant(root, edits):
+    for fname, old, new, count in edits:
+        path = os.path.join(root, "oracle", fname)
+        with open(path) as f:
+            src = f.read()
+        assert src.count(old) == count, "the oracle's source changed: update this mutation (%s)" % old
+        with open(path, "w") as f:
+            f.write(src.replace(old, new))
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("mistake,edits,nodes", CONSISTENT_MUTATIONS, ids=[m[0] for m in CONSISTENT_MUTATIONS])
+def test_consistent_model_mistake_fails_a_dynamics_pin(tmp_path, mistake, edits, nodes):
+    _copy(str(tmp_path))
+    _plant(str(tmp_path), edits)
+    res = _run_pins(str(tmp_path), CONSISTENCY)
+    assert res.returncode == 0, ("the mistake is not consistent", mistake, res.stdout[-2000:] + res.stderr[-2000:])
+    for node in nodes:
+        res = _run_pins(str(tmp_path), [node])
+        assert res.returncode == 1 and " failed" in res.stdout, (mistake, node, res.stdout[-2000:] + res.stderr[-2000:])

@@ -360,3 +360,135 @@ def test_slv_fd_and_martingale(orc):
     pb0 = replace(pb, K=np.zeros(pb.m))
     Ey, se = batched(lambda p0, k: orc.forward(pb0, w.theta, k, path0=p0), 1 << 15)
     assert np.all(np.abs(Ey - pb.S0) < 5 * se)
+
+
+# ------------------------------------------- Heston / SLV variance dynamics
+
+def one_step_problem(kind, dt=0.25):
+    """One Euler step of the Heston or SLV variance model (Heston SLV model paragraph:
+    dV = kappa (theta_h - V) dt + xi sqrt(V) dW^V, d<W^S, W^V> = rho dt)."""
+    pb = inputs.Problem(kind=kind, S0=100.0, r=0.02, dt=dt, n_steps=1,
+                        K=np.array([100.0]), mat_step=np.array([1], dtype=np.int32))
+    if kind == "slv":
+        pb = replace(pb, nt=2, nx=2, t_max=1.0, x_lo=-1.0, x_hi=1.0)
+    return pb
+
+
+def moment_se(a, b):
+    """Sample covariance of a and b and its standard error (delta method on the products)."""
+    da, db = a - a.mean(), b - b.mean()
+    prod = da * db
+    return prod.mean(), prod.std(ddof=1) / math.sqrt(len(a))
+
+
+@pytest.mark.parametrize("kind,lev", [("heston", 1.0), ("slv", 1.3), ("slv", 0.7)])
+def test_one_step_conditional_moments(orc, kind, lev):
+    """From a fixed v0 > 0 one full-truncation Euler step has exactly
+    E dx = (r - L^2 v0/2) dt, Var dx = L^2 v0 dt, E dv = kappa (theta_h - v0) dt,
+    Var dv = xi^2 v0 dt and Cov(dx, dv) = rho xi L v0 dt (L the leverage, 1 for Heston):
+    the drift, diffusion and correlation of both equations, independent of the adjoint."""
+    kappa, thh, xi, rho, v0 = 1.5, 0.06, 0.7, -0.3, 0.04
+    theta = np.array([kappa, thh, xi, rho, v0])
+    pb = one_step_problem(kind)
+    if kind == "slv":
+        theta = np.concatenate([theta, np.full(4, lev)])
+    N = 1 << 20
+    st = orc.states_at(pb, theta, 1, N)
+    dx, dv = st[:, 0], st[:, 1] - v0
+    dt, r = pb.dt, pb.r
+    sd_x, sd_v = math.sqrt(dx.var()), math.sqrt(dv.var())
+    assert abs(dx.mean() - (r - 0.5 * lev * lev * v0) * dt) < 5 * sd_x / math.sqrt(N)
+    assert abs(dv.mean() - kappa * (thh - v0) * dt) < 5 * sd_v / math.sqrt(N)
+    for a, b, ref in [(dx, dx, lev * lev * v0 * dt), (dv, dv, xi * xi * v0 * dt),
+                      (dx, dv, rho * xi * lev * v0 * dt)]:
+        got, se = moment_se(a, b)
+        assert abs(got - ref) < 5 * se, (got, ref, se)
+
+
+def test_one_step_full_truncation(orc):
+    """From v0 < 0 the step uses v+ = 0: no diffusion in x or v, and v moves by
+    kappa theta_h dt exactly."""
+    kappa, thh, xi, rho, v0 = 1.5, 0.06, 0.7, -0.3, -0.01
+    pb = one_step_problem("heston")
+    st = orc.states_at(pb, np.array([kappa, thh, xi, rho, v0]), 1, 1024)
+    assert np.all(st[:, 0] == pb.r * pb.dt)
+    assert np.allclose(st[:, 1], v0 + kappa * thh * pb.dt, rtol=0, atol=1e-17)
+
+
+def heston_cf_call(S0, K, T, r, kappa, thh, xi, rho, v0):
+    """Heston (1993) call price from the characteristic function of ln S_T, in the form of
+    Albrecher, Mayer, Schoutens and Tistaert (2007, "the little Heston trap"), which stays
+    on the principal branch of the complex logarithm: C = S0 P1 - K e^{-rT} P2 with
+    P_j = 1/2 + (1/pi) int_0^inf Re[e^{-iu ln K} f_j(u) / (iu)] du,
+    f_2(u) = phi(u), f_1(u) = phi(u - i) / phi(-i)."""
+    from scipy.integrate import quad
+
+    def phi(u):
+        iu = 1j * u
+        b = kappa - rho * xi * iu
+        d = np.sqrt(b * b + xi * xi * (iu + u * u))
+        g = (b - d) / (b + d)
+        e = np.exp(-d * T)
+        C = r * iu * T + kappa * thh / (xi * xi) * ((b - d) * T - 2.0 * np.log((1.0 - g * e) / (1.0 - g)))
+        D = (b - d) / (xi * xi) * (1.0 - e) / (1.0 - g * e)
+        return np.exp(C + D * v0 + iu * math.log(S0))
+
+    lk = math.log(K)
+    fwd = phi(-1j)
+
+    def p1(u):
+        return (np.exp(-1j * u * lk) * phi(u - 1j) / (1j * u * fwd)).real
+
+    def p2(u):
+        return (np.exp(-1j * u * lk) * phi(u) / (1j * u)).real
+
+    P1 = 0.5 + quad(p1, 1e-10, 200.0, limit=500, epsabs=1e-12)[0] / math.pi
+    P2 = 0.5 + quad(p2, 1e-10, 200.0, limit=500, epsabs=1e-12)[0] / math.pi
+    return S0 * P1 - K * math.exp(-r * T) * P2
+
+
+def test_heston_cf_pricer_reduces_to_black_scholes():
+    """The pricer itself: at a tiny vol of vol the variance is deterministic, so the price is
+    Black-Scholes at the integrated variance theta_h T + (v0 - theta_h)(1 - e^{-kappa T})/kappa."""
+    kappa, thh, v0, T, r = 2.0, 0.05, 0.03, 1.0, 0.02
+    var = thh * T + (v0 - thh) * (1.0 - math.exp(-kappa * T)) / kappa
+    for K in (80.0, 100.0, 120.0):
+        got = heston_cf_call(100.0, K, T, r, kappa, thh, 1e-3, -0.5, v0)
+        ref = bs_call(100.0, K, T, r, math.sqrt(var / T))
+        assert abs(got - ref) < 2e-3, (K, got, ref)
+
+
+@pytest.mark.slow
+def test_heston_matches_characteristic_function_price(orc):
+    """The full-truncation Euler prices converge to Heston's closed-form price: at dt/2 the oracle's
+    price lies within 5 standard errors plus the Euler bias, estimated by halving the step
+    (weak order one: bias(dt/2) ~ price(dt) - price(dt/2)).  The two step sizes share their
+    Brownian increments (a coarse normal is the scaled sum of two fine ones), so the bias estimate
+    carries little noise."""
+    kappa, thh, xi, rho, v0 = 3.0, 0.05, 0.5, -0.7, 0.03
+    theta = np.array([kappa, thh, xi, rho, v0])
+    strikes = np.array([80.0, 100.0, 120.0])
+    T, n = 1.0, 64
+    P, nb = 1 << 19, 16
+    b = P // nb
+
+    def problem(steps, Z, p0):
+        return inputs.Problem(kind="heston", S0=100.0, r=0.02, dt=T / steps, n_steps=steps, K=strikes,
+                              mat_step=np.full(3, steps, dtype=np.int32), normals=Z, normals_path0=p0)
+
+    fine, diff = [], []
+    for k in range(nb):
+        Zf = np.random.default_rng(7000 + k).standard_normal((b, 2 * n, 2))  # [path, fine step, (z1, z2)]
+        Zc = (Zf[:, 0::2, :] + Zf[:, 1::2, :]) / math.sqrt(2.0)
+        yf = orc.forward(problem(2 * n, Zf.reshape(b, -1), k * b), theta, b, path0=k * b)
+        yc = orc.forward(problem(n, np.ascontiguousarray(Zc.reshape(b, -1)), k * b), theta, b, path0=k * b)
+        fine.append(yf)
+        diff.append(yc - yf)
+    fine, diff = np.array(fine), np.array(diff)
+    pf, sf = fine.mean(0), fine.std(0, ddof=1) / math.sqrt(nb)
+    bias, sb = diff.mean(0), diff.std(0, ddof=1) / math.sqrt(nb)
+    ref = np.array([heston_cf_call(100.0, K, T, 0.02, kappa, thh, xi, rho, v0) for K in strikes])
+    tol = 5 * sf + np.abs(bias) + 5 * sb
+    assert np.all(np.abs(pf - ref) < tol), (pf, ref, sf, bias, sb)
+    # the tolerance is a small part of each price: the pin sees the dynamics' shape
+    assert np.all(tol < 0.02 * ref + 0.02), tol
