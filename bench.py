@@ -1,9 +1,13 @@
 """Benchmark: G + grad G path-steps/s of the two-step MC-AAD algorithm on GB300.
 
-One step = one mc_value_and_grad call (forward sweep, E y / lambda / G,
-reverse sweep with recompute, grad G) over the Heston workload: 2^20 paths x
-512 steps (Delta = 1/256, 2y), 64 calls, FP32 paths, FP64 sums.  The metric is
-path-steps per second, P * S / (time per step).
+One step = one mc_value_and_grad call (forward sweep, E y / lambda / G, reverse
+sweep, grad G).  The headline workload is the largest one: local volatility on a
+bilinear 20 x 10 node surface, 2^22 paths x 500 steps (Delta = 0.01, 5y), 200
+calls, 200 parameters, FP32 paths, FP64 sums.  The Heston workload (2^20 paths x
+512 steps, 64 calls) is measured after it and reported under "workloads", and
+the surrogate-assisted against plain calibration under "calibration".  The
+metric is path-steps per second, P * S / (time per step); the roofline is the
+per-pipe ALU issue bound of the dominant kernel, with its HBM fraction beside it.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -92,7 +96,9 @@ MEASURED_TRAFFIC = {
     ("heston", "normals", 8, 2, "forward_sweep"): {"bytes": 95232 + 4770265856, "sources": "ec3cdf7bd07c5dc4"},
     ("heston", "normals", 8, 2, "reverse_sweep"): {"bytes": 4831930880 + 521984, "sources": "ec3cdf7bd07c5dc4"},
 }
-KERNEL_SOURCES = ["mc_common.cuh", "mc_paths.cuh", "mc_paths_heston.cu"]
+KERNEL_SOURCES = ["mc_common.cuh", "mc_paths.cuh"]
+MODEL_SOURCE = {"gbm": "mc_paths_gbm.cu", "heston": "mc_paths_heston.cu", "lv": "mc_paths_lv.cu",
+                "slv": "mc_paths_slv.cu"}
 
 
 def code_tokens(src):
@@ -120,10 +126,10 @@ def code_tokens(src):
     return " ".join("".join(out).split())
 
 
-def kernel_sources_hash():
+def kernel_sources_hash(model="heston"):
     import hashlib
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
+    for f in KERNEL_SOURCES + [MODEL_SOURCE[model]]:
         with open(os.path.join(ROOT, "paper_1901_04200_gb300", "csrc", f)) as fh:
             h.update(code_tokens(fh.read()).encode())
     return h.hexdigest()[:16]
@@ -131,7 +137,7 @@ def kernel_sources_hash():
 
 def measured_traffic(model, storage, k, ppt, kernel):
     rec = MEASURED_TRAFFIC.get((model, storage, k, ppt, kernel))
-    if rec and rec["sources"] == kernel_sources_hash():
+    if rec and rec["sources"] == kernel_sources_hash(model):
         return rec["bytes"]
     return None
 
@@ -175,19 +181,20 @@ def kernel_rooflines(model, storage, K, ppt, P, S, n_groups, prof, issue_peak, h
                        "alu_pipe_bound": max(pipes, key=pipes.get)}
     dom = max(kern, key=lambda k: kern[k]["ms"])
     d = kern[dom]
-    hbm_bound = d["hbm_frac"] > d["alu_frac"]
-    return {"bound": "hbm" if hbm_bound else "alu",
-            "achieved": d["hbm_gbs"] if hbm_bound else d["alu_tops"],
-            "peak": hbm_peak / 1e9 if hbm_bound else issue_peak / 1e12,
-            "unit": "GB/s" if hbm_bound else "Tops/s",
-            "frac": d["hbm_frac"] if hbm_bound else d["alu_frac"],
+    # The path is ALU work (the per-pipe issue bound); the HBM fraction of the bytes the storage
+    # mode moves is reported beside it.
+    return {"bound": "alu",
+            "achieved": d["alu_tops"], "peak": issue_peak / 1e12, "unit": "Tops/s", "frac": d["alu_frac"],
+            "fp32_pipe_frac": d["pipe_fracs"]["fp32"], "pipe_fracs": d["pipe_fracs"],
+            "alu_pipe_bound": d["alu_pipe_bound"],
+            "hbm": {"achieved": d["hbm_gbs"], "peak": hbm_peak / 1e9, "unit": "GB/s", "frac": d["hbm_frac"],
+                    "peak_basis": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs, %s)" % peak_src},
             "traffic": measured_traffic(model, storage, K, ppt, dom),
             "algorithmic_bytes": P * S * d["bytes_per_path_step"],
             "kernel": "%s (%s, %s, K=%d, %d paths/thread)" % (dom, model, storage if storage == "tangent"
                                                                else storage + " storage", K, ppt),
-            "peak_basis": ("measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs, %s)" % peak_src) if hbm_bound
-                          else "SM issue rate 128 thread-ops/clk x %d SMs x %.0f MHz (%s max clock)"
-                               % (n_sm, sm_mhz_peak, peak_src),
+            "peak_basis": "SM issue rate 128 thread-ops/clk x %d SMs x %.0f MHz (%s max clock); each pipe "
+                          "against its own rate in pipe_fracs" % (n_sm, sm_mhz_peak, peak_src),
             "kernels": kern}
 
 
@@ -494,20 +501,35 @@ def calibration_experiment(cases):
             verified = calibrate.verify_by_mc(ctx, mc.theta, theta_star, seed + 1, P)
     n_samples = n_theta * pb.m
 
+    one_off = t_data + t_train
+
     def summary(rows, seconds_key):
         ok = [x for x in rows if x["converged"]]
-        return {"converged": len(ok) / len(rows),
+        secs = [x[seconds_key] for x in rows]
+        return {"converged": len(ok) / len(rows), "n_converged": len(ok),
+                "median_mc_evals_all": float(np.median([x["mc_evals"] for x in rows])),
+                "median_seconds_all": float(np.median(secs)), "mean_seconds_all": float(np.mean(secs)),
                 "median_mc_evals_converged": float(np.median([x["mc_evals"] for x in ok])) if ok else None,
                 "median_seconds_converged": float(np.median([x[seconds_key] for x in ok])) if ok else None,
                 "cases": rows}
 
+    ps, ss = summary(plain, "seconds"), summary(sur_rows, "seconds_excl_training")
+    ss["median_seconds_all_incl_one_off"] = ss["median_seconds_all"] + one_off
+    ss["mean_seconds_all_incl_one_off"] = ss["mean_seconds_all"] + one_off
+    gain = ps["mean_seconds_all"] - ss["mean_seconds_all"]
     return {"tol": 1e-8, "paths": P, "cases": cases, "start": "theta*, theta0 drawn in the Heston box (Feller)",
+            "all_cases_note": "medians and means over all cases; a case that stops before G < tol (evaluation "
+                              "cap or a stalled line search) counts at its stopping time, a lower bound on its "
+                              "time to tolerance",
             "labels": {"samples": n_samples, "paths_per_sample": n_paths, "seconds": t_data},
             "training": {"epochs": epochs, "batch": 4096, "seconds": t_train,
                          "samples_per_s": epochs * (n_samples // 4096) * 4096 / t_train},
-            "plain": dict(summary(plain, "seconds"), method="L-BFGS-B on MC-AAD G and grad G, restarts, 300 evaluations"),
-            "surrogate": dict(summary(sur_rows, "seconds_excl_training"), one_off_seconds=t_data + t_train,
+            "plain": dict(ps, method="L-BFGS-B on MC-AAD G and grad G, restarts, 300 evaluations"),
+            "surrogate": dict(ss, one_off_seconds=one_off,
                               method="L-BFGS-B on the surrogate, then MC-AAD steps with its Gauss-Newton metric"),
+            "break_even_recalibrations": (one_off / gain) if gain > 0 else None,
+            "break_even_note": "calibrations after which the one-off labels + training cost is repaid: one-off "
+                               "seconds / (plain - surrogate mean seconds per calibration, all cases)",
             "verified_by_mc": dict(verified, case=0, note="prices at the calibrated theta vs theta*, fresh seed")}
 
 
@@ -569,68 +591,47 @@ def run_reference(args):
     print(json.dumps(line))
 
 
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--paths", type=int, default=1 << 20)
-    ap.add_argument("--cpu-paths", type=int, default=1 << 17)
-    ap.add_argument("--ref-paths", type=int, default=1 << 15, help="--impl reference: largest sample per step")
-    ap.add_argument("--ref-seconds", type=float, default=90.0,
-                    help="--impl reference: host time the whole run is sized for")
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--ppt", type=int, default=0, help="paths per GPU thread (0 = library default)")
-    ap.add_argument("--tape-paths", type=int, default=1 << 18, help="paths of the --workload tape run")
-    ap.add_argument("--tape-precision", default="fp32", choices=["fp32", "fp64"],
-                    help="per-path values and adjoints of the --workload tape run")
-    ap.add_argument("--tape-interpret", action="store_true",
-                    help="--workload tape: run the interpreter instead of the compiled program")
-    ap.add_argument("--tape-seg", type=int, default=768,
-                    help="--workload tape: nodes per compiled segment (0 = library default, 384)")
-    ap.add_argument("--tape-store", dest="tape_recompute", action="store_false",
-                    help="--workload tape: compiled backward kernels read every value they need from the "
-                         "tape; by default they re-run their segment's forward, which measured faster")
-    ap.add_argument("--workload", default="heston", choices=["heston", "lv", "slv", "surrogate", "tape"],
-                    help="heston (the metric's workload), lv (2^22 x 500 local vol) or surrogate "
-                         "(one differential-loss training step of the pricing network), for measurement")
-    ap.add_argument("--no-calibration", action="store_true", help="skip the surrogate vs plain calibration")
-    ap.add_argument("--no-arms", action="store_true",
-                    help="skip the recompute and forward-mode comparison arms")
-    ap.add_argument("--calib-cases", type=int, default=4)
-    ap.add_argument("--ckpt", type=int, default=0, help="checkpoint interval (0 = workload default)")
-    ap.add_argument("--storage", default="auto", choices=["auto", "checkpoint", "normals", "full"],
-                    help="what the reverse sweep reads: checkpoints (re-run with regenerated normals), "
-                         "checkpoints and stored normals, the whole stored tape, or the library's choice")
-    args = ap.parse_args()
-    if args.impl == "reference":
-        return run_reference(args)
+WORKLOAD_TITLES = {"lv": "local vol, 2^22 paths x 500 steps, m=200, M=200",
+                   "heston": "Heston FT, 2^20 paths x 512 steps, m=64, M=5",
+                   "slv": "Heston SLV, 2^20 paths x 512 steps, m=64, M=95"}
 
+
+def make_workload(model, args):
+    from paper_1901_04200_gb300 import inputs
+    if model == "lv":
+        w = inputs.lv_config(n_paths=args.paths or (1 << 22))
+    elif model == "slv":
+        w = inputs.slv_config(n_paths=args.paths or (1 << 20))
+    else:
+        w = inputs.heston_config(n_paths=args.paths or (1 << 20))
+    return w
+
+
+def oracle_precision(ctx, w, theta, C, keep, n_cpu):
+    """The FP32 path's error against the FP64 oracle, per result, on the same paths."""
+    import numpy as np
+    Ey_o, G_o, g_o = keep
+    Gs, gs, Eys = (x.cpu().numpy() for x in ctx.value_and_grad(theta, C, w.problem.seed, n_cpu))
+    return {"sample": "paths [0, %d) of the workload: GPU FP32 paths and FP64 sums vs the FP64 oracle" % n_cpu,
+            "Ey_max_rel": float(np.max(np.abs(Eys - Ey_o)) / np.max(np.abs(Ey_o))),
+            "G_rel": float(abs(Gs[0] - G_o) / abs(G_o)),
+            "grad_normwise_rel": float(np.max(np.abs(gs - g_o)) / np.max(np.abs(g_o)))}
+
+
+def run_path_workload(model, args, rank, world, local, headline):
+    """Times mc_value_and_grad on one path workload: the device-timed steps (inputs resident),
+    the end-to-end steps through host buffers, and (one GPU) the comparison arms.  Returns the
+    JSON fields of that workload."""
     import numpy as np
     import torch
 
-    from paper_1901_04200_gb300 import _lib, inputs
-    from paper_1901_04200_gb300 import build as _build
+    from paper_1901_04200_gb300 import _lib
 
-    rank, world, local = dist_setup(args.gpus)
-    if rank == 0:
-        _build.build()
-    barrier(world)
-    if args.workload == "surrogate":
-        return surrogate_step_bench(args, rank, world)
-    if args.workload == "tape":
-        return tape_bench(args, rank, world)
-    if args.workload == "lv":
-        w = inputs.lv_config(n_paths=args.paths if args.paths != (1 << 20) else (1 << 22))
-    elif args.workload == "slv":
-        w = inputs.slv_config(n_paths=args.paths)
-    else:
-        w = inputs.heston_config(n_paths=args.paths)
-    if args.ppt or args.ckpt:
+    w = make_workload(model, args)
+    if headline and (args.ppt or args.ckpt):
         w.problem.paths_per_thread = args.ppt
         w.problem.ckpt_every = args.ckpt or w.problem.ckpt_every
-    w.problem.storage = args.storage
+    w.problem.storage = args.storage if headline else "auto"
     pb, P, S = w.problem, w.n_paths, w.problem.last_step
     path0 = rank * P
     dev = torch.device("cuda", torch.cuda.current_device())
@@ -641,6 +642,7 @@ def main():
            torch.empty(ctx.m, dtype=torch.float64, device=dev))
     seed = pb.seed
     stream = torch.cuda.current_stream()
+    steps = args.steps if headline else max(3, args.steps // 2)
 
     if world > 1:
         from paper_1901_04200_gb300.sharding import sharded_value_and_grad
@@ -661,10 +663,10 @@ def main():
     time.sleep(0.3)
     barrier(world)
     torch.cuda.synchronize()
-    ctx.profile_begin(8 * args.steps)
+    ctx.profile_begin(8 * steps)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for _ in range(args.steps):
+    for _ in range(steps):
         step()
     e1.record(stream)
     torch.cuda.synchronize()
@@ -697,97 +699,192 @@ def main():
     torch.cuda.synchronize()
     barrier(world)
     t0 = time.perf_counter()
-    for _ in range(args.steps):
+    for _ in range(steps):
         e2e_step()
         torch.cuda.current_stream().synchronize()
     e2e_s = time.perf_counter() - t0
     clk = clocks.stop()
 
-    ms_step = max_over_ranks(ms_total / args.steps, world)
-    e2e_ms = max_over_ranks(e2e_s * 1e3 / args.steps, world)
+    ms_step = max_over_ranks(ms_total / steps, world)
+    e2e_ms = max_over_ranks(e2e_s * 1e3 / steps, world)
     value = world * P * S / (ms_step * 1e-3)
     peaks, peak_src = load_peaks()
     sm_mhz_peak = float(peaks.get("sm_max_mhz", 2070.0))
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     issue_peak = 128 * n_sm * sm_mhz_peak * 1e6  # thread-ops/s: 4 warp instructions per SM per clock
     hbm_peak = float(peaks["hbm_gbs"]) * 1e9
-    model = args.workload
     storage = ctx.storage
     K = pb.ckpt_every
-    ppt = pb.paths_per_thread or (2 if model == "heston" else 1)
+    ppt = pb.paths_per_thread or 2
     n_groups = len(set(np.asarray(pb.mat_step).tolist()))
     bytes_ps = kernel_bytes(model, storage, K, S, n_groups)
     roof_args = (P, S, n_groups)
     peak_args = (issue_peak, hbm_peak, peak_src, n_sm, sm_mhz_peak)
     roofline = kernel_rooflines(model, storage, K, ppt, *roof_args, prof, *peak_args)
-    launches = sum(n for _, n in prof.values())
-
-    line = {}
-    if rank == 0:
-        line = {
-            "metric": METRIC if model == "heston" else METRIC.replace(
-                "Heston FT, 2^20 paths x 512 steps, m=64, M=5",
-                "local vol, 2^22 paths x 500 steps, m=200, M=200" if model == "lv" else
-                "Heston SLV, 2^20 paths x 512 steps, m=64, M=95"),
-            "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": max(args.warmup, 3), "ms_per_step": ms_step, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": w.name, "paths_per_gpu": P, "steps": S, "instruments": pb.m, "params": pb.n_params,
-                       "storage": storage,
-                       "ckpt_every": pb.ckpt_every, "paths_per_thread": pb.paths_per_thread or "default",
-                       "precision": "fp32 paths, fp64 sums",
-                       "l2": "inputs larger than L2: %.0f MB stored and re-read per step" %
-                             (P * S * bytes_ps["forward_sweep"] / 1e6)},
-            "roofline": roofline,
-            "kernels_ms_per_step": {k: v[0] / max(v[1], 1) for k, v in prof.items() if v[1]},
-            "gpu_launches": launches,
-            "e2e": {"value": world * P * S / (e2e_ms * 1e-3), "unit": UNIT,
-                    "h2d_bytes_per_step": 8 * (ctx.M + ctx.m), "d2h_bytes_per_step": 8 * (1 + ctx.M + ctx.m)},
-            "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"]},
-        }
+    res = {
+        "metric": "G+grad G path-steps/s (%s)" % WORKLOAD_TITLES[model],
+        "value": value, "unit": UNIT, "ms_per_step": ms_step, "steps": steps,
+        "config": {"workload": w.name, "paths_per_gpu": P, "steps": S, "instruments": pb.m, "params": pb.n_params,
+                   "storage": storage, "ckpt_every": pb.ckpt_every, "paths_per_thread": ppt,
+                   "precision": "fp32 paths, fp64 sums",
+                   "l2": "inputs larger than L2: %.0f MB stored and re-read per step" %
+                         (P * S * bytes_ps["forward_sweep"] / 1e6)},
+        "roofline": roofline,
+        "kernels_ms_per_step": {k: v[0] / max(v[1], 1) for k, v in prof.items() if v[1]},
+        "gpu_launches": sum(n for _, n in prof.values()),
+        "e2e": {"value": world * P * S / (e2e_ms * 1e-3), "unit": UNIT,
+                "h2d_bytes_per_step": 8 * (ctx.M + ctx.m), "d2h_bytes_per_step": 8 * (1 + ctx.M + ctx.m)},
+        "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"]},
+    }
     if world == 1 and not args.no_arms:
         # the same workload by the design that regenerates the normals and recomputes every
-        # segment (checkpoints only), and for Heston by forward-mode tangents (no reverse sweep)
-        arms = {}
+        # segment (checkpoints only; local vol at the 25-step interval the workload names), and
+        # for Heston by forward-mode tangents (no reverse sweep)
         if storage != "checkpoint":
-            ctx_r = _lib.Context(replace(pb, storage="checkpoint"), max_paths=P, device=dev)
+            K_r, ppt_r = (25, 1) if model == "lv" else (K, pb.paths_per_thread)
+            pb_r = replace(pb, storage="checkpoint", ckpt_every=K_r, paths_per_thread=ppt_r)
+            ctx_r = _lib.Context(pb_r, max_paths=P, device=dev)
             ms_r, prof_r = time_arm(ctx_r, lambda: ctx_r.value_and_grad(theta, C, seed, P, path0=path0, out=out),
-                                    args.steps, stream)
-            arms["recompute_arm"] = {"ms_per_step": ms_r, "value": P * S / (ms_r * 1e-3), "unit": UNIT,
-                                     "storage": "checkpoint",
-                                     "roofline": kernel_rooflines(model, "checkpoint", K, ppt, *roof_args, prof_r,
-                                                                  *peak_args)}
+                                    steps, stream)
+            res["recompute_arm"] = {"ms_per_step": ms_r, "value": P * S / (ms_r * 1e-3), "unit": UNIT,
+                                    "storage": "checkpoint", "ckpt_every": K_r, "paths_per_thread": ppt_r or 2,
+                                    "roofline": kernel_rooflines(model, "checkpoint", K_r, ppt_r or 2, *roof_args,
+                                                                 prof_r, *peak_args)}
             del ctx_r
         if model == "heston":
             ms_t, prof_t = time_arm(ctx, lambda: ctx.value_and_grad_tangent(theta, C, seed, P, path0=path0,
-                                                                            out=out), args.steps, stream)
-            arms["tangent_arm"] = {"ms_per_step": ms_t, "value": P * S / (ms_t * 1e-3), "unit": UNIT,
-                                   "method": "forward-mode tangents, grad G = J^T lambda",
-                                   "roofline": kernel_rooflines(model, "tangent", K, 1, *roof_args, prof_t,
-                                                                *peak_args)}
-        if rank == 0:
-            line.update(arms)
+                                                                            out=out), steps, stream)
+            res["tangent_arm"] = {"ms_per_step": ms_t, "value": P * S / (ms_t * 1e-3), "unit": UNIT,
+                                  "method": "forward-mode tangents, grad G = J^T lambda",
+                                  "roofline": kernel_rooflines(model, "tangent", K, 1, *roof_args, prof_t,
+                                                               *peak_args)}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        n_cpu = args.cpu_paths or (1 << 18 if model == "lv" else 1 << 17)
+        keep = []
+        res["cpu_baseline"] = cpu_baseline(w, n_cpu, keep=keep)
+        res["precision"] = oracle_precision(ctx, w, theta, C, keep[0], n_cpu)
+        # the GPU analogues of the paper's cost table (eq. 1311A with c = one GPU)
+        cost_f = oracle_single_path_cost(w)
+        kf = roofline["kernels"]["forward_sweep"]["ms"] * 1e-3
+        kr = roofline["kernels"]["reverse_sweep"]["ms"] * 1e-3
+        res["paper_table"] = {"cost_F_one_core_s": cost_f, "K_F_over_c": kf / (P * cost_f),
+                              "K_R_over_c": kr / (P * cost_f), "cost_G_over_P_cost_F": ms_step * 1e-3 / (P * cost_f),
+                              "note": "Cost(F): the oracle's FP64 forward sweep of one path on one host core"}
+    del ctx
+    torch.cuda.empty_cache()
+    return res
+
+
+def run_reference(args):
+    """The oracle timed on the host cores, as the reference arm: each step one bounded sample of
+    the headline workload's paths (the whole workload would take hours on the host)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = make_workload(args.workload, args)
+    S = w.problem.last_step
+    # size the per-step sample from a short probe of the host's rate, so the whole run
+    # (warm-ups at an eighth of the sample) takes about --ref-seconds
+    rate = cpu_baseline(w, 2048)["value"]
+    budget_steps = args.steps + args.warmup / 8.0
+    n = int(rate * args.ref_seconds / max(budget_steps, 1.0) / S) // 1024 * 1024
+    n = max(1024, min(n, args.ref_paths))
+    for _ in range(args.warmup):
+        cpu_baseline(w, max(n // 8, 256))
+    vals = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        vals.append(cpu_baseline(w, n))
+        vals[-1]["wall_s"] = time.perf_counter() - t0
+    v = statistics.median(x["value"] for x in vals)
+    line = {"metric": "G+grad G path-steps/s (%s)" % WORKLOAD_TITLES[args.workload], "value": v, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": statistics.median(x["wall_s"] for x in vals) * 1e3,
+            "ms_per_step_is": "the timed sample step (%d of the workload's %d paths)" % (n, w.n_paths),
+            "full_workload_ms_per_step_extrapolated": S * w.n_paths / v * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": w.name, "paths_per_gpu": w.n_paths, "steps": S, "instruments": w.problem.m,
+                       "params": w.problem.n_params},
+            "sample_paths_per_step": n,
+            "cpu_baseline": dict(vals[0], value=v),
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--paths", type=int, default=0, help="paths per GPU (0 = the workload's own count)")
+    ap.add_argument("--cpu-paths", type=int, default=0,
+                    help="oracle sample for cpu_baseline and precision (0 = 2^18 local vol, 2^17 Heston)")
+    ap.add_argument("--ref-paths", type=int, default=1 << 15, help="--impl reference: largest sample per step")
+    ap.add_argument("--ref-seconds", type=float, default=90.0,
+                    help="--impl reference: host time the whole run is sized for")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ppt", type=int, default=0, help="paths per GPU thread (0 = library default)")
+    ap.add_argument("--tape-paths", type=int, default=1 << 18, help="paths of the --workload tape run")
+    ap.add_argument("--tape-precision", default="fp32", choices=["fp32", "fp64"],
+                    help="per-path values and adjoints of the --workload tape run")
+    ap.add_argument("--tape-interpret", action="store_true",
+                    help="--workload tape: run the interpreter instead of the compiled program")
+    ap.add_argument("--tape-seg", type=int, default=768,
+                    help="--workload tape: nodes per compiled segment (0 = library default, 384)")
+    ap.add_argument("--tape-store", dest="tape_recompute", action="store_false",
+                    help="--workload tape: compiled backward kernels read every value they need from the "
+                         "tape; by default they re-run their segment's forward, which measured faster")
+    ap.add_argument("--workload", default="lv", choices=["lv", "heston", "slv", "surrogate", "tape"],
+                    help="lv (the largest workload, 2^22 x 500 local vol: the headline), heston (2^20 x 512), "
+                         "slv (Heston SLV), surrogate (one differential-loss training step of the pricing "
+                         "network) or tape (the expected-backward tape)")
+    ap.add_argument("--also", default="heston",
+                    help="comma-separated path workloads measured after the headline, reported under "
+                         "'workloads' ('' for none)")
+    ap.add_argument("--no-calibration", action="store_true", help="skip the surrogate vs plain calibration")
+    ap.add_argument("--no-arms", action="store_true",
+                    help="skip the recompute and forward-mode comparison arms")
+    ap.add_argument("--calib-cases", type=int, default=16)
+    ap.add_argument("--ckpt", type=int, default=0, help="checkpoint interval (0 = workload default)")
+    ap.add_argument("--storage", default="auto", choices=["auto", "checkpoint", "normals", "full"],
+                    help="what the reverse sweep reads: checkpoints (re-run with regenerated normals), "
+                         "checkpoints and stored normals, the whole stored tape, or the library's choice")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        if args.workload not in WORKLOAD_TITLES:
+            args.workload = "lv"
+        return run_reference(args)
+
+    from paper_1901_04200_gb300 import build as _build
+
+    rank, world, local = dist_setup(args.gpus)
     if rank == 0:
-        if not args.no_cpu_baseline and world == 1:
-            n_cpu = args.cpu_paths if model == "heston" else args.cpu_paths // 4
-            keep = []
-            line["cpu_baseline"] = cpu_baseline(w, n_cpu, keep=keep)
-            # the FP32 path's error against the FP64 oracle, per result, on the same paths
-            Ey_o, G_o, g_o = keep[0]
-            Gs, gs, Eys = (x.cpu().numpy() for x in ctx.value_and_grad(theta, C, seed, n_cpu))
-            line["precision"] = {
-                "sample": "paths [0, %d) of the workload: GPU FP32 paths and FP64 sums vs the FP64 oracle" % n_cpu,
-                "Ey_max_rel": float(np.max(np.abs(Eys - Ey_o)) / np.max(np.abs(Ey_o))),
-                "G_rel": float(abs(Gs[0] - G_o) / abs(G_o)),
-                "grad_normwise_rel": float(np.max(np.abs(gs - g_o)) / np.max(np.abs(g_o)))}
-            # the GPU analogues of the paper's cost table (eq. 1311A with c = one GPU)
-            cost_f = oracle_single_path_cost(w)
-            kf, kr = roofline["kernels"]["forward_sweep"]["ms"] * 1e-3, roofline["kernels"]["reverse_sweep"]["ms"] * 1e-3
-            line["paper_table"] = {"cost_F_one_core_s": cost_f, "K_F_over_c": kf / (P * cost_f),
-                                   "K_R_over_c": kr / (P * cost_f), "cost_G_over_P_cost_F": ms_step * 1e-3 / (P * cost_f),
-                                   "note": "Cost(F): the oracle's FP64 forward sweep of one path on one host core"}
-        if not args.no_calibration and world == 1 and model == "heston":
-            line["calibration"] = calibration_experiment(args.calib_cases)
+        _build.build()
+    barrier(world)
+    if args.workload == "surrogate":
+        return surrogate_step_bench(args, rank, world)
+    if args.workload == "tape":
+        return tape_bench(args, rank, world)
+    head = run_path_workload(args.workload, args, rank, world, local, headline=True)
+    line = {}
+    if rank == 0:
+        line = {"metric": head.pop("metric"), "value": head.pop("value"), "unit": UNIT, "n_gpus": world,
+                "steps": head.pop("steps"), "warmup": max(args.warmup, 3), "ms_per_step": head.pop("ms_per_step"),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic"}
+        line.update(head)
+    others = [m for m in args.also.split(",") if m and m != args.workload] if not args.paths else []
+    if others:
+        line["workloads"] = {}
+    for m in others:
+        r = run_path_workload(m, args, rank, world, local, headline=False)
+        if rank == 0:
+            line["workloads"][r["config"]["workload"]] = r
+    if rank == 0 and not args.no_calibration and world == 1:
+        line["calibration"] = calibration_experiment(args.calib_cases)
+    if rank == 0:
         print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist

@@ -320,11 +320,18 @@ mc_status mc_profile_end(mc_ctx *ctx, double *ms_out, int32_t *launches_out);
  * device array of MC_STATIC_SCRATCH_BYTES that every GPU loading the library
  * holds until the process exits.  The first call on a device looks up that
  * array's device address, so make the first call on each device before any
- * stream capture.  A problem whose tables and one row of partial sums do not
- * fit returns MC_ERR_INVALID_ARG with a message on stderr.  Every call
- * shares the array and leaves the last call's contents in it (nothing is read
- * before this call writes it); calls that overlap on the GPU, on any stream,
- * race on it.  No checkpoints are kept (use a context for mc_vjp). */
+ * stream capture.  Each call copies the model tables into the array with one
+ * cudaMemcpyAsync from pageable host memory, which waits for the work already
+ * on the stream, unless they are byte-identical to the tables the previous
+ * call on this device uploaded (then nothing is copied).  A path range that
+ * wraps around 2^64 returns MC_ERR_INVALID_ARG.  The forward sweep's shared
+ * memory is checked first: tables beyond it return MC_ERR_UNSUPPORTED.  A
+ * problem whose tables and one row of partial sums exceed the array would
+ * return MC_ERR_INVALID_ARG, but the shared-memory limit (which holds the same
+ * tables) refuses every such problem first; that check is a backstop.  Every
+ * call shares the array and leaves the last call's contents in it (nothing is
+ * read before this call writes it); calls that overlap on the GPU, on any
+ * stream, race on it.  No checkpoints are kept (use a context for mc_vjp). */
 #define MC_STATIC_SCRATCH_BYTES ((size_t)4 << 20)
 mc_status mc_forward_static(const mc_model *model, const mc_instruments *inst, const double *theta,
                             uint64_t seed, uint64_t path0, uint64_t n_paths, double *Ey_out,

@@ -9,6 +9,7 @@
 #include <cstdlib>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <numeric>
 #include <string>
@@ -332,9 +333,53 @@ int env_int(const char *name) {
     return v ? atoi(v) : 0;
 }
 
+// Raise a kernel's dynamic shared-memory limit to at least `bytes`, never lower it: every
+// context and call that shares the kernel keeps the limit it was planned with.
+static std::mutex g_smem_mu;
+cudaError_t ensure_smem(const void *fn, size_t bytes) {
+    std::lock_guard<std::mutex> lk(g_smem_mu);
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, fn);
+    if (e != cudaSuccess) return e;
+    if ((size_t)fa.maxDynamicSharedSizeBytes >= bytes) return cudaSuccess;
+    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
 void block_caps(int *fwd, int *rev) {
     *fwd = env_int("MCAAD_MAX_BLOCKS_FWD") > 0 ? env_int("MCAAD_MAX_BLOCKS_FWD") : 0;
     *rev = env_int("MCAAD_MAX_BLOCKS_REV") > 0 ? env_int("MCAAD_MAX_BLOCKS_REV") : 0;
+}
+
+// The forward sweep's shape alone (mc_forward_static): its shared memory and
+// resident blocks, (blocks per SM) x SMs.
+mc_status forward_shape(const Plan &p, int device, const void *fwd, int nx, int *grid, size_t *smem,
+                        std::string &why) {
+    int n_sm = 1;
+    cudaError_t e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, device);
+    if (e != cudaSuccess) {
+        why = cudaGetErrorString(e);
+        return MC_ERR_CUDA;
+    }
+    const int real = p.precision == MC_FP64 ? 8 : 4;
+    *smem = SmemPlan(p.kind, real, p.m, p.n_groups, p.M, p.n_seg * p.K, nx, false).total;
+    int optin = 0;
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+    if (*smem > (size_t)optin) {
+        why = "problem tables exceed shared memory";
+        return MC_ERR_UNSUPPORTED;
+    }
+    e = ensure_smem(fwd, *smem);
+    int occ = 0;
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fwd, kBlock, *smem);
+    if (e != cudaSuccess || occ < 1) {
+        why = e != cudaSuccess ? cudaGetErrorString(e) : "path kernel does not fit on an SM";
+        return e != cudaSuccess ? MC_ERR_CUDA : MC_ERR_UNSUPPORTED;
+    }
+    int cap_fwd, cap_rev;
+    block_caps(&cap_fwd, &cap_rev);
+    if (cap_fwd > 0 && occ > cap_fwd) occ = cap_fwd;
+    *grid = occ * n_sm;
+    return MC_OK;
 }
 
 mc_status launch_shape(const Plan &p, int device, const KernelPair &kp, int nx, int *n_sm, Launch &ln,
@@ -367,7 +412,7 @@ mc_status launch_shape(const Plan &p, int device, const KernelPair &kp, int nx, 
     block_caps(&cap_fwd, &cap_rev);
     const int caps[3] = {cap_fwd, cap_fwd, cap_rev};
     for (int q = 0; q < 3; ++q) {
-        e = cudaFuncSetAttribute(fns[q], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm[q]);
+        e = ensure_smem(fns[q], sm[q]);
         if (e != cudaSuccess) {
             why = cudaGetErrorString(e);
             return MC_ERR_CUDA;
@@ -891,8 +936,6 @@ mc_status mc_normals_fill(uint64_t seed, uint64_t path0, uint32_t n_paths, uint3
 // is looked up once per device with cudaGetSymbolAddress.
 // ---------------------------------------------------------------------------
 
-#include <mutex>
-
 namespace {
 
 constexpr size_t kStaticScratchBytes = (size_t)4 << 20;  // MC_STATIC_SCRATCH_BYTES
@@ -901,6 +944,9 @@ static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBy
 constexpr int kMaxDevices = 64;
 std::mutex g_static_mu;
 unsigned char *g_static_ptr[kMaxDevices] = {nullptr};
+// The table image each device's scratch last received (host copy), so an unchanged problem
+// skips the upload.
+std::vector<unsigned char> g_static_image[kMaxDevices];
 
 }  // namespace
 
@@ -917,6 +963,10 @@ extern "C" mc_status mc_forward_static(const mc_model *model, const mc_instrumen
     if (st != MC_OK) {
         fprintf(stderr, "mc_forward_static: %s\n", why.c_str());
         return st;
+    }
+    if (path0 + n_paths < path0) {
+        fprintf(stderr, "mc_forward_static: path range wraps around 2^64\n");
+        return MC_ERR_INVALID_ARG;
     }
     if (model->normals) {
         if (path0 < model->normals_path0 || path0 + n_paths > model->normals_path0 + model->normals_rows) {
@@ -947,11 +997,9 @@ extern "C" mc_status mc_forward_static(const mc_model *model, const mc_instrumen
         }
         scratch = g_static_ptr[device];
     }
-    int n_sm = 1;
-    Launch ln;
-    st = launch_shape(p, device, kp, model->nx, &n_sm, ln, why);
-    const int grid_fwd = ln.grid_fwd;
-    const size_t smem_fwd = ln.smem_fwd;
+    int grid_fwd = 1;
+    size_t smem_fwd = 0;
+    st = forward_shape(p, device, kp.fwd, model->nx, &grid_fwd, &smem_fwd, why);
     if (st != MC_OK) {
         fprintf(stderr, "mc_forward_static: %s\n", why.c_str());
         return st;
@@ -968,20 +1016,32 @@ extern "C" mc_status mc_forward_static(const mc_model *model, const mc_instrumen
     const int fit = (int)((kStaticScratchBytes - L.total) / part_bytes);
     int grid = grid_for_paths(grid_fwd < fit ? grid_fwd : fit, n_paths, p.ppt);
     cudaStream_t s = (cudaStream_t)stream;
-    auto up = [&](size_t off, const void *src, size_t bytes) {
-        return bytes ? cudaMemcpyAsync(scratch + off, src, bytes, cudaMemcpyHostToDevice, s) : cudaSuccess;
+    // The tables as one image of the scratch's first L.total bytes, uploaded with one copy and
+    // only when it differs from the image this device last received.
+    std::vector<unsigned char> img(L.total, 0);
+    auto put = [&](size_t off, const void *src, size_t bytes) {
+        if (bytes) memcpy(img.data() + off, src, bytes);
     };
-    e = up(L.strike, p.strike.data(), p.m * 8);
-    if (e == cudaSuccess) e = up(L.disc, p.disc.data(), p.m * 8);
-    if (e == cudaSuccess) e = up(L.perm, p.perm.data(), p.m * 4);
-    if (e == cudaSuccess) e = up(L.grp_seg, p.grp_seg.data(), p.n_groups * 4);
-    if (e == cudaSuccess) e = up(L.grp_begin, p.grp_begin.data(), (p.n_groups + 1) * 4);
-    if (e == cudaSuccess) e = up(L.bucket, p.bucket.data(), p.bucket.size() * 4);
-    if (e == cudaSuccess) e = up(L.lv_jt, p.lv_jt.data(), p.lv_jt.size() * 4);
-    if (e == cudaSuccess) e = up(L.lv_a, p.lv_a.data(), p.lv_a.size() * 8);
-    if (e != cudaSuccess) {
-        fprintf(stderr, "mc_forward_static: table upload: %s\n", cudaGetErrorString(e));
-        return MC_ERR_CUDA;
+    put(L.strike, p.strike.data(), p.m * 8);
+    put(L.disc, p.disc.data(), p.m * 8);
+    put(L.perm, p.perm.data(), p.m * 4);
+    put(L.grp_seg, p.grp_seg.data(), p.n_groups * 4);
+    put(L.grp_begin, p.grp_begin.data(), (p.n_groups + 1) * 4);
+    put(L.bucket, p.bucket.data(), p.bucket.size() * 4);
+    put(L.lv_jt, p.lv_jt.data(), p.lv_jt.size() * 4);
+    put(L.lv_a, p.lv_a.data(), p.lv_a.size() * 8);
+    {
+        std::lock_guard<std::mutex> lk(g_static_mu);
+        std::vector<unsigned char> &last = g_static_image[device];
+        if (last != img) {
+            last.swap(img);
+            e = cudaMemcpyAsync(scratch, last.data(), last.size(), cudaMemcpyHostToDevice, s);
+            if (e != cudaSuccess) {
+                last.clear();
+                fprintf(stderr, "mc_forward_static: table upload: %s\n", cudaGetErrorString(e));
+                return MC_ERR_CUDA;
+            }
+        }
     }
     DevProblem pb{};
     pb.kind = p.kind;

@@ -40,8 +40,8 @@ def test_pipe_fractions(storage):
             assert math.isclose(k["pipe_fracs"][kind], want, rel_tol=1e-12)
         assert k["alu_pipe_bound"] == max(k["pipe_fracs"], key=k["pipe_fracs"].get)
     dom = r["kernels"]["forward_sweep"]  # the longer kernel
-    assert r["frac"] == max(dom["alu_frac"], dom["hbm_frac"])
-    assert r["bound"] == ("hbm" if dom["hbm_frac"] > dom["alu_frac"] else "alu")
+    assert r["bound"] == "alu" and r["frac"] == dom["alu_frac"] and r["fp32_pipe_frac"] == dom["pipe_fracs"]["fp32"]
+    assert r["hbm"]["frac"] == dom["hbm_frac"]
 
 
 def test_tangent_sweep_counts_f_and_the_tangents():
@@ -58,8 +58,8 @@ def test_measured_traffic_only_for_the_profiled_sources(monkeypatch):
     and null once they differ."""
     key = ("heston", "normals", 8, 2, "forward_sweep")
     rec = bench.MEASURED_TRAFFIC[key]
-    monkeypatch.setattr(bench, "kernel_sources_hash", lambda: rec["sources"])
+    monkeypatch.setattr(bench, "kernel_sources_hash", lambda model="heston": rec["sources"])
     assert bench.measured_traffic(*key) == rec["bytes"]
     assert bench.measured_traffic("heston", "normals", 4, 2, "forward_sweep") is None
-    monkeypatch.setattr(bench, "kernel_sources_hash", lambda: "another version")
+    monkeypatch.setattr(bench, "kernel_sources_hash", lambda model="heston": "another version")
     assert bench.measured_traffic(*key) is None

@@ -73,8 +73,11 @@ def test_loss_grad_matches_oracle(L, alpha, B):
     for name, s in omlp.SHAPES:
         a = omlp.unflatten(gv)[name]
         b = omlp.unflatten(gr)[name]
-        assert np.max(np.abs(a - b)) <= 2e-2 * np.max(np.abs(gr)), (name, np.max(np.abs(a - b)), np.max(np.abs(b)))
-    assert rel(gv, gr) <= 1e-2
+        # each parameter block against its own scale: the oracle rounds to BF16 at the kernels'
+        # storage points, so what is left is FP32 accumulation order (and the odd BF16 rounding
+        # tie it moves)
+        assert np.max(np.abs(a - b)) <= 5e-3 * np.max(np.abs(b)), (name, np.max(np.abs(a - b)), np.max(np.abs(b)))
+    assert rel(gv, gr) <= 2e-3
 
 
 def test_adam_step_matches_oracle(L):

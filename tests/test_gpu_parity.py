@@ -258,24 +258,41 @@ def test_heston_full_size(L, orc):
     check(L, orc, replace(w, problem=replace(w.problem, storage="checkpoint")), 1e-4, 2e-6)
 
 
-@pytest.mark.slow
-def test_lv_full_size_sampled(L, orc):
-    """2^22 x 500 local vol: a 2^13-path slice at the top of the range vs the oracle, and the
-    full run equals the size-weighted combination of its two halves."""
-    w = inputs.lv_config()
+def full_size_sampled(L, orc, w, n_slice):
+    """A full-size workload in the bench's context: a slice of n_slice paths at the top of the
+    range against the oracle -- E y, G and grad G of the slice, and the full run's lambda pulled
+    back through the slice (vjp) -- and the full run's E y and grad G equal the size-weighted
+    combination of its two halves (the gradient rebuilt from the halves' vjp with the full run's
+    lambda)."""
     n = w.n_paths
     ctx = L.Context(w.problem, max_paths=n)
-    p0 = n - (1 << 13)
-    Ey_s = ctx.forward(w.theta, w.problem.seed, 1 << 13, path0=p0).cpu().numpy()
-    Eo = orc.forward(w.problem, w.theta, 1 << 13, path0=p0)
-    assert rel(Ey_s, Eo) <= 2e-6
+    p0 = n - n_slice
+    Gs, gs, Eys = (x.cpu().numpy() for x in ctx.value_and_grad(w.theta, w.C, w.problem.seed, n_slice, path0=p0))
+    Eo, Go, go = orc.value_and_grad(w.problem, w.theta, w.C, n_slice, path0=p0)
+    assert rel(Eys, Eo) <= 2e-6, ("Ey", rel(Eys, Eo))
+    assert abs(Gs[0] - Go) <= 1e-4 * abs(Go), ("G", Gs[0], Go)
+    assert rel(gs, go) <= 1e-4, ("grad", rel(gs, go))
     G, g, Ey = ctx.value_and_grad(w.theta, w.C, w.problem.seed, n)
-    Ey = Ey.cpu().numpy()
+    Ey, g = Ey.cpu().numpy(), g.cpu().numpy()
+    lam = Ey - w.C
+    ctx.forward(w.theta, w.problem.seed, n_slice, path0=p0, keep=True)
+    vs = ctx.vjp(lam).cpu().numpy()
+    assert rel(vs, orc.vjp(w.problem, w.theta, lam, n_slice, path0=p0)) <= 1e-4
     h = n // 2
-    a = ctx.forward(w.theta, w.problem.seed, h).cpu().numpy()
-    b = ctx.forward(w.theta, w.problem.seed, n - h, path0=h).cpu().numpy()
+    a = ctx.forward(w.theta, w.problem.seed, h, keep=True).cpu().numpy()
+    va = ctx.vjp(lam).cpu().numpy()
+    b = ctx.forward(w.theta, w.problem.seed, n - h, path0=h, keep=True).cpu().numpy()
+    vb = ctx.vjp(lam).cpu().numpy()
     assert rel((a + b) / 2, Ey) <= 1e-12
-    assert np.all(np.isfinite(g.cpu().numpy()))
+    assert rel((va + vb) / 2, g) <= 1e-5
+    return ctx
+
+
+@pytest.mark.slow
+def test_lv_full_size_sampled(L, orc):
+    """2^22 x 500 local vol (the bench's headline workload and launch shape)."""
+    ctx = full_size_sampled(L, orc, inputs.lv_config(), 1 << 13)
+    assert ctx.storage == "normals"
 
 
 # ------------------------------------------------- Heston SLV (the paper's model)
@@ -398,32 +415,9 @@ def test_auto_storage_resolves(L):
 
 @pytest.mark.slow
 def test_slv_full_size_sampled(L, orc):
-    """Heston SLV at the bench's size (2^20 x 512, M = 95, stored normals): a 2^12-path slice at
-    the top of the range vs the oracle, and the full run equals the size-weighted combination of
-    its two halves."""
-    w = inputs.slv_config()
-    n = w.n_paths
-    ctx = L.Context(w.problem, max_paths=n)
+    """Heston SLV at the bench's size (2^20 x 512, M = 95, stored normals)."""
+    ctx = full_size_sampled(L, orc, inputs.slv_config(), 1 << 12)
     assert ctx.storage == "normals"
-    p0 = n - (1 << 12)
-    Ey_s = ctx.forward(w.theta, w.problem.seed, 1 << 12, path0=p0).cpu().numpy()
-    assert rel(Ey_s, orc.forward(w.problem, w.theta, 1 << 12, path0=p0)) <= 2e-6
-    G, g, Ey = ctx.value_and_grad(w.theta, w.C, w.problem.seed, n)
-    Ey, g = Ey.cpu().numpy(), g.cpu().numpy()
-    h = n // 2
-    ga = ctx.value_and_grad(w.theta, w.C, w.problem.seed, h)[1].cpu().numpy()
-    gb = ctx.value_and_grad(w.theta, w.C, w.problem.seed, n - h, path0=h)[1].cpu().numpy()
-    a = ctx.forward(w.theta, w.problem.seed, h).cpu().numpy()
-    b = ctx.forward(w.theta, w.problem.seed, n - h, path0=h).cpu().numpy()
-    assert rel((a + b) / 2, Ey) <= 1e-12
-    assert np.all(np.isfinite(g))
-    # the gradient is linear in lambda: rebuild it from the halves' vjp with the full run's lambda
-    lam = Ey - w.C
-    ctx.forward(w.theta, w.problem.seed, h, keep=True)
-    va = ctx.vjp(lam).cpu().numpy()
-    ctx.forward(w.theta, w.problem.seed, n - h, path0=h, keep=True)
-    vb = ctx.vjp(lam).cpu().numpy()
-    assert rel((va + vb) / 2, g) <= 1e-5
 
 
 # ------------------------------------------------------------- size limits

@@ -58,7 +58,8 @@ def test_static_forward_matches_context_forward_twice(L, kind):
 
 
 def test_static_forward_rejects_oversized_problem(L):
-    """A local-vol grid whose tables exceed the fixed scratch (and shared memory) is refused."""
+    """A local-vol grid whose tables exceed shared memory (checked before the fixed scratch, which
+    holds the same tables) is refused as unsupported."""
     lv = inputs.lv_config(n_paths=64, n_steps=100000, T=100.0, nt=20, nx=10, n_mat=1, n_strike=1)
     pl = L._ProblemC(lv.problem, torch.device("cuda"))
     thl = torch.tensor(lv.theta, dtype=torch.float64, device="cuda")
@@ -66,4 +67,17 @@ def test_static_forward_rejects_oversized_problem(L):
     st = L.load().mc_forward_static(ctypes.byref(pl.model), ctypes.byref(pl.inst),
                                     ctypes.c_void_p(thl.data_ptr()), 1, 0, 64, ctypes.c_void_p(Ey.data_ptr()),
                                     ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
-    assert st in (L.MC_ERR_INVALID_ARG, L.MC_ERR_UNSUPPORTED)
+    assert st == L.MC_ERR_UNSUPPORTED
+
+
+def test_static_forward_rejects_wrapping_path_range(L):
+    """path0 + n_paths beyond 2^64 is refused before any launch (with a normals table the wrapped
+    range would otherwise pass the table's bounds check)."""
+    w = inputs.gbm_config(n_paths=256)
+    pc = L._ProblemC(w.problem, torch.device("cuda"))
+    th = torch.tensor(w.theta, dtype=torch.float64, device="cuda")
+    Ey = torch.empty(w.problem.m, dtype=torch.float64, device="cuda")
+    st = L.load().mc_forward_static(ctypes.byref(pc.model), ctypes.byref(pc.inst), ctypes.c_void_p(th.data_ptr()),
+                                    1, (1 << 64) - 4, 16, ctypes.c_void_p(Ey.data_ptr()),
+                                    ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert st == L.MC_ERR_INVALID_ARG
