@@ -30,6 +30,8 @@
 #pragma once
 #include "mc_common.cuh"
 
+#include <type_traits>
+
 namespace mcaad {
 
 template <typename T>
@@ -378,14 +380,19 @@ struct LvModel {
             r[0] = r[1] = Real(0);
         }
     }
-    // Rows jt and jt+1 are the contiguous node range [jt*nx, (jt+2)*nx).
+    // Rows jt and jt+1 are the contiguous node range [jt*nx, (jt+2)*nx); each node's pair is read
+    // and cleared with one 2-vector access per lane (conflict-free: lanes hit consecutive pairs).
     __device__ __noinline__ static void flush_rows(Acc &a, const Shared &sh, double *wacc, int lane) {
+        using Pair = typename std::conditional<sizeof(Real) == 4, float2, double2>::type;
         const int nx = sh.nx;
         Real mine0 = Real(0), mine1 = Real(0);
         for (int k = 0; k < nx; ++k) {
-            Real *r = acc_slot(sh, k);
-            const Real s0 = warp_sum(r[0]), s1 = warp_sum(r[1]);
-            r[0] = r[1] = Real(0);
+            Pair *r = (Pair *)acc_slot(sh, k);
+            const Pair v = *r;
+            Pair z;
+            z.x = z.y = Real(0);
+            *r = z;
+            const Real s0 = warp_sum(v.x), s1 = warp_sum(v.y);
             mine0 = (lane == k) ? s0 : mine0;
             mine1 = (lane == k) ? s1 : mine1;
         }
