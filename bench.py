@@ -88,13 +88,18 @@ def kernel_bytes(model, storage, K, S, n_groups):
     return {"forward_sweep": b, "reverse_sweep": b}
 
 
-# DRAM bytes (read + write) per launch of a path kernel, from one ncu capture of
-# the bench command (profiles/); reported only while the kernel sources' code
-# (comments and layout aside) hashes to the profiled version.  Key: (model,
+# DRAM bytes (read + write) per launch of a path kernel, from one ncu capture of a small case of
+# the bench workload (profiles/), scaled to the full launch by its paths (the traffic is
+# proportional to the paths; dirty lines still in L2 when the kernel ends are not counted, so a
+# write-heavy kernel reads a little under its algorithmic bytes); reported only while the kernel
+# sources' code (comments and layout aside) hashes to the captured version.  Key: (model,
 # storage, K, paths per thread, kernel).
 MEASURED_TRAFFIC = {
-    ("heston", "normals", 8, 2, "forward_sweep"): {"bytes": 95232 + 4770265856, "sources": "ec3cdf7bd07c5dc4"},
-    ("heston", "normals", 8, 2, "reverse_sweep"): {"bytes": 4831930880 + 521984, "sources": "ec3cdf7bd07c5dc4"},
+    # 2^19 of 2^22 paths (x 8): read 1.258435 GB + write 3.349504 MB; read 189.44 KB + write 1.197627 GB
+    ("lv", "normals", 5, 2, "reverse_sweep"): {"bytes": 10094276032, "sources": "2c91e802b4f5d7dd"},
+    ("lv", "normals", 5, 2, "forward_sweep"): {"bytes": 9582531520, "sources": "2c91e802b4f5d7dd"},
+    # 2^18 of 2^20 paths (x 4): read 236.288 KB + write 1.146647 GB
+    ("heston", "normals", 8, 2, "forward_sweep"): {"bytes": 4587533152, "sources": "54f0a78454a8cd82"},
 }
 KERNEL_SOURCES = ["mc_common.cuh", "mc_paths.cuh"]
 MODEL_SOURCE = {"gbm": "mc_paths_gbm.cu", "heston": "mc_paths_heston.cu", "lv": "mc_paths_lv.cu",
