@@ -60,7 +60,7 @@ struct Bufs {
     float *z[5];         // [B][H], l = 1..4
     bf16 *h[5];          // [B][H], l = 1..4
     float *out, *obar, *loss_rows;  // [B]
-    float *outp;         // [H / kBN][B] partial dot products of F4
+    float *outp;         // [H / 32][B] partial dot products of F4, per 32-column piece
     bf16 *p[5];          // [B][H], l = 1..4
     float *g[5];         // [B][H], l = 1..3 ; g[0]: [B][NX]
     bf16 *gb0;           // [B][KX]
@@ -97,66 +97,107 @@ __device__ __forceinline__ void store_row_f32(float *D, long long ld, long long 
     for (int i = 0; i < n; i += 4) *(float4 *)(D + row * ld + c0 + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
 }
 
+// Column-per-lane helpers (tc::gemm_body with kColumns): lane j holds column `col` of the warp's
+// rows row0..row0+31, u[r] for row row0 + r.
+__device__ __forceinline__ void col_load(const float *S, long long ld, int row0, int col, float (&w)[32]) {
+#pragma unroll
+    for (int r = 0; r < 32; ++r) w[r] = S[(long long)(row0 + r) * ld + col];
+}
+__device__ __forceinline__ void col_store_f32(float *D, long long ld, int row0, int col, const float (&u)[32]) {
+#pragma unroll
+    for (int r = 0; r < 32; ++r) D[(long long)(row0 + r) * ld + col] = u[r];
+}
+__device__ __forceinline__ void col_store_bf16(bf16 *D, long long ld, int row0, int col, const float (&u)[32]) {
+#pragma unroll
+    for (int r = 0; r < 32; ++r) D[(long long)(row0 + r) * ld + col] = __float2bfloat16_rn(u[r]);
+}
+// transposed: T[col][off + row0 + r]; the lane's 32 values are 64 contiguous bytes (16-byte
+// aligned: ldt, off and row0 are multiples of 8), written as four 16-byte vectors
+__device__ __forceinline__ void col_store_t(bf16 *T, long long ldt, long long off, int row0, int col,
+                                            const float (&u)[32]) {
+    uint4 *dst = (uint4 *)(T + (long long)col * ldt + off + row0);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        __nv_bfloat162 p[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) p[k] = __floats2bfloat162_rn(u[8 * q + 2 * k], u[8 * q + 2 * k + 1]);
+        dst[q] = *(const uint4 *)p;
+    }
+}
+
 // F1..F3: z = acc + b; h = silu(z)
 struct EpiFwd {
+    static constexpr bool kColumns = true;
     const float *bias;
     float *z;
     bf16 *h;
     bf16 *hT;  // Bop_{l+1}: [H][2B], column B + row
     long long B2, Boff;
-    __device__ void apply(long long row, int c0, const float (&acc)[32], int n, int, float &) const {
+    __device__ void apply_cols(int row0, int col, const float (&u)[32], bool valid, int, int) const {
+        if (!valid) return;
+        const float b = bias[col];
         float zz[32], hh[32];
-        for (int i = 0; i < 32; ++i) {
-            zz[i] = acc[i] + bias[c0 + i];
-            hh[i] = silu(zz[i]);
+#pragma unroll
+        for (int r = 0; r < 32; ++r) {
+            zz[r] = u[r] + b;
+            hh[r] = silu(zz[r]);
         }
-        store_row_f32(z, H, row, c0, zz, n);
-        store_row_bf16(h, H, row, c0, hh, n);
-        store_t(hT, B2, Boff, row, c0, hh, n);
+        col_store_f32(z, H, row0, col, zz);
+        col_store_bf16(h, H, row0, col, hh);
+        col_store_t(hT, B2, Boff, row0, col, hh);
     }
 };
 
-// F4: as F1..F3, plus the partial dot product h . w5 of this CTA's columns
-// (outp[tile][row], summed by finish_out_kernel) and p_4 = w5 silu'(z_4).
+// F4: as F1..F3, plus the partial dot product h . w5 over this 32-column piece
+// (outp[piece][row], summed by finish_out_kernel) and p_4 = w5 silu'(z_4).
 struct EpiFwdLast {
+    static constexpr bool kColumns = true;
     const float *bias, *w5;
     float *z, *outp;
     bf16 *h, *p4, *p4T;  // p4T = Aop_4, column row
     long long B2, B;
-    int BN;
-    __device__ void apply(long long row, int c0, const float (&acc)[32], int n, int, float &acc_out) const {
-        float zz[32], hh[32], pp[32];
-        for (int i = 0; i < 32; ++i) {
-            zz[i] = acc[i] + bias[c0 + i];
-            hh[i] = silu(zz[i]);
-            pp[i] = w5[c0 + i] * dsilu(zz[i]);
-            acc_out = fmaf(hh[i], w5[c0 + i], acc_out);
+    __device__ void apply_cols(int row0, int col, const float (&u)[32], bool valid, int, int lane) const {
+        const float b = valid ? bias[col] : 0.0f, w = valid ? w5[col] : 0.0f;
+        float zz[32], hh[32], pp[32], dot[32];
+#pragma unroll
+        for (int r = 0; r < 32; ++r) {
+            zz[r] = u[r] + b;
+            hh[r] = silu(zz[r]);
+            pp[r] = w * dsilu(zz[r]);
+            dot[r] = hh[r] * w;
         }
-        store_row_f32(z, H, row, c0, zz, n);
-        store_row_bf16(h, H, row, c0, hh, n);
-        store_row_bf16(p4, H, row, c0, pp, n);
-        store_t(p4T, B2, 0, row, c0, pp, n);
-        if ((c0 + n) % BN == 0) outp[(long long)(c0 / BN) * B + row] = acc_out;
+        const float row_dot = tc::warp_sum_scatter(dot, lane);  // lane r: row row0 + r
+        outp[(long long)((col - lane) / 32) * B + row0 + lane] = row_dot;
+        if (!valid) return;
+        col_store_f32(z, H, row0, col, zz);
+        col_store_bf16(h, H, row0, col, hh);
+        col_store_bf16(p4, H, row0, col, pp);
+        col_store_t(p4T, B2, 0, row0, col, pp);
     }
 };
 
 // T4..T2: g = acc; p = g silu'(z_{l-1})
 struct EpiTan {
+    static constexpr bool kColumns = true;
     const float *zprev;
     float *g;
     bf16 *p, *pT;  // pT = Aop_{l-1}, column row
     long long B2;
-    __device__ void apply(long long row, int c0, const float (&acc)[32], int n, int, float &) const {
-        float pp[32];
-        for (int i = 0; i < 32; ++i) pp[i] = acc[i] * dsilu(zprev[row * H + c0 + i]);
-        store_row_f32(g, H, row, c0, acc, n);
-        store_row_bf16(p, H, row, c0, pp, n);
-        store_t(pT, B2, 0, row, c0, pp, n);
+    __device__ void apply_cols(int row0, int col, const float (&u)[32], bool valid, int, int) const {
+        if (!valid) return;
+        float zp[32], pp[32];
+        col_load(zprev, H, row0, col, zp);
+#pragma unroll
+        for (int r = 0; r < 32; ++r) pp[r] = u[r] * dsilu(zp[r]);
+        col_store_f32(g, H, row0, col, u);
+        col_store_bf16(p, H, row0, col, pp);
+        col_store_t(pT, B2, 0, row0, col, pp);
     }
 };
 
 // T1: g_0 = acc (16 columns, 7 valid); g0_bar on the theta columns; derivative loss
 struct EpiTanIn {
+    static constexpr bool kColumns = false;
     float *g0;
     const float *dy;  // [B][NTH] or null (inference)
     bf16 *gb0, *gb0T;  // gb0 [B][KX]; gb0T = Bop_1 [NX][2B], column row
@@ -185,76 +226,88 @@ struct EpiTanIn {
 
 // R1..R3: g_bar = acc silu'(z_l); z_bar(tangent) = acc g_l silu''(z_l)
 struct EpiTbar {
+    static constexpr bool kColumns = true;
     const float *zl, *gl;
     bf16 *gb, *gbT;  // gbT = Bop_{l+1}, column row
     float *zbt;
     long long B2;
-    __device__ void apply(long long row, int c0, const float (&acc)[32], int n, int, float &) const {
-        float a[32], t[32];
-        for (int i = 0; i < 32; ++i) {
-            const float zz = zl[row * H + c0 + i];
-            a[i] = acc[i] * dsilu(zz);
-            t[i] = acc[i] * gl[row * H + c0 + i] * d2silu(zz);
+    __device__ void apply_cols(int row0, int col, const float (&u)[32], bool valid, int, int) const {
+        if (!valid) return;
+        float zz[32], gg[32], a[32], t[32];
+        col_load(zl, H, row0, col, zz);
+        col_load(gl, H, row0, col, gg);
+#pragma unroll
+        for (int r = 0; r < 32; ++r) {
+            a[r] = u[r] * dsilu(zz[r]);
+            t[r] = u[r] * gg[r] * d2silu(zz[r]);
         }
-        store_row_bf16(gb, H, row, c0, a, n);
-        store_t(gbT, B2, 0, row, c0, a, n);
-        store_row_f32(zbt, H, row, c0, t, n);
+        col_store_bf16(gb, H, row0, col, a);
+        col_store_t(gbT, B2, 0, row0, col, a);
+        col_store_f32(zbt, H, row0, col, t);
     }
 };
 
 // R4: g_bar_4 (FP32, for dw5), and the full z_bar_4 = out_bar w5 silu'(z_4) + tangent part
 struct EpiTbarLast {
+    static constexpr bool kColumns = true;
     const float *z4, *w5, *obar;
     float *gb4f, *zb4;
     bf16 *zbb4, *zb4T;  // zb4T = Aop_4, column B + row
     long long B2, Boff;
-    __device__ void apply(long long row, int c0, const float (&acc)[32], int n, int, float &) const {
-        float a[32], zb[32];
-        const float ob = obar[row];
-        for (int i = 0; i < 32; ++i) {
-            const float zz = z4[row * H + c0 + i];
-            const float ds = dsilu(zz);
-            a[i] = acc[i] * ds;
-            const float t = acc[i] * w5[c0 + i] * d2silu(zz);
-            zb[i] = fmaf(ob * w5[c0 + i], ds, t);
+    __device__ void apply_cols(int row0, int col, const float (&u)[32], bool valid, int, int) const {
+        if (!valid) return;
+        const float w = w5[col];
+        float zz[32], a[32], zb[32];
+        col_load(z4, H, row0, col, zz);
+#pragma unroll
+        for (int r = 0; r < 32; ++r) {
+            const float ds = dsilu(zz[r]);
+            a[r] = u[r] * ds;
+            const float t = u[r] * w * d2silu(zz[r]);
+            zb[r] = fmaf(obar[row0 + r] * w, ds, t);
         }
-        store_row_f32(gb4f, H, row, c0, a, n);
-        store_row_f32(zb4, H, row, c0, zb, n);
-        store_row_bf16(zbb4, H, row, c0, zb, n);
-        store_t(zb4T, B2, Boff, row, c0, zb, n);
+        col_store_f32(gb4f, H, row0, col, a);
+        col_store_f32(zb4, H, row0, col, zb);
+        col_store_bf16(zbb4, H, row0, col, zb);
+        col_store_t(zb4T, B2, Boff, row0, col, zb);
     }
 };
 
 // D4..D2: z_bar_{l-1} = acc silu'(z_{l-1}) + z_bar_{l-1}(tangent)
 struct EpiDbar {
+    static constexpr bool kColumns = true;
     const float *zprev, *zbt;
     float *zb;
     bf16 *zbb, *zbT;  // zbb may be null (layer 1); zbT = Aop_{l-1}, column B + row
     long long B2, Boff;
-    __device__ void apply(long long row, int c0, const float (&acc)[32], int n, int, float &) const {
-        float v[32];
-        for (int i = 0; i < 32; ++i) v[i] = fmaf(acc[i], dsilu(zprev[row * H + c0 + i]), zbt[row * H + c0 + i]);
-        store_row_f32(zb, H, row, c0, v, n);
-        if (zbb) store_row_bf16(zbb, H, row, c0, v, n);
-        store_t(zbT, B2, Boff, row, c0, v, n);
+    __device__ void apply_cols(int row0, int col, const float (&u)[32], bool valid, int, int) const {
+        if (!valid) return;
+        float zp[32], tb[32], v[32];
+        col_load(zprev, H, row0, col, zp);
+        col_load(zbt, H, row0, col, tb);
+#pragma unroll
+        for (int r = 0; r < 32; ++r) v[r] = fmaf(u[r], dsilu(zp[r]), tb[r]);
+        col_store_f32(zb, H, row0, col, v);
+        if (zbb) col_store_bf16(zbb, H, row0, col, v);
+        col_store_t(zbT, B2, Boff, row0, col, v);
     }
 };
 
 // G1..G4: FP32 partial of K slice s
 struct EpiPartial {
+    static constexpr bool kColumns = true;
     float *part;
     int N;
     long long M;
-    __device__ void apply(long long row, int c0, const float (&acc)[32], int n, int ks, float &) const {
-        float *o = part + (long long)ks * M * N + row * N + c0;
-        for (int i = 0; i < 32; ++i)
-            if (i < n) o[i] = acc[i];
+    __device__ void apply_cols(int row0, int col, const float (&u)[32], bool valid, int ks, int) const {
+        if (valid) col_store_f32(part + (long long)ks * M * N, N, row0, col, u);
     }
 };
 
 template <class Epi>
-__global__ void __launch_bounds__(tc::kThreads) gemm_kernel(const tc::GemmShape g, const Epi e) {
-    tc::gemm_body(g, e);
+__global__ void __launch_bounds__(tc::kThreads) gemm_kernel(const __grid_constant__ tc::TensorMaps tm,
+                                                            const tc::GemmShape g, const Epi e) {
+    tc::gemm_body(tm, g, e);
 }
 
 // Columns per CTA for N >= 32: 32-column tiles give 256 CTAs (about two per SM) for the
@@ -267,21 +320,24 @@ template <class Epi>
 cudaError_t gemm(const bf16 *A, long long lda, const bf16 *Bm, long long ldb, int M, int N, int K, int k_slice,
                  const Epi &e, int *err, cudaStream_t st) {
     const int BN = tile_n(N);
-    tc::GemmShape g{A, lda, Bm, ldb, M, N, K, BN, k_slice, err};
-    const int kb = (k_slice / tc::kBK) < tc::kMaxKB ? (k_slice / tc::kBK) : tc::kMaxKB;
+    tc::TensorMaps tm;
+    cudaError_t r = tc::make_maps(&tm, A, lda, Bm, ldb, M, N, K, BN);
+    if (r != cudaSuccess) return r;
+    tc::GemmShape g{M, N, K, BN, k_slice, err};
+    const int kb = (k_slice / tc::kBK) < tc::kStages ? (k_slice / tc::kBK) : tc::kStages;
     const size_t smem = tc::smem_bytes(BN, kb);
-    // the largest tile any call uses (BN = kBN, four k-blocks), set once per device
+    // the largest tile any call uses (BN = kBN, a full ring), set once per device
     static bool attr_set[64] = {false};
     int dev = 0;
-    cudaError_t r = cudaGetDevice(&dev);
+    r = cudaGetDevice(&dev);
     if (r != cudaSuccess) return r;
     if (dev < 0 || dev >= 64 || !attr_set[dev]) {
         r = cudaFuncSetAttribute(gemm_kernel<Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)tc::smem_bytes(kBN, tc::kMaxKB));
+                                 (int)tc::smem_bytes(kBN, tc::kStages));
         if (r != cudaSuccess) return r;
         if (dev >= 0 && dev < 64) attr_set[dev] = true;
     }
-    gemm_kernel<Epi><<<dim3(M / tc::kBM, N / BN, K / k_slice), tc::kThreads, smem, st>>>(g, e);
+    gemm_kernel<Epi><<<dim3(M / tc::kBM, N / BN, K / k_slice), tc::kThreads, smem, st>>>(tm, g, e);
     return cudaGetLastError();
 }
 
@@ -449,7 +505,7 @@ size_t layout(unsigned char *base, int B, Bufs *out) {
     b.out = c.take<float>(B);
     b.obar = c.take<float>(B);
     b.loss_rows = c.take<float>(B);
-    b.outp = c.take<float>((size_t)(H / kBN) * B);
+    b.outp = c.take<float>((size_t)(H / 32) * B);
     for (int l = 1; l <= 4; ++l) b.p[l] = c.take<bf16>(BH);
     b.g[0] = c.take<float>((size_t)B * NX);
     for (int l = 1; l <= 3; ++l) b.g[l] = c.take<float>(BH);
@@ -498,10 +554,10 @@ cudaError_t run_forward(mlp_ctx *c, const float *prm, const float *y, const floa
         if (e != cudaSuccess) return e;
     }
     {
-        EpiFwdLast ep{prm + ob4, prm + ow5, b.z[4], b.outp, b.h[4], b.p[4], b.Aop[4], B2, B, kBN};
+        EpiFwdLast ep{prm + ob4, prm + ow5, b.z[4], b.outp, b.h[4], b.p[4], b.Aop[4], B2, B};
         e = gemm(b.h[3], H, b.Wb[4], H, B, H, H, H, ep, b.err, st);
         if (e != cudaSuccess) return e;
-        finish_out_kernel<<<grid_for(B), 256, 0, st>>>(b.outp, H / kBN, B, prm + ob5, y, inv_b, b.out, b.obar,
+        finish_out_kernel<<<grid_for(B), 256, 0, st>>>(b.outp, H / 32, B, prm + ob5, y, inv_b, b.out, b.obar,
                                                       b.loss_rows);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;

@@ -4,17 +4,27 @@
 //
 // One CTA of 128 threads computes a 128 x BN tile (BN <= 256, a multiple of
 // 16) of D: blockIdx.x picks the 128 rows, blockIdx.y the BN columns and
-// blockIdx.z the K slice when K is split.  Operand
-// k-blocks of 64 elements (128 bytes per row) are copied to shared memory with
-// 16-byte cp.async in the 128-byte-swizzle K-major layout (row r at r*128 B,
-// 16-byte chunk c stored at chunk c ^ (r & 7), tiles 1024-byte aligned), up to
-// four k-blocks per round; thread 0 issues four m128 x nN x k16 MMAs per
-// k-block and commits them to an mbarrier; the epilogue reads each warp's 32
-// accumulator rows (TMEM lanes 32w..32w+31) in 32-column pieces with
-// tcgen05.ld and hands them to the epilogue functor.  Every wait on the
-// mbarrier has an iteration limit; on expiry the kernel records an error code
-// and returns after freeing its tensor memory.
+// blockIdx.z the K slice when K is split.  Operand k-blocks of 64 elements
+// (128 bytes per row) arrive in shared memory by TMA (cp.async.bulk.tensor,
+// 128-byte swizzle: row r at r*128 B, 16-byte chunk c at chunk c ^ (r & 7),
+// tiles 1024-byte aligned) into a ring of up to kStages stages:
+//   lane 0 of warp 0 (producer) waits until a stage is free (its "empty"
+//     mbarrier), arms its "full" mbarrier with the stage's byte count and
+//     issues the A and B tile loads;
+//   lane 0 of warp 1 (MMA issuer) waits for a stage's "full" mbarrier, issues
+//     four m128 x nN x k16 MMAs and commits them to the stage's "empty"
+//     mbarrier, which the tensor cores arrive on once they have read the
+//     stage -- so the loads of later k-blocks overlap the MMAs of earlier
+//     ones; after the last k-block it commits to the "done" mbarrier;
+//   all four warps wait for "done" and run the epilogue: each warp reads its
+//     32 accumulator rows (TMEM lanes 32w..32w+31) in 32-column pieces with
+//     tcgen05.ld and hands them to the epilogue functor.
+// Every mbarrier wait has an iteration limit; on expiry the kernel records an
+// error code, waits (again with a limit) for the loads it issued, frees its
+// tensor memory and returns.
 #pragma once
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -25,15 +35,22 @@ namespace tc {
 constexpr int kThreads = 128;
 constexpr int kBM = 128;       // rows per CTA (one TMEM lane per row)
 constexpr int kBK = 64;        // k-block: 64 BF16 = 128 bytes per row
-constexpr int kMaxKB = 4;      // k-blocks per load round
+constexpr int kStages = 4;     // shared-memory ring depth
 constexpr uint32_t kWaitLimit = 1u << 22;
 
 __host__ __device__ constexpr size_t tile_a_bytes() { return (size_t)kBM * kBK * 2; }
 __host__ __device__ constexpr size_t tile_b_bytes(int n) { return (size_t)n * kBK * 2; }
-// dynamic shared memory: 1024 B alignment slack + KB rounds of A and B tiles + barrier words
-__host__ __device__ constexpr size_t smem_bytes(int n, int kb) {
-    return 1024 + (size_t)kb * (tile_a_bytes() + tile_b_bytes(n)) + 64;
+// dynamic shared memory: 1024 B alignment slack + `stages` ring stages of A and B tiles +
+// barrier words (full[kStages], empty[kStages], done) and the TMEM address slot
+__host__ __device__ constexpr size_t smem_bytes(int n, int stages) {
+    return 1024 + (size_t)stages * (tile_a_bytes() + tile_b_bytes(n)) + 8 * (2 * kStages + 1) + 8;
 }
+
+// The two operands' TMA descriptors (built on the host by make_tensor_maps), passed by value
+// as one __grid_constant__ kernel parameter so that their addresses are valid for TMA.
+struct TensorMaps {
+    CUtensorMap a, b;
+};
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -67,11 +84,24 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64
         "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
 }
 
+// The mbarrier at `bar` receives one arrival when all previously issued MMAs of this thread
+// have completed (and so have finished reading their shared-memory operands).
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
                  : "memory");
 }
 
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
+}
+
+// Arrive on `bar` and add `bytes` to the transaction count its current phase waits for.
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+// Bounded wait for the completion of the phase with parity `phase`; false once the limit
+// expires.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase) {
     for (uint32_t it = 0; it < kWaitLimit; ++it) {
         uint32_t ok;
@@ -87,8 +117,14 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase) {
     return false;
 }
 
-__device__ __forceinline__ void cp_async16(uint32_t saddr, const void *g) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(saddr), "l"(g) : "memory");
+// TMA: the box at coordinates (x = k element, y = row) of the 2-D tensor map into shared
+// memory at `dst`, completing `bytes` of the transaction count of mbarrier `bar`.
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            dst),
+        "l"((uint64_t)map), "r"(x), "r"(y), "r"(bar)
+        : "memory");
 }
 
 // 32 consecutive FP32 accumulator columns of this thread's row.
@@ -127,34 +163,53 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[32]) {
 }
 
 struct GemmShape {
-    const __nv_bfloat16 *A;
-    long long lda;  // elements between rows of A (>= K, multiple of 8)
-    const __nv_bfloat16 *B;
-    long long ldb;
     int M, N, K;    // M % 128 == 0, N % BN == 0, K % 64 == 0
     int BN;         // columns per CTA: a multiple of 16, at most 256; gridDim.y = N / BN
     int k_slice;    // K per CTA (a multiple of 64); gridDim.z = K / k_slice
     int *err;       // set to 1 if an mbarrier wait expired
 };
 
-// The GEMM body; Epi::apply(row, col0, v[32], ncols, kslice, state) consumes
+// Warp reduce-scatter: lane r returns the sum over the 32 lanes of their x[r] (a butterfly that
+// halves the values each step: 31 shuffles for 32 sums).
+__device__ __forceinline__ float warp_sum_scatter(float (&x)[32], int lane) {
+#pragma unroll
+    for (int o = 16, n = 32; o >= 1; o >>= 1, n >>= 1) {
+        const bool up = (lane & o) != 0;
+#pragma unroll
+        for (int j = 0; j < n / 2; ++j) {
+            const float keep = up ? x[j + n / 2] : x[j];
+            const float send = up ? x[j] : x[j + n / 2];
+            x[j] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+    }
+    return x[0];
+}
+
+// The GEMM body.  With Epi::kColumns false, Epi::apply(row, col0, v[32], ncols, kslice, state) consumes
 // the accumulator columns col0..col0+ncols-1 (global column indices) of
 // global row `row`, in increasing col0 within this CTA's BN columns; `state`
 // is a per-thread float the epilogue may carry from one piece of its row to
-// the next (it starts at 0).
+// the next (it starts at 0).  With Epi::kColumns true, Epi::apply_cols(row0, col, u[32], valid,
+// kslice, lane) receives in lane j the column col = col0 + j of the warp's 32 rows row0..row0+31
+// (u[r] for row row0 + r; valid is false for columns beyond N).  tm.a maps A as a 2-D tensor (K contiguous, M
+// rows) with a 64 x 128 box, tm.b maps B (K contiguous, N rows) with a
+// 64 x BN box, both 128-byte swizzled.
 template <class Epi>
-__device__ __forceinline__ void gemm_body(const GemmShape &g, const Epi &epi) {
+__device__ __forceinline__ void gemm_body(const TensorMaps &tm, const GemmShape &g, const Epi &epi) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *base = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     const int N = g.BN;
     const int kb_total = g.k_slice / kBK;
-    const int kb_round = kb_total < kMaxKB ? kb_total : kMaxKB;
+    const int S = kb_total < kStages ? kb_total : kStages;
     unsigned char *tA = base;
-    unsigned char *tB = base + (size_t)kb_round * tile_a_bytes();
-    uint64_t *bar = (uint64_t *)(tB + (size_t)kb_round * tile_b_bytes(N));
-    uint32_t *tslot = (uint32_t *)(bar + 1);
+    unsigned char *tB = base + (size_t)S * tile_a_bytes();
+    uint64_t *bars = (uint64_t *)(tB + (size_t)S * tile_b_bytes(N));  // full[kStages], empty[kStages], done
+    uint32_t *tslot = (uint32_t *)(bars + 2 * kStages + 1);
+    volatile int *fail = (volatile int *)(tslot + 1);  // set by the producer or MMA lane on an expired wait
     const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
     const uint32_t ncols = N <= 32 ? 32u : (N <= 64 ? 64u : (N <= 128 ? 128u : 256u));
+    const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + kStages), done = smem_u32(bars + 2 * kStages);
+    const uint32_t stage_bytes = (uint32_t)(tile_a_bytes() + tile_b_bytes(N));
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
@@ -162,66 +217,108 @@ __device__ __forceinline__ void gemm_body(const GemmShape &g, const Epi &epi) {
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(1));
+        *fail = 0;
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(full0 + 8 * s, 1);
+            mbar_init(empty0 + 8 * s, 1);
+        }
+        mbar_init(done, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tm.a) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tm.b) : "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tslot;
-    const uint32_t bar_s = smem_u32(bar);
-    const uint32_t idesc = idesc_bf16(kBM, N);
-    const long long row0 = (long long)blockIdx.x * kBM;
-    const long long col_base = (long long)blockIdx.y * g.BN;
-    const long long kbase = (long long)blockIdx.z * g.k_slice;
-    uint32_t phase = 0;
+    const int row0 = blockIdx.x * kBM;
+    const int col_base = blockIdx.y * g.BN;
+    const int kbase = blockIdx.z * g.k_slice;
     bool ok = true;
 
-    for (int kb0 = 0; kb0 < kb_total && ok; kb0 += kb_round) {
-        const int nkb = (kb_total - kb0) < kb_round ? (kb_total - kb0) : kb_round;
-        // A: 128 rows x 8 chunks per k-block; B: N rows x 8 chunks per k-block
-        for (int q = tid; q < nkb * kBM * 8; q += kThreads) {
-            const int kb = q / (kBM * 8), rem = q - kb * (kBM * 8), r = rem >> 3, c = rem & 7;
-            const __nv_bfloat16 *src = g.A + (row0 + r) * g.lda + kbase + (long long)(kb0 + kb) * kBK + c * 8;
-            cp_async16(smem_u32(tA + kb * tile_a_bytes() + r * 128 + ((c ^ (r & 7)) << 4)), src);
-        }
-        for (int q = tid; q < nkb * N * 8; q += kThreads) {
-            const int kb = q / (N * 8), rem = q - kb * (N * 8), r = rem >> 3, c = rem & 7;
-            const __nv_bfloat16 *src = g.B + (col_base + r) * g.ldb + kbase + (long long)(kb0 + kb) * kBK + c * 8;
-            cp_async16(smem_u32(tB + kb * tile_b_bytes(N) + r * 128 + ((c ^ (r & 7)) << 4)), src);
-        }
-        asm volatile("cp.async.wait_all;" ::: "memory");
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        if (tid == 0) {
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            for (int kb = 0; kb < nkb; ++kb) {
-                const uint32_t a0 = smem_u32(tA + kb * tile_a_bytes());
-                const uint32_t b0 = smem_u32(tB + kb * tile_b_bytes(N));
-#pragma unroll
-                for (int k = 0; k < kBK / 16; ++k) {
-                    mma_bf16(tmem, desc_sw128(a0 + k * 32), desc_sw128(b0 + k * 32), idesc,
-                             (kb0 + kb + k) > 0 ? 1u : 0u);
+    if (warp == 0) {
+        if (lane == 0) {
+            // producer: k-block kb goes to stage kb % S; from the second round on, the stage is
+            // reused once the MMAs that read it have completed (its empty barrier's phase)
+            int issued = 0;
+            for (int kb = 0; kb < kb_total; ++kb) {
+                const int s = kb % S;
+                if (kb >= S && !mbar_wait(empty0 + 8 * s, (uint32_t)((kb / S - 1) & 1))) {
+                    ok = false;
+                    break;
                 }
+                mbar_arrive_expect_tx(full0 + 8 * s, stage_bytes);
+                tma_load_2d(smem_u32(tA + (size_t)s * tile_a_bytes()), &tm.a, kbase + kb * kBK, row0, full0 + 8 * s);
+                tma_load_2d(smem_u32(tB + (size_t)s * tile_b_bytes(N)), &tm.b, kbase + kb * kBK, col_base,
+                            full0 + 8 * s);
+                ++issued;
             }
-            mma_commit(bar_s);
+            // before anything can leave: the loads of the last round have landed (bounded)
+            for (int kb = issued - S < 0 ? 0 : issued - S; kb < issued; ++kb)
+                if (!mbar_wait(full0 + 8 * (kb % S), (uint32_t)((kb / S) & 1))) ok = false;
+            if (!ok) *fail = 1;
         }
-        ok = mbar_wait(bar_s, phase);
-        phase ^= 1u;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        __syncthreads();
+        __syncwarp();
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // MMA issuer
+            const uint32_t idesc = idesc_bf16(kBM, N);
+            for (int kb = 0; kb < kb_total; ++kb) {
+                const int s = kb % S;
+                if (!mbar_wait(full0 + 8 * s, (uint32_t)((kb / S) & 1))) {
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t a0 = smem_u32(tA + (size_t)s * tile_a_bytes());
+                const uint32_t b0 = smem_u32(tB + (size_t)s * tile_b_bytes(N));
+#pragma unroll
+                for (int k = 0; k < kBK / 16; ++k)
+                    mma_bf16(tmem, desc_sw128(a0 + k * 32), desc_sw128(b0 + k * 32), idesc, (kb + k) > 0 ? 1u : 0u);
+                mma_commit(empty0 + 8 * s);
+            }
+            // "done" arrives when every MMA issued above has completed (also after an expired
+            // wait, so that no MMA is still running when the tensor memory is freed)
+            mma_commit(done);
+            if (!ok) *fail = 1;
+        }
+        __syncwarp();
     }
-    if (!ok) {
+    ok = mbar_wait(done, 0u) && ok;
+    if (!ok) *fail = 1;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (*fail) {
         if (tid == 0 && g.err) atomicExch(g.err, 1);
+    } else if constexpr (Epi::kColumns) {
+        // column-per-lane epilogue: each 32 x 32 piece of the warp's rows goes through shared
+        // memory (the drained ring; pitch 33 floats, conflict-free both ways), so that lane j
+        // holds column col_base + c0 + j of the warp's 32 rows and the functor's loads and
+        // row-major stores are coalesced across lanes
+        float *stage = (float *)base + warp * 32 * 33;
+        const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+        for (int c0 = 0; c0 < N; c0 += 32) {
+            float v[32];
+            if (N - c0 >= 32) tmem_ld32(trow + (uint32_t)c0, v);
+            else tmem_ld16(trow + (uint32_t)c0, v);
+#pragma unroll
+            for (int i = 0; i < 32; ++i) stage[lane * 33 + i] = v[i];
+            __syncwarp();
+            float u[32];
+#pragma unroll
+            for (int r = 0; r < 32; ++r) u[r] = stage[r * 33 + lane];
+            __syncwarp();
+            epi.apply_cols(row0 + warp * 32, col_base + c0 + lane, u, lane < N - c0, (int)blockIdx.z, lane);
+        }
     } else {
-        const long long row = row0 + warp * 32 + lane;
+        const int row = row0 + warp * 32 + lane;
         const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
         float state = 0.0f;
         for (int c0 = 0; c0 < N; c0 += 32) {
             float v[32];
             if (N - c0 >= 32) tmem_ld32(trow + (uint32_t)c0, v);
             else tmem_ld16(trow + (uint32_t)c0, v);
-            epi.apply(row, (int)col_base + c0, v, (N - c0) < 32 ? (N - c0) : 32, blockIdx.z, state);
+            epi.apply((long long)row, col_base + c0, v, (N - c0) < 32 ? (N - c0) : 32, blockIdx.z, state);
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -229,6 +326,41 @@ __device__ __forceinline__ void gemm_body(const GemmShape &g, const Epi &epi) {
     if (warp == 0) {
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols));
     }
+}
+
+// Host: the TMA descriptor of a BF16 operand stored as `rows` rows of `cols` elements (K
+// contiguous) with a row pitch of `ld` elements, loaded in boxes of 64 elements x `box_rows`
+// rows with the 128-byte swizzle the MMA descriptors expect.  The encoder comes from the driver
+// through the runtime's entry-point query (no link against the driver library).  The base address
+// and the pitch must be multiples of 16 bytes (checked by the encoder).
+inline cudaError_t make_map(CUtensorMap *map, const void *ptr, long long ld, long long cols, long long rows,
+                            int box_rows) {
+    static const PFN_cuTensorMapEncodeTiled_v12000 encode = []() -> PFN_cuTensorMapEncodeTiled_v12000 {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return nullptr;
+        return (PFN_cuTensorMapEncodeTiled_v12000)fn;
+    }();
+    if (!encode) return cudaErrorNotSupported;
+    const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+    const cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(ptr), dims, strides, box,
+                              estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+// Host: both descriptors of D[M x N] = A[M x K] B[N x K]^T with N-tiles of BN columns.
+inline cudaError_t make_maps(TensorMaps *tm, const void *A, long long lda, const void *B, long long ldb, int M, int N,
+                             int K, int BN) {
+    cudaError_t e = make_map(&tm->a, A, lda, K, M, kBM);
+    if (e == cudaSuccess) e = make_map(&tm->b, B, ldb, K, N, BN);
+    return e;
 }
 
 }  // namespace tc
