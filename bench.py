@@ -366,8 +366,7 @@ def surrogate_step_bench(args, rank, world):
     sur = surrogate.Surrogate(batch=B, device=dev)
 
     def step(t):
-        sur.train_net.loss_grad(sur.params, X, y, dy, 1.0, sur.grads, sur.loss)
-        sur.train_net.adam_step(sur.params, sur.grads, sur.m, sur.v, t, lr=1e-4)
+        sur.train_net.train_step(sur.params, X, y, dy, 1.0, sur.grads, sur.loss, sur.m, sur.v, t, lr=1e-4)
 
     for t in range(1, max(args.warmup, 3) + 1):
         step(t)

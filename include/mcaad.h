@@ -278,6 +278,18 @@ mc_status mlp_loss_grad(mlp_ctx *ctx, const float *params, const float *X, const
  * BF16 weight copies are refreshed. */
 mc_status mlp_adam_step(mlp_ctx *ctx, float *params, const float *grads, float *m, float *v, int32_t t, float lr,
                         float beta1, float beta2, float eps, void *stream);
+/* One training step: mlp_loss_grad on the batch (X [batch][7], y [batch], dy [batch][5]), then
+ * mlp_adam_step t with learning rate lr (no counterpart in the paper: the learned surrogate).
+ * The batch is first copied into buffers of the context, so the caller's batch may live
+ * anywhere and change every step.  The first call with a given set of params, grads, loss_out,
+ * m and v buffers and (alpha, beta1, beta2, eps) runs eagerly and then records the step as a
+ * CUDA graph on a stream of the context; later calls with the same set replay that graph on
+ * `stream`, with only t and lr changed, which removes the per-kernel launch cost of the ~40
+ * kernels of a step.  Results equal those of mlp_loss_grad followed by mlp_adam_step.  Calls on
+ * one context must not overlap on the GPU (they share its buffers). */
+mc_status mlp_train_step(mlp_ctx *ctx, float *params, const float *X, const float *y, const float *dy, float alpha,
+                         float *grads, float *loss_out, float *m, float *v, int32_t t, float lr, float beta1,
+                         float beta2, float eps, void *stream);
 /* Host copy of the tensor-core wait-expiry flag (0 = every wait completed). Synchronous. */
 mc_status mlp_error_flag(mlp_ctx *ctx, int32_t *flag_host);
 

@@ -98,6 +98,8 @@ SIGNATURES = [
     ("mlp_loss_grad", ctypes.c_int, [_V, _V, _V, _V, _V, ctypes.c_float, _V, _V, _V]),
     ("mlp_adam_step", ctypes.c_int, [_V, _V, _V, _V, _V, _I32, ctypes.c_float, ctypes.c_float, ctypes.c_float,
                                      ctypes.c_float, _V]),
+    ("mlp_train_step", ctypes.c_int, [_V, _V, _V, _V, _V, ctypes.c_float, _V, _V, _V, _V, _I32, ctypes.c_float,
+                                      ctypes.c_float, ctypes.c_float, ctypes.c_float, _V]),
     ("mlp_error_flag", ctypes.c_int, [_V, _P(_I32)]),
 ]
 KERNEL_NAMES = ["forward_sweep", "finalize_y", "seed", "reverse_sweep", "finalize_grad", "tangent_sweep",
@@ -381,6 +383,14 @@ class Mlp:
     def adam_step(self, params, grads, m, v, t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
         _check(load().mlp_adam_step(self.handle, _ptr(params), _ptr(grads), _ptr(m), _ptr(v), int(t), float(lr),
                                     float(beta1), float(beta2), float(eps), _stream(stream)), what="mlp_adam_step")
+
+    def train_step(self, params, X, y, dy, alpha, grads, loss, m, v, t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8,
+                   stream=None):
+        """mlp_loss_grad then mlp_adam_step, replayed as a captured graph after the first call."""
+        _check(load().mlp_train_step(self.handle, _ptr(params), _ptr(X), _ptr(y), _ptr(dy), float(alpha), _ptr(grads),
+                                     _ptr(loss) if loss is not None else None, _ptr(m), _ptr(v), int(t), float(lr),
+                                     float(beta1), float(beta2), float(eps), _stream(stream)),
+               what="mlp_train_step")
 
     def error_flag(self):
         f = ctypes.c_int32(0)

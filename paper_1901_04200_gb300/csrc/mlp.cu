@@ -25,6 +25,8 @@
 
 #include <cstdio>
 #include <new>
+#include <utility>
+#include <vector>
 
 #include "mcaad.h"
 #include "tc_gemm.cuh"
@@ -71,10 +73,11 @@ struct Bufs {
     bf16 *zbb[5];        // [B][H], l = 2..4
     bf16 *Aop[5];        // [H][2B]
     bf16 *Bop[5];        // l = 1: [NX][2B], else [H][2B]
-    float *part;         // [kSplit][H][H]
+    float *part[5];      // l = 1..4: [kSplit][H][N_l] split-K partials of dW_l
     float *colpart;      // [B / 128][41 * 32] column-sum chunks
     bf16 *Wb[5], *Wt[5];  // W1b [H][KX], W1t [NX][H], Wlb/Wlt [H][H]
     float *lsum;         // [1] loss scratch
+    float *Xin, *yin, *dyin;  // [B][7], [B], [B][5]: the batch of mlp_train_step (fixed addresses)
     int *err;            // [1] tensor-core wait expiry flag
 };
 
@@ -316,28 +319,47 @@ __global__ void __launch_bounds__(tc::kThreads) gemm_kernel(const __grid_constan
 constexpr int kBN = 32;
 __host__ __device__ constexpr int tile_n(int N) { return N >= kBN ? kBN : N; }
 
+// Launch with programmatic stream serialization: the kernel may start while the previous kernel
+// in the stream finishes; every kernel launched this way calls tc::pdl_wait before it reads what
+// its predecessors wrote.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, Args &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k, std::forward<Args>(args)...);
+}
+
 template <class Epi>
 cudaError_t gemm(const bf16 *A, long long lda, const bf16 *Bm, long long ldb, int M, int N, int K, int k_slice,
-                 const Epi &e, int *err, cudaStream_t st) {
-    const int BN = tile_n(N);
+                 const Epi &e, int *err, cudaStream_t st, int bn = 0) {
+    const int BN = bn ? bn : tile_n(N);
     tc::TensorMaps tm;
     cudaError_t r = tc::make_maps(&tm, A, lda, Bm, ldb, M, N, K, BN);
     if (r != cudaSuccess) return r;
     tc::GemmShape g{M, N, K, BN, k_slice, err};
     const int kb = (k_slice / tc::kBK) < tc::kStages ? (k_slice / tc::kBK) : tc::kStages;
     const size_t smem = tc::smem_bytes(BN, kb);
-    // the largest tile any call uses (BN = kBN, a full ring), set once per device
+    // the largest tile any call uses (BN = 256, a full ring), set once per device
     static bool attr_set[64] = {false};
     int dev = 0;
     r = cudaGetDevice(&dev);
     if (r != cudaSuccess) return r;
     if (dev < 0 || dev >= 64 || !attr_set[dev]) {
         r = cudaFuncSetAttribute(gemm_kernel<Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)tc::smem_bytes(kBN, tc::kStages));
+                                 (int)tc::smem_bytes(256, tc::kStages));
         if (r != cudaSuccess) return r;
         if (dev >= 0 && dev < 64) attr_set[dev] = true;
     }
-    gemm_kernel<Epi><<<dim3(M / tc::kBM, N / BN, K / k_slice), tc::kThreads, smem, st>>>(tm, g, e);
+    r = launch_pdl(gemm_kernel<Epi>, dim3(M / tc::kBM, N / BN, K / k_slice), dim3(tc::kThreads), smem, st, tm, g, e);
+    if (r != cudaSuccess) return r;
     return cudaGetLastError();
 }
 
@@ -345,6 +367,8 @@ cudaError_t gemm(const bf16 *A, long long lda, const bf16 *Bm, long long ldb, in
 
 // X [n_rows][7] FP32 -> x0 [B][KX] BF16 (zero padding) and X^T into Bop_1 columns B + row.
 __global__ void prep_input_kernel(const float *__restrict__ X, int n_rows, int B, bf16 *x0, bf16 *xT, long long B2) {
+    tc::pdl_wait();
+    tc::pdl_trigger();
     for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < B * DIN; q += gridDim.x * blockDim.x) {
         const int r = q / DIN, j = q - r * DIN;
         const float v = r < n_rows ? X[(long long)r * DIN + j] : 0.0f;
@@ -357,6 +381,8 @@ __global__ void prep_input_kernel(const float *__restrict__ X, int n_rows, int B
 // FP32 parameters -> BF16 W_l (row-major, layer 1 padded to KX columns) and W_l^T.
 __global__ void weights_to_bf16_kernel(const float *__restrict__ prm, bf16 *W1b, bf16 *W1t, bf16 *W2b, bf16 *W2t,
                                        bf16 *W3b, bf16 *W3t, bf16 *W4b, bf16 *W4t) {
+    tc::pdl_wait();
+    tc::pdl_trigger();
     for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < 3 * H * H + H * DIN; q += gridDim.x * blockDim.x) {
         if (q < H * DIN) {
             const int n = q / DIN, k = q - n * DIN;
@@ -381,6 +407,8 @@ __global__ void weights_to_bf16_kernel(const float *__restrict__ prm, bf16 *W1b,
 __global__ void finish_out_kernel(const float *__restrict__ outp, int ntile, int B, const float *__restrict__ b5,
                                   const float *__restrict__ y, float inv_b, float *out, float *obar,
                                   float *loss_rows) {
+    tc::pdl_wait();
+    tc::pdl_trigger();
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < B; r += gridDim.x * blockDim.x) {
         float o = b5[0];
         for (int t = 0; t < ntile; ++t) o += outp[(long long)t * B + r];
@@ -393,13 +421,25 @@ __global__ void finish_out_kernel(const float *__restrict__ outp, int ntile, int
     }
 }
 
-// dW_l[i][k] = sum over K slices in order (layer 1: k < 7 of the 16 computed columns).
-__global__ void reduce_split_kernel(const float *__restrict__ part, int N, int ncopy, float *dW) {
-    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < H * ncopy; q += gridDim.x * blockDim.x) {
-        const int i = q / ncopy, k = q - i * ncopy;
+// dW_l[i][k] = sum over K slices in order, all four layers in one launch (layer 1: k < 7 of the
+// 16 computed columns).
+struct Partials {
+    const float *part[5];
+};
+__global__ void reduce_split_kernel(const Partials pp, float *grads) {
+    tc::pdl_wait();
+    tc::pdl_trigger();
+    constexpr long long n1 = (long long)H * DIN, nl = (long long)H * H;
+    for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n1 + 3 * nl;
+         q += (long long)gridDim.x * blockDim.x) {
+        const int l = q < n1 ? 1 : 2 + (int)((q - n1) / nl);
+        const long long e = q < n1 ? q : (q - n1) % nl;
+        const int ncopy = l == 1 ? DIN : H, N = l == 1 ? NX : H;
+        const long long i = e / ncopy, k = e - i * ncopy;
+        const float *part = pp.part[l];
         float s = 0.0f;
         for (int sl = 0; sl < kSplit; ++sl) s += part[((long long)sl * H + i) * N + k];
-        dW[q] = s;
+        grads[oW(l) + e] = s;
     }
 }
 
@@ -414,6 +454,8 @@ constexpr int kColChunk = 128;
 constexpr int kColOut = 41 * 32;
 
 __global__ void __launch_bounds__(256) colsum_kernel(const Bufs b, float *colpart) {
+    tc::pdl_wait();
+    tc::pdl_trigger();
     __shared__ float red[8][33];
     const int q = blockIdx.x, chunk = blockIdx.y, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int r0 = chunk * kColChunk, r1 = min(b.B, r0 + kColChunk);
@@ -438,6 +480,8 @@ __global__ void __launch_bounds__(256) colsum_kernel(const Bufs b, float *colpar
 }
 
 __global__ void colsum_finish_kernel(const float *__restrict__ colpart, int n_chunks, float *grads, float *loss_out) {
+    tc::pdl_wait();
+    tc::pdl_trigger();
     for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < kColOut; o += gridDim.x * blockDim.x) {
         float t = 0.0f;
         for (int c = 0; c < n_chunks; ++c) t += colpart[(long long)c * kColOut + o];
@@ -449,16 +493,45 @@ __global__ void colsum_finish_kernel(const float *__restrict__ colpart, int n_ch
     }
 }
 
-// Adam (Kingma & Ba) on the FP32 master parameters; t counts from 1.
+// The BF16 weight copies the GEMMs read (W_l row-major, layer 1 padded to KX columns, and W_l^T).
+struct WCopies {
+    bf16 *Wb[5], *Wt[5];
+};
+__device__ __forceinline__ void put_weight_bf16(const WCopies &w, long long q, float val) {
+    if (q < oW1 + H * DIN) {
+        const int n = (int)(q / DIN), k = (int)(q - (long long)n * DIN);
+        const bf16 b = __float2bfloat16_rn(val);
+        w.Wb[1][n * KX + k] = b;
+        w.Wt[1][k * H + n] = b;
+        return;
+    }
+    for (int l = 2; l <= 4; ++l) {
+        const long long e = q - oW(l);
+        if (e >= 0 && e < (long long)H * H) {
+            const int n = (int)(e / H), k = (int)(e - (long long)n * H);
+            const bf16 b = __float2bfloat16_rn(val);
+            w.Wb[l][n * H + k] = b;
+            w.Wt[l][k * H + n] = b;
+            return;
+        }
+    }
+}
+
+// Adam (Kingma & Ba) on the FP32 master parameters (t counts from 1, c1 and c2 its bias
+// corrections), and the BF16 copies of the updated weights.
 __global__ void adam_kernel(float *prm, const float *__restrict__ g, float *m, float *v, long long n, float lr,
-                            float b1, float b2, float eps, float c1, float c2) {
+                            float b1, float b2, float eps, float c1, float c2, const WCopies w) {
+    tc::pdl_wait();
+    tc::pdl_trigger();
     for (long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (long long)gridDim.x * blockDim.x) {
         const float gg = g[q];
         const float mm = fmaf(b1, m[q], (1.0f - b1) * gg);
         const float vv = fmaf(b2, v[q], (1.0f - b2) * gg * gg);
         m[q] = mm;
         v[q] = vv;
-        prm[q] -= lr * (mm * c1) / (sqrtf(vv * c2) + eps);
+        const float p = prm[q] - lr * (mm * c1) / (sqrtf(vv * c2) + eps);
+        prm[q] = p;
+        put_weight_bf16(w, q, p);
     }
 }
 
@@ -473,12 +546,25 @@ int grid_for(long long work) {
 using namespace mcaad;
 using namespace mcaad::mlp;
 
+// A captured training step (mlp_train_step): the graph of loss and gradient, Adam and the weight
+// refresh for one set of caller buffers, and its Adam node (whose learning rate and bias
+// corrections change every step).
+struct TrainGraph {
+    cudaStream_t cap = nullptr;  // private stream the step is captured on
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphNode_t adam = nullptr;
+    const void *key[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // params, grads, loss, m, v
+    float alpha = 0, beta1 = 0, beta2 = 0, eps = 0;
+};
+
 struct mlp_ctx {
     int device = 0;
     int B = 0;
     Bufs b{};
     unsigned char *ws = nullptr;
     bool owns = false;
+    TrainGraph tg;
 };
 
 namespace {
@@ -518,7 +604,7 @@ size_t layout(unsigned char *base, int B, Bufs *out) {
     for (int l = 1; l <= 4; ++l) b.Aop[l] = c.take<bf16>(H * B2);
     b.Bop[1] = c.take<bf16>(NX * B2);
     for (int l = 2; l <= 4; ++l) b.Bop[l] = c.take<bf16>(H * B2);
-    b.part = c.take<float>((size_t)kSplit * H * H);
+    for (int l = 1; l <= 4; ++l) b.part[l] = c.take<float>((size_t)kSplit * H * (l == 1 ? NX : H));
     b.colpart = c.take<float>((size_t)(B / 128) * 41 * 32);
     b.Wb[1] = c.take<bf16>((size_t)H * KX);
     b.Wt[1] = c.take<bf16>((size_t)NX * H);
@@ -527,6 +613,9 @@ size_t layout(unsigned char *base, int B, Bufs *out) {
         b.Wt[l] = c.take<bf16>((size_t)H * H);
     }
     b.lsum = c.take<float>(1);
+    b.Xin = c.take<float>((size_t)B * DIN);
+    b.yin = c.take<float>(B);
+    b.dyin = c.take<float>((size_t)B * NTH);
     b.err = c.take<int>(1);
     if (out) *out = b;
     return c.off;
@@ -557,8 +646,9 @@ cudaError_t run_forward(mlp_ctx *c, const float *prm, const float *y, const floa
         EpiFwdLast ep{prm + ob4, prm + ow5, b.z[4], b.outp, b.h[4], b.p[4], b.Aop[4], B2, B};
         e = gemm(b.h[3], H, b.Wb[4], H, B, H, H, H, ep, b.err, st);
         if (e != cudaSuccess) return e;
-        finish_out_kernel<<<grid_for(B), 256, 0, st>>>(b.outp, H / 32, B, prm + ob5, y, inv_b, b.out, b.obar,
-                                                      b.loss_rows);
+        e = launch_pdl(finish_out_kernel, dim3(grid_for(B)), dim3(256), 0, st, (const float *)b.outp, H / 32, B,
+                       prm + ob5, y, inv_b, b.out, b.obar, b.loss_rows);
+        if (e != cudaSuccess) return e;
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -570,6 +660,81 @@ cudaError_t run_forward(mlp_ctx *c, const float *prm, const float *y, const floa
     }
     EpiTanIn ep{b.g[0], dy, b.gb0, b.Bop[1], b.loss_rows, B2, 2.0f * alpha * inv_b, alpha * inv_b};
     return gemm(b.p[1], H, b.Wt[1], H, B, NX, H, H, ep, b.err, st);
+}
+
+void drop_graph(TrainGraph &tg) {
+    if (tg.exec) cudaGraphExecDestroy(tg.exec);
+    if (tg.graph) cudaGraphDestroy(tg.graph);
+    tg.exec = nullptr;
+    tg.graph = nullptr;
+    tg.adam = nullptr;
+}
+
+// The differential loss and its gradient for the batch (X, y, dy), all stream-ordered on st.
+cudaError_t loss_grad_impl(mlp_ctx *c, const float *params, const float *X, const float *y, const float *dy,
+                           float alpha, float *loss_out, float *grads, cudaStream_t st) {
+    Bufs &b = c->b;
+    const int B = b.B;
+    const long long B2 = 2LL * B;
+    cudaError_t e0 = launch_pdl(prep_input_kernel, dim3(grid_for((long long)B * DIN)), dim3(256), 0, st, X, B, B, b.x0,
+                                b.Bop[1], B2);
+    if (e0 != cudaSuccess) return e0;
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = run_forward(c, params, y, dy, alpha, true, st);
+    // R1..R4: up the tangent chain
+    for (int l = 1; l <= 4 && e == cudaSuccess; ++l) {
+        const bf16 *A = l == 1 ? b.gb0 : b.gb[l - 1];
+        const int K = l == 1 ? KX : H;
+        if (l < 4) {
+            EpiTbar ep{b.z[l], b.g[l], b.gb[l], b.Bop[l + 1], b.zbt[l], B2};
+            e = gemm(A, K, b.Wb[l], K, B, H, K, K, ep, b.err, st);
+        } else {
+            EpiTbarLast ep{b.z[4], params + ow5, b.obar, b.gb4f, b.zb[4], b.zbb[4], b.Aop[4], B2, B};
+            e = gemm(A, K, b.Wb[4], K, B, H, K, K, ep, b.err, st);
+        }
+    }
+    // D4..D2: down the forward chain
+    for (int l = 4; l >= 2 && e == cudaSuccess; --l) {
+        EpiDbar ep{b.z[l - 1], b.zbt[l - 1], b.zb[l - 1], l - 1 >= 2 ? b.zbb[l - 1] : nullptr, b.Aop[l - 1], B2, B};
+        e = gemm(b.zbb[l], H, b.Wt[l], H, B, H, H, H, ep, b.err, st);
+    }
+    // G1..G4: weight gradients over the concatenated 2B rows, split along K (32-column tiles: 256
+    // CTAs; one CTA over all 256 columns gave 32 CTAs and a slower step)
+    for (int l = 1; l <= 4 && e == cudaSuccess; ++l) {
+        const int N = l == 1 ? NX : H;
+        EpiPartial ep{b.part[l], N, H};
+        e = gemm(b.Aop[l], B2, b.Bop[l], B2, H, N, (int)B2, (int)(B2 / kSplit), ep, b.err, st);
+    }
+    if (e == cudaSuccess) {
+        e = launch_pdl(reduce_split_kernel, dim3(grid_for((long long)H * DIN + 3LL * H * H)), dim3(256), 0, st,
+                       Partials{{nullptr, b.part[1], b.part[2], b.part[3], b.part[4]}}, grads);
+    }
+    if (e == cudaSuccess) {
+        const int n_chunks = B / kColChunk;
+        e = launch_pdl(colsum_kernel, dim3(41, n_chunks), dim3(256), 0, st, b, b.colpart);
+        if (e == cudaSuccess)
+            e = launch_pdl(colsum_finish_kernel, dim3(grid_for(kColOut)), dim3(256), 0, st, (const float *)b.colpart,
+                           n_chunks, grads, loss_out);
+    }
+    return e;
+}
+
+WCopies wcopies(const Bufs &b) {
+    WCopies w{};
+    for (int l = 1; l <= 4; ++l) {
+        w.Wb[l] = b.Wb[l];
+        w.Wt[l] = b.Wt[l];
+    }
+    return w;
+}
+
+// Adam step t on the parameters and the BF16 weight copies (one kernel).
+cudaError_t adam_impl(mlp_ctx *c, float *params, const float *grads, float *m, float *v, int t, float lr, float beta1,
+                      float beta2, float eps, cudaStream_t st) {
+    const float c1 = 1.0f / (1.0f - powf(beta1, (float)t));
+    const float c2 = 1.0f / (1.0f - powf(beta2, (float)t));
+    return launch_pdl(adam_kernel, dim3(grid_for(kParams)), dim3(256), 0, st, params, grads, m, v, (long long)kParams,
+                      lr, beta1, beta2, eps, c1, c2, wcopies(c->b));
 }
 
 }  // namespace
@@ -622,6 +787,9 @@ mc_status mlp_create(int device, int32_t batch, void *workspace, size_t workspac
 
 void mlp_destroy(mlp_ctx *c) {
     if (!c) return;
+    cudaSetDevice(c->device);
+    drop_graph(c->tg);
+    if (c->tg.cap) cudaStreamDestroy(c->tg.cap);
     if (c->owns && c->ws) {
         cudaSetDevice(c->device);
         cudaFree(c->ws);
@@ -655,60 +823,110 @@ mc_status mlp_forward(mlp_ctx *c, const float *params, const float *X, int32_t n
 mc_status mlp_loss_grad(mlp_ctx *c, const float *params, const float *X, const float *y, const float *dy, float alpha,
                         float *loss_out, float *grads, void *stream) {
     if (!c || !params || !X || !y || !dy || !grads) return MC_ERR_INVALID_ARG;
-    cudaStream_t st = (cudaStream_t)stream;
-    Bufs &b = c->b;
-    const int B = b.B;
-    const long long B2 = 2LL * B;
-    prep_input_kernel<<<grid_for((long long)B * DIN), 256, 0, st>>>(X, B, B, b.x0, b.Bop[1], B2);
-    cudaError_t e = cudaGetLastError();
-    if (e == cudaSuccess) e = run_forward(c, params, y, dy, alpha, true, st);
-    // R1..R4: up the tangent chain
-    for (int l = 1; l <= 4 && e == cudaSuccess; ++l) {
-        const bf16 *A = l == 1 ? b.gb0 : b.gb[l - 1];
-        const int K = l == 1 ? KX : H;
-        if (l < 4) {
-            EpiTbar ep{b.z[l], b.g[l], b.gb[l], b.Bop[l + 1], b.zbt[l], B2};
-            e = gemm(A, K, b.Wb[l], K, B, H, K, K, ep, b.err, st);
-        } else {
-            EpiTbarLast ep{b.z[4], params + ow5, b.obar, b.gb4f, b.zb[4], b.zbb[4], b.Aop[4], B2, B};
-            e = gemm(A, K, b.Wb[4], K, B, H, K, K, ep, b.err, st);
-        }
-    }
-    // D4..D2: down the forward chain
-    for (int l = 4; l >= 2 && e == cudaSuccess; --l) {
-        EpiDbar ep{b.z[l - 1], b.zbt[l - 1], b.zb[l - 1], l - 1 >= 2 ? b.zbb[l - 1] : nullptr, b.Aop[l - 1], B2, B};
-        e = gemm(b.zbb[l], H, b.Wt[l], H, B, H, H, H, ep, b.err, st);
-    }
-    // G1..G4: weight gradients over the concatenated 2B rows, split along K
-    for (int l = 1; l <= 4 && e == cudaSuccess; ++l) {
-        const int N = l == 1 ? NX : H;
-        EpiPartial ep{b.part, N, H};
-        e = gemm(b.Aop[l], B2, b.Bop[l], B2, H, N, (int)B2, (int)(B2 / kSplit), ep, b.err, st);
-        if (e == cudaSuccess) {
-            const int ncopy = l == 1 ? DIN : H;
-            reduce_split_kernel<<<grid_for((long long)H * ncopy), 256, 0, st>>>(b.part, N, ncopy, grads + oW(l));
-            e = cudaGetLastError();
-        }
-    }
-    if (e == cudaSuccess) {
-        const int n_chunks = B / kColChunk;
-        colsum_kernel<<<dim3(41, n_chunks), 256, 0, st>>>(b, b.colpart);
-        colsum_finish_kernel<<<grid_for(kColOut), 256, 0, st>>>(b.colpart, n_chunks, grads, loss_out);
-        e = cudaGetLastError();
-    }
-    return cuda_st(e, "mlp_loss_grad");
+    return cuda_st(loss_grad_impl(c, params, X, y, dy, alpha, loss_out, grads, (cudaStream_t)stream), "mlp_loss_grad");
 }
 
 mc_status mlp_adam_step(mlp_ctx *c, float *params, const float *grads, float *m, float *v, int32_t t, float lr,
                         float beta1, float beta2, float eps, void *stream) {
     if (!c || !params || !grads || !m || !v || t < 1) return MC_ERR_INVALID_ARG;
+    return cuda_st(adam_impl(c, params, grads, m, v, t, lr, beta1, beta2, eps, (cudaStream_t)stream), "adam");
+}
+
+}  // extern "C"
+
+namespace {
+
+// Capture loss and gradient, Adam and the weight refresh of the context's own batch buffers into
+// a graph (on the context's private stream: capture is not possible on the legacy default
+// stream), and find the Adam node.
+cudaError_t capture_step(mlp_ctx *c, float *params, float *grads, float *loss_out, float *m, float *v, float alpha,
+                         float beta1, float beta2, float eps) {
+    TrainGraph &tg = c->tg;
+    drop_graph(tg);
+    cudaError_t e = cudaSuccess;
+    if (!tg.cap) e = cudaStreamCreateWithFlags(&tg.cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return e;
+    e = cudaStreamBeginCapture(tg.cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    Bufs &b = c->b;
+    cudaError_t e1 = loss_grad_impl(c, params, b.Xin, b.yin, b.dyin, alpha, loss_out, grads, tg.cap);
+    if (e1 == cudaSuccess) e1 = adam_impl(c, params, grads, m, v, 1, 1e-3f, beta1, beta2, eps, tg.cap);
+    e = cudaStreamEndCapture(tg.cap, &tg.graph);
+    if (e1 != cudaSuccess) e = e1;
+    if (e != cudaSuccess) {
+        drop_graph(tg);
+        return e;
+    }
+    size_t n = 0;
+    e = cudaGraphGetNodes(tg.graph, nullptr, &n);
+    std::vector<cudaGraphNode_t> nodes(n);
+    if (e == cudaSuccess && n) e = cudaGraphGetNodes(tg.graph, nodes.data(), &n);
+    for (size_t i = 0; e == cudaSuccess && i < n && !tg.adam; ++i) {
+        cudaGraphNodeType ty;
+        if (cudaGraphNodeGetType(nodes[i], &ty) != cudaSuccess || ty != cudaGraphNodeTypeKernel) continue;
+        cudaKernelNodeParams kp;
+        if (cudaGraphKernelNodeGetParams(nodes[i], &kp) == cudaSuccess && kp.func == (void *)adam_kernel)
+            tg.adam = nodes[i];
+    }
+    if (e == cudaSuccess && !tg.adam) e = cudaErrorUnknown;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&tg.exec, tg.graph, 0);
+    if (e != cudaSuccess) {
+        drop_graph(tg);
+        return e;
+    }
+    const void *key[5] = {params, grads, loss_out, m, v};
+    for (int i = 0; i < 5; ++i) tg.key[i] = key[i];
+    tg.alpha = alpha;
+    tg.beta1 = beta1;
+    tg.beta2 = beta2;
+    tg.eps = eps;
+    return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" {
+
+mc_status mlp_train_step(mlp_ctx *c, float *params, const float *X, const float *y, const float *dy, float alpha,
+                         float *grads, float *loss_out, float *m, float *v, int32_t t, float lr, float beta1,
+                         float beta2, float eps, void *stream) {
+    if (!c || !params || !X || !y || !dy || !grads || !m || !v || t < 1) return MC_ERR_INVALID_ARG;
     cudaStream_t st = (cudaStream_t)stream;
-    const float c1 = 1.0f / (1.0f - powf(beta1, (float)t));
-    const float c2 = 1.0f / (1.0f - powf(beta2, (float)t));
-    adam_kernel<<<grid_for(kParams), 256, 0, st>>>(params, grads, m, v, kParams, lr, beta1, beta2, eps, c1, c2);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_st(e, "adam");
-    return mlp_set_weights(c, params, stream);
+    Bufs &b = c->b;
+    const int B = b.B;
+    cudaError_t e = cudaMemcpyAsync(b.Xin, X, sizeof(float) * B * DIN, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b.yin, y, sizeof(float) * B, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b.dyin, dy, sizeof(float) * B * NTH, cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return cuda_st(e, "mlp_train_step");
+    TrainGraph &tg = c->tg;
+    const void *key[5] = {params, grads, loss_out, m, v};
+    bool same = tg.exec && tg.alpha == alpha && tg.beta1 == beta1 && tg.beta2 == beta2 && tg.eps == eps;
+    for (int i = 0; i < 5; ++i) same = same && tg.key[i] == key[i];
+    if (!same) {
+        // this step runs eagerly (it also sets every kernel's launch attributes); the graph is
+        // captured for the following steps with these buffers
+        e = loss_grad_impl(c, params, b.Xin, b.yin, b.dyin, alpha, loss_out, grads, st);
+        if (e == cudaSuccess) e = adam_impl(c, params, grads, m, v, t, lr, beta1, beta2, eps, st);
+        if (e == cudaSuccess) e = capture_step(c, params, grads, loss_out, m, v, alpha, beta1, beta2, eps);
+        return cuda_st(e, "mlp_train_step");
+    }
+    // the Adam node's learning rate and bias corrections for step t
+    float lr_ = lr, b1 = beta1, b2 = beta2, ep = eps;
+    float c1 = 1.0f / (1.0f - powf(beta1, (float)t)), c2 = 1.0f / (1.0f - powf(beta2, (float)t));
+    long long n = kParams;
+    float *prm = params, *mm = m, *vv = v;
+    const float *g = grads;
+    WCopies wc = wcopies(b);
+    void *args[12] = {&prm, &g, &mm, &vv, &n, &lr_, &b1, &b2, &ep, &c1, &c2, &wc};
+    cudaKernelNodeParams kp;
+    e = cudaGraphKernelNodeGetParams(tg.adam, &kp);
+    if (e == cudaSuccess) {
+        kp.kernelParams = args;
+        kp.extra = nullptr;
+        e = cudaGraphExecKernelNodeSetParams(tg.exec, tg.adam, &kp);
+    }
+    if (e == cudaSuccess) e = cudaGraphLaunch(tg.exec, st);
+    return cuda_st(e, "mlp_train_step");
 }
 
 mc_status mlp_error_flag(mlp_ctx *c, int32_t *flag_host) {

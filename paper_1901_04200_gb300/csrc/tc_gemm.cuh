@@ -117,6 +117,12 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase) {
     return false;
 }
 
+// Programmatic dependent launch: pdl_wait blocks until the grids this one depends on have
+// completed and their memory is visible (a no-op without such a dependency); pdl_trigger lets
+// the dependent grid start launching (its blocks then run their prologue and wait in pdl_wait).
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // TMA: the box at coordinates (x = k element, y = row) of the 2-D tensor map into shared
 // memory at `dst`, completing `bytes` of the transaction count of mbarrier `bar`.
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t bar) {
@@ -231,6 +237,9 @@ __device__ __forceinline__ void gemm_body(const TensorMaps &tm, const GemmShape 
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tslot;
+    // everything above (tensor memory, barriers, descriptor prefetch) overlaps the previous
+    // kernel; the operands and the epilogue's inputs are its outputs
+    pdl_wait();
     const int row0 = blockIdx.x * kBM;
     const int col_base = blockIdx.y * g.BN;
     const int kbase = blockIdx.z * g.k_slice;
@@ -288,6 +297,7 @@ __device__ __forceinline__ void gemm_body(const TensorMaps &tm, const GemmShape 
     if (!ok) *fail = 1;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     __syncthreads();
+    pdl_trigger();  // the next kernel may start its prologue during this epilogue
     if (*fail) {
         if (tid == 0 && g.err) atomicExch(g.err, 1);
     } else if constexpr (Epi::kColumns) {

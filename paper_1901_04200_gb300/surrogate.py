@@ -146,9 +146,9 @@ class Surrogate:
                 torch.index_select(dy, 0, idx, out=dyb)
                 # cosine decay of the learning rate from lr to lr_final
                 a = lr_final + 0.5 * (lr - lr_final) * (1.0 + math.cos(math.pi * step / total))
-                self.train_net.loss_grad(self.params, Xb, yb, dyb, alpha, self.grads, self.loss)
                 self.t += 1
-                self.train_net.adam_step(self.params, self.grads, self.m, self.v, self.t, lr=a)
+                self.train_net.train_step(self.params, Xb, yb, dyb, alpha, self.grads, self.loss, self.m, self.v,
+                                          self.t, lr=a)
                 step += 1
                 if log_every and step % log_every == 0:
                     self.history.append((step, float(self.loss.item())))

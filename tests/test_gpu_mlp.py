@@ -95,3 +95,37 @@ def test_adam_step_matches_oracle(L):
         pv, mv, vv = omlp.adam(pv, g * t, mv, vv, t, lr=1e-3)
     torch.cuda.synchronize()
     assert np.max(np.abs(prm.cpu().numpy() - pv)) <= 1e-6
+
+
+def test_train_step_graph_equals_eager_steps(L):
+    """mlp_train_step (first call eager, then a replayed CUDA graph with the step's learning rate
+    and bias corrections patched in) gives bit-identical parameters, moments and loss to
+    mlp_loss_grad + mlp_adam_step, over batches that live at different addresses each step."""
+    B, steps = 512, 6
+    p, _, _, _ = setup(B, seed=5)
+    rng = np.random.default_rng(9)
+    batches = [(cuda32(rng.uniform(-1, 1, (B, 7))), cuda32(rng.normal(size=B)), cuda32(rng.normal(size=(B, 5))))
+               for _ in range(steps)]
+    runs = []
+    for graph in (False, True):
+        net = L.Mlp(B)
+        prm = cuda32(omlp.flatten(p))
+        net.set_weights(prm)
+        g = torch.zeros_like(prm)
+        m, v = torch.zeros_like(prm), torch.zeros_like(prm)
+        loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+        losses = []
+        for t in range(1, steps + 1):
+            X, y, dy = batches[t - 1]
+            lr = 1e-3 / t
+            if graph:
+                net.train_step(prm, X, y, dy, 0.7, g, loss, m, v, t, lr=lr)
+            else:
+                net.loss_grad(prm, X, y, dy, 0.7, g, loss)
+                net.adam_step(prm, g, m, v, t, lr=lr)
+            losses.append(loss.clone())
+        torch.cuda.synchronize()
+        assert net.error_flag() == 0
+        runs.append((prm.cpu(), m.cpu(), v.cpu(), torch.cat(losses).cpu()))
+    for a, b in zip(*runs):
+        assert torch.equal(a, b)
