@@ -54,8 +54,12 @@ UNIT = "path-steps/s"
 # Heston SLV: the Heston step plus the leverage lookup (10) and L^2 vdt, L sq (2);
 # R adds the lookup again (10), L-bar and weights (4), four row-adjoint FMAs (4), the
 # extra L factors (3) and dL/dx (2) to the Heston adjoint.
+# Local vol from stored states ("Rs", the adjoint alone): the cell and lerp once 12, the step's
+# sqrt(dt) z from its two end states (difference, drift and sigma^2 terms) 4 and one reciprocal,
+# sigma-bar and weights 6, four row-adjoint FMAs 4, d sigma/dx 2.
 OPS = {"heston": {"F": {"fp32": 22, "mufu": 5, "int": 24}, "step": {"fp32": 13, "mufu": 1}, "R": {"fp32": 17}},
-       "lv": {"F": {"fp32": 21, "mufu": 2, "int": 12}, "step": {"fp32": 16}, "R": {"fp32": 24}},
+       "lv": {"F": {"fp32": 21, "mufu": 2, "int": 12}, "step": {"fp32": 16}, "R": {"fp32": 24},
+              "Rs": {"fp32": 28, "mufu": 1}},
        "slv": {"F": {"fp32": 34, "mufu": 5, "int": 24}, "step": {"fp32": 25, "mufu": 1}, "R": {"fp32": 40}}}
 # Forward-mode tangents of the Heston step (mc_value_and_grad_tangent), per path-step on top of
 # F: shared factors 10 FP32 (the 1{v>0} dt select; the x and v coefficients of d vdt, 2 + 2; the
@@ -65,7 +69,8 @@ OPS_TANGENT = {"heston": {"fp32": 29}}
 # What each path kernel runs per path-step, by storage mode.
 KERNEL_PARTS = {"checkpoint": {"forward_sweep": ["F"], "reverse_sweep": ["F", "R"]},
                 "normals": {"forward_sweep": ["F"], "reverse_sweep": ["step", "R"]},
-                "full": {"forward_sweep": ["F"], "reverse_sweep": ["R"]}}
+                "full": {"forward_sweep": ["F"], "reverse_sweep": ["R"]},
+                "states": {"forward_sweep": ["F"], "reverse_sweep": ["Rs"]}}
 # State words, normals per step and tape words per step of each model.
 DIMS = {"heston": (2, 2, 4), "lv": (1, 1, 2), "slv": (2, 2, 5)}
 
@@ -83,6 +88,8 @@ def kernel_bytes(model, storage, K, S, n_groups):
         b = 4.0 * sd / K
     elif storage == "normals":
         b = 4.0 * sd / K + 4.0 * dz
+    elif storage == "states":
+        b = 4.0 * sd + 4.0 * sd / S  # the state before every step, and the final state
     else:
         b = 4.0 * nf + 4.0 * n_groups / S
     return {"forward_sweep": b, "reverse_sweep": b}
@@ -852,7 +859,7 @@ def main():
                     help="skip the recompute and forward-mode comparison arms")
     ap.add_argument("--calib-cases", type=int, default=16)
     ap.add_argument("--ckpt", type=int, default=0, help="checkpoint interval (0 = workload default)")
-    ap.add_argument("--storage", default="auto", choices=["auto", "checkpoint", "normals", "full"],
+    ap.add_argument("--storage", default="auto", choices=["auto", "checkpoint", "normals", "full", "states"],
                     help="what the reverse sweep reads: checkpoints (re-run with regenerated normals), "
                          "checkpoints and stored normals, the whole stored tape, or the library's choice")
     args = ap.parse_args()

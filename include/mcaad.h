@@ -78,16 +78,26 @@ typedef enum { MC_FP64 = 0, MC_FP32 = 1 } mc_precision;
  *                          for GBM and LV, 2 for Heston and SLV, x 4 or 8 bytes
  *                          per path-step); the reverse sweep re-runs the model
  *                          step between checkpoints on the stored normals.
- * The three run the same step arithmetic, so E y is the same and the
+ *   MC_STORAGE_STATES      (local vol only) the state before every step (one
+ *                          word per path-step, no normals, no checkpoints); the
+ *                          reverse sweep runs only the adjoint, taking each
+ *                          step's sqrt(dt) z from the states at its two ends
+ *                          (the step's increment minus its drift, over sigma):
+ *                          valid where the surface is nonzero along the paths
+ *                          (a zero sigma gives a non-finite gradient).
+ * All run the same forward step arithmetic, so E y is the same and the
  * gradients agree to rounding (the compiler may fuse a multiply and an add
- * differently in different kernels).  The mode is fixed per context;
- * mc_workspace_size accounts for the storage it needs. */
+ * differently in different kernels; the stored-states adjoint divides by
+ * sigma).  The mode is fixed per context; mc_workspace_size accounts for the
+ * storage it needs. */
 typedef enum {
     MC_STORAGE_CHECKPOINT = 0,
     MC_STORAGE_FULL = 1,
     MC_STORAGE_NORMALS = 2,
-    MC_STORAGE_AUTO = 3 /* NORMALS when the stored normals for max_paths take at most a
-                           quarter of the device's total memory, else CHECKPOINT */
+    MC_STORAGE_AUTO = 3, /* local vol: STATES, the other models: NORMALS, when that storage for
+                            max_paths takes at most a quarter of the device's total memory,
+                            else CHECKPOINT */
+    MC_STORAGE_STATES = 4
 } mc_storage;
 
 /*

@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(_PKG, "libmcaad.so")
 MC_OK, MC_ERR_INVALID_ARG, MC_ERR_CUDA, MC_ERR_OOM, MC_ERR_UNSUPPORTED, MC_ERR_STATE = range(6)
 MC_FP64, MC_FP32 = 0, 1
 KIND = {"gbm": 0, "heston": 1, "lv": 2, "slv": 3}
-STORAGE = {"checkpoint": 0, "full": 1, "normals": 2, "auto": 3}  # mc_storage
+STORAGE = {"checkpoint": 0, "full": 1, "normals": 2, "auto": 3, "states": 4}  # mc_storage
 _STATUS = {1: "MC_ERR_INVALID_ARG", 2: "MC_ERR_CUDA", 3: "MC_ERR_OOM", 4: "MC_ERR_UNSUPPORTED",
            5: "MC_ERR_STATE"}
 

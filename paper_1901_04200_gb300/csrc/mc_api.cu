@@ -175,7 +175,11 @@ mc_status make_plan(const mc_model *md, const mc_instruments *in, Plan &p, std::
         if (md->nx > 32) return bad("LV needs nx <= 32");
     }
     if (md->paths_per_thread < 0 || md->paths_per_thread > 4) return bad("paths_per_thread must be in [0, 4]");
-    if (md->storage < MC_STORAGE_CHECKPOINT || md->storage > MC_STORAGE_AUTO) return bad("unknown storage mode");
+    if (md->storage < MC_STORAGE_CHECKPOINT || md->storage > MC_STORAGE_STATES) return bad("unknown storage mode");
+    if (md->storage == MC_STORAGE_STATES && md->kind != MC_MODEL_LV_BILINEAR) {
+        why = "stored states are implemented for local vol only";
+        return MC_ERR_UNSUPPORTED;
+    }
     p.storage = md->storage;
     p.dz = p.state_dim;  // normals per step: 1 (GBM, LV) or 2 (Heston, SLV)
     p.tape_fields = md->kind == MC_MODEL_GBM_PWC ? 1 : md->kind == MC_MODEL_HESTON_FT ? 4 : md->kind == MC_MODEL_LV_BILINEAR ? 2 : 5;
@@ -289,12 +293,16 @@ struct WsLayout {
         // checkpoint tiles (SegTile): per warp chunk of 32*ppt paths and segment, the state
         // words and, with stored normals, the segment's K * dz normals of each path, in rows of
         // 32 paths padded to whole 16-byte groups; ckpt_stride covers whole chunks
-        const bool full = p.storage == MC_STORAGE_FULL;
-        const size_t rows = (size_t)p.ppt * (p.state_dim + (p.storage == MC_STORAGE_NORMALS ? (size_t)p.K * p.dz : 0));
+        // (stored states: the state before each step of the segment, no checkpoint rows, and one
+        // extra tile for the state after the last step)
+        const bool full = p.storage == MC_STORAGE_FULL, states = p.storage == MC_STORAGE_STATES;
+        const size_t rows = states ? (size_t)p.ppt * p.K * p.state_dim
+                                   : (size_t)p.ppt * (p.state_dim + (p.storage == MC_STORAGE_NORMALS ? (size_t)p.K * p.dz : 0));
         const size_t group = 16 / real;
         const size_t rows_padded = (rows + group - 1) / group * group;
         const size_t chunks = ckpt_stride / (32 * (size_t)p.ppt);
-        ckpt = take(full ? 0 : (size_t)p.n_seg * chunks * rows_padded * 32 * real);
+        const size_t tiles = (size_t)p.n_seg + (states ? 1 : 0);
+        ckpt = take(full ? 0 : tiles * chunks * rows_padded * 32 * real);
         tape = take(full ? (size_t)p.n_last * p.tape_fields * ckpt_stride * real : 0);
         xmat = take(full ? (size_t)p.n_groups * ckpt_stride * real : 0);
         total = o;
@@ -317,8 +325,10 @@ mc_status resolve_storage(Plan &p, uint64_t max_paths, int device, std::string &
         return MC_ERR_CUDA;
     }
     const uint64_t stride = path_stride(max_paths, p.ppt);
-    const double normals_bytes = (double)p.n_last * p.dz * (double)stride * (p.precision == MC_FP64 ? 8 : 4);
-    p.storage = normals_bytes <= 0.25 * (double)total_b ? MC_STORAGE_NORMALS : MC_STORAGE_CHECKPOINT;
+    // local vol stores its states (one word per path-step), the other models their normals
+    const bool states = p.kind == MC_MODEL_LV_BILINEAR;
+    const double bytes = (double)p.n_last * (states ? p.state_dim : p.dz) * (double)stride * (p.precision == MC_FP64 ? 8 : 4);
+    p.storage = bytes <= 0.25 * (double)total_b ? (states ? MC_STORAGE_STATES : MC_STORAGE_NORMALS) : MC_STORAGE_CHECKPOINT;
     return MC_OK;
 }
 
@@ -393,9 +403,11 @@ mc_status launch_shape(const Plan &p, int device, const KernelPair &kp, int nx, 
     const int n_steps = p.n_seg * p.K;
     const size_t zst = p.storage == MC_STORAGE_NORMALS      ? kp.stage_bytes_z
                        : p.storage == MC_STORAGE_CHECKPOINT ? kp.stage_bytes_ckpt
+                       : p.storage == MC_STORAGE_STATES     ? kp.stage_bytes_x
                                                             : 0;
     ln.smem_fwd = SmemPlan(p.kind, real, p.m, p.n_groups, p.M, n_steps, nx, false).total;
-    ln.smem_rev = SmemPlan(p.kind, real, p.m, p.n_groups, p.M, n_steps, nx, true, zst).total;
+    ln.smem_rev = SmemPlan(p.kind, real, p.m, p.n_groups, p.M, n_steps, nx, true, zst,
+                           p.storage == MC_STORAGE_STATES).total;
     int optin = 0;
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
     if (ln.smem_fwd > (size_t)optin || ln.smem_rev > (size_t)optin) {
@@ -403,8 +415,18 @@ mc_status launch_shape(const Plan &p, int device, const KernelPair &kp, int nx, 
         return MC_ERR_UNSUPPORTED;
     }
     ln.fwd = kp.fwd;
-    ln.fwd_keep = p.storage == MC_STORAGE_FULL ? kp.fwd_store : p.storage == MC_STORAGE_NORMALS ? kp.fwd_z : kp.fwd;
-    ln.rev = p.storage == MC_STORAGE_FULL ? kp.rev_tape : p.storage == MC_STORAGE_NORMALS ? kp.rev_z : kp.rev;
+    ln.fwd_keep = p.storage == MC_STORAGE_FULL      ? kp.fwd_store
+                  : p.storage == MC_STORAGE_NORMALS ? kp.fwd_z
+                  : p.storage == MC_STORAGE_STATES  ? kp.fwd_x
+                                                    : kp.fwd;
+    ln.rev = p.storage == MC_STORAGE_FULL      ? kp.rev_tape
+             : p.storage == MC_STORAGE_NORMALS ? kp.rev_z
+             : p.storage == MC_STORAGE_STATES  ? kp.rev_x
+                                               : kp.rev;
+    if (!ln.fwd_keep || !ln.rev) {
+        why = "storage mode not instantiated for this model";
+        return MC_ERR_UNSUPPORTED;
+    }
     const void *fns[3] = {ln.fwd, ln.fwd_keep, ln.rev};
     const size_t sm[3] = {ln.smem_fwd, ln.smem_fwd, ln.smem_rev};
     int *grids[3] = {&ln.grid_fwd, &ln.grid_fwd_keep, &ln.grid_rev};

@@ -17,6 +17,9 @@ struct KernelPair {
     const void *rev_z = nullptr;      // reverse sweep recomputing from checkpoints on the stored normals
     size_t stage_bytes_ckpt = 0;      // rev's shared staging buffers per block
     size_t stage_bytes_z = 0;         // rev_z's shared staging buffers per block
+    const void *fwd_x = nullptr;      // forward sweep storing the state before every step (local vol)
+    const void *rev_x = nullptr;      // reverse sweep running the adjoint from the stored states
+    size_t stage_bytes_x = 0;         // rev_x's shared staging buffers per block
 };
 
 // Path kernels of (kind, precision, segment length K, paths per thread);

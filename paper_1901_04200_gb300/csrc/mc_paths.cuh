@@ -41,6 +41,18 @@ __device__ __forceinline__ float rsqrt_r<float>(float x) { return rsqrt_approx(x
 template <>
 __device__ __forceinline__ double rsqrt_r<double>(double x) { return rsqrt(x); }
 
+// 1/x: the hardware approximation in FP32 (relative error about one ulp), exact division in FP64
+template <typename T>
+__device__ __forceinline__ T recip_r(T x);
+template <>
+__device__ __forceinline__ float recip_r<float>(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+template <>
+__device__ __forceinline__ double recip_r<double>(double x) { return 1.0 / x; }
+
 template <typename T>
 __device__ __forceinline__ T exp_r(T x);
 template <>
@@ -63,8 +75,10 @@ __host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a -
 struct SmemPlan {
     size_t strike, grp_seg, grp_begin, seed_w, wacc_y, wacc_g, model, zstage, total;
     // zstage_bytes: the reverse sweep's staging buffers for stored normals (0 otherwise)
+    // node_table: the local-vol surface as node pairs per time cell instead of per-step rows (the
+    // stored-states reverse sweep, which looks the surface up once per step)
     __host__ __device__ SmemPlan(int kind, int real_bytes, int m, int n_groups, int M, int n_steps,
-                                 int nx, bool reverse, size_t zstage_bytes = 0) {
+                                 int nx, bool reverse, size_t zstage_bytes = 0, bool node_table = false) {
         size_t o = 0;
         strike = o;    o = align_up(o + (size_t)m * real_bytes, 16);
         grp_seg = o;   o = align_up(o + (size_t)n_groups * 4, 16);
@@ -78,7 +92,8 @@ struct SmemPlan {
             o = align_up(o, 16);
             o += (size_t)n_steps * 4;
         } else if (kind == kLv || kind == kSlv) {
-            o += (size_t)n_steps * nx * real_bytes;  // time-interpolated node rows
+            if (node_table) o += (size_t)((kind == kSlv ? M - 5 : M) / nx - 1) * nx * 2 * real_bytes;  // node pairs
+            else o += (size_t)n_steps * nx * real_bytes;  // time-interpolated node rows
             o = align_up(o, 16);
             o += (size_t)n_steps * real_bytes;       // time weight a_n
             o = align_up(o, 16);
@@ -278,6 +293,7 @@ struct LvModel {
         const Real *a;    // [n_steps]
         const int *jt;    // [n_steps]
         Real *racc;       // reverse: [nx][kBlock][2] per-thread node adjoints of rows jt, jt+1
+        const Real *node; // node_table: [nt-1][nx][2] (theta[j][c], theta[j+1][c] - theta[j][c])
         int nx;
     };
     struct Par { Real rdt, dt, sdt, x_lo, inv_hx; int nxm2; };
@@ -286,10 +302,11 @@ struct LvModel {
     struct Acc { int jt; Real at, oma; };
 
     __device__ static void setup(unsigned char *base, const SmemPlan &sp, const DevProblem &pb,
-                                 const double *theta, int n_steps, Shared &sh, Par &par) {
+                                 const double *theta, int n_steps, Shared &sh, Par &par, bool node_table = false) {
         const int nx = pb.nx;
         Real *row = (Real *)(base + sp.model);
-        size_t o = align_up(sp.model + (size_t)n_steps * nx * sizeof(Real), 16);
+        size_t o = align_up(sp.model + (node_table ? (size_t)(pb.nt - 1) * nx * 2 : (size_t)n_steps * nx) * sizeof(Real),
+                            16);
         Real *a = (Real *)(base + o);
         o = align_up(o + (size_t)n_steps * sizeof(Real), 16);
         int *jt = (int *)(base + o);
@@ -299,13 +316,23 @@ struct LvModel {
             a[n] = (Real)pb.lv_a[n];
             jt[n] = pb.lv_jt[n];
         }
-        for (int q = threadIdx.x; q < n_steps * nx; q += blockDim.x) {
-            const int n = q / nx, c = q - n * nx;
-            const int j = pb.lv_jt[n];
-            const double w = pb.lv_a[n];
-            row[q] = (Real)((1.0 - w) * theta[j * nx + c] + w * theta[(j + 1) * nx + c]);
+        if (node_table) {
+            for (int q = threadIdx.x; q < (pb.nt - 1) * nx; q += blockDim.x) {
+                row[2 * q] = (Real)theta[q];
+                row[2 * q + 1] = (Real)(theta[q + nx] - theta[q]);
+            }
+            sh.row = nullptr;
+            sh.node = row;
+        } else {
+            for (int q = threadIdx.x; q < n_steps * nx; q += blockDim.x) {
+                const int n = q / nx, c = q - n * nx;
+                const int j = pb.lv_jt[n];
+                const double w = pb.lv_a[n];
+                row[q] = (Real)((1.0 - w) * theta[j * nx + c] + w * theta[(j + 1) * nx + c]);
+            }
+            sh.node = nullptr;
         }
-        sh.row = row;
+        sh.row = node_table ? nullptr : row;
         sh.a = a;
         sh.jt = jt;
         sh.nx = nx;
@@ -423,6 +450,30 @@ struct LvModel {
         const Real ds = s1 - s0;
         const Real sig = fma(b, ds, s0);
         const Real sb = xb * fma(p.sdt, t.z, -sig * p.dt);
+        const Real g1 = sb * b, g0 = sb - g1;
+        add_node(sh, a, c, g0);
+        add_node(sh, a, c + 1, g1);
+        if (inside) xb = fma(sb * p.inv_hx, ds, xb);
+    }
+    // The adjoint of step n from the states at both of its ends (stored-states variant): the
+    // step x1 = x0 + r dt - sigma^2 dt / 2 + sigma sqrt(dt) z gives
+    // d x1 / d sigma = sqrt(dt) z - sigma dt = (x1 - x0 - r dt - sigma^2 dt / 2) / sigma,
+    // so the adjoint needs neither the normal nor a re-run of the step (sigma != 0).
+    __device__ __forceinline__ static void adjoint_states(const State &s0, const State &s1, int n, Real &xb, Real &,
+                                                          Acc &a, const Par &p, const Shared &sh) {
+        const Real u = (s0.x - p.x_lo) * p.inv_hx;
+        int c;
+        Real b;
+        bool inside;
+        cell(u, p, c, b, inside);
+        using P2 = typename std::conditional<sizeof(Real) == 4, float2, double2>::type;
+        const P2 *nd = (const P2 *)sh.node + a.jt * sh.nx + c;  // the time cell's node pairs (a.jt, a.at: step n)
+        const P2 n0 = nd[0], n1 = nd[1];
+        const Real v0 = fma(a.at, n0.y, n0.x), v1 = fma(a.at, n1.y, n1.x);
+        const Real ds = v1 - v0;
+        const Real sig = fma(b, ds, v0);
+        const Real dsig = (s1.x - s0.x - p.rdt - Real(0.5) * p.dt * sig * sig) * recip_r<Real>(sig);
+        const Real sb = xb * dsig;
         const Real g1 = sb * b, g0 = sb - g1;
         add_node(sh, a, c, g0);
         add_node(sh, a, c + 1, g1);
@@ -582,12 +633,16 @@ struct Vec16<double> {
 // warp's tile of segment s-1 into its half of a two-buffer shared staging
 // area (same layout) while it works on segment s, so HBM latency is paid
 // once per chunk instead of once per segment.
-template <class Md, int K, int PPT, bool kZ>
+// kMode 2 (stored states) keeps instead the state before each of the segment's steps, row
+// (i*SD + w)*PPT + q, and no checkpoint rows; the state after the last step goes to one extra
+// tile (segment index n_seg).
+template <class Md, int K, int PPT, int kMode>
 struct SegTile {
     using Real = typename Md::Real;
     using V = Vec16<Real>;
-    static constexpr int RZ = kZ ? K * Md::DZ * PPT : 0;           // normals rows
-    static constexpr int R = RZ + Md::SD * PPT;                     // + checkpoint rows
+    static constexpr bool kZ = kMode == 1;
+    static constexpr int RZ = kZ ? K * Md::DZ * PPT : 0;                          // normals rows
+    static constexpr int R = kMode == 2 ? K * Md::SD * PPT : RZ + Md::SD * PPT;    // + checkpoint rows
     static constexpr int kG = 16 / (int)sizeof(Real);               // rows per vector group
     static constexpr int Rp = (R + kG - 1) / kG * kG;               // rows padded to whole groups
     static constexpr int kElems = Rp * kWarp;                       // elements per tile
@@ -596,6 +651,7 @@ struct SegTile {
     static constexpr size_t kBlockBytes = kWarpBytes * kWarpsPerBlock;
     __device__ static constexpr int zrow(int i, int c, int q) { return (i * Md::DZ + c) * PPT + q; }
     __device__ static constexpr int crow(int w, int q) { return RZ + w * PPT + q; }
+    __device__ static constexpr int srow(int i, int w, int q) { return (i * Md::SD + w) * PPT + q; }
     // group g of this lane (tile or staging buffer base, lane)
     __device__ __forceinline__ static typename V::T *group(Real *t, int g, int lane) {
         return (typename V::T *)(t + ((size_t)g * kWarp + lane) * kG);
@@ -915,6 +971,246 @@ __global__ void __launch_bounds__(kBlock) path_reverse_kernel(const DevProblem p
     }
 }
 
+// ------------------------------------------------------ stored-states variant --
+// The forward sweep stores the state before every step (SegTile mode 2: no normals, no
+// checkpoints; the state after the last step in one extra tile), and the reverse sweep runs the
+// adjoint alone: the model's adjoint_states takes a step's quantities from the states at both
+// of its ends instead of re-running it (local vol: the step's increment gives sqrt(dt) z).
+
+template <class Md, int K, int PPT>
+__global__ void __launch_bounds__(kBlock) path_forward_states_kernel(const DevProblem pb, const DevCall cl) {
+    using Real = typename Md::Real;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int n_steps = pb.n_seg * K;
+    const SmemPlan sp(Md::kind, sizeof(Real), pb.m, pb.n_groups, pb.M, n_steps, pb.nx, false);
+    load_tables<Md>(smem, sp, pb, false, cl);
+    typename Md::Shared sh;
+    typename Md::Par par;
+    Md::setup(smem, sp, pb, cl.theta, n_steps, sh, par);
+    __syncthreads();
+
+    const Real *strike = (const Real *)(smem + sp.strike);
+    const int *gseg = (const int *)(smem + sp.grp_seg);
+    const int *gbeg = (const int *)(smem + sp.grp_begin);
+    const int warp = threadIdx.x / kWarp, lane = threadIdx.x % kWarp;
+    double *wy = (double *)(smem + sp.wacc_y) + warp * pb.m;
+    const Real S0 = (Real)pb.S0;
+    using TL = SegTile<Md, K, PPT, 2>;
+    constexpr int kRowsPerStep = Md::SD * PPT;
+    const RoundKeys rk = Md::kKeysInRegisters ? philox_round_keys(cl.seed) : cl.rk;
+
+    constexpr uint64_t kChunk = (uint64_t)kWarp * PPT;
+    const uint64_t n_chunks = (cl.n_paths + kChunk - 1) / kChunk;
+    const uint64_t ws_chunks = cl.ckpt_stride / kChunk;
+    for (uint64_t ch = (uint64_t)blockIdx.x * kWarpsPerBlock + warp; ch < n_chunks;
+         ch += (uint64_t)gridDim.x * kWarpsPerBlock) {
+        uint64_t local[PPT];
+        bool active[PPT];
+        NormalSource<Md> rng[PPT];
+        typename Md::State st[PPT];
+#pragma unroll
+        for (int q = 0; q < PPT; ++q) {
+            local[q] = ch * kChunk + q * kWarp + lane;
+            active[q] = local[q] < cl.n_paths;
+            rng[q].init(pb, cl, cl.path0 + (active[q] ? local[q] : 0));
+            st[q] = Md::init(par);
+        }
+        int g = 0;
+        constexpr int kPeriod = philox_period_segments(K * Md::DZ);
+        for (int sg = 0; sg * kPeriod < pb.n_seg; ++sg) {
+#pragma unroll
+            for (int ss = 0; ss < kPeriod; ++ss) {
+                const int s = sg * kPeriod + ss;
+                if (kPeriod > 1 && s >= pb.n_seg) break;
+                Real zs[K][PPT][Md::DZ];
+                Real xs[K][PPT][Md::SD];  // the state before each step
+                Real *tl = TL::tile(cl.ckpt, ch, ws_chunks, s);
+#pragma unroll
+                for (int i = 0; i < K; ++i) {
+                    const int n = s * K + i;
+#pragma unroll
+                    for (int q = 0; q < PPT; ++q) rng[q].get(n, s == 0 && i == 0, zs[i][q], rk);
+                }
+#pragma unroll
+                for (int i = 0; i < K; ++i) {
+#pragma unroll
+                    for (int q = 0; q < PPT; ++q) {
+                        xs[i][q][0] = st[q].x;
+                        if constexpr (Md::SD == 2) xs[i][q][1] = st[q].v;
+                    }
+                    // groups whose last row is a state of step i go out now
+#pragma unroll
+                    for (int g0 = 0; g0 < TL::Rp; g0 += TL::kG) {
+                        if ((min(g0 + TL::kG, TL::R) - 1) / kRowsPerStep != i) continue;
+                        Real v[TL::kG];
+#pragma unroll
+                        for (int k = 0; k < TL::kG; ++k) {
+                            const int r = g0 + k;
+                            v[k] = r < TL::R ? xs[r / kRowsPerStep][r % PPT][(r / PPT) % Md::SD] : Real(0);
+                        }
+                        *TL::group(tl, g0 / TL::kG, lane) = TL::V::make(v);
+                    }
+#pragma unroll
+                    for (int q = 0; q < PPT; ++q) Md::step(st[q], zs[i][q], s * K + i, par, sh, nullptr);
+                }
+                if (g < pb.n_groups && gseg[g] == s) {
+                    Real S[PPT];
+#pragma unroll
+                    for (int q = 0; q < PPT; ++q) S[q] = S0 * exp_r<Real>(st[q].x);
+                    for (int i0 = gbeg[g]; i0 < gbeg[g + 1]; i0 += kWarp) {
+                        const int cnt = min(kWarp, gbeg[g + 1] - i0);
+                        Real mine = Real(0);
+                        for (int j = 0; j < cnt; ++j) {
+                            Real pay = Real(0);
+#pragma unroll
+                            for (int q = 0; q < PPT; ++q)
+                                pay += active[q] ? fmax(S[q] - strike[i0 + j], Real(0)) : Real(0);
+                            const Real sum = warp_sum(pay);
+                            mine = (lane == j) ? sum : mine;
+                        }
+                        if (lane < cnt) wy[i0 + lane] += (double)mine;
+                    }
+                    ++g;
+                }
+            }
+        }
+        // the state after the last step: rows w*PPT + q of the extra tile
+        Real *tf = TL::tile(cl.ckpt, ch, ws_chunks, pb.n_seg);
+#pragma unroll
+        for (int g0 = 0; g0 < kRowsPerStep; g0 += TL::kG) {
+            Real v[TL::kG];
+#pragma unroll
+            for (int k = 0; k < TL::kG; ++k) {
+                const int r = g0 + k;
+                if (r < kRowsPerStep) {
+                    const int w = r / PPT, q = r % PPT;
+                    if constexpr (Md::SD == 2) v[k] = w == 0 ? st[q].x : st[q].v;
+                    else v[k] = st[q].x;
+                } else {
+                    v[k] = Real(0);
+                }
+            }
+            *TL::group(tf, g0 / TL::kG, lane) = TL::V::make(v);
+        }
+    }
+    __syncthreads();
+    const double *wall = (const double *)(smem + sp.wacc_y);
+    for (int i = threadIdx.x; i < pb.m; i += blockDim.x) {
+        double sum = 0.0;
+        for (int w = 0; w < kWarpsPerBlock; ++w) sum += wall[w * pb.m + i];
+        cl.part_y[(size_t)blockIdx.x * pb.m + i] = sum;
+    }
+}
+
+// Reverse sweep over stored states: per warp chunk, the extra tile gives the final states, then
+// the segments from last to first, each staged (cp.async, two buffers, the next one in flight)
+// while the previous runs: payoff seeds at the segment's end state, then the adjoints of its
+// steps backwards from (state before, state after).
+template <class Md, int K, int PPT>
+__global__ void __launch_bounds__(kBlock) path_reverse_states_kernel(const DevProblem pb, const DevCall cl) {
+    using Real = typename Md::Real;
+    using ZS = SegTile<Md, K, PPT, 2>;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int n_steps = pb.n_seg * K;
+    const SmemPlan sp(Md::kind, sizeof(Real), pb.m, pb.n_groups, pb.M, n_steps, pb.nx, true, ZS::kBlockBytes, true);
+    load_tables<Md>(smem, sp, pb, true, cl);
+    typename Md::Shared sh;
+    typename Md::Par par;
+    Md::setup(smem, sp, pb, cl.theta, n_steps, sh, par, true);
+    __syncthreads();
+
+    const Real *strike = (const Real *)(smem + sp.strike);
+    const Real *sw = (const Real *)(smem + sp.seed_w);
+    const int *gseg = (const int *)(smem + sp.grp_seg);
+    const int *gbeg = (const int *)(smem + sp.grp_begin);
+    const int warp = threadIdx.x / kWarp, lane = threadIdx.x % kWarp;
+    double *wg = (double *)(smem + sp.wacc_g) + warp * pb.M;
+    const Real S0 = (Real)pb.S0;
+    Real *zstage = (Real *)(smem + sp.zstage) + (size_t)warp * 2 * ZS::kElems;
+
+    constexpr uint64_t kChunk = (uint64_t)kWarp * PPT;
+    const uint64_t n_chunks = (cl.n_paths + kChunk - 1) / kChunk;
+    const uint64_t ws_chunks = cl.ckpt_stride / kChunk;
+    for (uint64_t ch = (uint64_t)blockIdx.x * kWarpsPerBlock + warp; ch < n_chunks;
+         ch += (uint64_t)gridDim.x * kWarpsPerBlock) {
+        bool active[PPT];
+        Real xb[PPT], vb[PPT];
+        typename Md::State nx_[PPT];  // the state after the segment being processed
+#pragma unroll
+        for (int q = 0; q < PPT; ++q) {
+            active[q] = ch * kChunk + q * kWarp + lane < cl.n_paths;
+            xb[q] = Real(0);
+            vb[q] = Real(0);
+        }
+        // the final states (extra tile, buffer n_seg & 1), and the last segment behind it
+        ZS::issue(zstage, cl.ckpt, ch, ws_chunks, pb.n_seg, lane);
+        ZS::issue(zstage, cl.ckpt, ch, ws_chunks, pb.n_seg - 1, lane);
+        cp_async_wait<1>();
+        __syncwarp();
+        {
+            const Real *fbuf = zstage + (size_t)(pb.n_seg & 1) * ZS::kElems;
+#pragma unroll
+            for (int q = 0; q < PPT; ++q) {
+                nx_[q].x = ZS::row(fbuf, ZS::srow(0, 0, q), lane);
+                if constexpr (Md::SD == 2) nx_[q].v = ZS::row(fbuf, ZS::srow(0, 1, q), lane);
+            }
+        }
+        typename Md::Acc acc;
+        Md::acc_begin(acc, n_steps, sh);
+        int g = pb.n_groups - 1;
+        for (int s = pb.n_seg - 1; s >= 0; --s) {
+            if (s > 0) {
+                ZS::issue(zstage, cl.ckpt, ch, ws_chunks, s - 1, lane);  // into the buffer of s + 1
+                cp_async_wait<1>();
+            } else {
+                cp_async_wait<0>();
+            }
+            __syncwarp();  // the other lanes' copies of segment s are visible
+            const Real *sbuf = zstage + (size_t)(s & 1) * ZS::kElems;
+            // the lane's rows of the segment, one 16-byte load per group (conflict-free)
+            typename ZS::V::T grp[ZS::Rp / ZS::kG];
+#pragma unroll
+            for (int k = 0; k < ZS::Rp / ZS::kG; ++k) grp[k] = *ZS::group(sbuf, k, lane);
+            if (g >= 0 && gseg[g] == s) {
+#pragma unroll
+                for (int q = 0; q < PPT; ++q) {
+                    const Real S = S0 * exp_r<Real>(nx_[q].x);
+                    Real seed = Real(0);
+                    for (int i = gbeg[g]; i < gbeg[g + 1]; ++i)
+                        if (S > strike[i]) seed = fma(sw[i], S, seed);
+                    if (active[q]) xb[q] += seed;
+                }
+                --g;
+            }
+#pragma unroll
+            for (int i = K - 1; i >= 0; --i) {
+                const int n = s * K + i;
+                Md::boundary(acc, n, sh, wg, lane);
+#pragma unroll
+                for (int q = 0; q < PPT; ++q) {
+                    typename Md::State cur;
+                    constexpr int kG = ZS::kG;
+                    cur.x = ZS::V::get(grp[ZS::srow(i, 0, q) / kG], ZS::srow(i, 0, q) % kG);
+                    if constexpr (Md::SD == 2) cur.v = ZS::V::get(grp[ZS::srow(i, 1, q) / kG], ZS::srow(i, 1, q) % kG);
+                    Md::adjoint_states(cur, nx_[q], n, xb[q], vb[q], acc, par, sh);
+                    nx_[q] = cur;
+                }
+            }
+        }
+        Real vb_sum = Real(0);
+#pragma unroll
+        for (int q = 0; q < PPT; ++q) vb_sum += vb[q];
+        Md::acc_end(acc, vb_sum, par, sh, wg, lane);
+    }
+    __syncthreads();
+    const double *wall = (const double *)(smem + sp.wacc_g);
+    for (int j = threadIdx.x; j < pb.M; j += blockDim.x) {
+        double sum = 0.0;
+        for (int w = 0; w < kWarpsPerBlock; ++w) sum += wall[w * pb.M + j];
+        cl.part_g[(size_t)blockIdx.x * pb.M + j] = sum;
+    }
+}
+
 // ---------------------------------------------------- full-storage variant --
 // The paper's branch for unconstrained memory (two-step algorithm, step 2:
 // with the first step's intermediate values kept, the reverse sweep costs
@@ -1104,6 +1400,11 @@ void set_kernels(Table *out) {
     out->rev_z = (const void *)path_reverse_kernel<Md, K, PPT, true>;
     out->stage_bytes_ckpt = SegTile<Md, K, PPT, false>::kBlockBytes;
     out->stage_bytes_z = SegTile<Md, K, PPT, true>::kBlockBytes;
+    if constexpr (Md::kind == kLv) {  // stored states: local vol only
+        out->fwd_x = (const void *)path_forward_states_kernel<Md, K, PPT>;
+        out->rev_x = (const void *)path_reverse_states_kernel<Md, K, PPT>;
+        out->stage_bytes_x = SegTile<Md, K, PPT, 2>::kBlockBytes;
+    }
 }
 
 }  // namespace mcaad

@@ -24,6 +24,10 @@ static bool pick(int K, int ppt, KernelPair *out) {
         set_kernels<LvModel<Real>, 5, 2>(out);
         return true;
     }
+    if (K == 5 && ppt == 4) {
+        set_kernels<LvModel<Real>, 5, 4>(out);
+        return true;
+    }
     return false;
 }
 

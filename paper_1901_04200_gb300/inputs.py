@@ -69,7 +69,8 @@ class Problem:
     paths_per_thread: int = 0
     # what the reverse sweep reads: "checkpoint" (states every K steps, re-run with
     # regenerated normals), "normals" (the checkpoints and every normal drawn),
-    # "full" (every step's tape), "auto" (normals if they fit a quarter of the
+    # "full" (every step's tape), "states" (local vol: the state before every step),
+    # "auto" (states for local vol, normals otherwise, if they fit a quarter of the
     # device's memory, else checkpoint)
     storage: str = "auto"
 
@@ -185,11 +186,11 @@ def heston_config(n_paths: int = 1 << 20, steps_per_year: int = 256, T: float = 
 
 def lv_config(n_paths: int = 1 << 22, n_steps: int = 500, T: float = 5.0, nt: int = 20,
               nx: int = 10, n_mat: int = 20, n_strike: int = 10, seed: int = PHILOX_SEED,
-              ckpt_every: int = 5, paths_per_thread: int = 2) -> Workload:
+              ckpt_every: int = 5, paths_per_thread: int = 4) -> Workload:
     """Bilinear local-vol surface over (t, ln S/S0); FP32 path arithmetic.  Segments of 5
-    steps with two paths per thread: the fastest launch shape measured on 2^22 x 500
-    (11.0 ms per value and gradient with stored normals, against 14.6 ms at K = 25 with one
-    path per thread)."""
+    steps with four paths per thread: the fastest launch shape measured on 2^22 x 500 with the
+    stored states the library picks for local vol (7.5 ms per value and gradient, against 8.1 ms
+    with two paths per thread and 8.5 ms with stored normals)."""
     dt = T / n_steps
     steps = (np.arange(1, n_mat + 1) * (n_steps // n_mat)).astype(np.int32)
     strikes = np.linspace(60.0, 150.0, n_strike)

@@ -122,8 +122,8 @@ def test_heston_fp64_no_feller(L, orc):
     check(L, orc, w, 1e-9, 1e-12)
 
 
-@pytest.mark.parametrize("storage", ["checkpoint", "normals"])
-@pytest.mark.parametrize("K,ppt", [(1, 1), (5, 1), (25, 1), (5, 2)])
+@pytest.mark.parametrize("storage", ["checkpoint", "normals", "states"])
+@pytest.mark.parametrize("K,ppt", [(1, 1), (5, 1), (25, 1), (5, 2), (5, 4)])
 def test_lv_fp64(L, orc, K, ppt, storage):
     w = inputs.lv_config(n_paths=1500, n_steps=100, T=2.0, nt=5, nx=6, n_mat=4, n_strike=5)
     w = replace(w, problem=replace(w.problem, precision="fp64", ckpt_every=K, paths_per_thread=ppt,
@@ -131,8 +131,8 @@ def test_lv_fp64(L, orc, K, ppt, storage):
     check(L, orc, w, 1e-10, 1e-12)
 
 
-@pytest.mark.parametrize("storage", ["checkpoint", "normals"])
-@pytest.mark.parametrize("K,ppt", [(1, 1), (5, 1), (5, 2)])
+@pytest.mark.parametrize("storage", ["checkpoint", "normals", "states"])
+@pytest.mark.parametrize("K,ppt", [(1, 1), (5, 1), (5, 2), (5, 4)])
 def test_lv_fp64_partial_philox_period(L, orc, K, ppt, storage):
     """95 steps: 19 segments at K = 5 and 95 at K = 1, so the forward sweep's last group of
     segments (four per Philox period of 20 or 4 normals) is partial."""
@@ -142,9 +142,10 @@ def test_lv_fp64_partial_philox_period(L, orc, K, ppt, storage):
     check(L, orc, w, 1e-10, 1e-12)
 
 
-def test_lv_fp64_clamped_surface(L, orc):
+@pytest.mark.parametrize("storage", ["normals", "states"])
+def test_lv_fp64_clamped_surface(L, orc, storage):
     w = inputs.lv_config(n_paths=999, n_steps=100, T=2.0, nt=5, nx=6, n_mat=4, n_strike=5)
-    w = replace(w, problem=replace(w.problem, precision="fp64", x_lo=-0.1, x_hi=0.15))
+    w = replace(w, problem=replace(w.problem, precision="fp64", x_lo=-0.1, x_hi=0.15, storage=storage))
     check(L, orc, w, 1e-10, 1e-12)
 
 
@@ -292,7 +293,7 @@ def full_size_sampled(L, orc, w, n_slice):
 def test_lv_full_size_sampled(L, orc):
     """2^22 x 500 local vol (the bench's headline workload and launch shape)."""
     ctx = full_size_sampled(L, orc, inputs.lv_config(), 1 << 13)
-    assert ctx.storage == "normals"
+    assert ctx.storage == "states"
 
 
 # ------------------------------------------------- Heston SLV (the paper's model)
@@ -365,8 +366,8 @@ def test_stored_normals_staging_shapes_fp64(L, orc, kind, K, ppt):
           1e-10, 1e-12)
 
 
-@pytest.mark.parametrize("storage", STORED)
-@pytest.mark.parametrize("kind", ["heston", "lv", "slv"])
+@pytest.mark.parametrize("kind,storage", [(k, st) for k in ("heston", "lv", "slv") for st in STORED]
+                         + [("lv", "states")])
 def test_stored_equals_recompute_fp32(L, kind, storage):
     """The stored variants run the same step arithmetic as checkpoint/recompute: the same
     E y, and the gradient to FP32 rounding of the re-run segments."""
@@ -406,11 +407,58 @@ def test_heston_full_size_stored_normals(L, orc):
 
 
 def test_auto_storage_resolves(L):
-    """"auto" picks the stored normals when they fit a quarter of the device's memory."""
+    """"auto" picks the stored normals (local vol: the stored states) when they fit a quarter of
+    the device's memory."""
     w = inputs.heston_config(n_paths=4096, steps_per_year=16, T=1.0, n_mat=2, n_strike=3)
     assert L.Context(w.problem, max_paths=4096).storage == "normals"
     for st in ("checkpoint", "normals", "full"):
         assert L.Context(with_pb(w, storage=st).problem, max_paths=4096).storage == st
+    wl = small_case("lv", n_paths=4096)
+    assert L.Context(wl.problem, max_paths=4096).storage == "states"
+
+
+# ----------------------------------------------- stored states (local vol)
+# The forward sweep stores the state before every step; the reverse sweep runs only the
+# adjoint, with each step's sqrt(dt) z taken from the states at its two ends.
+
+@pytest.mark.parametrize("n", [1, 31, 33, 4097])
+@pytest.mark.parametrize("precision,tol_g,tol_ey", [("fp64", 1e-10, 1e-12), ("fp32", 1e-4, 2e-6)])
+def test_states_ragged(L, orc, n, precision, tol_g, tol_ey):
+    w = with_pb(small_case("lv", n_paths=n), precision=precision, storage="states")
+    check(L, orc, w, tol_g, tol_ey, path0=5)
+
+
+def test_states_vjp_after_forward(L, orc):
+    """mc_forward with kept results, then mc_vjp with an arbitrary seed, on the stored states."""
+    w = with_pb(small_case("lv"), precision="fp64", storage="states")
+    ctx = L.Context(w.problem, max_paths=w.n_paths)
+    Ey = ctx.forward(w.theta, w.problem.seed, w.n_paths, path0=3, keep=True).cpu().numpy()
+    ybar = np.linspace(-1.0, 1.0, len(Ey))
+    g = ctx.vjp(ybar).cpu().numpy()
+    assert rel(Ey, orc.forward(w.problem, w.theta, w.n_paths, path0=3)) <= 1e-12
+    assert rel(g, orc.vjp(w.problem, w.theta, ybar, w.n_paths, path0=3)) <= 1e-10
+
+
+def test_states_single_segment_and_reuse(L, orc):
+    """One segment (K = 25 over 25 steps: the extra tile follows directly), and a context reused
+    with fewer paths, another seed and other node values."""
+    w = with_pb(inputs.lv_config(n_paths=700, n_steps=25, T=0.5, nt=3, nx=4, n_mat=1, n_strike=4),
+                precision="fp64", storage="states", ckpt_every=25, paths_per_thread=1)
+    check(L, orc, w, 1e-10, 1e-12)
+    ctx = L.Context(w.problem, max_paths=700)
+    th = w.theta * 1.1
+    G, g, Ey = (x.cpu().numpy() for x in ctx.value_and_grad(th, w.C, 99, 400, path0=11))
+    pb = replace(w.problem, seed=99)
+    Eo, Go, go = orc.value_and_grad(pb, th, w.C, 400, path0=11)
+    assert rel(Ey, Eo) <= 1e-12 and abs(G[0] - Go) <= 1e-10 * abs(Go) and rel(g, go) <= 1e-10
+
+
+@pytest.mark.parametrize("kind", ["gbm", "heston", "slv"])
+def test_states_only_for_local_vol(L, kind):
+    w = with_pb(small_case(kind, n_paths=64), storage="states")
+    with pytest.raises(L.McError) as e:
+        L.Context(w.problem, max_paths=64)
+    assert e.value.status == L.MC_ERR_UNSUPPORTED
 
 
 @pytest.mark.slow

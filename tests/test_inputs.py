@@ -44,7 +44,7 @@ def test_local_vol_workload():
     pb = w.problem
     assert w.n_paths == 1 << 22 and pb.kind == "lv" and pb.n_steps == 500 and abs(pb.dt - 0.01) < 1e-15
     assert (pb.nt, pb.nx, pb.x_lo, pb.x_hi, pb.t_max) == (20, 10, -1.0, 1.0, 5.0)
-    assert pb.ckpt_every == 5 and pb.paths_per_thread == 2 and pb.m == 200
+    assert pb.ckpt_every == 5 and pb.paths_per_thread == 4 and pb.m == 200
     steps, strikes = _by_maturity(pb)
     assert steps == [25 * k for k in range(1, 21)]
     for k in strikes:
