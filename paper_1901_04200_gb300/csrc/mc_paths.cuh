@@ -296,7 +296,8 @@ struct LvModel {
         const Real *node; // node_table: [nt-1][nx][2] (theta[j][c], theta[j+1][c] - theta[j][c])
         int nx;
     };
-    struct Par { Real rdt, dt, sdt, x_lo, inv_hx; int nxm2; };
+    // u0 = -x_lo / hx, so that the scaled coordinate u = (x - x_lo) / hx is one FMA
+    struct Par { Real rdt, dt, sdt, x_lo, inv_hx, u0, nxm1; int nxm2; };
     // jt: the time row being accumulated; at, oma: a_n and 1 - a_n of the step
     // whose adjoints run next
     struct Acc { int jt; Real at, oma; };
@@ -341,33 +342,37 @@ struct LvModel {
         par.sdt = (Real)sqrt(pb.dt);
         par.x_lo = (Real)pb.x_lo;
         par.inv_hx = (Real)(1.0 / pb.hx);
+        par.u0 = (Real)(-pb.x_lo / pb.hx);
+        par.nxm1 = (Real)(nx - 1);
         par.nxm2 = nx - 2;
     }
     __device__ static State init(const Par &) { return State{Real(0)}; }
 
-    // Cell c = clamp(floor(u), 0, nx-2) = floor(clamp(u, 0, nx-2)) and weight
-    // b = clamp(u - c, 0, 1).  In FP32 the floor of the clamped u (in [0, 30])
-    // comes from one addition of 1.5 2^23 rounded toward minus infinity: the
-    // sum's last place is 1, so it holds 1.5 2^23 + floor, its low bits are the
-    // integer, and subtracting 1.5 2^23 again is exact -- no conversion
-    // instructions.
+    // The scaled coordinate u = (x - x_lo) / hx.
+    __device__ __forceinline__ static Real scaled(Real x, const Par &p) { return fma(x, p.inv_hx, p.u0); }
+    // Cell c = clamp(floor(u), 0, nx-2) and weight b = clamp(u - c, 0, 1): with uc = clamp(u, 0,
+    // nx-1), c = floor(min(uc, nx-2)) and b = uc - c lies in [0, 1] by construction; inside
+    // (x not clamped, d sigma/dx not zero) is u == uc.  In FP32 the floor (of a value in
+    // [0, 30]) comes from one addition of 1.5 2^23 rounded toward minus infinity: the sum's last
+    // place is 1, so it holds 1.5 2^23 + floor, its low bits are the integer, and subtracting
+    // 1.5 2^23 again is exact -- no conversion instructions.
     __device__ __forceinline__ static void cell(Real u, const Par &p, int &c, Real &b, bool &inside) {
+        const Real uc = fmin(fmax(u, Real(0)), p.nxm1);
         Real f;
         if constexpr (sizeof(Real) == 4) {
-            const float r = __fadd_rd(fminf(fmaxf(u, 0.0f), (float)p.nxm2), 12582912.0f);
+            const float r = __fadd_rd(fminf(uc, (float)p.nxm2), 12582912.0f);
             f = r - 12582912.0f;
             c = __float_as_int(r) - 0x4B400000;
         } else {
-            f = fmin(fmax(floor(u), Real(0)), (Real)p.nxm2);
+            f = floor(fmin(uc, (Real)p.nxm2));
             c = (int)f;
         }
-        const Real bb = u - f;
-        inside = (bb >= Real(0)) && (bb <= Real(1));
-        b = fmin(fmax(bb, Real(0)), Real(1));
+        b = uc - f;
+        inside = u == uc;
     }
     __device__ __forceinline__ static void step(State &s, const Real *z, int n, const Par &p,
                                                 const Shared &sh, Tape *t) {
-        const Real u = (s.x - p.x_lo) * p.inv_hx;
+        const Real u = scaled(s.x, p);
         int c;
         Real b;
         bool inside;
@@ -461,7 +466,7 @@ struct LvModel {
     // so the adjoint needs neither the normal nor a re-run of the step (sigma != 0).
     __device__ __forceinline__ static void adjoint_states(const State &s0, const State &s1, int n, Real &xb, Real &,
                                                           Acc &a, const Par &p, const Shared &sh) {
-        const Real u = (s0.x - p.x_lo) * p.inv_hx;
+        const Real u = scaled(s0.x, p);
         int c;
         Real b;
         bool inside;
@@ -521,7 +526,7 @@ struct SlvModel {
     __device__ static State init(const Par &p) { return State{Real(0), p.h.v0}; }
     __device__ __forceinline__ static void step(State &s, const Real *z, int n, const Par &p,
                                                 const Shared &sh, Tape *t) {
-        const Real u = (s.x - p.l.x_lo) * p.l.inv_hx;
+        const Real u = Lv::scaled(s.x, p.l);
         int c;
         Real b;
         bool inside;
