@@ -944,14 +944,20 @@ __global__ void __launch_bounds__(kBlock) path_reverse_kernel(const DevProblem p
                 }
             }
             if (g >= 0 && gseg[g] == s) {
+                Real S[PPT], seed[PPT];
 #pragma unroll
                 for (int q = 0; q < PPT; ++q) {
-                    const Real S = S0 * exp_r<Real>(st[q].x);
-                    Real seed = Real(0);
-                    for (int i = gbeg[g]; i < gbeg[g + 1]; ++i)
-                        if (S > strike[i]) seed = fma(sw[i], S, seed);
-                    if (active[q]) xb[q] += seed;
+                    S[q] = S0 * exp_r<Real>(st[q].x);
+                    seed[q] = Real(0);
                 }
+                for (int i = gbeg[g]; i < gbeg[g + 1]; ++i) {  // each strike and weight read once
+                    const Real k = strike[i], wgt = sw[i];
+#pragma unroll
+                    for (int q = 0; q < PPT; ++q) seed[q] = S[q] > k ? fma(wgt, S[q], seed[q]) : seed[q];
+                }
+#pragma unroll
+                for (int q = 0; q < PPT; ++q)
+                    if (active[q]) xb[q] += seed[q];
                 --g;
             }
 #pragma unroll
@@ -1177,14 +1183,20 @@ __global__ void __launch_bounds__(kBlock) path_reverse_states_kernel(const DevPr
 #pragma unroll
             for (int k = 0; k < ZS::Rp / ZS::kG; ++k) grp[k] = *ZS::group(sbuf, k, lane);
             if (g >= 0 && gseg[g] == s) {
+                Real S[PPT], seed[PPT];
 #pragma unroll
                 for (int q = 0; q < PPT; ++q) {
-                    const Real S = S0 * exp_r<Real>(nx_[q].x);
-                    Real seed = Real(0);
-                    for (int i = gbeg[g]; i < gbeg[g + 1]; ++i)
-                        if (S > strike[i]) seed = fma(sw[i], S, seed);
-                    if (active[q]) xb[q] += seed;
+                    S[q] = S0 * exp_r<Real>(nx_[q].x);
+                    seed[q] = Real(0);
                 }
+                for (int i = gbeg[g]; i < gbeg[g + 1]; ++i) {  // each strike and weight read once
+                    const Real k = strike[i], wgt = sw[i];
+#pragma unroll
+                    for (int q = 0; q < PPT; ++q) seed[q] = S[q] > k ? fma(wgt, S[q], seed[q]) : seed[q];
+                }
+#pragma unroll
+                for (int q = 0; q < PPT; ++q)
+                    if (active[q]) xb[q] += seed[q];
                 --g;
             }
 #pragma unroll
