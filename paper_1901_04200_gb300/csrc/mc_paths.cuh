@@ -868,8 +868,15 @@ __global__ void __launch_bounds__(kBlock) path_forward_kernel(const DevProblem p
     }
 }
 
+// Resident blocks per SM the reverse sweep is compiled for: long local-vol segments (K = 25, one
+// path per thread: 25 steps unrolled with their tapes) otherwise take up to 253 registers, two
+// blocks per SM; three blocks (at most 168 registers) measured faster.
+template <class Md, int K>
+__host__ __device__ constexpr int reverse_min_blocks() { return (Md::kind == kLv && K >= 25) ? 3 : 1; }
+
 template <class Md, int K, int PPT, bool kLoadZ = false>
-__global__ void __launch_bounds__(kBlock) path_reverse_kernel(const DevProblem pb, const DevCall cl) {
+__global__ void __launch_bounds__(kBlock, (reverse_min_blocks<Md, K>())) path_reverse_kernel(const DevProblem pb,
+                                                                                             const DevCall cl) {
     using Real = typename Md::Real;
     using ZS = SegTile<Md, K, PPT, kLoadZ>;
     extern __shared__ __align__(16) unsigned char smem[];
