@@ -102,11 +102,12 @@ def kernel_bytes(model, storage, K, S, n_groups):
 # sources' code (comments and layout aside) hashes to the captured version.  Key: (model,
 # storage, K, paths per thread, kernel).
 MEASURED_TRAFFIC = {
-    # 2^19 of 2^22 paths (x 8): read 1.258435 GB + write 3.349504 MB; read 189.44 KB + write 1.197627 GB
-    ("lv", "normals", 5, 2, "reverse_sweep"): {"bytes": 10094276032, "sources": "2c91e802b4f5d7dd"},
-    ("lv", "normals", 5, 2, "forward_sweep"): {"bytes": 9582531520, "sources": "2c91e802b4f5d7dd"},
-    # 2^18 of 2^20 paths (x 4): read 236.288 KB + write 1.146647 GB
-    ("heston", "normals", 8, 2, "forward_sweep"): {"bytes": 4587533152, "sources": "54f0a78454a8cd82"},
+    # stored states, 2^20 of 2^22 paths (x 4): read 2.118247 GB + write 5.651 MB; read 0.112 MB + write 2.040825 GB
+    ("lv", "states", 5, 4, "reverse_sweep"): {"bytes": 8495592000, "sources": "07c64ee22ca8b8cb"},
+    ("lv", "states", 5, 4, "forward_sweep"): {"bytes": 8163748000, "sources": "07c64ee22ca8b8cb"},
+    # stored normals, 2^18 of 2^20 paths (x 4): read 1.208042 GB + write 0.583 MB; read 0.045 MB + write 1.146336 GB
+    ("heston", "normals", 8, 2, "reverse_sweep"): {"bytes": 4834500000, "sources": "17ad4774d2211d15"},
+    ("heston", "normals", 8, 2, "forward_sweep"): {"bytes": 4585524000, "sources": "17ad4774d2211d15"},
 }
 KERNEL_SOURCES = ["mc_common.cuh", "mc_paths.cuh"]
 MODEL_SOURCE = {"gbm": "mc_paths_gbm.cu", "heston": "mc_paths_heston.cu", "lv": "mc_paths_lv.cu",
