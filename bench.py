@@ -426,7 +426,8 @@ def tape_bench(args, rank, world):
     ctx = tape.TapeContext(prog, G, 5, max_paths=P, device=dev, precision=args.tape_precision)
     compile_s, per_path = None, tape.plan(prog, G, 5, P, args.tape_precision)[4]  # interpreter HBM bytes per path
     if not args.tape_interpret:
-        compile_s, per_path = ctx.compile(seg_nodes=args.tape_seg, recompute=args.tape_recompute)  # untimed
+        compile_s, per_path = ctx.compile(seg_nodes=args.tape_seg, recompute=args.tape_recompute,
+                                          piece=args.tape_piece)  # untimed
     theta = torch.tensor(w.theta, dtype=torch.float64, device=dev)
     out = (torch.empty(1, dtype=torch.float64, device=dev), torch.empty(5, dtype=torch.float64, device=dev))
     path0 = rank * P
@@ -467,8 +468,10 @@ def tape_bench(args, rank, world):
                        "precision": args.tape_precision + " per-path values and adjoints, fp64 sums",
                        "execution": "interpreter" if args.tape_interpret else
                                     "compiled (segments of %s nodes%s, %.1f s run-time compilation)"
-                                    % (args.tape_seg or 384, ", backward recomputes" if args.tape_recompute else "",
-                                       compile_s),
+                                    % (args.tape_seg or 384,
+                                       (", backward recomputes in pieces of %d nodes" % args.tape_piece
+                                        if args.tape_piece >= 2 else ", backward recomputes")
+                                       if args.tape_recompute else "", compile_s),
                        "l2": "inputs larger than L2: %.1f GB of tape and adjoints" % (byts / 1e9)},
             "roofline": {"bound": "hbm", "achieved": byts / (ms * 1e-3) / 1e9, "peak": hbm / 1e9, "unit": "GB/s",
                          "frac": byts / (ms * 1e-3) / hbm, "traffic": None,
@@ -843,6 +846,9 @@ def main():
                     help="per-path values and adjoints of the --workload tape run")
     ap.add_argument("--tape-interpret", action="store_true",
                     help="--workload tape: run the interpreter instead of the compiled program")
+    ap.add_argument("--tape-piece", type=int, default=256,
+                    help="--workload tape: backward recompute in pieces of this many nodes (0: whole segments); "
+                         "256 measured fastest with 768-node segments")
     ap.add_argument("--tape-seg", type=int, default=768,
                     help="--workload tape: nodes per compiled segment (0 = library default, 384)")
     ap.add_argument("--tape-store", dest="tape_recompute", action="store_false",

@@ -135,7 +135,10 @@ mc_status mc_tape_value_and_grad(mc_tape *t, const double *theta, uint64_t seed,
  * partials, through the HBM tape (with recompute != 0, the backward kernel
  * first re-runs its segment's forward code, normals included, so only values
  * crossing a segment or stage boundary or feeding an expectation use the
- * tape); the rest of the evaluation (deterministic
+ * tape; with recompute >= 2, the backward kernel does that in pieces of
+ * `recompute` nodes, last piece first, each piece loading the values it needs
+ * from earlier pieces, which the forward kernel then keeps on the tape: one
+ * piece's values live in registers at a time); the rest of the evaluation (deterministic
  * nodes, expectations, fixed-order sums) is unchanged, so the results agree
  * with the interpreter's to the rounding of the reordered sums.  Later
  * mc_tape_value_and_grad calls run the compiled kernels.  Allocates a small

@@ -782,6 +782,7 @@ struct JitSeg {
 
 struct JitPlan {
     bool recompute = false;             // backward kernels re-run their segment's forward
+    int piece = 0;                      // with recompute: pieces of this many nodes (0: the whole segment)
     std::vector<JitSeg> segs;           // stage order, then program order
     std::vector<int> seg_begin;         // per stage: first segment; + end entry
     std::vector<char> store, far;       // per node, compiled mode
@@ -924,12 +925,17 @@ namespace {
 
 // ------------------------------------------------ tape compiler: plan ----
 
+// piece > 0 (with recompute): the backward kernel re-runs and differentiates its segment in
+// pieces of `piece` consecutive nodes, last piece first; a value one piece computes and a later
+// piece of the same segment uses is kept by the forward kernel on the tape, so each piece starts
+// from loads and only one piece's values are live at a time.
 JitPlan *make_jit_plan(const std::vector<mc_tape_node> &nodes, const TapePlan &p, int seg_nodes, size_t rb,
-                       bool recompute) {
+                       bool recompute, int piece = 0) {
     JitPlan *J = new JitPlan;
     J->recompute = recompute;
+    J->piece = recompute ? std::max(piece, 0) : 0;
     const int n = p.n_nodes;
-    std::vector<int> seg_of(n, -1);
+    std::vector<int> seg_of(n, -1), piece_of(n, -1);
     for (int s = 0; s < p.n_stages; ++s) {
         J->seg_begin.push_back((int)J->segs.size());
         const std::vector<int> &path = p.st[s].path;
@@ -939,6 +945,7 @@ JitPlan *make_jit_plan(const std::vector<mc_tape_node> &nodes, const TapePlan &p
             for (size_t k = k0; k < std::min(path.size(), k0 + (size_t)seg_nodes); ++k) {
                 sg.nodes.push_back(path[k]);
                 seg_of[path[k]] = (int)J->segs.size();
+                piece_of[path[k]] = J->piece > 0 ? (int)((k - k0) / (size_t)J->piece) : 0;
             }
             J->segs.push_back(std::move(sg));
         }
@@ -952,6 +959,7 @@ JitPlan *make_jit_plan(const std::vector<mc_tape_node> &nodes, const TapePlan &p
             const int a = args[q];
             if (p.cls[a] != 1) continue;
             if (!(p.cls[i] == 1 && seg_of[i] == seg_of[a])) J->store[a] = J->far[a] = 1;  // outside user
+            else if (piece_of[i] != piece_of[a]) J->store[a] = 1;  // a later piece's input
             if (!recompute && needs_arg_value(nodes[i].op, q)) J->store[a] = 1;
         }
         if (!recompute && p.cls[i] == 1 && needs_own_value(nodes[i].op)) J->store[i] = 1;
@@ -986,8 +994,25 @@ JitPlan *make_jit_plan(const std::vector<mc_tape_node> &nodes, const TapePlan &p
                 if (needs_arg_value(nodes[i].op, q)) add(bwd_loads, a);
             }
         }
-        // with recompute the backward kernel loads what the forward kernel loads, and nothing more
-        b += rb * (fwd_loads.size() + (recompute ? fwd_loads.size() : bwd_loads.size())) + 2 * rb * far_rows.size();
+        // with recompute the backward kernel loads what the forward kernel loads (in pieces: also each
+        // piece's inputs from earlier pieces), and nothing more
+        size_t piece_loads = 0;
+        if (J->piece > 0) {
+            std::vector<std::pair<int, int>> seen;  // (piece, value)
+            for (int i : sg.nodes) {
+                const int args[2] = {nodes[i].a, nodes[i].b};
+                for (int q = 0; q < n_args(nodes[i].op); ++q) {
+                    const int a = args[q];
+                    if (p.cls[a] == 1 && seg_of[a] == (int)k && piece_of[a] != piece_of[i]) {
+                        const std::pair<int, int> key(piece_of[i], a);
+                        if (std::find(seen.begin(), seen.end(), key) == seen.end()) seen.push_back(key);
+                    }
+                }
+            }
+            piece_loads = seen.size();
+        }
+        b += rb * (fwd_loads.size() + (recompute ? fwd_loads.size() + piece_loads : bwd_loads.size())) +
+             2 * rb * far_rows.size();
         for (int d : sg.dargs) J->dslot.push_back(-p.ref[d] - 1);
     }
     J->bytes_per_path = b;
@@ -1018,19 +1043,22 @@ std::string gen_segment(const std::vector<mc_tape_node> &nodes, const TapePlan &
 
     // The segment's forward body: values in registers; values from outside the segment loaded
     // at first use through `ptr` (w<row>); with `stores`, values flagged kept go to the tape.
-    auto emit_forward = [&](bool stores, const char *ptr) {
+    // Nodes [q0, q1) of the segment (all of them by default): values computed before q0 count as
+    // loaded from the tape like values from outside the segment.
+    auto emit_forward = [&](bool stores, const char *ptr, size_t q0 = 0, size_t q1 = (size_t)-1) {
+        if (q1 > sg.nodes.size()) q1 = sg.nodes.size();
         std::vector<char> loaded(p.n_nodes, 0);
         long long call = -1;
         auto val = [&](int a) -> std::string {
             if (p.cls[a] == 0) return det_ref(a);
-            if (local[a] >= 0) return "v" + std::to_string(local[a]);
+            if (local[a] >= (int)q0) return "v" + std::to_string(local[a]);
             if (!loaded[a]) {
                 o << "  const R w" << p.ref[a] << " = " << ptr << "[(u64)" << p.ref[a] << " * stride];\n";
                 loaded[a] = 1;
             }
             return "w" + std::to_string(p.ref[a]);
         };
-        for (size_t q = 0; q < sg.nodes.size(); ++q) {
+        for (size_t q = q0; q < q1; ++q) {
             const int i = sg.nodes[q];
             const mc_tape_node &d = nodes[i];
             const std::string A = n_args(d.op) >= 1 ? val(d.a) : std::string();
@@ -1108,18 +1136,27 @@ std::string gen_segment(const std::vector<mc_tape_node> &nodes, const TapePlan &
          "  const bool active = p < n_paths;\n"
          "  const R *tv = tape + p;\n"
          "  R *ta = adj + p;\n";
-    if (J.recompute) {  // the segment's values, re-run in registers: the partials need no tape loads
-        o << "  mcaad::PathNormals<R> rng;\n  rng.init(path0 + (active ? p : 0));\n";
-        emit_forward(false, "tv");
-    }
-    for (size_t q = 0; q < sg.nodes.size(); ++q) o << "  R a" << q << " = R(0);\n";
+    // With recompute the segment's values are re-run in registers (the partials need no tape loads):
+    // all at once, or piece by piece from the last piece, each piece's inputs loaded from the tape.
+    const size_t nq = sg.nodes.size();
+    const size_t piece = J.recompute && J.piece > 0 ? (size_t)J.piece : nq;
+    if (J.recompute) o << "  mcaad::PathNormals<R> rng;\n  rng.init(path0 + (active ? p : 0));\n";
+    if (J.recompute && piece >= nq) emit_forward(false, "tv");
+    for (size_t q = 0; q < nq; ++q) o << "  R a" << q << " = R(0);\n";
     for (int a : far_rows) o << "  R f" << p.ref[a] << " = R(0);\n";
     for (size_t l = 0; l < sg.dargs.size(); ++l) o << "  R g" << l << " = R(0);\n";
-    {
+    for (size_t q1 = nq; q1 > 0;) {
+        const size_t q0 = (q1 - 1) / piece * piece;  // pieces start at multiples of `piece`, as planned
+        const bool pieced = J.recompute && piece < nq;
+        if (pieced) {
+            o << "  {\n";
+            emit_forward(false, "tv", q0, q1);
+        }
         std::vector<char> vloaded(p.n_nodes, 0);
         auto value = [&](int a) -> std::string {
             if (p.cls[a] == 0) return det_ref(a);
-            if (J.recompute) return local[a] >= 0 ? "v" + std::to_string(local[a]) : "w" + std::to_string(p.ref[a]);
+            if (J.recompute) return local[a] >= (int)(pieced ? q0 : 0) ? "v" + std::to_string(local[a])
+                                                                      : "w" + std::to_string(p.ref[a]);
             if (!vloaded[a]) {
                 o << "  const R u" << p.ref[a] << " = tv[(u64)" << p.ref[a] << " * stride];\n";
                 vloaded[a] = 1;
@@ -1134,7 +1171,7 @@ std::string gen_segment(const std::vector<mc_tape_node> &nodes, const TapePlan &
             else
                 o << "  f" << p.ref[a] << " += " << g << ";\n";
         };
-        for (int q = (int)sg.nodes.size() - 1; q >= 0; --q) {
+        for (int q = (int)q1 - 1; q >= (int)q0; --q) {
             const int i = sg.nodes[q];
             const mc_tape_node &d = nodes[i];
             const std::string D = "D" + std::to_string(q);
@@ -1181,6 +1218,8 @@ std::string gen_segment(const std::vector<mc_tape_node> &nodes, const TapePlan &
             default: break;
             }
         }
+        if (pieced) o << "  }\n";
+        q1 = q0;
     }
     for (int a : far_rows) o << "  if (active) ta[(u64)" << p.ref[a] << " * stride] += f" << p.ref[a] << ";\n";
     for (size_t l = 0; l < sg.dargs.size(); ++l)
@@ -1472,7 +1511,7 @@ mc_status mc_tape_compile(mc_tape *t, int32_t seg_nodes, int32_t recompute, int3
     if (threads <= 0) threads = (int)std::max(1u, std::thread::hardware_concurrency());
     const auto t0 = std::chrono::steady_clock::now();
     const size_t rb = t->precision == MC_FP64 ? 8 : 4;
-    JitPlan *J = make_jit_plan(t->src_nodes, t->plan, seg_nodes, rb, recompute != 0);
+    JitPlan *J = make_jit_plan(t->src_nodes, t->plan, seg_nodes, rb, recompute != 0, recompute > 1 ? recompute : 0);
     const int nseg = (int)J->segs.size();
     for (int k = 0; k < nseg; ++k) J->segs[k].src = gen_segment(t->src_nodes, t->plan, *J, k, t->precision);
     std::atomic<int> next(0), failed(-1);

@@ -172,13 +172,15 @@ class TapeContext:
         self._n = int(n_paths)
         return val, grad[:self.n_params]
 
-    def compile(self, seg_nodes: int = 0, recompute: bool = False, threads: int = 0):
+    def compile(self, seg_nodes: int = 0, recompute: bool = False, threads: int = 0, piece: int = 0):
         """Compile the program into straight-line kernels (mc_tape_compile); with recompute the
-        backward kernels re-run their segment's forward instead of reloading values.  Returns
-        (compile seconds, HBM bytes per path of one compiled value and gradient)."""
+        backward kernels re-run their segment's forward instead of reloading values, in pieces of
+        `piece` nodes when piece >= 2 (each piece's inputs kept on the tape by the forward kernel).
+        Returns (compile seconds, HBM bytes per path of one compiled value and gradient)."""
         from . import _lib
         sec, hb = ctypes.c_double(0.0), ctypes.c_size_t(0)
-        self._check(_lib.load().mc_tape_compile(self.handle, int(seg_nodes), 1 if recompute else 0, int(threads),
+        mode = (int(piece) if piece >= 2 else 1) if recompute else 0
+        self._check(_lib.load().mc_tape_compile(self.handle, int(seg_nodes), mode, int(threads),
                                                 ctypes.byref(sec), ctypes.byref(hb)))
         return sec.value, hb.value
 

@@ -224,10 +224,10 @@ def test_heston_tape_bench_size_equals_two_step(T):
 
 # ------------------------------------------------------ compiled programs
 
-@pytest.mark.parametrize("recompute", [False, True])
+@pytest.mark.parametrize("recompute,piece", [(False, 0), (True, 0), (True, 3), (True, 16)])
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
 @pytest.mark.parametrize("seed,seg", [(1, 40), (3, 7), (4, 1000)])
-def test_compiled_equals_interpreter_and_oracle(T, orc, seed, seg, precision, tol, recompute):
+def test_compiled_equals_interpreter_and_oracle(T, orc, seed, seg, precision, tol, recompute, piece):
     """mc_tape_compile: straight-line segment kernels give the interpreter's results (to the
     rounding of reordered sums) and the oracle's."""
     P = 3000
@@ -238,7 +238,7 @@ def test_compiled_equals_interpreter_and_oracle(T, orc, seed, seg, precision, to
     a = T.TapeContext(prog, nodes[obj], 4, max_paths=P, precision=precision)
     Ga, ga = a.value_and_grad(theta, phil, P)
     b = T.TapeContext(prog, nodes[obj], 4, max_paths=P, precision=precision)
-    sec, hb = b.compile(seg_nodes=seg, recompute=recompute)
+    sec, hb = b.compile(seg_nodes=seg, recompute=recompute, piece=piece)
     assert sec > 0 and hb > 0
     Gb, gb = b.value_and_grad(theta, phil, P)
     assert abs(Gb.item() - Ga.item()) <= tol * max(abs(Ga.item()), 1.0)
@@ -253,12 +253,13 @@ def test_compiled_equals_interpreter_and_oracle(T, orc, seed, seg, precision, to
                 assert rel(b.path_values(nodes[k]).cpu().numpy(), vals[k].v) <= 1e-12
 
 
-def test_compiled_heston_objective_equals_two_step(T, orc):
+@pytest.mark.parametrize("piece", [0, 16])
+def test_compiled_heston_objective_equals_two_step(T, orc, piece):
     w = inputs.heston_config(n_paths=2000, steps_per_year=16, T=1.0, n_mat=4, n_strike=3)
     pb = replace(w.problem, precision="fp64", ckpt_every=4)
     prog, G = T.heston_objective(pb, w.C)
     ctx = T.TapeContext(prog, G, 5, max_paths=2000)
-    ctx.compile(seg_nodes=64, recompute=True)
+    ctx.compile(seg_nodes=64, recompute=True, piece=piece)
     Gt, gt = ctx.value_and_grad(w.theta, pb.seed, 2000, path0=77)
     _, Go, go = orc.value_and_grad(pb, w.theta, w.C, 2000, path0=77)
     assert abs(Gt.item() - Go) <= 1e-10 * abs(Go)
