@@ -745,7 +745,7 @@ def run_path_workload(model, args, rank, world, local, headline):
                    "l2": "inputs larger than L2: %.0f MB stored and re-read per step" %
                          (P * S * bytes_ps["forward_sweep"] / 1e6)},
         "roofline": roofline,
-        "kernels_ms_per_step": {k: v[0] / max(v[1], 1) for k, v in prof.items() if v[1]},
+        "kernels_ms_per_step": {k: v[0] / steps for k, v in prof.items() if v[1]},
         "gpu_launches": sum(n for _, n in prof.values()),
         "e2e": {"value": world * P * S / (e2e_ms * 1e-3), "unit": UNIT,
                 "h2d_bytes_per_step": 8 * (ctx.M + ctx.m), "d2h_bytes_per_step": 8 * (1 + ctx.M + ctx.m)},

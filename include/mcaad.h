@@ -323,8 +323,10 @@ mc_status mc_normals_fill(uint64_t seed, uint64_t path0, uint32_t n_paths, uint3
  * MC_K_FINALIZE_T (mc_value_and_grad_tangent).
  * mc_profile_begin creates events for up to max_launches launches (host
  * call).  mc_profile_end waits for the recorded events, writes the summed
- * milliseconds and launch counts per kernel id into ms_out[MC_N_KERNELS] and
- * launches_out[MC_N_KERNELS] (either may be NULL), and stops recording. */
+ * milliseconds and kernel launches per kernel id into ms_out[MC_N_KERNELS]
+ * and launches_out[MC_N_KERNELS] (either may be NULL; a finalize that first
+ * folds many partial rows in a second kernel counts two launches under one
+ * event pair, max_launches counts event pairs), and stops recording. */
 enum { MC_K_FORWARD = 0, MC_K_FINALIZE_Y = 1, MC_K_SEED = 2, MC_K_REVERSE = 3, MC_K_FINALIZE_G = 4,
        MC_K_TANGENT = 5, MC_K_FINALIZE_T = 6, MC_N_KERNELS = 7 };
 mc_status mc_profile_begin(mc_ctx *ctx, int32_t max_launches);

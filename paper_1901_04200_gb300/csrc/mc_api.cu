@@ -52,7 +52,9 @@ struct mc_ctx {
     void *ckpt = nullptr;
     void *tape = nullptr, *xmat = nullptr;
     double *part_y = nullptr, *part_g = nullptr, *seed_w = nullptr, *lam2 = nullptr;
+    double *part1_y = nullptr, *part1_g = nullptr;  // first-level sums of the finalize
     unsigned int *ticket = nullptr;
+    unsigned long long *queue = nullptr;  // the path sweeps' chunk queue (two words, zero between launches)
     // state for mc_vjp
     bool have_ckpt = false;
     DevCall last{};
@@ -61,7 +63,7 @@ struct mc_ctx {
     bool prof_on = false;
     int prof_max = 0, prof_n = 0;
     std::vector<cudaEvent_t> prof_ev;
-    std::vector<int> prof_id;
+    std::vector<int> prof_id, prof_k;  // per bracket: kernel part, kernels launched
 };
 
 namespace {
@@ -267,7 +269,8 @@ mc_status make_plan(const mc_model *md, const mc_instruments *in, Plan &p, std::
 
 // Workspace carve-out (256-byte aligned pieces).
 struct WsLayout {
-    size_t strike, disc, perm, grp_seg, grp_begin, bucket, lv_jt, lv_a, seed_w, lam2, ticket, part_y, part_g,
+    size_t strike, disc, perm, grp_seg, grp_begin, bucket, lv_jt, lv_a, seed_w, lam2, ticket, queue, part_y, part_g,
+        part1_y, part1_g,
         ckpt, tape, xmat, total;
     WsLayout(const Plan &p, int grid_max, uint64_t ckpt_stride) {
         size_t o = 0;
@@ -287,8 +290,14 @@ struct WsLayout {
         seed_w = take(p.m * 8);
         lam2 = take(p.m * 8);
         ticket = take(4);
-        part_y = take((size_t)grid_max * p.m * 8);
-        part_g = take((size_t)grid_max * p.M * 8);
+        queue = take(16);
+        // partial sums: one row per block (static chunk assignment) or per warp chunk (queue)
+        const size_t part_rows = std::max((size_t)grid_max, ckpt_stride / (32 * (size_t)p.ppt));
+        part_y = take(part_rows * p.m * 8);
+        part_g = take(part_rows * p.M * 8);
+        const size_t rows1 = (part_rows + kRowsPerBlock - 1) / kRowsPerBlock;
+        part1_y = take(rows1 * p.m * 8);
+        part1_g = take(rows1 * p.M * 8);
         const size_t real = p.precision == MC_FP64 ? 8 : 4;
         // checkpoint tiles (SegTile): per warp chunk of 32*ppt paths and segment, the state
         // words and, with stored normals, the segment's K * dz normals of each path, in rows of
@@ -479,21 +488,32 @@ int grid_for_paths(int grid_max, uint64_t n_paths, int ppt, int n_sm = 0) {
     return best_b * n_sm;
 }
 
+// Warp chunks of n_paths (32 * ppt paths each).
+uint64_t chunk_count(uint64_t n_paths, int ppt) { return (n_paths + (uint64_t)kWarp * ppt - 1) / ((uint64_t)kWarp * ppt); }
+
+// Blocks of a queue-fed sweep: every resident block (no round to balance), at most one warp per
+// chunk.
+int queue_grid(int grid_max, uint64_t n_paths, int ppt) {
+    const uint64_t want = (chunk_count(n_paths, ppt) + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    return (int)(want < (uint64_t)grid_max ? want : grid_max);
+}
+
 cudaError_t launch(const void *fn, int grid, size_t smem, const DevProblem &pb, const DevCall &cl,
                    cudaStream_t st) {
     void *args[2] = {(void *)&pb, (void *)&cl};
     return cudaLaunchKernel(fn, dim3(grid), dim3(kBlock), args, smem, st);
 }
 
-// Launch f() on st; when profiling, bracket it with events tagged `id`.
+// Launch f() (`kernels` kernel launches) on st; when profiling, bracket it with events tagged `id`.
 template <class F>
-cudaError_t timed(mc_ctx *ctx, int id, cudaStream_t st, F &&f) {
+cudaError_t timed(mc_ctx *ctx, int id, cudaStream_t st, F &&f, int kernels = 1) {
     const bool rec = ctx->prof_on && ctx->prof_n < ctx->prof_max;
     if (rec) cudaEventRecord(ctx->prof_ev[2 * ctx->prof_n], st);
     cudaError_t e = f();
     if (rec) {
         cudaEventRecord(ctx->prof_ev[2 * ctx->prof_n + 1], st);
-        ctx->prof_id[ctx->prof_n++] = id;
+        ctx->prof_id[ctx->prof_n] = id;
+        ctx->prof_k[ctx->prof_n++] = kernels;
     }
     return e;
 }
@@ -502,6 +522,7 @@ void prof_free(mc_ctx *ctx) {
     for (cudaEvent_t ev : ctx->prof_ev) cudaEventDestroy(ev);
     ctx->prof_ev.clear();
     ctx->prof_id.clear();
+    ctx->prof_k.clear();
     ctx->prof_on = false;
     ctx->prof_max = ctx->prof_n = 0;
 }
@@ -611,6 +632,7 @@ mc_status mc_context_create(int device, const mc_model *model, const mc_instrume
     if (e == cudaSuccess) e = up(L.lv_jt, p.lv_jt.data(), p.lv_jt.size() * 4);
     if (e == cudaSuccess) e = up(L.lv_a, p.lv_a.data(), p.lv_a.size() * 8);
     if (e == cudaSuccess) e = cudaMemset(w + L.ticket, 0, 4);
+    if (e == cudaSuccess) e = cudaMemset(w + L.queue, 0, 16);
     if (e != cudaSuccess) {
         fprintf(stderr, "mc_context_create: table upload: %s\n", cudaGetErrorString(e));
         mc_context_destroy(ctx);
@@ -621,9 +643,12 @@ mc_status mc_context_create(int device, const mc_model *model, const mc_instrume
     ctx->xmat = w + L.xmat;
     ctx->part_y = (double *)(w + L.part_y);
     ctx->part_g = (double *)(w + L.part_g);
+    ctx->part1_y = (double *)(w + L.part1_y);
+    ctx->part1_g = (double *)(w + L.part1_g);
     ctx->seed_w = (double *)(w + L.seed_w);
     ctx->lam2 = (double *)(w + L.lam2);
     ctx->ticket = (unsigned int *)(w + L.ticket);
+    ctx->queue = (unsigned long long *)(w + L.queue);
     DevProblem &pb = ctx->pb;
     pb.kind = p.kind;
     pb.K = p.K;
@@ -703,21 +728,31 @@ static mc_status do_forward(mc_ctx *ctx, const double *theta, uint64_t seed, uin
     cl.tape = ctx->tape;
     cl.xmat = ctx->xmat;
     const Launch &ln = ctx->ln;
-    grid = grid_for_paths(keep ? ln.grid_fwd_keep : ln.grid_fwd, n_paths, ctx->ppt, ctx->n_sm);
+    // the sweeps take their chunks from the queue (all resident blocks busy to the end, one
+    // partial row per chunk), except the full-tape kernels (static assignment, per-block rows)
+    const bool dyn = !(keep && ctx->storage == MC_STORAGE_FULL);
+    cl.queue = dyn ? ctx->queue : nullptr;
+    const int gmax = keep ? ln.grid_fwd_keep : ln.grid_fwd;
+    grid = dyn ? queue_grid(gmax, n_paths, ctx->ppt) : grid_for_paths(gmax, n_paths, ctx->ppt, ctx->n_sm);
     const void *fn = keep ? ln.fwd_keep : ln.fwd;
     cudaError_t e = timed(ctx, MC_K_FORWARD, st, [&] { return launch(fn, grid, ln.smem_fwd, ctx->pb, cl, st); });
     if (e != cudaSuccess) return cuda_fail(ctx, e, "forward sweep launch");
+    if (dyn) grid = (int)chunk_count(n_paths, ctx->ppt);  // the rows the finalize sums
     return MC_OK;
 }
 
 static mc_status do_reverse(mc_ctx *ctx, cudaStream_t st, double *grad_out) {
     const Launch &ln = ctx->ln;
-    const int grid = grid_for_paths(ln.grid_rev, ctx->last.n_paths, ctx->ppt, ctx->n_sm);
+    const bool dyn = ctx->last.queue != nullptr;
+    const int grid = dyn ? queue_grid(ln.grid_rev, ctx->last.n_paths, ctx->ppt)
+                         : grid_for_paths(ln.grid_rev, ctx->last.n_paths, ctx->ppt, ctx->n_sm);
+    const int rows = dyn ? (int)chunk_count(ctx->last.n_paths, ctx->ppt) : grid;
     cudaError_t e = timed(ctx, MC_K_REVERSE, st, [&] { return launch(ln.rev, grid, ln.smem_rev, ctx->pb, ctx->last, st); });
     if (e != cudaSuccess) return cuda_fail(ctx, e, "reverse sweep launch");
     e = timed(ctx, MC_K_FINALIZE_G, st, [&] {
-        return launch_finalize_grad(ctx->part_g, grid, ctx->M, 1.0 / (double)ctx->last.n_paths, grad_out, st);
-    });
+        return launch_finalize_grad(ctx->part_g, rows, ctx->M, 1.0 / (double)ctx->last.n_paths, grad_out, st,
+                                    ctx->part1_g);
+    }, finalize_kernels(rows, ctx->part1_g));
     if (e != cudaSuccess) return cuda_fail(ctx, e, "gradient finalize launch");
     return MC_OK;
 }
@@ -736,8 +771,9 @@ mc_status mc_forward(mc_ctx *ctx, const double *theta, uint64_t seed, uint64_t p
     if (s != MC_OK) return s;
     cudaError_t e = timed(ctx, MC_K_FINALIZE_Y, st, [&] {
         return launch_finalize_forward(ctx->part_y, grid, ctx->m, 1.0 / (double)n_paths, ctx->pb.disc,
-                                       ctx->pb.perm, nullptr, Ey_out, nullptr, nullptr, nullptr, nullptr, st);
-    });
+                                       ctx->pb.perm, nullptr, Ey_out, nullptr, nullptr, nullptr, nullptr, st,
+                                       ctx->part1_y);
+    }, finalize_kernels(grid, ctx->part1_y));
     if (e != cudaSuccess) return cuda_fail(ctx, e, "forward finalize launch");
     if (keep_checkpoints) {
         ctx->last = cl;
@@ -776,8 +812,9 @@ mc_status mc_value_and_grad(mc_ctx *ctx, const double *theta, const double *C, u
     if (s != MC_OK) return s;
     cudaError_t e = timed(ctx, MC_K_FINALIZE_Y, st, [&] {
         return launch_finalize_forward(ctx->part_y, grid, ctx->m, 1.0 / (double)n_paths, ctx->pb.disc,
-                                       ctx->pb.perm, C, Ey_out, ctx->seed_w, ctx->lam2, ctx->ticket, G_out, st);
-    });
+                                       ctx->pb.perm, C, Ey_out, ctx->seed_w, ctx->lam2, ctx->ticket, G_out, st,
+                                       ctx->part1_y);
+    }, finalize_kernels(grid, ctx->part1_y));
     if (e != cudaSuccess) return cuda_fail(ctx, e, "forward finalize launch");
     ctx->last = cl;
     ctx->have_ckpt = true;
@@ -790,6 +827,7 @@ mc_status mc_profile_begin(mc_ctx *ctx, int32_t max_launches) {
     prof_free(ctx);
     ctx->prof_ev.resize(2 * (size_t)max_launches, nullptr);
     ctx->prof_id.resize(max_launches, -1);
+    ctx->prof_k.resize(max_launches, 0);
     for (auto &ev : ctx->prof_ev) {
         cudaError_t e = cudaEventCreate(&ev);
         if (e != cudaSuccess) {
@@ -817,7 +855,7 @@ mc_status mc_profile_end(mc_ctx *ctx, double *ms_out, int32_t *launches_out) {
             break;
         }
         ms[ctx->prof_id[q]] += t;
-        cnt[ctx->prof_id[q]] += 1;
+        cnt[ctx->prof_id[q]] += ctx->prof_k[q];
     }
     prof_free(ctx);
     for (int k = 0; k < MC_N_KERNELS; ++k) {

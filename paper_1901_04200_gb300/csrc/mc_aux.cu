@@ -113,10 +113,35 @@ static int grid_for(uint64_t work, int block) {
     return (int)(g ? g : 1);
 }
 
+// First level of a two-level fixed-order sum over many partial rows: block b adds rows
+// [b*R, (b+1)*R) in order, one thread per column (reads of a row are coalesced), into row b of out.
+__global__ void __launch_bounds__(kFinBlock)
+reduce_rows_kernel(const double *__restrict__ part, int rows, int width, int R, double *__restrict__ out) {
+    const int r0 = blockIdx.x * R, r1 = min(rows, r0 + R);
+    for (int c = threadIdx.x; c < width; c += blockDim.x) {
+        double s = 0.0;
+        for (int r = r0; r < r1; ++r) s += part[(size_t)r * width + c];
+        out[(size_t)blockIdx.x * width + c] = s;
+    }
+}
+
+// Many rows (one per warp chunk) and a scratch buffer of ceil(rows / kRowsPerBlock) rows: sum them
+// in two fixed-order levels; returns the rows the per-column finalize then adds.
+static cudaError_t fold_rows(const double *&part, int &nb, int width, double *scratch, cudaStream_t st) {
+    if (finalize_kernels(nb, scratch) == 1) return cudaSuccess;
+    const int nb1 = (nb + kRowsPerBlock - 1) / kRowsPerBlock;
+    reduce_rows_kernel<<<nb1, kFinBlock, 0, st>>>(part, nb, width, kRowsPerBlock, scratch);
+    part = scratch;
+    nb = nb1;
+    return cudaGetLastError();
+}
+
 cudaError_t launch_finalize_forward(const double *part_y, int nb, int m, double inv_n,
                                     const double *disc, const int *perm, const double *C,
                                     double *Ey_out, double *seed_w, double *lam2,
-                                    unsigned int *ticket, double *G_out, cudaStream_t st) {
+                                    unsigned int *ticket, double *G_out, cudaStream_t st, double *scratch) {
+    cudaError_t e = fold_rows(part_y, nb, m, scratch, st);
+    if (e != cudaSuccess) return e;
     finalize_forward_kernel<<<m, kFinBlock, 0, st>>>(part_y, nb, m, inv_n, disc, perm, C, Ey_out,
                                                       seed_w, lam2, ticket, G_out);
     return cudaGetLastError();
@@ -129,7 +154,9 @@ cudaError_t launch_seed_from_ybar(const double *ybar, const int *perm, const dou
 }
 
 cudaError_t launch_finalize_grad(const double *part_g, int nb, int M, double inv_n, double *grad,
-                                 cudaStream_t st) {
+                                 cudaStream_t st, double *scratch) {
+    cudaError_t e = fold_rows(part_g, nb, M, scratch, st);
+    if (e != cudaSuccess) return e;
     finalize_grad_kernel<<<M, kFinBlock, 0, st>>>(part_g, nb, M, inv_n, grad);
     return cudaGetLastError();
 }

@@ -203,6 +203,10 @@ struct DevCall {
     const double *seed_w; // [m] sorted: lambda_i * disc_i (reverse sweep seeds)
     void *tape;           // full storage: [n_steps][tape fields][ckpt_stride] of Real
     void *xmat;           // full storage: [n_groups][ckpt_stride] x at each maturity
+    // Work queue of the path sweeps (null: static chunk assignment, per-block partial sums): [0]
+    // the next warp chunk, [1] finished blocks; with it, part_y / part_g hold one row per chunk
+    // and the last block to finish resets both words to zero.
+    unsigned long long *queue;
 };
 
 }  // namespace mcaad

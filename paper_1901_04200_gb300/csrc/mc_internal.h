@@ -30,14 +30,20 @@ bool lv_kernels(int precision, int K, int ppt, KernelPair *out);
 bool slv_kernels(int precision, int K, int ppt, KernelPair *out);
 
 // Small kernels (mc_aux.cu).
+// Partial rows per block of the first level of a two-level finalize (launch_finalize_* with a
+// scratch buffer of ceil(rows / kRowsPerBlock) rows).
+constexpr int kRowsPerBlock = 64;
+// Kernels one launch_finalize_* call issues for nb partial rows: two when it folds them first.
+inline int finalize_kernels(int nb, const double *scratch) { return (scratch && nb > 2 * kRowsPerBlock) ? 2 : 1; }
 cudaError_t launch_finalize_forward(const double *part_y, int nb, int m, double inv_n,
                                     const double *disc, const int *perm, const double *C,
                                     double *Ey_out, double *seed_w, double *lam2,
-                                    unsigned int *ticket, double *G_out, cudaStream_t st);
+                                    unsigned int *ticket, double *G_out, cudaStream_t st,
+                                    double *scratch = nullptr);
 cudaError_t launch_seed_from_ybar(const double *ybar, const int *perm, const double *disc, int m,
                                   double *seed_w, cudaStream_t st);
 cudaError_t launch_finalize_grad(const double *part_g, int nb, int M, double inv_n, double *grad,
-                                 cudaStream_t st);
+                                 cudaStream_t st, double *scratch = nullptr);
 cudaError_t launch_philox_fill(uint64_t seed, uint64_t path0, uint32_t n_paths, uint32_t n_calls,
                                uint32_t *out, cudaStream_t st);
 cudaError_t launch_normals_fill(uint64_t seed, uint64_t path0, uint32_t n_paths,

@@ -595,6 +595,25 @@ struct SlvModel {
 
 // ============================================================== kernels ====
 
+// Dynamic chunk assignment: lane 0 takes the warp's next chunk from the queue.
+__device__ __forceinline__ uint64_t take_chunk(unsigned long long *q, int lane) {
+    unsigned long long c = 0;
+    if (lane == 0) c = atomicAdd(q, 1ull);
+    return __shfl_sync(0xffffffffu, c, 0);
+}
+// After the block's last chunk (all threads): the last block of the grid to finish resets the
+// queue for the next launch (every other block has stopped taking chunks by then).
+__device__ __forceinline__ void queue_done(unsigned long long *q) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(q + 1, 1ull) == (unsigned long long)gridDim.x - 1) {
+            q[0] = 0ull;
+            q[1] = 0ull;
+        }
+    }
+}
+
 // 16-byte asynchronous global -> shared copies (L1 bypassed), grouped per
 // segment; wait_group<N> returns when at most N of the thread's groups are
 // still in flight (a hardware wait, no polling).
@@ -771,8 +790,9 @@ __global__ void __launch_bounds__(kBlock) path_forward_kernel(const DevProblem p
 
     constexpr uint64_t kChunk = (uint64_t)kWarp * PPT;
     const uint64_t n_chunks = (cl.n_paths + kChunk - 1) / kChunk;
-    for (uint64_t ch = (uint64_t)blockIdx.x * kWarpsPerBlock + warp; ch < n_chunks;
-         ch += (uint64_t)gridDim.x * kWarpsPerBlock) {
+    const bool dyn = cl.queue != nullptr;  // chunks from the queue, one partial row per chunk
+    for (uint64_t ch = dyn ? take_chunk(cl.queue, lane) : (uint64_t)blockIdx.x * kWarpsPerBlock + warp; ch < n_chunks;
+         ch = dyn ? take_chunk(cl.queue, lane) : ch + (uint64_t)gridDim.x * kWarpsPerBlock) {
         uint64_t local[PPT];
         bool active[PPT];
         NormalSource<Md> rng[PPT];
@@ -852,12 +872,19 @@ __global__ void __launch_bounds__(kBlock) path_forward_kernel(const DevProblem p
                             const Real sum = warp_sum(pay);
                             mine = (lane == j) ? sum : mine;
                         }
-                        if (lane < cnt) wy[i0 + lane] += (double)mine;
+                        if (lane < cnt) {
+                            if (dyn) cl.part_y[ch * pb.m + i0 + lane] = (double)mine;
+                            else wy[i0 + lane] += (double)mine;
+                        }
                     }
                     ++g;
                 }
             }
         }
+    }
+    if (dyn) {
+        queue_done(cl.queue);
+        return;
     }
     __syncthreads();
     const double *wall = (const double *)(smem + sp.wacc_y);
@@ -868,15 +895,9 @@ __global__ void __launch_bounds__(kBlock) path_forward_kernel(const DevProblem p
     }
 }
 
-// Resident blocks per SM the reverse sweep is compiled for: long local-vol segments (K = 25, one
-// path per thread: 25 steps unrolled with their tapes) otherwise take up to 253 registers, two
-// blocks per SM; three blocks (at most 168 registers) measured faster.
-template <class Md, int K>
-__host__ __device__ constexpr int reverse_min_blocks() { return (Md::kind == kLv && K >= 25) ? 3 : 1; }
-
-template <class Md, int K, int PPT, bool kLoadZ = false>
-__global__ void __launch_bounds__(kBlock, (reverse_min_blocks<Md, K>())) path_reverse_kernel(const DevProblem pb,
-                                                                                             const DevCall cl) {
+// The reverse sweep's body; the kernels below differ only in the occupancy they are compiled for.
+template <class Md, int K, int PPT, bool kLoadZ>
+__device__ __forceinline__ void reverse_sweep(const DevProblem &pb, const DevCall &cl) {
     using Real = typename Md::Real;
     using ZS = SegTile<Md, K, PPT, kLoadZ>;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -901,8 +922,9 @@ __global__ void __launch_bounds__(kBlock, (reverse_min_blocks<Md, K>())) path_re
 
     constexpr uint64_t kChunk = (uint64_t)kWarp * PPT;
     const uint64_t n_chunks = (cl.n_paths + kChunk - 1) / kChunk;
-    for (uint64_t ch = (uint64_t)blockIdx.x * kWarpsPerBlock + warp; ch < n_chunks;
-         ch += (uint64_t)gridDim.x * kWarpsPerBlock) {
+    const bool dyn = cl.queue != nullptr;  // chunks from the queue, one partial row per chunk
+    for (uint64_t ch = dyn ? take_chunk(cl.queue, lane) : (uint64_t)blockIdx.x * kWarpsPerBlock + warp; ch < n_chunks;
+         ch = dyn ? take_chunk(cl.queue, lane) : ch + (uint64_t)gridDim.x * kWarpsPerBlock) {
         uint64_t local[PPT];
         bool active[PPT];
         NormalSource<Md> rng[PPT];
@@ -979,6 +1001,18 @@ __global__ void __launch_bounds__(kBlock, (reverse_min_blocks<Md, K>())) path_re
 #pragma unroll
         for (int q = 0; q < PPT; ++q) vb_sum += vb[q];
         Md::acc_end(acc, vb_sum, par, sh, wg, lane);
+        if (dyn) {  // this chunk's sums to its own row; the warp's accumulators back to zero
+            __syncwarp();
+            for (int j = lane; j < pb.M; j += kWarp) {
+                cl.part_g[ch * pb.M + j] = wg[j];
+                wg[j] = 0.0;
+            }
+            __syncwarp();
+        }
+    }
+    if (dyn) {
+        queue_done(cl.queue);
+        return;
     }
     __syncthreads();
     const double *wall = (const double *)(smem + sp.wacc_g);
@@ -988,6 +1022,24 @@ __global__ void __launch_bounds__(kBlock, (reverse_min_blocks<Md, K>())) path_re
         cl.part_g[(size_t)blockIdx.x * pb.M + j] = s;
     }
 }
+
+template <class Md, int K, int PPT, bool kLoadZ = false>
+__global__ void __launch_bounds__(kBlock) path_reverse_kernel(const DevProblem pb, const DevCall cl) {
+    reverse_sweep<Md, K, PPT, kLoadZ>(pb, cl);
+}
+
+// Long local-vol segments (K = 25, one path per thread: 25 steps unrolled with their tapes) take
+// up to 253 registers and two blocks per SM when unbounded; compiled for three blocks (at most 168
+// registers) they measured faster. Other models keep the unbounded kernel: a minimum of one block
+// per SM still changes ptxas's allocation (stochastic local vol: 164 -> 188 registers, three ->
+// two blocks per SM, 1.80 -> 2.21 ms).
+template <class Md, int K, int PPT, bool kLoadZ = false>
+__global__ void __launch_bounds__(kBlock, 3) path_reverse_kernel_b3(const DevProblem pb, const DevCall cl) {
+    reverse_sweep<Md, K, PPT, kLoadZ>(pb, cl);
+}
+
+template <class Md, int K>
+__host__ __device__ constexpr bool reverse_three_blocks() { return Md::kind == kLv && K >= 25; }
 
 // ------------------------------------------------------ stored-states variant --
 // The forward sweep stores the state before every step (SegTile mode 2: no normals, no
@@ -1020,8 +1072,9 @@ __global__ void __launch_bounds__(kBlock) path_forward_states_kernel(const DevPr
     constexpr uint64_t kChunk = (uint64_t)kWarp * PPT;
     const uint64_t n_chunks = (cl.n_paths + kChunk - 1) / kChunk;
     const uint64_t ws_chunks = cl.ckpt_stride / kChunk;
-    for (uint64_t ch = (uint64_t)blockIdx.x * kWarpsPerBlock + warp; ch < n_chunks;
-         ch += (uint64_t)gridDim.x * kWarpsPerBlock) {
+    const bool dyn = cl.queue != nullptr;  // chunks from the queue, one partial row per chunk
+    for (uint64_t ch = dyn ? take_chunk(cl.queue, lane) : (uint64_t)blockIdx.x * kWarpsPerBlock + warp; ch < n_chunks;
+         ch = dyn ? take_chunk(cl.queue, lane) : ch + (uint64_t)gridDim.x * kWarpsPerBlock) {
         uint64_t local[PPT];
         bool active[PPT];
         NormalSource<Md> rng[PPT];
@@ -1086,7 +1139,10 @@ __global__ void __launch_bounds__(kBlock) path_forward_states_kernel(const DevPr
                             const Real sum = warp_sum(pay);
                             mine = (lane == j) ? sum : mine;
                         }
-                        if (lane < cnt) wy[i0 + lane] += (double)mine;
+                        if (lane < cnt) {
+                            if (dyn) cl.part_y[ch * pb.m + i0 + lane] = (double)mine;
+                            else wy[i0 + lane] += (double)mine;
+                        }
                     }
                     ++g;
                 }
@@ -1110,6 +1166,10 @@ __global__ void __launch_bounds__(kBlock) path_forward_states_kernel(const DevPr
             }
             *TL::group(tf, g0 / TL::kG, lane) = TL::V::make(v);
         }
+    }
+    if (dyn) {
+        queue_done(cl.queue);
+        return;
     }
     __syncthreads();
     const double *wall = (const double *)(smem + sp.wacc_y);
@@ -1149,8 +1209,9 @@ __global__ void __launch_bounds__(kBlock) path_reverse_states_kernel(const DevPr
     constexpr uint64_t kChunk = (uint64_t)kWarp * PPT;
     const uint64_t n_chunks = (cl.n_paths + kChunk - 1) / kChunk;
     const uint64_t ws_chunks = cl.ckpt_stride / kChunk;
-    for (uint64_t ch = (uint64_t)blockIdx.x * kWarpsPerBlock + warp; ch < n_chunks;
-         ch += (uint64_t)gridDim.x * kWarpsPerBlock) {
+    const bool dyn = cl.queue != nullptr;  // chunks from the queue, one partial row per chunk
+    for (uint64_t ch = dyn ? take_chunk(cl.queue, lane) : (uint64_t)blockIdx.x * kWarpsPerBlock + warp; ch < n_chunks;
+         ch = dyn ? take_chunk(cl.queue, lane) : ch + (uint64_t)gridDim.x * kWarpsPerBlock) {
         bool active[PPT];
         Real xb[PPT], vb[PPT];
         typename Md::State nx_[PPT];  // the state after the segment being processed
@@ -1225,6 +1286,18 @@ __global__ void __launch_bounds__(kBlock) path_reverse_states_kernel(const DevPr
 #pragma unroll
         for (int q = 0; q < PPT; ++q) vb_sum += vb[q];
         Md::acc_end(acc, vb_sum, par, sh, wg, lane);
+        if (dyn) {  // this chunk's sums to its own row; the warp's accumulators back to zero
+            __syncwarp();
+            for (int j = lane; j < pb.M; j += kWarp) {
+                cl.part_g[ch * pb.M + j] = wg[j];
+                wg[j] = 0.0;
+            }
+            __syncwarp();
+        }
+    }
+    if (dyn) {
+        queue_done(cl.queue);
+        return;
     }
     __syncthreads();
     const double *wall = (const double *)(smem + sp.wacc_g);
@@ -1417,11 +1490,16 @@ __global__ void __launch_bounds__(kBlock) path_reverse_tape_kernel(const DevProb
 template <class Md, int K, int PPT, class Table>
 void set_kernels(Table *out) {
     out->fwd = (const void *)path_forward_kernel<Md, K, PPT>;
-    out->rev = (const void *)path_reverse_kernel<Md, K, PPT>;
+    if constexpr (reverse_three_blocks<Md, K>()) {
+        out->rev = (const void *)path_reverse_kernel_b3<Md, K, PPT>;
+        out->rev_z = (const void *)path_reverse_kernel_b3<Md, K, PPT, true>;
+    } else {
+        out->rev = (const void *)path_reverse_kernel<Md, K, PPT>;
+        out->rev_z = (const void *)path_reverse_kernel<Md, K, PPT, true>;
+    }
     out->fwd_store = (const void *)path_forward_store_kernel<Md, K, PPT>;
     out->rev_tape = (const void *)path_reverse_tape_kernel<Md, K, PPT>;
     out->fwd_z = (const void *)path_forward_kernel<Md, K, PPT, true>;
-    out->rev_z = (const void *)path_reverse_kernel<Md, K, PPT, true>;
     out->stage_bytes_ckpt = SegTile<Md, K, PPT, false>::kBlockBytes;
     out->stage_bytes_z = SegTile<Md, K, PPT, true>::kBlockBytes;
     if constexpr (Md::kind == kLv) {  // stored states: local vol only

@@ -249,6 +249,23 @@ def test_deterministic_repeat(L):
     assert np.array_equal(a[0], b[0]) and a[1] == b[1] and np.array_equal(a[2], b[2])
 
 
+@pytest.mark.parametrize("kind", ["heston", "lv"])
+def test_reused_context_queue_and_repeat(L, orc, kind):
+    """One context, calls of different path counts in a row (each sweep takes its chunks from a
+    queue the previous launch reset): every call equals the oracle, and repeating a call gives
+    the same bits whatever chunks the warps took."""
+    w = small_case(kind, n_paths=5000)
+    pb = with_pb(w, precision="fp64").problem
+    ctx = L.Context(pb, max_paths=5000)
+    runs = []
+    for n, p0 in [(1000, 0), (4097, 9), (33, 100), (1000, 0)]:
+        G, g, Ey = (x.cpu().numpy() for x in ctx.value_and_grad(w.theta, w.C, pb.seed, n, path0=p0))
+        Eo, Go, go = orc.value_and_grad(pb, w.theta, w.C, n, path0=p0)
+        assert rel(Ey, Eo) <= 1e-12 and abs(G[0] - Go) <= 1e-10 * abs(Go) and rel(g, go) <= 1e-10
+        runs.append((G, g, Ey))
+    assert all(np.array_equal(a, b) for a, b in zip(runs[0], runs[3]))
+
+
 # ------------------------------------------------------------ full sizes
 
 @pytest.mark.slow
