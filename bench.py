@@ -58,7 +58,7 @@ UNIT = "path-steps/s"
 # sqrt(dt) z from its two end states (difference, drift and sigma^2 terms) 4 and one reciprocal,
 # sigma-bar and weights 6, four row-adjoint FMAs 4, d sigma/dx 2.
 OPS = {"heston": {"F": {"fp32": 22, "mufu": 5, "int": 24}, "step": {"fp32": 13, "mufu": 1}, "R": {"fp32": 17}},
-       "lv": {"F": {"fp32": 21, "mufu": 2, "int": 12}, "step": {"fp32": 16}, "R": {"fp32": 24},
+       "lv": {"F": {"fp32": 20, "mufu": 2, "int": 12}, "step": {"fp32": 15}, "R": {"fp32": 23},
               "Rs": {"fp32": 28, "mufu": 1}},
        "slv": {"F": {"fp32": 34, "mufu": 5, "int": 24}, "step": {"fp32": 25, "mufu": 1}, "R": {"fp32": 40}}}
 # Forward-mode tangents of the Heston step (mc_value_and_grad_tangent), per path-step on top of

@@ -293,7 +293,7 @@ struct LvModel {
         const Real *a;    // [n_steps]
         const int *jt;    // [n_steps]
         Real *racc;       // reverse: [nx][kBlock][2] per-thread node adjoints of rows jt, jt+1
-        const Real *node; // node_table: [nt-1][nx][2] (theta[j][c], theta[j+1][c] - theta[j][c])
+        const Real *node; // node_table: [nt-1][nx][2] (theta[j][c], theta[j+1][c] - theta[j][c]) x sqrt(dt)
         int nx;
     };
     // u0 = -x_lo / hx, so that the scaled coordinate u = (x - x_lo) / hx is one FMA
@@ -302,9 +302,16 @@ struct LvModel {
     // whose adjoints run next
     struct Acc { int jt; Real at, oma; };
 
+    // Local vol keeps its surface premultiplied by sqrt(dt): a row entry is h = sigma sqrt(dt),
+    // the step's diffusion coefficient, so the step and its adjoint need no products with dt.
+    // The reverse sweep is linear in its seeds, which load_tables scales by sqrt(dt) for local
+    // vol, so the node adjoints come out as d/d theta = sqrt(dt) d/d h.  A leverage surface
+    // (SlvModel) is kept as it is.
     __device__ static void setup(unsigned char *base, const SmemPlan &sp, const DevProblem &pb,
-                                 const double *theta, int n_steps, Shared &sh, Par &par, bool node_table = false) {
+                                 const double *theta, int n_steps, Shared &sh, Par &par, bool node_table = false,
+                                 bool leverage = false) {
         const int nx = pb.nx;
+        const double sc = leverage ? 1.0 : sqrt(pb.dt);
         Real *row = (Real *)(base + sp.model);
         size_t o = align_up(sp.model + (node_table ? (size_t)(pb.nt - 1) * nx * 2 : (size_t)n_steps * nx) * sizeof(Real),
                             16);
@@ -319,8 +326,8 @@ struct LvModel {
         }
         if (node_table) {
             for (int q = threadIdx.x; q < (pb.nt - 1) * nx; q += blockDim.x) {
-                row[2 * q] = (Real)theta[q];
-                row[2 * q + 1] = (Real)(theta[q + nx] - theta[q]);
+                row[2 * q] = (Real)(sc * theta[q]);
+                row[2 * q + 1] = (Real)(sc * (theta[q + nx] - theta[q]));
             }
             sh.row = nullptr;
             sh.node = row;
@@ -329,7 +336,7 @@ struct LvModel {
                 const int n = q / nx, c = q - n * nx;
                 const int j = pb.lv_jt[n];
                 const double w = pb.lv_a[n];
-                row[q] = (Real)((1.0 - w) * theta[j * nx + c] + w * theta[(j + 1) * nx + c]);
+                row[q] = (Real)(sc * ((1.0 - w) * theta[j * nx + c] + w * theta[(j + 1) * nx + c]));
             }
             sh.node = nullptr;
         }
@@ -378,9 +385,11 @@ struct LvModel {
         bool inside;
         cell(u, p, c, b, inside);
         const Real *rw = sh.row + n * sh.nx;
-        const Real s0 = rw[c], s1 = rw[c + 1];
-        const Real sig = fma(b, s1 - s0, s0);
-        s.x = s.x + fma(sig, fma(p.sdt, z[0], Real(-0.5) * sig * p.dt), p.rdt);
+        const Real h0 = rw[c], h1 = rw[c + 1];
+        const Real h = fma(b, h1 - h0, h0);  // sigma sqrt(dt)
+        // x + r dt - sigma^2 dt / 2 + sigma sqrt(dt) z = x + (h (z - h / 2) + r dt): the small
+        // increment is formed first and x rounded once per step
+        s.x = s.x + fma(h, fma(Real(-0.5), h, z[0]), p.rdt);
         if (t) {
             t->u = u;
             t->z = z[0];
@@ -442,8 +451,8 @@ struct LvModel {
         a.at = sh.a[n];
         a.oma = Real(1) - a.at;
     }
-    // sigma-bar = xb (sqrt(dt) z - sigma dt); node adjoints sigma-bar times the
-    // bilinear weights; xb += sigma-bar d sigma/dx (0 where x is clamped).
+    // h-bar = xb (z - h) (h = sigma sqrt(dt)); node adjoints h-bar times the bilinear weights
+    // (xb carries the seeds' factor sqrt(dt)); xb += h-bar dh/dx (0 where x is clamped).
     __device__ __forceinline__ static void adjoint(const Tape &t, int n, Real &xb, Real &, Acc &a,
                                                    const Par &p, const Shared &sh) {
         int c;
@@ -451,18 +460,18 @@ struct LvModel {
         bool inside;
         cell(t.u, p, c, b, inside);
         const Real *rw = sh.row + n * sh.nx;
-        const Real s0 = rw[c], s1 = rw[c + 1];
-        const Real ds = s1 - s0;
-        const Real sig = fma(b, ds, s0);
-        const Real sb = xb * fma(p.sdt, t.z, -sig * p.dt);
-        const Real g1 = sb * b, g0 = sb - g1;
+        const Real h0 = rw[c], h1 = rw[c + 1];
+        const Real dh = h1 - h0;
+        const Real h = fma(b, dh, h0);
+        const Real hb = xb * (t.z - h);
+        const Real g1 = hb * b, g0 = hb - g1;
         add_node(sh, a, c, g0);
         add_node(sh, a, c + 1, g1);
-        if (inside) xb = fma(sb * p.inv_hx, ds, xb);
+        if (inside) xb = fma(hb * p.inv_hx, dh, xb);
     }
     // The adjoint of step n from the states at both of its ends (stored-states variant): the
-    // step x1 = x0 + r dt - sigma^2 dt / 2 + sigma sqrt(dt) z gives
-    // d x1 / d sigma = sqrt(dt) z - sigma dt = (x1 - x0 - r dt - sigma^2 dt / 2) / sigma,
+    // step x1 = x0 + r dt + h z - h^2 / 2 (h = sigma sqrt(dt)) gives
+    // d x1 / d h = z - h = (x1 - x0 - r dt - h^2 / 2) / h,
     // so the adjoint needs neither the normal nor a re-run of the step (sigma != 0).
     __device__ __forceinline__ static void adjoint_states(const State &s0, const State &s1, int n, Real &xb, Real &,
                                                           Acc &a, const Par &p, const Shared &sh) {
@@ -475,14 +484,14 @@ struct LvModel {
         const P2 *nd = (const P2 *)sh.node + a.jt * sh.nx + c;  // the time cell's node pairs (a.jt, a.at: step n)
         const P2 n0 = nd[0], n1 = nd[1];
         const Real v0 = fma(a.at, n0.y, n0.x), v1 = fma(a.at, n1.y, n1.x);
-        const Real ds = v1 - v0;
-        const Real sig = fma(b, ds, v0);
-        const Real dsig = (s1.x - s0.x - p.rdt - Real(0.5) * p.dt * sig * sig) * recip_r<Real>(sig);
-        const Real sb = xb * dsig;
-        const Real g1 = sb * b, g0 = sb - g1;
+        const Real dh = v1 - v0;
+        const Real h = fma(b, dh, v0);
+        const Real dxdh = fma(Real(-0.5) * h, h, s1.x - s0.x - p.rdt) * recip_r<Real>(h);
+        const Real hb = xb * dxdh;
+        const Real g1 = hb * b, g0 = hb - g1;
         add_node(sh, a, c, g0);
         add_node(sh, a, c + 1, g1);
-        if (inside) xb = fma(sb * p.inv_hx, ds, xb);
+        if (inside) xb = fma(hb * p.inv_hx, dh, xb);
     }
     __device__ static void acc_end(Acc &a, Real, const Par &, const Shared &sh, double *wacc, int lane) {
         flush_rows(a, sh, wacc, lane);
@@ -521,7 +530,7 @@ struct SlvModel {
                                  const double *theta, int n_steps, Shared &sh, Par &par) {
         typename Hs::Shared hs;
         Hs::setup(base, sp, pb, theta, n_steps, hs, par.h);
-        Lv::setup(base, sp, pb, theta + 5, n_steps, sh, par.l);
+        Lv::setup(base, sp, pb, theta + 5, n_steps, sh, par.l, false, true);
     }
     __device__ static State init(const Par &p) { return State{Real(0), p.h.v0}; }
     __device__ __forceinline__ static void step(State &s, const Real *z, int n, const Par &p,
@@ -753,7 +762,9 @@ __device__ __forceinline__ void load_tables(unsigned char *base, const SmemPlan 
     for (int g = threadIdx.x; g <= pb.n_groups; g += blockDim.x) gbeg[g] = pb.grp_begin[g];
     if (reverse) {
         Real *sw = (Real *)(base + sp.seed_w);
-        for (int i = threadIdx.x; i < pb.m; i += blockDim.x) sw[i] = (Real)cl.seed_w[i];
+        // local vol: sqrt(dt) turns the adjoints of its premultiplied surface into d/d theta
+        const double ss = Md::kind == kLv ? sqrt(pb.dt) : 1.0;
+        for (int i = threadIdx.x; i < pb.m; i += blockDim.x) sw[i] = (Real)(cl.seed_w[i] * ss);
         double *wg = (double *)(base + sp.wacc_g);
         for (int q = threadIdx.x; q < kWarpsPerBlock * pb.M; q += blockDim.x) wg[q] = 0.0;
     } else {
