@@ -36,7 +36,11 @@ namespace mlp {
 
 using bf16 = __nv_bfloat16;
 constexpr int H = 256, DIN = 7, NTH = 5, KX = 64, NX = 16;
-constexpr int kSplit = 16;  // K slices of the weight-gradient GEMMs
+constexpr int kSplit = 16;  // K slices of the weight-gradient GEMMs (at most; see k_split)
+// K slices for a batch of B rows (a multiple of 128): the weight-gradient GEMMs run over
+// K = 2B = B/32 k-blocks of 64, and each slice must be whole k-blocks, so the split is the
+// largest of 16, 8, 4 dividing B/32 (a multiple of 4).
+constexpr int k_split(int B) { return (B / 32) % 16 == 0 ? 16 : ((B / 32) % 8 == 0 ? 8 : 4); }
 
 // flat FP32 parameter layout
 constexpr long long oW1 = 0, ob1 = oW1 + H * DIN, oW2 = ob1 + H, ob2 = oW2 + H * H, oW3 = ob2 + H,
@@ -73,7 +77,8 @@ struct Bufs {
     bf16 *zbb[5];        // [B][H], l = 2..4
     bf16 *Aop[5];        // [H][2B]
     bf16 *Bop[5];        // l = 1: [NX][2B], else [H][2B]
-    float *part[5];      // l = 1..4: [kSplit][H][N_l] split-K partials of dW_l
+    float *part[5];      // l = 1..4: [split][H][N_l] split-K partials of dW_l
+    int split;           // k_split(B)
     float *colpart;      // [B / 128][41 * 32] column-sum chunks
     bf16 *Wb[5], *Wt[5];  // W1b [H][KX], W1t [NX][H], Wlb/Wlt [H][H]
     float *lsum;         // [1] loss scratch
@@ -341,6 +346,12 @@ template <class Epi>
 cudaError_t gemm(const bf16 *A, long long lda, const bf16 *Bm, long long ldb, int M, int N, int K, int k_slice,
                  const Epi &e, int *err, cudaStream_t st, int bn = 0) {
     const int BN = bn ? bn : tile_n(N);
+    // shapes the kernel handles: whole 128-row tiles, BN-column tiles (16..256, a multiple of
+    // 16), K slices of whole 64-wide k-blocks (the epilogue also stages through the ring, so at
+    // least one stage must exist)
+    if (M % tc::kBM || BN < 16 || BN > 256 || BN % 16 || N % BN || k_slice < tc::kBK || k_slice % tc::kBK ||
+        K % k_slice)
+        return cudaErrorInvalidValue;
     tc::TensorMaps tm;
     cudaError_t r = tc::make_maps(&tm, A, lda, Bm, ldb, M, N, K, BN);
     if (r != cudaSuccess) return r;
@@ -425,6 +436,7 @@ __global__ void finish_out_kernel(const float *__restrict__ outp, int ntile, int
 // 16 computed columns).
 struct Partials {
     const float *part[5];
+    int split;
 };
 __global__ void reduce_split_kernel(const Partials pp, float *grads) {
     tc::pdl_wait();
@@ -438,7 +450,7 @@ __global__ void reduce_split_kernel(const Partials pp, float *grads) {
         const long long i = e / ncopy, k = e - i * ncopy;
         const float *part = pp.part[l];
         float s = 0.0f;
-        for (int sl = 0; sl < kSplit; ++sl) s += part[((long long)sl * H + i) * N + k];
+        for (int sl = 0; sl < pp.split; ++sl) s += part[((long long)sl * H + i) * N + k];
         grads[oW(l) + e] = s;
     }
 }
@@ -584,6 +596,7 @@ size_t layout(unsigned char *base, int B, Bufs *out) {
     Carve c{base};
     Bufs b{};
     b.B = B;
+    b.split = k_split(B);
     const size_t BH = (size_t)B * H, B2 = 2 * (size_t)B;
     b.x0 = c.take<bf16>((size_t)B * KX);
     for (int l = 1; l <= 4; ++l) b.z[l] = c.take<float>(BH);
@@ -703,11 +716,11 @@ cudaError_t loss_grad_impl(mlp_ctx *c, const float *params, const float *X, cons
     for (int l = 1; l <= 4 && e == cudaSuccess; ++l) {
         const int N = l == 1 ? NX : H;
         EpiPartial ep{b.part[l], N, H};
-        e = gemm(b.Aop[l], B2, b.Bop[l], B2, H, N, (int)B2, (int)(B2 / kSplit), ep, b.err, st);
+        e = gemm(b.Aop[l], B2, b.Bop[l], B2, H, N, (int)B2, (int)(B2 / b.split), ep, b.err, st);
     }
     if (e == cudaSuccess) {
         e = launch_pdl(reduce_split_kernel, dim3(grid_for((long long)H * DIN + 3LL * H * H)), dim3(256), 0, st,
-                       Partials{{nullptr, b.part[1], b.part[2], b.part[3], b.part[4]}}, grads);
+                       Partials{{nullptr, b.part[1], b.part[2], b.part[3], b.part[4]}, b.split}, grads);
     }
     if (e == cudaSuccess) {
         const int n_chunks = B / kColChunk;

@@ -54,9 +54,10 @@ def test_forward_and_input_grad(L, B, n):
     assert rel(dx.cpu().numpy(), g_ref) <= 5e-3
 
 
-@pytest.mark.parametrize("alpha,B", [(0.0, 512), (0.5, 512), (1.0, 4096)])
+@pytest.mark.parametrize("alpha,B", [(0.0, 512), (0.5, 512), (1.0, 4096), (1.0, 128), (0.5, 640)])
 def test_loss_grad_matches_oracle(L, alpha, B):
-    """B = 4096, alpha = 1 is the training step the bench times."""
+    """B = 4096, alpha = 1 is the training step the bench times; B = 128 and 640 take the
+    weight-gradient GEMMs' smaller K splits (4 slices of 64 and 320 rows)."""
     p, X, y, dy = setup(B, seed=11)
     net = L.Mlp(B)
     prm = cuda32(omlp.flatten(p))
