@@ -59,7 +59,9 @@ UNIT = "path-steps/s"
 # sigma-bar and weights 6, four row-adjoint FMAs 4, d sigma/dx 2.
 OPS = {"heston": {"F": {"fp32": 22, "mufu": 5, "int": 24}, "step": {"fp32": 13, "mufu": 1}, "R": {"fp32": 17}},
        "lv": {"F": {"fp32": 20, "mufu": 2, "int": 12}, "step": {"fp32": 15}, "R": {"fp32": 23},
-              "Rs": {"fp32": 28, "mufu": 1}},
+              "Rs": {"fp32": 28, "mufu": 1},
+              # F with the surface from per-time-cell node pairs (two more FMAs per step)
+              "Fn": {"fp32": 22, "mufu": 2, "int": 12}},
        "slv": {"F": {"fp32": 34, "mufu": 5, "int": 24}, "step": {"fp32": 25, "mufu": 1}, "R": {"fp32": 40}}}
 # Forward-mode tangents of the Heston step (mc_value_and_grad_tangent), per path-step on top of
 # F: shared factors 10 FP32 (the 1{v>0} dt select; the x and v coefficients of d vdt, 2 + 2; the
@@ -71,12 +73,16 @@ KERNEL_PARTS = {"checkpoint": {"forward_sweep": ["F"], "reverse_sweep": ["F", "R
                 "normals": {"forward_sweep": ["F"], "reverse_sweep": ["step", "R"]},
                 "full": {"forward_sweep": ["F"], "reverse_sweep": ["R"]},
                 "states": {"forward_sweep": ["F"], "reverse_sweep": ["Rs"]}}
+# Local vol's checkpoint reverse sweep re-runs each segment into shared memory and runs the
+# stored-states adjoint over it.
+KERNEL_PARTS_MODEL = {("lv", "checkpoint"): {"forward_sweep": ["F"], "reverse_sweep": ["Fn", "Rs"]}}
 # State words, normals per step and tape words per step of each model.
 DIMS = {"heston": (2, 2, 4), "lv": (1, 1, 2), "slv": (2, 2, 5)}
 
 
 def kernel_ops(model, storage, kernel, kind=None):
-    parts = [OPS[model][q] for q in KERNEL_PARTS[storage][kernel]]
+    table = KERNEL_PARTS_MODEL.get((model, storage), KERNEL_PARTS[storage])
+    parts = [OPS[model][q] for q in table[kernel]]
     return sum(v for d in parts for k, v in d.items() if kind is None or k == kind)
 
 
@@ -644,7 +650,7 @@ def run_path_workload(model, args, rank, world, local, headline):
 
     w = make_workload(model, args)
     if headline and (args.ppt or args.ckpt):
-        w.problem.paths_per_thread = args.ppt
+        w.problem.paths_per_thread = args.ppt or w.problem.paths_per_thread
         w.problem.ckpt_every = args.ckpt or w.problem.ckpt_every
     w.problem.storage = args.storage if headline else "auto"
     pb, P, S = w.problem, w.n_paths, w.problem.last_step
@@ -756,7 +762,7 @@ def run_path_workload(model, args, rank, world, local, headline):
         # segment (checkpoints only; local vol at the 25-step interval the workload names), and
         # for Heston by forward-mode tangents (no reverse sweep)
         if storage != "checkpoint":
-            K_r, ppt_r = (25, 1) if model == "lv" else (K, pb.paths_per_thread)
+            K_r, ppt_r = (25, 2) if model == "lv" else (K, pb.paths_per_thread)
             pb_r = replace(pb, storage="checkpoint", ckpt_every=K_r, paths_per_thread=ppt_r)
             ctx_r = _lib.Context(pb_r, max_paths=P, device=dev)
             ms_r, prof_r = time_arm(ctx_r, lambda: ctx_r.value_and_grad(theta, C, seed, P, path0=path0, out=out),

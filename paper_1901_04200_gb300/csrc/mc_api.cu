@@ -416,7 +416,8 @@ mc_status launch_shape(const Plan &p, int device, const KernelPair &kp, int nx, 
                                                             : 0;
     ln.smem_fwd = SmemPlan(p.kind, real, p.m, p.n_groups, p.M, n_steps, nx, false).total;
     ln.smem_rev = SmemPlan(p.kind, real, p.m, p.n_groups, p.M, n_steps, nx, true, zst,
-                           p.storage == MC_STORAGE_STATES).total;
+                           p.storage == MC_STORAGE_STATES ||
+                               (p.storage == MC_STORAGE_CHECKPOINT && kp.rev_node_table)).total;
     int optin = 0;
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
     if (ln.smem_fwd > (size_t)optin || ln.smem_rev > (size_t)optin) {

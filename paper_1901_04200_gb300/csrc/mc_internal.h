@@ -16,6 +16,7 @@ struct KernelPair {
     const void *fwd_z = nullptr;      // forward sweep with checkpoints that also stores its normals
     const void *rev_z = nullptr;      // reverse sweep recomputing from checkpoints on the stored normals
     size_t stage_bytes_ckpt = 0;      // rev's shared staging buffers per block
+    bool rev_node_table = false;      // rev reads the surface as per-time-cell node pairs
     size_t stage_bytes_z = 0;         // rev_z's shared staging buffers per block
     const void *fwd_x = nullptr;      // forward sweep storing the state before every step (local vol)
     const void *rev_x = nullptr;      // reverse sweep running the adjoint from the stored states
@@ -27,6 +28,7 @@ struct KernelPair {
 bool gbm_kernels(int precision, int K, int ppt, KernelPair *out);
 bool heston_kernels(int precision, int K, int ppt, KernelPair *out);
 bool lv_kernels(int precision, int K, int ppt, KernelPair *out);
+bool lv_kernels_fp64(int K, int ppt, KernelPair *out);
 bool slv_kernels(int precision, int K, int ppt, KernelPair *out);
 
 // Small kernels (mc_aux.cu).

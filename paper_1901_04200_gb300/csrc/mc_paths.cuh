@@ -469,6 +469,24 @@ struct LvModel {
         add_node(sh, a, c + 1, g1);
         if (inside) xb = fma(hb * p.inv_hx, dh, xb);
     }
+    // Step n with the surface read from the per-time-cell node pairs (setup with node_table):
+    // the row value at the step's time is theta_jt + a_n (theta_jt+1 - theta_jt), formed in Real
+    // instead of read from a per-step row (the reverse sweep that re-runs segments into shared
+    // memory, which holds the node table and not the rows).
+    __device__ __forceinline__ static void step_nodes(State &s, Real z, int n, const Par &p, const Shared &sh) {
+        const Real u = scaled(s.x, p);
+        int c;
+        Real b;
+        bool inside;
+        cell(u, p, c, b, inside);
+        using P2 = typename std::conditional<sizeof(Real) == 4, float2, double2>::type;
+        const Real at = sh.a[n];
+        const P2 *nd = (const P2 *)sh.node + sh.jt[n] * sh.nx + c;
+        const P2 n0 = nd[0], n1 = nd[1];
+        const Real h0 = fma(at, n0.y, n0.x), h1 = fma(at, n1.y, n1.x);
+        const Real h = fma(b, h1 - h0, h0);
+        s.x = s.x + fma(h, fma(Real(-0.5), h, z), p.rdt);
+    }
     // The adjoint of step n from the states at both of its ends (stored-states variant): the
     // step x1 = x0 + r dt + h z - h^2 / 2 (h = sigma sqrt(dt)) gives
     // d x1 / d h = z - h = (x1 - x0 - r dt - h^2 / 2) / h,
@@ -1319,6 +1337,154 @@ __global__ void __launch_bounds__(kBlock) path_reverse_states_kernel(const DevPr
     }
 }
 
+// ------------------------------------------- recompute into shared memory --
+// Checkpoint-and-recompute (the two-step algorithm's step 2 with only every K-th state kept) for
+// local vol: per segment, last first, the reverse sweep re-runs the segment's K steps from its
+// checkpoint, regenerating the normals, and keeps the states x_0..x_K of its PPT paths per
+// thread in shared memory (per warp [K+1][PPT][32]) instead of a register tape; then it runs
+// adjoint_states backwards over consecutive states, as the stored-states sweep does with states
+// from HBM.  The registers no longer grow with K, so long segments keep several paths per thread.
+template <class Md, int K, int PPT>
+struct StateBuf {
+    static constexpr size_t kElems = (size_t)(K + 1) * PPT * kWarp;  // per warp
+    static constexpr size_t kBlockBytes = kElems * kWarpsPerBlock * sizeof(typename Md::Real);
+    __device__ static constexpr int at(int i, int q, int lane) { return (i * PPT + q) * kWarp + lane; }
+};
+
+template <class Md, int K, int PPT>
+__global__ void __launch_bounds__(kBlock) path_reverse_recompute_kernel(const DevProblem pb, const DevCall cl) {
+    using Real = typename Md::Real;
+    using SB = StateBuf<Md, K, PPT>;
+    using TL = SegTile<Md, K, PPT, 0>;
+    static_assert(Md::SD == 1, "one state word per path");
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int n_steps = pb.n_seg * K;
+    const SmemPlan sp(Md::kind, sizeof(Real), pb.m, pb.n_groups, pb.M, n_steps, pb.nx, true, SB::kBlockBytes, true);
+    load_tables<Md>(smem, sp, pb, true, cl);
+    typename Md::Shared sh;
+    typename Md::Par par;
+    Md::setup(smem, sp, pb, cl.theta, n_steps, sh, par, true);
+    __syncthreads();
+
+    const Real *strike = (const Real *)(smem + sp.strike);
+    const Real *sw = (const Real *)(smem + sp.seed_w);
+    const int *gseg = (const int *)(smem + sp.grp_seg);
+    const int *gbeg = (const int *)(smem + sp.grp_begin);
+    const int warp = threadIdx.x / kWarp, lane = threadIdx.x % kWarp;
+    double *wg = (double *)(smem + sp.wacc_g) + warp * pb.M;
+    const Real S0 = (Real)pb.S0;
+    Real *xs = (Real *)(smem + sp.zstage) + (size_t)warp * SB::kElems;
+    const RoundKeys rk = Md::kKeysInRegisters ? philox_round_keys(cl.seed) : cl.rk;
+
+    constexpr uint64_t kChunk = (uint64_t)kWarp * PPT;
+    const uint64_t n_chunks = (cl.n_paths + kChunk - 1) / kChunk;
+    const uint64_t ws_chunks = cl.ckpt_stride / kChunk;
+    const bool dyn = cl.queue != nullptr;  // chunks from the queue, one partial row per chunk
+    for (uint64_t ch = dyn ? take_chunk(cl.queue, lane) : (uint64_t)blockIdx.x * kWarpsPerBlock + warp; ch < n_chunks;
+         ch = dyn ? take_chunk(cl.queue, lane) : ch + (uint64_t)gridDim.x * kWarpsPerBlock) {
+        bool active[PPT];
+        Real xb[PPT], vb[PPT];
+        NormalSource<Md> rng[PPT];
+#pragma unroll
+        for (int q = 0; q < PPT; ++q) {
+            const uint64_t local = ch * kChunk + q * kWarp + lane;
+            active[q] = local < cl.n_paths;
+            rng[q].init(pb, cl, cl.path0 + (active[q] ? local : 0));
+            xb[q] = Real(0);
+            vb[q] = Real(0);
+        }
+        typename Md::Acc acc;
+        Md::acc_begin(acc, n_steps, sh);
+        int g = pb.n_groups - 1;
+        // the lane's checkpoint rows of the last segment (loaded one segment ahead)
+        typename TL::V::T grp[TL::Rp / TL::kG];
+        {
+            const Real *tl = TL::tile(cl.ckpt, ch, ws_chunks, pb.n_seg - 1);
+#pragma unroll
+            for (int k = 0; k < TL::Rp / TL::kG; ++k) grp[k] = *TL::group(tl, k, lane);
+        }
+        for (int s = pb.n_seg - 1; s >= 0; --s) {
+            typename Md::State st[PPT];
+#pragma unroll
+            for (int q = 0; q < PPT; ++q) {
+                const int r = TL::crow(0, q);
+                st[q].x = TL::V::get(grp[r / TL::kG], r % TL::kG);
+                xs[SB::at(0, q, lane)] = st[q].x;
+            }
+            if (s > 0) {  // the next segment's checkpoint, in flight during this one
+                const Real *tl = TL::tile(cl.ckpt, ch, ws_chunks, s - 1);
+#pragma unroll
+                for (int k = 0; k < TL::Rp / TL::kG; ++k) grp[k] = *TL::group(tl, k, lane);
+            }
+            // re-run the segment, keeping every state
+#pragma unroll
+            for (int i = 0; i < K; ++i) {
+                const int n = s * K + i;
+#pragma unroll
+                for (int q = 0; q < PPT; ++q) {
+                    Real z[Md::DZ];
+                    rng[q].get(n, i == 0, z, rk);
+                    Md::step_nodes(st[q], z[0], n, par, sh);
+                    xs[SB::at(i + 1, q, lane)] = st[q].x;
+                }
+            }
+            if (g >= 0 && gseg[g] == s) {  // payoff seeds at the segment's end
+                Real S[PPT], seed[PPT];
+#pragma unroll
+                for (int q = 0; q < PPT; ++q) {
+                    S[q] = S0 * exp_r<Real>(st[q].x);
+                    seed[q] = Real(0);
+                }
+                for (int i = gbeg[g]; i < gbeg[g + 1]; ++i) {
+                    const Real k = strike[i], wgt = sw[i];
+#pragma unroll
+                    for (int q = 0; q < PPT; ++q) seed[q] = S[q] > k ? fma(wgt, S[q], seed[q]) : seed[q];
+                }
+#pragma unroll
+                for (int q = 0; q < PPT; ++q)
+                    if (active[q]) xb[q] += seed[q];
+                --g;
+            }
+            // the adjoint backwards over the kept states
+#pragma unroll
+            for (int i = K - 1; i >= 0; --i) {
+                const int n = s * K + i;
+                Md::boundary(acc, n, sh, wg, lane);
+#pragma unroll
+                for (int q = 0; q < PPT; ++q) {
+                    typename Md::State x0, x1;
+                    x0.x = xs[SB::at(i, q, lane)];
+                    x1.x = xs[SB::at(i + 1, q, lane)];
+                    Md::adjoint_states(x0, x1, n, xb[q], vb[q], acc, par, sh);
+                }
+            }
+        }
+        Real vb_sum = Real(0);
+#pragma unroll
+        for (int q = 0; q < PPT; ++q) vb_sum += vb[q];
+        Md::acc_end(acc, vb_sum, par, sh, wg, lane);
+        if (dyn) {  // this chunk's sums to its own row; the warp's accumulators back to zero
+            __syncwarp();
+            for (int j = lane; j < pb.M; j += kWarp) {
+                cl.part_g[ch * pb.M + j] = wg[j];
+                wg[j] = 0.0;
+            }
+            __syncwarp();
+        }
+    }
+    if (dyn) {
+        queue_done(cl.queue);
+        return;
+    }
+    __syncthreads();
+    const double *wall = (const double *)(smem + sp.wacc_g);
+    for (int j = threadIdx.x; j < pb.M; j += blockDim.x) {
+        double sum = 0.0;
+        for (int w = 0; w < kWarpsPerBlock; ++w) sum += wall[w * pb.M + j];
+        cl.part_g[(size_t)blockIdx.x * pb.M + j] = sum;
+    }
+}
+
 // ---------------------------------------------------- full-storage variant --
 // The paper's branch for unconstrained memory (two-step algorithm, step 2:
 // with the first step's intermediate values kept, the reverse sweep costs
@@ -1514,6 +1680,10 @@ void set_kernels(Table *out) {
     out->stage_bytes_ckpt = SegTile<Md, K, PPT, false>::kBlockBytes;
     out->stage_bytes_z = SegTile<Md, K, PPT, true>::kBlockBytes;
     if constexpr (Md::kind == kLv) {  // stored states: local vol only
+        // checkpoint-and-recompute re-runs each segment into shared memory
+        out->rev = (const void *)path_reverse_recompute_kernel<Md, K, PPT>;
+        out->stage_bytes_ckpt = StateBuf<Md, K, PPT>::kBlockBytes;
+        out->rev_node_table = true;
         out->fwd_x = (const void *)path_forward_states_kernel<Md, K, PPT>;
         out->rev_x = (const void *)path_reverse_states_kernel<Md, K, PPT>;
         out->stage_bytes_x = SegTile<Md, K, PPT, 2>::kBlockBytes;
