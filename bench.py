@@ -108,16 +108,16 @@ def kernel_bytes(model, storage, K, S, n_groups):
 # sources' code (comments and layout aside) hashes to the captured version.  Key: (model,
 # storage, K, paths per thread, kernel).
 MEASURED_TRAFFIC = {
-    # stored states, 2^20 of 2^22 paths (x 4): read 2.118247 GB + write 5.651 MB; read 0.112 MB + write 2.040825 GB
-    ("lv", "states", 5, 4, "reverse_sweep"): {"bytes": 8495592000, "sources": "07c64ee22ca8b8cb"},
-    ("lv", "states", 5, 4, "forward_sweep"): {"bytes": 8163748000, "sources": "07c64ee22ca8b8cb"},
-    # stored normals, 2^18 of 2^20 paths (x 4): read 1.208042 GB + write 0.583 MB; read 0.045 MB + write 1.146336 GB
-    ("heston", "normals", 8, 2, "reverse_sweep"): {"bytes": 4834500000, "sources": "17ad4774d2211d15"},
-    ("heston", "normals", 8, 2, "forward_sweep"): {"bytes": 4585524000, "sources": "17ad4774d2211d15"},
+    # stored states, 2^20 of 2^22 paths (x 4): read 2.119408 GB + write 15.876 MB; read 0.525 MB + write 2.054665 GB
+    ("lv", "states", 5, 4, "reverse_sweep"): {"bytes": 8541136000, "sources": "ffbc6dfb4fe77cd3"},
+    ("lv", "states", 5, 4, "forward_sweep"): {"bytes": 8218760000, "sources": "ffbc6dfb4fe77cd3"},
+    # stored normals, 2^18 of 2^20 paths (x 4): read 1.208088 GB + write 3.704 MB; read 0.082 MB + write 1.148862 GB
+    ("heston", "normals", 8, 2, "reverse_sweep"): {"bytes": 4847168000, "sources": "3b9af2d7af9e1186"},
+    ("heston", "normals", 8, 2, "forward_sweep"): {"bytes": 4595776000, "sources": "3b9af2d7af9e1186"},
 }
 KERNEL_SOURCES = ["mc_common.cuh", "mc_paths.cuh"]
-MODEL_SOURCE = {"gbm": "mc_paths_gbm.cu", "heston": "mc_paths_heston.cu", "lv": "mc_paths_lv.cu",
-                "slv": "mc_paths_slv.cu"}
+MODEL_SOURCE = {"gbm": ["mc_paths_gbm.cu"], "heston": ["mc_paths_heston.cu"],
+                "lv": ["mc_paths_lv.cuh", "mc_paths_lv.cu"], "slv": ["mc_paths_slv.cu"]}
 
 
 def code_tokens(src):
@@ -148,7 +148,7 @@ def code_tokens(src):
 def kernel_sources_hash(model="heston"):
     import hashlib
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES + [MODEL_SOURCE[model]]:
+    for f in KERNEL_SOURCES + MODEL_SOURCE[model]:
         with open(os.path.join(ROOT, "paper_1901_04200_gb300", "csrc", f)) as fh:
             h.update(code_tokens(fh.read()).encode())
     return h.hexdigest()[:16]
