@@ -24,6 +24,7 @@
 #include <cuda_bf16.h>
 
 #include <cstdio>
+#include <cstdlib>
 #include <new>
 #include <utility>
 #include <vector>
@@ -41,6 +42,13 @@ constexpr int kSplit = 16;  // K slices of the weight-gradient GEMMs (at most; s
 // K = 2B = B/32 k-blocks of 64, and each slice must be whole k-blocks, so the split is the
 // largest of 16, 8, 4 dividing B/32 (a multiple of 4).
 constexpr int k_split(int B) { return (B / 32) % 16 == 0 ? 16 : ((B / 32) % 8 == 0 ? 8 : 4); }
+// Tuning knobs, read when a context is created: MCAAD_MLP_WGRAD_SPLIT (4, 8 or 16, used when it
+// divides B/32) and MCAAD_MLP_WGRAD_BN (columns per CTA of the weight-gradient GEMMs: 16..256, a
+// multiple of 16; 0 = 32).  Defaults: the measured-fastest shape.
+static int env_knob(const char *name) {
+    const char *v = getenv(name);
+    return v ? atoi(v) : 0;
+}
 
 // flat FP32 parameter layout
 constexpr long long oW1 = 0, ob1 = oW1 + H * DIN, oW2 = ob1 + H, ob2 = oW2 + H * H, oW3 = ob2 + H,
@@ -78,7 +86,8 @@ struct Bufs {
     bf16 *Aop[5];        // [H][2B]
     bf16 *Bop[5];        // l = 1: [NX][2B], else [H][2B]
     float *part[5];      // l = 1..4: [split][H][N_l] split-K partials of dW_l
-    int split;           // k_split(B)
+    int split;           // k_split(B), or MCAAD_MLP_WGRAD_SPLIT
+    int wgrad_bn;        // columns per CTA of G1..G4 (0: tile_n)
     float *colpart;      // [B / 128][41 * 32] column-sum chunks
     bf16 *Wb[5], *Wt[5];  // W1b [H][KX], W1t [NX][H], Wlb/Wlt [H][H]
     float *lsum;         // [1] loss scratch
@@ -597,6 +606,9 @@ size_t layout(unsigned char *base, int B, Bufs *out) {
     Bufs b{};
     b.B = B;
     b.split = k_split(B);
+    const int sp = env_knob("MCAAD_MLP_WGRAD_SPLIT"), bn = env_knob("MCAAD_MLP_WGRAD_BN");
+    if ((sp == 4 || sp == 8 || sp == 16) && (B / 32) % sp == 0) b.split = sp;
+    b.wgrad_bn = (bn >= 16 && bn <= 256 && bn % 16 == 0) ? bn : 0;
     const size_t BH = (size_t)B * H, B2 = 2 * (size_t)B;
     b.x0 = c.take<bf16>((size_t)B * KX);
     for (int l = 1; l <= 4; ++l) b.z[l] = c.take<float>(BH);
@@ -716,7 +728,8 @@ cudaError_t loss_grad_impl(mlp_ctx *c, const float *params, const float *X, cons
     for (int l = 1; l <= 4 && e == cudaSuccess; ++l) {
         const int N = l == 1 ? NX : H;
         EpiPartial ep{b.part[l], N, H};
-        e = gemm(b.Aop[l], B2, b.Bop[l], B2, H, N, (int)B2, (int)(B2 / b.split), ep, b.err, st);
+        e = gemm(b.Aop[l], B2, b.Bop[l], B2, H, N, (int)B2, (int)(B2 / b.split), ep, b.err, st,
+                 N >= b.wgrad_bn ? b.wgrad_bn : 0);
     }
     if (e == cudaSuccess) {
         e = launch_pdl(reduce_split_kernel, dim3(grid_for((long long)H * DIN + 3LL * H * H)), dim3(256), 0, st,

@@ -164,6 +164,15 @@ def test_lv_fp32_small(L, orc):
     check(L, orc, w, 1e-4, 2e-6)
 
 
+@pytest.mark.parametrize("K,ppt", [(25, 1), (25, 2), (5, 4)])
+def test_lv_fp32_recompute(L, orc, K, ppt):
+    """Checkpoints only, each segment re-run into shared memory (25 steps, two paths per thread:
+    the bench's recompute arm), on the workload's own grid and instruments, ragged path count."""
+    w = inputs.lv_config(n_paths=(1 << 13) - 17)
+    w = replace(w, problem=replace(w.problem, storage="checkpoint", ckpt_every=K, paths_per_thread=ppt))
+    check(L, orc, w, 1e-4, 2e-6)
+
+
 def test_gbm_fp32(L, orc):
     w = inputs.gbm_config()
     w = replace(w, problem=replace(w.problem, precision="fp32"))
@@ -311,6 +320,16 @@ def test_lv_full_size_sampled(L, orc):
     """2^22 x 500 local vol (the bench's headline workload and launch shape)."""
     ctx = full_size_sampled(L, orc, inputs.lv_config(), 1 << 13)
     assert ctx.storage == "states"
+
+
+@pytest.mark.slow
+def test_lv_full_size_sampled_recompute(L, orc):
+    """The same workload by checkpoints every 25 steps and recompute, two paths per thread (the
+    bench's recompute arm and launch shape)."""
+    w = inputs.lv_config()
+    w = replace(w, problem=replace(w.problem, storage="checkpoint", ckpt_every=25, paths_per_thread=2))
+    ctx = full_size_sampled(L, orc, w, 1 << 12)
+    assert ctx.storage == "checkpoint"
 
 
 # ------------------------------------------------- Heston SLV (the paper's model)
