@@ -20,11 +20,14 @@
 //
 // then fixed-order reductions (split-K slices, bias and w5 column sums, the
 // loss) and Adam on FP32 master parameters, which also refreshes the BF16
-// weight copies (W_l and W_l^T) the GEMMs read.
+// weight copies (W_l and W_l^T) the GEMMs read.  MCAAD_MLP_CHAIN=1 runs a
+// training step's F, T, R and D as one chain_kernel launch instead (each CTA
+// the whole sequence for its 128 rows), which measured slower.
 #include <cuda_bf16.h>
 
 #include <cstdio>
 #include <cstdlib>
+#include <cstring>
 #include <new>
 #include <utility>
 #include <vector>
@@ -464,6 +467,76 @@ __global__ void reduce_split_kernel(const Partials pp, float *grads) {
     }
 }
 
+// ------------------------------------------------------- the row chain --
+// Every product of the step except G1..G4 is row-local: a row's F, T, R and D stages read only
+// that row's earlier results.  chain_kernel runs them all for one 128-row block per CTA (tc::Chain:
+// one ring and one 256-column accumulator for the whole sequence), with the input staging and
+// the F4 output row sums in between, so the fifteen GEMMs, prep_input and finish_out become one
+// launch.  Stage order and epilogues are those of run_forward and loss_grad_impl.  Measured at
+// batch 4096 (32 CTAs): 0.47 ms per training step against 0.18 ms with one launch per GEMM -- the
+// epilogues' row-major and transposed stores (about 20 MB per step) then run on 32 SMs with four
+// warps each (13.8 % of issue slots busy, the tensor pipe 3 % of active cycles), where one launch
+// per GEMM spreads them over 256 CTAs; so it is opt-in (MCAAD_MLP_CHAIN=1).
+constexpr int kChainStages = 15;  // F1..F4, T4..T1, R1..R4, D4..D2
+struct ChainParams {
+    CUtensorMap a[kChainStages], b[kChainStages];  // each stage's A (the block's rows) and B (all N rows)
+    EpiFwd f[3];      // F1..F3
+    EpiFwdLast f4;
+    EpiTan t[3];      // T4, T3, T2
+    EpiTanIn t1;
+    EpiTbar r[3];     // R1..R3
+    EpiTbarLast r4;
+    EpiDbar d[3];     // D4, D3, D2
+    const float *X, *b5, *y, *outp;
+    bf16 *x0, *xT;
+    float *out, *obar, *loss_rows;
+    float inv_b;
+    int B;
+    long long B2;
+    int *err;
+};
+
+__global__ void __launch_bounds__(tc::kThreads, 1) chain_kernel(const __grid_constant__ ChainParams P) {
+    tc::Chain c;
+    tc::chain_setup(c);
+    tc::pdl_wait();
+    const int row0 = blockIdx.x * tc::kBM;
+    // the block's input rows: x0 (BF16, K padded to KX; the padding stays zero) and X^T into Bop_1
+    for (int q = threadIdx.x; q < tc::kBM * DIN; q += blockDim.x) {
+        const int r = row0 + q / DIN, j = q % DIN;
+        const bf16 v = __float2bfloat16_rn(P.X[(long long)r * DIN + j]);
+        P.x0[(long long)r * KX + j] = v;
+        P.xT[(long long)j * P.B2 + P.B + r] = v;
+    }
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+    __syncthreads();
+    bool ok = true;
+    int s = 0;
+    for (int l = 0; l < 3 && ok; ++l, ++s) ok = tc::chain_stage(c, &P.a[s], &P.b[s], l == 0 ? KX : H, H, row0, P.f[l]);
+    if (ok) ok = tc::chain_stage(c, &P.a[s], &P.b[s], H, H, row0, P.f4);
+    ++s;
+    if (ok) {  // out, out_bar and the value part of the loss for the block's rows
+        const int r = row0 + threadIdx.x;
+        float o = P.b5[0];
+        for (int t = 0; t < H / 32; ++t) o += P.outp[(long long)t * P.B + r];
+        P.out[r] = o;
+        const float d = o - P.y[r];
+        P.obar[r] = 2.0f * d * P.inv_b;
+        P.loss_rows[r] = d * d * P.inv_b;
+    }
+    __syncthreads();
+    for (int l = 0; l < 3 && ok; ++l, ++s) ok = tc::chain_stage(c, &P.a[s], &P.b[s], H, H, row0, P.t[l]);
+    if (ok) ok = tc::chain_stage(c, &P.a[s], &P.b[s], H, NX, row0, P.t1);
+    ++s;
+    for (int l = 0; l < 3 && ok; ++l, ++s) ok = tc::chain_stage(c, &P.a[s], &P.b[s], l == 0 ? KX : H, H, row0, P.r[l]);
+    if (ok) ok = tc::chain_stage(c, &P.a[s], &P.b[s], H, H, row0, P.r4);
+    ++s;
+    for (int l = 0; l < 3 && ok; ++l, ++s) ok = tc::chain_stage(c, &P.a[s], &P.b[s], H, H, row0, P.d[l]);
+    tc::pdl_trigger();
+    tc::chain_teardown(c);
+    if (!ok && threadIdx.x == 0 && P.err) atomicExch(P.err, 1);
+}
+
 // Column sums in a fixed order, coalesced, in two passes.  Pass 1: block
 // (q, c) covers 32 consecutive columns of one source over row chunk c of
 // kColChunk rows; lane = column, the 8 warps take rows r0 + w, r0 + w + 8, ...
@@ -696,18 +769,94 @@ void drop_graph(TrainGraph &tg) {
 }
 
 // The differential loss and its gradient for the batch (X, y, dy), all stream-ordered on st.
+// The row chain of the training step (F1..F4, T4..T1, R1..R4, D4..D2 and their input and output
+// row work) as one chain_kernel launch of B/128 CTAs.
+cudaError_t chain_impl(mlp_ctx *c, const float *prm, const float *X, const float *y, const float *dy, float alpha,
+                       cudaStream_t st) {
+    Bufs &b = c->b;
+    const int B = b.B;
+    const long long B2 = 2LL * B;
+    const float inv_b = 1.0f / (float)B;
+    ChainParams P;
+    memset(&P, 0, sizeof(P));
+    cudaError_t e = cudaSuccess;
+    int s = 0;
+    auto stage_maps = [&](const bf16 *A, int K, const bf16 *Bw, int N) {
+        if (e == cudaSuccess) e = tc::make_map(&P.a[s], A, K, K, B, tc::kBM);
+        if (e == cudaSuccess) e = tc::make_map(&P.b[s], Bw, K, K, N, N);
+        ++s;
+    };
+    for (int l = 1; l <= 3; ++l) {
+        P.f[l - 1] = EpiFwd{prm + ob(l), b.z[l], b.h[l], b.Bop[l + 1], B2, B};
+        stage_maps(l == 1 ? b.x0 : b.h[l - 1], l == 1 ? KX : H, b.Wb[l], H);
+    }
+    P.f4 = EpiFwdLast{prm + ob4, prm + ow5, b.z[4], b.outp, b.h[4], b.p[4], b.Aop[4], B2, B};
+    stage_maps(b.h[3], H, b.Wb[4], H);
+    for (int l = 4; l >= 2; --l) {
+        P.t[4 - l] = EpiTan{b.z[l - 1], b.g[l - 1], b.p[l - 1], b.Aop[l - 1], B2};
+        stage_maps(b.p[l], H, b.Wt[l], H);
+    }
+    P.t1 = EpiTanIn{b.g[0], dy, b.gb0, b.Bop[1], b.loss_rows, B2, 2.0f * alpha * inv_b, alpha * inv_b};
+    stage_maps(b.p[1], H, b.Wt[1], NX);
+    for (int l = 1; l <= 3; ++l) {
+        P.r[l - 1] = EpiTbar{b.z[l], b.g[l], b.gb[l], b.Bop[l + 1], b.zbt[l], B2};
+        stage_maps(l == 1 ? b.gb0 : b.gb[l - 1], l == 1 ? KX : H, b.Wb[l], H);
+    }
+    P.r4 = EpiTbarLast{b.z[4], prm + ow5, b.obar, b.gb4f, b.zb[4], b.zbb[4], b.Aop[4], B2, B};
+    stage_maps(b.gb[3], H, b.Wb[4], H);
+    for (int l = 4; l >= 2; --l) {
+        P.d[4 - l] = EpiDbar{b.z[l - 1], b.zbt[l - 1], b.zb[l - 1], l - 1 >= 2 ? b.zbb[l - 1] : nullptr, b.Aop[l - 1],
+                             B2, B};
+        stage_maps(b.zbb[l], H, b.Wt[l], H);
+    }
+    if (e != cudaSuccess) return e;
+    if (s != kChainStages) return cudaErrorInvalidValue;
+    P.X = X;
+    P.b5 = prm + ob5;
+    P.y = y;
+    P.outp = b.outp;
+    P.x0 = b.x0;
+    P.xT = b.Bop[1];
+    P.out = b.out;
+    P.obar = b.obar;
+    P.loss_rows = b.loss_rows;
+    P.inv_b = inv_b;
+    P.B = B;
+    P.B2 = B2;
+    P.err = b.err;
+    static bool attr_set[64] = {false};
+    int dev = 0;
+    e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64 || !attr_set[dev]) {
+        e = cudaFuncSetAttribute(chain_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)tc::chain_smem_bytes());
+        if (e != cudaSuccess) return e;
+        if (dev >= 0 && dev < 64) attr_set[dev] = true;
+    }
+    e = launch_pdl(chain_kernel, dim3(B / tc::kBM), dim3(tc::kThreads), tc::chain_smem_bytes(), st, P);
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
 cudaError_t loss_grad_impl(mlp_ctx *c, const float *params, const float *X, const float *y, const float *dy,
                            float alpha, float *loss_out, float *grads, cudaStream_t st) {
     Bufs &b = c->b;
     const int B = b.B;
     const long long B2 = 2LL * B;
-    cudaError_t e0 = launch_pdl(prep_input_kernel, dim3(grid_for((long long)B * DIN)), dim3(256), 0, st, X, B, B, b.x0,
-                                b.Bop[1], B2);
-    if (e0 != cudaSuccess) return e0;
-    cudaError_t e = cudaGetLastError();
-    if (e == cudaSuccess) e = run_forward(c, params, y, dy, alpha, true, st);
+    cudaError_t e = cudaSuccess;
+    // MCAAD_MLP_CHAIN=1: the row chain as one chain_kernel launch (measured slower, see chain_kernel)
+    const bool chain = env_knob("MCAAD_MLP_CHAIN") > 0;
+    if (chain) {
+        e = chain_impl(c, params, X, y, dy, alpha, st);
+    } else {
+        e = launch_pdl(prep_input_kernel, dim3(grid_for((long long)B * DIN)), dim3(256), 0, st, X, B, B, b.x0,
+                       b.Bop[1], B2);
+        if (e == cudaSuccess) e = cudaGetLastError();
+        if (e == cudaSuccess) e = run_forward(c, params, y, dy, alpha, true, st);
+    }
     // R1..R4: up the tangent chain
-    for (int l = 1; l <= 4 && e == cudaSuccess; ++l) {
+    for (int l = 1; l <= 4 && e == cudaSuccess && !chain; ++l) {
         const bf16 *A = l == 1 ? b.gb0 : b.gb[l - 1];
         const int K = l == 1 ? KX : H;
         if (l < 4) {
@@ -719,7 +868,7 @@ cudaError_t loss_grad_impl(mlp_ctx *c, const float *params, const float *X, cons
         }
     }
     // D4..D2: down the forward chain
-    for (int l = 4; l >= 2 && e == cudaSuccess; --l) {
+    for (int l = 4; l >= 2 && e == cudaSuccess && !chain; --l) {
         EpiDbar ep{b.z[l - 1], b.zbt[l - 1], b.zb[l - 1], l - 1 >= 2 ? b.zbb[l - 1] : nullptr, b.Aop[l - 1], B2, B};
         e = gemm(b.zbb[l], H, b.Wt[l], H, B, H, H, H, ep, b.err, st);
     }

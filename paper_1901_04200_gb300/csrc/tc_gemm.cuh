@@ -338,6 +338,169 @@ __device__ __forceinline__ void gemm_body(const TensorMaps &tm, const GemmShape 
     }
 }
 
+// ---------------------------------------------------------------- chains --
+// A CTA that runs a sequence of GEMMs over its own 128 rows (D_s[128 x N_s] = A_s B_s^T, every
+// N_s <= 256 in one tile), each stage's epilogue writing what later stages read: the ring, its
+// barriers and 256 columns of tensor memory are set up once, and the ring's slot and phase run on
+// across stages (k-block g of the chain uses slot g % kStages).  Between stages the CTA waits for
+// the epilogue's stores (generic proxy) to be visible to the next stage's TMA loads (async proxy).
+// Shared memory: chain_smem_bytes().  A stage with an expired wait sets `fail`; the caller stops
+// running stages (every thread sees the flag after the stage's closing barrier).
+constexpr int kChainBN = 256;
+__host__ __device__ constexpr size_t chain_smem_bytes() { return smem_bytes(kChainBN, kStages); }
+
+struct Chain {
+    unsigned char *base, *tA, *tB;
+    uint32_t full0, empty0, done, tmem;
+    volatile int *fail;
+    int kbg;     // k-blocks issued by earlier stages
+    int stages;  // stages run (the done barrier's phase)
+};
+
+// All threads: carve the ring, initialise the barriers, allocate the tensor memory.
+__device__ __forceinline__ void chain_setup(Chain &c) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    c.base = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    c.tA = c.base;
+    c.tB = c.base + (size_t)kStages * tile_a_bytes();
+    uint64_t *bars = (uint64_t *)(c.tB + (size_t)kStages * tile_b_bytes(kChainBN));
+    uint32_t *tslot = (uint32_t *)(bars + 2 * kStages + 1);
+    c.fail = (volatile int *)(tslot + 1);
+    c.full0 = smem_u32(bars);
+    c.empty0 = smem_u32(bars + kStages);
+    c.done = smem_u32(bars + 2 * kStages);
+    c.kbg = 0;
+    c.stages = 0;
+    const int tid = threadIdx.x;
+    if (tid / 32 == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                     "r"((uint32_t)kChainBN));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        *c.fail = 0;
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(c.full0 + 8 * s, 1);
+            mbar_init(c.empty0 + 8 * s, 1);
+        }
+        mbar_init(c.done, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    c.tmem = *tslot;
+}
+
+// One stage: D[row0 .. row0+127][0 .. N) = A[rows][0 .. K) B[0 .. N)[0 .. K)^T (K a multiple of
+// 64, at most kStages * 64 = 256; N a multiple of 16, at most 256; the B map's box is N rows),
+// then the epilogue as in gemm_body (Epi::kColumns: lane j
+// of a warp gets column c0 + j of the warp's 32 rows; else each thread its row).  Returns false
+// (and sets the chain's fail flag) if a wait expired.
+template <class Epi>
+__device__ __forceinline__ bool chain_stage(Chain &c, const CUtensorMap *ma, const CUtensorMap *mb, int K, int N,
+                                            int row0, const Epi &epi) {
+    const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
+    const int kbt = K / kBK;
+    const uint32_t stage_bytes = (uint32_t)(tile_a_bytes() + tile_b_bytes(N));
+    bool ok = true;
+    if (warp == 0) {
+        if (lane == 0) {  // producer
+            int issued = 0;
+            for (int kb = 0; kb < kbt; ++kb) {
+                const int g = c.kbg + kb, s = g % kStages;
+                if (g >= kStages && !mbar_wait(c.empty0 + 8 * s, (uint32_t)((g / kStages - 1) & 1))) {
+                    ok = false;
+                    break;
+                }
+                mbar_arrive_expect_tx(c.full0 + 8 * s, stage_bytes);
+                tma_load_2d(smem_u32(c.tA + (size_t)s * tile_a_bytes()), ma, kb * kBK, row0, c.full0 + 8 * s);
+                tma_load_2d(smem_u32(c.tB + (size_t)s * tile_b_bytes(kChainBN)), mb, kb * kBK, 0, c.full0 + 8 * s);
+                ++issued;
+            }
+            // no load in flight when the stage ends (bounded; K <= kStages * kBK, so each slot holds
+            // one k-block of this stage and its phase is the one armed above)
+            for (int kb = 0; kb < issued; ++kb) {
+                const int g = c.kbg + kb;
+                if (!mbar_wait(c.full0 + 8 * (g % kStages), (uint32_t)((g / kStages) & 1))) ok = false;
+            }
+            if (!ok) *c.fail = 1;
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        if (lane == 0) {  // MMA issuer
+            const uint32_t idesc = idesc_bf16(kBM, N);
+            for (int kb = 0; kb < kbt; ++kb) {
+                const int g = c.kbg + kb, s = g % kStages;
+                if (!mbar_wait(c.full0 + 8 * s, (uint32_t)((g / kStages) & 1))) {
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t a0 = smem_u32(c.tA + (size_t)s * tile_a_bytes());
+                const uint32_t b0 = smem_u32(c.tB + (size_t)s * tile_b_bytes(kChainBN));
+#pragma unroll
+                for (int k = 0; k < kBK / 16; ++k)
+                    mma_bf16(c.tmem, desc_sw128(a0 + k * 32), desc_sw128(b0 + k * 32), idesc,
+                             (kb + k) > 0 ? 1u : 0u);
+                mma_commit(c.empty0 + 8 * s);
+            }
+            mma_commit(c.done);  // also after an expired wait: no MMA runs past the stage
+            if (!ok) *c.fail = 1;
+        }
+        __syncwarp();
+    }
+    ok = mbar_wait(c.done, (uint32_t)(c.stages & 1)) && ok;
+    if (!ok) *c.fail = 1;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (!*c.fail) {
+        const uint32_t trow = c.tmem + ((uint32_t)(warp * 32) << 16);
+        if constexpr (Epi::kColumns) {
+            float *stage = (float *)c.base + warp * 32 * 33;  // the drained ring
+            for (int c0 = 0; c0 < N; c0 += 32) {
+                float v[32];
+                if (N - c0 >= 32) tmem_ld32(trow + (uint32_t)c0, v);
+                else tmem_ld16(trow + (uint32_t)c0, v);
+#pragma unroll
+                for (int i = 0; i < 32; ++i) stage[lane * 33 + i] = v[i];
+                __syncwarp();
+                float u[32];
+#pragma unroll
+                for (int r = 0; r < 32; ++r) u[r] = stage[r * 33 + lane];
+                __syncwarp();
+                epi.apply_cols(row0 + warp * 32, c0 + lane, u, lane < N - c0, 0, lane);
+            }
+        } else {
+            const int row = row0 + warp * 32 + lane;
+            float state = 0.0f;
+            for (int c0 = 0; c0 < N; c0 += 32) {
+                float v[32];
+                if (N - c0 >= 32) tmem_ld32(trow + (uint32_t)c0, v);
+                else tmem_ld16(trow + (uint32_t)c0, v);
+                epi.apply((long long)row, c0, v, (N - c0) < 32 ? (N - c0) : 32, 0, state);
+            }
+        }
+    }
+    // the stores reach the next stage's TMA loads; tensor memory is free for its MMAs
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    c.kbg += kbt;
+    ++c.stages;
+    return !*c.fail;
+}
+
+// All threads, after the last stage: free the tensor memory.
+__device__ __forceinline__ void chain_teardown(Chain &c) {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (threadIdx.x / 32 == 0) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(c.tmem), "r"((uint32_t)kChainBN));
+    }
+}
+
 // Host: the TMA descriptor of a BF16 operand stored as `rows` rows of `cols` elements (K
 // contiguous) with a row pitch of `ld` elements, loaded in boxes of 64 elements x `box_rows`
 // rows with the 128-byte swizzle the MMA descriptors expect.  The encoder comes from the driver

@@ -81,6 +81,30 @@ def test_loss_grad_matches_oracle(L, alpha, B):
     assert rel(gv, gr) <= 2e-3
 
 
+@pytest.mark.parametrize("B", [128, 4096])
+def test_row_chain_kernel_matches_oracle(L, B, monkeypatch):
+    """The opt-in single-launch row chain (MCAAD_MLP_CHAIN=1: F, T, R, D of each 128-row block in
+    one CTA) gives the loss gradient of the per-GEMM path."""
+    monkeypatch.setenv("MCAAD_MLP_CHAIN", "1")
+    p, X, y, dy = setup(B, seed=5)
+    net = L.Mlp(B)
+    prm = cuda32(omlp.flatten(p))
+    net.set_weights(prm)
+    grads = torch.zeros(net.n_params, dtype=torch.float32, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    net.loss_grad(prm, cuda32(X), cuda32(y), cuda32(dy), 1.0, grads, loss)
+    torch.cuda.synchronize()
+    assert net.error_flag() == 0
+    L_ref, g_ref, _, _ = omlp.loss_grad(p, X, y, dy, 1.0, bf16=True)
+    assert abs(loss.item() - L_ref) <= 2e-3 * abs(L_ref)
+    gv = grads.cpu().numpy().astype(np.float64)
+    gr = omlp.flatten(g_ref)
+    for name, s in omlp.SHAPES:
+        a = omlp.unflatten(gv)[name]
+        b = omlp.unflatten(gr)[name]
+        assert np.max(np.abs(a - b)) <= 5e-3 * np.max(np.abs(b)), (name, np.max(np.abs(a - b)), np.max(np.abs(b)))
+
+
 def test_adam_step_matches_oracle(L):
     B = 128
     p, X, y, dy = setup(B, seed=2)
