@@ -487,7 +487,7 @@ def tape_bench(args, rank, world):
             "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"]}}))
 
 
-def calibration_experiment(cases):
+def calibration_experiment(cases, epochs=40, label_paths=1 << 16, n_theta=16384):
     """Surrogate labels and training (the learned part), then Heston calibration to
     G < 1e-8 at 2^22 paths: surrogate-assisted vs plain MC-AAD descent from the same starts."""
     import numpy as np
@@ -495,14 +495,13 @@ def calibration_experiment(cases):
 
     from paper_1901_04200_gb300 import _lib, calibrate, inputs, surrogate
     pb = inputs.heston_config().problem
-    n_theta, n_paths = 16384, 1 << 16
+    n_paths = label_paths
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     X, y, dy = surrogate.make_dataset(pb, n_theta, n_paths)
     torch.cuda.synchronize()
     t_data = time.perf_counter() - t0
     sur = surrogate.Surrogate(batch=4096)
-    epochs = 40
     t_train = sur.train(X, y, dy, epochs=epochs, lr=2e-3)
     P, seed = 1 << 22, 777
     ctx = _lib.Context(pb, max_paths=P)
@@ -871,6 +870,10 @@ def main():
     ap.add_argument("--no-arms", action="store_true",
                     help="skip the recompute and forward-mode comparison arms")
     ap.add_argument("--calib-cases", type=int, default=16)
+    ap.add_argument("--calib-epochs", type=int, default=40, help="surrogate training epochs")
+    ap.add_argument("--calib-label-paths", type=int, default=1 << 16, help="MC paths per surrogate label")
+    ap.add_argument("--calib-thetas", type=int, default=16384,
+                    help="parameter draws for the surrogate labels (64 instruments each)")
     ap.add_argument("--ckpt", type=int, default=0, help="checkpoint interval (0 = workload default)")
     ap.add_argument("--storage", default="auto", choices=["auto", "checkpoint", "normals", "full", "states"],
                     help="what the reverse sweep reads: checkpoints (re-run with regenerated normals), "
@@ -907,7 +910,8 @@ def main():
         if rank == 0:
             line["workloads"][r["config"]["workload"]] = r
     if rank == 0 and not args.no_calibration and world == 1:
-        line["calibration"] = calibration_experiment(args.calib_cases)
+        line["calibration"] = calibration_experiment(args.calib_cases, args.calib_epochs, args.calib_label_paths,
+                                                     args.calib_thetas)
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
