@@ -111,6 +111,11 @@ MEASURED_TRAFFIC = {
     # stored states, 2^20 of 2^22 paths (x 4): read 2.119408 GB + write 15.876 MB; read 0.525 MB + write 2.054665 GB
     ("lv", "states", 5, 4, "reverse_sweep"): {"bytes": 8541136000, "sources": "ffbc6dfb4fe77cd3"},
     ("lv", "states", 5, 4, "forward_sweep"): {"bytes": 8218760000, "sources": "ffbc6dfb4fe77cd3"},
+    # checkpoints every 25 steps, two paths per thread (the recompute arm), 2^21 of 2^22 paths (x 2):
+    # read 336.460 MB + write 42.971 MB; read 0.306 MB + write 327.616 MB (each 4-row checkpoint
+    # group holds the two path slots and two padding rows, twice the algorithmic bytes)
+    ("lv", "checkpoint", 25, 2, "reverse_sweep"): {"bytes": 758862000, "sources": "ffbc6dfb4fe77cd3"},
+    ("lv", "checkpoint", 25, 2, "forward_sweep"): {"bytes": 655844000, "sources": "ffbc6dfb4fe77cd3"},
     # stored normals, 2^18 of 2^20 paths (x 4): read 1.208088 GB + write 3.704 MB; read 0.082 MB + write 1.148862 GB
     ("heston", "normals", 8, 2, "reverse_sweep"): {"bytes": 4847168000, "sources": "3b9af2d7af9e1186"},
     ("heston", "normals", 8, 2, "forward_sweep"): {"bytes": 4595776000, "sources": "3b9af2d7af9e1186"},
