@@ -22,7 +22,8 @@
 // loss) and Adam on FP32 master parameters, which also refreshes the BF16
 // weight copies (W_l and W_l^T) the GEMMs read.  MCAAD_MLP_CHAIN=1 runs a
 // training step's F, T, R and D as one chain_kernel launch instead (each CTA
-// the whole sequence for its 128 rows), which measured slower.
+// the whole sequence for its 128 rows), 2 as one chain_cluster_kernel launch
+// (a cluster of eight CTAs per 128 rows); both measured slower.
 #include <cuda_bf16.h>
 
 #include <cstdio>
@@ -541,6 +542,62 @@ __global__ void __launch_bounds__(tc::kThreads, 1) chain_kernel(const __grid_con
     if (!ok && threadIdx.x == 0 && P.err) atomicExch(P.err, 1);
 }
 
+// The same chain with each stage's 256 columns spread over a cluster of eight CTAs (32 columns
+// each, as the per-GEMM launches tile them): a stage's epilogue stores reach the next stage's
+// loads in the other CTAs through a cluster barrier (release/acquire) instead of a kernel
+// boundary.  Every CTA passes every barrier, computing or not (T1's 16 columns are rank 0's), so a
+// failed stage stops no CTA early.  Measured at batch 4096: 0.193 ms per training step against
+// 0.187 ms with one launch per GEMM (MCAAD_MLP_CHAIN=2 selects it): the kernel boundaries it
+// removes were not what each stage waits for; each CTA's own chain of TMA, MMA and epilogue
+// latencies is the same in both.
+constexpr int kClusterCtas = H / 32;
+constexpr int kClusterBN = 32;
+
+__global__ void __launch_bounds__(tc::kThreads, 1) chain_cluster_kernel(const __grid_constant__ ChainParams P) {
+    tc::Chain c;
+    tc::chain_setup(c, kClusterBN);
+    const int rank = (int)tc::cluster_rank();
+    const int row0 = (int)(blockIdx.x / kClusterCtas) * tc::kBM;
+    const int col0 = rank * kClusterBN;
+    constexpr int kRowsPer = tc::kBM / kClusterCtas;  // rows of the block's row work per CTA
+    tc::pdl_wait();
+    for (int q = threadIdx.x; q < kRowsPer * DIN; q += blockDim.x) {
+        const int r = row0 + rank * kRowsPer + q / DIN, j = q % DIN;
+        const bf16 v = __float2bfloat16_rn(P.X[(long long)r * DIN + j]);
+        P.x0[(long long)r * KX + j] = v;
+        P.xT[(long long)j * P.B2 + P.B + r] = v;
+    }
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+    tc::cluster_sync();
+    bool ok = true;
+    int s = 0;
+    auto stage = [&](const auto &epi, int K, int N, bool mine, int cb) {
+        if (ok && mine) ok = tc::chain_stage(c, &P.a[s], &P.b[s], K, N, row0, epi, cb);
+        ++s;
+        tc::cluster_sync();
+    };
+    for (int l = 0; l < 3; ++l) stage(P.f[l], l == 0 ? KX : H, kClusterBN, true, col0);
+    stage(P.f4, H, kClusterBN, true, col0);
+    if (ok && threadIdx.x < kRowsPer) {  // out, out_bar and the value part of the loss
+        const int r = row0 + rank * kRowsPer + threadIdx.x;
+        float o = P.b5[0];
+        for (int t = 0; t < H / 32; ++t) o += P.outp[(long long)t * P.B + r];
+        P.out[r] = o;
+        const float d = o - P.y[r];
+        P.obar[r] = 2.0f * d * P.inv_b;
+        P.loss_rows[r] = d * d * P.inv_b;
+    }
+    tc::cluster_sync();
+    for (int l = 0; l < 3; ++l) stage(P.t[l], H, kClusterBN, true, col0);
+    stage(P.t1, H, NX, rank == 0, 0);
+    for (int l = 0; l < 3; ++l) stage(P.r[l], l == 0 ? KX : H, kClusterBN, true, col0);
+    stage(P.r4, H, kClusterBN, true, col0);
+    for (int l = 0; l < 3; ++l) stage(P.d[l], H, kClusterBN, true, col0);
+    tc::pdl_trigger();
+    tc::chain_teardown(c);
+    if (!ok && threadIdx.x == 0 && P.err) atomicExch(P.err, 1);
+}
+
 // Column sums in a fixed order, coalesced, in two passes.  Pass 1: block
 // (q, c) covers 32 consecutive columns of one source over row chunk c of
 // kColChunk rows; lane = column, the 8 warps take rows r0 + w, r0 + w + 8, ...
@@ -776,7 +833,7 @@ void drop_graph(TrainGraph &tg) {
 // The row chain of the training step (F1..F4, T4..T1, R1..R4, D4..D2 and their input and output
 // row work) as one chain_kernel launch of B/128 CTAs.
 cudaError_t chain_impl(mlp_ctx *c, const float *prm, const float *X, const float *y, const float *dy, float alpha,
-                       cudaStream_t st) {
+                       cudaStream_t st, bool cluster) {
     Bufs &b = c->b;
     const int B = b.B;
     const long long B2 = 2LL * B;
@@ -787,7 +844,7 @@ cudaError_t chain_impl(mlp_ctx *c, const float *prm, const float *X, const float
     int s = 0;
     auto stage_maps = [&](const bf16 *A, int K, const bf16 *Bw, int N) {
         if (e == cudaSuccess) e = tc::make_map(&P.a[s], A, K, K, B, tc::kBM);
-        if (e == cudaSuccess) e = tc::make_map(&P.b[s], Bw, K, K, N, N);
+        if (e == cudaSuccess) e = tc::make_map(&P.b[s], Bw, K, K, N, cluster && N > kClusterBN ? kClusterBN : N);
         ++s;
     };
     for (int l = 1; l <= 3; ++l) {
@@ -828,17 +885,36 @@ cudaError_t chain_impl(mlp_ctx *c, const float *prm, const float *X, const float
     P.B = B;
     P.B2 = B2;
     P.err = b.err;
-    static bool attr_set[64] = {false};
+    static bool attr_set[2][64] = {{false}};
     int dev = 0;
     e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= 64 || !attr_set[dev]) {
-        e = cudaFuncSetAttribute(chain_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)tc::chain_smem_bytes());
+    const size_t smem = cluster ? tc::chain_smem_bytes(kClusterBN) : tc::chain_smem_bytes();
+    if (dev < 0 || dev >= 64 || !attr_set[cluster][dev]) {
+        e = cudaFuncSetAttribute(cluster ? chain_cluster_kernel : chain_kernel,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        if (dev >= 0 && dev < 64) attr_set[dev] = true;
+        if (dev >= 0 && dev < 64) attr_set[cluster][dev] = true;
     }
-    e = launch_pdl(chain_kernel, dim3(B / tc::kBM), dim3(tc::kThreads), tc::chain_smem_bytes(), st, P);
+    if (!cluster) {
+        e = launch_pdl(chain_kernel, dim3(B / tc::kBM), dim3(tc::kThreads), smem, st, P);
+    } else {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((B / tc::kBM) * kClusterCtas);
+        cfg.blockDim = dim3(tc::kThreads);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = st;
+        cudaLaunchAttribute at[2];
+        at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        at[0].val.programmaticStreamSerializationAllowed = 1;
+        at[1].id = cudaLaunchAttributeClusterDimension;
+        at[1].val.clusterDim.x = kClusterCtas;
+        at[1].val.clusterDim.y = 1;
+        at[1].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 2;
+        e = cudaLaunchKernelEx(&cfg, chain_cluster_kernel, P);
+    }
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
@@ -849,10 +925,12 @@ cudaError_t loss_grad_impl(mlp_ctx *c, const float *params, const float *X, cons
     const int B = b.B;
     const long long B2 = 2LL * B;
     cudaError_t e = cudaSuccess;
-    // MCAAD_MLP_CHAIN=1: the row chain as one chain_kernel launch (measured slower, see chain_kernel)
-    const bool chain = env_knob("MCAAD_MLP_CHAIN") > 0;
+    // MCAAD_MLP_CHAIN=1: the row chain as one chain_kernel launch (measured slower, see
+    // chain_kernel); 2: as one chain_cluster_kernel launch
+    const int chain_mode = env_knob("MCAAD_MLP_CHAIN");
+    const bool chain = chain_mode == 1 || chain_mode == 2;
     if (chain) {
-        e = chain_impl(c, params, X, y, dy, alpha, st);
+        e = chain_impl(c, params, X, y, dy, alpha, st, chain_mode == 2);
     } else {
         e = launch_pdl(prep_input_kernel, dim3(grid_for((long long)B * DIN)), dim3(256), 0, st, X, B, B, b.x0,
                        b.Bop[1], B2);

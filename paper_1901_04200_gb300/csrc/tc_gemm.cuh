@@ -344,26 +344,32 @@ __device__ __forceinline__ void gemm_body(const TensorMaps &tm, const GemmShape 
 // barriers and 256 columns of tensor memory are set up once, and the ring's slot and phase run on
 // across stages (k-block g of the chain uses slot g % kStages).  Between stages the CTA waits for
 // the epilogue's stores (generic proxy) to be visible to the next stage's TMA loads (async proxy).
-// Shared memory: chain_smem_bytes().  A stage with an expired wait sets `fail`; the caller stops
-// running stages (every thread sees the flag after the stage's closing barrier).
+// A chain whose stages are at most `bn` columns wide (the B tile's rows; 256 when one CTA takes a
+// whole layer, 32 when a cluster of CTAs splits its columns) needs chain_smem_bytes(bn) of shared
+// memory.  A stage with an expired wait sets `fail`; the caller stops running stages (every thread
+// sees the flag after the stage's closing barrier).
 constexpr int kChainBN = 256;
-__host__ __device__ constexpr size_t chain_smem_bytes() { return smem_bytes(kChainBN, kStages); }
+__host__ __device__ constexpr size_t chain_smem_bytes(int bn = kChainBN) { return smem_bytes(bn, kStages); }
 
 struct Chain {
     unsigned char *base, *tA, *tB;
     uint32_t full0, empty0, done, tmem;
     volatile int *fail;
+    int bn;      // the widest stage: B slot rows and tensor-memory columns
     int kbg;     // k-blocks issued by earlier stages
     int stages;  // stages run (the done barrier's phase)
 };
 
+__host__ __device__ constexpr uint32_t tmem_cols(int bn) { return bn <= 32 ? 32u : (bn <= 64 ? 64u : (bn <= 128 ? 128u : 256u)); }
+
 // All threads: carve the ring, initialise the barriers, allocate the tensor memory.
-__device__ __forceinline__ void chain_setup(Chain &c) {
+__device__ __forceinline__ void chain_setup(Chain &c, int bn = kChainBN) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
+    c.bn = bn;
     c.base = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     c.tA = c.base;
     c.tB = c.base + (size_t)kStages * tile_a_bytes();
-    uint64_t *bars = (uint64_t *)(c.tB + (size_t)kStages * tile_b_bytes(kChainBN));
+    uint64_t *bars = (uint64_t *)(c.tB + (size_t)kStages * tile_b_bytes(bn));
     uint32_t *tslot = (uint32_t *)(bars + 2 * kStages + 1);
     c.fail = (volatile int *)(tslot + 1);
     c.full0 = smem_u32(bars);
@@ -374,7 +380,7 @@ __device__ __forceinline__ void chain_setup(Chain &c) {
     const int tid = threadIdx.x;
     if (tid / 32 == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
-                     "r"((uint32_t)kChainBN));
+                     "r"(tmem_cols(bn)));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
@@ -392,14 +398,14 @@ __device__ __forceinline__ void chain_setup(Chain &c) {
     c.tmem = *tslot;
 }
 
-// One stage: D[row0 .. row0+127][0 .. N) = A[rows][0 .. K) B[0 .. N)[0 .. K)^T (K a multiple of
-// 64, at most kStages * 64 = 256; N a multiple of 16, at most 256; the B map's box is N rows),
-// then the epilogue as in gemm_body (Epi::kColumns: lane j
+// One stage: D[row0 .. row0+127][col0 .. col0+N) = A[rows][0 .. K) B[col0 .. col0+N)[0 .. K)^T (K a
+// multiple of 64, at most kStages * 64 = 256; N a multiple of 16, at most the chain's bn; the B
+// map's box is N rows), then the epilogue as in gemm_body (Epi::kColumns: lane j
 // of a warp gets column c0 + j of the warp's 32 rows; else each thread its row).  Returns false
 // (and sets the chain's fail flag) if a wait expired.
 template <class Epi>
 __device__ __forceinline__ bool chain_stage(Chain &c, const CUtensorMap *ma, const CUtensorMap *mb, int K, int N,
-                                            int row0, const Epi &epi) {
+                                            int row0, const Epi &epi, int col0 = 0) {
     const int tid = threadIdx.x, warp = tid / 32, lane = tid % 32;
     const int kbt = K / kBK;
     const uint32_t stage_bytes = (uint32_t)(tile_a_bytes() + tile_b_bytes(N));
@@ -415,7 +421,7 @@ __device__ __forceinline__ bool chain_stage(Chain &c, const CUtensorMap *ma, con
                 }
                 mbar_arrive_expect_tx(c.full0 + 8 * s, stage_bytes);
                 tma_load_2d(smem_u32(c.tA + (size_t)s * tile_a_bytes()), ma, kb * kBK, row0, c.full0 + 8 * s);
-                tma_load_2d(smem_u32(c.tB + (size_t)s * tile_b_bytes(kChainBN)), mb, kb * kBK, 0, c.full0 + 8 * s);
+                tma_load_2d(smem_u32(c.tB + (size_t)s * tile_b_bytes(c.bn)), mb, kb * kBK, col0, c.full0 + 8 * s);
                 ++issued;
             }
             // no load in flight when the stage ends (bounded; K <= kStages * kBK, so each slot holds
@@ -438,7 +444,7 @@ __device__ __forceinline__ bool chain_stage(Chain &c, const CUtensorMap *ma, con
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t a0 = smem_u32(c.tA + (size_t)s * tile_a_bytes());
-                const uint32_t b0 = smem_u32(c.tB + (size_t)s * tile_b_bytes(kChainBN));
+                const uint32_t b0 = smem_u32(c.tB + (size_t)s * tile_b_bytes(c.bn));
 #pragma unroll
                 for (int k = 0; k < kBK / 16; ++k)
                     mma_bf16(c.tmem, desc_sw128(a0 + k * 32), desc_sw128(b0 + k * 32), idesc,
@@ -469,7 +475,7 @@ __device__ __forceinline__ bool chain_stage(Chain &c, const CUtensorMap *ma, con
 #pragma unroll
                 for (int r = 0; r < 32; ++r) u[r] = stage[r * 33 + lane];
                 __syncwarp();
-                epi.apply_cols(row0 + warp * 32, c0 + lane, u, lane < N - c0, 0, lane);
+                epi.apply_cols(row0 + warp * 32, col0 + c0 + lane, u, lane < N - c0, 0, lane);
             }
         } else {
             const int row = row0 + warp * 32 + lane;
@@ -478,7 +484,7 @@ __device__ __forceinline__ bool chain_stage(Chain &c, const CUtensorMap *ma, con
                 float v[32];
                 if (N - c0 >= 32) tmem_ld32(trow + (uint32_t)c0, v);
                 else tmem_ld16(trow + (uint32_t)c0, v);
-                epi.apply((long long)row, c0, v, (N - c0) < 32 ? (N - c0) : 32, 0, state);
+                epi.apply((long long)row, col0 + c0, v, (N - c0) < 32 ? (N - c0) : 32, 0, state);
             }
         }
     }
@@ -497,8 +503,22 @@ __device__ __forceinline__ void chain_teardown(Chain &c) {
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (threadIdx.x / 32 == 0) {
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(c.tmem), "r"((uint32_t)kChainBN));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(c.tmem), "r"(tmem_cols(c.bn)));
     }
+}
+
+// All threads of every CTA of the cluster: a barrier that also orders memory (release before
+// arriving, acquire after waiting), then the acquired global data made visible to this thread's
+// later TMA loads.  Every CTA of a cluster must call it the same number of times.
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+    asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
 }
 
 // Host: the TMA descriptor of a BF16 operand stored as `rows` rows of `cols` elements (K

@@ -81,11 +81,13 @@ def test_loss_grad_matches_oracle(L, alpha, B):
     assert rel(gv, gr) <= 2e-3
 
 
+@pytest.mark.parametrize("mode", ["1", "2"])
 @pytest.mark.parametrize("B", [128, 4096])
-def test_row_chain_kernel_matches_oracle(L, B, monkeypatch):
-    """The opt-in single-launch row chain (MCAAD_MLP_CHAIN=1: F, T, R, D of each 128-row block in
-    one CTA) gives the loss gradient of the per-GEMM path."""
-    monkeypatch.setenv("MCAAD_MLP_CHAIN", "1")
+def test_row_chain_kernel_matches_oracle(L, B, mode, monkeypatch):
+    """The opt-in single-launch row chains (MCAAD_MLP_CHAIN=1: F, T, R, D of each 128-row block in
+    one CTA; 2: in a cluster of eight CTAs, 32 columns each) match the oracle as the per-GEMM path
+    does."""
+    monkeypatch.setenv("MCAAD_MLP_CHAIN", mode)
     p, X, y, dy = setup(B, seed=5)
     net = L.Mlp(B)
     prm = cuda32(omlp.flatten(p))
