@@ -63,3 +63,26 @@ def test_measured_traffic_only_for_the_profiled_sources(monkeypatch):
     assert bench.measured_traffic("heston", "normals", 4, 2, "forward_sweep") is None
     monkeypatch.setattr(bench, "kernel_sources_hash", lambda model="heston": "another version")
     assert bench.measured_traffic(*key) is None
+
+
+def test_local_vol_kernel_parts_by_storage():
+    """Local vol: the stored-states reverse sweep runs the adjoint alone (Rs), its checkpoint
+    reverse sweep re-runs each segment with the surface from the node table (Fn) and then runs the
+    same adjoint; the other models' checkpoint reverse sweeps re-run F and its tape adjoint R."""
+    ops = lambda part: sum(bench.OPS["lv"][part].values())  # noqa: E731
+    assert bench.kernel_ops("lv", "states", "reverse_sweep") == ops("Rs")
+    assert bench.kernel_ops("lv", "checkpoint", "reverse_sweep") == ops("Fn") + ops("Rs")
+    assert bench.kernel_ops("lv", "checkpoint", "forward_sweep") == ops("F")
+    assert ops("Fn") == ops("F") + 2
+    assert bench.kernel_ops("heston", "checkpoint", "reverse_sweep") == (
+        sum(bench.OPS["heston"]["F"].values()) + sum(bench.OPS["heston"]["R"].values()))
+    # stored states: 4 B per path-step and the final state once per 500 steps
+    assert bench.kernel_bytes("lv", "states", 5, 500, 20)["reverse_sweep"] == 4.0 + 4.0 / 500
+
+
+def test_kernel_sources_hash_covers_the_model_table():
+    """The hash that keys measured traffic reads every file the kernels are built from."""
+    files = bench.KERNEL_SOURCES + bench.MODEL_SOURCE["lv"]
+    assert "mc_paths_lv.cuh" in files and "mc_paths.cuh" in files
+    for f in files:
+        assert os.path.exists(os.path.join(ROOT, "paper_1901_04200_gb300", "csrc", f)), f
