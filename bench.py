@@ -492,7 +492,7 @@ def tape_bench(args, rank, world):
             "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"]}}))
 
 
-def calibration_experiment(cases, epochs=40, label_paths=1 << 16, n_theta=16384):
+def calibration_experiment(cases, epochs=40, label_paths=1 << 16, n_theta=16384, label_steps_per_year=256):
     """Surrogate labels and training (the learned part), then Heston calibration to
     G < 1e-8 at 2^22 paths: surrogate-assisted vs plain MC-AAD descent from the same starts."""
     import numpy as np
@@ -500,10 +500,12 @@ def calibration_experiment(cases, epochs=40, label_paths=1 << 16, n_theta=16384)
 
     from paper_1901_04200_gb300 import _lib, calibrate, inputs, surrogate
     pb = inputs.heston_config().problem
+    # the labels' time grid (the maturities lie on every grid that divides a quarter year)
+    pb_labels = pb if label_steps_per_year == 256 else inputs.heston_config(steps_per_year=label_steps_per_year).problem
     n_paths = label_paths
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    X, y, dy = surrogate.make_dataset(pb, n_theta, n_paths)
+    X, y, dy = surrogate.make_dataset(pb_labels, n_theta, n_paths)
     torch.cuda.synchronize()
     t_data = time.perf_counter() - t0
     sur = surrogate.Surrogate(batch=4096)
@@ -546,7 +548,8 @@ def calibration_experiment(cases, epochs=40, label_paths=1 << 16, n_theta=16384)
             "all_cases_note": "medians and means over all cases; a case that stops before G < tol (evaluation "
                               "cap or a stalled line search) counts at its stopping time, a lower bound on its "
                               "time to tolerance",
-            "labels": {"samples": n_samples, "paths_per_sample": n_paths, "seconds": t_data},
+            "labels": {"samples": n_samples, "paths_per_sample": n_paths, "steps": int(pb_labels.n_steps),
+                       "seconds": t_data},
             "training": {"epochs": epochs, "batch": 4096, "seconds": t_train,
                          "samples_per_s": epochs * (n_samples // 4096) * 4096 / t_train},
             "plain": dict(ps, method="L-BFGS-B on MC-AAD G and grad G, restarts, 300 evaluations"),
@@ -877,6 +880,8 @@ def main():
     ap.add_argument("--calib-cases", type=int, default=16)
     ap.add_argument("--calib-epochs", type=int, default=40, help="surrogate training epochs")
     ap.add_argument("--calib-label-paths", type=int, default=1 << 16, help="MC paths per surrogate label")
+    ap.add_argument("--calib-label-steps-per-year", type=int, default=256,
+                    help="time grid of the surrogate labels (the calibration itself runs at 256)")
     ap.add_argument("--calib-thetas", type=int, default=16384,
                     help="parameter draws for the surrogate labels (64 instruments each)")
     ap.add_argument("--ckpt", type=int, default=0, help="checkpoint interval (0 = workload default)")
@@ -916,7 +921,7 @@ def main():
             line["workloads"][r["config"]["workload"]] = r
     if rank == 0 and not args.no_calibration and world == 1:
         line["calibration"] = calibration_experiment(args.calib_cases, args.calib_epochs, args.calib_label_paths,
-                                                     args.calib_thetas)
+                                                     args.calib_thetas, args.calib_label_steps_per_year)
     if rank == 0:
         print(json.dumps(line))
     if world > 1:

@@ -189,8 +189,8 @@ def lv_config(n_paths: int = 1 << 22, n_steps: int = 500, T: float = 5.0, nt: in
               ckpt_every: int = 5, paths_per_thread: int = 4) -> Workload:
     """Bilinear local-vol surface over (t, ln S/S0); FP32 path arithmetic.  Segments of 5
     steps with four paths per thread: the fastest launch shape measured on 2^22 x 500 with the
-    stored states the library picks for local vol (7.5 ms per value and gradient, against 8.1 ms
-    with two paths per thread and 8.5 ms with stored normals)."""
+    stored states the library picks for local vol (7.1 ms per value and gradient; with two paths
+    per thread it measured 8.1 ms and with stored normals 8.5 ms, in earlier builds)."""
     dt = T / n_steps
     steps = (np.arange(1, n_mat + 1) * (n_steps // n_mat)).astype(np.int32)
     strikes = np.linspace(60.0, 150.0, n_strike)
