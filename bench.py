@@ -108,17 +108,17 @@ def kernel_bytes(model, storage, K, S, n_groups):
 # sources' code (comments and layout aside) hashes to the captured version.  Key: (model,
 # storage, K, paths per thread, kernel).
 MEASURED_TRAFFIC = {
-    # stored states, 2^20 of 2^22 paths (x 4): read 2.119408 GB + write 15.876 MB; read 0.525 MB + write 2.054665 GB
-    ("lv", "states", 5, 4, "reverse_sweep"): {"bytes": 8541136000, "sources": "ffbc6dfb4fe77cd3"},
-    ("lv", "states", 5, 4, "forward_sweep"): {"bytes": 8218760000, "sources": "ffbc6dfb4fe77cd3"},
+    # stored states, 2^20 of 2^22 paths (x 4): read 2.118220 GB + write 14.198 MB; read 0.536 MB + write 2.054537 GB
+    ("lv", "states", 5, 4, "reverse_sweep"): {"bytes": 8529672000, "sources": "6263506f6fa9e9c9"},
+    ("lv", "states", 5, 4, "forward_sweep"): {"bytes": 8218292000, "sources": "6263506f6fa9e9c9"},
     # checkpoints every 25 steps, two paths per thread (the recompute arm), 2^21 of 2^22 paths (x 2):
-    # read 336.460 MB + write 42.971 MB; read 0.306 MB + write 327.616 MB (each 4-row checkpoint
+    # read 335.837 MB + write 39.257 MB; read 0.134 MB + write 326.978 MB (each 4-row checkpoint
     # group holds the two path slots and two padding rows, twice the algorithmic bytes)
-    ("lv", "checkpoint", 25, 2, "reverse_sweep"): {"bytes": 758862000, "sources": "ffbc6dfb4fe77cd3"},
-    ("lv", "checkpoint", 25, 2, "forward_sweep"): {"bytes": 655844000, "sources": "ffbc6dfb4fe77cd3"},
-    # stored normals, 2^18 of 2^20 paths (x 4): read 1.208088 GB + write 3.704 MB; read 0.082 MB + write 1.148862 GB
-    ("heston", "normals", 8, 2, "reverse_sweep"): {"bytes": 4847168000, "sources": "3b9af2d7af9e1186"},
-    ("heston", "normals", 8, 2, "forward_sweep"): {"bytes": 4595776000, "sources": "3b9af2d7af9e1186"},
+    ("lv", "checkpoint", 25, 2, "reverse_sweep"): {"bytes": 750189000, "sources": "6263506f6fa9e9c9"},
+    ("lv", "checkpoint", 25, 2, "forward_sweep"): {"bytes": 654223000, "sources": "6263506f6fa9e9c9"},
+    # stored normals, 2^18 of 2^20 paths (x 4): read 1.208061 GB + write 0.248 MB; read 0.066 MB + write 1.148159 GB
+    ("heston", "normals", 8, 2, "reverse_sweep"): {"bytes": 4833235000, "sources": "882aaba6c5a33637"},
+    ("heston", "normals", 8, 2, "forward_sweep"): {"bytes": 4592903000, "sources": "882aaba6c5a33637"},
 }
 KERNEL_SOURCES = ["mc_common.cuh", "mc_paths.cuh"]
 MODEL_SOURCE = {"gbm": ["mc_paths_gbm.cu"], "heston": ["mc_paths_heston.cu"],

@@ -491,17 +491,19 @@ struct LvModel {
     // step x1 = x0 + r dt + h z - h^2 / 2 (h = sigma sqrt(dt)) gives
     // d x1 / d h = z - h = (x1 - x0 - r dt - h^2 / 2) / h,
     // so the adjoint needs neither the normal nor a re-run of the step (sigma != 0).
-    __device__ __forceinline__ static void adjoint_states(const State &s0, const State &s1, int n, Real &xb, Real &,
-                                                          Acc &a, const Par &p, const Shared &sh) {
-        const Real u = scaled(s0.x, p);
-        int c;
-        Real b;
-        bool inside;
-        cell(u, p, c, b, inside);
+    // The time cell's node pairs at x cells c and c+1: h = a0 + at d0 at node c, a1 + at d1 at c+1.
+    struct NodePair { Real a0, d0, a1, d1; };
+    __device__ __forceinline__ static NodePair node_pair(const Shared &sh, int jt, int c) {
         using P2 = typename std::conditional<sizeof(Real) == 4, float2, double2>::type;
-        const P2 *nd = (const P2 *)sh.node + a.jt * sh.nx + c;  // the time cell's node pairs (a.jt, a.at: step n)
+        const P2 *nd = (const P2 *)sh.node + jt * sh.nx + c;
         const P2 n0 = nd[0], n1 = nd[1];
-        const Real v0 = fma(a.at, n0.y, n0.x), v1 = fma(a.at, n1.y, n1.x);
+        return NodePair{n0.x, n0.y, n1.x, n1.y};
+    }
+    // Shared body of the two forms below, given the step's cell and its node pairs.
+    __device__ __forceinline__ static void adjoint_states_with(const State &s0, const State &s1, int c, Real b,
+                                                               bool inside, const NodePair &q, Real &xb, Acc &a,
+                                                               const Par &p, const Shared &sh) {
+        const Real v0 = fma(a.at, q.d0, q.a0), v1 = fma(a.at, q.d1, q.a1);
         const Real dh = v1 - v0;
         const Real h = fma(b, dh, v0);
         const Real dxdh = fma(Real(-0.5) * h, h, s1.x - s0.x - p.rdt) * recip_r<Real>(h);
@@ -510,6 +512,37 @@ struct LvModel {
         add_node(sh, a, c, g0);
         add_node(sh, a, c + 1, g1);
         if (inside) xb = fma(hb * p.inv_hx, dh, xb);
+    }
+    __device__ __forceinline__ static void adjoint_states(const State &s0, const State &s1, int n, Real &xb, Real &,
+                                                          Acc &a, const Par &p, const Shared &sh) {
+        const Real u = scaled(s0.x, p);
+        int c;
+        Real b;
+        bool inside;
+        cell(u, p, c, b, inside);
+        adjoint_states_with(s0, s1, c, b, inside, node_pair(sh, a.jt, c), xb, a, p, sh);  // (a.jt, a.at: step n)
+    }
+    // The same with the last node pairs a path slot read kept in registers: a path stays in its cell
+    // for most steps, so the reload (a shared-memory read by the lanes whose cell or time cell
+    // changed) is predicated off for most lanes, and the warp's read costs one wavefront instead
+    // of two per pair.
+    struct NodeCache {
+        int key;  // jt * 64 + c of the pairs held (nx <= kMaxNx = 32), -1 for none
+        NodePair q;
+    };
+    __device__ __forceinline__ static void adjoint_states_cached(const State &s0, const State &s1, Real &xb, Acc &a,
+                                                                 const Par &p, const Shared &sh, NodeCache &nc) {
+        const Real u = scaled(s0.x, p);
+        int c;
+        Real b;
+        bool inside;
+        cell(u, p, c, b, inside);
+        const int key = a.jt * 64 + c;
+        if (key != nc.key) {
+            nc.q = node_pair(sh, a.jt, c);
+            nc.key = key;
+        }
+        adjoint_states_with(s0, s1, c, b, inside, nc.q, xb, a, p, sh);
     }
     __device__ static void acc_end(Acc &a, Real, const Par &, const Shared &sh, double *wacc, int lane) {
         flush_rows(a, sh, wacc, lane);
@@ -1214,7 +1247,9 @@ __global__ void __launch_bounds__(kBlock) path_forward_states_kernel(const DevPr
 // while the previous runs: payoff seeds at the segment's end state, then the adjoints of its
 // steps backwards from (state before, state after).
 template <class Md, int K, int PPT>
-__global__ void __launch_bounds__(kBlock) path_reverse_states_kernel(const DevProblem pb, const DevCall cl) {
+// Compiled for five resident blocks per SM (96 registers, no spills); unbounded, the node caches
+// take it to 121 registers and four blocks, measured slower (3.62 against 3.48 ms).
+__global__ void __launch_bounds__(kBlock, 5) path_reverse_states_kernel(const DevProblem pb, const DevCall cl) {
     using Real = typename Md::Real;
     using ZS = SegTile<Md, K, PPT, 2>;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -1244,11 +1279,13 @@ __global__ void __launch_bounds__(kBlock) path_reverse_states_kernel(const DevPr
         bool active[PPT];
         Real xb[PPT], vb[PPT];
         typename Md::State nx_[PPT];  // the state after the segment being processed
+        typename Md::NodeCache ncache[PPT];
 #pragma unroll
         for (int q = 0; q < PPT; ++q) {
             active[q] = ch * kChunk + q * kWarp + lane < cl.n_paths;
             xb[q] = Real(0);
             vb[q] = Real(0);
+            ncache[q].key = -1;
         }
         // the final states (extra tile, buffer n_seg & 1), and the last segment behind it
         ZS::issue(zstage, cl.ckpt, ch, ws_chunks, pb.n_seg, lane);
@@ -1306,7 +1343,7 @@ __global__ void __launch_bounds__(kBlock) path_reverse_states_kernel(const DevPr
                     constexpr int kG = ZS::kG;
                     cur.x = ZS::V::get(grp[ZS::srow(i, 0, q) / kG], ZS::srow(i, 0, q) % kG);
                     if constexpr (Md::SD == 2) cur.v = ZS::V::get(grp[ZS::srow(i, 1, q) / kG], ZS::srow(i, 1, q) % kG);
-                    Md::adjoint_states(cur, nx_[q], n, xb[q], vb[q], acc, par, sh);
+                    Md::adjoint_states_cached(cur, nx_[q], xb[q], acc, par, sh, ncache[q]);
                     nx_[q] = cur;
                 }
             }
