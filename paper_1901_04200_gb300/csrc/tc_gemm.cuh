@@ -21,7 +21,8 @@
 //     tcgen05.ld and hands them to the epilogue functor.
 // Every mbarrier wait has an iteration limit; on expiry the kernel records an
 // error code, waits (again with a limit) for the loads it issued, frees its
-// tensor memory and returns.
+// tensor memory and returns.  The same pieces also run a chain of GEMMs in one
+// CTA (tc::Chain, below).
 #pragma once
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -339,10 +340,11 @@ __device__ __forceinline__ void gemm_body(const TensorMaps &tm, const GemmShape 
 }
 
 // ---------------------------------------------------------------- chains --
-// A CTA that runs a sequence of GEMMs over its own 128 rows (D_s[128 x N_s] = A_s B_s^T, every
-// N_s <= 256 in one tile), each stage's epilogue writing what later stages read: the ring, its
-// barriers and 256 columns of tensor memory are set up once, and the ring's slot and phase run on
-// across stages (k-block g of the chain uses slot g % kStages).  Between stages the CTA waits for
+// A CTA that runs a sequence of GEMMs over its own 128 rows (D_s[128 x N_s] = A_s B_s^T, each
+// stage one tile of at most the chain's `bn` columns, from column col0), each stage's epilogue
+// writing what later stages read: the ring, its barriers and the tensor memory are set up once,
+// and the ring's slot and phase run on across stages (k-block g of the chain uses slot
+// g % kStages).  Between stages the CTA waits for
 // the epilogue's stores (generic proxy) to be visible to the next stage's TMA loads (async proxy).
 // A chain whose stages are at most `bn` columns wide (the B tile's rows; 256 when one CTA takes a
 // whole layer, 32 when a cluster of CTAs splits its columns) needs chain_smem_bytes(bn) of shared
